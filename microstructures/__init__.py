@@ -1,0 +1,290 @@
+"""Seeded synthetic microstructures for the periodic scalar-conductivity cell problem.
+
+This module only describes and samples geometry: a periodic cell, an odd grid size
+N, a matrix phase A0 and a list of non-overlapping inclusions (boxes, balls/disks)
+with absolute SPD phase tensors. It holds none of the homogenisation arithmetic
+(no Fourier coefficients, no projections, no bounds). Both the CPU oracle and the
+GPU library's Python binding read these descriptions.
+
+Geometry model (Vondrejc-Zeman-Marek, Sec. 6, Eq. A_with_inclusions):
+    A(x) = A0 + sum_j f_j(x - x_j) (A_j - A0)
+with f_j the indicator of a box (Remark "inclusion") or a ball, extended
+periodically. The phases are given as absolute tensors A_j (a reading of the
+paper's increments, which are A_j - A0).
+
+Workload recipes (the paper uses no public dataset for these workloads):
+  * square_inclusion_2d  - centred square, side 0.6 of a unit cell, a = 1 / 10, N = 23.
+  * cube_inclusion_3d    - centred cube, side 0.5 of a unit cell, a = 1 / 100, N = 41.
+  * random_rectangles_2d - 1..16 non-overlapping axis-aligned rectangles, volume
+                           fraction U(0.1, 0.5), inclusion conductivity log-uniform in
+                           [1e-2, 1e3] over a matrix of 1, N drawn from {23, 63, 113, 203}.
+  * random_spheres_3d    - 16 equal non-overlapping balls, volume fraction 0.3,
+                           contrast 1000, N = 113.
+  * paper_square_2d      - the paper's Sec. 7 cell (-1, 1)^2 with |x_a| < 3/5 and
+                           A = (1 + rho f) I.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+from typing import List, Sequence
+
+import numpy as np
+
+BOX = "box"
+BALL = "ball"   # a disk when d == 2
+
+
+@dataclasses.dataclass
+class Inclusion:
+    shape: str                 # BOX or BALL
+    center: np.ndarray         # (d,)
+    size: np.ndarray           # BOX: side lengths h (d,); BALL: (radius,)
+    A: np.ndarray              # (d, d) absolute SPD phase tensor inside the inclusion
+
+    def volume(self) -> float:
+        d = self.center.shape[0]
+        if self.shape == BOX:
+            return float(np.prod(self.size))
+        r = float(self.size[0])
+        return math.pi * r * r if d == 2 else 4.0 / 3.0 * math.pi * r ** 3
+
+
+@dataclasses.dataclass
+class Problem:
+    d: int
+    Y: np.ndarray              # (d,) cell side lengths, cell = prod (-Y/2, Y/2)
+    N: np.ndarray              # (d,) odd grid sizes
+    A0: np.ndarray             # (d, d) matrix phase
+    inclusions: List[Inclusion]
+
+    @property
+    def M(self) -> np.ndarray:
+        """Double-grid size 2N - 1 per axis."""
+        return 2 * self.N - 1
+
+    def with_N(self, N) -> "Problem":
+        N = np.broadcast_to(np.asarray(N, dtype=np.int64), (self.d,)).copy()
+        return dataclasses.replace(self, N=N)
+
+    def volume_fraction(self) -> float:
+        return sum(inc.volume() for inc in self.inclusions) / float(np.prod(self.Y))
+
+    def is_isotropic(self) -> bool:
+        def iso(A):
+            return np.allclose(A, A[0, 0] * np.eye(self.d), rtol=0, atol=0)
+        return iso(self.A0) and all(iso(inc.A) for inc in self.inclusions)
+
+
+def _vec(x, d):
+    return np.broadcast_to(np.asarray(x, dtype=np.float64), (d,)).copy()
+
+
+def make_problem(d, N, Y=1.0, a0=1.0, inclusions=()) -> Problem:
+    A0 = np.asarray(a0, dtype=np.float64)
+    if A0.ndim == 0:
+        A0 = float(A0) * np.eye(d)
+    return Problem(d=d, Y=_vec(Y, d), N=np.broadcast_to(np.asarray(N, dtype=np.int64), (d,)).copy(),
+                   A0=A0, inclusions=list(inclusions))
+
+
+def box(center, h, a, d) -> Inclusion:
+    A = np.asarray(a, dtype=np.float64)
+    if A.ndim == 0:
+        A = float(A) * np.eye(d)
+    return Inclusion(BOX, _vec(center, d), _vec(h, d), A)
+
+
+def ball(center, radius, a, d) -> Inclusion:
+    A = np.asarray(a, dtype=np.float64)
+    if A.ndim == 0:
+        A = float(A) * np.eye(d)
+    return Inclusion(BALL, _vec(center, d), np.array([float(radius)]), A)
+
+
+# ----------------------------------------------------------------------------------
+# fixed workloads
+# ----------------------------------------------------------------------------------
+def square_inclusion_2d(N=23, side=0.6, a_matrix=1.0, a_incl=10.0) -> Problem:
+    """Unit cell, one centred square inclusion (2D, d = 2)."""
+    return make_problem(2, N, 1.0, a_matrix, [box(0.0, side, a_incl, 2)])
+
+
+def cube_inclusion_3d(N=41, side=0.5, a_matrix=1.0, a_incl=100.0) -> Problem:
+    """Unit cell, one centred cube inclusion (3D, d = 3)."""
+    return make_problem(3, N, 1.0, a_matrix, [box(0.0, side, a_incl, 3)])
+
+
+def paper_square_2d(N, rho) -> Problem:
+    """Cell (-1, 1)^2 with A = (1 + rho f) I and f the indicator of |x_a| < 3/5 (Sec. 7)."""
+    return make_problem(2, N, 2.0, 1.0, [box(0.0, 1.2, 1.0 + rho, 2)])
+
+
+def laminate_2d(N, width=0.4, a_matrix=1.0, a_incl=10.0, Y=1.0) -> Problem:
+    """A stripe of the inclusion phase across the whole cell height: layers normal to x1."""
+    Yv = _vec(Y, 2)
+    return make_problem(2, N, Yv, a_matrix, [box(0.0, (width * Yv[0], Yv[1]), a_incl, 2)])
+
+
+def checkerboard_2d(N, a1=1.0, a2=5.0, Y=1.0) -> Problem:
+    """Two-phase checkerboard: two quarter-cell squares of phase a2 on a matrix a1."""
+    Yv = _vec(Y, 2)
+    q = Yv / 4.0
+    return make_problem(2, N, Yv, a1, [box(-q, Yv / 2, a2, 2), box(q, Yv / 2, a2, 2)])
+
+
+def homogeneous(d, N, A0) -> Problem:
+    return make_problem(d, N, 1.0, A0, [])
+
+
+# ----------------------------------------------------------------------------------
+# periodic overlap tests (geometry only)
+# ----------------------------------------------------------------------------------
+def _pdist(a, b, Y):
+    """Periodic (minimum-image) per-axis distance."""
+    t = np.abs(np.asarray(a) - np.asarray(b))
+    return np.minimum(t, Y - t)
+
+
+def inclusions_overlap(p: Inclusion, q: Inclusion, Y, gap=0.0) -> bool:
+    """True when two inclusions share an open set in the periodic cell.
+
+    Touching is allowed (the interface has measure zero). ``gap`` widens both
+    inclusions, so that ``gap > 0`` also rejects near-contacts.
+    """
+    Y = np.asarray(Y, dtype=np.float64)
+    dist = _pdist(p.center, q.center, Y)
+    if p.shape == BOX and q.shape == BOX:
+        return bool(np.all(dist < 0.5 * (p.size + q.size) + gap))
+    if p.shape == BALL and q.shape == BALL:
+        return bool(np.sqrt(np.sum(dist ** 2)) < p.size[0] + q.size[0] + gap)
+    bx, bl = (p, q) if p.shape == BOX else (q, p)
+    dist = _pdist(bx.center, bl.center, Y)
+    outside = np.maximum(dist - 0.5 * bx.size, 0.0)
+    return bool(np.sqrt(np.sum(outside ** 2)) < bl.size[0] + gap)
+
+
+def fits_cell(inc: Inclusion, Y) -> bool:
+    """An inclusion must not overlap its own periodic images."""
+    Y = np.asarray(Y, dtype=np.float64)
+    if inc.shape == BOX:
+        return bool(np.all(inc.size <= Y))
+    return bool(2.0 * inc.size[0] <= np.min(Y))
+
+
+# ----------------------------------------------------------------------------------
+# random workloads
+# ----------------------------------------------------------------------------------
+RANDOM_RECT_N = (23, 63, 113, 203)
+
+
+def random_rectangles_2d(seed: int, N=None, max_restarts=200) -> Problem:
+    """Seeded random-rectangle cell (matrix a = 1, unit cell).
+
+    Draws, in this order: N from {23, 63, 113, 203} (unless given), the number of
+    rectangles J ~ U{1..16}, the volume fraction phi ~ U(0.1, 0.5), one inclusion
+    conductivity a ~ 10^U(-2, 3) shared by all rectangles, a Dirichlet(1) split of
+    phi over the J rectangles, and per rectangle an aspect ratio log-uniform in
+    [1/4, 4] and a uniform centre. Rectangles are placed by rejection with a
+    periodic clearance of 1e-3; a failed layout restarts with a new split.
+    """
+    rng = np.random.default_rng(np.random.SeedSequence([0x5EC7, int(seed)]))
+    if N is None:
+        N = int(rng.choice(RANDOM_RECT_N))
+    J = int(rng.integers(1, 17))
+    phi = float(rng.uniform(0.1, 0.5))
+    a_incl = float(10.0 ** rng.uniform(-2.0, 3.0))
+    Y = np.ones(2)
+    for _ in range(max_restarts):
+        w = rng.dirichlet(np.ones(J))
+        areas = phi * w
+        placed: List[Inclusion] = []
+        ok = True
+        for area in sorted(areas, reverse=True):
+            rho = float(np.exp(rng.uniform(np.log(0.25), np.log(4.0))))
+            h = np.array([math.sqrt(area * rho), math.sqrt(area / rho)])
+            h = np.minimum(h, 0.95)
+            for _attempt in range(400):
+                c = rng.uniform(-0.5, 0.5, size=2)
+                cand = box(c, h, a_incl, 2)
+                if not any(inclusions_overlap(cand, o, Y, gap=1e-3) for o in placed):
+                    placed.append(cand)
+                    break
+            else:
+                ok = False
+                break
+        if ok:
+            return make_problem(2, N, Y, 1.0, placed)
+    raise RuntimeError(f"random_rectangles_2d: no layout found for seed {seed}")
+
+
+def random_spheres_3d(seed: int, N=113, n_balls=16, phi=0.3, contrast=1000.0,
+                      max_restarts=200) -> Problem:
+    """Seeded random sequential addition of equal balls in the unit cube.
+
+    Radius R = (3 phi / (4 pi n))^(1/3); periodic centre distance >= 2R + 1e-3;
+    matrix a = 1, balls a = contrast.
+    """
+    rng = np.random.default_rng(np.random.SeedSequence([0xB411, int(seed)]))
+    R = (3.0 * phi / (4.0 * math.pi * n_balls)) ** (1.0 / 3.0)
+    Y = np.ones(3)
+    for _ in range(max_restarts):
+        placed: List[Inclusion] = []
+        for _i in range(n_balls):
+            for _attempt in range(2000):
+                cand = ball(rng.uniform(-0.5, 0.5, size=3), R, contrast, 3)
+                if not any(inclusions_overlap(cand, o, Y, gap=1e-3) for o in placed):
+                    placed.append(cand)
+                    break
+            else:
+                break
+        if len(placed) == n_balls:
+            return make_problem(3, N, Y, 1.0, placed)
+    raise RuntimeError(f"random_spheres_3d: no packing found for seed {seed}")
+
+
+def random_anisotropic_2d(seed: int, N=7, n_boxes=2) -> Problem:
+    """Small anisotropic test cell: SPD A0 and SPD box phases with random rotations."""
+    rng = np.random.default_rng(np.random.SeedSequence([0xA150, int(seed)]))
+
+    def spd():
+        t = rng.uniform(0, math.pi)
+        Rm = np.array([[math.cos(t), -math.sin(t)], [math.sin(t), math.cos(t)]])
+        lam = 10.0 ** rng.uniform(-1, 1, size=2)
+        return Rm @ np.diag(lam) @ Rm.T
+
+    Y = np.array([1.0, float(rng.uniform(0.7, 1.4))])
+    placed: List[Inclusion] = []
+    while len(placed) < n_boxes:
+        h = rng.uniform(0.15, 0.45, size=2) * Y
+        cand = box(rng.uniform(-0.5, 0.5, size=2) * Y, h, spd(), 2)
+        if not any(inclusions_overlap(cand, o, Y, gap=1e-3) for o in placed):
+            placed.append(cand)
+    return make_problem(2, N, Y, spd(), placed)
+
+
+def random_anisotropic_3d(seed: int, N=5, n_incl=2) -> Problem:
+    """Small anisotropic 3D test cell with one box and one ball (when n_incl >= 2)."""
+    rng = np.random.default_rng(np.random.SeedSequence([0xA153, int(seed)]))
+
+    def spd():
+        Q, _ = np.linalg.qr(rng.normal(size=(3, 3)))
+        lam = 10.0 ** rng.uniform(-1, 1, size=3)
+        return Q @ np.diag(lam) @ Q.T
+
+    Y = np.array([1.0, float(rng.uniform(0.8, 1.25)), float(rng.uniform(0.8, 1.25))])
+    placed: List[Inclusion] = []
+    k = 0
+    while len(placed) < n_incl:
+        if k % 2 == 0:
+            cand = box(rng.uniform(-0.5, 0.5, size=3) * Y, rng.uniform(0.2, 0.45, size=3) * Y, spd(), 3)
+        else:
+            cand = ball(rng.uniform(-0.5, 0.5, size=3) * Y, float(rng.uniform(0.1, 0.2)), spd(), 3)
+        if not any(inclusions_overlap(cand, o, Y, gap=1e-3) for o in placed):
+            placed.append(cand)
+            k += 1
+    return make_problem(3, N, Y, spd(), placed)
+
+
+def batch_rectangles_2d(seeds: Sequence[int], N=None) -> List[Problem]:
+    return [random_rectangles_2d(s, N=N) for s in seeds]
