@@ -1,0 +1,199 @@
+/*
+ * homb.h - C ABI of the GB300 library for guaranteed upper-lower bounds on the
+ * homogenized conductivity matrix A_H of a periodic matrix-inclusion composite,
+ * computed by the FFT-based Galerkin method with exact (double-grid) integration
+ * (J. Vondrejc, J. Zeman, I. Marek, "Guaranteed upper-lower bounds on homogenized
+ * properties by FFT-based Galerkin method").
+ *
+ * The problem statement follows the paper:
+ *   cell Y = prod_a (-Y_a/2, Y_a/2), odd grid N (Eq. N_odd), coefficient
+ *   A(x) = A0 + sum_j f_j(x - x_j) (A_j - A0)            (Eq. A_with_inclusions)
+ *   with f_j the indicator of a box (Remark "inclusion") or a ball/disk;
+ *   upper bound  A_up[a][b] = a(e_b + e^(b), e_a + e^(a)), e^(a) in E_N minimising
+ *   the energy; lower bound inv(B_up) from the dual fields in J_N
+ *   (Def. upper_lower_bounds, Eqs. GaNi_bounds / approx_homog_with_error);
+ *   the Galerkin fields are found by conjugate gradients (Sec. 6.1) whose matvec
+ *   zero-pads to the 2N-1 grid, transforms, multiplies by the double-grid
+ *   coefficient A_{2N-1} (Lemma double-grid, Eq. MBA_GA; Lemma
+ *   bounds_for_matrix-inclusion) and projects with Gamma^E or Gamma^J (Def. projection).
+ *
+ * Conventions shared by every entry point
+ *   - Every function returns hom_status; no exception crosses the ABI.
+ *   - Host inputs are read during the call only; the library keeps no caller pointer.
+ *   - Device memory: the library never allocates device memory. Every device buffer
+ *     (workspace, fields, coefficients) is owned by the caller (e.g. a torch tensor)
+ *     and must stay valid until the work queued on `stream` has finished. Pointers
+ *     given as `void* d_...` are device pointers, 256-byte aligned.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *     hom_bounds / hom_bounds_batched synchronise `stream` before returning; the
+ *     step-level calls (hom_coefficient ... hom_energy) only enqueue work.
+ *   - A hom_ctx is bound to one device and is not thread-safe; use one per thread.
+ *
+ * Axis convention: coordinate x_1 (index 0) is the fastest-varying memory axis.
+ *
+ * Device field layout ("half spectrum"): a set of R vector fields with C = d
+ * components each, stored as interleaved complex numbers (double2 for FP64,
+ * float2 for FP32), index [r][c][k3][k2][k1] (2D: [r][c][k2][k1]) with
+ *   k1 in [0, (N1+1)/2)          (non-negative frequencies only, Hermitian symmetry
+ *                                 u(-k) = conj u(k) gives the rest),
+ *   k2 in [0, N2), k3 in [0, N3) (FFT order: index i is frequency i for
+ *                                 i <= (N-1)/2, else i - N).
+ * Coefficient layout: real, [q][j3][j2][j1] on the double grid M = 2N-1, j in [0, M)
+ * (grid point x = Y j / M, periodic), q over `ncomp` components: 1 for isotropic
+ * phases (a scalar field), else the symmetric tensor packed (11,22,12) in 2D and
+ * (11,22,33,23,13,12) in 3D.
+ */
+#ifndef HOMB_H
+#define HOMB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  HOM_OK = 0,
+  HOM_WARN_NOT_CONVERGED = 1,  /* max_iter reached: the returned bounds are still
+                                  guaranteed (any conforming field gives a bound,
+                                  Lemma bounds), only looser                      */
+  HOM_ERR_INVALID_ARG = -1,    /* even N, d not 2/3, non-SPD phase, overlapping or
+                                  oversized inclusion, NULL pointer, bad sizes    */
+  HOM_ERR_BREAKDOWN = -2,      /* CG breakdown: NaN/Inf or p.Cp <= 0              */
+  HOM_ERR_CUDA = -3,           /* a CUDA runtime call failed (see hom_last_error) */
+  HOM_ERR_WORKSPACE = -4,      /* workspace smaller than hom_workspace_size      */
+  HOM_ERR_NOT_SPD_RESULT = -6  /* dual energy matrix not invertible              */
+} hom_status;
+
+typedef enum { HOM_BOX = 0, HOM_BALL = 1 /* disk when d == 2 */ } hom_shape;
+typedef enum { HOM_FP64 = 0, HOM_MIXED = 1 /* FP32 inner CG, FP64 scalars/bounds */,
+               HOM_FP32 = 2 /* step-level calls only */ } hom_precision;
+typedef enum { HOM_PRIMAL = 0 /* A, Gamma^E: upper bound */,
+               HOM_DUAL = 1   /* A^{-1}, Gamma^J: lower bound */ } hom_side;
+
+typedef struct {
+  int32_t shape;       /* hom_shape                                              */
+  int32_t reserved;
+  double center[3];    /* x_j                                                    */
+  double size[3];      /* HOM_BOX: side lengths h (0 < h_a <= Y_a);
+                          HOM_BALL: size[0] = radius (2R <= min Y_a)            */
+  double A[9];         /* absolute SPD phase tensor, row-major, leading dim 3   */
+} hom_inclusion;
+
+typedef struct {
+  int32_t d;                   /* 2 or 3                                         */
+  int32_t N[3];                /* odd grid sizes N_a, a < d                      */
+  double Y[3];                 /* cell side lengths Y_a > 0                      */
+  double A0[9];                /* matrix phase, SPD, row-major, leading dim 3    */
+  int32_t n_incl;              /* number of inclusions (may be 0)                */
+  int32_t reserved;
+  const hom_inclusion* incl;   /* host array [n_incl]; inclusions must not
+                                  overlap (touching is allowed)                 */
+} hom_problem;
+
+typedef struct {
+  int32_t precision;    /* hom_precision: HOM_FP64 or HOM_MIXED                  */
+  int32_t max_iter;     /* per solve; <= 0 selects 10000                         */
+  double tol;           /* stop when ||r_i|| <= tol ||E|| (Remark "Convergence
+                           criteria", Parseval L2 norm); <= 0 selects 1e-8       */
+  int32_t check_every;  /* host polls convergence every k iterations; 0 -> 8     */
+  int32_t sides;        /* bit 0: primal (upper), bit 1: dual (lower); 0 -> both */
+} hom_opts;
+
+typedef struct {
+  int32_t iters[2][3];  /* [side][rhs] CG iterations                             */
+  double resid[2][3];   /* [side][rhs] final recursive residual / ||E||          */
+  int32_t matvecs;      /* operator applications issued (all rhs together)       */
+  int32_t status[2][3]; /* per solve: 0 converged, 1 max_iter, -2 breakdown      */
+  double ms_total;      /* host wall time of the call                            */
+} hom_report;
+
+typedef struct hom_ctx hom_ctx;
+
+/* Context bound to `device` (cudaSetDevice is called inside each entry point).
+ * Allocates only host memory (a small pinned staging buffer). */
+hom_status hom_create(hom_ctx** ctx, int device);
+hom_status hom_destroy(hom_ctx* ctx);
+/* Last error message of this context (static storage of the context; "" if none). */
+const char* hom_last_error(const hom_ctx* ctx);
+/* Library version string, e.g. "homb 0.1". */
+const char* hom_version(void);
+
+/* Sizes for a problem: ncomp (coefficient components), M[3] (double grid, 1 for
+ * unused axes), field_elems = complex elements of ONE component of ONE field in
+ * the half-spectrum layout, grid_elems = prod M. Validates the problem. */
+hom_status hom_problem_info(hom_ctx* ctx, const hom_problem* prob, int32_t* ncomp,
+                            int32_t M[3], int64_t* field_elems, int64_t* grid_elems);
+
+/* Bytes of device workspace hom_bounds needs for this problem and options. */
+hom_status hom_workspace_size(hom_ctx* ctx, const hom_problem* prob, const hom_opts* opts,
+                              size_t* bytes);
+
+/* Whole pipeline (Algorithm of Sec. 6.2 with the exact double-grid operator in CG):
+ * build both double-grid coefficients once, run d primal and d dual CG solves from
+ * x0 = 0, re-project the fields in FP64 and evaluate the bound energies exactly on
+ * the double grid. Outputs are host arrays, d x d row-major with leading dim d;
+ * any of upper/lower/mean/D/rep may be NULL. lower = inv(B_up); mean = (upper +
+ * lower)/2; D = (upper - lower)/2 (Eq. approx_homog_with_error). With `sides` not
+ * both, the missing outputs are left untouched. */
+hom_status hom_bounds(hom_ctx* ctx, const hom_problem* prob, const hom_opts* opts,
+                      void* d_workspace, size_t workspace_bytes, void* stream,
+                      double* upper, double* lower, double* mean, double* D,
+                      hom_report* rep);
+
+/* Step-level entry points (device buffers; enqueue only). Workspace for these is
+ * hom_step_workspace_size. */
+hom_status hom_step_workspace_size(hom_ctx* ctx, const hom_problem* prob, int32_t nrhs,
+                                   size_t* bytes);
+
+/* Double-grid coefficient A_{2N-1}(x_j) = sum_{n in Z_{2N-1}} w^{jn} A_hat(n) (Eq. MBA_GA)
+ * of the primal (A) or dual (A^{-1}) side from the closed-form inclusion
+ * coefficients (Lemma bounds_for_matrix-inclusion). d_coef: real, coefficient
+ * layout above, FP64 (precision HOM_FP64) or FP32 (HOM_FP32: computed in FP64,
+ * rounded). */
+hom_status hom_coefficient(hom_ctx* ctx, const hom_problem* prob, int32_t side,
+                           int32_t precision, void* d_coef, void* d_workspace,
+                           size_t workspace_bytes, void* stream);
+
+/* Right-hand sides b_r = -Gamma(k) A_hat(k) e_r, r < nrhs <= d (Eq. linear_system_primal /
+ * _dual with E = e_r), in the half-spectrum layout, precision HOM_FP64 or HOM_FP32. */
+hom_status hom_rhs(hom_ctx* ctx, const hom_problem* prob, int32_t side, int32_t precision,
+                   int32_t nrhs, void* d_b, void* d_workspace, size_t workspace_bytes,
+                   void* stream);
+
+/* Galerkin operator on nrhs fields: d_out = Gamma P_N F_M (A_M/|M|) F_M^{-1} Pad(d_in)
+ * (project = 1) or without Gamma (project = 0). d_coef from hom_coefficient in the
+ * same precision; d_in / d_out half-spectrum fields [nrhs][d]... (must not alias). */
+hom_status hom_matvec(hom_ctx* ctx, const hom_problem* prob, int32_t side, int32_t precision,
+                      int32_t project, int32_t nrhs, const void* d_coef, const void* d_in,
+                      void* d_out, void* d_workspace, size_t workspace_bytes, void* stream);
+
+/* Energy matrix W[r][s] = a(u_s, u_r) with u_r = e_r + x_r (add_constant = 1) or
+ * u_r = x_r (add_constant = 0), evaluated exactly on the double grid
+ * (Lemma double-grid): (1/|M|) sum_j u_r(x_j) . A_M(x_j) u_s(x_j). FP64 only;
+ * d_x: [nrhs][d] half-spectrum FP64; W: host, nrhs x nrhs row-major. Synchronises
+ * `stream`. */
+hom_status hom_energy(hom_ctx* ctx, const hom_problem* prob, int32_t nrhs,
+                      int32_t add_constant, const void* d_coef, const void* d_x, double* W,
+                      void* d_workspace, size_t workspace_bytes, void* stream);
+
+/* Batched 1D FFT of `howmany` contiguous complex sequences of odd length M
+ * (any factorisation; radix-3/5 and generic odd-prime butterflies):
+ * out[j] = sum_k in[k] exp(dir * 2 pi i j k / M), dir = -1 (forward) or +1
+ * (inverse), no normalisation. FP64 (double2) or FP32 (float2). */
+hom_status hom_fft(hom_ctx* ctx, int32_t M, int32_t precision, int32_t dir, int32_t howmany,
+                   const void* d_in, void* d_out, void* d_workspace, size_t workspace_bytes,
+                   void* stream);  /* workspace >= 16*M bytes (twiddle table) */
+
+/* Kernel timing (CUDA events around each launch of one kernel family on the
+ * launching stream). name: "zpass", "ypass", "xpass", "final", "cg", "coef", or ""
+ * to disable. hom_kernel_timing returns launches and total milliseconds since the
+ * last hom_profile_kernel call (synchronises the events). */
+hom_status hom_profile_kernel(hom_ctx* ctx, const char* name);
+hom_status hom_kernel_timing(hom_ctx* ctx, int64_t* launches, double* total_ms);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HOMB_H */

@@ -1,0 +1,253 @@
+"""ctypes binding of libhomb (include/homb.h): argument marshalling only.
+
+Every entry point keeps the C name. The functions take host structures built from a
+``microstructures.Problem`` and raw device pointers (``tensor.data_ptr()``); torch is
+used by callers only to own device memory and streams. There is no CPU fallback: if
+the shared library cannot be loaded, importing the binding raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libhomb.so")
+
+HOM_OK = 0
+HOM_WARN_NOT_CONVERGED = 1
+HOM_ERR_INVALID_ARG = -1
+HOM_ERR_BREAKDOWN = -2
+HOM_ERR_CUDA = -3
+HOM_ERR_WORKSPACE = -4
+HOM_ERR_NOT_SPD_RESULT = -6
+
+HOM_BOX, HOM_BALL = 0, 1
+HOM_FP64, HOM_MIXED, HOM_FP32 = 0, 1, 2
+HOM_PRIMAL, HOM_DUAL = 0, 1
+
+
+class hom_inclusion(C.Structure):
+    _fields_ = [("shape", C.c_int32), ("reserved", C.c_int32), ("center", C.c_double * 3),
+                ("size", C.c_double * 3), ("A", C.c_double * 9)]
+
+
+class hom_problem(C.Structure):
+    _fields_ = [("d", C.c_int32), ("N", C.c_int32 * 3), ("Y", C.c_double * 3), ("A0", C.c_double * 9),
+                ("n_incl", C.c_int32), ("reserved", C.c_int32), ("incl", C.POINTER(hom_inclusion))]
+
+
+class hom_opts(C.Structure):
+    _fields_ = [("precision", C.c_int32), ("max_iter", C.c_int32), ("tol", C.c_double),
+                ("check_every", C.c_int32), ("sides", C.c_int32)]
+
+
+class hom_report(C.Structure):
+    _fields_ = [("iters", (C.c_int32 * 3) * 2), ("resid", (C.c_double * 3) * 2), ("matvecs", C.c_int32),
+                ("status", (C.c_int32 * 3) * 2), ("ms_total", C.c_double)]
+
+
+class HombError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"homb status {status}: {msg}")
+        self.status = status
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"libhomb.so not built at {LIB_PATH}; run __graft_entry__.build()")
+    lib = C.CDLL(LIB_PATH)
+    vp, sz, i32, i64, dp = C.c_void_p, C.c_size_t, C.c_int32, C.c_int64, C.POINTER(C.c_double)
+    P = C.POINTER
+    sigs = {
+        "hom_create": (i32, [P(vp), C.c_int]),
+        "hom_destroy": (i32, [vp]),
+        "hom_last_error": (C.c_char_p, [vp]),
+        "hom_version": (C.c_char_p, []),
+        "hom_problem_info": (i32, [vp, P(hom_problem), P(i32), P(i32), P(i64), P(i64)]),
+        "hom_workspace_size": (i32, [vp, P(hom_problem), P(hom_opts), P(sz)]),
+        "hom_bounds": (i32, [vp, P(hom_problem), P(hom_opts), vp, sz, vp, dp, dp, dp, dp, P(hom_report)]),
+        "hom_step_workspace_size": (i32, [vp, P(hom_problem), i32, P(sz)]),
+        "hom_coefficient": (i32, [vp, P(hom_problem), i32, i32, vp, vp, sz, vp]),
+        "hom_rhs": (i32, [vp, P(hom_problem), i32, i32, i32, vp, vp, sz, vp]),
+        "hom_matvec": (i32, [vp, P(hom_problem), i32, i32, i32, i32, vp, vp, vp, vp, sz, vp]),
+        "hom_energy": (i32, [vp, P(hom_problem), i32, i32, vp, vp, dp, vp, sz, vp]),
+        "hom_fft": (i32, [vp, i32, i32, i32, i32, vp, vp, vp, sz, vp]),
+        "hom_profile_kernel": (i32, [vp, C.c_char_p]),
+        "hom_kernel_timing": (i32, [vp, P(i64), dp]),
+    }
+    for name, (res, args) in sigs.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
+lib = _load()
+
+
+def declared_symbols():
+    """Names of the functions the C header declares (parsed from include/homb.h)."""
+    import re
+    hdr = os.path.join(os.path.dirname(HERE), "include", "homb.h")
+    src = open(hdr).read()
+    return sorted(set(re.findall(r"^(?:hom_status|const char\*)\s+(hom_\w+)\s*\(", src, re.M)))
+
+
+# ------------------------------------------------------------------------------------
+# marshalling helpers
+# ------------------------------------------------------------------------------------
+def _mat3(A, d):
+    out = np.zeros((3, 3))
+    out[:d, :d] = np.asarray(A, dtype=np.float64)
+    return out.reshape(-1)
+
+
+def problem_struct(problem):
+    """hom_problem from a microstructures.Problem. Returns (struct, keepalive)."""
+    d = int(problem.d)
+    n = len(problem.inclusions)
+    arr = (hom_inclusion * max(n, 1))()
+    for i, inc in enumerate(problem.inclusions):
+        s = arr[i]
+        s.shape = HOM_BOX if inc.shape == "box" else HOM_BALL
+        c = np.zeros(3)
+        c[:d] = inc.center
+        sz = np.zeros(3)
+        sz[:len(inc.size)] = inc.size
+        s.center[:] = list(c)
+        s.size[:] = list(sz)
+        s.A[:] = list(_mat3(inc.A, d))
+    p = hom_problem()
+    p.d = d
+    N = np.ones(3, dtype=np.int64)
+    N[:d] = problem.N
+    Y = np.ones(3)
+    Y[:d] = problem.Y
+    p.N[:] = [int(v) for v in N]
+    p.Y[:] = [float(v) for v in Y]
+    p.A0[:] = list(_mat3(problem.A0, d))
+    p.n_incl = n
+    p.incl = C.cast(arr, C.POINTER(hom_inclusion))
+    return p, arr
+
+
+def check(ctx, status, allow_warn=True):
+    if status == HOM_OK or (allow_warn and status == HOM_WARN_NOT_CONVERGED):
+        return status
+    msg = lib.hom_last_error(ctx).decode() if ctx else ""
+    raise HombError(status, msg)
+
+
+def hom_create(device=0):
+    h = C.c_void_p()
+    st = lib.hom_create(C.byref(h), int(device))
+    if st != HOM_OK:
+        raise HombError(st, "hom_create failed (no CUDA device?)")
+    return h
+
+
+def hom_destroy(ctx):
+    return lib.hom_destroy(ctx)
+
+
+def hom_version():
+    return lib.hom_version().decode()
+
+
+def hom_last_error(ctx):
+    return lib.hom_last_error(ctx).decode()
+
+
+def hom_problem_info(ctx, problem):
+    p, keep = problem_struct(problem)
+    ncomp = C.c_int32()
+    M = (C.c_int32 * 3)()
+    fe = C.c_int64()
+    ge = C.c_int64()
+    check(ctx, lib.hom_problem_info(ctx, C.byref(p), C.byref(ncomp), M, C.byref(fe), C.byref(ge)))
+    return {"ncomp": ncomp.value, "M": list(M), "field_elems": fe.value, "grid_elems": ge.value}
+
+
+def make_opts(precision=HOM_FP64, tol=1e-8, max_iter=10000, check_every=8, sides=3):
+    o = hom_opts()
+    o.precision, o.tol, o.max_iter, o.check_every, o.sides = precision, tol, max_iter, check_every, sides
+    return o
+
+
+def hom_workspace_size(ctx, problem, opts):
+    p, keep = problem_struct(problem)
+    n = C.c_size_t()
+    check(ctx, lib.hom_workspace_size(ctx, C.byref(p), C.byref(opts), C.byref(n)))
+    return n.value
+
+
+def hom_step_workspace_size(ctx, problem, nrhs):
+    p, keep = problem_struct(problem)
+    n = C.c_size_t()
+    check(ctx, lib.hom_step_workspace_size(ctx, C.byref(p), int(nrhs), C.byref(n)))
+    return n.value
+
+
+def hom_bounds(ctx, problem, opts, d_ws, ws_bytes, stream=0):
+    """Returns dict(upper, lower, mean, D, report, status) with d x d numpy arrays."""
+    p, keep = problem_struct(problem)
+    d = int(problem.d)
+    bufs = {k: (C.c_double * (d * d))() for k in ("upper", "lower", "mean", "D")}
+    rep = hom_report()
+    st = lib.hom_bounds(ctx, C.byref(p), C.byref(opts), C.c_void_p(d_ws), ws_bytes, C.c_void_p(stream),
+                        bufs["upper"], bufs["lower"], bufs["mean"], bufs["D"], C.byref(rep))
+    check(ctx, st)
+    out = {k: np.array(v[:]).reshape(d, d) for k, v in bufs.items()}
+    out["status"] = st
+    out["report"] = {
+        "iters": [list(rep.iters[s]) for s in range(2)],
+        "resid": [list(rep.resid[s]) for s in range(2)],
+        "status": [list(rep.status[s]) for s in range(2)],
+        "matvecs": rep.matvecs, "ms_total": rep.ms_total,
+    }
+    return out
+
+
+def hom_coefficient(ctx, problem, side, precision, d_coef, d_ws, ws_bytes, stream=0):
+    p, keep = problem_struct(problem)
+    return check(ctx, lib.hom_coefficient(ctx, C.byref(p), side, precision, C.c_void_p(d_coef),
+                                          C.c_void_p(d_ws), ws_bytes, C.c_void_p(stream)))
+
+
+def hom_rhs(ctx, problem, side, precision, nrhs, d_b, d_ws, ws_bytes, stream=0):
+    p, keep = problem_struct(problem)
+    return check(ctx, lib.hom_rhs(ctx, C.byref(p), side, precision, nrhs, C.c_void_p(d_b),
+                                  C.c_void_p(d_ws), ws_bytes, C.c_void_p(stream)))
+
+
+def hom_matvec(ctx, problem, side, precision, project, nrhs, d_coef, d_in, d_out, d_ws, ws_bytes, stream=0):
+    p, keep = problem_struct(problem)
+    return check(ctx, lib.hom_matvec(ctx, C.byref(p), side, precision, project, nrhs, C.c_void_p(d_coef),
+                                     C.c_void_p(d_in), C.c_void_p(d_out), C.c_void_p(d_ws), ws_bytes,
+                                     C.c_void_p(stream)))
+
+
+def hom_energy(ctx, problem, nrhs, add_constant, d_coef, d_x, d_ws, ws_bytes, stream=0):
+    p, keep = problem_struct(problem)
+    W = (C.c_double * (nrhs * nrhs))()
+    check(ctx, lib.hom_energy(ctx, C.byref(p), nrhs, add_constant, C.c_void_p(d_coef), C.c_void_p(d_x), W,
+                              C.c_void_p(d_ws), ws_bytes, C.c_void_p(stream)))
+    return np.array(W[:]).reshape(nrhs, nrhs)
+
+
+def hom_fft(ctx, M, precision, direction, howmany, d_in, d_out, d_ws, ws_bytes, stream=0):
+    return check(ctx, lib.hom_fft(ctx, M, precision, direction, howmany, C.c_void_p(d_in), C.c_void_p(d_out),
+                                  C.c_void_p(d_ws), ws_bytes, C.c_void_p(stream)))
+
+
+def hom_profile_kernel(ctx, name):
+    return check(ctx, lib.hom_profile_kernel(ctx, (name or "").encode()))
+
+
+def hom_kernel_timing(ctx):
+    n = C.c_int64()
+    ms = C.c_double()
+    check(ctx, lib.hom_kernel_timing(ctx, C.byref(n), C.byref(ms)))
+    return n.value, ms.value

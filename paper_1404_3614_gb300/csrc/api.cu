@@ -1,0 +1,922 @@
+// C ABI (include/homb.h): problem validation, plans, workspace layout and the
+// orchestration of the guaranteed-bounds pipeline on one GPU.
+//
+// Pipeline per side (Algorithm of Sec. 6.2, with the exact double-grid operator of
+// Lemma double-grid inside CG as the Galerkin method without numerical integration):
+//   1. closed-form Fourier coefficients on Z_{2N-1} (Lemma bounds_for_matrix-inclusion)
+//      -> inverse FFT -> A_{2N-1}(x_j) (Eq. MBA_GA), once per problem;
+//   2. d right-hand sides b = -Gamma A_hat(k) e_a (Eq. linear_system_primal / _dual),
+//      solved together by d independent CG recurrences sharing every operator pass;
+//   3. FP64 re-projection of the fields and the exact double-grid energies
+//      (Def. upper_lower_bounds) -> upper = A_bar, lower = inv(B_bar).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/homb.h"
+#include "kernels.cuh"
+
+using namespace homb;
+
+struct hom_ctx {
+  int device = 0;
+  std::string err;
+  CgScalars* host_cg = nullptr;        // pinned staging for convergence polls
+  double* host_e = nullptr;            // pinned staging for energies
+  std::string prof_family;
+  std::vector<cudaEvent_t> ev;         // start/stop pairs
+  size_t ev_used = 0;
+};
+
+namespace {
+
+constexpr int kVecBlocks = 304;   // 2 x 152 SMs for the elementwise CG kernels
+
+#define CK(expr)                                                                               \
+  do {                                                                                         \
+    cudaError_t _e = (expr);                                                                   \
+    if (_e != cudaSuccess) {                                                                   \
+      char _b[256];                                                                            \
+      snprintf(_b, sizeof _b, "%s:%d: %s (%s)", __FILE__, __LINE__, cudaGetErrorString(_e), #expr); \
+      ctx->err = _b;                                                                           \
+      return HOM_ERR_CUDA;                                                                     \
+    }                                                                                          \
+  } while (0)
+
+#define CKS(expr)                                                                              \
+  do {                                                                                         \
+    hom_status _s = (expr);                                                                    \
+    if (_s != HOM_OK) return _s;                                                               \
+  } while (0)
+
+hom_status fail(hom_ctx* ctx, hom_status s, const std::string& msg) {
+  if (ctx) ctx->err = msg;
+  return s;
+}
+
+// ---------------------------------------------------------------------------------
+// geometry / validation
+// ---------------------------------------------------------------------------------
+struct Geometry {
+  int d = 2;
+  int N[3] = {1, 1, 1};
+  int M[3] = {1, 1, 1};
+  int Nh = 1;       // (N1 + 1)/2
+  int Nxs = 1;      // (M1 + 1)/2 = N1: half range of the coefficient spectrum
+  double Y[3] = {1, 1, 1};
+  double invY[3] = {1, 1, 1};
+  int ncomp = 1;
+  long long field = 0;   // Nz*Ny*Nh
+  long long planes = 0;  // Mz*My
+  long long grid = 0;    // Mz*My*Mx
+  long long spec = 0;    // Mz*My*Nxs
+  double A0[3][3];
+  std::vector<hom_inclusion> incl;
+  FftPlan plan[3];
+};
+
+bool spd(const double* A, int d) {
+  // symmetric and Cholesky-positive (leading dim 3)
+  for (int i = 0; i < d; ++i)
+    for (int j = 0; j < d; ++j) {
+      const double a = A[3 * i + j], b = A[3 * j + i];
+      if (!std::isfinite(a) || std::fabs(a - b) > 1e-12 * (std::fabs(a) + std::fabs(b) + 1e-300)) return false;
+    }
+  double L[3][3] = {};
+  for (int i = 0; i < d; ++i)
+    for (int j = 0; j <= i; ++j) {
+      double s = A[3 * i + j];
+      for (int k = 0; k < j; ++k) s -= L[i][k] * L[j][k];
+      if (i == j) {
+        if (!(s > 0)) return false;
+        L[i][i] = std::sqrt(s);
+      } else {
+        L[i][j] = s / L[j][j];
+      }
+    }
+  return true;
+}
+
+bool isotropic(const double* A, int d) {
+  for (int i = 0; i < d; ++i)
+    for (int j = 0; j < d; ++j)
+      if (i != j ? A[3 * i + j] != 0.0 : A[3 * i + i] != A[0]) return false;
+  return true;
+}
+
+void inv3(const double* A, int d, double* out) {  // leading dim 3
+  if (d == 2) {
+    const double det = A[0] * A[4] - A[1] * A[3];
+    out[0] = A[4] / det; out[1] = -A[1] / det; out[3] = -A[3] / det; out[4] = A[0] / det;
+    return;
+  }
+  const double a = A[0], b = A[1], c = A[2], e = A[3], f = A[4], g = A[5], h = A[6], i = A[7], k = A[8];
+  const double det = a * (f * k - g * i) - b * (e * k - g * h) + c * (e * i - f * h);
+  out[0] = (f * k - g * i) / det; out[1] = (c * i - b * k) / det; out[2] = (b * g - c * f) / det;
+  out[3] = (g * h - e * k) / det; out[4] = (a * k - c * h) / det; out[5] = (c * e - a * g) / det;
+  out[6] = (e * i - f * h) / det; out[7] = (b * h - a * i) / det; out[8] = (a * f - b * e) / det;
+}
+
+double pdist(double a, double b, double Y) {
+  double t = std::fabs(a - b);
+  t = std::fmod(t, Y);
+  return std::min(t, Y - t);
+}
+
+bool overlap(const hom_inclusion& p, const hom_inclusion& q, const double* Y, int d) {
+  double dist[3];
+  for (int a = 0; a < d; ++a) dist[a] = pdist(p.center[a], q.center[a], Y[a]);
+  if (p.shape == HOM_BOX && q.shape == HOM_BOX) {
+    for (int a = 0; a < d; ++a)
+      if (!(dist[a] < 0.5 * (p.size[a] + q.size[a]))) return false;
+    return true;
+  }
+  if (p.shape == HOM_BALL && q.shape == HOM_BALL) {
+    double s = 0;
+    for (int a = 0; a < d; ++a) s += dist[a] * dist[a];
+    return std::sqrt(s) < p.size[0] + q.size[0];
+  }
+  const hom_inclusion& bx = p.shape == HOM_BOX ? p : q;
+  const hom_inclusion& bl = p.shape == HOM_BOX ? q : p;
+  double s = 0;
+  for (int a = 0; a < d; ++a) {
+    const double o = std::max(pdist(bx.center[a], bl.center[a], Y[a]) - 0.5 * bx.size[a], 0.0);
+    s += o * o;
+  }
+  return std::sqrt(s) < bl.size[0];
+}
+
+void make_plan(int M, FftPlan& p) {
+  p.M = M;
+  p.nrad = 0;
+  int m = M;
+  const int small[] = {5, 3, 7, 11, 13};
+  for (int r : small)
+    while (m % r == 0 && p.nrad < kMaxRadices) { p.radix[p.nrad++] = r; m /= r; }
+  for (int r = 17; m > 1; r += 2)
+    while (m % r == 0 && p.nrad < kMaxRadices) { p.radix[p.nrad++] = r; m /= r; }
+}
+
+hom_status build_geometry(hom_ctx* ctx, const hom_problem* P, Geometry& g) {
+  if (!P) return fail(ctx, HOM_ERR_INVALID_ARG, "problem is NULL");
+  if (P->d != 2 && P->d != 3) return fail(ctx, HOM_ERR_INVALID_ARG, "d must be 2 or 3");
+  g.d = P->d;
+  for (int a = 0; a < 3; ++a) {
+    g.N[a] = a < g.d ? P->N[a] : 1;
+    g.Y[a] = a < g.d ? P->Y[a] : 1.0;
+    if (a < g.d) {
+      if (g.N[a] < 1 || g.N[a] % 2 != 1) return fail(ctx, HOM_ERR_INVALID_ARG, "grid sizes N must be odd and >= 1");
+      if (g.N[a] > 2049) return fail(ctx, HOM_ERR_INVALID_ARG, "grid size N too large (max 2049)");
+      if (!(g.Y[a] > 0) || !std::isfinite(g.Y[a])) return fail(ctx, HOM_ERR_INVALID_ARG, "cell sizes Y must be > 0");
+    }
+    g.M[a] = 2 * g.N[a] - 1;
+    g.invY[a] = 1.0 / g.Y[a];
+  }
+  g.Nh = (g.N[0] + 1) / 2;
+  g.Nxs = (g.M[0] + 1) / 2;
+  if (!spd(P->A0, g.d)) return fail(ctx, HOM_ERR_INVALID_ARG, "A0 is not symmetric positive definite");
+  if (P->n_incl < 0 || (P->n_incl > 0 && !P->incl)) return fail(ctx, HOM_ERR_INVALID_ARG, "bad inclusion list");
+  if (P->n_incl > 4096) return fail(ctx, HOM_ERR_INVALID_ARG, "too many inclusions (max 4096)");
+  g.incl.assign(P->incl, P->incl + P->n_incl);
+  bool iso = isotropic(P->A0, g.d);
+  double minY = g.Y[0];
+  for (int a = 1; a < g.d; ++a) minY = std::min(minY, g.Y[a]);
+  for (size_t j = 0; j < g.incl.size(); ++j) {
+    const hom_inclusion& I = g.incl[j];
+    if (I.shape != HOM_BOX && I.shape != HOM_BALL) return fail(ctx, HOM_ERR_INVALID_ARG, "unknown inclusion shape");
+    if (!spd(I.A, g.d)) return fail(ctx, HOM_ERR_INVALID_ARG, "inclusion phase is not SPD");
+    if (I.shape == HOM_BOX) {
+      for (int a = 0; a < g.d; ++a)
+        if (!(I.size[a] > 0) || I.size[a] > g.Y[a]) return fail(ctx, HOM_ERR_INVALID_ARG, "box side must be in (0, Y]");
+    } else if (!(I.size[0] > 0) || 2 * I.size[0] > minY) {
+      return fail(ctx, HOM_ERR_INVALID_ARG, "ball radius must be in (0, min(Y)/2]");
+    }
+    for (int a = 0; a < g.d; ++a)
+      if (!std::isfinite(I.center[a])) return fail(ctx, HOM_ERR_INVALID_ARG, "inclusion centre not finite");
+    iso = iso && isotropic(I.A, g.d);
+    for (size_t k = 0; k < j; ++k)
+      if (overlap(I, g.incl[k], g.Y, g.d)) return fail(ctx, HOM_ERR_INVALID_ARG, "inclusions overlap");
+  }
+  g.ncomp = iso ? 1 : g.d * (g.d + 1) / 2;
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) g.A0[i][j] = P->A0[3 * i + j];
+  g.field = (long long)g.Nh * g.N[1] * g.N[2];
+  g.planes = (long long)g.M[1] * g.M[2];
+  g.grid = g.planes * g.M[0];
+  g.spec = g.planes * g.Nxs;
+  for (int a = 0; a < 3; ++a) make_plan(g.M[a], g.plan[a]);
+  return HOM_OK;
+}
+
+void pack_sym(const double* A, int d, int ncomp, double* out) {  // A leading dim 3
+  if (ncomp == 1) { out[0] = A[0]; return; }
+  if (d == 2) { out[0] = A[0]; out[1] = A[4]; out[2] = A[1]; return; }
+  out[0] = A[0]; out[1] = A[4]; out[2] = A[8]; out[3] = A[5]; out[4] = A[2]; out[5] = A[1];
+}
+
+// ---------------------------------------------------------------------------------
+// workspace layout
+// ---------------------------------------------------------------------------------
+struct Layout {
+  size_t tw64[3], tw32[3], incl, phase, sinc, coef64, coef32, x, r, p, q, x64, t1, t2, cg[2],
+      partial, epart, eout, total;
+  int Mmax, maxblk, nblk_energy;
+  size_t off = 0;
+  size_t take(size_t bytes) {
+    const size_t o = off;
+    off += (bytes + 255) & ~size_t(255);
+    return o;
+  }
+};
+
+int final_xc_elem(const Geometry& g, size_t elem) {
+  const int M = g.d == 3 ? g.M[2] : g.M[1];
+  const int X = g.d == 3 ? g.N[1] * g.Nh : g.Nh;
+  return elem == 16 ? pencil_xc<double>(M, X, g.d) : pencil_xc<float>(M, X, g.d);
+}
+
+// mode: 0 = hom_bounds (CG vectors in `elem`), 1 = step-level calls
+Layout make_layout(const Geometry& g, int R, size_t elem, int mode) {
+  Layout L{};
+  L.Mmax = std::max(g.M[0], std::max(g.M[1], g.M[2]));
+  for (int a = 0; a < 3; ++a) {
+    L.tw64[a] = L.take((size_t)g.M[a] * 16);
+    L.tw32[a] = L.take((size_t)g.M[a] * 8);
+  }
+  const size_t ni = std::max<size_t>(g.incl.size(), 1);
+  L.incl = L.take(2 * ni * sizeof(DevIncl));
+  L.phase = L.take(ni * 3 * L.Mmax * sizeof(double2));
+  L.sinc = L.take(ni * 3 * L.Mmax * sizeof(double));
+  const long long RC = (long long)R * g.d;
+  const size_t spec_b = (size_t)g.ncomp * g.spec * 16;
+  const size_t t1_b = g.d == 3 ? (size_t)RC * g.M[2] * g.N[1] * g.Nh * 16 : 0;
+  const size_t t2_b = (size_t)RC * g.planes * g.Nh * 16;
+  L.t1 = L.take(std::max(t1_b, spec_b));
+  L.t2 = L.take(std::max(t2_b, spec_b));
+  if (mode == 0) {
+    L.coef64 = L.take((size_t)g.ncomp * g.grid * 8);
+    L.coef32 = elem == 8 ? L.take((size_t)g.ncomp * g.grid * 4) : 0;
+    const size_t fb = (size_t)RC * g.field * elem;
+    L.x = L.take(fb);
+    L.r = L.take(fb);
+    L.p = L.take(fb);
+    L.q = L.take(fb);
+    L.x64 = elem == 8 ? L.take((size_t)RC * g.field * 16) : L.x;
+  }
+  L.cg[0] = L.take(sizeof(CgScalars));
+  L.cg[1] = L.take(sizeof(CgScalars));
+  const int X = g.d == 3 ? g.N[1] * g.Nh : g.Nh;
+  const int xc = std::max(1, std::min(final_xc_elem(g, 16), final_xc_elem(g, 8)));
+  L.maxblk = std::max(kVecBlocks, (X + xc - 1) / xc);
+  L.partial = L.take((size_t)3 * L.maxblk * sizeof(double));
+  L.nblk_energy = (int)g.planes;   // upper bound of the energy pass grid
+  L.epart = L.take((size_t)L.nblk_energy * 9 * sizeof(double));
+  L.eout = L.take(2 * 9 * sizeof(double));
+  L.total = L.off;
+  return L;
+}
+
+void twiddles(int M, std::vector<double2>& w64, std::vector<float2>& w32) {
+  w64.resize(M);
+  w32.resize(M);
+  for (int j = 0; j < M; ++j) {
+    const long double ang = -2.0L * 3.14159265358979323846264338327950288L * (long double)j / (long double)M;
+    const long double c = std::cos(ang), s = std::sin(ang);
+    w64[j] = make_double2((double)c, (double)s);
+    w32[j] = make_float2((float)c, (float)s);
+  }
+}
+
+// ---------------------------------------------------------------------------------
+// per-call runner
+// ---------------------------------------------------------------------------------
+struct Prof {
+  hom_ctx* ctx;
+  cudaStream_t s;
+  bool on;
+  cudaEvent_t stop_ev = nullptr;
+  Prof(hom_ctx* c, const char* fam, cudaStream_t st) : ctx(c), s(st), on(false) {
+    if (c->prof_family.empty() || c->prof_family != fam) return;
+    if (c->ev_used + 2 > c->ev.size()) {
+      for (int i = 0; i < 256; ++i) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) return;
+        c->ev.push_back(e);
+      }
+    }
+    on = true;
+    cudaEventRecord(c->ev[c->ev_used], s);
+    stop_ev = c->ev[c->ev_used + 1];
+    c->ev_used += 2;
+  }
+  ~Prof() {
+    if (on) cudaEventRecord(stop_ev, s);
+  }
+};
+
+struct Runner {
+  hom_ctx* ctx;
+  const Geometry& g;
+  Layout L;
+  unsigned char* base;
+  cudaStream_t st;
+  int R;
+
+  template <typename X> X* at(size_t off) const { return reinterpret_cast<X*>(base + off); }
+
+  hom_status upload_tables() {
+    std::vector<double2> w64;
+    std::vector<float2> w32;
+    for (int a = 0; a < 3; ++a) {
+      twiddles(g.M[a], w64, w32);
+      CK(cudaMemcpyAsync(base + L.tw64[a], w64.data(), w64.size() * sizeof(double2), cudaMemcpyHostToDevice, st));
+      CK(cudaMemcpyAsync(base + L.tw32[a], w32.data(), w32.size() * sizeof(float2), cudaMemcpyHostToDevice, st));
+    }
+    // inclusion tables for both sides: [side][j]
+    const size_t n = g.incl.size();
+    std::vector<DevIncl> di(2 * std::max<size_t>(n, 1));
+    double B0[9] = {};
+    double A0f[9];
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 3; ++j) A0f[3 * i + j] = g.A0[i][j];
+    inv3(A0f, g.d, B0);
+    for (int side = 0; side < 2; ++side)
+      for (size_t j = 0; j < n; ++j) {
+        const hom_inclusion& I = g.incl[j];
+        DevIncl& D = di[side * n + j];
+        memset(&D, 0, sizeof D);
+        D.shape = I.shape == HOM_BOX ? 0 : 1;
+        D.same_as_prev = 0;
+        if (j > 0 && I.shape == HOM_BALL && g.incl[j - 1].shape == HOM_BALL && I.size[0] == g.incl[j - 1].size[0])
+          D.same_as_prev = 1;
+        for (int a = 0; a < 3; ++a) {
+          D.c[a] = I.center[a];
+          D.h[a] = I.size[a];
+        }
+        double dA[9] = {};
+        if (side == 0) {
+          for (int k = 0; k < 9; ++k) dA[k] = I.A[k] - A0f[k];
+        } else {
+          double Bi[9] = {};
+          inv3(I.A, g.d, Bi);
+          for (int k = 0; k < 9; ++k) dA[k] = Bi[k] - B0[k];
+        }
+        pack_sym(dA, g.d, g.ncomp, D.dA);
+      }
+    CK(cudaMemcpyAsync(base + L.incl, di.data(), di.size() * sizeof(DevIncl), cudaMemcpyHostToDevice, st));
+    return HOM_OK;
+  }
+
+  SpecArgs spec_args(int side) const {
+    SpecArgs a{};
+    a.d = g.d;
+    a.ncomp = g.ncomp;
+    a.nincl = (int)g.incl.size();
+    for (int k = 0; k < 3; ++k) {
+      a.M[k] = g.M[k];
+      a.invY[k] = g.invY[k];
+    }
+    a.len[0] = g.Nxs;
+    a.len[1] = g.M[1];
+    a.len[2] = g.M[2];
+    a.Nmod[0] = g.M[0];
+    a.Nmod[1] = g.M[1];
+    a.Nmod[2] = g.M[2];
+    a.invVol = 1.0 / (g.Y[0] * g.Y[1] * g.Y[2]);
+    double C0[9], A0f[9];
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 3; ++j) A0f[3 * i + j] = g.A0[i][j];
+    if (side == 0) memcpy(C0, A0f, sizeof C0);
+    else inv3(A0f, g.d, C0);
+    pack_sym(C0, g.d, g.ncomp, a.A0p);
+    a.incl = at<DevIncl>(L.incl) + side * g.incl.size();
+    a.phase = at<double2>(L.phase);
+    a.sinc = at<double>(L.sinc);
+    a.Mmax = L.Mmax;
+    return a;
+  }
+
+  // Double-grid coefficient of one side into `coef` (FP64, real). Uses t1/t2.
+  hom_status build_coefficient(int side, double* coef) {
+    Prof pr(ctx, "coef", st);
+    SpecArgs sa = spec_args(side);
+    CK(launch_axis_tables(sa.nincl, g.d, g.M, L.Mmax, g.invY, sa.incl, at<double2>(L.phase), at<double>(L.sinc), st));
+    double2* S = at<double2>(L.t1);
+    CK(launch_spectrum(sa, S, st));
+    // 3D: z pass t1 -> t2, y pass t2 -> t1, rows from t1; 2D: y pass t1 -> t2, rows from t2
+    const void* cur = S;
+    void* nxt = at<void>(L.t2);
+    if (g.d == 3) {
+      PencilArgs z{};
+      z.in = cur; z.out = nxt; z.aux = nullptr;
+      z.in_slab = z.out_slab = g.spec;
+      z.nslab = g.ncomp; z.X = g.M[1] * g.Nxs;
+      z.XC = pencil_xc<double>(g.M[2], z.X, 1);
+      z.Pin = z.Pout = z.Nlog = g.M[2]; z.dir = +1;
+      z.slabs_per_rhs = z.nslab; z.slabs_per_comp = 1; z.C = 1; z.prologue = 0;
+      z.W = base + L.tw64[2]; z.plan = g.plan[2]; z.cg = nullptr;
+      if (z.XC < 1) return fail(ctx, HOM_ERR_INVALID_ARG, "grid too large for the shared-memory FFT");
+      CK(launch_pencil<double>(z, st));
+      cur = at<void>(L.t2);
+      nxt = at<void>(L.t1);
+    }
+    PencilArgs y{};
+    y.in = cur; y.out = nxt; y.aux = nullptr;
+    y.in_slab = y.out_slab = (long long)g.M[1] * g.Nxs;
+    y.nslab = g.ncomp * g.M[2]; y.X = g.Nxs;
+    y.XC = pencil_xc<double>(g.M[1], y.X, 1);
+    y.Pin = y.Pout = y.Nlog = g.M[1]; y.dir = +1;
+    y.slabs_per_rhs = y.nslab; y.slabs_per_comp = 1; y.C = 1; y.prologue = 0;
+    y.W = base + L.tw64[1]; y.plan = g.plan[1]; y.cg = nullptr;
+    if (y.XC < 1) return fail(ctx, HOM_ERR_INVALID_ARG, "grid too large for the shared-memory FFT");
+    CK(launch_pencil<double>(y, st));
+    XArgs x{};
+    x.in = nxt; x.out = coef; x.coef = nullptr; x.mode = 2;
+    x.planes = (int)g.planes; x.YB = xpass_yb<double>(g.M[0], 1, (int)g.planes);
+    x.Nin = g.Nxs; x.Nout = 0; x.M = g.M[0]; x.R = 1; x.C = 1; x.ncomp = g.ncomp; x.d = g.d;
+    x.comp_stride = g.planes * g.Nxs; x.scale = 1.0;
+    x.W = base + L.tw64[0]; x.plan = g.plan[0]; x.cg = nullptr; x.partial = nullptr;
+    if (x.YB < 1) return fail(ctx, HOM_ERR_INVALID_ARG, "grid too large for the shared-memory FFT");
+    CK(launch_xpass<double>(x, g.ncomp, st));
+    return HOM_OK;
+  }
+
+  // Operator passes on R fields: out = Gamma^{side} P F (A/|M|) F^{-1} Pad(in).
+  // cgmode: first pass updates p = r + beta p (in = p, aux = r), last pass writes p.q partials.
+  // project: 0 none, 1 Gamma^E, 2 Gamma^J.  addE: energy-style constant added (not used here).
+  template <typename T>
+  hom_status matvec(const void* in, void* out, const void* coef, int project, CgScalars* cg,
+                    const void* r_aux, const void* p_aux, int prologue) {
+    const size_t tw = sizeof(T) == 8 ? 0 : 1;
+    auto W = [&](int a) -> const void* { return base + (tw == 0 ? L.tw64[a] : L.tw32[a]); };
+    const int C = g.d;
+    const int Mx = g.M[0], My = g.M[1], Mz = g.M[2];
+    const int Ny = g.N[1], Nz = g.N[2], Nh = g.Nh;
+    void* T1 = at<void>(L.t1);
+    void* T2 = at<void>(L.t2);
+    const void* ycur = in;
+    if (g.d == 3) {
+      Prof pr(ctx, "zpass", st);
+      PencilArgs z{};
+      z.in = in; z.out = T1; z.aux = r_aux;
+      z.in_slab = (long long)Nz * Ny * Nh; z.out_slab = (long long)Mz * Ny * Nh;
+      z.nslab = R * C; z.X = Ny * Nh; z.XC = pencil_xc<T>(Mz, z.X, 1);
+      z.Pin = Nz; z.Pout = Mz; z.Nlog = Nz; z.dir = +1;
+      z.slabs_per_rhs = C; z.slabs_per_comp = 1; z.C = C; z.prologue = prologue;
+      z.W = W(2); z.plan = g.plan[2]; z.cg = cg;
+      if (z.XC < 1) return fail(ctx, HOM_ERR_INVALID_ARG, "grid too large for the shared-memory FFT");
+      CK(launch_pencil<T>(z, st));
+      ycur = T1;
+    }
+    {
+      Prof pr(ctx, "ypass", st);
+      PencilArgs y{};
+      y.in = ycur; y.out = T2; y.aux = g.d == 3 ? nullptr : r_aux;
+      y.in_slab = (long long)Ny * Nh; y.out_slab = (long long)My * Nh;
+      y.nslab = R * C * Mz; y.X = Nh; y.XC = pencil_xc<T>(My, Nh, 1);
+      y.Pin = Ny; y.Pout = My; y.Nlog = Ny; y.dir = +1;
+      y.slabs_per_rhs = C * Mz; y.slabs_per_comp = Mz; y.C = C;
+      y.prologue = g.d == 3 ? 0 : prologue;
+      y.W = W(1); y.plan = g.plan[1]; y.cg = cg;
+      if (y.XC < 1) return fail(ctx, HOM_ERR_INVALID_ARG, "grid too large for the shared-memory FFT");
+      CK(launch_pencil<T>(y, st));
+    }
+    {
+      Prof pr(ctx, "xpass", st);
+      XArgs x{};
+      x.in = T2; x.out = T2; x.coef = coef; x.mode = 0;
+      x.planes = (int)g.planes; x.YB = xpass_yb<T>(Mx, C, (int)g.planes);
+      x.Nin = Nh; x.Nout = Nh; x.M = Mx; x.R = R; x.C = C; x.ncomp = g.ncomp; x.d = g.d;
+      x.comp_stride = g.planes * Nh; x.scale = 1.0 / (double)g.grid;
+      x.W = W(0); x.plan = g.plan[0]; x.cg = cg; x.partial = nullptr;
+      if (x.YB < 1) return fail(ctx, HOM_ERR_INVALID_ARG, "grid too large for the shared-memory FFT");
+      CK(launch_xpass<T>(x, R, st));
+    }
+    const void* fin = T2;
+    if (g.d == 3) {
+      Prof pr(ctx, "ypass", st);
+      PencilArgs y{};
+      y.in = T2; y.out = T1; y.aux = nullptr;
+      y.in_slab = (long long)My * Nh; y.out_slab = (long long)Ny * Nh;
+      y.nslab = R * C * Mz; y.X = Nh; y.XC = pencil_xc<T>(My, Nh, 1);
+      y.Pin = My; y.Pout = Ny; y.Nlog = Ny; y.dir = -1;
+      y.slabs_per_rhs = C * Mz; y.slabs_per_comp = Mz; y.C = C; y.prologue = 0;
+      y.W = W(1); y.plan = g.plan[1]; y.cg = cg;
+      CK(launch_pencil<T>(y, st));
+      fin = T1;
+    }
+    {
+      Prof pr(ctx, "final", st);
+      FinalArgs f{};
+      f.in = fin; f.out = out; f.aux = p_aux;
+      const int Mlast = g.d == 3 ? Mz : My;
+      const int Nlast = g.d == 3 ? Nz : Ny;
+      f.X = g.d == 3 ? Ny * Nh : Nh;
+      f.in_comp = (long long)Mlast * f.X; f.out_comp = (long long)Nlast * f.X;
+      f.nrhs = R; f.C = C; f.XC = pencil_xc<T>(Mlast, f.X, C); f.M = Mlast; f.Nlog = Nlast;
+      f.project = project; f.d = g.d; f.Ny = Ny; f.Nh = Nh;
+      for (int k = 0; k < 3; ++k) f.invY[k] = g.invY[k];
+      f.W = W(g.d == 3 ? 2 : 1); f.plan = g.plan[g.d == 3 ? 2 : 1];
+      f.cg = cg; f.partial = at<double>(L.partial); f.partial_ld = L.maxblk;
+      if (f.XC < 1) return fail(ctx, HOM_ERR_INVALID_ARG, "grid too large for the shared-memory FFT");
+      CK(launch_final<T>(f, st));
+    }
+    return HOM_OK;
+  }
+
+  int final_blocks(size_t elem) const {
+    const int X = g.d == 3 ? g.N[1] * g.Nh : g.Nh;
+    const int xc = final_xc_elem(g, elem);
+    return (X + xc - 1) / xc;
+  }
+
+  // Energy matrix of the R FP64 fields x64 (u = e_r + x_r when addE) -> eout[slot*9 ...]
+  hom_status energy(const double* coef, const double2* x64, int addE, int slot) {
+    Prof pr(ctx, "energy", st);
+    const int C = g.d;
+    const int My = g.M[1], Mz = g.M[2];
+    const int Ny = g.N[1], Nz = g.N[2], Nh = g.Nh;
+    void* T1 = at<void>(L.t1);
+    void* T2 = at<void>(L.t2);
+    const void* ycur = x64;
+    if (g.d == 3) {
+      PencilArgs z{};
+      z.in = x64; z.out = T1; z.aux = nullptr;
+      z.in_slab = (long long)Nz * Ny * Nh; z.out_slab = (long long)Mz * Ny * Nh;
+      z.nslab = R * C; z.X = Ny * Nh; z.XC = pencil_xc<double>(Mz, z.X, 1);
+      z.Pin = Nz; z.Pout = Mz; z.Nlog = Nz; z.dir = +1;
+      z.slabs_per_rhs = C; z.slabs_per_comp = 1; z.C = C; z.prologue = addE ? 2 : 0;
+      z.W = base + L.tw64[2]; z.plan = g.plan[2]; z.cg = nullptr;
+      CK(launch_pencil<double>(z, st));
+      ycur = T1;
+    }
+    PencilArgs y{};
+    y.in = ycur; y.out = T2; y.aux = nullptr;
+    y.in_slab = (long long)Ny * Nh; y.out_slab = (long long)My * Nh;
+    y.nslab = R * C * Mz; y.X = Nh; y.XC = pencil_xc<double>(My, Nh, 1);
+    y.Pin = Ny; y.Pout = My; y.Nlog = Ny; y.dir = +1;
+    y.slabs_per_rhs = C * Mz; y.slabs_per_comp = Mz; y.C = C;
+    y.prologue = (g.d == 2 && addE) ? 2 : 0;
+    y.W = base + L.tw64[1]; y.plan = g.plan[1]; y.cg = nullptr;
+    CK(launch_pencil<double>(y, st));
+    XArgs x{};
+    x.in = T2; x.out = nullptr; x.coef = coef; x.mode = 1;
+    x.planes = (int)g.planes; x.YB = xpass_yb<double>(g.M[0], R * C, (int)g.planes);
+    if (x.YB < 1) return fail(ctx, HOM_ERR_INVALID_ARG, "grid too large for the shared-memory FFT");
+    x.Nin = Nh; x.Nout = 0; x.M = g.M[0]; x.R = R; x.C = C; x.ncomp = g.ncomp; x.d = g.d;
+    x.comp_stride = g.planes * Nh; x.scale = 1.0;
+    x.W = base + L.tw64[0]; x.plan = g.plan[0]; x.cg = nullptr; x.partial = at<double>(L.epart);
+    CK(launch_xpass<double>(x, 1, st));
+    const int nblk = (int)((g.planes + x.YB - 1) / x.YB);
+    CK(launch_energy_reduce(at<double>(L.epart), nblk, R * R, at<double>(L.eout) + slot * 9, st));
+    return HOM_OK;
+  }
+
+  template <typename T>
+  hom_status solve_side(int side, const hom_opts& o, hom_report* rep, int* matvecs) {
+    const size_t elem = sizeof(T) * 2;
+    double* coef64 = at<double>(L.coef64);
+    CKS(build_coefficient(side, coef64));
+    const void* coefT = coef64;
+    if (sizeof(T) == 4) {
+      CK(launch_convert_d2f(coef64, at<float>(L.coef32), (long long)g.ncomp * g.grid, st));
+      coefT = at<float>(L.coef32);
+    }
+    const size_t fb = (size_t)R * g.d * g.field * elem;
+    CK(cudaMemsetAsync(base + L.x, 0, fb, st));
+    CK(cudaMemsetAsync(base + L.p, 0, fb, st));
+    CgScalars* cg = at<CgScalars>(L.cg[side]);
+    SpecArgs sa = spec_args(side);
+    const int N3[3] = {g.N[0], g.N[1], g.N[2]};
+    CK(launch_rhs<T>(sa, side, R, g.Nh, N3, base + L.r, at<double>(L.partial), kVecBlocks, st));
+    const double tol = o.tol > 0 ? o.tol : 1e-8;
+    CK(launch_cg_init(cg, at<double>(L.partial), kVecBlocks, kVecBlocks, R, tol * tol, st));
+    const int maxit = o.max_iter > 0 ? o.max_iter : 10000;
+    const int every = o.check_every > 0 ? o.check_every : 8;
+    const int nfin = final_blocks(elem);
+    // an initial poll avoids work when b = 0 (homogeneous cells)
+    CK(cudaMemcpyAsync(ctx->host_cg, cg, sizeof(CgScalars), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    bool any = false;
+    for (int r = 0; r < R; ++r) any = any || ctx->host_cg->active[r];
+    for (int it = 0; any && it < maxit; ++it) {
+      CKS(matvec<T>(base + L.p, base + L.q, coefT, side + 1, cg, base + L.r, base + L.p, 1));
+      {
+        Prof pr(ctx, "cg", st);
+        CK(launch_cg_alpha(cg, at<double>(L.partial), L.maxblk, nfin, R, st));
+        CK(launch_cg_update<T>(base + L.x, base + L.r, base + L.p, base + L.q, R, g.d, g.field, g.Nh, cg,
+                               at<double>(L.partial), kVecBlocks, st));
+        CK(launch_cg_beta(cg, at<double>(L.partial), kVecBlocks, kVecBlocks, R, st));
+      }
+      ++*matvecs;
+      if ((it + 1) % every == 0 || it + 1 == maxit) {
+        CK(cudaMemcpyAsync(ctx->host_cg, cg, sizeof(CgScalars), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        any = false;
+        for (int r = 0; r < R; ++r) any = any || ctx->host_cg->active[r];
+      }
+    }
+    CK(cudaMemcpyAsync(ctx->host_cg, cg, sizeof(CgScalars), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    hom_status result = HOM_OK;
+    for (int r = 0; r < R; ++r) {
+      const CgScalars& h = *ctx->host_cg;
+      int stt = h.status[r] == 1 ? 1 : h.status[r];
+      if (rep) {
+        rep->iters[side][r] = h.iters[r];
+        rep->resid[side][r] = std::sqrt(std::max(h.rr[r], 0.0));
+        rep->status[side][r] = stt;
+      }
+      if (stt == -2) result = fail(ctx, HOM_ERR_BREAKDOWN, "CG breakdown (non-finite value or p.Cp <= 0)");
+      else if (stt == 1 && result == HOM_OK) result = HOM_WARN_NOT_CONVERGED;
+    }
+    if (result == HOM_ERR_BREAKDOWN) return result;
+    // FP64 re-projection (and promotion for the mixed path), then the exact energies
+    CK(launch_project_promote<T>(base + L.x, at<double2>(L.x64), R, g.d, g.N[1], g.N[2], g.Nh, g.invY, side, st));
+    CKS(energy(coef64, at<double2>(L.x64), 1, side));
+    return result;
+  }
+};
+
+hom_status set_device(hom_ctx* ctx) {
+  CK(cudaSetDevice(ctx->device));
+  return HOM_OK;
+}
+
+bool sym_inv_spd(const double* B, int d, double* out) {  // leading dim d
+  double A3[9] = {}, I3[9] = {};
+  for (int i = 0; i < d; ++i)
+    for (int j = 0; j < d; ++j) A3[3 * i + j] = B[d * i + j];
+  if (!spd(A3, d)) return false;
+  inv3(A3, d, I3);
+  for (int i = 0; i < d; ++i)
+    for (int j = 0; j < d; ++j) out[d * i + j] = I3[3 * i + j];
+  return true;
+}
+
+}  // namespace
+
+// =====================================================================================
+// C ABI
+// =====================================================================================
+extern "C" {
+
+const char* hom_version(void) { return "homb 0.1"; }
+
+hom_status hom_create(hom_ctx** out, int device) {
+  if (!out) return HOM_ERR_INVALID_ARG;
+  hom_ctx* ctx = new hom_ctx();
+  ctx->device = device;
+  cudaError_t e = cudaSetDevice(device);
+  if (e == cudaSuccess) e = cudaMallocHost((void**)&ctx->host_cg, sizeof(CgScalars));
+  if (e == cudaSuccess) e = cudaMallocHost((void**)&ctx->host_e, 64 * sizeof(double));
+  if (e != cudaSuccess) {
+    delete ctx;
+    *out = nullptr;
+    return HOM_ERR_CUDA;
+  }
+  *out = ctx;
+  return HOM_OK;
+}
+
+hom_status hom_destroy(hom_ctx* ctx) {
+  if (!ctx) return HOM_OK;
+  cudaSetDevice(ctx->device);
+  for (cudaEvent_t e : ctx->ev) cudaEventDestroy(e);
+  if (ctx->host_cg) cudaFreeHost(ctx->host_cg);
+  if (ctx->host_e) cudaFreeHost(ctx->host_e);
+  delete ctx;
+  return HOM_OK;
+}
+
+const char* hom_last_error(const hom_ctx* ctx) { return ctx ? ctx->err.c_str() : ""; }
+
+hom_status hom_problem_info(hom_ctx* ctx, const hom_problem* prob, int32_t* ncomp, int32_t M[3],
+                            int64_t* field_elems, int64_t* grid_elems) {
+  if (!ctx) return HOM_ERR_INVALID_ARG;
+  Geometry g;
+  CKS(build_geometry(ctx, prob, g));
+  if (ncomp) *ncomp = g.ncomp;
+  if (M)
+    for (int a = 0; a < 3; ++a) M[a] = g.M[a];
+  if (field_elems) *field_elems = g.field;
+  if (grid_elems) *grid_elems = g.grid;
+  return HOM_OK;
+}
+
+hom_status hom_workspace_size(hom_ctx* ctx, const hom_problem* prob, const hom_opts* opts,
+                              size_t* bytes) {
+  if (!ctx || !opts || !bytes) return fail(ctx, HOM_ERR_INVALID_ARG, "NULL argument");
+  Geometry g;
+  CKS(build_geometry(ctx, prob, g));
+  const size_t elem = opts->precision == HOM_MIXED ? 8 : 16;
+  *bytes = make_layout(g, g.d, elem, 0).total;
+  return HOM_OK;
+}
+
+hom_status hom_step_workspace_size(hom_ctx* ctx, const hom_problem* prob, int32_t nrhs,
+                                   size_t* bytes) {
+  if (!ctx || !bytes || nrhs < 1 || nrhs > 3) return fail(ctx, HOM_ERR_INVALID_ARG, "bad argument");
+  Geometry g;
+  CKS(build_geometry(ctx, prob, g));
+  if (nrhs > g.d) return fail(ctx, HOM_ERR_INVALID_ARG, "nrhs > d");
+  *bytes = make_layout(g, nrhs, 16, 1).total;
+  return HOM_OK;
+}
+
+hom_status hom_bounds(hom_ctx* ctx, const hom_problem* prob, const hom_opts* opts, void* d_ws,
+                      size_t ws_bytes, void* stream, double* upper, double* lower, double* mean,
+                      double* D, hom_report* rep) {
+  if (!ctx || !opts) return fail(ctx, HOM_ERR_INVALID_ARG, "NULL argument");
+  const auto t0 = std::chrono::steady_clock::now();
+  ctx->err.clear();
+  CKS(set_device(ctx));
+  Geometry g;
+  CKS(build_geometry(ctx, prob, g));
+  if (opts->precision != HOM_FP64 && opts->precision != HOM_MIXED)
+    return fail(ctx, HOM_ERR_INVALID_ARG, "precision must be HOM_FP64 or HOM_MIXED");
+  const size_t elem = opts->precision == HOM_MIXED ? 8 : 16;
+  Runner run{ctx, g, make_layout(g, g.d, elem, 0), static_cast<unsigned char*>(d_ws),
+             static_cast<cudaStream_t>(stream), g.d};
+  if (!d_ws || ws_bytes < run.L.total) return fail(ctx, HOM_ERR_WORKSPACE, "workspace too small");
+  if (reinterpret_cast<uintptr_t>(d_ws) % 256) return fail(ctx, HOM_ERR_INVALID_ARG, "workspace must be 256-byte aligned");
+  if (rep) memset(rep, 0, sizeof *rep);
+  CKS(run.upload_tables());
+  const int sides = opts->sides ? opts->sides : 3;
+  int matvecs = 0;
+  hom_status worst = HOM_OK;
+  for (int side = 0; side < 2; ++side) {
+    if (!(sides & (1 << side))) continue;
+    hom_status s = elem == 16 ? run.solve_side<double>(side, *opts, rep, &matvecs)
+                              : run.solve_side<float>(side, *opts, rep, &matvecs);
+    if (s < 0) return s;
+    if (s == HOM_WARN_NOT_CONVERGED) worst = s;
+  }
+  CK(cudaMemcpyAsync(ctx->host_e, run.at<double>(run.L.eout), 18 * sizeof(double), cudaMemcpyDeviceToHost,
+                     run.st));
+  CK(cudaStreamSynchronize(run.st));
+  const int d = g.d;
+  const double invM = 1.0 / (double)g.grid;
+  double Au[9] = {}, Bu[9] = {}, Lo[9] = {};
+  for (int i = 0; i < d * d; ++i) {
+    Au[i] = ctx->host_e[i] * invM;
+    Bu[i] = ctx->host_e[9 + i] * invM;
+  }
+  if (sides & 1)
+    if (upper) memcpy(upper, Au, sizeof(double) * d * d);
+  if (sides & 2) {
+    if (!sym_inv_spd(Bu, d, Lo)) return fail(ctx, HOM_ERR_NOT_SPD_RESULT, "dual energy matrix is not SPD");
+    if (lower) memcpy(lower, Lo, sizeof(double) * d * d);
+  }
+  if ((sides & 3) == 3) {
+    for (int i = 0; i < d * d; ++i) {
+      if (mean) mean[i] = 0.5 * (Au[i] + Lo[i]);
+      if (D) D[i] = 0.5 * (Au[i] - Lo[i]);
+    }
+  }
+  if (rep) {
+    rep->matvecs = matvecs;
+    rep->ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  }
+  return worst;
+}
+
+hom_status hom_coefficient(hom_ctx* ctx, const hom_problem* prob, int32_t side, int32_t precision,
+                           void* d_coef, void* d_ws, size_t ws_bytes, void* stream) {
+  if (!ctx || !d_coef) return fail(ctx, HOM_ERR_INVALID_ARG, "NULL argument");
+  if (side != 0 && side != 1) return fail(ctx, HOM_ERR_INVALID_ARG, "side must be 0 or 1");
+  if (precision != HOM_FP64 && precision != HOM_FP32) return fail(ctx, HOM_ERR_INVALID_ARG, "precision");
+  CKS(set_device(ctx));
+  Geometry g;
+  CKS(build_geometry(ctx, prob, g));
+  Runner run{ctx, g, make_layout(g, 1, 16, 1), static_cast<unsigned char*>(d_ws),
+             static_cast<cudaStream_t>(stream), 1};
+  if (!d_ws || ws_bytes < run.L.total) return fail(ctx, HOM_ERR_WORKSPACE, "workspace too small");
+  CKS(run.upload_tables());
+  if (precision == HOM_FP64) return run.build_coefficient(side, static_cast<double*>(d_coef));
+  // FP32: build in FP64 into the buffer the last pass does not read, then round
+  double* tmp = run.at<double>(g.d == 3 ? run.L.t2 : run.L.t1);
+  CKS(run.build_coefficient(side, tmp));
+  CK(launch_convert_d2f(tmp, static_cast<float*>(d_coef), (long long)g.ncomp * g.grid, run.st));
+  return HOM_OK;
+}
+
+hom_status hom_rhs(hom_ctx* ctx, const hom_problem* prob, int32_t side, int32_t precision,
+                   int32_t nrhs, void* d_b, void* d_ws, size_t ws_bytes, void* stream) {
+  if (!ctx || !d_b) return fail(ctx, HOM_ERR_INVALID_ARG, "NULL argument");
+  if (side != 0 && side != 1) return fail(ctx, HOM_ERR_INVALID_ARG, "side must be 0 or 1");
+  if (precision != HOM_FP64 && precision != HOM_FP32) return fail(ctx, HOM_ERR_INVALID_ARG, "precision");
+  CKS(set_device(ctx));
+  Geometry g;
+  CKS(build_geometry(ctx, prob, g));
+  if (nrhs < 1 || nrhs > g.d) return fail(ctx, HOM_ERR_INVALID_ARG, "nrhs must be in [1, d]");
+  Runner run{ctx, g, make_layout(g, nrhs, 16, 1), static_cast<unsigned char*>(d_ws),
+             static_cast<cudaStream_t>(stream), nrhs};
+  if (!d_ws || ws_bytes < run.L.total) return fail(ctx, HOM_ERR_WORKSPACE, "workspace too small");
+  CKS(run.upload_tables());
+  SpecArgs sa = run.spec_args(side);
+  CK(launch_axis_tables(sa.nincl, g.d, g.M, run.L.Mmax, g.invY, sa.incl, run.at<double2>(run.L.phase),
+                        run.at<double>(run.L.sinc), run.st));
+  const int N3[3] = {g.N[0], g.N[1], g.N[2]};
+  if (precision == HOM_FP64)
+    CK(launch_rhs<double>(sa, side, nrhs, g.Nh, N3, d_b, run.at<double>(run.L.partial), kVecBlocks, run.st));
+  else
+    CK(launch_rhs<float>(sa, side, nrhs, g.Nh, N3, d_b, run.at<double>(run.L.partial), kVecBlocks, run.st));
+  return HOM_OK;
+}
+
+hom_status hom_matvec(hom_ctx* ctx, const hom_problem* prob, int32_t side, int32_t precision,
+                      int32_t project, int32_t nrhs, const void* d_coef, const void* d_in, void* d_out,
+                      void* d_ws, size_t ws_bytes, void* stream) {
+  if (!ctx || !d_coef || !d_in || !d_out) return fail(ctx, HOM_ERR_INVALID_ARG, "NULL argument");
+  if (d_in == d_out) return fail(ctx, HOM_ERR_INVALID_ARG, "d_in and d_out must not alias");
+  if (side != 0 && side != 1) return fail(ctx, HOM_ERR_INVALID_ARG, "side must be 0 or 1");
+  if (precision != HOM_FP64 && precision != HOM_FP32) return fail(ctx, HOM_ERR_INVALID_ARG, "precision");
+  CKS(set_device(ctx));
+  Geometry g;
+  CKS(build_geometry(ctx, prob, g));
+  if (nrhs < 1 || nrhs > g.d) return fail(ctx, HOM_ERR_INVALID_ARG, "nrhs must be in [1, d]");
+  Runner run{ctx, g, make_layout(g, nrhs, 16, 1), static_cast<unsigned char*>(d_ws),
+             static_cast<cudaStream_t>(stream), nrhs};
+  if (!d_ws || ws_bytes < run.L.total) return fail(ctx, HOM_ERR_WORKSPACE, "workspace too small");
+  CKS(run.upload_tables());
+  const int proj = project ? side + 1 : 0;
+  if (precision == HOM_FP64)
+    return run.matvec<double>(d_in, d_out, d_coef, proj, nullptr, nullptr, nullptr, 0);
+  return run.matvec<float>(d_in, d_out, d_coef, proj, nullptr, nullptr, nullptr, 0);
+}
+
+hom_status hom_energy(hom_ctx* ctx, const hom_problem* prob, int32_t nrhs, int32_t add_constant,
+                      const void* d_coef, const void* d_x, double* W, void* d_ws, size_t ws_bytes,
+                      void* stream) {
+  if (!ctx || !d_coef || !d_x || !W) return fail(ctx, HOM_ERR_INVALID_ARG, "NULL argument");
+  CKS(set_device(ctx));
+  Geometry g;
+  CKS(build_geometry(ctx, prob, g));
+  if (nrhs < 1 || nrhs > g.d) return fail(ctx, HOM_ERR_INVALID_ARG, "nrhs must be in [1, d]");
+  Runner run{ctx, g, make_layout(g, nrhs, 16, 1), static_cast<unsigned char*>(d_ws),
+             static_cast<cudaStream_t>(stream), nrhs};
+  if (!d_ws || ws_bytes < run.L.total) return fail(ctx, HOM_ERR_WORKSPACE, "workspace too small");
+  CKS(run.upload_tables());
+  CKS(run.energy(static_cast<const double*>(d_coef), static_cast<const double2*>(d_x), add_constant, 0));
+  CK(cudaMemcpyAsync(ctx->host_e, run.at<double>(run.L.eout), 9 * sizeof(double), cudaMemcpyDeviceToHost, run.st));
+  CK(cudaStreamSynchronize(run.st));
+  for (int i = 0; i < nrhs * nrhs; ++i) W[i] = ctx->host_e[i] / (double)g.grid;
+  return HOM_OK;
+}
+
+hom_status hom_fft(hom_ctx* ctx, int32_t M, int32_t precision, int32_t dir, int32_t howmany,
+                   const void* d_in, void* d_out, void* d_ws, size_t ws_bytes, void* stream) {
+  if (!ctx || !d_in || !d_out || !d_ws) return fail(ctx, HOM_ERR_INVALID_ARG, "NULL argument");
+  if (M < 1 || M % 2 != 1 || M > 4095) return fail(ctx, HOM_ERR_INVALID_ARG, "M must be odd in [1, 4095]");
+  if (dir != 1 && dir != -1) return fail(ctx, HOM_ERR_INVALID_ARG, "dir must be +1 or -1");
+  if (howmany < 0) return fail(ctx, HOM_ERR_INVALID_ARG, "howmany < 0");
+  if (precision != HOM_FP64 && precision != HOM_FP32) return fail(ctx, HOM_ERR_INVALID_ARG, "precision");
+  if (ws_bytes < (size_t)M * 16) return fail(ctx, HOM_ERR_WORKSPACE, "workspace too small");
+  if (howmany == 0) return HOM_OK;
+  CKS(set_device(ctx));
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  std::vector<double2> w64;
+  std::vector<float2> w32;
+  twiddles(M, w64, w32);
+  FftPlan plan;
+  make_plan(M, plan);
+  if (precision == HOM_FP64) {
+    CK(cudaMemcpyAsync(d_ws, w64.data(), M * sizeof(double2), cudaMemcpyHostToDevice, st));
+    CK(launch_fft_batch<double>(d_in, d_out, M, howmany, dir, d_ws, plan, st));
+  } else {
+    CK(cudaMemcpyAsync(d_ws, w32.data(), M * sizeof(float2), cudaMemcpyHostToDevice, st));
+    CK(launch_fft_batch<float>(d_in, d_out, M, howmany, dir, d_ws, plan, st));
+  }
+  return HOM_OK;
+}
+
+hom_status hom_profile_kernel(hom_ctx* ctx, const char* name) {
+  if (!ctx) return HOM_ERR_INVALID_ARG;
+  ctx->prof_family = name ? name : "";
+  ctx->ev_used = 0;
+  return HOM_OK;
+}
+
+hom_status hom_kernel_timing(hom_ctx* ctx, int64_t* launches, double* total_ms) {
+  if (!ctx) return HOM_ERR_INVALID_ARG;
+  double tot = 0;
+  for (size_t i = 0; i + 1 < ctx->ev_used; i += 2) {
+    CK(cudaEventSynchronize(ctx->ev[i + 1]));
+    float ms = 0;
+    CK(cudaEventElapsedTime(&ms, ctx->ev[i], ctx->ev[i + 1]));
+    tot += ms;
+  }
+  if (launches) *launches = (int64_t)(ctx->ev_used / 2);
+  if (total_ms) *total_ms = tot;
+  ctx->ev_used = 0;
+  return HOM_OK;
+}
+
+}  // extern "C"

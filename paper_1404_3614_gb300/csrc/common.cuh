@@ -1,0 +1,200 @@
+// Shared device helpers: complex arithmetic, the shared-memory FFT engine,
+// deterministic block reductions and the launch-argument structures.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace homb {
+
+template <typename T> struct cplx_t;
+template <> struct cplx_t<double> { using type = double2; };
+template <> struct cplx_t<float> { using type = float2; };
+template <typename T> using cpx = typename cplx_t<T>::type;
+
+template <typename T> __device__ __forceinline__ cpx<T> mk(T x, T y) { cpx<T> r; r.x = x; r.y = y; return r; }
+template <typename T> __device__ __forceinline__ cpx<T> add(cpx<T> a, cpx<T> b) { return mk<T>(a.x + b.x, a.y + b.y); }
+template <typename T> __device__ __forceinline__ cpx<T> sub(cpx<T> a, cpx<T> b) { return mk<T>(a.x - b.x, a.y - b.y); }
+template <typename T> __device__ __forceinline__ cpx<T> scl(cpx<T> a, T s) { return mk<T>(a.x * s, a.y * s); }
+template <typename T> __device__ __forceinline__ cpx<T> conj_(cpx<T> a) { return mk<T>(a.x, -a.y); }
+// a * b
+template <typename T> __device__ __forceinline__ cpx<T> mul(cpx<T> a, cpx<T> b) {
+  return mk<T>(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
+}
+// a * (b or conj b)
+template <typename T> __device__ __forceinline__ cpx<T> mulc(cpx<T> a, cpx<T> b, bool conjb) {
+  T by = conjb ? -b.y : b.y;
+  return mk<T>(fma(a.x, b.x, -a.y * by), fma(a.x, by, a.y * b.x));
+}
+// i * a  (s = +1) or -i * a (s = -1)
+template <typename T> __device__ __forceinline__ cpx<T> rot(cpx<T> a, int s) {
+  return s > 0 ? mk<T>(-a.y, a.x) : mk<T>(a.y, -a.x);
+}
+
+constexpr int kMaxRadices = 24;
+
+// Factorised plan of one odd transform length M (Stockham autosort, mixed radix).
+struct FftPlan {
+  int M;
+  int nrad;
+  int radix[kMaxRadices];
+};
+
+// ---------------------------------------------------------------------------------
+// Small DFT butterflies. dir = -1: forward (w = exp(-2 pi i / r)); dir = +1: inverse.
+// The constants are cos/sin of 2 pi/3, 2 pi/5, 4 pi/5.
+// ---------------------------------------------------------------------------------
+template <typename T> __device__ __forceinline__ void dft3(cpx<T>* v, int dir) {
+  const T h = T(0.5);
+  const T s3 = T(0.86602540378443864676372317075294);
+  cpx<T> t1 = add<T>(v[1], v[2]);
+  cpx<T> t2 = mk<T>(fma(-h, t1.x, v[0].x), fma(-h, t1.y, v[0].y));
+  cpx<T> t3 = scl<T>(sub<T>(v[1], v[2]), s3);
+  v[0] = add<T>(v[0], t1);
+  // forward: V1 = t2 - i t3, V2 = t2 + i t3
+  cpx<T> it3 = rot<T>(t3, dir > 0 ? 1 : -1);
+  v[1] = add<T>(t2, it3);
+  v[2] = sub<T>(t2, it3);
+}
+
+template <typename T> __device__ __forceinline__ void dft5(cpx<T>* v, int dir) {
+  const T c1 = T(0.30901699437494742410229341718282);    // cos(2 pi/5)
+  const T c2 = T(-0.80901699437494742410229341718282);   // cos(4 pi/5)
+  const T s1 = T(0.95105651629515357211643933337938);    // sin(2 pi/5)
+  const T s2 = T(0.58778525229247312916870595463907);    // sin(4 pi/5)
+  cpx<T> a1 = add<T>(v[1], v[4]), b1 = sub<T>(v[1], v[4]);
+  cpx<T> a2 = add<T>(v[2], v[3]), b2 = sub<T>(v[2], v[3]);
+  cpx<T> m1 = mk<T>(fma(c1, a1.x, fma(c2, a2.x, v[0].x)), fma(c1, a1.y, fma(c2, a2.y, v[0].y)));
+  cpx<T> m2 = mk<T>(fma(c2, a1.x, fma(c1, a2.x, v[0].x)), fma(c2, a1.y, fma(c1, a2.y, v[0].y)));
+  cpx<T> n1 = mk<T>(fma(s1, b1.x, s2 * b2.x), fma(s1, b1.y, s2 * b2.y));
+  cpx<T> n2 = mk<T>(fma(s2, b1.x, -s1 * b2.x), fma(s2, b1.y, -s1 * b2.y));
+  v[0] = add<T>(v[0], add<T>(a1, a2));
+  int s = dir > 0 ? 1 : -1;     // forward: V1 = m1 - i n1
+  cpx<T> in1 = rot<T>(n1, s), in2 = rot<T>(n2, s);
+  v[1] = add<T>(m1, in1);
+  v[4] = sub<T>(m1, in1);
+  v[2] = add<T>(m2, in2);
+  v[3] = sub<T>(m2, in2);
+}
+
+// Generic compile-time radix R from registers, roots from the length-M table W.
+template <typename T, int R>
+__device__ __forceinline__ void dftR(cpx<T>* v, const cpx<T>* W, int M, int dir) {
+  cpx<T> o[R];
+  const int step = M / R;
+#pragma unroll
+  for (int s = 0; s < R; ++s) {
+    cpx<T> acc = v[0];
+#pragma unroll
+    for (int q = 1; q < R; ++q) acc = add<T>(acc, mulc<T>(v[q], W[((q * s) % R) * step], dir > 0));
+    o[s] = acc;
+  }
+#pragma unroll
+  for (int s = 0; s < R; ++s) v[s] = o[s];
+}
+
+// One Stockham stage for butterfly j of one pencil (src/dst of length M).
+template <typename T, int R>
+__device__ __forceinline__ void stage_bfly(const cpx<T>* __restrict__ src, cpx<T>* __restrict__ dst,
+                                           int j, int Ns, int M, const cpx<T>* W, int dir) {
+  const int nb = M / R;
+  const int k = j % Ns;
+  cpx<T> v[R];
+#pragma unroll
+  for (int q = 0; q < R; ++q) v[q] = src[j + q * nb];
+  const int tstep = k * (M / (Ns * R));
+  if (k) {
+#pragma unroll
+    for (int q = 1; q < R; ++q) v[q] = mulc<T>(v[q], W[q * tstep], dir > 0);
+  }
+  if (R == 3) dft3<T>(v, dir);
+  else if (R == 5) dft5<T>(v, dir);
+  else dftR<T, R>(v, W, M, dir);
+  const int base = (j / Ns) * Ns * R + k;
+#pragma unroll
+  for (int q = 0; q < R; ++q) dst[base + q * Ns] = v[q];
+}
+
+// Runtime radix (any odd prime) straight from shared memory: O(R^2) per butterfly.
+template <typename T>
+__device__ void stage_bfly_generic(const cpx<T>* __restrict__ src, cpx<T>* __restrict__ dst,
+                                   int j, int Ns, int M, int R, const cpx<T>* W, int dir) {
+  const int nb = M / R;
+  const int k = j % Ns;
+  const int tstep = k * (M / (Ns * R));
+  const int step = M / R;
+  const int base = (j / Ns) * Ns * R + k;
+  for (int s = 0; s < R; ++s) {
+    cpx<T> acc = src[j];
+    for (int q = 1; q < R; ++q) {
+      cpx<T> vq = mulc<T>(src[j + q * nb], W[q * tstep], dir > 0);
+      acc = add<T>(acc, mulc<T>(vq, W[((q * s) % R) * step], dir > 0));
+    }
+    dst[base + s * Ns] = acc;
+  }
+}
+
+// G pencils of length M at a + g*ld (ping-pong with b, same strides). The CTA runs
+// all stages; returns the buffer holding the result. Ends with __syncthreads().
+template <typename T>
+__device__ cpx<T>* fft_pencils(cpx<T>* a, cpx<T>* b, int G, int ld, const FftPlan& plan,
+                               const cpx<T>* W, int dir) {
+  const int M = plan.M;
+  int Ns = 1;
+  cpx<T>* src = a;
+  cpx<T>* dst = b;
+  for (int s = 0; s < plan.nrad; ++s) {
+    const int R = plan.radix[s];
+    const int nb = M / R;
+    const int total = G * nb;
+    for (int t = threadIdx.x; t < total; t += blockDim.x) {
+      const int g = t / nb;
+      const int j = t - g * nb;
+      const cpx<T>* sp = src + (size_t)g * ld;
+      cpx<T>* dp = dst + (size_t)g * ld;
+      switch (R) {
+        case 3: stage_bfly<T, 3>(sp, dp, j, Ns, M, W, dir); break;
+        case 5: stage_bfly<T, 5>(sp, dp, j, Ns, M, W, dir); break;
+        case 7: stage_bfly<T, 7>(sp, dp, j, Ns, M, W, dir); break;
+        case 11: stage_bfly<T, 11>(sp, dp, j, Ns, M, W, dir); break;
+        case 13: stage_bfly<T, 13>(sp, dp, j, Ns, M, W, dir); break;
+        default: stage_bfly_generic<T>(sp, dp, j, Ns, M, R, W, dir); break;
+      }
+    }
+    __syncthreads();
+    cpx<T>* t = src; src = dst; dst = t;
+    Ns *= R;
+  }
+  return src;
+}
+
+// Deterministic block sum of one double per thread (fixed tree order).
+__device__ __forceinline__ double block_sum(double v, double* red) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) red[wid] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (threadIdx.x == 0) {
+    const int nw = (blockDim.x + 31) >> 5;
+    for (int w = 0; w < nw; ++w) s += red[w];
+  }
+  return s;  // valid in thread 0 only
+}
+
+// Frequency of storage index i in FFT order for odd length n.
+__device__ __forceinline__ int sfreq(int i, int n) { return i <= (n - 1) / 2 ? i : i - n; }
+
+// Per-side CG scalars (device memory), one slot per right-hand side.
+struct CgScalars {
+  double rr[3];
+  double pq[3];
+  double alpha[3];
+  double beta[3];
+  double tol2;
+  int active[3];   // 1 while the solve runs
+  int iters[3];
+  int status[3];   // 0 ok/converged, 1 running, -2 breakdown
+};
+
+}  // namespace homb

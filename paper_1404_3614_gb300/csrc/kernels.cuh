@@ -1,0 +1,129 @@
+// Launch interface between the C-ABI layer (api.cu) and the kernels (kernels.cu).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "common.cuh"
+
+namespace homb {
+
+// Pencil pass along a strided axis: data[slab][P][X] with X contiguous.
+// dir = +1: input holds Nlog frequencies in FFT order, zero-padded to M, inverse
+//           transform, M outputs (Pout == M).
+// dir = -1: input holds M grid values, forward transform, the Nlog kept
+//           frequencies are written in FFT order (Pout == Nlog).
+// prologue: 0 none; 1 CG direction update p = r + beta p (in = p, aux = r, writes p);
+//           2 add the constant field e_rhs at k = 0 (energy fields u = e + x).
+struct PencilArgs {
+  const void* in;
+  void* out;
+  const void* aux;
+  long long in_slab, out_slab;
+  int nslab, X, XC, Pin, Pout, Nlog, dir;
+  int slabs_per_rhs, slabs_per_comp, C;
+  int prologue;
+  const void* W;
+  FftPlan plan;
+  CgScalars* cg;   // may be null: no skipping
+};
+
+// Last forward pass (z in 3D, y in 2D) over all C components of one field:
+// in [rhs][c][M][X] -> out [rhs][c][N][X], then Gamma^E / Gamma^J (project = 1 / 2),
+// none (0), and with `cg` the CG partial sums p.q (aux = p).
+struct FinalArgs {
+  const void* in;
+  void* out;
+  const void* aux;
+  long long in_comp, out_comp;   // element stride between components
+  int nrhs, C, X, XC, M, Nlog;
+  int project;                   // 0 none, 1 Gamma^E, 2 Gamma^J
+  int d, Ny, Nh;                 // frequency decoding (3D: X = Ny*Nh; 2D: X = Nh)
+  double invY[3];
+  const void* W;
+  FftPlan plan;
+  CgScalars* cg;
+  double* partial;               // [rhs][gridDim.x]
+  int partial_ld;
+};
+
+// Row pass along x (the contiguous axis) on rows of Nin complex values (k1 >= 0):
+// mode 0 (matvec): c2r, v = (A u) * scale per grid point, r2c, keep Nout values;
+// mode 1 (energy): c2r, partial sums of u_r . A u_s over the rows;
+// mode 2 (c2r):    c2r only, real rows written to out_real.
+struct XArgs {
+  const void* in;
+  void* out;           // mode 0: complex rows (may equal in); mode 2: real rows
+  const void* coef;    // real [ncomp][planes][M]
+  int mode;
+  int planes;          // rows per component (Mz*My)
+  int YB;              // planes per CTA
+  int Nin, Nout, M;
+  int R, C, ncomp, d;
+  long long comp_stride;  // elements between components of the row storage
+  double scale;
+  const void* W;
+  FftPlan plan;
+  CgScalars* cg;
+  double* partial;        // mode 1: [gridDim.x][R*R]
+};
+
+struct DevIncl {
+  int shape;       // 0 box, 1 ball / disk
+  int same_as_prev;// 1 when shape and size equal the previous inclusion's (radial reuse)
+  double c[3];
+  double h[3];     // box sides, or radius in h[0]
+  double dA[6];    // increment of this side's coefficient, packed symmetric
+};
+
+struct SpecArgs {
+  int d, ncomp, nincl;
+  int M[3];        // double grid (1 for unused axes)
+  int len[3];      // stored extents of the output index set (x is the half range)
+  int Nmod[3];     // modulus for signed decoding of y/z storage indices
+  double invY[3];
+  double invVol;
+  double A0p[6];
+  const DevIncl* incl;
+  const double2* phase;   // [nincl][3][Mmax]
+  const double* sinc;     // [nincl][3][Mmax]
+  int Mmax;
+};
+
+// launchers (return cudaGetLastError())
+template <typename T> cudaError_t launch_pencil(const PencilArgs& a, cudaStream_t s);
+template <typename T> cudaError_t launch_final(const FinalArgs& a, cudaStream_t s);
+template <typename T> cudaError_t launch_xpass(const XArgs& a, int grid_y, cudaStream_t s);
+template <typename T> int pencil_xc(int M, int X, int C);   // chunk that fits shared memory
+template <typename T> int xpass_yb(int M, int rows_per_plane, int planes);
+
+cudaError_t launch_axis_tables(int nincl, int d, const int* M, int Mmax, const double* invY,
+                               const DevIncl* incl, double2* phase, double* sinc, cudaStream_t s);
+// Fourier coefficients of the side's coefficient on the half index set of Z_M,
+// out [ncomp][Mz][My][(Mx+1)/2] complex FP64.
+cudaError_t launch_spectrum(const SpecArgs& a, double2* out, cudaStream_t s);
+// b_r(k) = -Gamma(k) A_hat(k) e_r on Z_N (half), FP64 or FP32, plus |b|^2 partials.
+template <typename T>
+cudaError_t launch_rhs(const SpecArgs& a, int side, int nrhs, int Nh, const int* N, void* b,
+                       double* partial, int nblk, cudaStream_t s);
+template <typename T>
+cudaError_t launch_cg_update(void* x, void* r, const void* p, const void* q, int nrhs, int C,
+                             long long field, int Nh, CgScalars* cg, double* partial, int nblk,
+                             cudaStream_t s);
+cudaError_t launch_cg_init(CgScalars* cg, const double* partial, int ld, int nblk, int nrhs,
+                           double tol2, cudaStream_t s);
+cudaError_t launch_cg_alpha(CgScalars* cg, const double* partial, int ld, int nblk, int nrhs,
+                            cudaStream_t s);
+cudaError_t launch_cg_beta(CgScalars* cg, const double* partial, int ld, int nblk, int nrhs,
+                           cudaStream_t s);
+// x64 = Gamma (double) x_T (in place allowed for T = double)
+template <typename T>
+cudaError_t launch_project_promote(const void* x, double2* x64, int nrhs, int d, int Ny, int Nz,
+                                   int Nh, const double* invY, int side, cudaStream_t s);
+cudaError_t launch_energy_reduce(const double* partial, int nblk, int nrr, double* out,
+                                 cudaStream_t s);
+cudaError_t launch_convert_d2f(const double* in, float* out, long long n, cudaStream_t s);
+template <typename T>
+cudaError_t launch_fft_batch(const void* in, void* out, int M, int howmany, int dir, const void* W,
+                             const FftPlan& plan, cudaStream_t s);
+
+}  // namespace homb

@@ -1,0 +1,169 @@
+"""Whole-pipeline parity of hom_bounds against the oracle, and properties at full size.
+
+FP64: upper and lower bounds within 1e-10 relative (Frobenius-scaled max entry error)
+of the dense oracle (the Galerkin definition) on small grids; mixed precision (FP32
+inner CG, FP64 re-projection and energies) within 1e-6 with lower <= upper kept.
+The full-size 3D N = 41 cube cell is checked on sampled operator rows (computed one
+by one by the oracle from the Fourier convolution of Lemma Ga_full) and on the
+properties that hold at any size.
+"""
+import numpy as np
+import pytest
+
+import microstructures as ms
+import oracle
+from oracle import matfree
+
+from layout import full_to_half, half_to_full, random_real_field
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def hb():
+    import paper_1404_3614_gb300 as hb
+    return hb
+
+
+@pytest.fixture(scope="module")
+def solver(hb):
+    s = hb.Bounds(0)
+    yield s
+    s.close()
+
+
+def rel(a, b):
+    return np.abs(a - b).max() / np.linalg.norm(b)
+
+
+def loewner_ge(A, B, tol=1e-12):
+    S = 0.5 * ((A - B) + (A - B).T)
+    return np.linalg.eigvalsh(S).min() >= -tol * max(1.0, np.abs(A).max())
+
+
+CASES = {
+    "square2d_N9": lambda: ms.square_inclusion_2d(N=9),
+    "square2d_N23": lambda: ms.square_inclusion_2d(N=23),
+    "paper_rho1000_N15": lambda: ms.paper_square_2d(15, 1000.0),
+    "aniso2d_N9": lambda: ms.random_anisotropic_2d(3, N=9),
+    "aniso3d_N5": lambda: ms.random_anisotropic_3d(4, N=5),
+    "cube3d_N7": lambda: ms.cube_inclusion_3d(N=7),
+    "rect2d_N15": lambda: ms.random_rectangles_2d(11, N=15),
+    "spheres3d_N7": lambda: ms.random_spheres_3d(2, N=7, n_balls=6, phi=0.25, contrast=30.0),
+    "laminate_N11": lambda: ms.laminate_2d(11),
+    "homogeneous3d": lambda: ms.homogeneous(3, 5, np.array([[2.0, 0.1, 0.0], [0.1, 1.5, 0.2], [0.0, 0.2, 1.0]])),
+    "N1_voigt_reuss": lambda: ms.random_anisotropic_2d(5, N=1),
+}
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_fp64_bounds_match_dense_oracle(hb, solver, name):
+    p = CASES[name]()
+    ref = oracle.dense_bounds(p)
+    out = solver(p, precision=hb.HOM_FP64, tol=1e-12)
+    for key in ("upper", "lower", "mean", "D"):
+        scale = np.linalg.norm(ref["upper"])
+        assert np.abs(out[key] - ref[key]).max() <= 1e-10 * scale, (name, key, out[key], ref[key])
+    assert out["status"] == 0
+
+
+@pytest.mark.parametrize("name", [n for n in CASES if n != "homogeneous3d"])
+def test_mixed_bounds_within_1e6_and_ordered(hb, solver, name):
+    p = CASES[name]()
+    ref = oracle.dense_bounds(p)
+    out = solver(p, precision=hb.HOM_MIXED, tol=1e-6)
+    for key in ("upper", "lower"):
+        assert rel(out[key], ref[key]) <= 1e-6, (name, key, rel(out[key], ref[key]))
+    assert loewner_ge(out["upper"], out["lower"])
+    # guaranteed: any conforming field bounds from the correct side
+    assert loewner_ge(out["upper"], ref["upper"], 1e-9)
+    assert loewner_ge(ref["lower"], out["lower"], 1e-9)
+
+
+def test_double_grid_cg_oracle_at_mid_size(hb, solver):
+    """2D N = 45 (double grid 89): O2 (naive DFT + CG) against the FP64 CUDA path."""
+    p = ms.random_rectangles_2d(17, N=45)
+    ref = oracle.matfree_bounds(p, tol=1e-11)
+    out = solver(p, precision=hb.HOM_FP64, tol=1e-11)
+    for key in ("upper", "lower"):
+        assert rel(out[key], ref[key]) <= 1e-10, (key, rel(out[key], ref[key]))
+
+
+def test_repeatable_bitwise(hb, solver):
+    p = ms.random_anisotropic_3d(9, N=7)
+    a = solver(p, precision=hb.HOM_FP64, tol=1e-10)
+    b = solver(p, precision=hb.HOM_FP64, tol=1e-10)
+    assert np.array_equal(a["upper"], b["upper"]) and np.array_equal(a["lower"], b["lower"])
+    assert a["report"]["iters"] == b["report"]["iters"]
+
+
+def test_not_converged_still_bounds(hb, solver):
+    """max_iter reached: HOM_WARN_NOT_CONVERGED, the bounds stay guaranteed (Lemma bounds)."""
+    p = ms.paper_square_2d(15, 1000.0)
+    ref = oracle.dense_bounds(p)
+    out = solver(p, precision=hb.HOM_FP64, tol=1e-14, max_iter=3, check_every=1)
+    assert out["status"] == hb.binding.HOM_WARN_NOT_CONVERGED
+    assert loewner_ge(out["upper"], ref["upper"], 1e-12)
+    assert loewner_ge(ref["lower"], out["lower"], 1e-12)
+
+
+def test_homogeneous_takes_no_iterations(hb, solver):
+    p = CASES["homogeneous3d"]()
+    out = solver(p, precision=hb.HOM_FP64)
+    assert out["report"]["matvecs"] == 0
+    assert np.abs(out["upper"] - p.A0).max() < 1e-14 and np.abs(out["lower"] - p.A0).max() < 1e-14
+
+
+# ------------------------------------------------------------------------------------
+# full size: the 3D N = 41 cube cell (double grid 81^3), the bench workload
+# ------------------------------------------------------------------------------------
+def test_full_size_cube_matvec_sampled_rows(hb):
+    p = ms.cube_inclusion_3d()
+    d = 3
+    N = tuple(int(n) for n in p.N)
+    ctx = hb.hom_create(0)
+    try:
+        rng = np.random.default_rng(123)
+        info = hb.hom_problem_info(ctx, p)
+        nws = hb.hom_step_workspace_size(ctx, p, d)
+        ws = torch.empty(nws, dtype=torch.uint8, device="cuda")
+        fields = [random_real_field(rng, d, N) for _ in range(d)]
+        uin = torch.from_numpy(np.stack([full_to_half(u, d) for u in fields])).cuda()
+        ls = np.array([[0, 0, 0], [1, 0, 0], [0, -3, 2], [20, 20, -20], [-7, 13, 5], [3, -20, 11]])
+        for side in (0, 1):
+            coef = torch.empty((info["ncomp"],) + tuple(info["M"][::-1]), dtype=torch.float64, device="cuda")
+            hb.hom_coefficient(ctx, p, side, hb.HOM_FP64, coef.data_ptr(), ws.data_ptr(), nws)
+            out = torch.zeros_like(uin)
+            hb.hom_matvec(ctx, p, side, hb.HOM_FP64, 1, d, coef.data_ptr(), uin.data_ptr(), out.data_ptr(),
+                          ws.data_ptr(), nws)
+            got = out.cpu().numpy()
+            for r in range(d):
+                full = half_to_full(got[r], d, N[0])
+                rows = matfree.matvec_sampled(p, "primal" if side == 0 else "dual", fields[r], ls)
+                for i, l in enumerate(ls):
+                    idx = tuple(l + (np.array(N) - 1) // 2)
+                    v = full[(slice(None),) + idx]
+                    assert np.abs(v - rows[i]).max() <= 1e-11 * max(1.0, np.abs(rows[i]).max()), (side, r, l)
+    finally:
+        hb.hom_destroy(ctx)
+
+
+def test_full_size_cube_bounds_properties(hb, solver):
+    p = ms.cube_inclusion_3d()
+    f = p.volume_fraction()
+    voigt = (1 - f) * 1.0 + f * 100.0
+    reuss = 1.0 / ((1 - f) / 1.0 + f / 100.0)
+    out64 = solver(p, precision=hb.HOM_FP64, tol=1e-8)
+    outmx = solver(p, precision=hb.HOM_MIXED, tol=1e-6)
+    for out in (out64, outmx):
+        up, lo = out["upper"], out["lower"]
+        assert loewner_ge(up, lo) and loewner_ge(voigt * np.eye(3), up) and loewner_ge(lo, reuss * np.eye(3))
+        # centred cube + isotropic phases: bounds proportional to I (Sec. 7)
+        assert np.abs(up - up[0, 0] * np.eye(3)).max() < 1e-9 * up[0, 0]
+        assert np.abs(lo - lo[0, 0] * np.eye(3)).max() < 1e-9 * lo[0, 0]
+    assert rel(outmx["upper"], out64["upper"]) < 1e-6 and rel(outmx["lower"], out64["lower"]) < 1e-6
+    # bounds tighten from N = 21 to N = 41 (nested spaces, exact integration)
+    small = solver(p.with_N(21), precision=hb.HOM_FP64, tol=1e-8)
+    assert out64["upper"][0, 0] <= small["upper"][0, 0] + 1e-9
+    assert out64["lower"][0, 0] >= small["lower"][0, 0] - 1e-9
