@@ -1,0 +1,412 @@
+#!/usr/bin/env python
+"""Benchmark: time to guaranteed bounds on the 3D cube cell, N = 41^3 (double grid 81^3).
+
+One step = one hom_bounds call = the whole hot path: both double-grid coefficients
+built from the closed-form inclusion coefficients, 3 primal and 3 dual CG solves (E =
+e1, e2, e3) to a relative residual of 1e-4, FP64 re-projection and the exact
+double-grid bound energies, upper and inv(lower) on the host.
+
+Prints one JSON line (rank 0). Default: 1 GPU, plain FP64 CG (the workload's stated
+precision), 10 timed steps after 3 warm-up steps, L2 flushed between steps. Extra
+keys report the mixed-precision path (FP32 inner CG, FP64 outer) on the same
+workload and single-matvec timings. ``--impl reference`` times the CPU oracle
+instead (the reference arm of this comparison).
+
+Multi-GPU: independent replicas (the path does not shard): under torchrun each rank
+runs the same workload on its own GPU; timing is max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "time to bounds at 1e-4 rel. residual; matvec HBM GB/s; vs plain FP64 CG"
+WORKLOAD = ("3D d=3, N=41^3 (double grid 81^3), centred cube inclusion side 0.5, contrast 100 "
+            "(a=1 matrix, a=100 inclusion), plain CG, primal and dual bounds for E=e1,e2,e3, "
+            "stop at ||r|| <= 1e-4 ||E||")
+TOL = 1e-4
+# FP64 CG iterations of this workload at 1e-4 (primal, dual), per right-hand side: a
+# property of the problem (CG in exact arithmetic); measured by running the oracle's
+# own CG to completion, pinned by tests/test_bench_host.py.
+ORACLE_ITERS = {"primal": 46, "dual": 24}
+FP64_PEAK_TFLOPS = 1.25     # nominal GB300 FP64 (the recipe's table); a probe measured 1.256
+
+
+def workload():
+    import microstructures as ms
+    return ms.cube_inclusion_3d()
+
+
+# ------------------------------------------------------------------------------------
+# distributed helpers (host logic; covered by CPU gloo tests)
+# ------------------------------------------------------------------------------------
+def dist_env():
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), \
+        int(os.environ.get("LOCAL_RANK", "0"))
+
+
+def max_over_ranks(value: float, world: int, device=None) -> float:
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world: int):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+# ------------------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ------------------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------------------------
+# algorithmic FLOP counts (conventional 5 M log2 M per complex length-M FFT)
+# ------------------------------------------------------------------------------------
+def fft_flops(M: int) -> float:
+    return 5.0 * M * math.log2(M) if M > 1 else 0.0
+
+
+def family_flops_per_launch(problem, family: str, nrhs: int) -> float:
+    """FFT flops one launch of a kernel family performs on the operator of `problem`."""
+    d = problem.d
+    N = [int(n) for n in problem.N] + [1] * (3 - d)
+    M = [2 * n - 1 for n in N]
+    Nh = (N[0] + 1) // 2
+    RC = nrhs * d
+    if family == "xpass":
+        return RC * M[1] * M[2] * fft_flops(M[0])          # pairs of real rows -> one complex FFT each way
+    if family == "zpass":
+        return RC * N[1] * Nh * fft_flops(M[2])
+    if family == "final":
+        return RC * (N[1] * Nh * fft_flops(M[2]) if d == 3 else Nh * fft_flops(M[1]))
+    if family == "ypass":
+        return RC * M[2] * Nh * fft_flops(M[1])
+    return 0.0
+
+
+# ------------------------------------------------------------------------------------
+# CPU oracle leg
+# ------------------------------------------------------------------------------------
+def oracle_sample(problem, iters, n_matvec: int):
+    """Time the oracle on a bounded sample and extrapolate to one full time to bounds.
+
+    Sample: both double-grid coefficient builds (naive inverse DFT) + n_matvec
+    double-grid matvecs per side on one right-hand side. Estimate: coefficient builds
+    + (iters_side x d) matvecs per side + d/2 matvec-equivalents per side for the energies.
+    """
+    import numpy as np
+    from oracle import matfree
+    d = problem.d
+    total = 0.0
+    t_coef = 0.0
+    t_mv = {}
+    for side in ("primal", "dual"):
+        t = time.perf_counter()
+        op = matfree.MatFreeOperator(problem, side)
+        t_coef += time.perf_counter() - t
+        u = op.constant_field(np.eye(d)[0])
+        u = op.apply(u)
+        t = time.perf_counter()
+        for _ in range(n_matvec):
+            u = op.apply(u)
+            u /= max(np.abs(u).max(), 1e-300)
+        t_mv[side] = (time.perf_counter() - t) / n_matvec
+    for side in ("primal", "dual"):
+        total += (iters[side] * d + 0.5 * d) * t_mv[side]
+    est = (t_coef + total) * 1e3
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    threads = int(os.environ.get("OPENBLAS_NUM_THREADS", os.environ.get("OMP_NUM_THREADS", cores)))
+    sample = (f"oracle O2 (naive-DFT double-grid CG, numpy fp64): both coefficient builds + {n_matvec} "
+              f"matvecs per side on one RHS, timed; extrapolated with {iters['primal']}/{iters['dual']} "
+              f"CG iterations x {d} RHS per side + d/2 matvecs per side for the energies")
+    return est, {"value": est, "unit": "ms", "cores": min(threads, cores), "kind": "oracle", "sample": sample,
+                 "matvec_ms": {k: v * 1e3 for k, v in t_mv.items()}, "coef_ms": t_coef * 1e3}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    problem = workload()
+    vals = []
+    info = None
+    for i in range(args.warmup + args.steps):
+        v, info = oracle_sample(problem, ORACLE_ITERS, n_matvec=max(2, args.ref_matvecs // 3))
+        if i >= args.warmup:
+            vals.append(v)
+    value = statistics.mean(vals)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "ms", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": value, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "impl": "CPU oracle (naive DFT double-grid CG)"},
+            "cpu_baseline": info, "e2e": {"value": value, "unit": "ms", "h2d_bytes_per_step": 0,
+                                          "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------------------------
+# GPU leg
+# ------------------------------------------------------------------------------------
+def run_gpu(args):
+    import numpy as np
+    import torch
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1404_3614_gb300 as hb
+
+    problem = workload()
+    prec = hb.HOM_FP64 if args.precision == "fp64" else hb.HOM_MIXED
+    solver = hb.Bounds(local)
+    stream = torch.cuda.current_stream(dev)
+    s_ptr = stream.cuda_stream
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)   # > L2 (129 MB)
+
+    def step(precision):
+        return solver(problem, precision=precision, tol=TOL, stream=s_ptr)
+
+    for _ in range(args.warmup):
+        out = step(prec)
+    torch.cuda.synchronize()
+
+    # dominant kernel family: one untimed profiled step per family
+    fam_ms = {}
+    for fam in ("xpass", "ypass", "zpass", "final", "cg", "coef", "energy"):
+        hb.hom_profile_kernel(solver.ctx, fam)
+        step(prec)
+        n, ms = hb.hom_kernel_timing(solver.ctx)
+        fam_ms[fam] = (n, ms)
+    hb.hom_profile_kernel(solver.ctx, "")
+    dom = max(fam_ms, key=lambda f: fam_ms[f][1])
+
+    # timed region: K steps, device time by CUDA events on the launching stream,
+    # L2 flushed between steps (outside the events), dominant family timed live
+    hb.hom_profile_kernel(solver.ctx, dom)
+    times = []
+    launches = 0
+    reports = []
+    barrier(world)
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        for _ in range(args.steps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            out = step(prec)
+            e1.record(stream)
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1))
+            reports.append(out["report"])
+            launches += out["report"]["launches"]
+    torch.cuda.synchronize()
+    barrier(world)
+    dom_n, dom_ms = hb.hom_kernel_timing(solver.ctx)
+    hb.hom_profile_kernel(solver.ctx, "")
+    ms_step = statistics.mean(times)
+    ms_step = max_over_ranks(ms_step, world, dev)
+
+    # end to end through the public API: host problem in, host bounds out, wall clock
+    e2e = []
+    for _ in range(max(3, args.steps // 2)):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        o = step(prec)
+        e2e.append((time.perf_counter() - t) * 1e3)
+    e2e_ms = max_over_ranks(statistics.mean(e2e), world, dev)
+    rep = o["report"]
+
+    # the other precision on the same workload (plain FP64 vs mixed)
+    other = hb.HOM_MIXED if prec == hb.HOM_FP64 else hb.HOM_FP64
+    alt = []
+    for _ in range(max(3, args.steps // 2)):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        oo = step(other)
+        e1.record(stream)
+        e1.synchronize()
+        alt.append(e0.elapsed_time(e1))
+    alt_ms = statistics.mean(alt)
+
+    # one operator application (3 fields) per precision, through hom_matvec
+    mv = matvec_timings(hb, solver, problem, dev, stream)
+
+    # roofline of the dominant kernel family
+    nrhs = problem.d
+    per_launch_ms = dom_ms / max(dom_n, 1)
+    flops = family_flops_per_launch(problem, dom, nrhs)
+    roof = None
+    if flops > 0 and per_launch_ms > 0:
+        achieved = flops / (per_launch_ms * 1e-3) / 1e12
+        roof = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
+                "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                "flops_per_launch": flops, "launches": dom_n, "avg_launch_ms": per_launch_ms,
+                "peak_note": "FP64 nominal 1.25 TFLOP/s (recipe table); FMA probe measured 1.256"}
+        if prec != hb.HOM_FP64:
+            roof["note"] = "mixed: dominant family mixes FP32 inner and FP64 outer launches"
+
+    line = {
+        "metric": METRIC, "value": ms_step, "unit": "ms", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64" if prec == hb.HOM_FP64 else "f32+f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "precision": args.precision, "tol": TOL,
+                   "l2": "flushed between steps (256 MiB write, outside the timed region)",
+                   "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
+        "bounds": {"upper_11": float(out["upper"][0, 0]), "lower_11": float(out["lower"][0, 0])},
+        "iters": reports[-1]["iters"], "matvecs": reports[-1]["matvecs"],
+        "gpu_launches": launches,
+        "e2e": {"value": e2e_ms, "unit": "ms", "h2d_bytes_per_step": rep["h2d_bytes"],
+                "d2h_bytes_per_step": rep["d2h_bytes"],
+                "note": "hom_bounds wall clock: host problem in, host bounds out"},
+        "alt_precision": {"precision": "mixed" if other == hb.HOM_MIXED else "fp64", "ms": alt_ms,
+                          "speedup_vs_this": ms_step / alt_ms if alt_ms > 0 else None,
+                          "upper_11": float(oo["upper"][0, 0]), "lower_11": float(oo["lower"][0, 0])},
+        "matvec": mv,
+        "kernel_families_ms_one_step": {k: v[1] for k, v in fam_ms.items()},
+        "roofline": roof,
+        "clocks": clk.summary(),
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        iters = {"primal": max(reports[-1]["iters"][0]), "dual": max(reports[-1]["iters"][1])}
+        _, info = oracle_sample(problem, iters, n_matvec=args.ref_matvecs)
+        line["cpu_baseline"] = info
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    solver.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def matvec_timings(hb, solver, problem, dev, stream, reps=20):
+    """Device time of one operator application on d fields, FP64 and FP32."""
+    import torch
+    ctx = solver.ctx
+    info = hb.hom_problem_info(ctx, problem)
+    d = problem.d
+    nws = hb.hom_step_workspace_size(ctx, problem, d)
+    ws = torch.empty(nws, dtype=torch.uint8, device=dev)
+    shape = (d, d, int(problem.N[2]), int(problem.N[1]), (int(problem.N[0]) + 1) // 2)
+    out = {}
+    for name, prec, cdt, rdt in (("fp64", hb.HOM_FP64, torch.complex128, torch.float64),
+                                 ("fp32", hb.HOM_FP32, torch.complex64, torch.float32)):
+        coef = torch.empty((info["ncomp"],) + tuple(info["M"][::-1]), dtype=rdt, device=dev)
+        hb.hom_coefficient(ctx, problem, 0, prec, coef.data_ptr(), ws.data_ptr(), nws, stream.cuda_stream)
+        x = torch.randn(shape, dtype=cdt, device=dev)
+        y = torch.empty_like(x)
+        for _ in range(3):
+            hb.hom_matvec(ctx, problem, 0, prec, 1, d, coef.data_ptr(), x.data_ptr(), y.data_ptr(),
+                          ws.data_ptr(), nws, stream.cuda_stream)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            hb.hom_matvec(ctx, problem, 0, prec, 1, d, coef.data_ptr(), x.data_ptr(), y.data_ptr(),
+                          ws.data_ptr(), nws, stream.cuda_stream)
+        e1.record(stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        flops = sum(family_flops_per_launch(problem, f, d) * (2 if f == "ypass" else 1)
+                    for f in ("zpass", "ypass", "xpass", "final"))
+        out[name] = {"ms": ms, "fft_tflops": flops / (ms * 1e-3) / 1e12, "fields": d}
+    return out
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--ref-matvecs", type=int, default=20)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

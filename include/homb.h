@@ -105,8 +105,11 @@ typedef struct {
   int32_t iters[2][3];  /* [side][rhs] CG iterations                             */
   double resid[2][3];   /* [side][rhs] final recursive residual / ||E||          */
   int32_t matvecs;      /* operator applications issued (all rhs together)       */
-  int32_t status[2][3]; /* per solve: 0 converged, 1 max_iter, -2 breakdown      */
+  int32_t status[2][3]; /* per solve: 0 converged, 1 max_iter or stalled         */
   double ms_total;      /* host wall time of the call                            */
+  int64_t launches;     /* CUDA kernels launched by the call                     */
+  int64_t h2d_bytes;    /* host->device bytes copied by the call                 */
+  int64_t d2h_bytes;    /* device->host bytes copied by the call                 */
 } hom_report;
 
 typedef struct hom_ctx hom_ctx;

@@ -45,7 +45,8 @@ class hom_opts(C.Structure):
 
 class hom_report(C.Structure):
     _fields_ = [("iters", (C.c_int32 * 3) * 2), ("resid", (C.c_double * 3) * 2), ("matvecs", C.c_int32),
-                ("status", (C.c_int32 * 3) * 2), ("ms_total", C.c_double)]
+                ("status", (C.c_int32 * 3) * 2), ("ms_total", C.c_double), ("launches", C.c_int64),
+                ("h2d_bytes", C.c_int64), ("d2h_bytes", C.c_int64)]
 
 
 class HombError(RuntimeError):
@@ -205,7 +206,8 @@ def hom_bounds(ctx, problem, opts, d_ws, ws_bytes, stream=0):
         "iters": [list(rep.iters[s]) for s in range(2)],
         "resid": [list(rep.resid[s]) for s in range(2)],
         "status": [list(rep.status[s]) for s in range(2)],
-        "matvecs": rep.matvecs, "ms_total": rep.ms_total,
+        "matvecs": rep.matvecs, "ms_total": rep.ms_total, "launches": rep.launches,
+        "h2d_bytes": rep.h2d_bytes, "d2h_bytes": rep.d2h_bytes,
     }
     return out
 

@@ -32,6 +32,8 @@ struct hom_ctx {
   std::string prof_family;
   std::vector<cudaEvent_t> ev;         // start/stop pairs
   size_t ev_used = 0;
+  long long launches = 0;              // kernels launched (since the call began)
+  long long h2d = 0, d2h = 0;          // bytes copied
 };
 
 namespace {
@@ -49,11 +51,27 @@ constexpr int kVecBlocks = 304;   // 2 x 152 SMs for the elementwise CG kernels
     }                                                                                          \
   } while (0)
 
+// a kernel launch: checked and counted
+#define KL(expr)          \
+  do {                    \
+    CK(expr);             \
+    ++ctx->launches;      \
+  } while (0)
+
 #define CKS(expr)                                                                              \
   do {                                                                                         \
     hom_status _s = (expr);                                                                    \
     if (_s != HOM_OK) return _s;                                                               \
   } while (0)
+
+cudaError_t h2d_copy(hom_ctx* ctx, void* dst, const void* src, size_t bytes, cudaStream_t st) {
+  ctx->h2d += (long long)bytes;
+  return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, st);
+}
+cudaError_t d2h_copy(hom_ctx* ctx, void* dst, const void* src, size_t bytes, cudaStream_t st) {
+  ctx->d2h += (long long)bytes;
+  return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, st);
+}
 
 hom_status fail(hom_ctx* ctx, hom_status s, const std::string& msg) {
   if (ctx) ctx->err = msg;
@@ -82,12 +100,16 @@ struct Geometry {
 };
 
 bool spd(const double* A, int d) {
-  // symmetric and Cholesky-positive (leading dim 3)
+  // symmetric (relative to the largest entry) and Cholesky-positive (leading dim 3)
+  double amax = 0.0;
   for (int i = 0; i < d; ++i)
     for (int j = 0; j < d; ++j) {
-      const double a = A[3 * i + j], b = A[3 * j + i];
-      if (!std::isfinite(a) || std::fabs(a - b) > 1e-12 * (std::fabs(a) + std::fabs(b) + 1e-300)) return false;
+      if (!std::isfinite(A[3 * i + j])) return false;
+      amax = std::max(amax, std::fabs(A[3 * i + j]));
     }
+  for (int i = 0; i < d; ++i)
+    for (int j = 0; j < i; ++j)
+      if (std::fabs(A[3 * i + j] - A[3 * j + i]) > 1e-12 * amax) return false;
   double L[3][3] = {};
   for (int i = 0; i < d; ++i)
     for (int j = 0; j <= i; ++j) {
@@ -224,8 +246,8 @@ void pack_sym(const double* A, int d, int ncomp, double* out) {  // A leading di
 // workspace layout
 // ---------------------------------------------------------------------------------
 struct Layout {
-  size_t tw64[3], tw32[3], incl, phase, sinc, coef64, coef32, x, r, p, q, x64, t1, t2, cg[2],
-      partial, epart, eout, total;
+  size_t tw64[3], tw32[3], incl, phase, sinc, coef64, coef32, x, r, p, q, x64, b64, r64, t1, t2,
+      cg[2], cgo[2], partial, epart, eout, total;
   int Mmax, maxblk, nblk_energy;
   size_t off = 0;
   size_t take(size_t bytes) {
@@ -268,9 +290,13 @@ Layout make_layout(const Geometry& g, int R, size_t elem, int mode) {
     L.p = L.take(fb);
     L.q = L.take(fb);
     L.x64 = elem == 8 ? L.take((size_t)RC * g.field * 16) : L.x;
+    L.b64 = elem == 8 ? L.take((size_t)RC * g.field * 16) : 0;
+    L.r64 = elem == 8 ? L.take((size_t)RC * g.field * 16) : 0;
   }
   L.cg[0] = L.take(sizeof(CgScalars));
   L.cg[1] = L.take(sizeof(CgScalars));
+  L.cgo[0] = L.take(sizeof(CgScalars));
+  L.cgo[1] = L.take(sizeof(CgScalars));
   const int X = g.d == 3 ? g.N[1] * g.Nh : g.Nh;
   const int xc = std::max(1, std::min(final_xc_elem(g, 16), final_xc_elem(g, 8)));
   L.maxblk = std::max(kVecBlocks, (X + xc - 1) / xc);
@@ -335,8 +361,8 @@ struct Runner {
     std::vector<float2> w32;
     for (int a = 0; a < 3; ++a) {
       twiddles(g.M[a], w64, w32);
-      CK(cudaMemcpyAsync(base + L.tw64[a], w64.data(), w64.size() * sizeof(double2), cudaMemcpyHostToDevice, st));
-      CK(cudaMemcpyAsync(base + L.tw32[a], w32.data(), w32.size() * sizeof(float2), cudaMemcpyHostToDevice, st));
+      CK(h2d_copy(ctx, base + L.tw64[a], w64.data(), w64.size() * sizeof(double2), st));
+      CK(h2d_copy(ctx, base + L.tw32[a], w32.data(), w32.size() * sizeof(float2), st));
     }
     // inclusion tables for both sides: [side][j]
     const size_t n = g.incl.size();
@@ -369,7 +395,7 @@ struct Runner {
         }
         pack_sym(dA, g.d, g.ncomp, D.dA);
       }
-    CK(cudaMemcpyAsync(base + L.incl, di.data(), di.size() * sizeof(DevIncl), cudaMemcpyHostToDevice, st));
+    CK(h2d_copy(ctx, base + L.incl, di.data(), di.size() * sizeof(DevIncl), st));
     return HOM_OK;
   }
 
@@ -406,9 +432,9 @@ struct Runner {
   hom_status build_coefficient(int side, double* coef) {
     Prof pr(ctx, "coef", st);
     SpecArgs sa = spec_args(side);
-    CK(launch_axis_tables(sa.nincl, g.d, g.M, L.Mmax, g.invY, sa.incl, at<double2>(L.phase), at<double>(L.sinc), st));
+    KL(launch_axis_tables(sa.nincl, g.d, g.M, L.Mmax, g.invY, sa.incl, at<double2>(L.phase), at<double>(L.sinc), st));
     double2* S = at<double2>(L.t1);
-    CK(launch_spectrum(sa, S, st));
+    KL(launch_spectrum(sa, S, st));
     // 3D: z pass t1 -> t2, y pass t2 -> t1, rows from t1; 2D: y pass t1 -> t2, rows from t2
     const void* cur = S;
     void* nxt = at<void>(L.t2);
@@ -422,7 +448,7 @@ struct Runner {
       z.slabs_per_rhs = z.nslab; z.slabs_per_comp = 1; z.C = 1; z.prologue = 0;
       z.W = base + L.tw64[2]; z.plan = g.plan[2]; z.cg = nullptr;
       if (z.XC < 1) return fail(ctx, HOM_ERR_INVALID_ARG, "grid too large for the shared-memory FFT");
-      CK(launch_pencil<double>(z, st));
+      KL(launch_pencil<double>(z, st));
       cur = at<void>(L.t2);
       nxt = at<void>(L.t1);
     }
@@ -435,7 +461,7 @@ struct Runner {
     y.slabs_per_rhs = y.nslab; y.slabs_per_comp = 1; y.C = 1; y.prologue = 0;
     y.W = base + L.tw64[1]; y.plan = g.plan[1]; y.cg = nullptr;
     if (y.XC < 1) return fail(ctx, HOM_ERR_INVALID_ARG, "grid too large for the shared-memory FFT");
-    CK(launch_pencil<double>(y, st));
+    KL(launch_pencil<double>(y, st));
     XArgs x{};
     x.in = nxt; x.out = coef; x.coef = nullptr; x.mode = 2;
     x.planes = (int)g.planes; x.YB = xpass_yb<double>(g.M[0], 1, (int)g.planes);
@@ -443,7 +469,7 @@ struct Runner {
     x.comp_stride = g.planes * g.Nxs; x.scale = 1.0;
     x.W = base + L.tw64[0]; x.plan = g.plan[0]; x.cg = nullptr; x.partial = nullptr;
     if (x.YB < 1) return fail(ctx, HOM_ERR_INVALID_ARG, "grid too large for the shared-memory FFT");
-    CK(launch_xpass<double>(x, g.ncomp, st));
+    KL(launch_xpass<double>(x, g.ncomp, st));
     return HOM_OK;
   }
 
@@ -452,7 +478,7 @@ struct Runner {
   // project: 0 none, 1 Gamma^E, 2 Gamma^J.  addE: energy-style constant added (not used here).
   template <typename T>
   hom_status matvec(const void* in, void* out, const void* coef, int project, CgScalars* cg,
-                    const void* r_aux, const void* p_aux, int prologue) {
+                    const void* r_aux, const void* p_aux, int prologue, const void* bsub = nullptr) {
     const size_t tw = sizeof(T) == 8 ? 0 : 1;
     auto W = [&](int a) -> const void* { return base + (tw == 0 ? L.tw64[a] : L.tw32[a]); };
     const int C = g.d;
@@ -471,7 +497,7 @@ struct Runner {
       z.slabs_per_rhs = C; z.slabs_per_comp = 1; z.C = C; z.prologue = prologue;
       z.W = W(2); z.plan = g.plan[2]; z.cg = cg;
       if (z.XC < 1) return fail(ctx, HOM_ERR_INVALID_ARG, "grid too large for the shared-memory FFT");
-      CK(launch_pencil<T>(z, st));
+      KL(launch_pencil<T>(z, st));
       ycur = T1;
     }
     {
@@ -485,7 +511,7 @@ struct Runner {
       y.prologue = g.d == 3 ? 0 : prologue;
       y.W = W(1); y.plan = g.plan[1]; y.cg = cg;
       if (y.XC < 1) return fail(ctx, HOM_ERR_INVALID_ARG, "grid too large for the shared-memory FFT");
-      CK(launch_pencil<T>(y, st));
+      KL(launch_pencil<T>(y, st));
     }
     {
       Prof pr(ctx, "xpass", st);
@@ -496,7 +522,7 @@ struct Runner {
       x.comp_stride = g.planes * Nh; x.scale = 1.0 / (double)g.grid;
       x.W = W(0); x.plan = g.plan[0]; x.cg = cg; x.partial = nullptr;
       if (x.YB < 1) return fail(ctx, HOM_ERR_INVALID_ARG, "grid too large for the shared-memory FFT");
-      CK(launch_xpass<T>(x, R, st));
+      KL(launch_xpass<T>(x, R, st));
     }
     const void* fin = T2;
     if (g.d == 3) {
@@ -508,7 +534,7 @@ struct Runner {
       y.Pin = My; y.Pout = Ny; y.Nlog = Ny; y.dir = -1;
       y.slabs_per_rhs = C * Mz; y.slabs_per_comp = Mz; y.C = C; y.prologue = 0;
       y.W = W(1); y.plan = g.plan[1]; y.cg = cg;
-      CK(launch_pencil<T>(y, st));
+      KL(launch_pencil<T>(y, st));
       fin = T1;
     }
     {
@@ -523,9 +549,10 @@ struct Runner {
       f.project = project; f.d = g.d; f.Ny = Ny; f.Nh = Nh;
       for (int k = 0; k < 3; ++k) f.invY[k] = g.invY[k];
       f.W = W(g.d == 3 ? 2 : 1); f.plan = g.plan[g.d == 3 ? 2 : 1];
-      f.cg = cg; f.partial = at<double>(L.partial); f.partial_ld = L.maxblk;
+      f.cg = cg; f.partial_ld = L.maxblk; f.bsub = bsub;
+      f.partial = ((cg && p_aux) || bsub) ? at<double>(L.partial) : nullptr;
       if (f.XC < 1) return fail(ctx, HOM_ERR_INVALID_ARG, "grid too large for the shared-memory FFT");
-      CK(launch_final<T>(f, st));
+      KL(launch_final<T>(f, st));
     }
     return HOM_OK;
   }
@@ -553,7 +580,7 @@ struct Runner {
       z.Pin = Nz; z.Pout = Mz; z.Nlog = Nz; z.dir = +1;
       z.slabs_per_rhs = C; z.slabs_per_comp = 1; z.C = C; z.prologue = addE ? 2 : 0;
       z.W = base + L.tw64[2]; z.plan = g.plan[2]; z.cg = nullptr;
-      CK(launch_pencil<double>(z, st));
+      KL(launch_pencil<double>(z, st));
       ycur = T1;
     }
     PencilArgs y{};
@@ -564,7 +591,7 @@ struct Runner {
     y.slabs_per_rhs = C * Mz; y.slabs_per_comp = Mz; y.C = C;
     y.prologue = (g.d == 2 && addE) ? 2 : 0;
     y.W = base + L.tw64[1]; y.plan = g.plan[1]; y.cg = nullptr;
-    CK(launch_pencil<double>(y, st));
+    KL(launch_pencil<double>(y, st));
     XArgs x{};
     x.in = T2; x.out = nullptr; x.coef = coef; x.mode = 1;
     x.planes = (int)g.planes; x.YB = xpass_yb<double>(g.M[0], R * C, (int)g.planes);
@@ -572,9 +599,9 @@ struct Runner {
     x.Nin = Nh; x.Nout = 0; x.M = g.M[0]; x.R = R; x.C = C; x.ncomp = g.ncomp; x.d = g.d;
     x.comp_stride = g.planes * Nh; x.scale = 1.0;
     x.W = base + L.tw64[0]; x.plan = g.plan[0]; x.cg = nullptr; x.partial = at<double>(L.epart);
-    CK(launch_xpass<double>(x, 1, st));
+    KL(launch_xpass<double>(x, 1, st));
     const int nblk = (int)((g.planes + x.YB - 1) / x.YB);
-    CK(launch_energy_reduce(at<double>(L.epart), nblk, R * R, at<double>(L.eout) + slot * 9, st));
+    KL(launch_energy_reduce(at<double>(L.epart), nblk, R * R, at<double>(L.eout) + slot * 9, st));
     return HOM_OK;
   }
 
@@ -585,7 +612,7 @@ struct Runner {
     CKS(build_coefficient(side, coef64));
     const void* coefT = coef64;
     if (sizeof(T) == 4) {
-      CK(launch_convert_d2f(coef64, at<float>(L.coef32), (long long)g.ncomp * g.grid, st));
+      KL(launch_convert_d2f(coef64, at<float>(L.coef32), (long long)g.ncomp * g.grid, st));
       coefT = at<float>(L.coef32);
     }
     const size_t fb = (size_t)R * g.d * g.field * elem;
@@ -594,14 +621,14 @@ struct Runner {
     CgScalars* cg = at<CgScalars>(L.cg[side]);
     SpecArgs sa = spec_args(side);
     const int N3[3] = {g.N[0], g.N[1], g.N[2]};
-    CK(launch_rhs<T>(sa, side, R, g.Nh, N3, base + L.r, at<double>(L.partial), kVecBlocks, st));
+    KL(launch_rhs<T>(sa, side, R, g.Nh, N3, base + L.r, at<double>(L.partial), kVecBlocks, st));
     const double tol = o.tol > 0 ? o.tol : 1e-8;
-    CK(launch_cg_init(cg, at<double>(L.partial), kVecBlocks, kVecBlocks, R, tol * tol, st));
+    KL(launch_cg_init(cg, at<double>(L.partial), kVecBlocks, kVecBlocks, R, tol * tol, 0.0, 0, st));
     const int maxit = o.max_iter > 0 ? o.max_iter : 10000;
     const int every = o.check_every > 0 ? o.check_every : 8;
     const int nfin = final_blocks(elem);
     // an initial poll avoids work when b = 0 (homogeneous cells)
-    CK(cudaMemcpyAsync(ctx->host_cg, cg, sizeof(CgScalars), cudaMemcpyDeviceToHost, st));
+    CK(d2h_copy(ctx, ctx->host_cg, cg, sizeof(CgScalars), st));
     CK(cudaStreamSynchronize(st));
     bool any = false;
     for (int r = 0; r < R; ++r) any = any || ctx->host_cg->active[r];
@@ -609,20 +636,20 @@ struct Runner {
       CKS(matvec<T>(base + L.p, base + L.q, coefT, side + 1, cg, base + L.r, base + L.p, 1));
       {
         Prof pr(ctx, "cg", st);
-        CK(launch_cg_alpha(cg, at<double>(L.partial), L.maxblk, nfin, R, st));
-        CK(launch_cg_update<T>(base + L.x, base + L.r, base + L.p, base + L.q, R, g.d, g.field, g.Nh, cg,
+        KL(launch_cg_alpha(cg, at<double>(L.partial), L.maxblk, nfin, R, st));
+        KL(launch_cg_update<T>(base + L.x, base + L.r, base + L.p, base + L.q, R, g.d, g.field, g.Nh, cg,
                                at<double>(L.partial), kVecBlocks, st));
-        CK(launch_cg_beta(cg, at<double>(L.partial), kVecBlocks, kVecBlocks, R, st));
+        KL(launch_cg_beta(cg, at<double>(L.partial), kVecBlocks, kVecBlocks, R, st));
       }
       ++*matvecs;
       if ((it + 1) % every == 0 || it + 1 == maxit) {
-        CK(cudaMemcpyAsync(ctx->host_cg, cg, sizeof(CgScalars), cudaMemcpyDeviceToHost, st));
+        CK(d2h_copy(ctx, ctx->host_cg, cg, sizeof(CgScalars), st));
         CK(cudaStreamSynchronize(st));
         any = false;
         for (int r = 0; r < R; ++r) any = any || ctx->host_cg->active[r];
       }
     }
-    CK(cudaMemcpyAsync(ctx->host_cg, cg, sizeof(CgScalars), cudaMemcpyDeviceToHost, st));
+    CK(d2h_copy(ctx, ctx->host_cg, cg, sizeof(CgScalars), st));
     CK(cudaStreamSynchronize(st));
     hom_status result = HOM_OK;
     for (int r = 0; r < R; ++r) {
@@ -638,11 +665,110 @@ struct Runner {
     }
     if (result == HOM_ERR_BREAKDOWN) return result;
     // FP64 re-projection (and promotion for the mixed path), then the exact energies
-    CK(launch_project_promote<T>(base + L.x, at<double2>(L.x64), R, g.d, g.N[1], g.N[2], g.Nh, g.invY, side, st));
+    KL(launch_project_promote<T>(base + L.x, at<double2>(L.x64), R, g.d, g.N[1], g.N[2], g.Nh, g.invY, side, st));
     CKS(energy(coef64, at<double2>(L.x64), 1, side));
     return result;
   }
 };
+
+// Mixed precision (FP32 inner CG, FP64 outer): iterative refinement on the FP64 residual.
+// r64 = b - C x64 in FP64; each inner FP32 CG solves C d = r64 to
+// max(tol/2, eta |r64|), stopping early when FP32 accuracy runs out; x64 += d. The CG
+// scalars (alpha, beta, r.r, p.Cp) are FP64 reductions of FP32 products. The outer loop
+// stops at |r64| <= tol |E| or when a step fails to halve |r64|; any field is a valid
+// conforming test field after the FP64 re-projection, so the bounds stay guaranteed.
+hom_status Runner_solve_mixed(Runner& run, int side, const hom_opts& o, hom_report* rep, int* matvecs) {
+  hom_ctx* ctx = run.ctx;
+  const Geometry& g = run.g;
+  const Layout& L = run.L;
+  const int R = run.R;
+  cudaStream_t st = run.st;
+  unsigned char* base = run.base;
+  double* coef64 = run.at<double>(L.coef64);
+  CKS(run.build_coefficient(side, coef64));
+  KL(launch_convert_d2f(coef64, run.at<float>(L.coef32), (long long)g.ncomp * g.grid, st));
+  const float* coef32 = run.at<float>(L.coef32);
+  const long long n = (long long)R * g.d * g.field;
+  double2* b64 = run.at<double2>(L.b64);
+  double2* r64 = run.at<double2>(L.r64);
+  double2* x64 = run.at<double2>(L.x64);
+  CgScalars* inner = run.at<CgScalars>(L.cg[side]);
+  CgScalars* outer = run.at<CgScalars>(L.cgo[side]);
+  SpecArgs sa = run.spec_args(side);
+  const int N3[3] = {g.N[0], g.N[1], g.N[2]};
+  double* partial = run.at<double>(L.partial);
+  KL(launch_rhs<double>(sa, side, R, g.Nh, N3, b64, partial, kVecBlocks, st));
+  const double tol = o.tol > 0 ? o.tol : 1e-8;
+  KL(launch_cg_init(outer, partial, kVecBlocks, kVecBlocks, R, tol * tol, 0.0, 0, st));
+  CK(cudaMemcpyAsync(r64, b64, n * sizeof(double2), cudaMemcpyDeviceToDevice, st));
+  CK(cudaMemsetAsync(x64, 0, n * sizeof(double2), st));
+  const int maxit = o.max_iter > 0 ? o.max_iter : 10000;
+  const int every = o.check_every > 0 ? o.check_every : 8;
+  const int nfin32 = run.final_blocks(8), nfin64 = run.final_blocks(16);
+  const double eta = 1e-5;
+  int used = 0;
+  int inner_iters[3] = {0, 0, 0};
+  for (int outer_it = 0; outer_it < 30; ++outer_it) {
+    CK(d2h_copy(ctx, ctx->host_cg, outer, sizeof(CgScalars), st));
+    CK(cudaStreamSynchronize(st));
+    bool any = false;
+    for (int r = 0; r < R; ++r) any = any || ctx->host_cg->active[r];
+    if (!any || used >= maxit) break;
+    // inner FP32 CG on the current FP64 residual
+    KL(launch_demote(r64, run.at<float2>(L.r), R, g.d, g.field, g.Nh, outer, partial, kVecBlocks, st));
+    CK(cudaMemsetAsync(base + L.x, 0, n * sizeof(float2), st));
+    CK(cudaMemsetAsync(base + L.p, 0, n * sizeof(float2), st));
+    KL(launch_cg_init(inner, partial, kVecBlocks, kVecBlocks, R, 0.25 * tol * tol, eta * eta, 1, st));
+    CK(d2h_copy(ctx, ctx->host_cg, inner, sizeof(CgScalars), st));
+    CK(cudaStreamSynchronize(st));
+    bool ia = false;
+    for (int r = 0; r < R; ++r) ia = ia || ctx->host_cg->active[r];
+    for (int it = 0; ia && used < maxit; ++it) {
+      CKS(run.matvec<float>(base + L.p, base + L.q, coef32, side + 1, inner, base + L.r, base + L.p, 1));
+      {
+        Prof pr(ctx, "cg", st);
+        KL(launch_cg_alpha(inner, partial, L.maxblk, nfin32, R, st));
+        KL(launch_cg_update<float>(base + L.x, base + L.r, base + L.p, base + L.q, R, g.d, g.field, g.Nh,
+                                   inner, partial, kVecBlocks, st));
+        KL(launch_cg_beta(inner, partial, kVecBlocks, kVecBlocks, R, st));
+      }
+      ++*matvecs;
+      ++used;
+      if ((it + 1) % every == 0 || used >= maxit) {
+        CK(d2h_copy(ctx, ctx->host_cg, inner, sizeof(CgScalars), st));
+        CK(cudaStreamSynchronize(st));
+        ia = false;
+        for (int r = 0; r < R; ++r) ia = ia || ctx->host_cg->active[r];
+      }
+    }
+    CK(d2h_copy(ctx, ctx->host_cg, inner, sizeof(CgScalars), st));
+    CK(cudaStreamSynchronize(st));
+    for (int r = 0; r < R; ++r) inner_iters[r] += ctx->host_cg->iters[r];
+    // x64 += d, then the exact FP64 residual r64 = b - C x64
+    KL(launch_promote_add(run.at<float2>(L.x), x64, n, st));
+    CKS(run.matvec<double>(x64, r64, coef64, side + 1, outer, nullptr, nullptr, 0, b64));
+    KL(launch_outer_check(outer, partial, L.maxblk, nfin64, R, 0.25, st));
+    ++*matvecs;
+  }
+  CK(d2h_copy(ctx, ctx->host_cg, outer, sizeof(CgScalars), st));
+  CK(cudaStreamSynchronize(st));
+  hom_status result = HOM_OK;
+  for (int r = 0; r < R; ++r) {
+    const CgScalars& h = *ctx->host_cg;
+    const int stt = h.status[r];
+    if (rep) {
+      rep->iters[side][r] = inner_iters[r];
+      rep->resid[side][r] = std::sqrt(std::max(h.rr[r], 0.0));
+      rep->status[side][r] = stt;
+    }
+    if (stt == -2) result = fail(ctx, HOM_ERR_BREAKDOWN, "non-finite FP64 residual");
+    else if (stt == 1 && result == HOM_OK) result = HOM_WARN_NOT_CONVERGED;
+  }
+  if (result == HOM_ERR_BREAKDOWN) return result;
+  KL(launch_project_promote<double>(x64, x64, R, g.d, g.N[1], g.N[2], g.Nh, g.invY, side, st));
+  CKS(run.energy(coef64, x64, 1, side));
+  return result;
+}
 
 hom_status set_device(hom_ctx* ctx) {
   CK(cudaSetDevice(ctx->device));
@@ -736,6 +862,7 @@ hom_status hom_bounds(hom_ctx* ctx, const hom_problem* prob, const hom_opts* opt
   if (!ctx || !opts) return fail(ctx, HOM_ERR_INVALID_ARG, "NULL argument");
   const auto t0 = std::chrono::steady_clock::now();
   ctx->err.clear();
+  ctx->launches = ctx->h2d = ctx->d2h = 0;
   CKS(set_device(ctx));
   Geometry g;
   CKS(build_geometry(ctx, prob, g));
@@ -754,20 +881,22 @@ hom_status hom_bounds(hom_ctx* ctx, const hom_problem* prob, const hom_opts* opt
   for (int side = 0; side < 2; ++side) {
     if (!(sides & (1 << side))) continue;
     hom_status s = elem == 16 ? run.solve_side<double>(side, *opts, rep, &matvecs)
-                              : run.solve_side<float>(side, *opts, rep, &matvecs);
+                              : Runner_solve_mixed(run, side, *opts, rep, &matvecs);
     if (s < 0) return s;
     if (s == HOM_WARN_NOT_CONVERGED) worst = s;
   }
-  CK(cudaMemcpyAsync(ctx->host_e, run.at<double>(run.L.eout), 18 * sizeof(double), cudaMemcpyDeviceToHost,
-                     run.st));
+  CK(d2h_copy(ctx, ctx->host_e, run.at<double>(run.L.eout), 18 * sizeof(double), run.st));
   CK(cudaStreamSynchronize(run.st));
   const int d = g.d;
   const double invM = 1.0 / (double)g.grid;
   double Au[9] = {}, Bu[9] = {}, Lo[9] = {};
-  for (int i = 0; i < d * d; ++i) {
-    Au[i] = ctx->host_e[i] * invM;
-    Bu[i] = ctx->host_e[9 + i] * invM;
-  }
+  // the bound matrices are symmetric bilinear forms (Eq. upper_lower_bounds): report the
+  // symmetric part of the two energy matrices
+  for (int i = 0; i < d; ++i)
+    for (int j = 0; j < d; ++j) {
+      Au[d * i + j] = 0.5 * (ctx->host_e[d * i + j] + ctx->host_e[d * j + i]) * invM;
+      Bu[d * i + j] = 0.5 * (ctx->host_e[9 + d * i + j] + ctx->host_e[9 + d * j + i]) * invM;
+    }
   if (sides & 1)
     if (upper) memcpy(upper, Au, sizeof(double) * d * d);
   if (sides & 2) {
@@ -781,6 +910,9 @@ hom_status hom_bounds(hom_ctx* ctx, const hom_problem* prob, const hom_opts* opt
     }
   }
   if (rep) {
+    rep->launches = ctx->launches;
+    rep->h2d_bytes = ctx->h2d;
+    rep->d2h_bytes = ctx->d2h;
     rep->matvecs = matvecs;
     rep->ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   }
@@ -803,7 +935,7 @@ hom_status hom_coefficient(hom_ctx* ctx, const hom_problem* prob, int32_t side, 
   // FP32: build in FP64 into the buffer the last pass does not read, then round
   double* tmp = run.at<double>(g.d == 3 ? run.L.t2 : run.L.t1);
   CKS(run.build_coefficient(side, tmp));
-  CK(launch_convert_d2f(tmp, static_cast<float*>(d_coef), (long long)g.ncomp * g.grid, run.st));
+  KL(launch_convert_d2f(tmp, static_cast<float*>(d_coef), (long long)g.ncomp * g.grid, run.st));
   return HOM_OK;
 }
 
@@ -821,13 +953,13 @@ hom_status hom_rhs(hom_ctx* ctx, const hom_problem* prob, int32_t side, int32_t 
   if (!d_ws || ws_bytes < run.L.total) return fail(ctx, HOM_ERR_WORKSPACE, "workspace too small");
   CKS(run.upload_tables());
   SpecArgs sa = run.spec_args(side);
-  CK(launch_axis_tables(sa.nincl, g.d, g.M, run.L.Mmax, g.invY, sa.incl, run.at<double2>(run.L.phase),
+  KL(launch_axis_tables(sa.nincl, g.d, g.M, run.L.Mmax, g.invY, sa.incl, run.at<double2>(run.L.phase),
                         run.at<double>(run.L.sinc), run.st));
   const int N3[3] = {g.N[0], g.N[1], g.N[2]};
   if (precision == HOM_FP64)
-    CK(launch_rhs<double>(sa, side, nrhs, g.Nh, N3, d_b, run.at<double>(run.L.partial), kVecBlocks, run.st));
+    KL(launch_rhs<double>(sa, side, nrhs, g.Nh, N3, d_b, run.at<double>(run.L.partial), kVecBlocks, run.st));
   else
-    CK(launch_rhs<float>(sa, side, nrhs, g.Nh, N3, d_b, run.at<double>(run.L.partial), kVecBlocks, run.st));
+    KL(launch_rhs<float>(sa, side, nrhs, g.Nh, N3, d_b, run.at<double>(run.L.partial), kVecBlocks, run.st));
   return HOM_OK;
 }
 
@@ -865,7 +997,7 @@ hom_status hom_energy(hom_ctx* ctx, const hom_problem* prob, int32_t nrhs, int32
   if (!d_ws || ws_bytes < run.L.total) return fail(ctx, HOM_ERR_WORKSPACE, "workspace too small");
   CKS(run.upload_tables());
   CKS(run.energy(static_cast<const double*>(d_coef), static_cast<const double2*>(d_x), add_constant, 0));
-  CK(cudaMemcpyAsync(ctx->host_e, run.at<double>(run.L.eout), 9 * sizeof(double), cudaMemcpyDeviceToHost, run.st));
+  CK(d2h_copy(ctx, ctx->host_e, run.at<double>(run.L.eout), 9 * sizeof(double), run.st));
   CK(cudaStreamSynchronize(run.st));
   for (int i = 0; i < nrhs * nrhs; ++i) W[i] = ctx->host_e[i] / (double)g.grid;
   return HOM_OK;
@@ -889,10 +1021,10 @@ hom_status hom_fft(hom_ctx* ctx, int32_t M, int32_t precision, int32_t dir, int3
   make_plan(M, plan);
   if (precision == HOM_FP64) {
     CK(cudaMemcpyAsync(d_ws, w64.data(), M * sizeof(double2), cudaMemcpyHostToDevice, st));
-    CK(launch_fft_batch<double>(d_in, d_out, M, howmany, dir, d_ws, plan, st));
+    KL(launch_fft_batch<double>(d_in, d_out, M, howmany, dir, d_ws, plan, st));
   } else {
     CK(cudaMemcpyAsync(d_ws, w32.data(), M * sizeof(float2), cudaMemcpyHostToDevice, st));
-    CK(launch_fft_batch<float>(d_in, d_out, M, howmany, dir, d_ws, plan, st));
+    KL(launch_fft_batch<float>(d_in, d_out, M, howmany, dir, d_ws, plan, st));
   }
   return HOM_OK;
 }

@@ -114,23 +114,25 @@ __device__ __forceinline__ void stage_bfly(const cpx<T>* __restrict__ src, cpx<T
   for (int q = 0; q < R; ++q) dst[base + q * Ns] = v[q];
 }
 
-// Runtime radix (any odd prime) straight from shared memory: O(R^2) per butterfly.
+// Runtime radix (any odd prime) straight from shared memory: output s of butterfly j,
+// O(R) per output, so that a large prime radix spreads over R threads.
 template <typename T>
-__device__ void stage_bfly_generic(const cpx<T>* __restrict__ src, cpx<T>* __restrict__ dst,
-                                   int j, int Ns, int M, int R, const cpx<T>* W, int dir) {
+__device__ void stage_out_generic(const cpx<T>* __restrict__ src, cpx<T>* __restrict__ dst,
+                                  int j, int s, int Ns, int M, int R, const cpx<T>* W, int dir) {
   const int nb = M / R;
   const int k = j % Ns;
   const int tstep = k * (M / (Ns * R));
   const int step = M / R;
   const int base = (j / Ns) * Ns * R + k;
-  for (int s = 0; s < R; ++s) {
-    cpx<T> acc = src[j];
-    for (int q = 1; q < R; ++q) {
-      cpx<T> vq = mulc<T>(src[j + q * nb], W[q * tstep], dir > 0);
-      acc = add<T>(acc, mulc<T>(vq, W[((q * s) % R) * step], dir > 0));
-    }
-    dst[base + s * Ns] = acc;
+  cpx<T> acc = src[j];
+  int ws = 0;   // (q * s) mod R, advanced incrementally
+  for (int q = 1; q < R; ++q) {
+    ws += s;
+    if (ws >= R) ws -= R;
+    const cpx<T> vq = mulc<T>(src[j + q * nb], W[q * tstep], dir > 0);
+    acc = add<T>(acc, mulc<T>(vq, W[ws * step], dir > 0));
   }
+  dst[base + s * Ns] = acc;
 }
 
 // G pencils of length M at a + g*ld (ping-pong with b, same strides). The CTA runs
@@ -145,19 +147,30 @@ __device__ cpx<T>* fft_pencils(cpx<T>* a, cpx<T>* b, int G, int ld, const FftPla
   for (int s = 0; s < plan.nrad; ++s) {
     const int R = plan.radix[s];
     const int nb = M / R;
-    const int total = G * nb;
-    for (int t = threadIdx.x; t < total; t += blockDim.x) {
-      const int g = t / nb;
-      const int j = t - g * nb;
-      const cpx<T>* sp = src + (size_t)g * ld;
-      cpx<T>* dp = dst + (size_t)g * ld;
-      switch (R) {
-        case 3: stage_bfly<T, 3>(sp, dp, j, Ns, M, W, dir); break;
-        case 5: stage_bfly<T, 5>(sp, dp, j, Ns, M, W, dir); break;
-        case 7: stage_bfly<T, 7>(sp, dp, j, Ns, M, W, dir); break;
-        case 11: stage_bfly<T, 11>(sp, dp, j, Ns, M, W, dir); break;
-        case 13: stage_bfly<T, 13>(sp, dp, j, Ns, M, W, dir); break;
-        default: stage_bfly_generic<T>(sp, dp, j, Ns, M, R, W, dir); break;
+    if (R <= 13) {
+      const int total = G * nb;
+      for (int t = threadIdx.x; t < total; t += blockDim.x) {
+        const int g = t / nb;
+        const int j = t - g * nb;
+        const cpx<T>* sp = src + (size_t)g * ld;
+        cpx<T>* dp = dst + (size_t)g * ld;
+        switch (R) {
+          case 3: stage_bfly<T, 3>(sp, dp, j, Ns, M, W, dir); break;
+          case 5: stage_bfly<T, 5>(sp, dp, j, Ns, M, W, dir); break;
+          case 7: stage_bfly<T, 7>(sp, dp, j, Ns, M, W, dir); break;
+          case 11: stage_bfly<T, 11>(sp, dp, j, Ns, M, W, dir); break;
+          default: stage_bfly<T, 13>(sp, dp, j, Ns, M, W, dir); break;
+        }
+      }
+    } else {
+      const int per = nb * R;
+      const int total = G * per;
+      for (int t = threadIdx.x; t < total; t += blockDim.x) {
+        const int g = t / per;
+        const int rem = t - g * per;
+        const int j = rem / R;
+        const int so = rem - j * R;
+        stage_out_generic<T>(src + (size_t)g * ld, dst + (size_t)g * ld, j, so, Ns, M, R, W, dir);
       }
     }
     __syncthreads();
@@ -191,10 +204,13 @@ struct CgScalars {
   double pq[3];
   double alpha[3];
   double beta[3];
-  double tol2;
-  int active[3];   // 1 while the solve runs
+  double tol2[3];    // stop when r.r <= tol2 (per right-hand side)
+  double rr_min[3];  // smallest r.r seen (divergence guard of the FP32 inner solves)
+  int min_iter[3];   // iteration of the last new minimum of r.r (stagnation guard)
+  int active[3];     // 1 while the solve runs
   int iters[3];
-  int status[3];   // 0 ok/converged, 1 running, -2 breakdown
+  int status[3];     // 0 converged, 1 running / max_iter, 2 stopped by a guard, -2 breakdown
+  int guard;         // 1: an FP32 inner solve; breakdown and divergence stop it (status 2)
 };
 
 }  // namespace homb

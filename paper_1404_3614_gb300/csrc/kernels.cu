@@ -111,8 +111,10 @@ __global__ void __launch_bounds__(kThreads) k_final(FinalArgs a) {
   __syncthreads();
   cpx<T>* res = fft_pencils<T>(A, B, C * XC, M, a.plan, Ws, -1);
   cpx<T>* out = reinterpret_cast<cpx<T>*>(a.out) + (long long)rhs * C * a.out_comp;
-  const cpx<T>* pdir = a.cg ? reinterpret_cast<const cpx<T>*>(a.aux) + (long long)rhs * C * a.out_comp
-                            : nullptr;
+  const cpx<T>* pdir = (a.cg && a.aux) ? reinterpret_cast<const cpx<T>*>(a.aux) + (long long)rhs * C * a.out_comp
+                                       : nullptr;
+  const cpx<T>* bsub = a.bsub ? reinterpret_cast<const cpx<T>*>(a.bsub) + (long long)rhs * C * a.out_comp
+                              : nullptr;
   double acc = 0.0;
   for (int t = threadIdx.x; t < a.Nlog * XC; t += blockDim.x) {
     const int i = t / XC;
@@ -158,6 +160,16 @@ __global__ void __launch_bounds__(kThreads) k_final(FinalArgs a) {
       }
     }
     const long long oi = (long long)i * a.X + x;
+    if (bsub) {
+      double s = 0.0;
+#pragma unroll
+      for (int c = 0; c < 3; ++c)
+        if (c < C) {
+          u[c] = sub<T>(bsub[(long long)c * a.out_comp + oi], u[c]);
+          s += (double)u[c].x * (double)u[c].x + (double)u[c].y * (double)u[c].y;
+        }
+      acc += (kx == 0 ? 1.0 : 2.0) * s;
+    }
 #pragma unroll
     for (int c = 0; c < 3; ++c)
       if (c < C) out[(long long)c * a.out_comp + oi] = u[c];
@@ -173,7 +185,7 @@ __global__ void __launch_bounds__(kThreads) k_final(FinalArgs a) {
       acc += w * s;
     }
   }
-  if (a.cg) {
+  if (a.partial) {
     const double s = block_sum(acc, red);
     if (threadIdx.x == 0) a.partial[rhs * a.partial_ld + blockIdx.x] = s;
   }
@@ -552,18 +564,22 @@ __device__ double reduce_row(const double* v, int n, double* red) {
 }
 
 __global__ void k_cg_init(CgScalars* cg, const double* partial, int ld, int nblk, int nrhs,
-                          double tol2) {
+                          double tol2_abs, double rel2, int guard) {
   __shared__ double red[32];
   for (int r = 0; r < 3; ++r) {
     double s = 0.0;
     if (r < nrhs) s = reduce_row(partial + (long long)r * ld, nblk, red);
     __syncthreads();
     if (threadIdx.x == 0) {
-      cg->tol2 = tol2;
+      const double t2 = fmax(tol2_abs, rel2 * s);
+      cg->tol2[r] = t2;
       cg->beta[r] = 0.0;
       cg->alpha[r] = 0.0;
       cg->iters[r] = 0;
       cg->rr[r] = s;
+      cg->rr_min[r] = s;
+      cg->min_iter[r] = 0;
+      cg->guard = guard;
       if (r >= nrhs) {
         cg->active[r] = 0;
         cg->status[r] = 0;
@@ -571,8 +587,8 @@ __global__ void k_cg_init(CgScalars* cg, const double* partial, int ld, int nblk
         cg->active[r] = 0;
         cg->status[r] = -2;
       } else {
-        cg->active[r] = s > tol2 ? 1 : 0;
-        cg->status[r] = s > tol2 ? 1 : 0;
+        cg->active[r] = s > t2 ? 1 : 0;
+        cg->status[r] = s > t2 ? 1 : 0;
       }
     }
   }
@@ -588,7 +604,7 @@ __global__ void k_cg_alpha(CgScalars* cg, const double* partial, int ld, int nbl
       cg->pq[r] = pq;
       if (!(pq > 0.0) || !isfinite(pq)) {
         cg->active[r] = 0;
-        cg->status[r] = -2;
+        cg->status[r] = cg->guard ? 2 : -2;
       } else {
         cg->alpha[r] = cg->rr[r] / pq;
       }
@@ -607,17 +623,89 @@ __global__ void k_cg_beta(CgScalars* cg, const double* partial, int ld, int nblk
       cg->iters[r] += 1;
       if (!isfinite(rr)) {
         cg->active[r] = 0;
-        cg->status[r] = -2;
-      } else if (rr <= cg->tol2) {
+        cg->status[r] = cg->guard ? 2 : -2;
+      } else if (rr <= cg->tol2[r]) {
         cg->active[r] = 0;
         cg->status[r] = 0;
+        cg->rr[r] = rr;
+      } else if (cg->guard && (rr > 1e4 * cg->rr_min[r] || cg->iters[r] - cg->min_iter[r] > 40)) {
+        // FP32 inner solve diverging or stagnating at its accuracy floor: stop, keep x
+        cg->active[r] = 0;
+        cg->status[r] = 2;
         cg->rr[r] = rr;
       } else {
         cg->beta[r] = rr / cg->rr[r];
         cg->rr[r] = rr;
+        if (rr < cg->rr_min[r]) {
+          cg->rr_min[r] = rr;
+          cg->min_iter[r] = cg->iters[r];
+        }
       }
     }
     __syncthreads();
+  }
+}
+
+__global__ void k_outer_check(CgScalars* cg, const double* partial, int ld, int nblk, int nrhs,
+                              double shrink2) {
+  __shared__ double red[32];
+  for (int r = 0; r < nrhs; ++r) {
+    if (!cg->active[r]) continue;
+    const double rr = reduce_row(partial + (long long)r * ld, nblk, red);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      cg->iters[r] += 1;
+      if (!isfinite(rr)) {
+        cg->active[r] = 0;
+        cg->status[r] = -2;
+      } else if (rr <= cg->tol2[r]) {
+        cg->active[r] = 0;
+        cg->status[r] = 0;
+        cg->rr[r] = rr;
+      } else if (rr > shrink2 * cg->rr[r]) {
+        cg->active[r] = 0;   // refinement stalled: the field is kept, bounds stay guaranteed
+        cg->status[r] = 1;
+        cg->rr[r] = rr;
+      } else {
+        cg->rr[r] = rr;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+__global__ void __launch_bounds__(kThreads) k_demote(const double2* r64, float2* r32, int C,
+                                                      long long field, int Nh, const CgScalars* outer,
+                                                      double* partial, int ld) {
+  __shared__ double red[32];
+  const int rhs = blockIdx.y;
+  const bool on = outer->active[rhs] != 0;
+  const long long n = (long long)C * field;
+  const long long base = (long long)rhs * n;
+  double acc = 0.0;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
+       e += (long long)gridDim.x * blockDim.x) {
+    float2 v = make_float2(0.f, 0.f);
+    if (on) {
+      const double2 w = r64[base + e];
+      v = make_float2((float)w.x, (float)w.y);
+    }
+    r32[base + e] = v;
+    const double wt = (e % Nh) == 0 ? 1.0 : 2.0;
+    acc += wt * ((double)v.x * v.x + (double)v.y * v.y);
+  }
+  const double s = block_sum(acc, red);
+  if (threadIdx.x == 0) partial[rhs * ld + blockIdx.x] = s;
+}
+
+__global__ void k_promote_add(const float2* x32, double2* x64, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const float2 a = x32[i];
+    double2 b = x64[i];
+    b.x += (double)a.x;
+    b.y += (double)a.y;
+    x64[i] = b;
   }
 }
 
@@ -810,8 +898,25 @@ cudaError_t launch_cg_update(void* x, void* r, const void* p, const void* q, int
 }
 
 cudaError_t launch_cg_init(CgScalars* cg, const double* partial, int ld, int nblk, int nrhs,
-                           double tol2, cudaStream_t s) {
-  k_cg_init<<<1, kThreads, 0, s>>>(cg, partial, ld, nblk, nrhs, tol2);
+                           double tol2_abs, double rel2, int guard, cudaStream_t s) {
+  k_cg_init<<<1, kThreads, 0, s>>>(cg, partial, ld, nblk, nrhs, tol2_abs, rel2, guard);
+  return cudaGetLastError();
+}
+cudaError_t launch_outer_check(CgScalars* cg, const double* partial, int ld, int nblk, int nrhs,
+                               double shrink2, cudaStream_t s) {
+  k_outer_check<<<1, kThreads, 0, s>>>(cg, partial, ld, nblk, nrhs, shrink2);
+  return cudaGetLastError();
+}
+cudaError_t launch_demote(const double2* r64, float2* r32, int nrhs, int C, long long field, int Nh,
+                          const CgScalars* outer, double* partial, int nblk, cudaStream_t s) {
+  dim3 grid(nblk, nrhs);
+  k_demote<<<grid, kThreads, 0, s>>>(r64, r32, C, field, Nh, outer, partial, nblk);
+  return cudaGetLastError();
+}
+cudaError_t launch_promote_add(const float2* x32, double2* x64, long long n, cudaStream_t s) {
+  long long blocks = (n + kThreads - 1) / kThreads;
+  if (blocks > 152 * 32) blocks = 152 * 32;
+  k_promote_add<<<(int)blocks, kThreads, 0, s>>>(x32, x64, n);
   return cudaGetLastError();
 }
 cudaError_t launch_cg_alpha(CgScalars* cg, const double* partial, int ld, int nblk, int nrhs,

@@ -44,6 +44,7 @@ struct FinalArgs {
   CgScalars* cg;
   double* partial;               // [rhs][gridDim.x]
   int partial_ld;
+  const void* bsub;              // residual mode: out = bsub - Gamma(...), partial |out|^2
 };
 
 // Row pass along x (the contiguous axis) on rows of Nin complex values (k1 >= 0):
@@ -109,8 +110,18 @@ template <typename T>
 cudaError_t launch_cg_update(void* x, void* r, const void* p, const void* q, int nrhs, int C,
                              long long field, int Nh, CgScalars* cg, double* partial, int nblk,
                              cudaStream_t s);
+// r.r from the partials; tol2[r] = max(tol2_abs, rel2 * r.r); guard as given.
 cudaError_t launch_cg_init(CgScalars* cg, const double* partial, int ld, int nblk, int nrhs,
-                           double tol2, cudaStream_t s);
+                           double tol2_abs, double rel2, int guard, cudaStream_t s);
+// outer refinement step: r.r_new from the partials; converged when <= tol2[r]; stalled
+// (status 1, stop) when r.r_new > shrink2 * r.r.
+cudaError_t launch_outer_check(CgScalars* cg, const double* partial, int ld, int nblk, int nrhs,
+                               double shrink2, cudaStream_t s);
+// r32 = (float) r64 for active outer rhs (0 otherwise), plus |r32|^2 partials
+cudaError_t launch_demote(const double2* r64, float2* r32, int nrhs, int C, long long field, int Nh,
+                          const CgScalars* outer, double* partial, int nblk, cudaStream_t s);
+// x64 += (double) x32
+cudaError_t launch_promote_add(const float2* x32, double2* x64, long long n, cudaStream_t s);
 cudaError_t launch_cg_alpha(CgScalars* cg, const double* partial, int ld, int nblk, int nrhs,
                             cudaStream_t s);
 cudaError_t launch_cg_beta(CgScalars* cg, const double* partial, int ld, int nblk, int nrhs,

@@ -14,8 +14,8 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 def libpath():
     if shutil.which("nvcc") is None and not os.path.exists("/usr/local/cuda/bin/nvcc"):
         pytest.skip("nvcc not available")
-    from paper_1404_3614_gb300 import build as b
-    return b.build()
+    import __graft_entry__
+    return __graft_entry__._builder().build()
 
 
 def header_functions():

@@ -1,0 +1,62 @@
+"""Host-side logic of bench.py (no GPU): the oracle iteration counts it extrapolates
+with, the FLOP model, and the max-over-ranks reduction on 2 gloo ranks."""
+import os
+import socket
+
+import numpy as np
+import pytest
+import torch.multiprocessing as mp
+
+import bench
+import microstructures as ms
+from oracle import matfree
+
+
+def test_oracle_iteration_counts_pinned():
+    """bench.ORACLE_ITERS are the oracle CG's own iteration counts at 1e-4 (E = e1)."""
+    p = bench.workload()
+    for side in ("primal", "dual"):
+        op = matfree.MatFreeOperator(p, side)
+        _, it, res = matfree.cg_solve(op, [1.0, 0.0, 0.0], tol=bench.TOL)
+        assert it == bench.ORACLE_ITERS[side] and res <= bench.TOL
+
+
+def test_flop_model():
+    p = ms.cube_inclusion_3d()
+    assert bench.fft_flops(1) == 0.0
+    assert bench.fft_flops(81) == pytest.approx(5 * 81 * np.log2(81))
+    x = bench.family_flops_per_launch(p, "xpass", 3)
+    assert x == pytest.approx(9 * 81 * 81 * bench.fft_flops(81))
+    assert bench.family_flops_per_launch(p, "cg", 3) == 0.0
+
+
+def _free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    port = s.getsockname()[1]
+    s.close()
+    return port
+
+
+def _worker(rank, world, port, q):
+    import torch.distributed as dist
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    v = bench.max_over_ranks(10.0 + rank * 3.5, world)
+    bench.barrier(world)
+    q.put((rank, v))
+    dist.destroy_process_group()
+
+
+def test_max_over_ranks_gloo_two_ranks():
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_worker, args=(r, 2, port, q)) for r in range(2)]
+    for pr in procs:
+        pr.start()
+    for pr in procs:
+        pr.join(timeout=120)
+        assert pr.exitcode == 0
+    got = sorted(q.get(timeout=10) for _ in range(2))
+    assert got == [(0, 13.5), (1, 13.5)]
