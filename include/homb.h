@@ -189,6 +189,30 @@ hom_status hom_fft(hom_ctx* ctx, int32_t M, int32_t precision, int32_t dir, int3
                    const void* d_in, void* d_out, void* d_workspace, size_t workspace_bytes,
                    void* stream);  /* workspace >= 16*M bytes (twiddle table) */
 
+/* hom_matvec without a caller workspace. The paper has no counterpart: this entry point
+ * exists for callers that cannot call cudaMalloc (or cannot hand the library a scratch
+ * buffer): code whose device memory is owned and capped by another allocator, such as a
+ * framework's caching allocator or an application that reserves all device memory up
+ * front, and loops that must not allocate because an allocation could block or fail at
+ * an unpredictable moment. Instead of a workspace it uses one scratch array that lives
+ * in the library itself (HOM_NOALLOC_SCRATCH_BYTES = 32 MiB of device memory, held on
+ * every GPU that loads the library until the process exits).
+ * Arguments and results are those of hom_matvec without d_workspace/workspace_bytes.
+ * - Problems whose scratch (twiddle and inclusion tables plus the two intermediate
+ *   double-grid buffers) exceeds the array are rejected with HOM_ERR_WORKSPACE and a
+ *   message giving the bytes needed; e.g. the 3D N = 41 cube with 3 fields in FP64 fits.
+ * - The first call on a device looks up the array's device address (cudaGetSymbolAddress,
+ *   device made current); make that first call before any stream capture.
+ * - Every call on a device shares the same array and it keeps the last call's contents;
+ *   nothing in it needs to start at zero (every pass writes all it later reads). Calls
+ *   whose work can overlap on the GPU (different streams or threads without ordering)
+ *   race on the array: serialise them.
+ * - Allocates nothing: no cudaMalloc, cudaFree or allocating library routine. */
+#define HOM_NOALLOC_SCRATCH_BYTES (32u * 1024u * 1024u)
+hom_status hom_matvec_noalloc(hom_ctx* ctx, const hom_problem* prob, int32_t side,
+                              int32_t precision, int32_t project, int32_t nrhs,
+                              const void* d_coef, const void* d_in, void* d_out, void* stream);
+
 /* Kernel timing (CUDA events around each launch of one kernel family on the
  * launching stream). name: "zpass", "ypass", "xpass", "final", "cg", "coef", or ""
  * to disable. hom_kernel_timing returns launches and total milliseconds since the

@@ -75,6 +75,7 @@ def _load():
         "hom_matvec": (i32, [vp, P(hom_problem), i32, i32, i32, i32, vp, vp, vp, vp, sz, vp]),
         "hom_energy": (i32, [vp, P(hom_problem), i32, i32, vp, vp, dp, vp, sz, vp]),
         "hom_fft": (i32, [vp, i32, i32, i32, i32, vp, vp, vp, sz, vp]),
+        "hom_matvec_noalloc": (i32, [vp, P(hom_problem), i32, i32, i32, i32, vp, vp, vp, vp]),
         "hom_profile_kernel": (i32, [vp, C.c_char_p]),
         "hom_kernel_timing": (i32, [vp, P(i64), dp]),
     }
@@ -229,6 +230,17 @@ def hom_matvec(ctx, problem, side, precision, project, nrhs, d_coef, d_in, d_out
     return check(ctx, lib.hom_matvec(ctx, C.byref(p), side, precision, project, nrhs, C.c_void_p(d_coef),
                                      C.c_void_p(d_in), C.c_void_p(d_out), C.c_void_p(d_ws), ws_bytes,
                                      C.c_void_p(stream)))
+
+
+def hom_matvec_noalloc(ctx, problem, side, precision, project, nrhs, d_coef, d_in, d_out, stream=0):
+    """hom_matvec with the library's own static device scratch (no workspace argument)."""
+    p, keep = problem_struct(problem)
+    return check(ctx, lib.hom_matvec_noalloc(ctx, C.byref(p), side, precision, project, nrhs,
+                                             C.c_void_p(d_coef), C.c_void_p(d_in), C.c_void_p(d_out),
+                                             C.c_void_p(stream)))
+
+
+HOM_NOALLOC_SCRATCH_BYTES = 32 * 1024 * 1024
 
 
 def hom_energy(ctx, problem, nrhs, add_constant, d_coef, d_x, d_ws, ws_bytes, stream=0):

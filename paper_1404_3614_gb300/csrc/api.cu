@@ -16,6 +16,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -1027,6 +1028,67 @@ hom_status hom_fft(hom_ctx* ctx, int32_t M, int32_t precision, int32_t dir, int3
     KL(launch_fft_batch<float>(d_in, d_out, M, howmany, dir, d_ws, plan, st));
   }
   return HOM_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------------
+// hom_matvec_noalloc: the operator with library-owned scratch instead of a workspace
+// ---------------------------------------------------------------------------------
+namespace {
+// Scratch of hom_matvec_noalloc, resident on every device that loads the library.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[HOM_NOALLOC_SCRATCH_BYTES];
+
+std::mutex g_noalloc_mutex;
+void* g_noalloc_ptr[256] = {};   // device address of the array, per device ordinal
+
+// Device address of the scratch on `device` (which must be current). Host code cannot use
+// the symbol's name as a device pointer; the runtime gives the address once per device.
+hom_status noalloc_scratch(hom_ctx* ctx, int device, void** out) {
+  if (device < 0 || device >= 256) return fail(ctx, HOM_ERR_INVALID_ARG, "device ordinal out of range");
+  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+  if (!g_noalloc_ptr[device]) {
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || p == nullptr) {
+      return fail(ctx, HOM_ERR_CUDA, std::string("cudaGetSymbolAddress of the static scratch failed: ") +
+                                         cudaGetErrorString(e));
+    }
+    g_noalloc_ptr[device] = p;
+  }
+  *out = g_noalloc_ptr[device];
+  return HOM_OK;
+}
+}  // namespace
+
+extern "C" {
+
+hom_status hom_matvec_noalloc(hom_ctx* ctx, const hom_problem* prob, int32_t side, int32_t precision,
+                              int32_t project, int32_t nrhs, const void* d_coef, const void* d_in,
+                              void* d_out, void* stream) {
+  if (!ctx || !d_coef || !d_in || !d_out) return fail(ctx, HOM_ERR_INVALID_ARG, "NULL argument");
+  if (d_in == d_out) return fail(ctx, HOM_ERR_INVALID_ARG, "d_in and d_out must not alias");
+  if (side != 0 && side != 1) return fail(ctx, HOM_ERR_INVALID_ARG, "side must be 0 or 1");
+  if (precision != HOM_FP64 && precision != HOM_FP32) return fail(ctx, HOM_ERR_INVALID_ARG, "precision");
+  CKS(set_device(ctx));
+  Geometry g;
+  CKS(build_geometry(ctx, prob, g));
+  if (nrhs < 1 || nrhs > g.d) return fail(ctx, HOM_ERR_INVALID_ARG, "nrhs must be in [1, d]");
+  const Layout L = make_layout(g, nrhs, 16, 1);
+  if (L.total > (size_t)HOM_NOALLOC_SCRATCH_BYTES) {
+    char b[200];
+    snprintf(b, sizeof b, "hom_matvec_noalloc: problem needs %zu bytes of scratch, the static scratch holds %u",
+             L.total, (unsigned)HOM_NOALLOC_SCRATCH_BYTES);
+    return fail(ctx, HOM_ERR_WORKSPACE, b);
+  }
+  void* scratch = nullptr;
+  CKS(noalloc_scratch(ctx, ctx->device, &scratch));
+  Runner run{ctx, g, L, static_cast<unsigned char*>(scratch), static_cast<cudaStream_t>(stream), nrhs};
+  CKS(run.upload_tables());
+  const int proj = project ? side + 1 : 0;
+  if (precision == HOM_FP64)
+    return run.matvec<double>(d_in, d_out, d_coef, proj, nullptr, nullptr, nullptr, 0);
+  return run.matvec<float>(d_in, d_out, d_coef, proj, nullptr, nullptr, nullptr, 0);
 }
 
 hom_status hom_profile_kernel(hom_ctx* ctx, const char* name) {
