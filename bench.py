@@ -42,9 +42,38 @@ ORACLE_ITERS = {"primal": 46, "dual": 24}
 FP64_PEAK_TFLOPS = 1.25     # nominal GB300 FP64 (the recipe's table); a probe measured 1.256
 
 
-def workload():
+WORKLOADS = {
+    "cube3d_N41": "3D cube cell N=41^3 (double grid 81^3), contrast 100",
+    "spheres3d_N113": "3D cell with 16 random balls, volume fraction 0.3, contrast 1000, N=113^3 (double grid 225^3), seed 0",
+    "square2d_N23": "2D square inclusion side 0.6, a=1/10, N=23^2 (double grid 45^2)",
+}
+
+
+def workload(name: str = "cube3d_N41"):
     import microstructures as ms
-    return ms.cube_inclusion_3d()
+    if name == "cube3d_N41":
+        return ms.cube_inclusion_3d()
+    if name == "spheres3d_N113":
+        return ms.random_spheres_3d(0, N=113)
+    if name == "square2d_N23":
+        return ms.square_inclusion_2d()
+    raise ValueError(name)
+
+
+def run_matvec_only(args):
+    """Operator applications only (for kernel captures): `--reps` hom_matvec calls on d fields."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1404_3614_gb300 as hb
+    problem = workload(args.workload)
+    solver = hb.Bounds(0)
+    stream = torch.cuda.current_stream()
+    mv = matvec_timings(hb, solver, problem, torch.device("cuda", 0), stream, reps=args.reps,
+                        precisions=(args.precision,) if args.precision != "mixed" else ("fp32",))
+    print(json.dumps({"workload": WORKLOADS[args.workload], "matvec": mv}), flush=True)
+    solver.close()
+    return 0
 
 
 # ------------------------------------------------------------------------------------
@@ -357,7 +386,25 @@ def run_gpu(args):
     return 0
 
 
-def matvec_timings(hb, solver, problem, dev, stream, reps=20):
+def matvec_bytes(problem, elem_bytes: int) -> float:
+    """Algorithmic bytes of one operator application on d fields in the pass structure used
+    (z inverse, y inverse, x rows, y forward, z forward + projection + p.Cp): every pass reads
+    and writes its input and output once, the coefficient is read once per field set."""
+    d = problem.d
+    N = [int(n) for n in problem.N] + [1] * (3 - d)
+    M = [2 * n - 1 for n in N]
+    Nh = (N[0] + 1) // 2
+    if d == 3:
+        per = Nh * (2 * N[2] * N[1] + 4 * M[2] * N[1] + 4 * M[2] * M[1])
+    else:
+        per = Nh * (2 * N[1] + 4 * M[1])
+    cplx = 2 * elem_bytes
+    fields = d * d
+    coef = M[0] * M[1] * M[2] * elem_bytes * d      # read once per right-hand side
+    return fields * per * cplx + coef
+
+
+def matvec_timings(hb, solver, problem, dev, stream, reps=20, precisions=("fp64", "fp32")):
     """Device time of one operator application on d fields, FP64 and FP32."""
     import torch
     ctx = solver.ctx
@@ -369,6 +416,8 @@ def matvec_timings(hb, solver, problem, dev, stream, reps=20):
     out = {}
     for name, prec, cdt, rdt in (("fp64", hb.HOM_FP64, torch.complex128, torch.float64),
                                  ("fp32", hb.HOM_FP32, torch.complex64, torch.float32)):
+        if name not in precisions:
+            continue
         coef = torch.empty((info["ncomp"],) + tuple(info["M"][::-1]), dtype=rdt, device=dev)
         hb.hom_coefficient(ctx, problem, 0, prec, coef.data_ptr(), ws.data_ptr(), nws, stream.cuda_stream)
         x = torch.randn(shape, dtype=cdt, device=dev)
@@ -387,7 +436,9 @@ def matvec_timings(hb, solver, problem, dev, stream, reps=20):
         ms = e0.elapsed_time(e1) / reps
         flops = sum(family_flops_per_launch(problem, f, d) * (2 if f == "ypass" else 1)
                     for f in ("zpass", "ypass", "xpass", "final"))
-        out[name] = {"ms": ms, "fft_tflops": flops / (ms * 1e-3) / 1e12, "fields": d}
+        nbytes = matvec_bytes(problem, 8 if name == "fp64" else 4)
+        out[name] = {"ms": ms, "fft_tflops": flops / (ms * 1e-3) / 1e12, "fields": d,
+                     "model_bytes": nbytes, "model_gbs": nbytes / (ms * 1e-3) / 1e9}
     return out
 
 
@@ -400,11 +451,16 @@ def main():
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
     ap.add_argument("--ref-matvecs", type=int, default=20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="cube3d_N41", choices=sorted(WORKLOADS))
+    ap.add_argument("--matvec-only", action="store_true", help="operator applications only")
+    ap.add_argument("--reps", type=int, default=20)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
+    if args.matvec_only:
+        return run_matvec_only(args)
     return run_gpu(args)
 
 
