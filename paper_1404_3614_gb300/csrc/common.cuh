@@ -32,6 +32,48 @@ template <typename T> __device__ __forceinline__ cpx<T> rot(cpx<T> a, int s) {
 
 constexpr int kMaxRadices = 24;
 
+// Division by a runtime divisor d >= 1 for numerators n < 2^31 with one high multiply:
+// q = (umulhi(n, m) + n) >> s, s = ceil(log2 d), m = floor(2^32 (2^s - d) / d) + 1
+// (the round-up method of Granlund and Montgomery, "Division by invariant integers using
+// multiplication", 1994).
+struct FastDiv {
+  uint32_t d, m, s;
+  __host__ __device__ FastDiv() : d(1), m(1), s(0) {}
+  __host__ explicit FastDiv(uint32_t dd) : d(dd ? dd : 1) {
+    uint32_t sh = 0;
+    while ((1ull << sh) < d) ++sh;
+    s = sh;
+    m = (uint32_t)((((uint64_t)1 << 32) * (((uint64_t)1 << sh) - d)) / d + 1);
+  }
+  __device__ __forceinline__ int div(int n) const {
+    return (int)((__umulhi((uint32_t)n, m) + (uint32_t)n) >> s);
+  }
+};
+
+// Compile-time factorisation of a transform length (same radix order as the runtime
+// plan: fives, threes, then 7, 11, 13).
+__host__ __device__ constexpr int cf_radix(int M, int stage) {
+  int m = M, idx = 0;
+  const int rs[5] = {5, 3, 7, 11, 13};
+  for (int i = 0; i < 5; ++i)
+    while (m > 1 && m % rs[i] == 0) {
+      if (idx == stage) return rs[i];
+      m /= rs[i];
+      ++idx;
+    }
+  return 0;
+}
+__host__ __device__ constexpr int cf_nstages(int M) {
+  int n = 0;
+  while (cf_radix(M, n) != 0) ++n;
+  return n;
+}
+__host__ __device__ constexpr int cf_ns(int M, int stage) {
+  int p = 1;
+  for (int i = 0; i < stage; ++i) p *= cf_radix(M, i);
+  return p;
+}
+
 // Factorised plan of one odd transform length M (Stockham autosort, mixed radix).
 struct FftPlan {
   int M;
@@ -178,6 +220,53 @@ __device__ cpx<T>* fft_pencils(cpx<T>* a, cpx<T>* b, int G, int ld, const FftPla
     Ns *= R;
   }
   return src;
+}
+
+// ---------------------------------------------------------------------------------
+// Compile-time length M (product of radices 3 and 5): every divisor is a constant.
+// ---------------------------------------------------------------------------------
+template <typename T, int M, int R, int Ns>
+__device__ __forceinline__ void cbfly(const cpx<T>* __restrict__ src, cpx<T>* __restrict__ dst, int j,
+                                      const cpx<T>* W, int dir) {
+  constexpr int nb = M / R;
+  const int k = j % Ns;
+  cpx<T> v[R];
+#pragma unroll
+  for (int q = 0; q < R; ++q) v[q] = src[j + q * nb];
+  if (Ns > 1) {
+    constexpr int step = M / (Ns * R);
+#pragma unroll
+    for (int q = 1; q < R; ++q) v[q] = mulc<T>(v[q], W[q * k * step], dir > 0);
+  }
+  if (R == 3) dft3<T>(v, dir);
+  else dft5<T>(v, dir);
+  const int base = (j / Ns) * Ns * R + k;
+#pragma unroll
+  for (int q = 0; q < R; ++q) dst[base + q * Ns] = v[q];
+}
+
+template <typename T, int M, int S>
+__device__ __forceinline__ cpx<T>* cfft_from(cpx<T>* a, cpx<T>* b, int G, const cpx<T>* W, int dir) {
+  if constexpr (S >= cf_nstages(M)) {
+    return a;
+  } else {
+    constexpr int R = cf_radix(M, S);
+    constexpr int Ns = cf_ns(M, S);
+    constexpr int nb = M / R;
+    for (int t = threadIdx.x; t < G * nb; t += blockDim.x) {
+      const int g = t / nb;
+      const int j = t - g * nb;
+      cbfly<T, M, R, Ns>(a + g * M, b + g * M, j, W, dir);
+    }
+    __syncthreads();
+    return cfft_from<T, M, S + 1>(b, a, G, W, dir);
+  }
+}
+
+// G contiguous pencils of compile-time length M (stride M), ping-pong between a and b.
+template <typename T, int M>
+__device__ __forceinline__ cpx<T>* cfft(cpx<T>* a, cpx<T>* b, int G, const cpx<T>* W, int dir) {
+  return cfft_from<T, M, 0>(a, b, G, W, dir);
 }
 
 // Deterministic block sum of one double per thread (fixed tree order).

@@ -14,360 +14,11 @@
 namespace homb {
 
 constexpr int kThreads = 256;
-constexpr size_t kSmemBudget = 96 * 1024;
-constexpr size_t kSmemMax = 220 * 1024;
 
 template <typename T>
 __device__ __forceinline__ void load_twiddles(cpx<T>* Ws, const void* W, int M) {
   const cpx<T>* w = reinterpret_cast<const cpx<T>*>(W);
   for (int t = threadIdx.x; t < M; t += blockDim.x) Ws[t] = w[t];
-}
-
-// ---------------------------------------------------------------------------------
-// pencil pass along y or z (one component slab per CTA, XC contiguous positions)
-// ---------------------------------------------------------------------------------
-template <typename T>
-__global__ void __launch_bounds__(kThreads) k_pencil(PencilArgs a) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  const int M = a.plan.M;
-  cpx<T>* Ws = reinterpret_cast<cpx<T>*>(smem);
-  cpx<T>* A = Ws + M;
-  cpx<T>* B = A + (size_t)a.XC * M;
-  const int s = blockIdx.y;
-  const int x0 = blockIdx.x * a.XC;
-  const int rhs = s / a.slabs_per_rhs;
-  if (a.cg != nullptr && !a.cg->active[rhs]) return;
-  const int comp = (s / a.slabs_per_comp) % a.C;
-  const int XC = min(a.XC, a.X - x0);
-  load_twiddles<T>(Ws, a.W, M);
-  const bool pad = a.dir > 0 && a.Pin != M;
-  if (pad) {
-    for (int t = threadIdx.x; t < XC * M; t += blockDim.x) A[t] = mk<T>(T(0), T(0));
-    __syncthreads();
-  }
-  cpx<T>* pin = const_cast<cpx<T>*>(reinterpret_cast<const cpx<T>*>(a.in)) + (long long)s * a.in_slab;
-  const T beta = a.prologue == 1 ? T(a.cg->beta[rhs]) : T(0);
-  for (int t = threadIdx.x; t < a.Pin * XC; t += blockDim.x) {
-    const int p = t / XC;
-    const int xx = t - p * XC;
-    const long long gi = (long long)p * a.X + x0 + xx;
-    cpx<T> v = pin[gi];
-    if (a.prologue == 1) {
-      const cpx<T> r = reinterpret_cast<const cpx<T>*>(a.aux)[(long long)s * a.in_slab + gi];
-      v = mk<T>(fma(beta, v.x, r.x), fma(beta, v.y, r.y));
-      pin[gi] = v;
-    } else if (a.prologue == 2) {
-      if (comp == rhs && p == 0 && x0 + xx == 0) v.x += T(1);
-    }
-    int pos = p;
-    if (pad) {
-      const int k = sfreq(p, a.Nlog);
-      pos = k < 0 ? k + M : k;
-    }
-    A[xx * M + pos] = v;
-  }
-  __syncthreads();
-  cpx<T>* res = fft_pencils<T>(A, B, XC, M, a.plan, Ws, a.dir);
-  cpx<T>* out = reinterpret_cast<cpx<T>*>(a.out) + (long long)s * a.out_slab;
-  const bool trunc = a.dir < 0 && a.Pout != M;
-  for (int t = threadIdx.x; t < a.Pout * XC; t += blockDim.x) {
-    const int i = t / XC;
-    const int xx = t - i * XC;
-    int pos = i;
-    if (trunc) {
-      const int k = sfreq(i, a.Nlog);
-      pos = k < 0 ? k + M : k;
-    }
-    out[(long long)i * a.X + x0 + xx] = res[xx * M + pos];
-  }
-}
-
-// ---------------------------------------------------------------------------------
-// final forward pass + truncation + projection (+ CG partial p.q)
-// ---------------------------------------------------------------------------------
-template <typename T>
-__global__ void __launch_bounds__(kThreads) k_final(FinalArgs a) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  const int M = a.M;
-  const int C = a.C;
-  cpx<T>* Ws = reinterpret_cast<cpx<T>*>(smem);
-  cpx<T>* A = Ws + M;
-  cpx<T>* B = A + (size_t)C * a.XC * M;
-  double* red = reinterpret_cast<double*>(B + (size_t)C * a.XC * M);
-  const int rhs = blockIdx.y;
-  if (a.cg != nullptr && !a.cg->active[rhs]) return;
-  const int x0 = blockIdx.x * a.XC;
-  const int XC = min(a.XC, a.X - x0);
-  load_twiddles<T>(Ws, a.W, M);
-  const cpx<T>* in = reinterpret_cast<const cpx<T>*>(a.in) + (long long)rhs * C * a.in_comp;
-  const int per = M * XC;
-  for (int t = threadIdx.x; t < C * per; t += blockDim.x) {
-    const int g = t / per;
-    const int rem = t - g * per;
-    const int p = rem / XC;
-    const int xx = rem - p * XC;
-    A[(g * XC + xx) * M + p] = in[(long long)g * a.in_comp + (long long)p * a.X + x0 + xx];
-  }
-  __syncthreads();
-  cpx<T>* res = fft_pencils<T>(A, B, C * XC, M, a.plan, Ws, -1);
-  cpx<T>* out = reinterpret_cast<cpx<T>*>(a.out) + (long long)rhs * C * a.out_comp;
-  const cpx<T>* pdir = (a.cg && a.aux) ? reinterpret_cast<const cpx<T>*>(a.aux) + (long long)rhs * C * a.out_comp
-                                       : nullptr;
-  const cpx<T>* bsub = a.bsub ? reinterpret_cast<const cpx<T>*>(a.bsub) + (long long)rhs * C * a.out_comp
-                              : nullptr;
-  double acc = 0.0;
-  for (int t = threadIdx.x; t < a.Nlog * XC; t += blockDim.x) {
-    const int i = t / XC;
-    const int xx = t - i * XC;
-    const int kl = sfreq(i, a.Nlog);
-    const int pos = kl < 0 ? kl + M : kl;
-    const int x = x0 + xx;
-    int kx, ky, kz;
-    if (a.d == 3) {
-      const int iy = x / a.Nh;
-      kx = x - iy * a.Nh;
-      ky = sfreq(iy, a.Ny);
-      kz = kl;
-    } else {
-      kx = x;
-      ky = kl;
-      kz = 0;
-    }
-    cpx<T> u[3];
-#pragma unroll
-    for (int c = 0; c < 3; ++c) u[c] = c < C ? res[(c * XC + xx) * M + pos] : mk<T>(T(0), T(0));
-    if (a.project) {
-      const T xi[3] = {T(kx * a.invY[0]), T(ky * a.invY[1]), T(kz * a.invY[2])};
-      T n2 = T(0);
-      cpx<T> dot = mk<T>(T(0), T(0));
-#pragma unroll
-      for (int c = 0; c < 3; ++c)
-        if (c < C) {
-          n2 = fma(xi[c], xi[c], n2);
-          dot = mk<T>(fma(xi[c], u[c].x, dot.x), fma(xi[c], u[c].y, dot.y));
-        }
-      if (n2 == T(0)) {
-#pragma unroll
-        for (int c = 0; c < 3; ++c) u[c] = mk<T>(T(0), T(0));
-      } else {
-        const T inv = T(1) / n2;
-#pragma unroll
-        for (int c = 0; c < 3; ++c)
-          if (c < C) {
-            const cpx<T> ge = mk<T>(xi[c] * dot.x * inv, xi[c] * dot.y * inv);
-            u[c] = a.project == 1 ? ge : sub<T>(u[c], ge);
-          }
-      }
-    }
-    const long long oi = (long long)i * a.X + x;
-    if (bsub) {
-      double s = 0.0;
-#pragma unroll
-      for (int c = 0; c < 3; ++c)
-        if (c < C) {
-          u[c] = sub<T>(bsub[(long long)c * a.out_comp + oi], u[c]);
-          s += (double)u[c].x * (double)u[c].x + (double)u[c].y * (double)u[c].y;
-        }
-      acc += (kx == 0 ? 1.0 : 2.0) * s;
-    }
-#pragma unroll
-    for (int c = 0; c < 3; ++c)
-      if (c < C) out[(long long)c * a.out_comp + oi] = u[c];
-    if (pdir) {
-      const double w = kx == 0 ? 1.0 : 2.0;
-      double s = 0.0;
-#pragma unroll
-      for (int c = 0; c < 3; ++c)
-        if (c < C) {
-          const cpx<T> pv = pdir[(long long)c * a.out_comp + oi];
-          s += (double)pv.x * (double)u[c].x + (double)pv.y * (double)u[c].y;
-        }
-      acc += w * s;
-    }
-  }
-  if (a.partial) {
-    const double s = block_sum(acc, red);
-    if (threadIdx.x == 0) a.partial[rhs * a.partial_ld + blockIdx.x] = s;
-  }
-}
-
-// ---------------------------------------------------------------------------------
-// row pass along x: Hermitian-half rows, two real rows packed per complex FFT
-// ---------------------------------------------------------------------------------
-template <typename T>
-__device__ __forceinline__ void apply_coef(const T* coef, long long gi, long long cstride, int ncomp,
-                                           int d, const T* u, T* v, T scale) {
-  if (ncomp == 1) {
-    const T a = coef[gi] * scale;
-    for (int c = 0; c < d; ++c) v[c] = a * u[c];
-  } else if (d == 2) {
-    const T a11 = coef[gi] * scale, a22 = coef[gi + cstride] * scale, a12 = coef[gi + 2 * cstride] * scale;
-    v[0] = fma(a11, u[0], a12 * u[1]);
-    v[1] = fma(a12, u[0], a22 * u[1]);
-  } else {
-    const T a11 = coef[gi] * scale, a22 = coef[gi + cstride] * scale, a33 = coef[gi + 2 * cstride] * scale;
-    const T a23 = coef[gi + 3 * cstride] * scale, a13 = coef[gi + 4 * cstride] * scale,
-            a12 = coef[gi + 5 * cstride] * scale;
-    v[0] = fma(a11, u[0], fma(a12, u[1], a13 * u[2]));
-    v[1] = fma(a12, u[0], fma(a22, u[1], a23 * u[2]));
-    v[2] = fma(a13, u[0], fma(a23, u[1], a33 * u[2]));
-  }
-}
-
-template <typename T>
-__global__ void __launch_bounds__(kThreads) k_xpass(XArgs a) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  const int M = a.M;
-  const int p0 = blockIdx.x * a.YB;
-  const int YB = min(a.YB, a.planes - p0);
-  int rhs = 0, comp0 = 0, rpp;
-  if (a.mode == 0) {
-    rhs = blockIdx.y;
-    rpp = a.C;
-    if (a.cg != nullptr && !a.cg->active[rhs]) return;
-  } else if (a.mode == 1) {
-    rpp = a.R * a.C;
-  } else {
-    comp0 = blockIdx.y;
-    rpp = 1;
-  }
-  const int nrow = YB * rpp;
-  const int npair = (nrow + 1) / 2;
-  const int bufsz = npair * (M + 1);
-  cpx<T>* Ws = reinterpret_cast<cpx<T>*>(smem);
-  cpx<T>* A = Ws + M;
-  cpx<T>* B = A + bufsz;
-  double* red = reinterpret_cast<double*>(B + bufsz);
-  const int Nin = a.Nin;
-  const cpx<T>* in = reinterpret_cast<const cpx<T>*>(a.in);
-  auto row_off = [&](int row) -> long long {
-    const int yy = row / rpp;
-    const int rem = row - yy * rpp;
-    const int f = a.mode == 0 ? rhs * a.C + rem : (a.mode == 1 ? rem : comp0);
-    return (long long)f * a.comp_stride + (long long)(p0 + yy) * Nin;
-  };
-  // stage the rows
-  for (int t = threadIdx.x; t < nrow * Nin; t += blockDim.x) {
-    const int row = t / Nin;
-    const int k = t - row * Nin;
-    B[t] = in[row_off(row) + k];
-  }
-  load_twiddles<T>(Ws, a.W, M);
-  __syncthreads();
-  // Z(k) = X_a(k) + i X_b(k) over the full length-M spectrum (Hermitian extension)
-  for (int t = threadIdx.x; t < npair * M; t += blockDim.x) {
-    const int pp = t / M;
-    const int k = t - pp * M;
-    cpx<T> z[2];
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const int row = 2 * pp + h;
-      cpx<T> v = mk<T>(T(0), T(0));
-      if (row < nrow) {
-        if (k < Nin) {
-          v = B[row * Nin + k];
-          if (k == 0) v.y = T(0);
-        } else if (k > M - Nin) {
-          v = conj_<T>(B[row * Nin + (M - k)]);
-        }
-      }
-      z[h] = v;
-    }
-    A[pp * M + k] = mk<T>(z[0].x - z[1].y, z[0].y + z[1].x);
-  }
-  __syncthreads();
-  cpx<T>* res = fft_pencils<T>(A, B, npair, M, a.plan, Ws, +1);
-  cpx<T>* oth = res == A ? B : A;
-  const T* coef = reinterpret_cast<const T*>(a.coef);
-  const long long cstride = (long long)a.planes * M;
-  if (a.mode == 0) {
-    const int C = a.C;
-    for (int t = threadIdx.x; t < YB * M; t += blockDim.x) {
-      const int yy = t / M;
-      const int x = t - yy * M;
-      T u[3], v[3];
-#pragma unroll
-      for (int c = 0; c < 3; ++c)
-        if (c < C) {
-          const int row = yy * C + c;
-          const cpx<T> z = res[(row >> 1) * M + x];
-          u[c] = (row & 1) ? z.y : z.x;
-        }
-      apply_coef<T>(coef, (long long)(p0 + yy) * M + x, cstride, a.ncomp, C, u, v, T(a.scale));
-#pragma unroll
-      for (int c = 0; c < 3; ++c)
-        if (c < C) {
-          const int row = yy * C + c;
-          if (row & 1) res[(row >> 1) * M + x].y = v[c];
-          else res[(row >> 1) * M + x].x = v[c];
-        }
-    }
-    __syncthreads();
-    cpx<T>* r2 = fft_pencils<T>(res, oth, npair, M, a.plan, Ws, -1);
-    cpx<T>* out = reinterpret_cast<cpx<T>*>(a.out);
-    const int Nout = a.Nout;
-    for (int t = threadIdx.x; t < nrow * Nout; t += blockDim.x) {
-      const int row = t / Nout;
-      const int k = t - row * Nout;
-      const int pp = row >> 1;
-      const cpx<T> zk = r2[pp * M + k];
-      const cpx<T> zm = r2[pp * M + (k == 0 ? 0 : M - k)];
-      cpx<T> X;
-      if ((row & 1) == 0) {
-        X = mk<T>(T(0.5) * (zk.x + zm.x), T(0.5) * (zk.y - zm.y));
-      } else {
-        X = mk<T>(T(0.5) * (zk.y + zm.y), T(-0.5) * (zk.x - zm.x));
-      }
-      out[row_off(row) + k] = X;
-    }
-  } else if (a.mode == 1) {
-    const int R = a.R, C = a.C;
-    double acc[9];
-#pragma unroll
-    for (int i = 0; i < 9; ++i) acc[i] = 0.0;
-    for (int t = threadIdx.x; t < YB * M; t += blockDim.x) {
-      const int yy = t / M;
-      const int x = t - yy * M;
-      T u[3][3];
-#pragma unroll
-      for (int r = 0; r < 3; ++r)
-#pragma unroll
-        for (int c = 0; c < 3; ++c)
-          if (r < R && c < C) {
-            const int row = (yy * R + r) * C + c;
-            const cpx<T> z = res[(row >> 1) * M + x];
-            u[r][c] = (row & 1) ? z.y : z.x;
-          }
-#pragma unroll
-      for (int s = 0; s < 3; ++s)
-        if (s < R) {
-          T v[3];
-          apply_coef<T>(coef, (long long)(p0 + yy) * M + x, cstride, a.ncomp, C, u[s], v, T(1));
-#pragma unroll
-          for (int r = 0; r < 3; ++r)
-            if (r < R) {
-              double e = 0.0;
-#pragma unroll
-              for (int c = 0; c < 3; ++c)
-                if (c < C) e += (double)u[r][c] * (double)v[c];
-              acc[r * 3 + s] += e;
-            }
-        }
-    }
-    for (int r = 0; r < R; ++r)
-      for (int s = 0; s < R; ++s) {
-        const double v = block_sum(acc[r * 3 + s], red);
-        if (threadIdx.x == 0) a.partial[(long long)blockIdx.x * R * R + r * R + s] = v;
-      }
-  } else {
-    T* out = reinterpret_cast<T*>(a.out);
-    for (int t = threadIdx.x; t < YB * M; t += blockDim.x) {
-      const int yy = t / M;
-      const int x = t - yy * M;
-      const cpx<T> z = res[(yy >> 1) * M + x];
-      out[((long long)comp0 * a.planes + p0 + yy) * M + x] = (yy & 1) ? z.y : z.x;
-    }
-  }
 }
 
 // ---------------------------------------------------------------------------------
@@ -761,104 +412,9 @@ __global__ void k_convert_d2f(const double* in, float* out, long long n) {
     out[i] = (float)in[i];
 }
 
-template <typename T>
-__global__ void __launch_bounds__(kThreads) k_fft_batch(const cpx<T>* in, cpx<T>* out, int M,
-                                                         int howmany, int G, int dir, const void* W,
-                                                         FftPlan plan) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  cpx<T>* Ws = reinterpret_cast<cpx<T>*>(smem);
-  cpx<T>* A = Ws + M;
-  cpx<T>* B = A + (size_t)G * M;
-  const int g0 = blockIdx.x * G;
-  const int Ge = min(G, howmany - g0);
-  load_twiddles<T>(Ws, W, M);
-  for (int t = threadIdx.x; t < Ge * M; t += blockDim.x) A[t] = in[(long long)g0 * M + t];
-  __syncthreads();
-  cpx<T>* res = fft_pencils<T>(A, B, Ge, M, plan, Ws, dir);
-  for (int t = threadIdx.x; t < Ge * M; t += blockDim.x) out[(long long)g0 * M + t] = res[t];
-}
-
 // ---------------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------------
-static int current_device() {
-  int dev = 0;
-  cudaGetDevice(&dev);
-  return dev;
-}
-
-template <typename F>
-static cudaError_t ensure_smem(F* fn, size_t bytes) {
-  if (bytes <= 48 * 1024) return cudaSuccess;
-  static thread_local size_t done[64][4] = {};
-  static thread_local const void* fns[64] = {};
-  const int dev = current_device() & 3;
-  int slot = -1;
-  for (int i = 0; i < 64; ++i) {
-    if (fns[i] == (const void*)fn) { slot = i; break; }
-    if (fns[i] == nullptr) { fns[i] = (const void*)fn; slot = i; break; }
-  }
-  if (slot >= 0 && done[slot][dev] >= bytes) return cudaSuccess;
-  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-  if (e == cudaSuccess && slot >= 0) done[slot][dev] = bytes;
-  return e;
-}
-
-template <typename T> int pencil_xc(int M, int X, int C) {
-  const size_t sz = sizeof(cpx<T>);
-  const size_t fixed = M * sz + 512;
-  const size_t per = 2 * (size_t)C * M * sz;
-  long long xc = (long long)((kSmemBudget > fixed ? kSmemBudget - fixed : 0) / per);
-  if (xc < 1) xc = (fixed + per <= kSmemMax) ? 1 : 0;
-  if (xc > 32) xc = 32;
-  if (xc > X) xc = X;
-  return (int)xc;
-}
-
-template <typename T> int xpass_yb(int M, int rpp, int planes) {
-  const size_t sz = sizeof(cpx<T>);
-  const size_t fixed = M * sz + 512;
-  const long long npmax = (long long)((kSmemBudget - fixed) / (2 * (size_t)(M + 1) * sz));
-  long long yb = (2 * npmax) / rpp;
-  if (yb < 1) {
-    const size_t need = fixed + 2 * (size_t)((rpp + 1) / 2) * (M + 1) * sz;
-    yb = need <= kSmemMax ? 1 : 0;
-  }
-  if (yb > 32) yb = 32;
-  if (yb > planes) yb = planes;
-  return (int)yb;
-}
-
-template <typename T> cudaError_t launch_pencil(const PencilArgs& a, cudaStream_t s) {
-  const size_t smem = (size_t)a.plan.M * sizeof(cpx<T>) * (1 + 2 * (size_t)a.XC);
-  cudaError_t e = ensure_smem(k_pencil<T>, smem);
-  if (e != cudaSuccess) return e;
-  dim3 grid((a.X + a.XC - 1) / a.XC, a.nslab);
-  k_pencil<T><<<grid, kThreads, smem, s>>>(a);
-  return cudaGetLastError();
-}
-
-template <typename T> cudaError_t launch_final(const FinalArgs& a, cudaStream_t s) {
-  const size_t smem = (size_t)a.M * sizeof(cpx<T>) * (1 + 2 * (size_t)a.C * a.XC) + 32 * sizeof(double);
-  cudaError_t e = ensure_smem(k_final<T>, smem);
-  if (e != cudaSuccess) return e;
-  dim3 grid((a.X + a.XC - 1) / a.XC, a.nrhs);
-  k_final<T><<<grid, kThreads, smem, s>>>(a);
-  return cudaGetLastError();
-}
-
-template <typename T> cudaError_t launch_xpass(const XArgs& a, int grid_y, cudaStream_t s) {
-  const int rpp = a.mode == 0 ? a.C : (a.mode == 1 ? a.R * a.C : 1);
-  const int npair = (a.YB * rpp + 1) / 2;
-  const size_t smem = (size_t)a.M * sizeof(cpx<T>) + 2 * (size_t)npair * (a.M + 1) * sizeof(cpx<T>) +
-                      32 * sizeof(double);
-  cudaError_t e = ensure_smem(k_xpass<T>, smem);
-  if (e != cudaSuccess) return e;
-  dim3 grid((a.planes + a.YB - 1) / a.YB, grid_y);
-  k_xpass<T><<<grid, kThreads, smem, s>>>(a);
-  return cudaGetLastError();
-}
-
 cudaError_t launch_axis_tables(int nincl, int d, const int* M, int Mmax, const double* invY,
                                const DevIncl* incl, double2* phase, double* sinc, cudaStream_t s) {
   if (nincl == 0) return cudaSuccess;
@@ -954,37 +510,15 @@ cudaError_t launch_convert_d2f(const double* in, float* out, long long n, cudaSt
   return cudaGetLastError();
 }
 
-template <typename T>
-cudaError_t launch_fft_batch(const void* in, void* out, int M, int howmany, int dir, const void* W,
-                             const FftPlan& plan, cudaStream_t s) {
-  int G = pencil_xc<T>(M, howmany, 1);
-  if (G < 1) return cudaErrorInvalidValue;
-  const size_t smem = (size_t)M * sizeof(cpx<T>) * (1 + 2 * (size_t)G);
-  cudaError_t e = ensure_smem(k_fft_batch<T>, smem);
-  if (e != cudaSuccess) return e;
-  const int blocks = (howmany + G - 1) / G;
-  k_fft_batch<T><<<blocks, kThreads, smem, s>>>(reinterpret_cast<const cpx<T>*>(in),
-                                                reinterpret_cast<cpx<T>*>(out), M, howmany, G, dir, W,
-                                                plan);
-  return cudaGetLastError();
-}
-
 // explicit instantiations
 #define HOMB_INST(T)                                                                             \
-  template cudaError_t launch_pencil<T>(const PencilArgs&, cudaStream_t);                        \
-  template cudaError_t launch_final<T>(const FinalArgs&, cudaStream_t);                          \
-  template cudaError_t launch_xpass<T>(const XArgs&, int, cudaStream_t);                         \
-  template int pencil_xc<T>(int, int, int);                                                      \
-  template int xpass_yb<T>(int, int, int);                                                       \
   template cudaError_t launch_rhs<T>(const SpecArgs&, int, int, int, const int*, void*, double*, \
                                      int, cudaStream_t);                                         \
   template cudaError_t launch_cg_update<T>(void*, void*, const void*, const void*, int, int,     \
                                            long long, int, CgScalars*, double*, int,             \
                                            cudaStream_t);                                        \
   template cudaError_t launch_project_promote<T>(const void*, double2*, int, int, int, int, int, \
-                                                 const double*, int, cudaStream_t);              \
-  template cudaError_t launch_fft_batch<T>(const void*, void*, int, int, int, const void*,       \
-                                           const FftPlan&, cudaStream_t);
+                                                 const double*, int, cudaStream_t);
 HOMB_INST(double)
 HOMB_INST(float)
 

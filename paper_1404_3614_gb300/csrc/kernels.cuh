@@ -25,6 +25,7 @@ struct PencilArgs {
   const void* W;
   FftPlan plan;
   CgScalars* cg;   // may be null: no skipping
+  FastDiv fd_XC;   // divides by XC (set by the launcher)
 };
 
 // Last forward pass (z in 3D, y in 2D) over all C components of one field:
@@ -45,6 +46,7 @@ struct FinalArgs {
   double* partial;               // [rhs][gridDim.x]
   int partial_ld;
   const void* bsub;              // residual mode: out = bsub - Gamma(...), partial |out|^2
+  FastDiv fd_XC, fd_per, fd_Nh;  // set by the launcher
 };
 
 // Row pass along x (the contiguous axis) on rows of Nin complex values (k1 >= 0):
@@ -66,6 +68,7 @@ struct XArgs {
   FftPlan plan;
   CgScalars* cg;
   double* partial;        // mode 1: [gridDim.x][R*R]
+  FastDiv fd_Nin, fd_Nout, fd_rpp;   // set by the launcher
 };
 
 struct DevIncl {
