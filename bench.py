@@ -258,7 +258,7 @@ def run_gpu(args):
     __graft_entry__.build()
     import paper_1404_3614_gb300 as hb
 
-    problem = workload()
+    problem = workload(args.workload)
     prec = hb.HOM_FP64 if args.precision == "fp64" else hb.HOM_MIXED
     solver = hb.Bounds(local)
     stream = torch.cuda.current_stream(dev)
@@ -356,7 +356,8 @@ def run_gpu(args):
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": False, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64" if prec == hb.HOM_FP64 else "f32+f64",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "precision": args.precision, "tol": TOL,
+        "config": {"workload": WORKLOAD if args.workload == "cube3d_N41" else WORKLOADS[args.workload],
+                   "precision": args.precision, "tol": TOL,
                    "l2": "flushed between steps (256 MiB write, outside the timed region)",
                    "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
         "bounds": {"upper_11": float(out["upper"][0, 0]), "lower_11": float(out["lower"][0, 0])},

@@ -15,7 +15,10 @@
 namespace homb {
 
 constexpr int kPassThreads = 256;
-constexpr size_t kPassSmemBudget = 96 * 1024;
+#ifndef HOMB_PASS_SMEM_KB
+#define HOMB_PASS_SMEM_KB 48
+#endif
+constexpr size_t kPassSmemBudget = HOMB_PASS_SMEM_KB * 1024;
 constexpr size_t kPassSmemMax = 220 * 1024;
 
 // compile-time lengths with specialised kernels (every M = 2N-1 of the paper's workloads)
