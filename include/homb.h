@@ -99,6 +99,10 @@ typedef struct {
                            criteria", Parseval L2 norm); <= 0 selects 1e-8       */
   int32_t check_every;  /* host polls convergence every k iterations; 0 -> 8     */
   int32_t sides;        /* bit 0: primal (upper), bit 1: dual (lower); 0 -> both */
+  int32_t graph;        /* hom_bounds_batched: replay the batch launch as a CUDA
+                           graph captured on `stream` (needs a non-NULL stream)   */
+  int32_t autotune;     /* hom_bounds_batched: time the shared-memory chunk sizes
+                           on this batch once and keep the fastest in the ctx    */
 } hom_opts;
 
 typedef struct {
@@ -144,6 +148,24 @@ hom_status hom_bounds(hom_ctx* ctx, const hom_problem* prob, const hom_opts* opt
                       void* d_workspace, size_t workspace_bytes, void* stream,
                       double* upper, double* lower, double* mean, double* D,
                       hom_report* rep);
+
+/* Batched bounds for n two-dimensional cells of possibly different N, geometry and
+ * phases, in ONE persistent kernel launch: each CTA takes (problem, side) tasks from an
+ * atomic work queue (largest grids first) and runs the whole pipeline of hom_bounds for
+ * its task (coefficient, CG on both right-hand sides with block reductions, FP64
+ * re-projection and exact energies). precision HOM_MIXED: FP32 CG vectors and matvecs,
+ * FP64 scalars, coefficients, re-projection and energies; HOM_FP64: everything FP64.
+ * There is no outer refinement: a mixed solve stops at tol or when FP32 accuracy runs
+ * out (status 2), and the bounds stay guaranteed. Outputs (host): upper, lower [n][2][2]
+ * row-major, status [n] (worst of the four solves: 0 ok, 1 max_iter/FP32 floor, -2
+ * breakdown), iters [n][2][2] (side, rhs; may be NULL), rep aggregated (may be NULL).
+ * Returns HOM_WARN_NOT_CONVERGED when any status is not 0. Synchronises `stream`. */
+hom_status hom_batched_workspace_size(hom_ctx* ctx, int32_t n, const hom_problem* probs,
+                                      const hom_opts* opts, size_t* bytes);
+hom_status hom_bounds_batched(hom_ctx* ctx, int32_t n, const hom_problem* probs,
+                              const hom_opts* opts, void* d_workspace, size_t workspace_bytes,
+                              void* stream, double* upper, double* lower, int32_t* status,
+                              int32_t* iters, hom_report* rep);
 
 /* Step-level entry points (device buffers; enqueue only). Workspace for these is
  * hom_step_workspace_size. */

@@ -9,12 +9,13 @@ from __future__ import annotations
 
 from . import binding
 from .binding import (HOM_BALL, HOM_BOX, HOM_DUAL, HOM_FP32, HOM_FP64, HOM_MIXED, HOM_PRIMAL,
-                      HombError, hom_bounds, hom_coefficient, hom_create, hom_destroy, hom_energy,
+                      HombError, hom_batched_workspace_size, hom_bounds, hom_bounds_batched, hom_coefficient, hom_create, hom_destroy, hom_energy,
                       hom_fft, hom_kernel_timing, hom_last_error, hom_matvec, hom_problem_info,
                       hom_profile_kernel, hom_rhs, hom_step_workspace_size, hom_version,
                       hom_workspace_size, make_opts)
 
-__all__ = ["binding", "Bounds", "HombError", "hom_bounds", "hom_coefficient", "hom_create",
+__all__ = ["binding", "Bounds", "HombError", "hom_bounds", "hom_bounds_batched", "hom_batched_workspace_size",
+           "hom_coefficient", "hom_create",
            "hom_destroy", "hom_energy", "hom_fft", "hom_kernel_timing", "hom_last_error",
            "hom_matvec", "hom_problem_info", "hom_profile_kernel", "hom_rhs",
            "hom_step_workspace_size", "hom_version", "hom_workspace_size", "make_opts",
@@ -48,6 +49,15 @@ class Bounds:
         ws = self.workspace(nbytes)
         s = stream if stream is not None else self.torch.cuda.current_stream(self.device).cuda_stream
         return hom_bounds(self.ctx, problem, opts, ws.data_ptr(), ws.numel(), s)
+
+    def batched(self, problems, precision=HOM_MIXED, tol=1e-4, max_iter=10000, graph=0, autotune=0,
+                stream=None):
+        """hom_bounds_batched on a list of 2D problems (one persistent launch)."""
+        opts = make_opts(precision, tol, max_iter, 8, 3, graph, autotune)
+        nbytes = hom_batched_workspace_size(self.ctx, problems, opts)
+        ws = self.workspace(nbytes)
+        s = stream if stream is not None else self.torch.cuda.current_stream(self.device).cuda_stream
+        return hom_bounds_batched(self.ctx, problems, opts, ws.data_ptr(), ws.numel(), s)
 
     def close(self):
         if self.ctx is not None:

@@ -40,7 +40,8 @@ class hom_problem(C.Structure):
 
 class hom_opts(C.Structure):
     _fields_ = [("precision", C.c_int32), ("max_iter", C.c_int32), ("tol", C.c_double),
-                ("check_every", C.c_int32), ("sides", C.c_int32)]
+                ("check_every", C.c_int32), ("sides", C.c_int32), ("graph", C.c_int32),
+                ("autotune", C.c_int32)]
 
 
 class hom_report(C.Structure):
@@ -70,6 +71,9 @@ def _load():
         "hom_workspace_size": (i32, [vp, P(hom_problem), P(hom_opts), P(sz)]),
         "hom_bounds": (i32, [vp, P(hom_problem), P(hom_opts), vp, sz, vp, dp, dp, dp, dp, P(hom_report)]),
         "hom_step_workspace_size": (i32, [vp, P(hom_problem), i32, P(sz)]),
+        "hom_batched_workspace_size": (i32, [vp, i32, P(hom_problem), P(hom_opts), P(sz)]),
+        "hom_bounds_batched": (i32, [vp, i32, P(hom_problem), P(hom_opts), vp, sz, vp, dp, dp, P(i32), P(i32),
+                                     P(hom_report)]),
         "hom_coefficient": (i32, [vp, P(hom_problem), i32, i32, vp, vp, sz, vp]),
         "hom_rhs": (i32, [vp, P(hom_problem), i32, i32, i32, vp, vp, sz, vp]),
         "hom_matvec": (i32, [vp, P(hom_problem), i32, i32, i32, i32, vp, vp, vp, vp, sz, vp]),
@@ -172,10 +176,47 @@ def hom_problem_info(ctx, problem):
     return {"ncomp": ncomp.value, "M": list(M), "field_elems": fe.value, "grid_elems": ge.value}
 
 
-def make_opts(precision=HOM_FP64, tol=1e-8, max_iter=10000, check_every=8, sides=3):
+def make_opts(precision=HOM_FP64, tol=1e-8, max_iter=10000, check_every=8, sides=3, graph=0, autotune=0):
     o = hom_opts()
     o.precision, o.tol, o.max_iter, o.check_every, o.sides = precision, tol, max_iter, check_every, sides
+    o.graph, o.autotune = graph, autotune
     return o
+
+
+def problems_array(problems):
+    """A contiguous hom_problem[n] array (and the objects it points into)."""
+    arr = (hom_problem * len(problems))()
+    keep = []
+    for i, pr in enumerate(problems):
+        p, k = problem_struct(pr)
+        arr[i] = p
+        keep.append(k)
+    return arr, keep
+
+
+def hom_batched_workspace_size(ctx, problems, opts):
+    arr, keep = problems_array(problems)
+    n = C.c_size_t()
+    check(ctx, lib.hom_batched_workspace_size(ctx, len(problems), arr, C.byref(opts), C.byref(n)))
+    return n.value
+
+
+def hom_bounds_batched(ctx, problems, opts, d_ws, ws_bytes, stream=0):
+    """Returns dict(upper [n,2,2], lower [n,2,2], status [n], iters [n,2,2], report, code)."""
+    arr, keep = problems_array(problems)
+    n = len(problems)
+    up = (C.c_double * (4 * n))()
+    lo = (C.c_double * (4 * n))()
+    stt = (C.c_int32 * n)()
+    its = (C.c_int32 * (4 * n))()
+    rep = hom_report()
+    code = lib.hom_bounds_batched(ctx, n, arr, C.byref(opts), C.c_void_p(d_ws), ws_bytes, C.c_void_p(stream),
+                                  up, lo, stt, its, C.byref(rep))
+    check(ctx, code)
+    return {"upper": np.array(up[:]).reshape(n, 2, 2), "lower": np.array(lo[:]).reshape(n, 2, 2),
+            "status": np.array(stt[:]), "iters": np.array(its[:]).reshape(n, 2, 2), "code": code,
+            "report": {"ms_total": rep.ms_total, "launches": rep.launches, "h2d_bytes": rep.h2d_bytes,
+                       "d2h_bytes": rep.d2h_bytes}}
 
 
 def hom_workspace_size(ctx, problem, opts):

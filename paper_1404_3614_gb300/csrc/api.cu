@@ -35,6 +35,15 @@ struct hom_ctx {
   size_t ev_used = 0;
   long long launches = 0;              // kernels launched (since the call began)
   long long h2d = 0, d2h = 0;          // bytes copied
+  // batched path: pinned staging, captured graph and autotuned chunk capacities
+  unsigned char* pin_in = nullptr;
+  size_t pin_in_bytes = 0;
+  unsigned char* pin_out = nullptr;
+  size_t pin_out_bytes = 0;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t graph_exec = nullptr;
+  std::vector<long long> graph_key;
+  std::vector<std::pair<long long, int>> tuned_cap;   // (key, cap)
 };
 
 namespace {
@@ -787,6 +796,142 @@ bool sym_inv_spd(const double* B, int d, double* out) {  // leading dim d
   return true;
 }
 
+// ---------------------------------------------------------------------------------
+// batched 2D path
+// ---------------------------------------------------------------------------------
+struct BatchPlan {
+  std::vector<BTask> tasks;
+  std::vector<DevIncl> incl;
+  std::vector<double2> tw64;
+  std::vector<float2> tw32;
+  int M0max = 1, M1max = 1, Mmax = 1;
+  long long slot_bytes = 0;
+  int nslots_max = 0;
+  // workspace offsets
+  size_t o_tasks, o_incl, o_tw64, o_tw32, o_counter, o_energy, o_iters, o_status, o_resid, o_slots, total;
+  size_t in_bytes;    // contiguous H2D region [o_tasks, o_counter)
+  size_t out_bytes;   // contiguous D2H region [o_energy, o_slots)
+};
+
+int device_sms(int device) {
+  int n = 0;
+  if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, device) != cudaSuccess || n <= 0) n = 152;
+  return n;
+}
+
+hom_status build_batch(hom_ctx* ctx, int n, const hom_problem* probs, const hom_opts* o, BatchPlan& bp) {
+  if (n < 1 || !probs) return fail(ctx, HOM_ERR_INVALID_ARG, "batch needs n >= 1 problems");
+  const size_t elem = o->precision == HOM_MIXED ? 8 : 16;
+  std::vector<int> Ms;
+  auto tw_off = [&](int M) -> int {
+    int off = 0;
+    for (int m : Ms) {
+      if (m == M) return off;
+      off += m;
+    }
+    Ms.push_back(M);
+    std::vector<double2> w64;
+    std::vector<float2> w32;
+    twiddles(M, w64, w32);
+    bp.tw64.insert(bp.tw64.end(), w64.begin(), w64.end());
+    bp.tw32.insert(bp.tw32.end(), w32.begin(), w32.end());
+    return off;
+  };
+  for (int i = 0; i < n; ++i) {
+    Geometry g;
+    CKS(build_geometry(ctx, &probs[i], g));
+    if (g.d != 2) return fail(ctx, HOM_ERR_INVALID_ARG, "hom_bounds_batched handles two-dimensional cells (d = 2)");
+    double A0f[9], B0[9] = {};
+    for (int a = 0; a < 3; ++a)
+      for (int b = 0; b < 3; ++b) A0f[3 * a + b] = g.A0[a][b];
+    inv3(A0f, 2, B0);
+    for (int side = 0; side < 2; ++side) {
+      BTask t;
+      memset(&t, 0, sizeof t);
+      t.prob = i;
+      t.side = side;
+      t.ncomp = g.ncomp;
+      t.nincl = (int)g.incl.size();
+      t.incl_off = (int)bp.incl.size();
+      t.N0 = g.N[0];
+      t.N1 = g.N[1];
+      t.M0 = g.M[0];
+      t.M1 = g.M[1];
+      t.Nh = g.Nh;
+      t.Nxs = g.Nxs;
+      t.invY[0] = g.invY[0];
+      t.invY[1] = g.invY[1];
+      t.invVol = 1.0 / (g.Y[0] * g.Y[1]);
+      pack_sym(side == 0 ? A0f : B0, 2, g.ncomp, t.C0p);
+      t.tw0 = tw_off(g.M[0]);
+      t.tw1 = tw_off(g.M[1]);
+      t.plan0 = g.plan[0];
+      t.plan1 = g.plan[1];
+      for (size_t j = 0; j < g.incl.size(); ++j) {
+        const hom_inclusion& I = g.incl[j];
+        DevIncl D;
+        memset(&D, 0, sizeof D);
+        D.shape = I.shape == HOM_BOX ? 0 : 1;
+        D.same_as_prev = (j > 0 && I.shape == HOM_BALL && g.incl[j - 1].shape == HOM_BALL &&
+                          I.size[0] == g.incl[j - 1].size[0]) ? 1 : 0;
+        for (int a = 0; a < 3; ++a) {
+          D.c[a] = I.center[a];
+          D.h[a] = I.size[a];
+        }
+        double dA[9] = {};
+        if (side == 0) {
+          for (int k = 0; k < 9; ++k) dA[k] = I.A[k] - A0f[k];
+        } else {
+          double Bi[9] = {};
+          inv3(I.A, 2, Bi);
+          for (int k = 0; k < 9; ++k) dA[k] = Bi[k] - B0[k];
+        }
+        pack_sym(dA, 2, g.ncomp, D.dA);
+        bp.incl.push_back(D);
+      }
+      bp.M0max = std::max(bp.M0max, t.M0);
+      bp.M1max = std::max(bp.M1max, t.M1);
+      bp.slot_bytes = std::max(bp.slot_bytes, batch_slot_bytes(t, (int)elem));
+      bp.tasks.push_back(t);
+    }
+  }
+  bp.Mmax = std::max(bp.M0max, bp.M1max);
+  if (bp.Mmax > 2047) return fail(ctx, HOM_ERR_INVALID_ARG, "batched grids are limited to N <= 1024");
+  // largest grids first (longest tasks start first)
+  std::stable_sort(bp.tasks.begin(), bp.tasks.end(), [](const BTask& a, const BTask& b) {
+    return (long long)a.M0 * a.M1 > (long long)b.M0 * b.M1;
+  });
+  if (bp.incl.empty()) bp.incl.resize(1);
+  const int nt = (int)bp.tasks.size();
+  bp.nslots_max = std::min(nt, device_sms(ctx->device) * 4);
+  Layout L{};
+  bp.o_tasks = L.take(bp.tasks.size() * sizeof(BTask));
+  bp.o_incl = L.take(bp.incl.size() * sizeof(DevIncl));
+  bp.o_tw64 = L.take(bp.tw64.size() * sizeof(double2));
+  bp.o_tw32 = L.take(bp.tw32.size() * sizeof(float2));
+  bp.o_counter = L.take(sizeof(int));
+  bp.in_bytes = bp.o_counter - bp.o_tasks;
+  bp.o_energy = L.take((size_t)nt * 4 * sizeof(double));
+  bp.o_iters = L.take((size_t)nt * 2 * sizeof(int));
+  bp.o_status = L.take((size_t)nt * 2 * sizeof(int));
+  bp.o_resid = L.take((size_t)nt * 2 * sizeof(double));
+  bp.o_slots = L.take(0);
+  bp.out_bytes = bp.o_slots - bp.o_energy;
+  L.off = bp.o_slots + (size_t)bp.nslots_max * (size_t)bp.slot_bytes;
+  bp.total = L.off;
+  return HOM_OK;
+}
+
+hom_status ensure_pinned(hom_ctx* ctx, unsigned char** buf, size_t* have, size_t need) {
+  if (*have >= need) return HOM_OK;
+  if (*buf) cudaFreeHost(*buf);
+  *buf = nullptr;
+  *have = 0;
+  CK(cudaMallocHost((void**)buf, need));
+  *have = need;
+  return HOM_OK;
+}
+
 }  // namespace
 
 // =====================================================================================
@@ -818,6 +963,10 @@ hom_status hom_destroy(hom_ctx* ctx) {
   for (cudaEvent_t e : ctx->ev) cudaEventDestroy(e);
   if (ctx->host_cg) cudaFreeHost(ctx->host_cg);
   if (ctx->host_e) cudaFreeHost(ctx->host_e);
+  if (ctx->pin_in) cudaFreeHost(ctx->pin_in);
+  if (ctx->pin_out) cudaFreeHost(ctx->pin_out);
+  if (ctx->graph_exec) cudaGraphExecDestroy(ctx->graph_exec);
+  if (ctx->graph) cudaGraphDestroy(ctx->graph);
   delete ctx;
   return HOM_OK;
 }
@@ -918,6 +1067,195 @@ hom_status hom_bounds(hom_ctx* ctx, const hom_problem* prob, const hom_opts* opt
     rep->ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   }
   return worst;
+}
+
+hom_status hom_batched_workspace_size(hom_ctx* ctx, int32_t n, const hom_problem* probs, const hom_opts* opts,
+                                      size_t* bytes) {
+  if (!ctx || !opts || !bytes) return fail(ctx, HOM_ERR_INVALID_ARG, "NULL argument");
+  BatchPlan bp;
+  CKS(build_batch(ctx, n, probs, opts, bp));
+  *bytes = bp.total;
+  return HOM_OK;
+}
+
+hom_status hom_bounds_batched(hom_ctx* ctx, int32_t n, const hom_problem* probs, const hom_opts* opts, void* d_ws,
+                              size_t ws_bytes, void* stream, double* upper, double* lower, int32_t* status,
+                              int32_t* iters, hom_report* rep) {
+  if (!ctx || !opts) return fail(ctx, HOM_ERR_INVALID_ARG, "NULL argument");
+  const auto t0 = std::chrono::steady_clock::now();
+  ctx->err.clear();
+  ctx->launches = ctx->h2d = ctx->d2h = 0;
+  CKS(set_device(ctx));
+  if (opts->precision != HOM_FP64 && opts->precision != HOM_MIXED)
+    return fail(ctx, HOM_ERR_INVALID_ARG, "precision must be HOM_FP64 or HOM_MIXED");
+  BatchPlan bp;
+  CKS(build_batch(ctx, n, probs, opts, bp));
+  if (!d_ws || ws_bytes < bp.total) return fail(ctx, HOM_ERR_WORKSPACE, "workspace too small");
+  if (reinterpret_cast<uintptr_t>(d_ws) % 256) return fail(ctx, HOM_ERR_INVALID_ARG, "workspace must be 256-byte aligned");
+  unsigned char* base = static_cast<unsigned char*>(d_ws);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const bool f32 = opts->precision == HOM_MIXED;
+  const int nt = (int)bp.tasks.size();
+  // stage the tables in pinned memory (a captured graph reads them at replay)
+  CKS(ensure_pinned(ctx, &ctx->pin_in, &ctx->pin_in_bytes, bp.in_bytes));
+  CKS(ensure_pinned(ctx, &ctx->pin_out, &ctx->pin_out_bytes, bp.out_bytes));
+  memset(ctx->pin_in, 0, bp.in_bytes);
+  memcpy(ctx->pin_in + (bp.o_tasks - bp.o_tasks), bp.tasks.data(), bp.tasks.size() * sizeof(BTask));
+  memcpy(ctx->pin_in + (bp.o_incl - bp.o_tasks), bp.incl.data(), bp.incl.size() * sizeof(DevIncl));
+  memcpy(ctx->pin_in + (bp.o_tw64 - bp.o_tasks), bp.tw64.data(), bp.tw64.size() * sizeof(double2));
+  memcpy(ctx->pin_in + (bp.o_tw32 - bp.o_tasks), bp.tw32.data(), bp.tw32.size() * sizeof(float2));
+  const double tol = opts->tol > 0 ? opts->tol : 1e-8;
+  const int sms = device_sms(ctx->device);
+  const int elem = f32 ? 8 : 16;
+  const int cap_min = 2 * (bp.Mmax + 1);
+  auto args_for = [&](int cap, int max_iter) {
+    BArgs a{};
+    a.tasks = reinterpret_cast<const BTask*>(base + bp.o_tasks);
+    a.ntasks = nt;
+    a.counter = reinterpret_cast<int*>(base + bp.o_counter);
+    a.incl = reinterpret_cast<const DevIncl*>(base + bp.o_incl);
+    a.tw64 = reinterpret_cast<const double2*>(base + bp.o_tw64);
+    a.tw32 = reinterpret_cast<const float2*>(base + bp.o_tw32);
+    a.slots = base + bp.o_slots;
+    a.slot_bytes = bp.slot_bytes;
+    a.energy = reinterpret_cast<double*>(base + bp.o_energy);
+    a.iters = reinterpret_cast<int*>(base + bp.o_iters);
+    a.status = reinterpret_cast<int*>(base + bp.o_status);
+    a.resid = reinterpret_cast<double*>(base + bp.o_resid);
+    a.tol2 = tol * tol;
+    a.max_iter = max_iter;
+    a.cap = cap;
+    a.M0max = bp.M0max;
+    a.M1max = bp.M1max;
+    return a;
+  };
+  auto grid_for = [&](int cap, size_t* smem) {
+    *smem = batch_smem_bytes(bp.M0max, bp.M1max, cap, elem);
+    const int bps = f32 ? batch_blocks_per_sm<float>(*smem) : batch_blocks_per_sm<double>(*smem);
+    return std::max(1, std::min(bp.nslots_max, sms * bps));
+  };
+  auto enqueue = [&](int cap, int max_iter) -> hom_status {
+    size_t smem = 0;
+    const int grid = grid_for(cap, &smem);
+    CK(h2d_copy(ctx, base + bp.o_tasks, ctx->pin_in, bp.in_bytes, st));
+    CK(cudaMemsetAsync(base + bp.o_counter, 0, sizeof(int), st));
+    const BArgs a = args_for(cap, max_iter);
+    if (f32) KL(launch_batch<float>(a, grid, smem, st));
+    else KL(launch_batch<double>(a, grid, smem, st));
+    CK(d2h_copy(ctx, ctx->pin_out, base + bp.o_energy, bp.out_bytes, st));
+    return HOM_OK;
+  };
+  // chunk capacity: autotuned once per (grid extent, precision) or the default
+  int cap = std::max(2048, cap_min);
+  const long long tkey = (long long)bp.Mmax * 4 + (f32 ? 1 : 0);
+  bool tuned = false;
+  for (auto& kv : ctx->tuned_cap)
+    if (kv.first == tkey) { cap = std::max(kv.second, cap_min); tuned = true; }
+  if (opts->autotune && !tuned) {
+    float best = 1e30f;
+    int best_cap = cap;
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    for (int c : {2048, 4096, 8192}) {
+      if (c < cap_min || batch_smem_bytes(bp.M0max, bp.M1max, c, elem) > 200 * 1024) continue;
+      CKS(enqueue(c, 3));                        // warm-up probe: 3 CG iterations per task
+      CK(cudaEventRecord(e0, st));
+      CKS(enqueue(c, 3));
+      CK(cudaEventRecord(e1, st));
+      CK(cudaEventSynchronize(e1));
+      float ms = 0;
+      CK(cudaEventElapsedTime(&ms, e0, e1));
+      if (ms < best) { best = ms; best_cap = c; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cap = best_cap;
+    ctx->tuned_cap.push_back({tkey, cap});
+  }
+  const int max_iter = opts->max_iter > 0 ? opts->max_iter : 10000;
+  if (opts->graph && st != nullptr) {
+    size_t smem = 0;
+    const int grid = grid_for(cap, &smem);
+    const std::vector<long long> key = {(long long)(uintptr_t)d_ws, (long long)bp.total, nt, grid, (long long)smem, cap,
+                                        (long long)f32, max_iter, (long long)(tol * 1e18), (long long)ctx->pin_in_bytes,
+                                        (long long)ctx->pin_out_bytes, bp.M0max, bp.M1max, bp.slot_bytes};
+    if (!ctx->graph_exec || ctx->graph_key != key) {
+      if (ctx->graph_exec) cudaGraphExecDestroy(ctx->graph_exec);
+      if (ctx->graph) cudaGraphDestroy(ctx->graph);
+      ctx->graph_exec = nullptr;
+      ctx->graph = nullptr;
+      CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+      const hom_status s = enqueue(cap, max_iter);
+      cudaGraph_t g = nullptr;
+      const cudaError_t ee = cudaStreamEndCapture(st, &g);
+      if (s != HOM_OK) return s;
+      CK(ee);
+      ctx->graph = g;
+      CK(cudaGraphInstantiate(&ctx->graph_exec, g, 0));
+      ctx->graph_key = key;
+    } else {
+      ctx->h2d += bp.in_bytes;
+      ctx->d2h += bp.out_bytes;
+      ctx->launches += 1;
+    }
+    CK(cudaGraphLaunch(ctx->graph_exec, st));
+  } else {
+    CKS(enqueue(cap, max_iter));
+  }
+  CK(cudaStreamSynchronize(st));
+  // results
+  const double* E = reinterpret_cast<const double*>(ctx->pin_out);
+  const int* IT = reinterpret_cast<const int*>(ctx->pin_out + (bp.o_iters - bp.o_energy));
+  const int* ST = reinterpret_cast<const int*>(ctx->pin_out + (bp.o_status - bp.o_energy));
+  const double* RS = reinterpret_cast<const double*>(ctx->pin_out + (bp.o_resid - bp.o_energy));
+  std::vector<int> task_of(2 * n, -1);
+  for (int k = 0; k < nt; ++k) task_of[2 * bp.tasks[k].prob + bp.tasks[k].side] = k;
+  hom_status worst = HOM_OK;
+  if (rep) memset(rep, 0, sizeof *rep);
+  for (int i = 0; i < n; ++i) {
+    const int kp = task_of[2 * i], kd = task_of[2 * i + 1];
+    double Au[4], Bu[4], Lo[4];
+    for (int a = 0; a < 2; ++a)
+      for (int b = 0; b < 2; ++b) {
+        Au[2 * a + b] = 0.5 * (E[kp * 4 + 2 * a + b] + E[kp * 4 + 2 * b + a]);
+        Bu[2 * a + b] = 0.5 * (E[kd * 4 + 2 * a + b] + E[kd * 4 + 2 * b + a]);
+      }
+    int stt = 0;
+    for (int k : {kp, kd})
+      for (int r = 0; r < 2; ++r) {
+        const int v = ST[k * 2 + r];
+        if (v == -2) stt = -2;
+        else if (v != 0 && stt == 0) stt = 1;
+      }
+    if (!sym_inv_spd(Bu, 2, Lo)) {
+      stt = -2;
+      for (int q = 0; q < 4; ++q) Lo[q] = NAN;
+    }
+    if (upper) memcpy(upper + 4 * i, Au, sizeof Au);
+    if (lower) memcpy(lower + 4 * i, Lo, sizeof Lo);
+    if (status) status[i] = stt;
+    if (iters)
+      for (int side = 0; side < 2; ++side)
+        for (int r = 0; r < 2; ++r) iters[4 * i + 2 * side + r] = IT[(side ? kd : kp) * 2 + r];
+    if (stt == -2) worst = HOM_ERR_BREAKDOWN;
+    else if (stt == 1 && worst == HOM_OK) worst = HOM_WARN_NOT_CONVERGED;
+    if (rep)
+      for (int side = 0; side < 2; ++side)
+        for (int r = 0; r < 2; ++r) {
+          const int k = side ? kd : kp;
+          rep->iters[side][r] = std::max(rep->iters[side][r], IT[k * 2 + r]);
+          rep->resid[side][r] = std::max(rep->resid[side][r], RS[k * 2 + r]);
+        }
+  }
+  if (rep) {
+    rep->launches = ctx->launches;
+    rep->h2d_bytes = ctx->h2d;
+    rep->d2h_bytes = ctx->d2h;
+    rep->ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  }
+  if (worst == HOM_ERR_BREAKDOWN) ctx->err = "a batched solve broke down (see status[])";
+  return worst == HOM_OK ? HOM_OK : HOM_WARN_NOT_CONVERGED;
 }
 
 hom_status hom_coefficient(hom_ctx* ctx, const hom_problem* prob, int32_t side, int32_t precision,

@@ -39,7 +39,7 @@ constexpr int kMaxRadices = 24;
 struct FastDiv {
   uint32_t d, m, s;
   __host__ __device__ FastDiv() : d(1), m(1), s(0) {}
-  __host__ explicit FastDiv(uint32_t dd) : d(dd ? dd : 1) {
+  __host__ __device__ explicit FastDiv(uint32_t dd) : d(dd ? dd : 1) {
     uint32_t sh = 0;
     while ((1ull << sh) < d) ++sh;
     s = sh;

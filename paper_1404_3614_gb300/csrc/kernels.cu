@@ -10,6 +10,7 @@
 #include <math.h>
 
 #include "kernels.cuh"
+#include "spectrum.cuh"
 
 namespace homb {
 
@@ -24,60 +25,6 @@ __device__ __forceinline__ void load_twiddles(cpx<T>* Ws, const void* W, int M) 
 // ---------------------------------------------------------------------------------
 // closed-form Fourier coefficients of the matrix-inclusion coefficient
 // ---------------------------------------------------------------------------------
-// (sin q - q cos q) / q^3, with its Taylor series near 0
-__device__ __forceinline__ double ball_radial(double q) {
-  if (q < 0.1) {
-    const double q2 = q * q;
-    return 1.0 / 3.0 + q2 * (-1.0 / 30.0 + q2 * (1.0 / 840.0 + q2 * (-1.0 / 45360.0 + q2 / 3991680.0)));
-  }
-  double s, c;
-  sincos(q, &s, &c);
-  return (s - q * c) / (q * q * q);
-}
-
-// J1(q) / q, with its Taylor series near 0
-__device__ __forceinline__ double disk_radial(double q) {
-  if (q < 1e-3) return 0.5 - q * q / 16.0;
-  return j1(q) / q;
-}
-
-__device__ void ahat_eval(const SpecArgs& a, const int* ni, const int* ns, double2* out) {
-  for (int q = 0; q < a.ncomp; ++q) out[q] = make_double2(0.0, 0.0);
-  if (ns[0] == 0 && ns[1] == 0 && ns[2] == 0)
-    for (int q = 0; q < a.ncomp; ++q) out[q].x = a.A0p[q];
-  double rad = 0.0;
-  for (int j = 0; j < a.nincl; ++j) {
-    const DevIncl& I = a.incl[j];
-    double f;
-    if (I.shape == 0) {
-      f = a.invVol;
-      for (int al = 0; al < a.d; ++al) f *= a.sinc[((long long)j * 3 + al) * a.Mmax + ni[al]];
-    } else {
-      if (!I.same_as_prev) {
-        double xi2 = 0.0;
-        for (int al = 0; al < a.d; ++al) {
-          const double xi = ns[al] * a.invY[al];
-          xi2 += xi * xi;
-        }
-        const double R = I.h[0];
-        const double q = 2.0 * M_PI * R * sqrt(xi2);
-        rad = a.d == 3 ? 4.0 * M_PI * R * R * R * ball_radial(q) : 2.0 * M_PI * R * R * disk_radial(q);
-      }
-      f = rad * a.invVol;
-    }
-    double2 ph = a.phase[((long long)j * 3 + 0) * a.Mmax + ni[0]];
-    for (int al = 1; al < a.d; ++al) {
-      const double2 t = a.phase[((long long)j * 3 + al) * a.Mmax + ni[al]];
-      ph = make_double2(ph.x * t.x - ph.y * t.y, ph.x * t.y + ph.y * t.x);
-    }
-    for (int q = 0; q < a.ncomp; ++q) {
-      const double s = f * I.dA[q];
-      out[q].x = fma(s, ph.x, out[q].x);
-      out[q].y = fma(s, ph.y, out[q].y);
-    }
-  }
-}
-
 __global__ void k_axis_tables(int nincl, int d, int M0, int M1, int M2, int Mmax, double iy0,
                               double iy1, double iy2, const DevIncl* incl, double2* phase,
                               double* sinc) {
@@ -120,15 +67,6 @@ __global__ void k_spectrum(SpecArgs a, double2* out) {
     ahat_eval(a, ni, ns, v);
     for (int q = 0; q < a.ncomp; ++q) out[q * total + e] = v[q];
   }
-}
-
-__device__ __forceinline__ int sym_index(int d, int al, int be) {
-  if (al == be) return al;
-  const int lo = al < be ? al : be, hi = al < be ? be : al;
-  if (d == 2) return 2;
-  if (lo == 1 && hi == 2) return 3;
-  if (lo == 0 && hi == 2) return 4;
-  return 5;
 }
 
 template <typename T>

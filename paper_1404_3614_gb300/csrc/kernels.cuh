@@ -93,6 +93,63 @@ struct SpecArgs {
   int Mmax;
 };
 
+// One batched 2D task: a (problem, side) pair solved entirely by one CTA of the
+// persistent batch kernel (coefficient build, CG on both right-hand sides, FP64 energies).
+struct BTask {
+  int prob, side, ncomp, nincl, incl_off;
+  int N0, N1, M0, M1, Nh, Nxs;
+  double invY[2];
+  double invVol;
+  double C0p[3];
+  int tw0, tw1;            // offsets of the length-M0 / M1 tables in the twiddle pools
+  FftPlan plan0, plan1;
+};
+
+struct BArgs {
+  const BTask* tasks;
+  int ntasks;
+  int* counter;            // work queue head (zero before launch)
+  const DevIncl* incl;
+  const double2* tw64;
+  const float2* tw32;
+  unsigned char* slots;    // per-CTA scratch, slot_bytes each
+  long long slot_bytes;
+  double* energy;          // [ntasks][4]: W[r][s] / |M|
+  int* iters;              // [ntasks][2]
+  int* status;             // [ntasks][2]: 0 converged, 1 max_iter, 2 stopped by the FP32 guard, -2 breakdown
+  double* resid;           // [ntasks][2]: final recursive residual norm
+  double tol2;
+  int max_iter;
+  int cap;                 // shared-memory chunk capacity (complex FP64 elements)
+  int M0max, M1max;
+};
+
+// bytes of one batch scratch slot for a task (same formula on host and device)
+__host__ __device__ inline long long batch_slot_bytes(const BTask& t, int elem) {
+  auto al = [](long long b) { return (b + 255) & ~255LL; };
+  const long long fld = (long long)t.N1 * t.Nh;
+  const int Mmax = t.M0 > t.M1 ? t.M0 : t.M1;
+  long long work = (long long)t.ncomp * t.M1 * t.Nxs;
+  if (4LL * t.M1 * t.Nh > work) work = 4LL * t.M1 * t.Nh;
+  long long b = 0;
+  b += al((long long)t.ncomp * t.M1 * t.M0 * 8);          // coef64
+  b += al((long long)t.ncomp * t.M1 * t.M0 * (elem / 2)); // coefT
+  b += al((long long)(t.nincl > 0 ? t.nincl : 1) * 3 * Mmax * 16);  // phase
+  b += al((long long)(t.nincl > 0 ? t.nincl : 1) * 3 * Mmax * 8);   // sinc
+  b += al(work * 16);                                      // work area (FP64 complex)
+  b += 4 * al(4 * fld * elem);                             // x r p q
+  b += al(4 * fld * 16);                                   // x64
+  return b;
+}
+
+// dynamic shared memory of the batch kernel for working precision of `elem` bytes per complex
+inline size_t batch_smem_bytes(int M0max, int M1max, int cap, int elem) {
+  const size_t tw = ((size_t)(M0max + M1max) * (16 + elem) + 15) & ~(size_t)15;
+  return tw + 2 * (size_t)cap * 16;
+}
+template <typename T> cudaError_t launch_batch(const BArgs& a, int nblocks, size_t smem, cudaStream_t s);
+template <typename T> int batch_blocks_per_sm(size_t smem);
+
 // launchers (return cudaGetLastError())
 template <typename T> cudaError_t launch_pencil(const PencilArgs& a, cudaStream_t s);
 template <typename T> cudaError_t launch_final(const FinalArgs& a, cudaStream_t s);
