@@ -336,6 +336,7 @@ def run_gpu(args):
 
     # one operator application (3 fields) per precision, through hom_matvec
     mv = matvec_timings(hb, solver, problem, dev, stream)
+    batched = None if args.no_batched else batched_timings(hb, solver, dev)
 
     # roofline of the dominant kernel family
     nrhs = problem.d
@@ -370,6 +371,7 @@ def run_gpu(args):
                           "speedup_vs_this": ms_step / alt_ms if alt_ms > 0 else None,
                           "upper_11": float(oo["upper"][0, 0]), "lower_11": float(oo["lower"][0, 0])},
         "matvec": mv,
+        "batched": batched,
         "kernel_families_ms_one_step": {k: v[1] for k, v in fam_ms.items()},
         "roofline": roof,
         "clocks": clk.summary(),
@@ -385,6 +387,45 @@ def run_gpu(args):
         import torch.distributed as dist
         dist.destroy_process_group()
     return 0
+
+
+def batched_timings(hb, solver, dev, n=256, reps=3, n_seq=8):
+    """The batched workload: n seeded random-rectangle 2D cells (N from {23, 63, 113, 203}),
+    FP32 inner CG / FP64 bounds, tol 1e-4, one persistent launch replayed as a CUDA graph
+    after an autotuning pass; against plain FP64 hom_bounds one cell at a time on the same
+    GPU (a sample of n_seq cells, extrapolated to n)."""
+    import statistics as st_
+    import torch
+    import microstructures as ms
+    probs = [ms.random_rectangles_2d(s) for s in range(n)]
+    stream = torch.cuda.Stream(device=dev)
+    out = solver.batched(probs, precision=hb.HOM_MIXED, tol=TOL, autotune=1, graph=1, stream=stream.cuda_stream)
+    times = []
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
+    for _ in range(reps):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+        out = solver.batched(probs, precision=hb.HOM_MIXED, tol=TOL, graph=1, stream=stream.cuda_stream)
+        with torch.cuda.stream(stream):
+            e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+    ms_batch = st_.mean(times)
+    seq = []
+    for p in probs[:n_seq]:
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        solver(p, precision=hb.HOM_FP64, tol=TOL)
+        seq.append((time.perf_counter() - t) * 1e3)
+    seq_ms = st_.mean(seq) * n
+    return {"workload": f"{n} random-rectangle 2D cells, N from {{23,63,113,203}}, FP32 inner CG, FP64 bounds, tol {TOL:g}",
+            "ms": ms_batch, "problems_per_s": n / (ms_batch * 1e-3), "launches": out["report"]["launches"],
+            "max_iters": int(out["iters"].max()), "status_nonzero": int((out["status"] != 0).sum()),
+            "sequential_fp64_ms_est": seq_ms, "speedup_vs_sequential_fp64": seq_ms / ms_batch,
+            "sequential_note": f"plain FP64 hom_bounds per cell, mean of the first {n_seq} cells x {n}"}
 
 
 def matvec_bytes(problem, elem_bytes: int) -> float:
@@ -452,6 +493,7 @@ def main():
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
     ap.add_argument("--ref-matvecs", type=int, default=20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--workload", default="cube3d_N41", choices=sorted(WORKLOADS))
     ap.add_argument("--matvec-only", action="store_true", help="operator applications only")
     ap.add_argument("--reps", type=int, default=20)

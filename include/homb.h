@@ -94,7 +94,8 @@ typedef struct {
 
 typedef struct {
   int32_t precision;    /* hom_precision: HOM_FP64 or HOM_MIXED                  */
-  int32_t max_iter;     /* per solve; <= 0 selects 10000                         */
+  int32_t max_iter;     /* per solve; <= 0 selects 10000 (hom_bounds_batched with
+                           starting fields takes 0 literally: no CG iteration)   */
   double tol;           /* stop when ||r_i|| <= tol ||E|| (Remark "Convergence
                            criteria", Parseval L2 norm); <= 0 selects 1e-8       */
   int32_t check_every;  /* host polls convergence every k iterations; 0 -> 8     */
@@ -160,12 +161,69 @@ hom_status hom_bounds(hom_ctx* ctx, const hom_problem* prob, const hom_opts* opt
  * row-major, status [n] (worst of the four solves: 0 ok, 1 max_iter/FP32 floor, -2
  * breakdown), iters [n][2][2] (side, rhs; may be NULL), rep aggregated (may be NULL).
  * Returns HOM_WARN_NOT_CONVERGED when any status is not 0. Synchronises `stream`. */
+/* Optional device pools of hom_bounds_batched for batches whose cells share one grid N:
+ * d_x0 (starting fields) and d_fields (final CG fields), both [n][side][rhs][comp][N][Nh]
+ * half spectra in the inner precision (float2 for HOM_MIXED, double2 for HOM_FP64). A
+ * starting field is projected with Gamma^E / Gamma^J before use, so any input gives
+ * guaranteed bounds (Lemma bounds); CG then runs from it (Remark after Eq.
+ * linear_system_dual: iterates stay in E_N / J_N). */
+typedef struct {
+  const void* d_x0;
+  void* d_fields;
+} hom_batch_io;
+
 hom_status hom_batched_workspace_size(hom_ctx* ctx, int32_t n, const hom_problem* probs,
                                       const hom_opts* opts, size_t* bytes);
 hom_status hom_bounds_batched(hom_ctx* ctx, int32_t n, const hom_problem* probs,
                               const hom_opts* opts, void* d_workspace, size_t workspace_bytes,
                               void* stream, double* upper, double* lower, int32_t* status,
-                              int32_t* iters, hom_report* rep);
+                              int32_t* iters, hom_report* rep, const hom_batch_io* io);
+
+/* ---- learned warm start: a 2D Fourier-layer network (no counterpart in the paper's
+ * algorithm; the paper's guarantee makes any starting field admissible after projection).
+ * Layers: lift (cin -> width), `layers` spectral layers keeping kx in [0, modes) and
+ * ky in [-modes, modes) with per-mode complex channel mixing plus a 1x1 path and GELU,
+ * projection width -> proj (GELU) -> cout. Every product is a BF16 tensor-core GEMM with
+ * FP32 accumulation; parameters are FP32 (a flat array, layout fixed by the config).
+ * Activations are channels-last [batch][N][N][ch] FP32. */
+typedef struct {
+  int32_t N, cin, width, modes, layers, proj, cout;
+} hom_net_config;
+
+/* number of parameters and workspace bytes for `batch` samples */
+hom_status hom_net_sizes(hom_ctx* ctx, const hom_net_config* cfg, int32_t batch, int64_t* n_params,
+                         size_t* workspace_bytes);
+hom_status hom_net_init(hom_ctx* ctx, const hom_net_config* cfg, uint64_t seed, float* d_params,
+                        void* stream);
+hom_status hom_net_forward(hom_ctx* ctx, const hom_net_config* cfg, const float* d_params,
+                           int32_t batch, const float* d_in, float* d_out, void* d_workspace,
+                           size_t workspace_bytes, void* stream);
+/* mean squared error against d_target and its gradient w.r.t. the parameters (d_grad
+ * overwritten); *loss (host) receives the loss; synchronises `stream`. */
+hom_status hom_net_gradient(hom_ctx* ctx, const hom_net_config* cfg, const float* d_params,
+                            int32_t batch, const float* d_in, const float* d_target, float* d_grad,
+                            float* loss, void* d_workspace, size_t workspace_bytes, void* stream);
+/* one Adam step (beta1 0.9, beta2 0.999, eps 1e-8, bias-corrected with `step` >= 1) on the
+ * gradient of one batch; loss written to *d_loss (device float, may be NULL); enqueue only. */
+hom_status hom_net_train_step(hom_ctx* ctx, const hom_net_config* cfg, float* d_params, float* d_m,
+                              float* d_v, float* d_grad, int32_t step, float lr, int32_t batch,
+                              const float* d_in, const float* d_target, float* d_loss,
+                              void* d_workspace, size_t workspace_bytes, void* stream);
+/* input features of n cells on their N grid: log10 of the mean diagonal phase value at
+ * the grid points x_j = Y j / N, [n][N][N][1]; enqueue only (tables copied from host). */
+hom_status hom_net_features(hom_ctx* ctx, int32_t n, const hom_problem* probs, float* d_features,
+                            void* d_workspace, size_t workspace_bytes, void* stream);
+/* real N-grid fields [B][N][N][ch] <-> half spectra [B][ch][N][(N+1)/2] with the 1/N^2 of
+ * Eq. DFT on the forward side; precision HOM_FP64 (double2) or HOM_FP32 (float2). */
+hom_status hom_grid_to_half(hom_ctx* ctx, int32_t N, int32_t batch, int32_t ch, const float* d_grid,
+                            void* d_half, int32_t precision, void* stream);
+hom_status hom_half_to_grid(hom_ctx* ctx, int32_t N, int32_t batch, int32_t ch, const void* d_half,
+                            float* d_grid, int32_t precision, void* stream);
+/* the tensor-core GEMM: C = alpha op(A) op(B) + beta C (row-major FP32 in memory, BF16
+ * products, FP32 accumulation); enqueue only. */
+hom_status hom_gemm_bf16(hom_ctx* ctx, int32_t M, int32_t N, int32_t K, const float* d_A, int32_t lda,
+                         int32_t transA, const float* d_B, int32_t ldb, int32_t transB, float* d_C,
+                         int32_t ldc, float alpha, float beta, void* stream);
 
 /* Step-level entry points (device buffers; enqueue only). Workspace for these is
  * hom_step_workspace_size. */

@@ -51,13 +51,16 @@ class Bounds:
         return hom_bounds(self.ctx, problem, opts, ws.data_ptr(), ws.numel(), s)
 
     def batched(self, problems, precision=HOM_MIXED, tol=1e-4, max_iter=10000, graph=0, autotune=0,
-                stream=None):
-        """hom_bounds_batched on a list of 2D problems (one persistent launch)."""
+                stream=None, x0=None, fields=None):
+        """hom_bounds_batched on a list of 2D problems (one persistent launch). x0 / fields:
+        optional device tensors [n, 2, 2, 2, N, (N+1)//2] complex (starting / final fields)."""
         opts = make_opts(precision, tol, max_iter, 8, 3, graph, autotune)
         nbytes = hom_batched_workspace_size(self.ctx, problems, opts)
         ws = self.workspace(nbytes)
         s = stream if stream is not None else self.torch.cuda.current_stream(self.device).cuda_stream
-        return hom_bounds_batched(self.ctx, problems, opts, ws.data_ptr(), ws.numel(), s)
+        return hom_bounds_batched(self.ctx, problems, opts, ws.data_ptr(), ws.numel(), s,
+                                  None if x0 is None else x0.data_ptr(),
+                                  None if fields is None else fields.data_ptr())
 
     def close(self):
         if self.ctx is not None:

@@ -50,6 +50,15 @@ class hom_report(C.Structure):
                 ("h2d_bytes", C.c_int64), ("d2h_bytes", C.c_int64)]
 
 
+class hom_batch_io(C.Structure):
+    _fields_ = [("d_x0", C.c_void_p), ("d_fields", C.c_void_p)]
+
+
+class hom_net_config(C.Structure):
+    _fields_ = [("N", C.c_int32), ("cin", C.c_int32), ("width", C.c_int32), ("modes", C.c_int32),
+                ("layers", C.c_int32), ("proj", C.c_int32), ("cout", C.c_int32)]
+
+
 class HombError(RuntimeError):
     def __init__(self, status, msg):
         super().__init__(f"homb status {status}: {msg}")
@@ -73,7 +82,17 @@ def _load():
         "hom_step_workspace_size": (i32, [vp, P(hom_problem), i32, P(sz)]),
         "hom_batched_workspace_size": (i32, [vp, i32, P(hom_problem), P(hom_opts), P(sz)]),
         "hom_bounds_batched": (i32, [vp, i32, P(hom_problem), P(hom_opts), vp, sz, vp, dp, dp, P(i32), P(i32),
-                                     P(hom_report)]),
+                                     P(hom_report), P(hom_batch_io)]),
+        "hom_net_sizes": (i32, [vp, P(hom_net_config), i32, P(i64), P(sz)]),
+        "hom_net_init": (i32, [vp, P(hom_net_config), C.c_uint64, vp, vp]),
+        "hom_net_forward": (i32, [vp, P(hom_net_config), vp, i32, vp, vp, vp, sz, vp]),
+        "hom_net_gradient": (i32, [vp, P(hom_net_config), vp, i32, vp, vp, vp, P(C.c_float), vp, sz, vp]),
+        "hom_net_train_step": (i32, [vp, P(hom_net_config), vp, vp, vp, vp, i32, C.c_float, i32, vp, vp, vp, vp,
+                                     sz, vp]),
+        "hom_net_features": (i32, [vp, i32, P(hom_problem), vp, vp, sz, vp]),
+        "hom_grid_to_half": (i32, [vp, i32, i32, i32, vp, vp, i32, vp]),
+        "hom_half_to_grid": (i32, [vp, i32, i32, i32, vp, vp, i32, vp]),
+        "hom_gemm_bf16": (i32, [vp, i32, i32, i32, vp, i32, i32, vp, i32, i32, vp, i32, C.c_float, C.c_float, vp]),
         "hom_coefficient": (i32, [vp, P(hom_problem), i32, i32, vp, vp, sz, vp]),
         "hom_rhs": (i32, [vp, P(hom_problem), i32, i32, i32, vp, vp, sz, vp]),
         "hom_matvec": (i32, [vp, P(hom_problem), i32, i32, i32, i32, vp, vp, vp, vp, sz, vp]),
@@ -201,7 +220,7 @@ def hom_batched_workspace_size(ctx, problems, opts):
     return n.value
 
 
-def hom_bounds_batched(ctx, problems, opts, d_ws, ws_bytes, stream=0):
+def hom_bounds_batched(ctx, problems, opts, d_ws, ws_bytes, stream=0, d_x0=None, d_fields=None):
     """Returns dict(upper [n,2,2], lower [n,2,2], status [n], iters [n,2,2], report, code)."""
     arr, keep = problems_array(problems)
     n = len(problems)
@@ -210,8 +229,11 @@ def hom_bounds_batched(ctx, problems, opts, d_ws, ws_bytes, stream=0):
     stt = (C.c_int32 * n)()
     its = (C.c_int32 * (4 * n))()
     rep = hom_report()
+    io = None
+    if d_x0 is not None or d_fields is not None:
+        io = hom_batch_io(C.c_void_p(d_x0 or 0), C.c_void_p(d_fields or 0))
     code = lib.hom_bounds_batched(ctx, n, arr, C.byref(opts), C.c_void_p(d_ws), ws_bytes, C.c_void_p(stream),
-                                  up, lo, stt, its, C.byref(rep))
+                                  up, lo, stt, its, C.byref(rep), C.byref(io) if io is not None else None)
     check(ctx, code)
     return {"upper": np.array(up[:]).reshape(n, 2, 2), "lower": np.array(lo[:]).reshape(n, 2, 2),
             "status": np.array(stt[:]), "iters": np.array(its[:]).reshape(n, 2, 2), "code": code,
@@ -306,3 +328,63 @@ def hom_kernel_timing(ctx):
     ms = C.c_double()
     check(ctx, lib.hom_kernel_timing(ctx, C.byref(n), C.byref(ms)))
     return n.value, ms.value
+
+
+# ------------------------------------------------------------------------------------
+# learned warm start
+# ------------------------------------------------------------------------------------
+def net_config(N, cin=1, width=32, modes=12, layers=4, proj=128, cout=8):
+    return hom_net_config(N, cin, width, modes, layers, proj, cout)
+
+
+def hom_net_sizes(ctx, cfg, batch):
+    n = C.c_int64()
+    b = C.c_size_t()
+    check(ctx, lib.hom_net_sizes(ctx, C.byref(cfg), batch, C.byref(n), C.byref(b)))
+    return n.value, b.value
+
+
+def hom_net_init(ctx, cfg, seed, d_params, stream=0):
+    return check(ctx, lib.hom_net_init(ctx, C.byref(cfg), seed, C.c_void_p(d_params), C.c_void_p(stream)))
+
+
+def hom_net_forward(ctx, cfg, d_params, batch, d_in, d_out, d_ws, ws_bytes, stream=0):
+    return check(ctx, lib.hom_net_forward(ctx, C.byref(cfg), C.c_void_p(d_params), batch, C.c_void_p(d_in),
+                                          C.c_void_p(d_out), C.c_void_p(d_ws), ws_bytes, C.c_void_p(stream)))
+
+
+def hom_net_gradient(ctx, cfg, d_params, batch, d_in, d_target, d_grad, d_ws, ws_bytes, stream=0):
+    loss = C.c_float()
+    check(ctx, lib.hom_net_gradient(ctx, C.byref(cfg), C.c_void_p(d_params), batch, C.c_void_p(d_in),
+                                    C.c_void_p(d_target), C.c_void_p(d_grad), C.byref(loss), C.c_void_p(d_ws),
+                                    ws_bytes, C.c_void_p(stream)))
+    return loss.value
+
+
+def hom_net_train_step(ctx, cfg, d_params, d_m, d_v, d_grad, step, lr, batch, d_in, d_target, d_loss, d_ws,
+                       ws_bytes, stream=0):
+    return check(ctx, lib.hom_net_train_step(ctx, C.byref(cfg), C.c_void_p(d_params), C.c_void_p(d_m),
+                                             C.c_void_p(d_v), C.c_void_p(d_grad), step, lr, batch,
+                                             C.c_void_p(d_in), C.c_void_p(d_target), C.c_void_p(d_loss),
+                                             C.c_void_p(d_ws), ws_bytes, C.c_void_p(stream)))
+
+
+def hom_net_features(ctx, problems, d_features, d_ws, ws_bytes, stream=0):
+    arr, keep = problems_array(problems)
+    return check(ctx, lib.hom_net_features(ctx, len(problems), arr, C.c_void_p(d_features), C.c_void_p(d_ws),
+                                           ws_bytes, C.c_void_p(stream)))
+
+
+def hom_grid_to_half(ctx, N, batch, ch, d_grid, d_half, precision, stream=0):
+    return check(ctx, lib.hom_grid_to_half(ctx, N, batch, ch, C.c_void_p(d_grid), C.c_void_p(d_half), precision,
+                                           C.c_void_p(stream)))
+
+
+def hom_half_to_grid(ctx, N, batch, ch, d_half, d_grid, precision, stream=0):
+    return check(ctx, lib.hom_half_to_grid(ctx, N, batch, ch, C.c_void_p(d_half), C.c_void_p(d_grid), precision,
+                                           C.c_void_p(stream)))
+
+
+def hom_gemm_bf16(ctx, M, N, K, d_A, lda, ta, d_B, ldb, tb, d_C, ldc, alpha=1.0, beta=0.0, stream=0):
+    return check(ctx, lib.hom_gemm_bf16(ctx, M, N, K, C.c_void_p(d_A), lda, ta, C.c_void_p(d_B), ldb, tb,
+                                        C.c_void_p(d_C), ldc, alpha, beta, C.c_void_p(stream)))

@@ -22,6 +22,7 @@
 
 #include "../../include/homb.h"
 #include "kernels.cuh"
+#include "net.cuh"
 
 using namespace homb;
 
@@ -1080,7 +1081,7 @@ hom_status hom_batched_workspace_size(hom_ctx* ctx, int32_t n, const hom_problem
 
 hom_status hom_bounds_batched(hom_ctx* ctx, int32_t n, const hom_problem* probs, const hom_opts* opts, void* d_ws,
                               size_t ws_bytes, void* stream, double* upper, double* lower, int32_t* status,
-                              int32_t* iters, hom_report* rep) {
+                              int32_t* iters, hom_report* rep, const hom_batch_io* io) {
   if (!ctx || !opts) return fail(ctx, HOM_ERR_INVALID_ARG, "NULL argument");
   const auto t0 = std::chrono::steady_clock::now();
   ctx->err.clear();
@@ -1096,6 +1097,11 @@ hom_status hom_bounds_batched(hom_ctx* ctx, int32_t n, const hom_problem* probs,
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const bool f32 = opts->precision == HOM_MIXED;
   const int nt = (int)bp.tasks.size();
+  const bool has_io = io && (io->d_x0 || io->d_fields);
+  if (has_io)
+    for (const BTask& t : bp.tasks)
+      if (t.N0 != bp.tasks[0].N0 || t.N1 != bp.tasks[0].N1)
+        return fail(ctx, HOM_ERR_INVALID_ARG, "starting/final field pools need one grid N for the whole batch");
   // stage the tables in pinned memory (a captured graph reads them at replay)
   CKS(ensure_pinned(ctx, &ctx->pin_in, &ctx->pin_in_bytes, bp.in_bytes));
   CKS(ensure_pinned(ctx, &ctx->pin_out, &ctx->pin_out_bytes, bp.out_bytes));
@@ -1127,6 +1133,8 @@ hom_status hom_bounds_batched(hom_ctx* ctx, int32_t n, const hom_problem* probs,
     a.cap = cap;
     a.M0max = bp.M0max;
     a.M1max = bp.M1max;
+    a.x0 = io ? io->d_x0 : nullptr;
+    a.fields = io ? io->d_fields : nullptr;
     return a;
   };
   auto grid_for = [&](int cap, size_t* smem) {
@@ -1173,11 +1181,14 @@ hom_status hom_bounds_batched(hom_ctx* ctx, int32_t n, const hom_problem* probs,
     cap = best_cap;
     ctx->tuned_cap.push_back({tkey, cap});
   }
-  const int max_iter = opts->max_iter > 0 ? opts->max_iter : 10000;
+  // with starting fields, max_iter = 0 is taken literally: bounds of the projected starts
+  const int max_iter = opts->max_iter > 0 ? opts->max_iter : ((opts->max_iter == 0 && io && io->d_x0) ? 0 : 10000);
   if (opts->graph && st != nullptr) {
     size_t smem = 0;
     const int grid = grid_for(cap, &smem);
-    const std::vector<long long> key = {(long long)(uintptr_t)d_ws, (long long)bp.total, nt, grid, (long long)smem, cap,
+    const std::vector<long long> key = {(long long)(uintptr_t)d_ws, (long long)(uintptr_t)(io ? io->d_x0 : nullptr),
+                                        (long long)(uintptr_t)(io ? io->d_fields : nullptr),
+                                        (long long)bp.total, nt, grid, (long long)smem, cap,
                                         (long long)f32, max_iter, (long long)(tol * 1e18), (long long)ctx->pin_in_bytes,
                                         (long long)ctx->pin_out_bytes, bp.M0max, bp.M1max, bp.slot_bytes};
     if (!ctx->graph_exec || ctx->graph_key != key) {
@@ -1448,6 +1459,223 @@ hom_status hom_kernel_timing(hom_ctx* ctx, int64_t* launches, double* total_ms) 
   if (launches) *launches = (int64_t)(ctx->ev_used / 2);
   if (total_ms) *total_ms = tot;
   ctx->ev_used = 0;
+  return HOM_OK;
+}
+
+
+// ---- learned warm start ------------------------------------------------------------
+static hom_status net_cfg(hom_ctx* ctx, const hom_net_config* c, NetConfig* out) {
+  if (!c) return fail(ctx, HOM_ERR_INVALID_ARG, "NULL config");
+  if (c->N < 3 || c->N % 2 == 0 || c->N > 255 || c->cin < 1 || c->width < 1 || c->width > 256 || c->modes < 1 ||
+      2 * c->modes > c->N || c->layers < 1 || c->layers > 8 || c->proj < 1 || c->cout < 1)
+    return fail(ctx, HOM_ERR_INVALID_ARG, "invalid network configuration");
+  *out = NetConfig{c->N, c->cin, c->width, c->modes, c->layers, c->proj, c->cout};
+  return HOM_OK;
+}
+
+static size_t net_ws_bytes(const NetConfig& c, int batch) {
+  return (size_t)(bases_floats(c) + 256 + net_workspace_floats(c, batch)) * sizeof(float) + 1024;
+}
+
+// bases at the front of the workspace (256-float aligned), the rest for activations
+static hom_status net_prepare(hom_ctx* ctx, const NetConfig& c, int batch, void* d_ws, size_t ws_bytes,
+                              cudaStream_t st, float** bases, float** rest) {
+  if (!d_ws || ws_bytes < net_ws_bytes(c, batch)) return fail(ctx, HOM_ERR_WORKSPACE, "workspace too small");
+  std::vector<float> hb((size_t)bases_floats(c));
+  fill_bases(c, hb.data());
+  float* b = static_cast<float*>(d_ws);
+  CK(h2d_copy(ctx, b, hb.data(), hb.size() * sizeof(float), st));
+  *bases = b;
+  *rest = b + ((bases_floats(c) + 255) / 256) * 256;
+  return HOM_OK;
+}
+
+hom_status hom_net_sizes(hom_ctx* ctx, const hom_net_config* cfg, int32_t batch, int64_t* n_params,
+                         size_t* workspace_bytes) {
+  NetConfig c;
+  CKS(net_cfg(ctx, cfg, &c));
+  if (batch < 1) return fail(ctx, HOM_ERR_INVALID_ARG, "batch < 1");
+  if (n_params) *n_params = net_offsets(c).total;
+  if (workspace_bytes) *workspace_bytes = net_ws_bytes(c, batch);
+  return HOM_OK;
+}
+
+hom_status hom_net_init(hom_ctx* ctx, const hom_net_config* cfg, uint64_t seed, float* d_params, void* stream) {
+  NetConfig c;
+  CKS(net_cfg(ctx, cfg, &c));
+  CKS(set_device(ctx));
+  KL(init_params(c, d_params, seed, static_cast<cudaStream_t>(stream)));
+  return HOM_OK;
+}
+
+hom_status hom_net_forward(hom_ctx* ctx, const hom_net_config* cfg, const float* d_params, int32_t batch,
+                           const float* d_in, float* d_out, void* d_ws, size_t ws_bytes, void* stream) {
+  NetConfig c;
+  CKS(net_cfg(ctx, cfg, &c));
+  if (!d_params || !d_in || !d_out || batch < 1) return fail(ctx, HOM_ERR_INVALID_ARG, "bad argument");
+  CKS(set_device(ctx));
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  float *bases, *rest;
+  CKS(net_prepare(ctx, c, batch, d_ws, ws_bytes, st, &bases, &rest));
+  KL(net_forward(c, d_params, bases, batch, d_in, d_out, rest, 0, st));
+  return HOM_OK;
+}
+
+hom_status hom_net_gradient(hom_ctx* ctx, const hom_net_config* cfg, const float* d_params, int32_t batch,
+                            const float* d_in, const float* d_target, float* d_grad, float* loss, void* d_ws,
+                            size_t ws_bytes, void* stream) {
+  NetConfig c;
+  CKS(net_cfg(ctx, cfg, &c));
+  if (!d_params || !d_in || !d_target || !d_grad || batch < 1) return fail(ctx, HOM_ERR_INVALID_ARG, "bad argument");
+  CKS(set_device(ctx));
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  float *bases, *rest;
+  CKS(net_prepare(ctx, c, batch, d_ws, ws_bytes, st, &bases, &rest));
+  // the loss scalar lives in the last float of the workspace
+  float* dloss = reinterpret_cast<float*>(static_cast<unsigned char*>(d_ws) + ws_bytes) - 1;
+  KL(net_backward(c, d_params, bases, batch, d_in, d_target, d_grad, dloss, rest, st));
+  float h = 0.f;
+  CK(d2h_copy(ctx, &h, dloss, sizeof(float), st));
+  CK(cudaStreamSynchronize(st));
+  if (loss) *loss = h;
+  return HOM_OK;
+}
+
+hom_status hom_net_train_step(hom_ctx* ctx, const hom_net_config* cfg, float* d_params, float* d_m, float* d_v,
+                              float* d_grad, int32_t step, float lr, int32_t batch, const float* d_in,
+                              const float* d_target, float* d_loss, void* d_ws, size_t ws_bytes, void* stream) {
+  NetConfig c;
+  CKS(net_cfg(ctx, cfg, &c));
+  if (!d_params || !d_m || !d_v || !d_grad || !d_in || !d_target || batch < 1 || step < 1)
+    return fail(ctx, HOM_ERR_INVALID_ARG, "bad argument");
+  CKS(set_device(ctx));
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  float *bases, *rest;
+  CKS(net_prepare(ctx, c, batch, d_ws, ws_bytes, st, &bases, &rest));
+  float* dloss = d_loss ? d_loss : reinterpret_cast<float*>(static_cast<unsigned char*>(d_ws) + ws_bytes) - 1;
+  KL(net_backward(c, d_params, bases, batch, d_in, d_target, d_grad, dloss, rest, st));
+  KL(adam_step(d_params, d_grad, d_m, d_v, net_offsets(c).total, lr, 0.9f, 0.999f, 1e-8f, step, st));
+  return HOM_OK;
+}
+
+namespace {
+struct FeatIncl {
+  int shape;
+  float c[2], h[2], value;
+};
+__global__ void k_features(int n, int N, const int* offs, const FeatIncl* incl, const float* base_val,
+                           const float* Y, float* out) {
+  const long long total = (long long)n * N * N;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int p = (int)(t / ((long long)N * N));
+    const int j = (int)(t - (long long)p * N * N);
+    const int jy = j / N, jx = j - jy * N;
+    const float Yx = Y[2 * p], Yy = Y[2 * p + 1];
+    const float x = Yx * jx / N, y = Yy * jy / N;
+    float v = base_val[p];
+    for (int k = offs[p]; k < offs[p + 1]; ++k) {
+      const FeatIncl& I = incl[k];
+      float dx = x - I.c[0], dy = y - I.c[1];
+      dx -= Yx * rintf(dx / Yx);
+      dy -= Yy * rintf(dy / Yy);
+      const bool in = I.shape == 0 ? (fabsf(dx) < 0.5f * I.h[0] && fabsf(dy) < 0.5f * I.h[1])
+                                   : (dx * dx + dy * dy < I.h[0] * I.h[0]);
+      if (in) v = I.value;
+    }
+    out[t] = v;
+  }
+}
+}  // namespace
+
+hom_status hom_net_features(hom_ctx* ctx, int32_t n, const hom_problem* probs, float* d_features, void* d_ws,
+                            size_t ws_bytes, void* stream) {
+  if (!ctx || n < 1 || !probs || !d_features) return fail(ctx, HOM_ERR_INVALID_ARG, "bad argument");
+  CKS(set_device(ctx));
+  std::vector<int> offs(n + 1, 0);
+  std::vector<FeatIncl> inc;
+  std::vector<float> basev(n), Y(2 * n);
+  int N = -1;
+  for (int i = 0; i < n; ++i) {
+    Geometry g;
+    CKS(build_geometry(ctx, &probs[i], g));
+    if (g.d != 2) return fail(ctx, HOM_ERR_INVALID_ARG, "features are two-dimensional");
+    if (g.N[0] != g.N[1] || (N >= 0 && g.N[0] != N)) return fail(ctx, HOM_ERR_INVALID_ARG, "features need one square grid");
+    N = g.N[0];
+    basev[i] = (float)std::log10(0.5 * (g.A0[0][0] + g.A0[1][1]));
+    Y[2 * i] = (float)g.Y[0];
+    Y[2 * i + 1] = (float)g.Y[1];
+    for (const hom_inclusion& I : g.incl) {
+      FeatIncl f;
+      f.shape = I.shape == HOM_BOX ? 0 : 1;
+      f.c[0] = (float)I.center[0];
+      f.c[1] = (float)I.center[1];
+      f.h[0] = (float)I.size[0];
+      f.h[1] = (float)I.size[1];
+      f.value = (float)std::log10(0.5 * (I.A[0] + I.A[4]));
+      inc.push_back(f);
+    }
+    offs[i + 1] = (int)inc.size();
+  }
+  if (inc.empty()) inc.resize(1);
+  const size_t need = 256 + offs.size() * 4 + 256 + inc.size() * sizeof(FeatIncl) + 256 + basev.size() * 4 + 256 +
+                      Y.size() * 4 + 256;
+  if (!d_ws || ws_bytes < need) return fail(ctx, HOM_ERR_WORKSPACE, "workspace too small");
+  unsigned char* b = static_cast<unsigned char*>(d_ws);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  size_t off = 0;
+  auto put = [&](const void* src, size_t bytes) {
+    void* dst = b + off;
+    off = (off + bytes + 255) & ~(size_t)255;
+    return std::make_pair(dst, bytes);
+  };
+  auto p_offs = put(offs.data(), offs.size() * 4);
+  auto p_inc = put(inc.data(), inc.size() * sizeof(FeatIncl));
+  auto p_base = put(basev.data(), basev.size() * 4);
+  auto p_Y = put(Y.data(), Y.size() * 4);
+  CK(h2d_copy(ctx, p_offs.first, offs.data(), p_offs.second, st));
+  CK(h2d_copy(ctx, p_inc.first, inc.data(), p_inc.second, st));
+  CK(h2d_copy(ctx, p_base.first, basev.data(), p_base.second, st));
+  CK(h2d_copy(ctx, p_Y.first, Y.data(), p_Y.second, st));
+  const long long total = (long long)n * N * N;
+  const int blocks = (int)std::min<long long>((total + 255) / 256, 152 * 16);
+  k_features<<<blocks, 256, 0, st>>>(n, N, static_cast<const int*>(p_offs.first), static_cast<const FeatIncl*>(p_inc.first),
+                                     static_cast<const float*>(p_base.first), static_cast<const float*>(p_Y.first),
+                                     d_features);
+  CK(cudaGetLastError());
+  ++ctx->launches;
+  // the host vectors must outlive the pageable copies: they are staged before return
+  CK(cudaStreamSynchronize(st));
+  return HOM_OK;
+}
+
+hom_status hom_grid_to_half(hom_ctx* ctx, int32_t N, int32_t batch, int32_t ch, const float* d_grid, void* d_half,
+                            int32_t precision, void* stream) {
+  if (!ctx || N < 1 || N % 2 == 0 || N > 511 || batch < 1 || ch < 1 || !d_grid || !d_half)
+    return fail(ctx, HOM_ERR_INVALID_ARG, "bad argument");
+  CKS(set_device(ctx));
+  KL(grid_to_half(N, batch, ch, d_grid, d_half, precision == HOM_FP64 ? 1 : 0, static_cast<cudaStream_t>(stream)));
+  return HOM_OK;
+}
+
+hom_status hom_half_to_grid(hom_ctx* ctx, int32_t N, int32_t batch, int32_t ch, const void* d_half, float* d_grid,
+                            int32_t precision, void* stream) {
+  if (!ctx || N < 1 || N % 2 == 0 || N > 511 || batch < 1 || ch < 1 || !d_grid || !d_half)
+    return fail(ctx, HOM_ERR_INVALID_ARG, "bad argument");
+  CKS(set_device(ctx));
+  KL(half_to_grid(N, batch, ch, d_half, d_grid, precision == HOM_FP64 ? 1 : 0, static_cast<cudaStream_t>(stream)));
+  return HOM_OK;
+}
+
+hom_status hom_gemm_bf16(hom_ctx* ctx, int32_t M, int32_t N, int32_t K, const float* d_A, int32_t lda,
+                         int32_t transA, const float* d_B, int32_t ldb, int32_t transB, float* d_C, int32_t ldc,
+                         float alpha, float beta, void* stream) {
+  if (!ctx || M < 0 || N < 0 || K < 0 || !d_A || !d_B || !d_C) return fail(ctx, HOM_ERR_INVALID_ARG, "bad argument");
+  CKS(set_device(ctx));
+  GemmArgs g;
+  g.A = d_A; g.B = d_B; g.C = d_C; g.M = M; g.N = N; g.K = K; g.lda = lda; g.ldb = ldb; g.ldc = ldc;
+  g.ta = transA; g.tb = transB; g.sA = g.sB = g.sC = 0; g.batch = 1; g.alpha = alpha; g.beta = beta;
+  KL(gemm_bf16(g, static_cast<cudaStream_t>(stream)));
   return HOM_OK;
 }
 

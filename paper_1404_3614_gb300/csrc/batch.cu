@@ -481,6 +481,57 @@ __global__ void __launch_bounds__(kBatchThreads, 2) k_batch(BArgs a) {
         acc[r] += w * ((double)b0.x * b0.x + (double)b0.y * b0.y + (double)b1.x * b1.x + (double)b1.y * b1.y);
       }
     }
+    const double scale = 1.0 / ((double)M0 * M1);
+    const long long io_off = ((long long)t.prob * 2 + t.side) * 4 * fld;   // start of this task's block
+    if (a.x0) {
+      // warm start: x = Gamma x0, r = b - C x (one operator application), p = 0
+      __syncthreads();
+      const cpx<T>* x0 = reinterpret_cast<const cpx<T>*>(a.x0) + io_off;
+      for (long long e = threadIdx.x; e < 2 * fld; e += blockDim.x) {
+        const int r = (int)(e / fld);
+        const long long k = e - r * fld;
+        const int kx = (int)(k % Nh);
+        const int iy = (int)(k / Nh);
+        const T xi0 = T(kx * t.invY[0]), xi1 = T(sfreq(iy, N1) * t.invY[1]);
+        const T n2 = xi0 * xi0 + xi1 * xi1;
+        const cpx<T> u0 = x0[(r * 2 + 0) * fld + k], u1 = x0[(r * 2 + 1) * fld + k];
+        cpx<T> g0 = mk<T>(T(0), T(0)), g1 = g0;
+        if (n2 > T(0)) {
+          const T dx = (xi0 * u0.x + xi1 * u1.x) / n2, dy = (xi0 * u0.y + xi1 * u1.y) / n2;
+          g0 = mk<T>(xi0 * dx, xi0 * dy);
+          g1 = mk<T>(xi1 * dx, xi1 * dy);
+          if (t.side == 1) {
+            g0 = sub<T>(u0, g0);
+            g1 = sub<T>(u1, g1);
+          }
+        }
+        vx[(r * 2 + 0) * fld + k] = g0;
+        vx[(r * 2 + 1) * fld + k] = g1;
+        vp[(r * 2 + 0) * fld + k] = g0;
+        vp[(r * 2 + 1) * fld + k] = g1;
+      }
+      if (threadIdx.x == 0) {
+        s_rlist[0] = 0; s_rlist[1] = 1; s_nrl = 2;
+        s_flist[0] = 0; s_flist[1] = 1; s_flist[2] = 2; s_flist[3] = 3; s_nfl = 4;
+      }
+      __syncthreads();
+      col_pass<T>(vp, T2, fld, t2_fs, s_flist, s_nfl, Nh, N1, M1, N1, M1, +1, t.plan1, W1, At, Bt, capT, nullptr);
+      double dummy0[4];
+      row_pass<T>(0, T2, t2_fs, M1, Nh, Nh, M0, coefT, t.ncomp, T(scale), s_rlist, s_nrl, nullptr, t.plan0, W0,
+                  At, Bt, capT, dummy0);
+      double pqd[2] = {0.0, 0.0};
+      col_final<T>(T2, vq, vp, t2_fs, fld, s_rlist, s_nrl, Nh, N1, M1, t.invY[0], t.invY[1], t.side, t.plan1, W1,
+                   At, Bt, capT, pqd);
+      acc[0] = acc[1] = 0.0;
+      for (long long i = threadIdx.x; i < 4 * fld; i += blockDim.x) {
+        const int r = (int)(i / (2 * fld));
+        const cpx<T> rv = sub<T>(vr[i], vq[i]);
+        vr[i] = rv;
+        vp[i] = mk<T>(T(0), T(0));
+        const double w = (i % Nh) == 0 ? 1.0 : 2.0;
+        acc[r] += w * ((double)rv.x * rv.x + (double)rv.y * rv.y);
+      }
+    }
     for (int r = 0; r < 2; ++r) {
       const double s = block_sum(acc[r], s_red);
       if (threadIdx.x == 0) {
@@ -497,7 +548,6 @@ __global__ void __launch_bounds__(kBatchThreads, 2) k_batch(BArgs a) {
     __syncthreads();
 
     // ---- CG on both right-hand sides
-    const double scale = 1.0 / ((double)M0 * M1);
     for (int it = 0; it < a.max_iter && (s_active[0] || s_active[1]); ++it) {
       if (threadIdx.x == 0) {
         int n = 0, m = 0;
@@ -587,6 +637,10 @@ __global__ void __launch_bounds__(kBatchThreads, 2) k_batch(BArgs a) {
         if (s_active[r]) s_status[r] = 1;   // max_iter reached
     __syncthreads();
 
+    if (a.fields) {
+      cpx<T>* fo = reinterpret_cast<cpx<T>*>(a.fields) + io_off;
+      for (long long i = threadIdx.x; i < 4 * fld; i += blockDim.x) fo[i] = vx[i];
+    }
     // ---- FP64 re-projection of the fields and the exact double-grid energies
     for (long long e = threadIdx.x; e < 2 * fld; e += blockDim.x) {
       const int r = (int)(e / fld);

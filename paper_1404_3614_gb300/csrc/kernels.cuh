@@ -122,6 +122,8 @@ struct BArgs {
   int max_iter;
   int cap;                 // shared-memory chunk capacity (complex FP64 elements)
   int M0max, M1max;
+  const void* x0;          // optional starting fields [prob][side][rhs][comp][N1][Nh] (working precision)
+  void* fields;            // optional final CG fields, same layout
 };
 
 // bytes of one batch scratch slot for a task (same formula on host and device)

@@ -1,0 +1,693 @@
+// Learned CG warm start: a 2D Fourier-layer network (lift, L spectral layers, projection)
+// trained and run with a BF16 tensor-core GEMM (mma.sync m16n8k16, FP32 accumulation).
+//
+// Every operation is a GEMM or an elementwise kernel:
+//   spectral layer  s = E_x [ H_y ( R_k ( G_y ( F_x v ) ) ) ]   (truncated DFTs as GEMMs
+//                   against DFT bases, per-mode complex channel mixing R_k), then
+//   z = s + v W + b, v' = GELU(z) (no activation after the last layer);
+//   lift v0 = x W_l + b_l, projection out = GELU(v_L P1 + b1) P2 + b2.
+// The network output is a real field on the N grid; its DFT, projected by Gamma^E /
+// Gamma^J inside the solver, is a conforming starting field, so the bounds stay
+// guaranteed whatever the network predicts (Lemma bounds; Krylov iterates stay in E_N,
+// the remark after Eq. linear_system_dual).
+#include <cuda_bf16.h>
+#include <math.h>
+
+#include <cmath>
+#include <vector>
+
+#include "net.cuh"
+
+namespace homb {
+
+// ---------------------------------------------------------------------------------
+// BF16 tensor-core GEMM (mma.sync.m16n8k16, FP32 accumulate)
+// ---------------------------------------------------------------------------------
+constexpr int GBM = 64, GBN = 64, GBK = 32, GPAD = 8;
+
+__device__ __forceinline__ uint32_t ld_pair(const __nv_bfloat16* p) {
+  return *reinterpret_cast<const uint32_t*>(p);
+}
+
+__global__ void __launch_bounds__(128) k_gemm(GemmArgs g, int ksplit, float* partial) {
+  __shared__ __align__(16) __nv_bfloat16 As[GBM][GBK + GPAD];
+  __shared__ __align__(16) __nv_bfloat16 Bs[GBN][GBK + GPAD];
+  const int bz = blockIdx.z / ksplit;
+  const int ks = blockIdx.z - bz * ksplit;
+  const float* A = g.A + (long long)bz * g.sA;
+  const float* B = g.B + (long long)bz * g.sB;
+  const int m0 = blockIdx.y * GBM, n0 = blockIdx.x * GBN;
+  const int kchunk = ((g.K + ksplit - 1) / ksplit + GBK - 1) / GBK * GBK;
+  const int kbeg = ks * kchunk;
+  const int kend = min(g.K, kbeg + kchunk);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int wm = warp >> 1, wn = warp & 1;
+  const int grp = lane >> 2, tig = lane & 3;
+  float acc[2][4][4];
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) acc[i][j][q] = 0.f;
+  for (int k0 = kbeg; k0 < kend; k0 += GBK) {
+    // A tile (m, k): contiguous along k when not transposed, along m when transposed
+    for (int idx = threadIdx.x; idx < GBM * GBK; idx += blockDim.x) {
+      int r, kk;
+      if (!g.ta) { r = idx / GBK; kk = idx - r * GBK; }
+      else { kk = idx / GBM; r = idx - kk * GBM; }
+      const int gm = m0 + r, gk = k0 + kk;
+      float v = 0.f;
+      if (gm < g.M && gk < kend) v = g.ta ? A[(long long)gk * g.lda + gm] : A[(long long)gm * g.lda + gk];
+      As[r][kk] = __float2bfloat16_rn(v);
+    }
+    // B tile stored n-major (n, k)
+    for (int idx = threadIdx.x; idx < GBN * GBK; idx += blockDim.x) {
+      int n, kk;
+      if (!g.tb) { kk = idx / GBN; n = idx - kk * GBN; }
+      else { n = idx / GBK; kk = idx - n * GBK; }
+      const int gn = n0 + n, gk = k0 + kk;
+      float v = 0.f;
+      if (gn < g.N && gk < kend) v = g.tb ? B[(long long)gn * g.ldb + gk] : B[(long long)gk * g.ldb + gn];
+      Bs[n][kk] = __float2bfloat16_rn(v);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < GBK; kk += 16) {
+      uint32_t a[2][4], b[4][2];
+#pragma unroll
+      for (int mt = 0; mt < 2; ++mt) {
+        const int r = wm * 32 + mt * 16 + grp;
+        a[mt][0] = ld_pair(&As[r][kk + tig * 2]);
+        a[mt][1] = ld_pair(&As[r + 8][kk + tig * 2]);
+        a[mt][2] = ld_pair(&As[r][kk + 8 + tig * 2]);
+        a[mt][3] = ld_pair(&As[r + 8][kk + 8 + tig * 2]);
+      }
+#pragma unroll
+      for (int nt = 0; nt < 4; ++nt) {
+        const int n = wn * 32 + nt * 8 + grp;
+        b[nt][0] = ld_pair(&Bs[n][kk + tig * 2]);
+        b[nt][1] = ld_pair(&Bs[n][kk + 8 + tig * 2]);
+      }
+#pragma unroll
+      for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+        for (int nt = 0; nt < 4; ++nt)
+          asm volatile(
+              "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+              "{%0,%1,%2,%3};\n"
+              : "+f"(acc[mt][nt][0]), "+f"(acc[mt][nt][1]), "+f"(acc[mt][nt][2]), "+f"(acc[mt][nt][3])
+              : "r"(a[mt][0]), "r"(a[mt][1]), "r"(a[mt][2]), "r"(a[mt][3]), "r"(b[nt][0]), "r"(b[nt][1]));
+    }
+    __syncthreads();
+  }
+  // epilogue: direct (ksplit == 1) or partial sums per split
+#pragma unroll
+  for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+    for (int nt = 0; nt < 4; ++nt)
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int row = m0 + wm * 32 + mt * 16 + grp + h * 8;
+        if (row >= g.M) continue;
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+          const int col = n0 + wn * 32 + nt * 8 + tig * 2 + c;
+          if (col >= g.N) continue;
+          const float v = acc[mt][nt][h * 2 + c];
+          if (ksplit == 1) {
+            float* C = g.C + (long long)bz * g.sC + (long long)row * g.ldc + col;
+            *C = g.beta == 0.f ? g.alpha * v : g.alpha * v + g.beta * *C;
+          } else {
+            partial[(((long long)ks * g.batch + bz) * g.M + row) * g.N + col] = v;
+          }
+        }
+      }
+}
+
+__global__ void k_gemm_reduce(GemmArgs g, int ksplit, const float* partial) {
+  const long long per = (long long)g.M * g.N;
+  const long long total = per * g.batch;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    float s = 0.f;
+    for (int k = 0; k < ksplit; ++k) s += partial[(long long)k * total + i];
+    const int bz = (int)(i / per);
+    const long long rc = i - bz * per;
+    const int row = (int)(rc / g.N), col = (int)(rc - (long long)row * g.N);
+    float* C = g.C + (long long)bz * g.sC + (long long)row * g.ldc + col;
+    *C = g.beta == 0.f ? g.alpha * s : g.alpha * s + g.beta * *C;
+  }
+}
+
+// split-K scratch, owned by the caller through net_workspace: set per call
+static thread_local float* g_split_ws = nullptr;
+static thread_local long long g_split_floats = 0;
+
+cudaError_t gemm_bf16(const GemmArgs& g, cudaStream_t s) {
+  if (g.M <= 0 || g.N <= 0 || g.batch <= 0) return cudaSuccess;
+  const int gm = (g.M + GBM - 1) / GBM, gn = (g.N + GBN - 1) / GBN;
+  int ksplit = 1;
+  const long long tiles = (long long)gm * gn * g.batch;
+  if (tiles < 152 && g.K > 2048 && g_split_ws) {
+    ksplit = (int)std::min<long long>(256, std::max<long long>(1, (304 + tiles - 1) / tiles));
+    ksplit = std::min(ksplit, (g.K + 1023) / 1024);
+    while (ksplit > 1 && (long long)ksplit * g.M * g.N * g.batch > g_split_floats) --ksplit;
+  }
+  dim3 grid(gn, gm, g.batch * ksplit);
+  k_gemm<<<grid, 128, 0, s>>>(g, ksplit, g_split_ws);
+  if (ksplit > 1) {
+    const long long total = (long long)g.M * g.N * g.batch;
+    const int blocks = (int)std::min<long long>((total + 255) / 256, 152 * 8);
+    k_gemm_reduce<<<blocks, 256, 0, s>>>(g, ksplit, g_split_ws);
+  }
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------------
+// elementwise kernels
+// ---------------------------------------------------------------------------------
+__device__ __forceinline__ float gelu(float x) { return 0.5f * x * (1.f + erff(x * 0.70710678118654752f)); }
+__device__ __forceinline__ float gelu_d(float x) {
+  return 0.5f * (1.f + erff(x * 0.70710678118654752f)) + x * 0.39894228040143268f * expf(-0.5f * x * x);
+}
+
+// z += b (per column); v = act(z)
+__global__ void k_bias_act(float* z, const float* b, float* v, long long rows, int cols, int act) {
+  const long long n = rows * cols;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const float t = z[i] + b[i % cols];
+    z[i] = t;
+    v[i] = act ? gelu(t) : t;
+  }
+}
+
+__global__ void k_gelu_back(const float* dv, const float* z, float* dz, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    dz[i] = dv[i] * gelu_d(z[i]);
+}
+
+// deterministic column sums: stage 1 per row block, stage 2 over blocks
+__global__ void k_colsum1(const float* x, long long rows, int cols, int rows_per, float* part) {
+  const long long r0 = (long long)blockIdx.x * rows_per;
+  const long long r1 = min(rows, r0 + rows_per);
+  for (int c = threadIdx.x; c < cols; c += blockDim.x) {
+    float s = 0.f;
+    for (long long r = r0; r < r1; ++r) s += x[r * cols + c];
+    part[(long long)blockIdx.x * cols + c] = s;
+  }
+}
+__global__ void k_colsum2(const float* part, int nblk, int cols, float* out) {
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < cols; c += gridDim.x * blockDim.x) {
+    float s = 0.f;
+    for (int b = 0; b < nblk; ++b) s += part[(long long)b * cols + c];
+    out[c] = s;
+  }
+}
+
+__global__ void k_mse(const float* out, const float* t, float* dout, long long n, float* part) {
+  __shared__ float red[32];
+  float acc = 0.f;
+  const float sc = 2.f / (float)n;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const float d = out[i] - t[i];
+    acc += d * d;
+    dout[i] = sc * d;
+  }
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float s = 0.f;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
+    part[blockIdx.x] = s;
+  }
+}
+__global__ void k_mse_final(const float* part, int nblk, long long n, float* loss) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    double s = 0.0;
+    for (int b = 0; b < nblk; ++b) s += part[b];
+    *loss = (float)(s / (double)n);
+  }
+}
+
+__global__ void k_adam(float* p, const float* g, float* m, float* v, long long n, float lr, float b1, float b2,
+                       float eps, float c1, float c2) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const float gi = g[i];
+    const float mi = b1 * m[i] + (1.f - b1) * gi;
+    const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    p[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+  }
+}
+
+// deterministic uniform numbers from a counter hash (SplitMix64 finaliser)
+__device__ __forceinline__ float hash_uniform(unsigned long long seed, long long i) {
+  unsigned long long z = seed + 0x9E3779B97F4A7C15ULL * (unsigned long long)(i + 1);
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+  z ^= z >> 31;
+  return (float)((z >> 40) * (1.0 / 16777216.0));   // [0, 1)
+}
+__global__ void k_init(float* p, long long n, float lo, float hi, unsigned long long seed) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    p[i] = lo + (hi - lo) * hash_uniform(seed, i);
+}
+__global__ void k_fill(float* p, long long n, float v) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    p[i] = v;
+}
+
+static int eblocks(long long n) { return (int)std::min<long long>((n + 255) / 256, 152 * 16); }
+
+// ---------------------------------------------------------------------------------
+// layout
+// ---------------------------------------------------------------------------------
+NetOffsets net_offsets(const NetConfig& c) {
+  NetOffsets o{};
+  long long off = 0;
+  auto take = [&](long long n) { const long long r = off; off += n; return r; };
+  const int K1 = 2 * c.modes;
+  o.lift_w = take((long long)c.cin * c.width);
+  o.lift_b = take(c.width);
+  for (int l = 0; l < c.layers; ++l) {
+    o.R[l] = take(2LL * K1 * c.modes * c.width * c.width);
+    o.W[l] = take((long long)c.width * c.width);
+    o.b[l] = take(c.width);
+  }
+  o.p1_w = take((long long)c.width * c.proj);
+  o.p1_b = take(c.proj);
+  o.p2_w = take((long long)c.proj * c.cout);
+  o.p2_b = take(c.cout);
+  o.total = off;
+  return o;
+}
+
+long long bases_floats(const NetConfig& c) {
+  const long long N = c.N, K = c.modes, K1 = 2 * c.modes;
+  return 2 * K * N + 2 * K1 * N + 2 * N * K1 + 2 * N * K;
+}
+
+// Fr, Fi [K x N]: e^{-2 pi i kx x / N}; Gc, Gs [K1 x N]: cos, sin of 2 pi ky y / N (ky in
+// 0..K-1, -K..-1); Hc, Hs [N x K1]: cos, sin of 2 pi ky y / N; Er, Ei [N x K]: the
+// half-spectrum inverse along x with weights c_kx (1, then 2) and 1/N^2.
+void fill_bases(const NetConfig& c, float* h) {
+  const int N = c.N, K = c.modes, K1 = 2 * c.modes;
+  const double tp = 6.283185307179586476925286766559;
+  float* Fr = h;
+  float* Fi = Fr + (long long)K * N;
+  float* Gc = Fi + (long long)K * N;
+  float* Gs = Gc + (long long)K1 * N;
+  float* Hc = Gs + (long long)K1 * N;
+  float* Hs = Hc + (long long)N * K1;
+  float* Er = Hs + (long long)N * K1;
+  float* Ei = Er + (long long)N * K;
+  auto ky_of = [&](int i) { return i < K ? i : i - K1; };
+  for (int k = 0; k < K; ++k)
+    for (int x = 0; x < N; ++x) {
+      const double a = tp * k * x / N;
+      Fr[k * N + x] = (float)std::cos(a);
+      Fi[k * N + x] = (float)-std::sin(a);
+      const double w = (k == 0 ? 1.0 : 2.0) / ((double)N * N);
+      Er[x * K + k] = (float)(w * std::cos(a));
+      Ei[x * K + k] = (float)(-w * std::sin(a));
+    }
+  for (int i = 0; i < K1; ++i)
+    for (int y = 0; y < N; ++y) {
+      const double a = tp * ky_of(i) * y / N;
+      Gc[i * N + y] = (float)std::cos(a);
+      Gs[i * N + y] = (float)std::sin(a);
+      Hc[y * K1 + i] = (float)std::cos(a);
+      Hs[y * K1 + i] = (float)std::sin(a);
+    }
+}
+
+struct NetWs {
+  float *v[9], *z[8], *x1r, *x1i, *x2r[8], *x2i[8], *yr, *yi, *z1r, *z1i, *pz, *ph;
+  float *dv, *dz, *dx1r, *dx1i, *dx2r, *dx2i, *dyr, *dyi, *dz1r, *dz1i, *dh, *colpart, *lpart, *split;
+  long long split_floats;
+};
+
+// Carves the workspace; returns the number of floats used (pointers set when ws != null).
+static long long carve_n(const NetConfig& c, int B, float* ws, NetWs& w) {
+  w = NetWs{};
+  const long long P = (long long)B * c.N * c.N, W = c.width, K = c.modes, K1 = 2 * c.modes;
+  const long long x1 = (long long)B * c.N * K * W, x2 = (long long)B * K1 * K * W;
+  long long off = 0;
+  auto take = [&](long long n) {
+    float* r = ws ? ws + off : nullptr;
+    off += (n + 63) & ~63LL;
+    return r;
+  };
+  for (int l = 0; l <= c.layers; ++l) w.v[l] = take(P * W);
+  for (int l = 0; l < c.layers; ++l) w.z[l] = take(P * W);
+  w.x1r = take(x1); w.x1i = take(x1);
+  for (int l = 0; l < c.layers; ++l) { w.x2r[l] = take(x2); w.x2i[l] = take(x2); }
+  w.yr = take(x2); w.yi = take(x2); w.z1r = take(x1); w.z1i = take(x1);
+  w.pz = take(P * c.proj); w.ph = take(P * c.proj);
+  w.dv = take(P * W); w.dz = take(P * W);
+  w.dx1r = take(x1); w.dx1i = take(x1); w.dx2r = take(x2); w.dx2i = take(x2);
+  w.dyr = take(x2); w.dyi = take(x2); w.dz1r = take(x1); w.dz1i = take(x1);
+  w.dh = take(P * c.proj);
+  w.colpart = take(1024LL * std::max<long long>(c.proj, W));
+  w.lpart = take(4096);
+  w.split_floats = 4LL * 1024 * 1024;
+  w.split = take(w.split_floats);
+  return off;
+}
+
+static NetWs carve(const NetConfig& c, int B, float* ws) {
+  NetWs w;
+  carve_n(c, B, ws, w);
+  return w;
+}
+
+long long net_workspace_floats(const NetConfig& c, int B) {
+  NetWs w;
+  return carve_n(c, B, nullptr, w);
+}
+
+static GemmArgs gemm(const float* A, const float* B, float* C, int M, int N, int K, int lda, int ldb, int ldc,
+                     int ta, int tb, long long sA, long long sB, long long sC, int batch, float alpha, float beta) {
+  GemmArgs g;
+  g.A = A; g.B = B; g.C = C; g.M = M; g.N = N; g.K = K; g.lda = lda; g.ldb = ldb; g.ldc = ldc;
+  g.ta = ta; g.tb = tb; g.sA = sA; g.sB = sB; g.sC = sC; g.batch = batch; g.alpha = alpha; g.beta = beta;
+  return g;
+}
+
+#define NCK(x)                                \
+  do {                                        \
+    cudaError_t _e = (x);                     \
+    if (_e != cudaSuccess) return _e;         \
+  } while (0)
+
+static cudaError_t colsum(const float* x, long long rows, int cols, float* out, float* part, cudaStream_t s) {
+  const int nblk = (int)std::min<long long>(1024, std::max<long long>(1, rows / 256));
+  const int rows_per = (int)((rows + nblk - 1) / nblk);
+  k_colsum1<<<nblk, 128, 0, s>>>(x, rows, cols, rows_per, part);
+  k_colsum2<<<(cols + 127) / 128, 128, 0, s>>>(part, nblk, cols, out);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------------
+// forward / backward
+// ---------------------------------------------------------------------------------
+struct Bases {
+  const float *Fr, *Fi, *Gc, *Gs, *Hc, *Hs, *Er, *Ei;
+};
+static Bases bases_of(const NetConfig& c, const float* b) {
+  const long long N = c.N, K = c.modes, K1 = 2 * c.modes;
+  Bases r;
+  r.Fr = b; r.Fi = r.Fr + K * N; r.Gc = r.Fi + K * N; r.Gs = r.Gc + K1 * N;
+  r.Hc = r.Gs + K1 * N; r.Hs = r.Hc + N * K1; r.Er = r.Hs + N * K1; r.Ei = r.Er + N * K;
+  return r;
+}
+
+cudaError_t net_forward(const NetConfig& c, const float* prm, const float* bases, int B, const float* in, float* out,
+                        float* ws, int train, cudaStream_t s) {
+  (void)train;
+  const NetOffsets o = net_offsets(c);
+  NetWs w = carve(c, B, ws);
+  g_split_ws = w.split;
+  g_split_floats = w.split_floats;
+  const Bases bs = bases_of(c, bases);
+  const int N = c.N, W = c.width, K = c.modes, K1 = 2 * c.modes, KW = K * W;
+  const long long P = (long long)B * N * N;
+  const int BN = B * N;
+  // lift
+  NCK(gemm_bf16(gemm(in, prm + o.lift_w, w.v[0], (int)P, W, c.cin, c.cin, W, W, 0, 0, 0, 0, 0, 1, 1.f, 0.f), s));
+  k_bias_act<<<eblocks(P * W), 256, 0, s>>>(w.v[0], prm + o.lift_b, w.v[0], P, W, 0);
+  for (int l = 0; l < c.layers; ++l) {
+    const float* v = w.v[l];
+    const float* Rr = prm + o.R[l];
+    const float* Ri = Rr + (long long)K1 * K * W * W;
+    // (1) x DFT, per (b, y): [K x N] x [N x W]
+    NCK(gemm_bf16(gemm(bs.Fr, v, w.x1r, K, W, N, N, W, W, 0, 0, 0, (long long)N * W, (long long)K * W, BN, 1.f, 0.f), s));
+    NCK(gemm_bf16(gemm(bs.Fi, v, w.x1i, K, W, N, N, W, W, 0, 0, 0, (long long)N * W, (long long)K * W, BN, 1.f, 0.f), s));
+    // (2) y DFT, per b: X2r = Gc X1r + Gs X1i, X2i = Gc X1i - Gs X1r   ([K1 x N] x [N x KW])
+    const long long sx1 = (long long)N * KW, sx2 = (long long)K1 * KW;
+    NCK(gemm_bf16(gemm(bs.Gc, w.x1r, w.x2r[l], K1, KW, N, N, KW, KW, 0, 0, 0, sx1, sx2, B, 1.f, 0.f), s));
+    NCK(gemm_bf16(gemm(bs.Gs, w.x1i, w.x2r[l], K1, KW, N, N, KW, KW, 0, 0, 0, sx1, sx2, B, 1.f, 1.f), s));
+    NCK(gemm_bf16(gemm(bs.Gc, w.x1i, w.x2i[l], K1, KW, N, N, KW, KW, 0, 0, 0, sx1, sx2, B, 1.f, 0.f), s));
+    NCK(gemm_bf16(gemm(bs.Gs, w.x1r, w.x2i[l], K1, KW, N, N, KW, KW, 0, 0, 0, sx1, sx2, B, -1.f, 1.f), s));
+    // (3) per mode m: Y = X2 R (complex), rows b (stride K1*K*W), batch over modes
+    const int nm = K1 * K;
+    const int ldm = nm * W;
+    NCK(gemm_bf16(gemm(w.x2r[l], Rr, w.yr, B, W, W, ldm, W, ldm, 0, 0, W, (long long)W * W, W, nm, 1.f, 0.f), s));
+    NCK(gemm_bf16(gemm(w.x2i[l], Ri, w.yr, B, W, W, ldm, W, ldm, 0, 0, W, (long long)W * W, W, nm, -1.f, 1.f), s));
+    NCK(gemm_bf16(gemm(w.x2r[l], Ri, w.yi, B, W, W, ldm, W, ldm, 0, 0, W, (long long)W * W, W, nm, 1.f, 0.f), s));
+    NCK(gemm_bf16(gemm(w.x2i[l], Rr, w.yi, B, W, W, ldm, W, ldm, 0, 0, W, (long long)W * W, W, nm, 1.f, 1.f), s));
+    // (4) inverse y, per b: Z1r = Hc Yr - Hs Yi, Z1i = Hc Yi + Hs Yr   ([N x K1] x [K1 x KW])
+    NCK(gemm_bf16(gemm(bs.Hc, w.yr, w.z1r, N, KW, K1, K1, KW, KW, 0, 0, 0, sx2, sx1, B, 1.f, 0.f), s));
+    NCK(gemm_bf16(gemm(bs.Hs, w.yi, w.z1r, N, KW, K1, K1, KW, KW, 0, 0, 0, sx2, sx1, B, -1.f, 1.f), s));
+    NCK(gemm_bf16(gemm(bs.Hc, w.yi, w.z1i, N, KW, K1, K1, KW, KW, 0, 0, 0, sx2, sx1, B, 1.f, 0.f), s));
+    NCK(gemm_bf16(gemm(bs.Hs, w.yr, w.z1i, N, KW, K1, K1, KW, KW, 0, 0, 0, sx2, sx1, B, 1.f, 1.f), s));
+    // (5) inverse x (half spectrum), per (b, y): s = Er Z1r + Ei Z1i   ([N x K] x [K x W]) into z
+    NCK(gemm_bf16(gemm(bs.Er, w.z1r, w.z[l], N, W, K, K, W, W, 0, 0, 0, (long long)K * W, (long long)N * W, BN, 1.f, 0.f), s));
+    NCK(gemm_bf16(gemm(bs.Ei, w.z1i, w.z[l], N, W, K, K, W, W, 0, 0, 0, (long long)K * W, (long long)N * W, BN, 1.f, 1.f), s));
+    // (6) z += v W ; (7) bias + activation
+    NCK(gemm_bf16(gemm(v, prm + o.W[l], w.z[l], (int)P, W, W, W, W, W, 0, 0, 0, 0, 0, 1, 1.f, 1.f), s));
+    k_bias_act<<<eblocks(P * W), 256, 0, s>>>(w.z[l], prm + o.b[l], w.v[l + 1], P, W, l + 1 < c.layers ? 1 : 0);
+  }
+  // projection
+  NCK(gemm_bf16(gemm(w.v[c.layers], prm + o.p1_w, w.pz, (int)P, c.proj, W, W, c.proj, c.proj, 0, 0, 0, 0, 0, 1, 1.f, 0.f), s));
+  k_bias_act<<<eblocks(P * c.proj), 256, 0, s>>>(w.pz, prm + o.p1_b, w.ph, P, c.proj, 1);
+  NCK(gemm_bf16(gemm(w.ph, prm + o.p2_w, out, (int)P, c.cout, c.proj, c.proj, c.cout, c.cout, 0, 0, 0, 0, 0, 1, 1.f, 0.f), s));
+  float* zero_z = nullptr;
+  (void)zero_z;
+  k_bias_act<<<eblocks(P * c.cout), 256, 0, s>>>(out, prm + o.p2_b, out, P, c.cout, 0);
+  g_split_ws = nullptr;
+  g_split_floats = 0;
+  return cudaGetLastError();
+}
+
+cudaError_t net_backward(const NetConfig& c, const float* prm, const float* bases, int B, const float* in,
+                         const float* target, float* grad, float* loss_dev, float* ws, cudaStream_t s) {
+  const NetOffsets o = net_offsets(c);
+  NetWs w = carve(c, B, ws);
+  const Bases bs = bases_of(c, bases);
+  const int N = c.N, W = c.width, K = c.modes, K1 = 2 * c.modes, KW = K * W;
+  const long long P = (long long)B * N * N;
+  const int BN = B * N;
+  // forward with the activations kept; output into dh's tail (reuse of pz for out is not possible)
+  float* out = w.dh;   // [P x cout] fits in [P x proj]
+  NCK(net_forward(c, prm, bases, B, in, out, ws, 1, s));
+  g_split_ws = w.split;
+  g_split_floats = w.split_floats;
+  // loss and d out (in place in out)
+  const long long nout = P * c.cout;
+  const int lb = (int)std::min<long long>(1024, (nout + 255) / 256);
+  k_mse<<<lb, 256, 0, s>>>(out, target, out, nout, w.lpart);
+  k_mse_final<<<1, 32, 0, s>>>(w.lpart, lb, nout, loss_dev);
+  // projection backward
+  NCK(colsum(out, P, c.cout, grad + o.p2_b, w.colpart, s));
+  NCK(gemm_bf16(gemm(w.ph, out, grad + o.p2_w, c.proj, c.cout, (int)P, c.proj, c.cout, c.cout, 1, 0, 0, 0, 0, 1, 1.f, 0.f), s));
+  // dh = dout P2^T into pz's buffer after using pz for gelu'
+  float* dh = w.ph;   // ph no longer needed after dP2
+  NCK(gemm_bf16(gemm(out, prm + o.p2_w, dh, (int)P, c.proj, c.cout, c.cout, c.cout, c.proj, 0, 1, 0, 0, 0, 1, 1.f, 0.f), s));
+  k_gelu_back<<<eblocks(P * c.proj), 256, 0, s>>>(dh, w.pz, dh, P * c.proj);
+  NCK(colsum(dh, P, c.proj, grad + o.p1_b, w.colpart, s));
+  NCK(gemm_bf16(gemm(w.v[c.layers], dh, grad + o.p1_w, W, c.proj, (int)P, W, c.proj, c.proj, 1, 0, 0, 0, 0, 1, 1.f, 0.f), s));
+  NCK(gemm_bf16(gemm(dh, prm + o.p1_w, w.dv, (int)P, W, c.proj, c.proj, c.proj, W, 0, 1, 0, 0, 0, 1, 1.f, 0.f), s));
+  // layers, last to first; w.dv holds d v_{l+1}
+  for (int l = c.layers - 1; l >= 0; --l) {
+    const float* v = w.v[l];
+    const float* Rr = prm + o.R[l];
+    const float* Ri = Rr + (long long)K1 * K * W * W;
+    float* dRr = grad + o.R[l];
+    float* dRi = dRr + (long long)K1 * K * W * W;
+    if (l + 1 < c.layers) k_gelu_back<<<eblocks(P * W), 256, 0, s>>>(w.dv, w.z[l], w.dz, P * W);
+    else NCK(cudaMemcpyAsync(w.dz, w.dv, P * W * sizeof(float), cudaMemcpyDeviceToDevice, s));
+    NCK(colsum(w.dz, P, W, grad + o.b[l], w.colpart, s));
+    NCK(gemm_bf16(gemm(v, w.dz, grad + o.W[l], W, W, (int)P, W, W, W, 1, 0, 0, 0, 0, 1, 1.f, 0.f), s));
+    NCK(gemm_bf16(gemm(w.dz, prm + o.W[l], w.dv, (int)P, W, W, W, W, W, 0, 1, 0, 0, 0, 1, 1.f, 0.f), s));
+    // (5') dZ1 = E^T dz, per (b, y): [K x N] x [N x W]
+    NCK(gemm_bf16(gemm(bs.Er, w.dz, w.dz1r, K, W, N, K, W, W, 1, 0, 0, (long long)N * W, (long long)K * W, BN, 1.f, 0.f), s));
+    NCK(gemm_bf16(gemm(bs.Ei, w.dz, w.dz1i, K, W, N, K, W, W, 1, 0, 0, (long long)N * W, (long long)K * W, BN, 1.f, 0.f), s));
+    // (4') dYr = Hc^T dZ1r + Hs^T dZ1i ; dYi = Hc^T dZ1i - Hs^T dZ1r   ([K1 x N] x [N x KW])
+    const long long sx1 = (long long)N * KW, sx2 = (long long)K1 * KW;
+    NCK(gemm_bf16(gemm(bs.Hc, w.dz1r, w.dyr, K1, KW, N, K1, KW, KW, 1, 0, 0, sx1, sx2, B, 1.f, 0.f), s));
+    NCK(gemm_bf16(gemm(bs.Hs, w.dz1i, w.dyr, K1, KW, N, K1, KW, KW, 1, 0, 0, sx1, sx2, B, 1.f, 1.f), s));
+    NCK(gemm_bf16(gemm(bs.Hc, w.dz1i, w.dyi, K1, KW, N, K1, KW, KW, 1, 0, 0, sx1, sx2, B, 1.f, 0.f), s));
+    NCK(gemm_bf16(gemm(bs.Hs, w.dz1r, w.dyi, K1, KW, N, K1, KW, KW, 1, 0, 0, sx1, sx2, B, -1.f, 1.f), s));
+    // (3') per mode: dRr = X2r^T dYr + X2i^T dYi ; dRi = X2r^T dYi - X2i^T dYr   ([W x B] x [B x W])
+    const int nm = K1 * K;
+    const int ldm = nm * W;
+    const long long WW = (long long)W * W;
+    NCK(gemm_bf16(gemm(w.x2r[l], w.dyr, dRr, W, W, B, ldm, ldm, W, 1, 0, W, W, WW, nm, 1.f, 0.f), s));
+    NCK(gemm_bf16(gemm(w.x2i[l], w.dyi, dRr, W, W, B, ldm, ldm, W, 1, 0, W, W, WW, nm, 1.f, 1.f), s));
+    NCK(gemm_bf16(gemm(w.x2r[l], w.dyi, dRi, W, W, B, ldm, ldm, W, 1, 0, W, W, WW, nm, 1.f, 0.f), s));
+    NCK(gemm_bf16(gemm(w.x2i[l], w.dyr, dRi, W, W, B, ldm, ldm, W, 1, 0, W, W, WW, nm, -1.f, 1.f), s));
+    //      dX2r = dYr Rr^T + dYi Ri^T ; dX2i = dYi Rr^T - dYr Ri^T   ([B x W] x [W x W]^T)
+    NCK(gemm_bf16(gemm(w.dyr, Rr, w.dx2r, B, W, W, ldm, W, ldm, 0, 1, W, WW, W, nm, 1.f, 0.f), s));
+    NCK(gemm_bf16(gemm(w.dyi, Ri, w.dx2r, B, W, W, ldm, W, ldm, 0, 1, W, WW, W, nm, 1.f, 1.f), s));
+    NCK(gemm_bf16(gemm(w.dyi, Rr, w.dx2i, B, W, W, ldm, W, ldm, 0, 1, W, WW, W, nm, 1.f, 0.f), s));
+    NCK(gemm_bf16(gemm(w.dyr, Ri, w.dx2i, B, W, W, ldm, W, ldm, 0, 1, W, WW, W, nm, -1.f, 1.f), s));
+    // (2') dX1r = Gc^T dX2r - Gs^T dX2i ; dX1i = Gs^T dX2r + Gc^T dX2i   ([N x K1] x [K1 x KW])
+    NCK(gemm_bf16(gemm(bs.Gc, w.dx2r, w.dx1r, N, KW, K1, N, KW, KW, 1, 0, 0, sx2, sx1, B, 1.f, 0.f), s));
+    NCK(gemm_bf16(gemm(bs.Gs, w.dx2i, w.dx1r, N, KW, K1, N, KW, KW, 1, 0, 0, sx2, sx1, B, -1.f, 1.f), s));
+    NCK(gemm_bf16(gemm(bs.Gs, w.dx2r, w.dx1i, N, KW, K1, N, KW, KW, 1, 0, 0, sx2, sx1, B, 1.f, 0.f), s));
+    NCK(gemm_bf16(gemm(bs.Gc, w.dx2i, w.dx1i, N, KW, K1, N, KW, KW, 1, 0, 0, sx2, sx1, B, 1.f, 1.f), s));
+    // (1') dv += Fr^T dX1r + Fi^T dX1i, per (b, y): [N x K] x [K x W]
+    NCK(gemm_bf16(gemm(bs.Fr, w.dx1r, w.dv, N, W, K, N, W, W, 1, 0, 0, (long long)K * W, (long long)N * W, BN, 1.f, 1.f), s));
+    NCK(gemm_bf16(gemm(bs.Fi, w.dx1i, w.dv, N, W, K, N, W, W, 1, 0, 0, (long long)K * W, (long long)N * W, BN, 1.f, 1.f), s));
+  }
+  // lift
+  NCK(colsum(w.dv, P, W, grad + o.lift_b, w.colpart, s));
+  NCK(gemm_bf16(gemm(in, w.dv, grad + o.lift_w, c.cin, W, (int)P, c.cin, W, W, 1, 0, 0, 0, 0, 1, 1.f, 0.f), s));
+  g_split_ws = nullptr;
+  g_split_floats = 0;
+  return cudaGetLastError();
+}
+
+cudaError_t adam_step(float* p, const float* g, float* m, float* v, long long n, float lr, float b1, float b2,
+                      float eps, int step, cudaStream_t s) {
+  const float c1 = 1.f - powf(b1, (float)step), c2 = 1.f - powf(b2, (float)step);
+  k_adam<<<eblocks(n), 256, 0, s>>>(p, g, m, v, n, lr, b1, b2, eps, c1, c2);
+  return cudaGetLastError();
+}
+
+cudaError_t init_params(const NetConfig& c, float* prm, unsigned long long seed, cudaStream_t s) {
+  const NetOffsets o = net_offsets(c);
+  auto uni = [&](long long off, long long n, float a, unsigned long long sd) {
+    k_init<<<eblocks(n), 256, 0, s>>>(prm + off, n, -a, a, seed * 1315423911ULL + sd);
+  };
+  auto zero = [&](long long off, long long n) { k_fill<<<eblocks(n), 256, 0, s>>>(prm + off, n, 0.f); };
+  const int K1 = 2 * c.modes;
+  uni(o.lift_w, (long long)c.cin * c.width, 1.f / sqrtf((float)c.cin), 1);
+  zero(o.lift_b, c.width);
+  for (int l = 0; l < c.layers; ++l) {
+    const float sc = 1.f / (float)(c.width * c.width);
+    k_init<<<eblocks(2LL * K1 * c.modes * c.width * c.width), 256, 0, s>>>(
+        prm + o.R[l], 2LL * K1 * c.modes * c.width * c.width, 0.f, sc, seed * 2654435761ULL + 100 + l);
+    uni(o.W[l], (long long)c.width * c.width, 1.f / sqrtf((float)c.width), 200 + l);
+    zero(o.b[l], c.width);
+  }
+  uni(o.p1_w, (long long)c.width * c.proj, 1.f / sqrtf((float)c.width), 300);
+  zero(o.p1_b, c.proj);
+  uni(o.p2_w, (long long)c.proj * c.cout, 1.f / sqrtf((float)c.proj), 301);
+  zero(o.p2_b, c.cout);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------------
+// real N-grid fields <-> half spectra (direct DFT, one CTA per (sample, channel))
+// ---------------------------------------------------------------------------------
+__global__ void k_grid_to_half(int N, int ch, const float* grid, void* half, int fp64) {
+  extern __shared__ __align__(16) unsigned char sm[];
+  float* u = reinterpret_cast<float*>(sm);                 // N*N
+  float2* tw = reinterpret_cast<float2*>(u + N * N + (N * N & 1));   // N
+  float2* R = tw + N;                                      // N * Nh
+  const int Nh = (N + 1) / 2;
+  const int b = blockIdx.x / ch, c = blockIdx.x - (blockIdx.x / ch) * ch;
+  for (int i = threadIdx.x; i < N * N; i += blockDim.x) u[i] = grid[((long long)b * N * N + i) * ch + c];
+  for (int i = threadIdx.x; i < N; i += blockDim.x) {
+    float sn, cs;
+    sincospif(2.f * i / N, &sn, &cs);
+    tw[i] = make_float2(cs, sn);
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < N * Nh; t += blockDim.x) {   // rows: R[y][kx] = sum_x u e^{-2 pi i kx x/N}
+    const int y = t / Nh, kx = t - y * Nh;
+    float re = 0.f, im = 0.f;
+    int idx = 0;
+    for (int x = 0; x < N; ++x) {
+      const float2 w = tw[idx];
+      re += u[y * N + x] * w.x;
+      im -= u[y * N + x] * w.y;
+      idx += kx;
+      if (idx >= N) idx -= N;
+    }
+    R[t] = make_float2(re, im);
+  }
+  __syncthreads();
+  const double inv = 1.0 / ((double)N * N);
+  for (int t = threadIdx.x; t < N * Nh; t += blockDim.x) {   // columns, FFT order ky
+    const int i = t / Nh, kx = t - i * Nh;
+    float re = 0.f, im = 0.f;
+    int idx = 0;
+    for (int y = 0; y < N; ++y) {
+      const float2 w = tw[idx];
+      const float2 r = R[y * Nh + kx];
+      re += r.x * w.x + r.y * w.y;
+      im += r.y * w.x - r.x * w.y;
+      idx += i;
+      if (idx >= N) idx -= N;
+    }
+    const long long o = ((long long)(b * ch + c) * N + i) * Nh + kx;
+    if (fp64) reinterpret_cast<double2*>(half)[o] = make_double2(re * inv, im * inv);
+    else reinterpret_cast<float2*>(half)[o] = make_float2((float)(re * inv), (float)(im * inv));
+  }
+}
+
+__global__ void k_half_to_grid(int N, int ch, const void* half, float* grid, int fp64) {
+  extern __shared__ __align__(16) unsigned char sm[];
+  float2* H = reinterpret_cast<float2*>(sm);   // N * Nh
+  const int Nh = (N + 1) / 2;
+  float2* S = H + N * Nh;                       // N * Nh
+  float2* tw = S + N * Nh;                      // N
+  const int b = blockIdx.x / ch, c = blockIdx.x - (blockIdx.x / ch) * ch;
+  for (int i = threadIdx.x; i < N * Nh; i += blockDim.x) {
+    const long long o = (long long)(b * ch + c) * N * Nh + i;
+    if (fp64) {
+      const double2 v = reinterpret_cast<const double2*>(half)[o];
+      H[i] = make_float2((float)v.x, (float)v.y);
+    } else {
+      H[i] = reinterpret_cast<const float2*>(half)[o];
+    }
+  }
+  for (int i = threadIdx.x; i < N; i += blockDim.x) {
+    float sn, cs;
+    sincospif(2.f * i / N, &sn, &cs);
+    tw[i] = make_float2(cs, sn);
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < N * Nh; t += blockDim.x) {   // S[y][kx] = sum_i H[i][kx] e^{2 pi i i y/N}
+    const int y = t / Nh, kx = t - y * Nh;
+    float re = 0.f, im = 0.f;
+    int idx = 0;
+    for (int i = 0; i < N; ++i) {
+      const float2 w = tw[idx];
+      const float2 h = H[i * Nh + kx];
+      re += h.x * w.x - h.y * w.y;
+      im += h.x * w.y + h.y * w.x;
+      idx += y;
+      if (idx >= N) idx -= N;
+    }
+    S[t] = make_float2(re, im);
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < N * N; t += blockDim.x) {   // u[y][x] = Re S[y][0] + 2 sum Re(S e^{...})
+    const int y = t / N, x = t - y * N;
+    float acc = S[y * Nh].x;
+    int idx = x;
+    for (int kx = 1; kx < Nh; ++kx) {
+      const float2 w = tw[idx];
+      const float2 sv = S[y * Nh + kx];
+      acc += 2.f * (sv.x * w.x - sv.y * w.y);
+      idx += x;
+      if (idx >= N) idx -= N;
+    }
+    grid[((long long)b * N * N + t) * ch + c] = acc;
+  }
+}
+
+cudaError_t grid_to_half(int N, int B, int ch, const float* grid, void* half, int fp64, cudaStream_t s) {
+  const int Nh = (N + 1) / 2;
+  const size_t smem = (size_t)N * N * 4 + 8 + (size_t)N * 8 + (size_t)N * Nh * 8;
+  if (smem > 48 * 1024) cudaFuncSetAttribute(k_grid_to_half, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  k_grid_to_half<<<B * ch, 256, smem, s>>>(N, ch, grid, half, fp64);
+  return cudaGetLastError();
+}
+
+cudaError_t half_to_grid(int N, int B, int ch, const void* half, float* grid, int fp64, cudaStream_t s) {
+  const int Nh = (N + 1) / 2;
+  const size_t smem = 2 * (size_t)N * Nh * 8 + (size_t)N * 8;
+  if (smem > 48 * 1024) cudaFuncSetAttribute(k_half_to_grid, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  k_half_to_grid<<<B * ch, 256, smem, s>>>(N, ch, half, grid, fp64);
+  return cudaGetLastError();
+}
+
+}  // namespace homb

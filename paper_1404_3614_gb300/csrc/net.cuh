@@ -1,0 +1,64 @@
+// Learned CG warm start: a 2D Fourier-layer network on the N-grid of one cell.
+// Declarations shared by net.cu (kernels, orchestration) and api.cu (C ABI).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace homb {
+
+struct NetConfig {
+  int N;       // grid points per axis (odd)
+  int cin;     // input channels
+  int width;   // hidden channels W
+  int modes;   // kept modes K: kx in [0, K), ky in [-K, K)
+  int layers;  // Fourier layers L
+  int proj;    // projection hidden channels P
+  int cout;    // output channels
+};
+
+// offsets (floats) of the parameter tensors in the flat parameter array
+struct NetOffsets {
+  long long lift_w, lift_b;
+  long long R[8], W[8], b[8];   // per layer: spectral weights (re then im), 1x1 weight, bias
+  long long p1_w, p1_b, p2_w, p2_b;
+  long long total;
+};
+
+NetOffsets net_offsets(const NetConfig& c);
+long long net_workspace_floats(const NetConfig& c, int batch);
+
+// GEMM on the tensor cores: C[b] = alpha * op(A[b]) op(B[b]) + beta * C[b]; A, B, C FP32 in
+// memory, rounded to BF16 when staged, FP32 accumulation. op = transpose when ta/tb.
+// A is M x K (row-major with lda) or K x M when ta; B is K x N (ldb) or N x K when tb.
+struct GemmArgs {
+  const float* A;
+  const float* B;
+  float* C;
+  int M, N, K;
+  int lda, ldb, ldc;
+  int ta, tb;
+  long long sA, sB, sC;   // batch strides
+  int batch;
+  float alpha, beta;
+};
+cudaError_t gemm_bf16(const GemmArgs& g, cudaStream_t s);
+
+// forward (keeps activations in ws for a backward when train != 0); out [B*N*N, cout]
+cudaError_t net_forward(const NetConfig& c, const float* params, const float* bases, int B, const float* in,
+                        float* out, float* ws, int train, cudaStream_t s);
+// loss = mean (out - target)^2 ; gradient of the parameters into grad (overwritten)
+cudaError_t net_backward(const NetConfig& c, const float* params, const float* bases, int B, const float* in,
+                         const float* target, float* grad, float* loss_dev, float* ws, cudaStream_t s);
+cudaError_t adam_step(float* p, const float* g, float* m, float* v, long long n, float lr, float b1, float b2,
+                      float eps, int step, cudaStream_t s);
+// DFT bases for the spectral layers, [bases_floats(c)] floats, computed on the host in FP64
+long long bases_floats(const NetConfig& c);
+void fill_bases(const NetConfig& c, float* host);
+cudaError_t init_params(const NetConfig& c, float* params, unsigned long long seed, cudaStream_t s);
+
+// real N-grid fields [B][N][N][ch] <-> half spectra [B][ch][N][Nh] (complex FP64/FP32), forward
+// with the 1/N^2 factor of Eq. DFT
+cudaError_t grid_to_half(int N, int B, int ch, const float* grid, void* half, int fp64, cudaStream_t s);
+cudaError_t half_to_grid(int N, int B, int ch, const void* half, float* grid, int fp64, cudaStream_t s);
+
+}  // namespace homb
