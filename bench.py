@@ -60,6 +60,24 @@ def workload(name: str = "cube3d_N41"):
     raise ValueError(name)
 
 
+def run_learned(args):
+    """The learned warm-start workload: train the Fourier-layer network on method-generated
+    correctors of random-rectangle cells at N = 63, then compare CG from zero and from the
+    projected prediction on held-out cells (one JSON line)."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1404_3614_gb300 as hb
+    from paper_1404_3614_gb300 import warmstart
+    solver = hb.Bounds(0)
+    res = warmstart.train_and_evaluate(N=args.learned_N, n_train=args.learned_train, n_test=args.learned_test,
+                                       epochs=args.learned_epochs, batch=32, width=32, modes=12, layers=4,
+                                       proj=128, tol=TOL, precision="mixed", solver=solver)
+    print(json.dumps({"workload": "learned warm start, random-rectangle cells", **res}), flush=True)
+    solver.close()
+    return 0
+
+
 def run_matvec_only(args):
     """Operator applications only (for kernel captures): `--reps` hom_matvec calls on d fields."""
     import torch
@@ -497,6 +515,11 @@ def main():
     ap.add_argument("--workload", default="cube3d_N41", choices=sorted(WORKLOADS))
     ap.add_argument("--matvec-only", action="store_true", help="operator applications only")
     ap.add_argument("--reps", type=int, default=20)
+    ap.add_argument("--learned", action="store_true", help="learned warm-start workload only")
+    ap.add_argument("--learned-N", type=int, default=63)
+    ap.add_argument("--learned-train", type=int, default=20000)
+    ap.add_argument("--learned-test", type=int, default=1024)
+    ap.add_argument("--learned-epochs", type=int, default=20)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -504,6 +527,8 @@ def main():
         return run_reference(args)
     if args.matvec_only:
         return run_matvec_only(args)
+    if args.learned:
+        return run_learned(args)
     return run_gpu(args)
 
 

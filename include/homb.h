@@ -185,7 +185,9 @@ hom_status hom_bounds_batched(hom_ctx* ctx, int32_t n, const hom_problem* probs,
  * ky in [-modes, modes) with per-mode complex channel mixing plus a 1x1 path and GELU,
  * projection width -> proj (GELU) -> cout. Every product is a BF16 tensor-core GEMM with
  * FP32 accumulation; parameters are FP32 (a flat array, layout fixed by the config).
- * Activations are channels-last [batch][N][N][ch] FP32. */
+ * Activations are channels-last [batch][N][N][ch] FP32. The network calls keep the DFT
+ * bases at the front of their workspace between calls with the same workspace pointer
+ * and grid: do not write into a network workspace between network calls. */
 typedef struct {
   int32_t N, cin, width, modes, layers, proj, cout;
 } hom_net_config;

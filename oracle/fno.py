@@ -95,4 +95,4 @@ def loss_and_grad(cfg, params, x, target):
     out = forward(cfg, p, x)
     loss = torch.mean((out - target) ** 2)
     loss.backward()
-    return float(loss), p.grad.detach(), out.detach()
+    return float(loss.detach()), p.grad.detach(), out.detach()

@@ -43,6 +43,9 @@ struct hom_ctx {
   size_t pin_out_bytes = 0;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t graph_exec = nullptr;
+  // network: DFT bases already uploaded to this workspace for this grid / mode count
+  const void* net_bases_ws = nullptr;
+  int net_bases_N = 0, net_bases_modes = 0;
   std::vector<long long> graph_key;
   std::vector<std::pair<long long, int>> tuned_cap;   // (key, cap)
 };
@@ -1481,10 +1484,15 @@ static size_t net_ws_bytes(const NetConfig& c, int batch) {
 static hom_status net_prepare(hom_ctx* ctx, const NetConfig& c, int batch, void* d_ws, size_t ws_bytes,
                               cudaStream_t st, float** bases, float** rest) {
   if (!d_ws || ws_bytes < net_ws_bytes(c, batch)) return fail(ctx, HOM_ERR_WORKSPACE, "workspace too small");
-  std::vector<float> hb((size_t)bases_floats(c));
-  fill_bases(c, hb.data());
   float* b = static_cast<float*>(d_ws);
-  CK(h2d_copy(ctx, b, hb.data(), hb.size() * sizeof(float), st));
+  if (ctx->net_bases_ws != d_ws || ctx->net_bases_N != c.N || ctx->net_bases_modes != c.modes) {
+    std::vector<float> hb((size_t)bases_floats(c));
+    fill_bases(c, hb.data());
+    CK(h2d_copy(ctx, b, hb.data(), hb.size() * sizeof(float), st));
+    ctx->net_bases_ws = d_ws;
+    ctx->net_bases_N = c.N;
+    ctx->net_bases_modes = c.modes;
+  }
   *bases = b;
   *rest = b + ((bases_floats(c) + 255) / 256) * 256;
   return HOM_OK;

@@ -116,9 +116,10 @@ def test_forward_and_gradient_match_cpu_reference(hb):
         assert abs(loss - rloss) <= 2e-2 * rloss
         offs = fno.offsets(**CFG)
         G = grad.cpu().double()
-        for name, (s, n) in offs.items():
+        for name, val in offs.items():
             if name == "total":
                 continue
+            s, n = val
             a, b = G[s:s + n], rgrad[s:s + n]
             scale = max(b.abs().max().item(), 1e-12)
             assert (a - b).abs().max().item() <= 5e-2 * scale, (name, (a - b).abs().max().item(), scale)
