@@ -522,10 +522,31 @@ __global__ void __launch_bounds__(kBatchThreads, 2) k_batch(BArgs a) {
       double pqd[2] = {0.0, 0.0};
       col_final<T>(T2, vq, vp, t2_fs, fld, s_rlist, s_nrl, Nh, N1, M1, t.invY[0], t.invY[1], t.side, t.plan1, W1,
                    At, Bt, capT, pqd);
+      // Rayleigh-Ritz on span{x0}: x = s x0 with s = (x0.b)/(x0.C x0) minimises the energy
+      // functional along the start direction, so a start never does worse than x = 0
+      double xb[2] = {0.0, 0.0};
+      for (long long i = threadIdx.x; i < 4 * fld; i += blockDim.x) {
+        const int r = (int)(i / (2 * fld));
+        const cpx<T> pv = vp[i], bv = vr[i];
+        const double w = (i % Nh) == 0 ? 1.0 : 2.0;
+        xb[r] += w * ((double)pv.x * bv.x + (double)pv.y * bv.y);
+      }
+      for (int r = 0; r < 2; ++r) {
+        const double num = block_sum(xb[r], s_red);
+        const double den = block_sum(pqd[r], s_red);   // x0 . C x0 (col_final's partial sums)
+        if (threadIdx.x == 0) {
+          const double s_ = den > 0.0 ? num / den : 0.0;
+          s_alpha[r] = isfinite(s_) ? s_ : 0.0;
+        }
+      }
+      __syncthreads();
       acc[0] = acc[1] = 0.0;
       for (long long i = threadIdx.x; i < 4 * fld; i += blockDim.x) {
         const int r = (int)(i / (2 * fld));
-        const cpx<T> rv = sub<T>(vr[i], vq[i]);
+        const T sr = T(s_alpha[r]);
+        const cpx<T> xv = vx[i], qv = vq[i];
+        vx[i] = mk<T>(sr * xv.x, sr * xv.y);
+        const cpx<T> rv = mk<T>(fma(-sr, qv.x, vr[i].x), fma(-sr, qv.y, vr[i].y));
         vr[i] = rv;
         vp[i] = mk<T>(T(0), T(0));
         const double w = (i % Nh) == 0 ? 1.0 : 2.0;

@@ -43,11 +43,23 @@ class WarmStart:
 
     # -- data -------------------------------------------------------------------------
     def features(self, problems):
+        """log10 of the phase value on the grid, divided by 3 (phase values span 1e-2..1e3)."""
         torch = self.torch
         out = torch.empty((len(problems), self.N, self.N, 1), dtype=torch.float32, device=self.dev)
         ws = torch.empty(1 << 22, dtype=torch.uint8, device=self.dev)
         bd.hom_net_features(self.ctx, problems, out.data_ptr(), ws.data_ptr(), ws.numel())
+        out.mul_(1.0 / 3.0)
         return out
+
+    @staticmethod
+    def normalise_targets(y):
+        """Scale each (side, rhs) pair of channels of each cell to unit RMS: the network
+        learns the shape of each corrector; the solver finds its scale (Rayleigh-Ritz on
+        the start direction), so the magnitude need not be predicted."""
+        n = y.shape[0]
+        blocks = y.view(n, -1, 4, 2)
+        rms = blocks.pow(2).mean(dim=(1, 3), keepdim=True).sqrt().clamp_min(1e-12)
+        return (blocks / rms).view_as(y)
 
     def solve(self, problems, precision, tol, x0=None, want_fields=False, max_iter=10000):
         torch = self.torch
@@ -140,7 +152,7 @@ def train_and_evaluate(N=63, n_train=20000, n_test=1024, epochs=20, batch=32, wi
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     _, fields = ws.solve(train_probs, prec, gen_tol, want_fields=True)
-    y = ws.fields_to_grid(fields)
+    y = WarmStart.normalise_targets(ws.fields_to_grid(fields))
     x = ws.features(train_probs)
     torch.cuda.synchronize()
     t_data = time.perf_counter() - t0
