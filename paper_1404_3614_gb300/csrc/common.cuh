@@ -50,27 +50,31 @@ struct FastDiv {
   }
 };
 
-// Compile-time factorisation of a transform length (same radix order as the runtime
-// plan: fives, threes, then 7, 11, 13).
-__host__ __device__ constexpr int cf_radix(int M, int stage) {
+// Compile-time factorisation of a transform length. big = false: radices 5 then 3 (the
+// runtime plan's order); big = true: composite radices done in registers (15, 25, 9,
+// then 5 and 3), fewer shared-memory stages for the same length.
+__host__ __device__ constexpr int cf_radix(int M, int stage, bool big = false) {
   int m = M, idx = 0;
-  const int rs[5] = {5, 3, 7, 11, 13};
-  for (int i = 0; i < 5; ++i)
-    while (m > 1 && m % rs[i] == 0) {
-      if (idx == stage) return rs[i];
-      m /= rs[i];
+  const int rs_small[5] = {5, 3, 7, 11, 13};
+  const int rs_big[5] = {15, 25, 9, 5, 3};
+  for (int i = 0; i < 5; ++i) {
+    const int r = big ? rs_big[i] : rs_small[i];
+    while (m > 1 && m % r == 0) {
+      if (idx == stage) return r;
+      m /= r;
       ++idx;
     }
+  }
   return 0;
 }
-__host__ __device__ constexpr int cf_nstages(int M) {
+__host__ __device__ constexpr int cf_nstages(int M, bool big = false) {
   int n = 0;
-  while (cf_radix(M, n) != 0) ++n;
+  while (cf_radix(M, n, big) != 0) ++n;
   return n;
 }
-__host__ __device__ constexpr int cf_ns(int M, int stage) {
+__host__ __device__ constexpr int cf_ns(int M, int stage, bool big = false) {
   int p = 1;
-  for (int i = 0; i < stage; ++i) p *= cf_radix(M, i);
+  for (int i = 0; i < stage; ++i) p *= cf_radix(M, i, big);
   return p;
 }
 
@@ -116,6 +120,88 @@ template <typename T> __device__ __forceinline__ void dft5(cpx<T>* v, int dir) {
   v[4] = sub<T>(m1, in1);
   v[2] = add<T>(m2, in2);
   v[3] = sub<T>(m2, in2);
+}
+
+// Compile-time cos / sin of 2 pi p / q from their Taylor series (argument reduced to
+// [-pi, pi]); used only for the twiddle constants inside the register DFTs.
+__host__ __device__ constexpr double ct_sin_red(double x) {
+  double term = x, sum = x;
+  for (int n = 1; n < 30; ++n) {
+    term *= -x * x / ((2.0 * n) * (2.0 * n + 1.0));
+    sum += term;
+  }
+  return sum;
+}
+__host__ __device__ constexpr double ct_cos_red(double x) {
+  double term = 1.0, sum = 1.0;
+  for (int n = 1; n < 30; ++n) {
+    term *= -x * x / ((2.0 * n - 1.0) * (2.0 * n));
+    sum += term;
+  }
+  return sum;
+}
+// angle 2 pi p / q reduced to (-pi, pi]
+__host__ __device__ constexpr double ct_angle(int p, int q) {
+  int r = p % q;
+  if (r < 0) r += q;
+  if (2 * r > q) r -= q;
+  return 6.283185307179586476925286766559 * (double)r / (double)q;
+}
+__host__ __device__ constexpr double ct_cos2pi(int p, int q) { return ct_cos_red(ct_angle(p, q)); }
+__host__ __device__ constexpr double ct_sin2pi(int p, int q) { return ct_sin_red(ct_angle(p, q)); }
+
+__host__ __device__ constexpr int ct_first_factor(int R) {
+  return R % 3 == 0 ? 3 : (R % 5 == 0 ? 5 : R);
+}
+
+// Register DFT of compile-time length R (a product of 3s and 5s): Cooley-Tukey with
+// R = R1 * R2, inner DFTs over n1 for each n2, constant twiddles w_R^{n2 k1}, outer
+// DFTs over n2; output index k1 + R1 k2. dir = -1 forward, +1 inverse.
+template <typename T, int R>
+__device__ __forceinline__ void dft_reg(cpx<T>* v, int dir);
+
+template <typename T, int R1, int R2>
+__device__ __forceinline__ void dft_ct(cpx<T>* v, int dir) {
+  constexpr int R = R1 * R2;
+  cpx<T> t[R];
+#pragma unroll
+  for (int n2 = 0; n2 < R2; ++n2) {
+    cpx<T> a[R1];
+#pragma unroll
+    for (int n1 = 0; n1 < R1; ++n1) a[n1] = v[R2 * n1 + n2];
+    dft_reg<T, R1>(a, dir);
+#pragma unroll
+    for (int k1 = 0; k1 < R1; ++k1) {
+      if (n2 * k1 == 0) {
+        t[n2 * R1 + k1] = a[k1];
+      } else {
+        const T c = T(ct_cos2pi(n2 * k1, R)), sn = T(ct_sin2pi(n2 * k1, R));
+        const T s = dir > 0 ? sn : -sn;    // w = exp(dir * 2 pi i n2 k1 / R)
+        t[n2 * R1 + k1] = mk<T>(fma(a[k1].x, c, -a[k1].y * s), fma(a[k1].x, s, a[k1].y * c));
+      }
+    }
+  }
+#pragma unroll
+  for (int k1 = 0; k1 < R1; ++k1) {
+    cpx<T> b[R2];
+#pragma unroll
+    for (int n2 = 0; n2 < R2; ++n2) b[n2] = t[n2 * R1 + k1];
+    dft_reg<T, R2>(b, dir);
+#pragma unroll
+    for (int k2 = 0; k2 < R2; ++k2) v[k1 + R1 * k2] = b[k2];
+  }
+}
+
+template <typename T, int R>
+__device__ __forceinline__ void dft_reg(cpx<T>* v, int dir) {
+  if constexpr (R == 3) {
+    dft3<T>(v, dir);
+  } else if constexpr (R == 5) {
+    dft5<T>(v, dir);
+  } else {
+    constexpr int R1 = ct_first_factor(R);
+    dft_ct<T, R1, R / R1>(v, dir);
+  }
 }
 
 // Generic compile-time radix R from registers, roots from the length-M table W.
@@ -238,20 +324,19 @@ __device__ __forceinline__ void cbfly(const cpx<T>* __restrict__ src, cpx<T>* __
 #pragma unroll
     for (int q = 1; q < R; ++q) v[q] = mulc<T>(v[q], W[q * k * step], dir > 0);
   }
-  if (R == 3) dft3<T>(v, dir);
-  else dft5<T>(v, dir);
+  dft_reg<T, R>(v, dir);
   const int base = (j / Ns) * Ns * R + k;
 #pragma unroll
   for (int q = 0; q < R; ++q) dst[base + q * Ns] = v[q];
 }
 
-template <typename T, int M, int S>
+template <typename T, int M, int S, bool BIG>
 __device__ __forceinline__ cpx<T>* cfft_from(cpx<T>* a, cpx<T>* b, int G, const cpx<T>* W, int dir) {
-  if constexpr (S >= cf_nstages(M)) {
+  if constexpr (S >= cf_nstages(M, BIG)) {
     return a;
   } else {
-    constexpr int R = cf_radix(M, S);
-    constexpr int Ns = cf_ns(M, S);
+    constexpr int R = cf_radix(M, S, BIG);
+    constexpr int Ns = cf_ns(M, S, BIG);
     constexpr int nb = M / R;
     for (int t = threadIdx.x; t < G * nb; t += blockDim.x) {
       const int g = t / nb;
@@ -259,14 +344,16 @@ __device__ __forceinline__ cpx<T>* cfft_from(cpx<T>* a, cpx<T>* b, int G, const 
       cbfly<T, M, R, Ns>(a + g * M, b + g * M, j, W, dir);
     }
     __syncthreads();
-    return cfft_from<T, M, S + 1>(b, a, G, W, dir);
+    return cfft_from<T, M, S + 1, BIG>(b, a, G, W, dir);
   }
 }
 
 // G contiguous pencils of compile-time length M (stride M), ping-pong between a and b.
+// FP32 uses the composite register radices (fewer shared-memory passes); FP64 keeps
+// radices 3 and 5, which need the fewest FP64 operations.
 template <typename T, int M>
 __device__ __forceinline__ cpx<T>* cfft(cpx<T>* a, cpx<T>* b, int G, const cpx<T>* W, int dir) {
-  return cfft_from<T, M, 0>(a, b, G, W, dir);
+  return cfft_from<T, M, 0, (sizeof(T) == 4)>(a, b, G, W, dir);
 }
 
 // Deterministic block sum of one double per thread (fixed tree order).
