@@ -28,6 +28,10 @@
  *     hom_bounds / hom_bounds_batched synchronise `stream` before returning; the
  *     step-level calls (hom_coefficient ... hom_energy) only enqueue work.
  *   - A hom_ctx is bound to one device and is not thread-safe; use one per thread.
+ *   - Small constant tables (twiddles, inclusion tables, DFT bases) stay at the front of a
+ *     workspace between calls on the same context and are not uploaded again while the
+ *     workspace pointer and the problem are unchanged: do not write into a workspace
+ *     between library calls (hand the library a workspace it owns for its lifetime).
  *
  * Axis convention: coordinate x_1 (index 0) is the fastest-varying memory axis.
  *

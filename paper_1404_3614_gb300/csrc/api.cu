@@ -46,6 +46,8 @@ struct hom_ctx {
   // network: DFT bases already uploaded to this workspace for this grid / mode count
   const void* net_bases_ws = nullptr;
   int net_bases_N = 0, net_bases_modes = 0;
+  // single-problem paths: tables already at the front of this workspace for this problem
+  std::vector<unsigned char> tables_key;
   std::vector<long long> graph_key;
   std::vector<std::pair<long long, int>> tuned_cap;   // (key, cap)
 };
@@ -370,7 +372,25 @@ struct Runner {
 
   template <typename X> X* at(size_t off) const { return reinterpret_cast<X*>(base + off); }
 
+  // Twiddle and inclusion tables at the front of the workspace. They are uploaded once per
+  // (workspace, problem) and kept across calls on the same context; other layouts that
+  // use a workspace (batched, network) clear the record.
   hom_status upload_tables() {
+    std::vector<unsigned char> key;
+    auto push = [&](const void* p, size_t n) {
+      const unsigned char* b = static_cast<const unsigned char*>(p);
+      key.insert(key.end(), b, b + n);
+    };
+    const void* wsp = base;
+    push(&wsp, sizeof wsp);
+    push(&g.d, sizeof g.d);
+    push(g.N, sizeof g.N);
+    push(g.Y, sizeof g.Y);
+    push(g.A0, sizeof g.A0);
+    push(&g.ncomp, sizeof g.ncomp);
+    if (!g.incl.empty()) push(g.incl.data(), g.incl.size() * sizeof(hom_inclusion));
+    if (key == ctx->tables_key) return HOM_OK;
+    ctx->tables_key.clear();
     std::vector<double2> w64;
     std::vector<float2> w32;
     for (int a = 0; a < 3; ++a) {
@@ -410,6 +430,7 @@ struct Runner {
         pack_sym(dA, g.d, g.ncomp, D.dA);
       }
     CK(h2d_copy(ctx, base + L.incl, di.data(), di.size() * sizeof(DevIncl), st));
+    ctx->tables_key = key;
     return HOM_OK;
   }
 
@@ -1095,6 +1116,8 @@ hom_status hom_bounds_batched(hom_ctx* ctx, int32_t n, const hom_problem* probs,
   BatchPlan bp;
   CKS(build_batch(ctx, n, probs, opts, bp));
   if (!d_ws || ws_bytes < bp.total) return fail(ctx, HOM_ERR_WORKSPACE, "workspace too small");
+  ctx->tables_key.clear();
+  ctx->net_bases_ws = nullptr;
   if (reinterpret_cast<uintptr_t>(d_ws) % 256) return fail(ctx, HOM_ERR_INVALID_ARG, "workspace must be 256-byte aligned");
   unsigned char* base = static_cast<unsigned char*>(d_ws);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -1436,7 +1459,9 @@ hom_status hom_matvec_noalloc(hom_ctx* ctx, const hom_problem* prob, int32_t sid
   void* scratch = nullptr;
   CKS(noalloc_scratch(ctx, ctx->device, &scratch));
   Runner run{ctx, g, L, static_cast<unsigned char*>(scratch), static_cast<cudaStream_t>(stream), nrhs};
+  ctx->tables_key.clear();   // the static scratch is shared by every context: always upload
   CKS(run.upload_tables());
+  ctx->tables_key.clear();
   const int proj = project ? side + 1 : 0;
   if (precision == HOM_FP64)
     return run.matvec<double>(d_in, d_out, d_coef, proj, nullptr, nullptr, nullptr, 0);
@@ -1485,6 +1510,7 @@ static hom_status net_prepare(hom_ctx* ctx, const NetConfig& c, int batch, void*
                               cudaStream_t st, float** bases, float** rest) {
   if (!d_ws || ws_bytes < net_ws_bytes(c, batch)) return fail(ctx, HOM_ERR_WORKSPACE, "workspace too small");
   float* b = static_cast<float*>(d_ws);
+  ctx->tables_key.clear();
   if (ctx->net_bases_ws != d_ws || ctx->net_bases_N != c.N || ctx->net_bases_modes != c.modes) {
     std::vector<float> hb((size_t)bases_floats(c));
     fill_bases(c, hb.data());
