@@ -41,6 +41,26 @@ TOL = 1e-4
 ORACLE_ITERS = {"primal": 46, "dual": 24}
 FP64_PEAK_TFLOPS = 1.25     # nominal GB300 FP64 (the recipe's table); a probe measured 1.256
 
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one k_xpass<double, 81> launch
+# on the 3D N = 41 cube workload (3 fields, isotropic coefficient), from one ncu capture of
+# the build whose kernel sources hash to `sha256_16`; reported only while they still do.
+XPASS_TRAFFIC = {"sha256_16": "77596041bd40b489", "bytes": 24162304 + 32512,
+                 "sources": ("common.cuh", "kernels.cuh", "passes.cuh", "passes_f64.cu"),
+                 "capture": "profiles/xpass_f64_cube3d_N41.md"}
+
+
+def xpass_traffic(workload_name, precision):
+    """Per-launch DRAM traffic of the FP64 row pass, or None once the kernel has changed."""
+    import hashlib
+    if workload_name != "cube3d_N41" or precision != "fp64":
+        return None
+    h = hashlib.sha256()
+    src = os.path.join(os.path.dirname(os.path.abspath(__file__)), "paper_1404_3614_gb300", "csrc")
+    for f in XPASS_TRAFFIC["sources"]:
+        with open(os.path.join(src, f), "rb") as fh:
+            h.update(fh.read())
+    return XPASS_TRAFFIC["bytes"] if h.hexdigest()[:16] == XPASS_TRAFFIC["sha256_16"] else None
+
 
 WORKLOADS = {
     "cube3d_N41": "3D cube cell N=41^3 (double grid 81^3), contrast 100",
@@ -364,11 +384,16 @@ def run_gpu(args):
     if flops > 0 and per_launch_ms > 0:
         achieved = flops / (per_launch_ms * 1e-3) / 1e12
         roof = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
-                "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
+                "traffic": xpass_traffic(args.workload, args.precision) if dom == "xpass" else None,
                 "flops_per_launch": flops, "launches": dom_n, "avg_launch_ms": per_launch_ms,
                 "peak_note": "FP64 nominal 1.25 TFLOP/s (recipe table); FMA probe measured 1.256"}
         if prec != hb.HOM_FP64:
             roof["note"] = "mixed: dominant family mixes FP32 inner and FP64 outer launches"
+        if roof["traffic"] is not None:
+            roof["traffic_note"] = ("ncu DRAM bytes per launch (" + XPASS_TRAFFIC["capture"] + "): the "
+                                    "input fields and coefficient are read once; the in-place output "
+                                    "stays in L2 during the launch")
 
     line = {
         "metric": METRIC, "value": ms_step, "unit": "ms", "n_gpus": world, "steps": args.steps,
@@ -378,6 +403,7 @@ def run_gpu(args):
         "config": {"workload": WORKLOAD if args.workload == "cube3d_N41" else WORKLOADS[args.workload],
                    "precision": args.precision, "tol": TOL,
                    "l2": "flushed between steps (256 MiB write, outside the timed region)",
+                   "launch": "CG iterations in blocks of 8 replayed from captured CUDA graphs",
                    "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
         "bounds": {"upper_11": float(out["upper"][0, 0]), "lower_11": float(out["lower"][0, 0])},
         "iters": reports[-1]["iters"], "matvecs": reports[-1]["matvecs"],

@@ -104,8 +104,10 @@ typedef struct {
                            criteria", Parseval L2 norm); <= 0 selects 1e-8       */
   int32_t check_every;  /* host polls convergence every k iterations; 0 -> 8     */
   int32_t sides;        /* bit 0: primal (upper), bit 1: dual (lower); 0 -> both */
-  int32_t graph;        /* hom_bounds_batched: replay the batch launch as a CUDA
-                           graph captured on `stream` (needs a non-NULL stream)   */
+  int32_t graph;        /* hom_bounds: 0 or 1 replays blocks of check_every CG
+                           iterations from captured CUDA graphs, -1 launches every
+                           kernel directly; hom_bounds_batched: 1 replays the batch
+                           launch as a graph captured on `stream` (non-NULL)     */
   int32_t autotune;     /* hom_bounds_batched: time the shared-memory chunk sizes
                            on this batch once and keep the fastest in the ctx    */
 } hom_opts;
@@ -302,7 +304,9 @@ hom_status hom_matvec_noalloc(hom_ctx* ctx, const hom_problem* prob, int32_t sid
 /* Kernel timing (CUDA events around each launch of one kernel family on the
  * launching stream). name: "zpass", "ypass", "xpass", "final", "cg", "coef", or ""
  * to disable. hom_kernel_timing returns launches and total milliseconds since the
- * last hom_profile_kernel call (synchronises the events). */
+ * last hom_profile_kernel call (synchronises the events). Inside the CG iteration
+ * graphs of hom_bounds the events are event-record nodes of the graph; each replay
+ * of a graph holding them is waited for and its pairs summed before the call goes on. */
 hom_status hom_profile_kernel(hom_ctx* ctx, const char* name);
 hom_status hom_kernel_timing(hom_ctx* ctx, int64_t* launches, double* total_ms);
 

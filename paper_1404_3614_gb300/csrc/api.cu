@@ -34,6 +34,12 @@ struct hom_ctx {
   std::string prof_family;
   std::vector<cudaEvent_t> ev;         // start/stop pairs
   size_t ev_used = 0;
+  // kernel timing inside captured graphs: event pairs recorded by the graph's own nodes,
+  // read after each replay and summed here
+  std::vector<cudaEvent_t>* capture_events = nullptr;
+  double graph_prof_ms = 0;
+  long long graph_prof_n = 0;
+  bool graph_prof_off = false;
   long long launches = 0;              // kernels launched (since the call began)
   long long h2d = 0, d2h = 0;          // bytes copied
   // batched path: pinned staging, captured graph and autotuned chunk capacities
@@ -48,6 +54,16 @@ struct hom_ctx {
   int net_bases_N = 0, net_bases_modes = 0;
   // single-problem paths: tables already at the front of this workspace for this problem
   std::vector<unsigned char> tables_key;
+  // CG iteration blocks captured as graphs (private capture stream, replayed on the caller's)
+  cudaStream_t cap_stream = nullptr;
+  struct CgGraph {
+    std::vector<unsigned char> key;
+    cudaGraphExec_t exec;
+    long long launches;
+    std::vector<cudaEvent_t> events;   // timing pairs of the profiled kernel family, if any
+  };
+  std::vector<CgGraph> cg_graphs;
+  bool graphs_off = false;
   std::vector<long long> graph_key;
   std::vector<std::pair<long long, int>> tuned_cap;   // (key, cap)
 };
@@ -343,8 +359,23 @@ struct Prof {
   cudaStream_t s;
   bool on;
   cudaEvent_t stop_ev = nullptr;
+  bool ext = false;
   Prof(hom_ctx* c, const char* fam, cudaStream_t st) : ctx(c), s(st), on(false) {
     if (c->prof_family.empty() || c->prof_family != fam) return;
+    if (c->capture_events) {   // being captured: the pair becomes two event-record nodes
+      cudaEvent_t a, b;
+      if (cudaEventCreate(&a) != cudaSuccess) return;
+      if (cudaEventCreate(&b) != cudaSuccess) {
+        cudaEventDestroy(a);
+        return;
+      }
+      c->capture_events->push_back(a);
+      c->capture_events->push_back(b);
+      ext = on = true;
+      cudaEventRecordWithFlags(a, s, cudaEventRecordExternal);
+      stop_ev = b;
+      return;
+    }
     if (c->ev_used + 2 > c->ev.size()) {
       for (int i = 0; i < 256; ++i) {
         cudaEvent_t e;
@@ -358,7 +389,8 @@ struct Prof {
     c->ev_used += 2;
   }
   ~Prof() {
-    if (on) cudaEventRecord(stop_ev, s);
+    if (on && ext) cudaEventRecordWithFlags(stop_ev, s, cudaEventRecordExternal);
+    else if (on) cudaEventRecord(stop_ev, s);
   }
 };
 
@@ -640,6 +672,106 @@ struct Runner {
     return HOM_OK;
   }
 
+  // One CG iteration on R right-hand sides (operator with the p update in its first pass
+  // and p.Cp in its last, alpha, x/r update with r.r, beta), enqueued on `st`.
+  template <typename T>
+  hom_status cg_iteration(CgScalars* cg, const void* coefT, int side, int nfin) {
+    CKS(matvec<T>(base + L.p, base + L.q, coefT, side + 1, cg, base + L.r, base + L.p, 1));
+    Prof pr(ctx, "cg", st);
+    KL(launch_cg_alpha(cg, at<double>(L.partial), L.maxblk, nfin, R, st));
+    KL(launch_cg_update<T>(base + L.x, base + L.r, base + L.p, base + L.q, R, g.d, g.field, g.Nh, cg,
+                           at<double>(L.partial), kVecBlocks, st));
+    KL(launch_cg_beta(cg, at<double>(L.partial), kVecBlocks, kVecBlocks, R, st));
+    return HOM_OK;
+  }
+
+  // K iterations: replayed from a captured graph (captured once per workspace, problem,
+  // side, precision and K on the context's private stream), or launched one by one when
+  // graphs are off or kernel timing is on.
+  template <typename T>
+  hom_status cg_block(CgScalars* cg, const void* coefT, int side, int nfin, int K, bool graphs) {
+    const bool prof = !ctx->prof_family.empty();
+    if (!graphs || ctx->graphs_off || (prof && ctx->graph_prof_off) || K <= 0) {
+      for (int k = 0; k < K; ++k) CKS((cg_iteration<T>(cg, coefT, side, nfin)));
+      return HOM_OK;
+    }
+    std::vector<unsigned char> key = ctx->tables_key;
+    const long long extra[8] = {(long long)side, (long long)sizeof(T), K, (long long)(uintptr_t)coefT,
+                                (long long)(uintptr_t)cg, (long long)L.total, R, nfin};
+    const unsigned char* eb = reinterpret_cast<const unsigned char*>(extra);
+    key.insert(key.end(), eb, eb + sizeof extra);
+    key.insert(key.end(), ctx->prof_family.begin(), ctx->prof_family.end());
+    for (auto& gr : ctx->cg_graphs)
+      if (gr.key == key) {
+        CK(cudaGraphLaunch(gr.exec, st));
+        ctx->launches += gr.launches;
+        return collect_graph_timing(gr);
+      }
+    if (!ctx->cap_stream) CK(cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking));
+    const cudaStream_t saved = st;
+    const long long l0 = ctx->launches;
+    std::vector<cudaEvent_t> events;
+    st = ctx->cap_stream;
+    CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+    ctx->capture_events = &events;
+    hom_status s = HOM_OK;
+    for (int k = 0; k < K && s == HOM_OK; ++k) s = cg_iteration<T>(cg, coefT, side, nfin);
+    ctx->capture_events = nullptr;
+    cudaGraph_t graph = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(st, &graph);
+    st = saved;
+    const long long per = ctx->launches - l0;
+    ctx->launches = l0;
+    if (s != HOM_OK || e != cudaSuccess)
+      for (cudaEvent_t ev : events) cudaEventDestroy(ev);
+    if (s != HOM_OK) {
+      if (graph) cudaGraphDestroy(graph);
+      return s;
+    }
+    cudaGraphExec_t exec = nullptr;
+    cudaError_t ei = e;
+    if (e == cudaSuccess) {
+      ei = cudaGraphInstantiate(&exec, graph, 0);
+      cudaGraphDestroy(graph);
+    }
+    if (ei != cudaSuccess) {   // capture not possible here: launch this context's kernels directly
+      cudaGetLastError();
+      if (e == cudaSuccess)
+        for (cudaEvent_t ev : events) cudaEventDestroy(ev);
+      if (prof) ctx->graph_prof_off = true;
+      else ctx->graphs_off = true;
+      for (int k = 0; k < K; ++k) CKS((cg_iteration<T>(cg, coefT, side, nfin)));
+      return HOM_OK;
+    }
+    if (ctx->cg_graphs.size() >= 8) {
+      cudaGraphExecDestroy(ctx->cg_graphs.front().exec);
+      for (cudaEvent_t ev : ctx->cg_graphs.front().events) cudaEventDestroy(ev);
+      ctx->cg_graphs.erase(ctx->cg_graphs.begin());
+    }
+    ctx->cg_graphs.push_back({key, exec, per, std::move(events)});
+    CK(cudaGraphLaunch(exec, st));
+    ctx->launches += per;
+    return collect_graph_timing(ctx->cg_graphs.back());
+  }
+
+  // Timing pairs recorded by a replayed graph: wait for the replay, sum the pairs into the
+  // context's kernel timing (the next replay reuses the same events).
+  hom_status collect_graph_timing(const hom_ctx::CgGraph& gr) {
+    if (gr.events.empty()) return HOM_OK;
+    CK(cudaStreamSynchronize(st));
+    for (size_t i = 0; i + 1 < gr.events.size(); i += 2) {
+      float ms = 0;
+      if (cudaEventElapsedTime(&ms, gr.events[i], gr.events[i + 1]) != cudaSuccess) {
+        cudaGetLastError();
+        ctx->graph_prof_off = true;   // no timing from graph nodes here: profile without graphs
+        return HOM_OK;
+      }
+      ctx->graph_prof_ms += ms;
+      ctx->graph_prof_n += 1;
+    }
+    return HOM_OK;
+  }
+
   template <typename T>
   hom_status solve_side(int side, const hom_opts& o, hom_report* rep, int* matvecs) {
     const size_t elem = sizeof(T) * 2;
@@ -667,22 +799,16 @@ struct Runner {
     CK(cudaStreamSynchronize(st));
     bool any = false;
     for (int r = 0; r < R; ++r) any = any || ctx->host_cg->active[r];
-    for (int it = 0; any && it < maxit; ++it) {
-      CKS(matvec<T>(base + L.p, base + L.q, coefT, side + 1, cg, base + L.r, base + L.p, 1));
-      {
-        Prof pr(ctx, "cg", st);
-        KL(launch_cg_alpha(cg, at<double>(L.partial), L.maxblk, nfin, R, st));
-        KL(launch_cg_update<T>(base + L.x, base + L.r, base + L.p, base + L.q, R, g.d, g.field, g.Nh, cg,
-                               at<double>(L.partial), kVecBlocks, st));
-        KL(launch_cg_beta(cg, at<double>(L.partial), kVecBlocks, kVecBlocks, R, st));
-      }
-      ++*matvecs;
-      if ((it + 1) % every == 0 || it + 1 == maxit) {
-        CK(d2h_copy(ctx, ctx->host_cg, cg, sizeof(CgScalars), st));
-        CK(cudaStreamSynchronize(st));
-        any = false;
-        for (int r = 0; r < R; ++r) any = any || ctx->host_cg->active[r];
-      }
+    const bool graphs = o.graph >= 0;
+    for (int it = 0; any && it < maxit;) {
+      const int K = std::min(every, maxit - it);
+      CKS((cg_block<T>(cg, coefT, side, nfin, K, graphs)));
+      *matvecs += K;
+      it += K;
+      CK(d2h_copy(ctx, ctx->host_cg, cg, sizeof(CgScalars), st));
+      CK(cudaStreamSynchronize(st));
+      any = false;
+      for (int r = 0; r < R; ++r) any = any || ctx->host_cg->active[r];
     }
     CK(d2h_copy(ctx, ctx->host_cg, cg, sizeof(CgScalars), st));
     CK(cudaStreamSynchronize(st));
@@ -758,23 +884,15 @@ hom_status Runner_solve_mixed(Runner& run, int side, const hom_opts& o, hom_repo
     CK(cudaStreamSynchronize(st));
     bool ia = false;
     for (int r = 0; r < R; ++r) ia = ia || ctx->host_cg->active[r];
-    for (int it = 0; ia && used < maxit; ++it) {
-      CKS(run.matvec<float>(base + L.p, base + L.q, coef32, side + 1, inner, base + L.r, base + L.p, 1));
-      {
-        Prof pr(ctx, "cg", st);
-        KL(launch_cg_alpha(inner, partial, L.maxblk, nfin32, R, st));
-        KL(launch_cg_update<float>(base + L.x, base + L.r, base + L.p, base + L.q, R, g.d, g.field, g.Nh,
-                                   inner, partial, kVecBlocks, st));
-        KL(launch_cg_beta(inner, partial, kVecBlocks, kVecBlocks, R, st));
-      }
-      ++*matvecs;
-      ++used;
-      if ((it + 1) % every == 0 || used >= maxit) {
-        CK(d2h_copy(ctx, ctx->host_cg, inner, sizeof(CgScalars), st));
-        CK(cudaStreamSynchronize(st));
-        ia = false;
-        for (int r = 0; r < R; ++r) ia = ia || ctx->host_cg->active[r];
-      }
+    while (ia && used < maxit) {
+      const int K = std::min(every, maxit - used);
+      CKS((run.cg_block<float>(inner, coef32, side, nfin32, K, o.graph >= 0)));
+      *matvecs += K;
+      used += K;
+      CK(d2h_copy(ctx, ctx->host_cg, inner, sizeof(CgScalars), st));
+      CK(cudaStreamSynchronize(st));
+      ia = false;
+      for (int r = 0; r < R; ++r) ia = ia || ctx->host_cg->active[r];
     }
     CK(d2h_copy(ctx, ctx->host_cg, inner, sizeof(CgScalars), st));
     CK(cudaStreamSynchronize(st));
@@ -992,6 +1110,11 @@ hom_status hom_destroy(hom_ctx* ctx) {
   if (ctx->pin_out) cudaFreeHost(ctx->pin_out);
   if (ctx->graph_exec) cudaGraphExecDestroy(ctx->graph_exec);
   if (ctx->graph) cudaGraphDestroy(ctx->graph);
+  for (auto& gr : ctx->cg_graphs) {
+    cudaGraphExecDestroy(gr.exec);
+    for (cudaEvent_t ev : gr.events) cudaEventDestroy(ev);
+  }
+  if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
   delete ctx;
   return HOM_OK;
 }
@@ -1472,6 +1595,8 @@ hom_status hom_profile_kernel(hom_ctx* ctx, const char* name) {
   if (!ctx) return HOM_ERR_INVALID_ARG;
   ctx->prof_family = name ? name : "";
   ctx->ev_used = 0;
+  ctx->graph_prof_ms = 0;
+  ctx->graph_prof_n = 0;
   return HOM_OK;
 }
 
@@ -1484,9 +1609,11 @@ hom_status hom_kernel_timing(hom_ctx* ctx, int64_t* launches, double* total_ms) 
     CK(cudaEventElapsedTime(&ms, ctx->ev[i], ctx->ev[i + 1]));
     tot += ms;
   }
-  if (launches) *launches = (int64_t)(ctx->ev_used / 2);
-  if (total_ms) *total_ms = tot;
+  if (launches) *launches = (int64_t)(ctx->ev_used / 2) + ctx->graph_prof_n;
+  if (total_ms) *total_ms = tot + ctx->graph_prof_ms;
   ctx->ev_used = 0;
+  ctx->graph_prof_ms = 0;
+  ctx->graph_prof_n = 0;
   return HOM_OK;
 }
 

@@ -416,6 +416,10 @@ template <typename T> int pencil_xc(int M, int X, int C) {
   if (xc < 1) xc = (fixed + per <= kPassSmemMax) ? 1 : 0;
   if (xc > 32) xc = 32;
   if (xc > X) xc = X;
+  if (xc >= 1) {   // balance the chunks: the same number of chunks, as equal as possible
+    const long long nch = (X + xc - 1) / xc;
+    xc = (X + nch - 1) / nch;
+  }
   return (int)xc;
 }
 
@@ -430,6 +434,10 @@ template <typename T> int xpass_yb(int M, int rpp, int planes) {
   }
   if (yb > 32) yb = 32;
   if (yb > planes) yb = planes;
+  if (yb >= 1) {
+    const long long nch = (planes + yb - 1) / yb;
+    yb = (planes + nch - 1) / nch;
+  }
   return (int)yb;
 }
 

@@ -21,6 +21,14 @@ def test_oracle_iteration_counts_pinned():
         assert it == bench.ORACLE_ITERS[side] and res <= bench.TOL
 
 
+def test_traffic_reported_only_for_the_captured_kernel(monkeypatch):
+    """The ncu DRAM figure is tied to the row-pass sources it was captured on."""
+    assert bench.xpass_traffic("spheres3d_N113", "fp64") is None
+    assert bench.xpass_traffic("cube3d_N41", "mixed") is None
+    monkeypatch.setitem(bench.XPASS_TRAFFIC, "sha256_16", "0" * 16)
+    assert bench.xpass_traffic("cube3d_N41", "fp64") is None
+
+
 def test_flop_model():
     p = ms.cube_inclusion_3d()
     assert bench.fft_flops(1) == 0.0

@@ -98,6 +98,33 @@ def test_repeatable_bitwise(hb, solver):
     assert a["report"]["iters"] == b["report"]["iters"]
 
 
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_graph_replay_matches_direct_launches(hb, solver, prec):
+    """CG iteration blocks replayed from captured graphs run the same kernels in the same
+    order as direct launches: bitwise equal bounds, equal iterations and launch counts,
+    also for a check interval that does not divide the iteration count and when the
+    kernel timing records event nodes inside the graphs."""
+    precision = hb.HOM_FP64 if prec == "fp64" else hb.HOM_MIXED
+    p = ms.random_anisotropic_3d(5, N=9)
+    for every in (8, 5):
+        d = solver(p, precision=precision, tol=1e-9, check_every=every, graph=-1)
+        g1 = solver(p, precision=precision, tol=1e-9, check_every=every, graph=0)
+        g2 = solver(p, precision=precision, tol=1e-9, check_every=every, graph=0)
+        for out in (g1, g2):
+            assert np.array_equal(out["upper"], d["upper"]) and np.array_equal(out["lower"], d["lower"])
+            assert out["report"]["iters"] == d["report"]["iters"]
+            assert out["report"]["launches"] == d["report"]["launches"]
+    counts = {}
+    for graph in (-1, 0, 0):
+        hb.hom_profile_kernel(solver.ctx, "xpass")
+        solver(p, precision=precision, tol=1e-9, graph=graph)
+        n, ms_ = hb.hom_kernel_timing(solver.ctx)
+        hb.hom_profile_kernel(solver.ctx, "")
+        assert ms_ > 0
+        counts.setdefault(graph, []).append(n)
+    assert counts[0] == [counts[-1][0]] * 2
+
+
 def test_not_converged_still_bounds(hb, solver):
     """max_iter reached: HOM_WARN_NOT_CONVERGED, the bounds stay guaranteed (Lemma bounds)."""
     p = ms.paper_square_2d(15, 1000.0)
