@@ -45,7 +45,7 @@ def bases(N, modes):
     ky = torch.tensor([i if i < K else i - K1 for i in range(K1)], dtype=torch.float64)
     ax = 2 * math.pi * torch.outer(kx, x) / N                 # [K, N]
     ay = 2 * math.pi * torch.outer(ky, x) / N                 # [K1, N]
-    w = torch.where(kx == 0, 1.0, 2.0) / (N * N)
+    w = torch.where(kx == 0, torch.ones_like(kx), 2.0 * torch.ones_like(kx)) / (N * N)
     return {"Fr": torch.cos(ax), "Fi": -torch.sin(ax), "Gc": torch.cos(ay), "Gs": torch.sin(ay),
             "Hc": torch.cos(ay).T, "Hs": torch.sin(ay).T, "Er": (w[:, None] * torch.cos(ax)).T,
             "Ei": (-w[:, None] * torch.sin(ax)).T}
