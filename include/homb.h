@@ -110,6 +110,13 @@ typedef struct {
                            launch as a graph captured on `stream` (non-NULL)     */
   int32_t autotune;     /* hom_bounds_batched: time the shared-memory chunk sizes
                            on this batch once and keep the fastest in the ctx    */
+  int32_t dual_start;   /* hom_bounds with both sides: 0 starts the dual CG from
+                           zero; 1 starts it from the primal minimisers (Remark
+                           "Avoiding the solution of dual formulation", Eq.
+                           FD_superposition_odd_A): j0 = Gamma^J[A sum_a E_a
+                           (e_a + e^(a))], E = inv(upper) e_b, through the
+                           double-grid operator of the primal coefficient. Any
+                           start in J_N keeps the lower bound guaranteed.        */
 } hom_opts;
 
 typedef struct {

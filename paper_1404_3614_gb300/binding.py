@@ -41,7 +41,7 @@ class hom_problem(C.Structure):
 class hom_opts(C.Structure):
     _fields_ = [("precision", C.c_int32), ("max_iter", C.c_int32), ("tol", C.c_double),
                 ("check_every", C.c_int32), ("sides", C.c_int32), ("graph", C.c_int32),
-                ("autotune", C.c_int32)]
+                ("autotune", C.c_int32), ("dual_start", C.c_int32)]
 
 
 class hom_report(C.Structure):
@@ -195,10 +195,11 @@ def hom_problem_info(ctx, problem):
     return {"ncomp": ncomp.value, "M": list(M), "field_elems": fe.value, "grid_elems": ge.value}
 
 
-def make_opts(precision=HOM_FP64, tol=1e-8, max_iter=10000, check_every=8, sides=3, graph=0, autotune=0):
+def make_opts(precision=HOM_FP64, tol=1e-8, max_iter=10000, check_every=8, sides=3, graph=0, autotune=0,
+              dual_start=0):
     o = hom_opts()
     o.precision, o.tol, o.max_iter, o.check_every, o.sides = precision, tol, max_iter, check_every, sides
-    o.graph, o.autotune = graph, autotune
+    o.graph, o.autotune, o.dual_start = graph, autotune, dual_start
     return o
 
 

@@ -772,8 +772,38 @@ struct Runner {
     return HOM_OK;
   }
 
+  // Start of the dual CG from the primal minimisers (Remark "Avoiding the solution of
+  // dual formulation", Eq. FD_superposition_odd_A): for each b, u_b = sum_a E_a (e_a +
+  // e^(a)) with E = inv(Abar) e_b (Abar = the primal energy matrix, the upper bound), and
+  // j0_b = Gamma^J P_N F_M (A_M/|M|) F_M^{-1} Pad(u_b) with the primal coefficient. Needs
+  // the re-projected primal fields in x64, the primal coefficient in coef64 and the primal
+  // energies in eout[0..]; writes the FP64 starts to `out`. *ok = false (and nothing
+  // written) when the primal energy matrix is not SPD.
+  hom_status dual_start(double2* out, bool* ok, int* matvecs) {
+    *ok = false;
+    CK(d2h_copy(ctx, ctx->host_e, at<double>(L.eout), 9 * sizeof(double), st));
+    CK(cudaStreamSynchronize(st));
+    const int d = g.d;
+    const double invM = 1.0 / (double)g.grid;
+    double A[9] = {}, Ai[9] = {};
+    for (int i = 0; i < d; ++i)
+      for (int j = 0; j < d; ++j) A[3 * i + j] = 0.5 * (ctx->host_e[d * i + j] + ctx->host_e[d * j + i]) * invM;
+    if (!spd(A, d)) return HOM_OK;
+    inv3(A, d, Ai);
+    double c[9] = {};   // c[b][a] = (inv(Abar) e_b)_a
+    for (int b = 0; b < R; ++b)
+      for (int a = 0; a < d; ++a) c[3 * b + a] = Ai[3 * a + b];
+    double2* x64 = at<double2>(L.x64);
+    KL(launch_combine_fields(x64, R, d, g.field, c, st));
+    CKS(matvec<double>(x64, out, at<double>(L.coef64), 2, nullptr, nullptr, nullptr, 0));
+    ++*matvecs;
+    *ok = true;
+    return HOM_OK;
+  }
+
   template <typename T>
-  hom_status solve_side(int side, const hom_opts& o, hom_report* rep, int* matvecs) {
+  hom_status solve_side(int side, const hom_opts& o, hom_report* rep, int* matvecs,
+                        const double2* x0 = nullptr) {
     const size_t elem = sizeof(T) * 2;
     double* coef64 = at<double>(L.coef64);
     CKS(build_coefficient(side, coef64));
@@ -783,17 +813,24 @@ struct Runner {
       coefT = at<float>(L.coef32);
     }
     const size_t fb = (size_t)R * g.d * g.field * elem;
-    CK(cudaMemsetAsync(base + L.x, 0, fb, st));
+    if (x0 && sizeof(T) == 8) CK(cudaMemcpyAsync(base + L.x, x0, fb, cudaMemcpyDeviceToDevice, st));
+    else CK(cudaMemsetAsync(base + L.x, 0, fb, st));
     CK(cudaMemsetAsync(base + L.p, 0, fb, st));
     CgScalars* cg = at<CgScalars>(L.cg[side]);
     SpecArgs sa = spec_args(side);
     const int N3[3] = {g.N[0], g.N[1], g.N[2]};
     KL(launch_rhs<T>(sa, side, R, g.Nh, N3, base + L.r, at<double>(L.partial), kVecBlocks, st));
     const double tol = o.tol > 0 ? o.tol : 1e-8;
-    KL(launch_cg_init(cg, at<double>(L.partial), kVecBlocks, kVecBlocks, R, tol * tol, 0.0, 0, st));
+    const int nfin = final_blocks(elem);
+    if (x0 && sizeof(T) == 8) {   // r0 = b - C x0 (in place over b), |r0|^2 partials
+      CKS(matvec<T>(base + L.x, base + L.r, coefT, side + 1, nullptr, nullptr, nullptr, 0, base + L.r));
+      ++*matvecs;
+      KL(launch_cg_init(cg, at<double>(L.partial), L.maxblk, nfin, R, tol * tol, 0.0, 0, st));
+    } else {
+      KL(launch_cg_init(cg, at<double>(L.partial), kVecBlocks, kVecBlocks, R, tol * tol, 0.0, 0, st));
+    }
     const int maxit = o.max_iter > 0 ? o.max_iter : 10000;
     const int every = o.check_every > 0 ? o.check_every : 8;
-    const int nfin = final_blocks(elem);
     // an initial poll avoids work when b = 0 (homogeneous cells)
     CK(d2h_copy(ctx, ctx->host_cg, cg, sizeof(CgScalars), st));
     CK(cudaStreamSynchronize(st));
@@ -838,7 +875,8 @@ struct Runner {
 // scalars (alpha, beta, r.r, p.Cp) are FP64 reductions of FP32 products. The outer loop
 // stops at |r64| <= tol |E| or when a step fails to halve |r64|; any field is a valid
 // conforming test field after the FP64 re-projection, so the bounds stay guaranteed.
-hom_status Runner_solve_mixed(Runner& run, int side, const hom_opts& o, hom_report* rep, int* matvecs) {
+hom_status Runner_solve_mixed(Runner& run, int side, const hom_opts& o, hom_report* rep, int* matvecs,
+                              bool warm = false) {
   hom_ctx* ctx = run.ctx;
   const Geometry& g = run.g;
   const Layout& L = run.L;
@@ -858,14 +896,22 @@ hom_status Runner_solve_mixed(Runner& run, int side, const hom_opts& o, hom_repo
   SpecArgs sa = run.spec_args(side);
   const int N3[3] = {g.N[0], g.N[1], g.N[2]};
   double* partial = run.at<double>(L.partial);
-  KL(launch_rhs<double>(sa, side, R, g.Nh, N3, b64, partial, kVecBlocks, st));
   const double tol = o.tol > 0 ? o.tol : 1e-8;
-  KL(launch_cg_init(outer, partial, kVecBlocks, kVecBlocks, R, tol * tol, 0.0, 0, st));
-  CK(cudaMemcpyAsync(r64, b64, n * sizeof(double2), cudaMemcpyDeviceToDevice, st));
-  CK(cudaMemsetAsync(x64, 0, n * sizeof(double2), st));
+  const int nfin32 = run.final_blocks(8), nfin64 = run.final_blocks(16);
+  if (warm) {   // the start is in b64 (Runner::dual_start): x64 = start, r64 = b - C x64
+    CK(cudaMemcpyAsync(x64, b64, n * sizeof(double2), cudaMemcpyDeviceToDevice, st));
+    KL(launch_rhs<double>(sa, side, R, g.Nh, N3, b64, partial, kVecBlocks, st));
+    CKS(run.matvec<double>(x64, r64, coef64, side + 1, nullptr, nullptr, nullptr, 0, b64));
+    ++*matvecs;
+    KL(launch_cg_init(outer, partial, L.maxblk, nfin64, R, tol * tol, 0.0, 0, st));
+  } else {
+    KL(launch_rhs<double>(sa, side, R, g.Nh, N3, b64, partial, kVecBlocks, st));
+    KL(launch_cg_init(outer, partial, kVecBlocks, kVecBlocks, R, tol * tol, 0.0, 0, st));
+    CK(cudaMemcpyAsync(r64, b64, n * sizeof(double2), cudaMemcpyDeviceToDevice, st));
+    CK(cudaMemsetAsync(x64, 0, n * sizeof(double2), st));
+  }
   const int maxit = o.max_iter > 0 ? o.max_iter : 10000;
   const int every = o.check_every > 0 ? o.check_every : 8;
-  const int nfin32 = run.final_blocks(8), nfin64 = run.final_blocks(16);
   const double eta = 1e-5;
   int used = 0;
   int inner_iters[3] = {0, 0, 0};
@@ -1176,10 +1222,13 @@ hom_status hom_bounds(hom_ctx* ctx, const hom_problem* prob, const hom_opts* opt
   const int sides = opts->sides ? opts->sides : 3;
   int matvecs = 0;
   hom_status worst = HOM_OK;
+  bool warm = false;
   for (int side = 0; side < 2; ++side) {
     if (!(sides & (1 << side))) continue;
-    hom_status s = elem == 16 ? run.solve_side<double>(side, *opts, rep, &matvecs)
-                              : Runner_solve_mixed(run, side, *opts, rep, &matvecs);
+    double2* x0 = elem == 16 ? run.at<double2>(run.L.q) : run.at<double2>(run.L.b64);
+    if (side == 1 && (sides & 3) == 3 && opts->dual_start == 1) CKS(run.dual_start(x0, &warm, &matvecs));
+    hom_status s = elem == 16 ? run.solve_side<double>(side, *opts, rep, &matvecs, warm ? x0 : nullptr)
+                              : Runner_solve_mixed(run, side, *opts, rep, &matvecs, warm);
     if (s < 0) return s;
     if (s == HOM_WARN_NOT_CONVERGED) worst = s;
   }

@@ -298,6 +298,27 @@ __global__ void k_promote_add(const float2* x32, double2* x64, long long n) {
   }
 }
 
+// In place over nrhs FP64 fields of d components: u_b = sum_a c[b][a] (e_a + x_a), the
+// constant e_a sitting at k = 0 of component a (the superposition of Eq.
+// FD_superposition_odd_A).
+__global__ void k_combine_fields(double2* x, int nrhs, int d, long long field, Coef3 c) {
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < d * field;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int comp = (int)(t / field);
+    const long long e = t - comp * field;
+    double2 v[3], o[3];
+    for (int a = 0; a < nrhs; ++a) v[a] = x[((long long)a * d + comp) * field + e];
+    for (int b = 0; b < nrhs; ++b) {
+      o[b] = make_double2(e == 0 ? c.v[3 * b + comp] : 0.0, 0.0);
+      for (int a = 0; a < nrhs; ++a) {
+        o[b].x = fma(c.v[3 * b + a], v[a].x, o[b].x);
+        o[b].y = fma(c.v[3 * b + a], v[a].y, o[b].y);
+      }
+    }
+    for (int b = 0; b < nrhs; ++b) x[((long long)b * d + comp) * field + e] = o[b];
+  }
+}
+
 template <typename T>
 __global__ void k_project_promote(const cpx<T>* x, double2* x64, int nrhs, int d, int Ny, int Nz,
                                   int Nh, double iy0, double iy1, double iy2, int side) {
@@ -432,6 +453,17 @@ cudaError_t launch_project_promote(const void* x, double2* x64, int nrhs, int d,
   if (blocks > 152 * 32) blocks = 152 * 32;
   k_project_promote<T><<<(int)blocks, kThreads, 0, s>>>(reinterpret_cast<const cpx<T>*>(x), x64, nrhs,
                                                         d, Ny, Nz, Nh, invY[0], invY[1], invY[2], side);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_combine_fields(double2* x, int nrhs, int d, long long field, const double* c,
+                                  cudaStream_t s) {
+  if (nrhs < 1 || nrhs > 3 || d < 1 || d > 3) return cudaErrorInvalidValue;
+  Coef3 cc;
+  for (int i = 0; i < 9; ++i) cc.v[i] = c[i];
+  long long blocks = (d * field + kThreads - 1) / kThreads;
+  if (blocks > 152 * 32) blocks = 152 * 32;
+  k_combine_fields<<<(int)blocks, kThreads, 0, s>>>(x, nrhs, d, field, cc);
   return cudaGetLastError();
 }
 

@@ -188,6 +188,10 @@ cudaError_t launch_cg_alpha(CgScalars* cg, const double* partial, int ld, int nb
                             cudaStream_t s);
 cudaError_t launch_cg_beta(CgScalars* cg, const double* partial, int ld, int nblk, int nrhs,
                            cudaStream_t s);
+struct Coef3 { double v[9]; };   // 3 x 3 row-major coefficients passed by value
+// u_b = sum_a c[b*3+a] (e_a + x_a) in place over nrhs FP64 fields of d components
+cudaError_t launch_combine_fields(double2* x, int nrhs, int d, long long field, const double* c,
+                                  cudaStream_t s);
 // x64 = Gamma (double) x_T (in place allowed for T = double)
 template <typename T>
 cudaError_t launch_project_promote(const void* x, double2* x64, int nrhs, int d, int Ny, int Nz,
