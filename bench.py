@@ -215,6 +215,9 @@ def family_flops_per_launch(problem, family: str, nrhs: int) -> float:
         return RC * (N[1] * Nh * fft_flops(M[2]) if d == 3 else Nh * fft_flops(M[1]))
     if family == "ypass":
         return RC * M[2] * Nh * fft_flops(M[1])
+    if family == "slab":    # fused inverse y, x row pass and forward y
+        return (2 * family_flops_per_launch(problem, "ypass", nrhs)
+                + family_flops_per_launch(problem, "xpass", nrhs))
     return 0.0
 
 
@@ -312,7 +315,7 @@ def run_gpu(args):
 
     # dominant kernel family: one untimed profiled step per family
     fam_ms = {}
-    for fam in ("xpass", "ypass", "zpass", "final", "cg", "coef", "energy"):
+    for fam in ("slab", "xpass", "ypass", "zpass", "final", "cg", "coef", "energy"):
         hb.hom_profile_kernel(solver.ctx, fam)
         step(prec)
         n, ms = hb.hom_kernel_timing(solver.ctx)

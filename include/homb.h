@@ -308,8 +308,15 @@ hom_status hom_matvec_noalloc(hom_ctx* ctx, const hom_problem* prob, int32_t sid
                               int32_t precision, int32_t project, int32_t nrhs,
                               const void* d_coef, const void* d_in, void* d_out, void* stream);
 
+/* The 3D operator with an isotropic coefficient and equal x and y transform lengths
+ * M = R * R (R in 3, 5, 9, 15) fuses the inverse y transforms, the x row pass and the
+ * forward y transforms into one pass over (rhs, component, z) slabs held in shared memory
+ * (enable != 0, the default). enable = 0 runs them as three separate passes; the results
+ * agree to rounding. Applies to later calls on this context. */
+hom_status hom_set_slab_pass(hom_ctx* ctx, int32_t enable);
+
 /* Kernel timing (CUDA events around each launch of one kernel family on the
- * launching stream). name: "zpass", "ypass", "xpass", "final", "cg", "coef", or ""
+ * launching stream). name: "zpass", "ypass", "xpass", "slab", "final", "cg", "coef", or ""
  * to disable. hom_kernel_timing returns launches and total milliseconds since the
  * last hom_profile_kernel call (synchronises the events). Inside the CG iteration
  * graphs of hom_bounds the events are event-record nodes of the graph; each replay

@@ -64,6 +64,7 @@ struct hom_ctx {
   };
   std::vector<CgGraph> cg_graphs;
   bool graphs_off = false;
+  bool slab_on = true;   // fused y-x-y slab pass where it applies
   std::vector<long long> graph_key;
   std::vector<std::pair<long long, int>> tuned_cap;   // (key, cap)
 };
@@ -567,6 +568,17 @@ struct Runner {
       KL(launch_pencil<T>(z, st));
       ycur = T1;
     }
+    const void* fin = T2;
+    if (g.d == 3 && g.ncomp == 1 && g.M[0] == g.M[1] && ctx->slab_on && slab_warps<T>(g.M[0], Nh) > 0) {
+      // fused inverse y, x row pass and forward y on each (rhs, comp, z) slab of T1
+      Prof pr(ctx, "slab", st);
+      SlabArgs sl{};
+      sl.in = T1; sl.out = T1; sl.coef = coef; sl.W = W(0); sl.cg = cg;
+      sl.nrc = R * C; sl.C = C; sl.Mz = Mz; sl.M = Mx; sl.Ny = Ny; sl.Nh = Nh;
+      sl.scale = 1.0 / (double)g.grid;
+      KL(launch_slab<T>(sl, st));
+      fin = T1;
+    } else {
     {
       Prof pr(ctx, "ypass", st);
       PencilArgs y{};
@@ -591,7 +603,6 @@ struct Runner {
       if (x.YB < 1) return fail(ctx, HOM_ERR_INVALID_ARG, "grid too large for the shared-memory FFT");
       KL(launch_xpass<T>(x, R, st));
     }
-    const void* fin = T2;
     if (g.d == 3) {
       Prof pr(ctx, "ypass", st);
       PencilArgs y{};
@@ -603,6 +614,7 @@ struct Runner {
       y.W = W(1); y.plan = g.plan[1]; y.cg = cg;
       KL(launch_pencil<T>(y, st));
       fin = T1;
+    }
     }
     {
       Prof pr(ctx, "final", st);
@@ -1638,6 +1650,12 @@ hom_status hom_matvec_noalloc(hom_ctx* ctx, const hom_problem* prob, int32_t sid
   if (precision == HOM_FP64)
     return run.matvec<double>(d_in, d_out, d_coef, proj, nullptr, nullptr, nullptr, 0);
   return run.matvec<float>(d_in, d_out, d_coef, proj, nullptr, nullptr, nullptr, 0);
+}
+
+hom_status hom_set_slab_pass(hom_ctx* ctx, int32_t enable) {
+  if (!ctx) return HOM_ERR_INVALID_ARG;
+  ctx->slab_on = enable != 0;
+  return HOM_OK;
 }
 
 hom_status hom_profile_kernel(hom_ctx* ctx, const char* name) {

@@ -71,6 +71,17 @@ struct XArgs {
   FastDiv fd_Nin, fd_Nout, fd_rpp;   // set by the launcher
 };
 
+// fused y-x-y slab pass (3D, isotropic coefficient, M = R * R on x and y)
+struct SlabArgs {
+  const void* in;       // [nrc][Mz][Ny][Nh] half spectra after the z inverse transform
+  void* out;            // same layout (may equal in)
+  const void* coef;     // real [Mz][M][M]
+  const void* W;        // twiddles w_M^j, j < M
+  const CgScalars* cg;  // skip right-hand sides that have converged (may be NULL)
+  int nrc, C, Mz, M, Ny, Nh;
+  double scale;         // 1 / |M|
+};
+
 struct DevIncl {
   int shape;       // 0 box, 1 ball / disk
   int same_as_prev;// 1 when shape and size equal the previous inclusion's (radial reuse)
@@ -158,6 +169,9 @@ template <typename T> cudaError_t launch_final(const FinalArgs& a, cudaStream_t 
 template <typename T> cudaError_t launch_xpass(const XArgs& a, int grid_y, cudaStream_t s);
 template <typename T> int pencil_xc(int M, int X, int C);   // chunk that fits shared memory
 template <typename T> int xpass_yb(int M, int rows_per_plane, int planes);
+// fused y-x-y slab pass; cudaErrorNotSupported when the length or size does not apply
+template <typename T> cudaError_t launch_slab(const SlabArgs& a, cudaStream_t s);
+template <typename T> int slab_warps(int M, int Nh);   // 0: slab pass not applicable
 
 cudaError_t launch_axis_tables(int nincl, int d, const int* M, int Mmax, const double* invY,
                                const DevIncl* incl, double2* phase, double* sinc, cudaStream_t s);

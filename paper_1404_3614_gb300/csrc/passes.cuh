@@ -537,7 +537,13 @@ cudaError_t launch_fft_batch(const void* in, void* out, int M, int howmany, int 
   }
 }
 
+}  // namespace homb
+#include "slab.cuh"
+namespace homb {
+
 #define HOMB_INST_PASSES(T)                                                           \
+  template cudaError_t launch_slab<T>(const SlabArgs&, cudaStream_t);                 \
+  template int slab_warps<T>(int, int);                                               \
   template cudaError_t launch_pencil<T>(const PencilArgs&, cudaStream_t);             \
   template cudaError_t launch_final<T>(const FinalArgs&, cudaStream_t);               \
   template cudaError_t launch_xpass<T>(const XArgs&, int, cudaStream_t);              \

@@ -56,6 +56,10 @@ PROBLEMS = {
     "aniso2d_N203x41_M405x81": lambda: ms.make_problem(2, (203, 41), (1.0, 0.5), np.array([[1.5, 0.2], [0.2, 0.8]]),
                                                        [ms.box((0.0, 0.1), (0.4, 0.2), 9.0, 2)]),
     "cube3d_N23_M45": lambda: ms.cube_inclusion_3d(N=23),
+    # isotropic 3D cells with M = R^2 on x and y: the fused y-x-y slab pass
+    "spheres3d_N5_M9": lambda: ms.random_spheres_3d(3, N=5, n_balls=3, phi=0.2, contrast=20.0),
+    "cube3d_N13_M25": lambda: ms.cube_inclusion_3d(N=13),
+    "spheres3d_N41_M81": lambda: ms.random_spheres_3d(4, N=41, n_balls=6, phi=0.25, contrast=100.0),
 }
 
 
@@ -191,3 +195,37 @@ def test_invalid_inputs_rejected(hb, ctx):
     with pytest.raises(hb.HombError) as e:
         hb.hom_bounds(ctx, p5, opts, ws.data_ptr(), n - 1024)
     assert e.value.status == hb.binding.HOM_ERR_WORKSPACE
+
+
+@pytest.mark.parametrize("N,prec", [(5, "fp32"), (13, "fp32"), (41, "fp32"), (113, "fp32"), (41, "fp64")])
+def test_slab_pass_matches_separate_passes(hb, ctx, N, prec):
+    """The fused y-x-y slab pass (FP32) and the three separate passes compute the same
+    operator: equal to rounding (2e-6 relative to the largest entry) at M = 9, 25, 81, 225.
+    FP64 always takes the separate passes: switching the slab pass makes no difference."""
+    p = ms.random_spheres_3d(7, N=N, n_balls=5, phi=0.2, contrast=100.0)
+    d = 3
+    rng = np.random.default_rng([zlib.crc32(b"slab"), N])
+    info = hb.hom_problem_info(ctx, p)
+    nws = hb.hom_step_workspace_size(ctx, p, d)
+    ws = torch.empty(nws, dtype=torch.uint8, device="cuda")
+    precision = hb.HOM_FP64 if prec == "fp64" else hb.HOM_FP32
+    cdt = torch.complex128 if prec == "fp64" else torch.complex64
+    rdt = torch.float64 if prec == "fp64" else torch.float32
+    Nh = (N + 1) // 2
+    x = torch.from_numpy(rng.normal(size=(d, d, N, N, Nh)) + 1j * rng.normal(size=(d, d, N, N, Nh))).to(cdt).cuda()
+    out = {}
+    try:
+        for side in (0, 1):
+            coef = torch.empty((info["ncomp"],) + tuple(info["M"][:d][::-1]), dtype=rdt, device="cuda")
+            hb.hom_coefficient(ctx, p, side, precision, coef.data_ptr(), ws.data_ptr(), nws)
+            for slab in (1, 0):
+                hb.hom_set_slab_pass(ctx, slab)
+                y = torch.zeros_like(x)
+                hb.hom_matvec(ctx, p, side, precision, 1, d, coef.data_ptr(), x.data_ptr(), y.data_ptr(),
+                              ws.data_ptr(), nws)
+                torch.cuda.synchronize()
+                out[side, slab] = y.cpu().numpy()
+            tol = 1e-13 if prec == "fp64" else 2e-6
+            assert relerr(out[side, 1], out[side, 0]) < tol, (N, prec, side, relerr(out[side, 1], out[side, 0]))
+    finally:
+        hb.hom_set_slab_pass(ctx, 1)
