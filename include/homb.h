@@ -315,6 +315,12 @@ hom_status hom_matvec_noalloc(hom_ctx* ctx, const hom_problem* prob, int32_t sid
  * agree to rounding. Applies to later calls on this context. */
 hom_status hom_set_slab_pass(hom_ctx* ctx, int32_t enable);
 
+/* Threads per CTA of the persistent batched kernel: 256 (two CTAs per SM), 512 or 1024
+ * (one CTA per SM: more threads per cell, fewer cells at a time), or 0 (default: the
+ * autotuned choice when hom_opts.autotune is set, else 256). Applies to later
+ * hom_bounds_batched calls on this context. */
+hom_status hom_set_batch_threads(hom_ctx* ctx, int32_t threads);
+
 /* Kernel timing (CUDA events around each launch of one kernel family on the
  * launching stream). name: "zpass", "ypass", "xpass", "slab", "final", "cg", "coef", or ""
  * to disable. hom_kernel_timing returns launches and total milliseconds since the

@@ -100,6 +100,7 @@ def _load():
         "hom_fft": (i32, [vp, i32, i32, i32, i32, vp, vp, vp, sz, vp]),
         "hom_matvec_noalloc": (i32, [vp, P(hom_problem), i32, i32, i32, i32, vp, vp, vp, vp]),
         "hom_set_slab_pass": (i32, [vp, i32]),
+        "hom_set_batch_threads": (i32, [vp, i32]),
         "hom_profile_kernel": (i32, [vp, C.c_char_p]),
         "hom_kernel_timing": (i32, [vp, P(i64), dp]),
     }
@@ -319,6 +320,10 @@ def hom_energy(ctx, problem, nrhs, add_constant, d_coef, d_x, d_ws, ws_bytes, st
 def hom_fft(ctx, M, precision, direction, howmany, d_in, d_out, d_ws, ws_bytes, stream=0):
     return check(ctx, lib.hom_fft(ctx, M, precision, direction, howmany, C.c_void_p(d_in), C.c_void_p(d_out),
                                   C.c_void_p(d_ws), ws_bytes, C.c_void_p(stream)))
+
+
+def hom_set_batch_threads(ctx, threads):
+    return check(ctx, lib.hom_set_batch_threads(ctx, int(threads)))
 
 
 def hom_set_slab_pass(ctx, enable):

@@ -66,7 +66,9 @@ struct hom_ctx {
   bool graphs_off = false;
   bool slab_on = true;   // fused y-x-y slab pass where it applies
   std::vector<long long> graph_key;
-  std::vector<std::pair<long long, int>> tuned_cap;   // (key, cap)
+  struct Tuned { long long key; int cap, threads; };
+  std::vector<Tuned> tuned_cap;
+  int batch_threads = 0;   // threads per batched CTA set by the caller (0: tuned / default)
 };
 
 namespace {
@@ -1347,56 +1349,61 @@ hom_status hom_bounds_batched(hom_ctx* ctx, int32_t n, const hom_problem* probs,
     a.fields = io ? io->d_fields : nullptr;
     return a;
   };
-  auto grid_for = [&](int cap, size_t* smem) {
+  auto grid_for = [&](int cap, int threads, size_t* smem) {
     *smem = batch_smem_bytes(bp.M0max, bp.M1max, cap, elem);
-    const int bps = f32 ? batch_blocks_per_sm<float>(*smem) : batch_blocks_per_sm<double>(*smem);
+    const int bps = f32 ? batch_blocks_per_sm<float>(*smem, threads) : batch_blocks_per_sm<double>(*smem, threads);
     return std::max(1, std::min(bp.nslots_max, sms * bps));
   };
-  auto enqueue = [&](int cap, int max_iter) -> hom_status {
+  auto enqueue = [&](int cap, int threads, int max_iter) -> hom_status {
     size_t smem = 0;
-    const int grid = grid_for(cap, &smem);
+    const int grid = grid_for(cap, threads, &smem);
     CK(h2d_copy(ctx, base + bp.o_tasks, ctx->pin_in, bp.in_bytes, st));
     CK(cudaMemsetAsync(base + bp.o_counter, 0, sizeof(int), st));
     const BArgs a = args_for(cap, max_iter);
-    if (f32) KL(launch_batch<float>(a, grid, smem, st));
-    else KL(launch_batch<double>(a, grid, smem, st));
+    if (f32) KL(launch_batch<float>(a, grid, smem, threads, st));
+    else KL(launch_batch<double>(a, grid, smem, threads, st));
     CK(d2h_copy(ctx, ctx->pin_out, base + bp.o_energy, bp.out_bytes, st));
     return HOM_OK;
   };
-  // chunk capacity: autotuned once per (grid extent, precision) or the default
+  // chunk capacity and threads per CTA: autotuned once per (grid extent, precision), or
+  // the defaults; a thread count set on the context overrides both
   int cap = std::max(2048, cap_min);
+  int threads = 256;
   const long long tkey = (long long)bp.Mmax * 4 + (f32 ? 1 : 0);
   bool tuned = false;
   for (auto& kv : ctx->tuned_cap)
-    if (kv.first == tkey) { cap = std::max(kv.second, cap_min); tuned = true; }
-  if (opts->autotune && !tuned) {
+    if (kv.key == tkey) { cap = std::max(kv.cap, cap_min); threads = kv.threads; tuned = true; }
+  if (opts->autotune && !tuned && ctx->batch_threads == 0) {
     float best = 1e30f;
-    int best_cap = cap;
+    int best_cap = cap, best_threads = threads;
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
-    for (int c : {2048, 4096, 8192}) {
-      if (c < cap_min || batch_smem_bytes(bp.M0max, bp.M1max, c, elem) > 200 * 1024) continue;
-      CKS(enqueue(c, 3));                        // warm-up probe: 3 CG iterations per task
-      CK(cudaEventRecord(e0, st));
-      CKS(enqueue(c, 3));
-      CK(cudaEventRecord(e1, st));
-      CK(cudaEventSynchronize(e1));
-      float ms = 0;
-      CK(cudaEventElapsedTime(&ms, e0, e1));
-      if (ms < best) { best = ms; best_cap = c; }
-    }
+    for (int th : {256, 512, 1024})
+      for (int c : {2048, 4096, 8192}) {
+        if (c < cap_min || batch_smem_bytes(bp.M0max, bp.M1max, c, elem) > 200 * 1024) continue;
+        CKS(enqueue(c, th, 3));                        // warm-up probe: 3 CG iterations per task
+        CK(cudaEventRecord(e0, st));
+        CKS(enqueue(c, th, 3));
+        CK(cudaEventRecord(e1, st));
+        CK(cudaEventSynchronize(e1));
+        float ms = 0;
+        CK(cudaEventElapsedTime(&ms, e0, e1));
+        if (ms < best) { best = ms; best_cap = c; best_threads = th; }
+      }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     cap = best_cap;
-    ctx->tuned_cap.push_back({tkey, cap});
+    threads = best_threads;
+    ctx->tuned_cap.push_back({tkey, cap, threads});
   }
+  if (ctx->batch_threads) threads = ctx->batch_threads;
   // with starting fields, max_iter = 0 is taken literally: bounds of the projected starts
   const int max_iter = opts->max_iter > 0 ? opts->max_iter : ((opts->max_iter == 0 && io && io->d_x0) ? 0 : 10000);
   if (opts->graph && st != nullptr) {
     size_t smem = 0;
-    const int grid = grid_for(cap, &smem);
-    const std::vector<long long> key = {(long long)(uintptr_t)d_ws, (long long)(uintptr_t)(io ? io->d_x0 : nullptr),
+    const int grid = grid_for(cap, threads, &smem);
+    const std::vector<long long> key = {(long long)threads, (long long)(uintptr_t)d_ws, (long long)(uintptr_t)(io ? io->d_x0 : nullptr),
                                         (long long)(uintptr_t)(io ? io->d_fields : nullptr),
                                         (long long)bp.total, nt, grid, (long long)smem, cap,
                                         (long long)f32, max_iter, (long long)(tol * 1e18), (long long)ctx->pin_in_bytes,
@@ -1407,7 +1414,7 @@ hom_status hom_bounds_batched(hom_ctx* ctx, int32_t n, const hom_problem* probs,
       ctx->graph_exec = nullptr;
       ctx->graph = nullptr;
       CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
-      const hom_status s = enqueue(cap, max_iter);
+      const hom_status s = enqueue(cap, threads, max_iter);
       cudaGraph_t g = nullptr;
       const cudaError_t ee = cudaStreamEndCapture(st, &g);
       if (s != HOM_OK) return s;
@@ -1422,7 +1429,7 @@ hom_status hom_bounds_batched(hom_ctx* ctx, int32_t n, const hom_problem* probs,
     }
     CK(cudaGraphLaunch(ctx->graph_exec, st));
   } else {
-    CKS(enqueue(cap, max_iter));
+    CKS(enqueue(cap, threads, max_iter));
   }
   CK(cudaStreamSynchronize(st));
   // results
@@ -1650,6 +1657,14 @@ hom_status hom_matvec_noalloc(hom_ctx* ctx, const hom_problem* prob, int32_t sid
   if (precision == HOM_FP64)
     return run.matvec<double>(d_in, d_out, d_coef, proj, nullptr, nullptr, nullptr, 0);
   return run.matvec<float>(d_in, d_out, d_coef, proj, nullptr, nullptr, nullptr, 0);
+}
+
+hom_status hom_set_batch_threads(hom_ctx* ctx, int32_t threads) {
+  if (!ctx) return HOM_ERR_INVALID_ARG;
+  if (threads != 0 && threads != 256 && threads != 512 && threads != 1024)
+    return fail(ctx, HOM_ERR_INVALID_ARG, "batched threads per CTA must be 0, 256, 512 or 1024");
+  ctx->batch_threads = threads;
+  return HOM_OK;
 }
 
 hom_status hom_set_slab_pass(hom_ctx* ctx, int32_t enable) {

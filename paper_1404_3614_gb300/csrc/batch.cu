@@ -16,7 +16,6 @@
 
 namespace homb {
 
-constexpr int kBatchThreads = 256;
 
 template <typename T>
 __device__ __noinline__ cpx<T>* fft_dyn(cpx<T>* a, cpx<T>* b, int G, int M, const FftPlan& plan,
@@ -294,8 +293,8 @@ __device__ __noinline__ void col_final(const cpx<T>* T2, cpx<T>* q, const cpx<T>
   }
 }
 
-template <typename T>
-__global__ void __launch_bounds__(kBatchThreads, 2) k_batch(BArgs a) {
+template <typename T, int NT>
+__global__ void __launch_bounds__(NT, NT <= 256 ? 2 : 1) k_batch(BArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ int s_task;
   __shared__ BTask s_t;
@@ -709,30 +708,47 @@ __global__ void __launch_bounds__(kBatchThreads, 2) k_batch(BArgs a) {
   }
 }
 
-template <typename T> cudaError_t launch_batch(const BArgs& a, int nblocks, size_t smem, cudaStream_t s) {
+template <typename T, int NT> cudaError_t launch_batch_nt(const BArgs& a, int nblocks, size_t smem, cudaStream_t s) {
   static size_t cache[16] = {};
   int dev = 0;
   cudaGetDevice(&dev);
   dev &= 15;
   if (smem > 48 * 1024 && cache[dev] < smem) {
-    const cudaError_t e = cudaFuncSetAttribute(k_batch<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const cudaError_t e = cudaFuncSetAttribute(k_batch<T, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     cache[dev] = smem;
   }
-  k_batch<T><<<nblocks, kBatchThreads, smem, s>>>(a);
+  k_batch<T, NT><<<nblocks, NT, smem, s>>>(a);
   return cudaGetLastError();
 }
 
-template <typename T> int batch_blocks_per_sm(size_t smem) {
-  if (smem > 48 * 1024) cudaFuncSetAttribute(k_batch<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+template <typename T> cudaError_t launch_batch(const BArgs& a, int nblocks, size_t smem, int threads, cudaStream_t s) {
+  switch (threads) {
+    case 256: return launch_batch_nt<T, 256>(a, nblocks, smem, s);
+    case 512: return launch_batch_nt<T, 512>(a, nblocks, smem, s);
+    case 1024: return launch_batch_nt<T, 1024>(a, nblocks, smem, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template <typename T, int NT> int batch_blocks_nt(size_t smem) {
+  if (smem > 48 * 1024) cudaFuncSetAttribute(k_batch<T, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   int n = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batch<T>, kBatchThreads, smem) != cudaSuccess) return 1;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batch<T, NT>, NT, smem) != cudaSuccess) return 1;
   return n > 0 ? n : 1;
 }
-template int batch_blocks_per_sm<double>(size_t);
-template int batch_blocks_per_sm<float>(size_t);
 
-template cudaError_t launch_batch<double>(const BArgs&, int, size_t, cudaStream_t);
-template cudaError_t launch_batch<float>(const BArgs&, int, size_t, cudaStream_t);
+template <typename T> int batch_blocks_per_sm(size_t smem, int threads) {
+  switch (threads) {
+    case 512: return batch_blocks_nt<T, 512>(smem);
+    case 1024: return batch_blocks_nt<T, 1024>(smem);
+    default: return batch_blocks_nt<T, 256>(smem);
+  }
+}
+template int batch_blocks_per_sm<double>(size_t, int);
+template int batch_blocks_per_sm<float>(size_t, int);
+
+template cudaError_t launch_batch<double>(const BArgs&, int, size_t, int, cudaStream_t);
+template cudaError_t launch_batch<float>(const BArgs&, int, size_t, int, cudaStream_t);
 
 }  // namespace homb

@@ -192,12 +192,40 @@ __device__ __forceinline__ void dft_ct(cpx<T>* v, int dir) {
   }
 }
 
+// Length 15 by the prime-factor (Good-Thomas) map, 15 = 3 * 5 with coprime factors:
+// input n = (5 n1 + 3 n2) mod 15, output k = (10 k1 + 6 k2) mod 15, so that
+// w_15^(n k) = w_3^(n1 k1) w_5^(n2 k2) and no twiddle multiplications are needed.
+template <typename T>
+__device__ __forceinline__ void dft15_pfa(cpx<T>* v, int dir) {
+  cpx<T> t[15];
+#pragma unroll
+  for (int n2 = 0; n2 < 5; ++n2) {
+    cpx<T> a[3];
+#pragma unroll
+    for (int n1 = 0; n1 < 3; ++n1) a[n1] = v[(5 * n1 + 3 * n2) % 15];
+    dft3<T>(a, dir);
+#pragma unroll
+    for (int k1 = 0; k1 < 3; ++k1) t[n2 * 3 + k1] = a[k1];
+  }
+#pragma unroll
+  for (int k1 = 0; k1 < 3; ++k1) {
+    cpx<T> b[5];
+#pragma unroll
+    for (int n2 = 0; n2 < 5; ++n2) b[n2] = t[n2 * 3 + k1];
+    dft5<T>(b, dir);
+#pragma unroll
+    for (int k2 = 0; k2 < 5; ++k2) v[(10 * k1 + 6 * k2) % 15] = b[k2];
+  }
+}
+
 template <typename T, int R>
 __device__ __forceinline__ void dft_reg(cpx<T>* v, int dir) {
   if constexpr (R == 3) {
     dft3<T>(v, dir);
   } else if constexpr (R == 5) {
     dft5<T>(v, dir);
+  } else if constexpr (R == 15) {
+    dft15_pfa<T>(v, dir);
   } else {
     constexpr int R1 = ct_first_factor(R);
     dft_ct<T, R1, R / R1>(v, dir);

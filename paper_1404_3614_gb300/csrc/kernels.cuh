@@ -160,8 +160,9 @@ inline size_t batch_smem_bytes(int M0max, int M1max, int cap, int elem) {
   const size_t tw = ((size_t)(M0max + M1max) * (16 + elem) + 15) & ~(size_t)15;
   return tw + 2 * (size_t)cap * 16;
 }
-template <typename T> cudaError_t launch_batch(const BArgs& a, int nblocks, size_t smem, cudaStream_t s);
-template <typename T> int batch_blocks_per_sm(size_t smem);
+// threads per CTA: 256 (two CTAs per SM), 512 or 1024 (one CTA per SM)
+template <typename T> cudaError_t launch_batch(const BArgs& a, int nblocks, size_t smem, int threads, cudaStream_t s);
+template <typename T> int batch_blocks_per_sm(size_t smem, int threads);
 
 // launchers (return cudaGetLastError())
 template <typename T> cudaError_t launch_pencil(const PencilArgs& a, cudaStream_t s);

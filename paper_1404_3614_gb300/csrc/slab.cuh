@@ -23,6 +23,7 @@ constexpr int kSlabMaxThreads = 512;
 
 // In-place FFT of one contiguous pencil of length R*R by the R lanes of a lane group
 // (lane index l < R). Every lane of the warp calls it (on = false: no memory access).
+// Wt holds w_M^(l k) at [k][l].
 template <typename T, int R>
 __device__ __forceinline__ void pencil_fft_inplace(cpx<T>* p, int l, const cpx<T>* Wt, int dir, bool on) {
   cpx<T> v[R];
@@ -30,7 +31,7 @@ __device__ __forceinline__ void pencil_fft_inplace(cpx<T>* p, int l, const cpx<T
   for (int n = 0; n < R; ++n) v[n] = on ? p[l + R * n] : mk<T>(T(0), T(0));
   dft_reg<T, R>(v, dir);
 #pragma unroll
-  for (int k = 1; k < R; ++k) v[k] = mulc<T>(v[k], Wt[l * k], dir > 0);
+  for (int k = 1; k < R; ++k) v[k] = mulc<T>(v[k], Wt[k * R + l], dir > 0);
   __syncwarp();
   if (on) {
 #pragma unroll
@@ -54,7 +55,7 @@ __device__ __forceinline__ void pencil_fft_inplace(cpx<T>* p, int l, const cpx<T
 template <typename T, int R>
 __device__ __forceinline__ void fft_finish(cpx<T>* v, cpx<T>* S, int l, const cpx<T>* Wt, int dir, bool own) {
 #pragma unroll
-  for (int k = 1; k < R; ++k) v[k] = mulc<T>(v[k], Wt[l * k], dir > 0);
+  for (int k = 1; k < R; ++k) v[k] = mulc<T>(v[k], Wt[k * R + l], dir > 0);
   __syncwarp();
   if (own) {
 #pragma unroll
@@ -83,8 +84,12 @@ __global__ void __launch_bounds__(kSlabMaxThreads) k_slab(SlabArgs a) {
   const int Ny = a.Ny, Nh = a.Nh, half = (Ny - 1) / 2;
   const cpx<T>* in = reinterpret_cast<const cpx<T>*>(a.in) + s * Ny * Nh;
   cpx<T>* out = reinterpret_cast<cpx<T>*>(a.out) + s * Ny * Nh;
+  // twiddles w_M^(l k) stored at [k][l] so that the R lanes of a group read consecutive words
   const cpx<T>* W = reinterpret_cast<const cpx<T>*>(a.W);
-  for (int t = threadIdx.x; t < M; t += blockDim.x) Wt[t] = W[t];
+  for (int t = threadIdx.x; t < M; t += blockDim.x) {
+    const int k = t / R;
+    Wt[t] = W[(t - k * R) * k];
+  }
   const int npad = M - Ny;
   for (int t = threadIdx.x; t < Nh * npad; t += blockDim.x) {
     const int kx = t / npad;
