@@ -66,7 +66,7 @@ struct hom_ctx {
   bool graphs_off = false;
   bool slab_on = true;   // fused y-x-y slab pass where it applies
   std::vector<long long> graph_key;
-  struct Tuned { long long key; int cap, threads; };
+  struct Tuned { long long key; int cap, threads, sched; };
   std::vector<Tuned> tuned_cap;
   int batch_threads = 0;   // threads per batched CTA set by the caller (0: tuned / default)
 };
@@ -212,6 +212,7 @@ bool overlap(const hom_inclusion& p, const hom_inclusion& q, const double* Y, in
 void make_plan(int M, FftPlan& p) {
   p.M = M;
   p.nrad = 0;
+  p.sched = 0;
   int m = M;
   const int small[] = {5, 3, 7, 11, 13};
   for (int r : small)
@@ -1368,35 +1369,46 @@ hom_status hom_bounds_batched(hom_ctx* ctx, int32_t n, const hom_problem* probs,
   // chunk capacity and threads per CTA: autotuned once per (grid extent, precision), or
   // the defaults; a thread count set on the context overrides both
   int cap = std::max(2048, cap_min);
-  int threads = 256;
+  int threads = 256, sched = 0;
+  // the radix schedule travels in the staged task table (both axes' plans of every task)
+  auto set_sched = [&](int sc) {
+    BTask* tk = reinterpret_cast<BTask*>(ctx->pin_in);
+    for (long long k = 0; k < nt; ++k) tk[k].plan0.sched = tk[k].plan1.sched = sc;
+  };
   const long long tkey = (long long)bp.Mmax * 4 + (f32 ? 1 : 0);
   bool tuned = false;
   for (auto& kv : ctx->tuned_cap)
-    if (kv.key == tkey) { cap = std::max(kv.cap, cap_min); threads = kv.threads; tuned = true; }
+    if (kv.key == tkey) { cap = std::max(kv.cap, cap_min); threads = kv.threads; sched = kv.sched; tuned = true; }
   if (opts->autotune && !tuned && ctx->batch_threads == 0) {
+    // search over (threads per CTA, chunk capacity, radix schedule), each timed on this
+    // batch with 3 CG iterations per task after an untimed run of the same configuration
     float best = 1e30f;
-    int best_cap = cap, best_threads = threads;
+    int best_cap = cap, best_threads = threads, best_sched = 0;
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
-    for (int th : {256, 512, 1024})
-      for (int c : {2048, 4096, 8192}) {
-        if (c < cap_min || batch_smem_bytes(bp.M0max, bp.M1max, c, elem) > 200 * 1024) continue;
-        CKS(enqueue(c, th, 3));                        // warm-up probe: 3 CG iterations per task
-        CK(cudaEventRecord(e0, st));
-        CKS(enqueue(c, th, 3));
-        CK(cudaEventRecord(e1, st));
-        CK(cudaEventSynchronize(e1));
-        float ms = 0;
-        CK(cudaEventElapsedTime(&ms, e0, e1));
-        if (ms < best) { best = ms; best_cap = c; best_threads = th; }
-      }
+    for (int sc : {1, 2})
+      for (int th : {256, 512, 1024})
+        for (int c : {2048, 4096, 8192}) {
+          if (c < cap_min || batch_smem_bytes(bp.M0max, bp.M1max, c, elem) > 200 * 1024) continue;
+          set_sched(sc);
+          CKS(enqueue(c, th, 3));
+          CK(cudaEventRecord(e0, st));
+          CKS(enqueue(c, th, 3));
+          CK(cudaEventRecord(e1, st));
+          CK(cudaEventSynchronize(e1));
+          float ms = 0;
+          CK(cudaEventElapsedTime(&ms, e0, e1));
+          if (ms < best) { best = ms; best_cap = c; best_threads = th; best_sched = sc; }
+        }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     cap = best_cap;
     threads = best_threads;
-    ctx->tuned_cap.push_back({tkey, cap, threads});
+    sched = best_sched;
+    ctx->tuned_cap.push_back({tkey, cap, threads, sched});
   }
+  set_sched(sched);
   if (ctx->batch_threads) threads = ctx->batch_threads;
   // with starting fields, max_iter = 0 is taken literally: bounds of the projected starts
   const int max_iter = opts->max_iter > 0 ? opts->max_iter : ((opts->max_iter == 0 && io && io->d_x0) ? 0 : 10000);

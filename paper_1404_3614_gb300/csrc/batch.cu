@@ -17,17 +17,29 @@
 namespace homb {
 
 
-template <typename T>
-__device__ __noinline__ cpx<T>* fft_dyn(cpx<T>* a, cpx<T>* b, int G, int M, const FftPlan& plan,
-                                           const cpx<T>* W, int dir) {
+// G pencils of compile-time length M with one radix schedule (BIG: composite register
+// radices), or the runtime plan for any other length. Each schedule is its own function
+// so that its registers are allocated on their own.
+template <typename T, bool BIG>
+__device__ __noinline__ cpx<T>* fft_sched(cpx<T>* a, cpx<T>* b, int G, int M, const FftPlan& plan,
+                                            const cpx<T>* W, int dir) {
   switch (M) {
-    case 45: return cfft<T, 45>(a, b, G, W, dir);
-    case 81: return cfft<T, 81>(a, b, G, W, dir);
-    case 125: return cfft<T, 125>(a, b, G, W, dir);
-    case 225: return cfft<T, 225>(a, b, G, W, dir);
-    case 405: return cfft<T, 405>(a, b, G, W, dir);
+    case 45: return cfft_from<T, 45, 0, BIG>(a, b, G, W, dir);
+    case 81: return cfft_from<T, 81, 0, BIG>(a, b, G, W, dir);
+    case 125: return cfft_from<T, 125, 0, BIG>(a, b, G, W, dir);
+    case 225: return cfft_from<T, 225, 0, BIG>(a, b, G, W, dir);
+    case 405: return cfft_from<T, 405, 0, BIG>(a, b, G, W, dir);
     default: return fft_pencils<T>(a, b, G, M, plan, W, dir);
   }
+}
+
+// G pencils of length M with the radix schedule of the plan (picked per batch by the
+// autotuner; 0 takes the precision's default).
+template <typename T>
+__device__ __forceinline__ cpx<T>* fft_dyn(cpx<T>* a, cpx<T>* b, int G, int M, const FftPlan& plan,
+                                           const cpx<T>* W, int dir) {
+  const bool big = plan.sched == 0 ? sizeof(T) == 4 : plan.sched == 2;
+  return big ? fft_sched<T, true>(a, b, G, M, plan, W, dir) : fft_sched<T, false>(a, b, G, M, plan, W, dir);
 }
 
 // Column pass over a list of fields: in field f (base in + f*in_fs) a column x holds Pin

@@ -83,6 +83,8 @@ struct FftPlan {
   int M;
   int nrad;
   int radix[kMaxRadices];
+  int sched;   // compile-time lengths in the batched kernel: 0 precision default,
+               // 1 radices 5 and 3, 2 composite register radices 15, 25, 9
 };
 
 // ---------------------------------------------------------------------------------
