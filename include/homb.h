@@ -321,6 +321,15 @@ hom_status hom_set_slab_pass(hom_ctx* ctx, int32_t enable);
  * hom_bounds_batched calls on this context. */
 hom_status hom_set_batch_threads(hom_ctx* ctx, int32_t threads);
 
+/* Thread-block clusters for the largest cells of a batch: the cells whose larger
+ * double-grid extent 2N-1 is at least coop_min_M are each worked on by all `cluster` CTAs
+ * of a cluster together (splitting every transform pass and reduction over them, with
+ * cluster barriers between passes); the other cells take one CTA each. cluster 1 turns
+ * this off; 0 (default) uses the autotuned choice when hom_opts.autotune is set, else 1.
+ * Results equal the single-CTA ones to rounding (reduction order). Applies to later
+ * hom_bounds_batched calls on this context. */
+hom_status hom_set_batch_cluster(hom_ctx* ctx, int32_t cluster, int32_t coop_min_M);
+
 /* Kernel timing (CUDA events around each launch of one kernel family on the
  * launching stream). name: "zpass", "ypass", "xpass", "slab", "final", "cg", "coef", or ""
  * to disable. hom_kernel_timing returns launches and total milliseconds since the

@@ -101,6 +101,7 @@ def _load():
         "hom_matvec_noalloc": (i32, [vp, P(hom_problem), i32, i32, i32, i32, vp, vp, vp, vp]),
         "hom_set_slab_pass": (i32, [vp, i32]),
         "hom_set_batch_threads": (i32, [vp, i32]),
+        "hom_set_batch_cluster": (i32, [vp, i32, i32]),
         "hom_profile_kernel": (i32, [vp, C.c_char_p]),
         "hom_kernel_timing": (i32, [vp, P(i64), dp]),
     }
@@ -324,6 +325,10 @@ def hom_fft(ctx, M, precision, direction, howmany, d_in, d_out, d_ws, ws_bytes, 
 
 def hom_set_batch_threads(ctx, threads):
     return check(ctx, lib.hom_set_batch_threads(ctx, int(threads)))
+
+
+def hom_set_batch_cluster(ctx, cluster, coop_min_M=0):
+    return check(ctx, lib.hom_set_batch_cluster(ctx, int(cluster), int(coop_min_M)))
 
 
 def hom_set_slab_pass(ctx, enable):

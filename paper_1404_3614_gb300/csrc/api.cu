@@ -66,9 +66,11 @@ struct hom_ctx {
   bool graphs_off = false;
   bool slab_on = true;   // fused y-x-y slab pass where it applies
   std::vector<long long> graph_key;
-  struct Tuned { long long key; int cap, threads, sched; };
+  struct Tuned { long long key; int cap, threads, sched, cluster, coopM; };
   std::vector<Tuned> tuned_cap;
   int batch_threads = 0;   // threads per batched CTA set by the caller (0: tuned / default)
+  int batch_cluster = 0;   // cluster size set by the caller (0: tuned / default)
+  int batch_coopM = 0;     // with batch_cluster: cells at least this large are cooperative
 };
 
 namespace {
@@ -1113,7 +1115,7 @@ hom_status build_batch(hom_ctx* ctx, int n, const hom_problem* probs, const hom_
   bp.o_incl = L.take(bp.incl.size() * sizeof(DevIncl));
   bp.o_tw64 = L.take(bp.tw64.size() * sizeof(double2));
   bp.o_tw32 = L.take(bp.tw32.size() * sizeof(float2));
-  bp.o_counter = L.take(sizeof(int));
+  bp.o_counter = L.take(2 * sizeof(int));
   bp.in_bytes = bp.o_counter - bp.o_tasks;
   bp.o_energy = L.take((size_t)nt * 4 * sizeof(double));
   bp.o_iters = L.take((size_t)nt * 2 * sizeof(int));
@@ -1327,11 +1329,20 @@ hom_status hom_bounds_batched(hom_ctx* ctx, int32_t n, const hom_problem* probs,
   const int sms = device_sms(ctx->device);
   const int elem = f32 ? 8 : 16;
   const int cap_min = 2 * (bp.Mmax + 1);
-  auto args_for = [&](int cap, int max_iter) {
+  // tasks whose larger double-grid extent is at least coopM go to whole clusters
+  auto ncoop_for = [&](int cluster, int coopM) {
+    if (cluster <= 1) return 0;
+    int n_ = 0;
+    while (n_ < nt && std::max(bp.tasks[n_].M0, bp.tasks[n_].M1) >= coopM) ++n_;
+    return n_;
+  };
+  auto args_for = [&](int cap, int max_iter, int ncoop) {
     BArgs a{};
     a.tasks = reinterpret_cast<const BTask*>(base + bp.o_tasks);
     a.ntasks = nt;
     a.counter = reinterpret_cast<int*>(base + bp.o_counter);
+    a.counter2 = a.counter + 1;
+    a.ncoop = ncoop;
     a.incl = reinterpret_cast<const DevIncl*>(base + bp.o_incl);
     a.tw64 = reinterpret_cast<const double2*>(base + bp.o_tw64);
     a.tw32 = reinterpret_cast<const float2*>(base + bp.o_tw32);
@@ -1350,26 +1361,35 @@ hom_status hom_bounds_batched(hom_ctx* ctx, int32_t n, const hom_problem* probs,
     a.fields = io ? io->d_fields : nullptr;
     return a;
   };
-  auto grid_for = [&](int cap, int threads, size_t* smem) {
+  // CTAs of one launch: as many as fit at once (0 when the cluster shape cannot be placed),
+  // at most one per scratch slot, a multiple of the cluster size
+  auto grid_for = [&](int cap, int threads, int cluster, size_t* smem) {
     *smem = batch_smem_bytes(bp.M0max, bp.M1max, cap, elem);
-    const int bps = f32 ? batch_blocks_per_sm<float>(*smem, threads) : batch_blocks_per_sm<double>(*smem, threads);
-    return std::max(1, std::min(bp.nslots_max, sms * bps));
+    const int mx = f32 ? batch_max_blocks<float>(*smem, threads, cluster)
+                       : batch_max_blocks<double>(*smem, threads, cluster);
+    const int g_ = std::min(bp.nslots_max, mx);
+    return (g_ / cluster) * cluster;
   };
-  auto enqueue = [&](int cap, int threads, int max_iter) -> hom_status {
+  auto enqueue = [&](int cap, int threads, int cluster, int coopM, int max_iter) -> hom_status {
     size_t smem = 0;
-    const int grid = grid_for(cap, threads, &smem);
+    int grid = grid_for(cap, threads, cluster, &smem);
+    if (grid < cluster) {   // the cluster shape does not fit: single CTAs
+      cluster = 1;
+      grid = grid_for(cap, threads, 1, &smem);
+    }
+    if (grid < 1) return fail(ctx, HOM_ERR_INVALID_ARG, "batched kernel does not fit on the device");
     CK(h2d_copy(ctx, base + bp.o_tasks, ctx->pin_in, bp.in_bytes, st));
-    CK(cudaMemsetAsync(base + bp.o_counter, 0, sizeof(int), st));
-    const BArgs a = args_for(cap, max_iter);
-    if (f32) KL(launch_batch<float>(a, grid, smem, threads, st));
-    else KL(launch_batch<double>(a, grid, smem, threads, st));
+    CK(cudaMemsetAsync(base + bp.o_counter, 0, 2 * sizeof(int), st));
+    const BArgs a = args_for(cap, max_iter, ncoop_for(cluster, coopM));
+    if (f32) KL(launch_batch<float>(a, grid, smem, threads, cluster, st));
+    else KL(launch_batch<double>(a, grid, smem, threads, cluster, st));
     CK(d2h_copy(ctx, ctx->pin_out, base + bp.o_energy, bp.out_bytes, st));
     return HOM_OK;
   };
   // chunk capacity and threads per CTA: autotuned once per (grid extent, precision), or
   // the defaults; a thread count set on the context overrides both
   int cap = std::max(2048, cap_min);
-  int threads = 256, sched = 0;
+  int threads = 256, sched = 0, cluster = 1, coopM = 0;
   // the radix schedule travels in the staged task table (both axes' plans of every task)
   auto set_sched = [&](int sc) {
     BTask* tk = reinterpret_cast<BTask*>(ctx->pin_in);
@@ -1378,7 +1398,14 @@ hom_status hom_bounds_batched(hom_ctx* ctx, int32_t n, const hom_problem* probs,
   const long long tkey = (long long)bp.Mmax * 4 + (f32 ? 1 : 0);
   bool tuned = false;
   for (auto& kv : ctx->tuned_cap)
-    if (kv.key == tkey) { cap = std::max(kv.cap, cap_min); threads = kv.threads; sched = kv.sched; tuned = true; }
+    if (kv.key == tkey) {
+      cap = std::max(kv.cap, cap_min);
+      threads = kv.threads;
+      sched = kv.sched;
+      cluster = kv.cluster;
+      coopM = kv.coopM;
+      tuned = true;
+    }
   if (opts->autotune && !tuned && ctx->batch_threads == 0) {
     // search over (threads per CTA, chunk capacity, radix schedule), each timed on this
     // batch with 3 CG iterations per task after an untimed run of the same configuration
@@ -1392,30 +1419,61 @@ hom_status hom_bounds_batched(hom_ctx* ctx, int32_t n, const hom_problem* probs,
         for (int c : {2048, 4096, 8192}) {
           if (c < cap_min || batch_smem_bytes(bp.M0max, bp.M1max, c, elem) > 200 * 1024) continue;
           set_sched(sc);
-          CKS(enqueue(c, th, 3));
+          CKS(enqueue(c, th, 1, 0, 3));
           CK(cudaEventRecord(e0, st));
-          CKS(enqueue(c, th, 3));
+          CKS(enqueue(c, th, 1, 0, 3));
           CK(cudaEventRecord(e1, st));
           CK(cudaEventSynchronize(e1));
           float ms = 0;
           CK(cudaEventElapsedTime(&ms, e0, e1));
           if (ms < best) { best = ms; best_cap = c; best_threads = th; best_sched = sc; }
         }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
     cap = best_cap;
     threads = best_threads;
     sched = best_sched;
-    ctx->tuned_cap.push_back({tkey, cap, threads, sched});
+    set_sched(sched);
+    // clusters for the largest cells: timed on whole solves of this batch, since they act
+    // on the longest tasks at the end of the launch, which short probes do not see
+    const int mtop = std::max(bp.tasks[0].M0, bp.tasks[0].M1);
+    int msecond = 0;
+    for (const BTask& tk : bp.tasks)
+      if (std::max(tk.M0, tk.M1) < mtop) { msecond = std::max(tk.M0, tk.M1); break; }
+    best = 1e30f;
+    const int solve_iter = opts->max_iter > 0 ? opts->max_iter : 10000;
+    struct Cand { int cl, m; };
+    std::vector<Cand> cands = {{1, 0}, {2, mtop}, {4, mtop}, {8, mtop}};
+    if (msecond > 0) {
+      cands.push_back({4, msecond});
+      cands.push_back({8, msecond});
+    }
+    for (const Cand& cd : cands) {
+      size_t sm_ = 0;
+      if (cd.cl > 1 && grid_for(cap, threads, cd.cl, &sm_) < cd.cl) continue;
+      CK(cudaEventRecord(e0, st));
+      CKS(enqueue(cap, threads, cd.cl, cd.m, solve_iter));
+      CK(cudaEventRecord(e1, st));
+      CK(cudaEventSynchronize(e1));
+      float ms = 0;
+      CK(cudaEventElapsedTime(&ms, e0, e1));
+      if (ms < best) { best = ms; cluster = cd.cl; coopM = cd.m; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    ctx->tuned_cap.push_back({tkey, cap, threads, sched, cluster, coopM});
   }
   set_sched(sched);
   if (ctx->batch_threads) threads = ctx->batch_threads;
+  if (ctx->batch_cluster) {
+    cluster = ctx->batch_cluster;
+    coopM = ctx->batch_coopM;
+  }
   // with starting fields, max_iter = 0 is taken literally: bounds of the projected starts
   const int max_iter = opts->max_iter > 0 ? opts->max_iter : ((opts->max_iter == 0 && io && io->d_x0) ? 0 : 10000);
   if (opts->graph && st != nullptr) {
     size_t smem = 0;
-    const int grid = grid_for(cap, threads, &smem);
-    const std::vector<long long> key = {(long long)threads, (long long)(uintptr_t)d_ws, (long long)(uintptr_t)(io ? io->d_x0 : nullptr),
+    const int grid = grid_for(cap, threads, cluster, &smem);
+    const std::vector<long long> key = {(long long)threads, (long long)cluster, (long long)coopM,
+                                        (long long)(uintptr_t)d_ws, (long long)(uintptr_t)(io ? io->d_x0 : nullptr),
                                         (long long)(uintptr_t)(io ? io->d_fields : nullptr),
                                         (long long)bp.total, nt, grid, (long long)smem, cap,
                                         (long long)f32, max_iter, (long long)(tol * 1e18), (long long)ctx->pin_in_bytes,
@@ -1426,7 +1484,7 @@ hom_status hom_bounds_batched(hom_ctx* ctx, int32_t n, const hom_problem* probs,
       ctx->graph_exec = nullptr;
       ctx->graph = nullptr;
       CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
-      const hom_status s = enqueue(cap, threads, max_iter);
+      const hom_status s = enqueue(cap, threads, cluster, coopM, max_iter);
       cudaGraph_t g = nullptr;
       const cudaError_t ee = cudaStreamEndCapture(st, &g);
       if (s != HOM_OK) return s;
@@ -1441,7 +1499,7 @@ hom_status hom_bounds_batched(hom_ctx* ctx, int32_t n, const hom_problem* probs,
     }
     CK(cudaGraphLaunch(ctx->graph_exec, st));
   } else {
-    CKS(enqueue(cap, threads, max_iter));
+    CKS(enqueue(cap, threads, cluster, coopM, max_iter));
   }
   CK(cudaStreamSynchronize(st));
   // results
@@ -1676,6 +1734,15 @@ hom_status hom_set_batch_threads(hom_ctx* ctx, int32_t threads) {
   if (threads != 0 && threads != 256 && threads != 512 && threads != 1024)
     return fail(ctx, HOM_ERR_INVALID_ARG, "batched threads per CTA must be 0, 256, 512 or 1024");
   ctx->batch_threads = threads;
+  return HOM_OK;
+}
+
+hom_status hom_set_batch_cluster(hom_ctx* ctx, int32_t cluster, int32_t coop_min_M) {
+  if (!ctx) return HOM_ERR_INVALID_ARG;
+  if (cluster != 0 && cluster != 1 && cluster != 2 && cluster != 4 && cluster != 8)
+    return fail(ctx, HOM_ERR_INVALID_ARG, "batched cluster size must be 0, 1, 2, 4 or 8");
+  ctx->batch_cluster = cluster;
+  ctx->batch_coopM = coop_min_M;
   return HOM_OK;
 }
 

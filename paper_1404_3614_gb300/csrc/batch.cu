@@ -9,12 +9,53 @@
 // upper_lower_bounds). No grid-wide synchronisation and no waits between CTAs: each
 // task is independent. Data live in a per-CTA global scratch slot (L2-resident for the
 // small grids) and pass through shared memory in chunks of FFT pencils.
+#include <cooperative_groups.h>
 #include <math.h>
 
 #include "kernels.cuh"
 #include "spectrum.cuh"
 
 namespace homb {
+
+namespace cg = cooperative_groups;
+
+// The CTAs that work on one task together: the whole thread-block cluster (rank, size)
+// for a cooperative task, or this CTA alone (0, 1). Task-wide loops stride over the
+// team's threads, chunk loops over its CTAs; team_sync orders their global and shared
+// memory accesses (a cluster barrier with release / acquire semantics, or
+// __syncthreads for a team of one).
+struct Team {
+  int rank, size;
+  __device__ long long tid() const { return (long long)rank * blockDim.x + threadIdx.x; }
+  __device__ long long nth() const { return (long long)size * blockDim.x; }
+};
+
+__device__ __forceinline__ void team_sync(const Team& tm) {
+  if (tm.size > 1) {
+    __threadfence();
+    cg::this_cluster().sync();
+  } else {
+    __syncthreads();
+  }
+}
+
+// Deterministic sum of one double per thread over the team, valid in thread 0 of every
+// CTA of the team: block sums in a fixed tree, then the per-CTA sums in rank order from
+// rank 0's exchange buffer xch[2][8] (alternating halves, so that one barrier per sum
+// suffices).
+__device__ double team_sum(const Team& tm, double v, double* red, double* xch, int& parity) {
+  const double s = block_sum(v, red);
+  if (tm.size == 1) return s;
+  cg::cluster_group cl = cg::this_cluster();
+  double* x0 = cl.map_shared_rank(xch, 0);
+  if (threadIdx.x == 0) x0[parity * 8 + tm.rank] = s;
+  cl.sync();
+  double t = 0.0;
+  if (threadIdx.x == 0)
+    for (int r = 0; r < tm.size; ++r) t += x0[parity * 8 + r];
+  parity ^= 1;
+  return t;
+}
 
 
 // G pencils of compile-time length M with one radix schedule (BIG: composite register
@@ -51,14 +92,14 @@ template <typename U>
 __device__ __noinline__ void col_pass(const cpx<U>* in, cpx<U>* out, long long in_fs, long long out_fs,
                          const int* flist, int nfl, int X, int Pin, int Pout, int Nlog, int M,
                          int dir, const FftPlan& plan, const cpx<U>* W, cpx<U>* A, cpx<U>* B, int cap,
-                         const int* add_e) {
+                         const int* add_e, Team tm) {
   const int G = max(1, min(cap / M, 32));
   const int ncol = nfl * X;
   const bool pad = dir > 0 && Pin != M;
   const bool trunc = dir < 0 && Pout != M;
   const int half = (Nlog - 1) / 2;
   const FastDiv fdX((uint32_t)X);
-  for (int c0 = 0; c0 < ncol; c0 += G) {
+  for (int c0 = tm.rank * G; c0 < ncol; c0 += tm.size * G) {
     const int Gc = min(G, ncol - c0);
     const FastDiv fdG((uint32_t)Gc);
     if (pad) {
@@ -114,7 +155,8 @@ __device__ __forceinline__ void coef_apply(const U* coef, long long gi, long lon
 template <typename U>
 __device__ __noinline__ void row_pass(int mode, cpx<U>* rows, long long field_stride, int M1, int Nin, int Nout, int M,
                          const U* coef, int ncomp, U scale, const int* rlist, int nrl, U* coef_out,
-                         const FftPlan& plan, const cpx<U>* W, cpx<U>* A, cpx<U>* B, int cap, double* acc) {
+                         const FftPlan& plan, const cpx<U>* W, cpx<U>* A, cpx<U>* B, int cap, double* acc,
+                         Team tm) {
   // number of pairs in the pass and pairs per chunk
   int npairs, per_chunk;
   if (mode == 0) {
@@ -131,7 +173,7 @@ __device__ __noinline__ void row_pass(int mode, cpx<U>* rows, long long field_st
   const FastDiv fdNin((uint32_t)Nin);
   const FastDiv fdNout((uint32_t)(Nout > 0 ? Nout : 1));
   const int nrows_total = ncomp * M1;
-  for (int q0 = 0; q0 < npairs; q0 += per_chunk) {
+  for (int q0 = tm.rank * per_chunk; q0 < npairs; q0 += tm.size * per_chunk) {
     const int P = min(per_chunk, npairs - q0);
     const int nrow = 2 * P;
     // storage row of chunk row h (0 <= h < 2P): returns pointer offset or -1
@@ -246,12 +288,12 @@ template <typename T>
 __device__ __noinline__ void col_final(const cpx<T>* T2, cpx<T>* q, const cpx<T>* p, long long t2_fs, long long fld_fs,
                           const int* rlist, int nrl, int Nh, int N1, int M1, double iy0, double iy1,
                           int side, const FftPlan& plan, const cpx<T>* W, cpx<T>* A, cpx<T>* B, int cap,
-                          double* pq_acc) {
+                          double* pq_acc, Team tm) {
   const int G = max(1, min(cap / (2 * M1), 16));     // columns per chunk (2 pencils each)
   const int ncol = nrl * Nh;
   const FastDiv fdNh((uint32_t)Nh);
   const int half = (N1 - 1) / 2;
-  for (int c0 = 0; c0 < ncol; c0 += G) {
+  for (int c0 = tm.rank * G; c0 < ncol; c0 += tm.size * G) {
     const int Gc = min(G, ncol - c0);
     const FastDiv fd2G((uint32_t)(2 * Gc));
     for (int t = threadIdx.x; t < 2 * Gc * M1; t += blockDim.x) {
@@ -316,6 +358,7 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 2 : 1) k_batch(BArgs a) {
   __shared__ int s_rlist[2], s_nrl;
   __shared__ int s_flist[4], s_nfl;
   __shared__ int s_adde[4];
+  __shared__ double s_xch[16];   // cluster sums: [parity][rank] (read from rank 0's copy)
   // shared memory: FP64 twiddles, working-precision twiddles, two chunk buffers (batch_smem_bytes)
   double2* W0d = reinterpret_cast<double2*>(smem);
   double2* W1d = W0d + a.M0max;
@@ -324,14 +367,39 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 2 : 1) k_batch(BArgs a) {
   const size_t tw_bytes = ((size_t)(a.M0max + a.M1max) * (16 + sizeof(cpx<T>)) + 15) & ~(size_t)15;
   double2* Ad = reinterpret_cast<double2*>(smem + tw_bytes);
   double2* Bd = Ad + a.cap;
-  unsigned char* slot = a.slots + (long long)blockIdx.x * a.slot_bytes;
   const bool f32 = sizeof(T) == 4;
+  // Tasks [0, ncoop) are taken by whole clusters (the CTAs of a cluster work on one task
+  // together, in the scratch slot of its rank-0 CTA); then every CTA takes tasks
+  // [ncoop, ntasks) on its own. The switch happens at the same pop in every CTA of a
+  // cluster, and no cluster barrier follows it.
+  cg::cluster_group cl = cg::this_cluster();
+  const int crank = (int)cl.block_rank(), csize = (int)cl.num_blocks();
+  bool coop = csize > 1 && a.ncoop > 0;
+  int parity = 0;
 
   for (;;) {
-    if (threadIdx.x == 0) s_task = atomicAdd(a.counter, 1);
-    __syncthreads();
-    const int task = s_task;
-    if (task >= a.ntasks) break;
+    Team tm{0, 1};
+    int task;
+    if (coop) {
+      tm = Team{crank, csize};
+      if (crank == 0 && threadIdx.x == 0) {
+        const int tk = atomicAdd(a.counter, 1);
+        for (int r = 0; r < csize; ++r) *cl.map_shared_rank(&s_task, r) = tk;
+      }
+      cl.sync();
+      task = s_task;
+      if (task >= a.ncoop) {
+        coop = false;
+        cl.sync();   // every CTA has read s_task before a later pop rewrites it
+        continue;
+      }
+    } else {
+      if (threadIdx.x == 0) s_task = a.ncoop + atomicAdd(a.counter2, 1);
+      __syncthreads();
+      task = s_task;
+      if (task >= a.ntasks) break;
+    }
+    unsigned char* slot = a.slots + (long long)(blockIdx.x - tm.rank) * a.slot_bytes;
     {
       // the task descriptor lives in shared memory (keeps the FFT plans out of registers)
       const int* src = reinterpret_cast<const int*>(a.tasks + task);
@@ -401,7 +469,7 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 2 : 1) k_batch(BArgs a) {
     sa.phase = phase;
     sa.sinc = sinc;
     sa.Mmax = Mmax;
-    for (long long i = threadIdx.x; i < (long long)t.nincl * 3 * Mmax; i += blockDim.x) {
+    for (long long i = tm.tid(); i < (long long)t.nincl * 3 * Mmax; i += tm.nth()) {
       const int n = (int)(i % Mmax);
       const int al_ = (int)((i / Mmax) % 3);
       const int j = (int)(i / (3LL * Mmax));
@@ -422,10 +490,10 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 2 : 1) k_batch(BArgs a) {
       const double xx = h * ns * t.invY[al_];
       sinc[i] = xx == 0.0 ? h : h * sinpi(xx) / (M_PI * xx);
     }
-    __syncthreads();
+    team_sync(tm);
     {
       const long long plane = (long long)M1 * Nxs;
-      for (long long e = threadIdx.x; e < plane; e += blockDim.x) {
+      for (long long e = tm.tid(); e < plane; e += tm.nth()) {
         const int ix = (int)(e % Nxs);
         const int iy = (int)(e / Nxs);
         const int ns[3] = {ix, sfreq(iy, M1), 0};
@@ -435,24 +503,26 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 2 : 1) k_batch(BArgs a) {
         for (int q = 0; q < t.ncomp; ++q) work[q * plane + e] = v[q];
       }
     }
-    __syncthreads();
+    team_sync(tm);
     {
       int flist[3] = {0, 1, 2};
       col_pass<double>(work, work, (long long)M1 * Nxs, (long long)M1 * Nxs, flist, t.ncomp, Nxs, M1, M1, M1,
-                       M1, +1, t.plan1, W1d, Ad, Bd, a.cap, nullptr);
+                       M1, +1, t.plan1, W1d, Ad, Bd, a.cap, nullptr, tm);
+      team_sync(tm);
       double dummy[4];
       row_pass<double>(2, work, (long long)M1 * Nxs, M1, Nxs, 0, M0, nullptr, t.ncomp, 1.0, nullptr, 0,
-                       coef64, t.plan0, W0d, Ad, Bd, a.cap, dummy);
+                       coef64, t.plan0, W0d, Ad, Bd, a.cap, dummy, tm);
+      team_sync(tm);
     }
     if (f32) {
-      for (long long i = threadIdx.x; i < (long long)t.ncomp * M1 * M0; i += blockDim.x)
+      for (long long i = tm.tid(); i < (long long)t.ncomp * M1 * M0; i += tm.nth())
         coefT[i] = T(coef64[i]);
-      __syncthreads();
+      team_sync(tm);
     }
 
     // ---- right-hand sides, x = p = 0
     double acc[4] = {0.0, 0.0, 0.0, 0.0};
-    for (long long e = threadIdx.x; e < fld; e += blockDim.x) {
+    for (long long e = tm.tid(); e < fld; e += tm.nth()) {
       const int kx = (int)(e % Nh);
       const int iy = (int)(e / Nh);
       const int ns[3] = {kx, sfreq(iy, N1), 0};
@@ -496,9 +566,9 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 2 : 1) k_batch(BArgs a) {
     const long long io_off = ((long long)t.prob * 2 + t.side) * 4 * fld;   // start of this task's block
     if (a.x0) {
       // warm start: x = Gamma x0, r = b - C x (one operator application), p = 0
-      __syncthreads();
+      team_sync(tm);
       const cpx<T>* x0 = reinterpret_cast<const cpx<T>*>(a.x0) + io_off;
-      for (long long e = threadIdx.x; e < 2 * fld; e += blockDim.x) {
+      for (long long e = tm.tid(); e < 2 * fld; e += tm.nth()) {
         const int r = (int)(e / fld);
         const long long k = e - r * fld;
         const int kx = (int)(k % Nh);
@@ -525,26 +595,29 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 2 : 1) k_batch(BArgs a) {
         s_rlist[0] = 0; s_rlist[1] = 1; s_nrl = 2;
         s_flist[0] = 0; s_flist[1] = 1; s_flist[2] = 2; s_flist[3] = 3; s_nfl = 4;
       }
-      __syncthreads();
-      col_pass<T>(vp, T2, fld, t2_fs, s_flist, s_nfl, Nh, N1, M1, N1, M1, +1, t.plan1, W1, At, Bt, capT, nullptr);
+      team_sync(tm);
+      col_pass<T>(vp, T2, fld, t2_fs, s_flist, s_nfl, Nh, N1, M1, N1, M1, +1, t.plan1, W1, At, Bt, capT, nullptr,
+                  tm);
+      team_sync(tm);
       double dummy0[4];
       row_pass<T>(0, T2, t2_fs, M1, Nh, Nh, M0, coefT, t.ncomp, T(scale), s_rlist, s_nrl, nullptr, t.plan0, W0,
-                  At, Bt, capT, dummy0);
+                  At, Bt, capT, dummy0, tm);
+      team_sync(tm);
       double pqd[2] = {0.0, 0.0};
       col_final<T>(T2, vq, vp, t2_fs, fld, s_rlist, s_nrl, Nh, N1, M1, t.invY[0], t.invY[1], t.side, t.plan1, W1,
-                   At, Bt, capT, pqd);
+                   At, Bt, capT, pqd, tm);
       // Rayleigh-Ritz on span{x0}: x = s x0 with s = (x0.b)/(x0.C x0) minimises the energy
       // functional along the start direction, so a start never does worse than x = 0
       double xb[2] = {0.0, 0.0};
-      for (long long i = threadIdx.x; i < 4 * fld; i += blockDim.x) {
+      for (long long i = tm.tid(); i < 4 * fld; i += tm.nth()) {
         const int r = (int)(i / (2 * fld));
         const cpx<T> pv = vp[i], bv = vr[i];
         const double w = (i % Nh) == 0 ? 1.0 : 2.0;
         xb[r] += w * ((double)pv.x * bv.x + (double)pv.y * bv.y);
       }
       for (int r = 0; r < 2; ++r) {
-        const double num = block_sum(xb[r], s_red);
-        const double den = block_sum(pqd[r], s_red);   // x0 . C x0 (col_final's partial sums)
+        const double num = team_sum(tm, xb[r], s_red, s_xch, parity);
+        const double den = team_sum(tm, pqd[r], s_red, s_xch, parity);   // x0 . C x0 (col_final's partial sums)
         if (threadIdx.x == 0) {
           const double s_ = den > 0.0 ? num / den : 0.0;
           s_alpha[r] = isfinite(s_) ? s_ : 0.0;
@@ -552,7 +625,7 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 2 : 1) k_batch(BArgs a) {
       }
       __syncthreads();
       acc[0] = acc[1] = 0.0;
-      for (long long i = threadIdx.x; i < 4 * fld; i += blockDim.x) {
+      for (long long i = tm.tid(); i < 4 * fld; i += tm.nth()) {
         const int r = (int)(i / (2 * fld));
         const T sr = T(s_alpha[r]);
         const cpx<T> xv = vx[i], qv = vq[i];
@@ -565,7 +638,7 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 2 : 1) k_batch(BArgs a) {
       }
     }
     for (int r = 0; r < 2; ++r) {
-      const double s = block_sum(acc[r], s_red);
+      const double s = team_sum(tm, acc[r], s_red, s_xch, parity);
       if (threadIdx.x == 0) {
         s_rr[r] = s;
         s_rrmin[r] = s;
@@ -594,24 +667,26 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 2 : 1) k_batch(BArgs a) {
       }
       __syncthreads();
       // p = r + beta p
-      for (long long i = threadIdx.x; i < 4 * fld; i += blockDim.x) {
+      for (long long i = tm.tid(); i < 4 * fld; i += tm.nth()) {
         const int r = (int)(i / (2 * fld));
         if (!s_active[r]) continue;
         const T b = T(s_beta[r]);
         const cpx<T> pv = vp[i], rv = vr[i];
         vp[i] = mk<T>(fma(b, pv.x, rv.x), fma(b, pv.y, rv.y));
       }
-      __syncthreads();
+      team_sync(tm);
       col_pass<T>(vp, T2, fld, t2_fs, s_flist, s_nfl, Nh, N1, M1, N1, M1, +1, t.plan1, W1, At, Bt, capT,
-                  nullptr);
+                  nullptr, tm);
+      team_sync(tm);
       double dummy[4];
       row_pass<T>(0, T2, t2_fs, M1, Nh, Nh, M0, coefT, t.ncomp, T(scale), s_rlist, s_nrl, nullptr, t.plan0, W0,
-                  At, Bt, capT, dummy);
+                  At, Bt, capT, dummy, tm);
+      team_sync(tm);
       double pq[2] = {0.0, 0.0};
       col_final<T>(T2, vq, vp, t2_fs, fld, s_rlist, s_nrl, Nh, N1, M1, t.invY[0], t.invY[1], t.side, t.plan1, W1,
-                   At, Bt, capT, pq);
+                   At, Bt, capT, pq, tm);
       for (int r = 0; r < 2; ++r) {
-        const double s = block_sum(pq[r], s_red);
+        const double s = team_sum(tm, pq[r], s_red, s_xch, parity);
         if (threadIdx.x == 0 && s_active[r]) {
           if (!(s > 0.0) || !isfinite(s)) {
             s_active[r] = 0;
@@ -624,7 +699,7 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 2 : 1) k_batch(BArgs a) {
       }
       __syncthreads();
       double rr[2] = {0.0, 0.0};
-      for (long long i = threadIdx.x; i < 4 * fld; i += blockDim.x) {
+      for (long long i = tm.tid(); i < 4 * fld; i += tm.nth()) {
         const int r = (int)(i / (2 * fld));
         if (!s_active[r]) continue;
         const T al_ = T(s_alpha[r]);
@@ -638,7 +713,7 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 2 : 1) k_batch(BArgs a) {
         rr[r] += w * ((double)rv.x * rv.x + (double)rv.y * rv.y);
       }
       for (int r = 0; r < 2; ++r) {
-        const double s = block_sum(rr[r], s_red);
+        const double s = team_sum(tm, rr[r], s_red, s_xch, parity);
         if (threadIdx.x == 0 && s_active[r]) {
           s_iters[r] += 1;
           if (!isfinite(s)) {
@@ -671,10 +746,10 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 2 : 1) k_batch(BArgs a) {
 
     if (a.fields) {
       cpx<T>* fo = reinterpret_cast<cpx<T>*>(a.fields) + io_off;
-      for (long long i = threadIdx.x; i < 4 * fld; i += blockDim.x) fo[i] = vx[i];
+      for (long long i = tm.tid(); i < 4 * fld; i += tm.nth()) fo[i] = vx[i];
     }
     // ---- FP64 re-projection of the fields and the exact double-grid energies
-    for (long long e = threadIdx.x; e < 2 * fld; e += blockDim.x) {
+    for (long long e = tm.tid(); e < 2 * fld; e += tm.nth()) {
       const int r = (int)(e / fld);
       const long long k = e - r * fld;
       const int kx = (int)(k % Nh);
@@ -700,27 +775,29 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 2 : 1) k_batch(BArgs a) {
       s_flist[0] = 0; s_flist[1] = 1; s_flist[2] = 2; s_flist[3] = 3;
       s_adde[0] = 1; s_adde[1] = 0; s_adde[2] = 0; s_adde[3] = 1;   // e_r in component r of field r
     }
-    __syncthreads();
+    team_sync(tm);
     col_pass<double>(x64, work, fld, t2_fs, s_flist, 4, Nh, N1, M1, N1, M1, +1, t.plan1, W1d, Ad, Bd, a.cap,
-                     s_adde);
+                     s_adde, tm);
+    team_sync(tm);
     double eacc[4] = {0.0, 0.0, 0.0, 0.0};
     row_pass<double>(1, work, t2_fs, M1, Nh, 0, M0, coef64, t.ncomp, 1.0, nullptr, 0, nullptr, t.plan0, W0d, Ad,
-                     Bd, a.cap, eacc);
+                     Bd, a.cap, eacc, tm);
     for (int i = 0; i < 4; ++i) {
-      const double s = block_sum(eacc[i], s_red);
-      if (threadIdx.x == 0) a.energy[(long long)task * 4 + i] = s * scale;
+      const double s = team_sum(tm, eacc[i], s_red, s_xch, parity);
+      if (threadIdx.x == 0 && tm.rank == 0) a.energy[(long long)task * 4 + i] = s * scale;
     }
-    if (threadIdx.x == 0)
+    if (threadIdx.x == 0 && tm.rank == 0)
       for (int r = 0; r < 2; ++r) {
         a.iters[task * 2 + r] = s_iters[r];
         a.status[task * 2 + r] = s_status[r];
         a.resid[task * 2 + r] = sqrt(fmax(s_rr[r], 0.0));
       }
-    __syncthreads();
+    team_sync(tm);
   }
 }
 
-template <typename T, int NT> cudaError_t launch_batch_nt(const BArgs& a, int nblocks, size_t smem, cudaStream_t s) {
+template <typename T, int NT>
+cudaError_t launch_batch_nt(const BArgs& a, int nblocks, size_t smem, int cluster, cudaStream_t s) {
   static size_t cache[16] = {};
   int dev = 0;
   cudaGetDevice(&dev);
@@ -730,37 +807,77 @@ template <typename T, int NT> cudaError_t launch_batch_nt(const BArgs& a, int nb
     if (e != cudaSuccess) return e;
     cache[dev] = smem;
   }
-  k_batch<T, NT><<<nblocks, NT, smem, s>>>(a);
-  return cudaGetLastError();
+  if (cluster <= 1) {
+    k_batch<T, NT><<<nblocks, NT, smem, s>>>(a);
+    return cudaGetLastError();
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(nblocks);
+  cfg.blockDim = dim3(NT);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = cluster;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_batch<T, NT>, a);
 }
 
-template <typename T> cudaError_t launch_batch(const BArgs& a, int nblocks, size_t smem, int threads, cudaStream_t s) {
+template <typename T>
+cudaError_t launch_batch(const BArgs& a, int nblocks, size_t smem, int threads, int cluster, cudaStream_t s) {
+  if (cluster != 1 && cluster != 2 && cluster != 4 && cluster != 8) return cudaErrorInvalidValue;
+  if (nblocks % cluster) return cudaErrorInvalidValue;
   switch (threads) {
-    case 256: return launch_batch_nt<T, 256>(a, nblocks, smem, s);
-    case 512: return launch_batch_nt<T, 512>(a, nblocks, smem, s);
-    case 1024: return launch_batch_nt<T, 1024>(a, nblocks, smem, s);
+    case 256: return launch_batch_nt<T, 256>(a, nblocks, smem, cluster, s);
+    case 512: return launch_batch_nt<T, 512>(a, nblocks, smem, cluster, s);
+    case 1024: return launch_batch_nt<T, 1024>(a, nblocks, smem, cluster, s);
     default: return cudaErrorInvalidValue;
   }
 }
 
-template <typename T, int NT> int batch_blocks_nt(size_t smem) {
+template <typename T, int NT> int batch_max_blocks_nt(size_t smem, int cluster) {
   if (smem > 48 * 1024) cudaFuncSetAttribute(k_batch<T, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  int n = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batch<T, NT>, NT, smem) != cudaSuccess) return 1;
-  return n > 0 ? n : 1;
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) sms = 1;
+  if (cluster <= 1) {
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batch<T, NT>, NT, smem) != cudaSuccess || n < 1) n = 1;
+    return n * sms;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(cluster * sms);
+  cfg.blockDim = dim3(NT);
+  cfg.dynamicSmemBytes = smem;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = cluster;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  int nc = 0;
+  if (cudaOccupancyMaxActiveClusters(&nc, k_batch<T, NT>, &cfg) != cudaSuccess || nc < 1) {
+    cudaGetLastError();
+    return 0;   // this cluster shape cannot be placed
+  }
+  return nc * cluster;
 }
 
-template <typename T> int batch_blocks_per_sm(size_t smem, int threads) {
+template <typename T> int batch_max_blocks(size_t smem, int threads, int cluster) {
   switch (threads) {
-    case 512: return batch_blocks_nt<T, 512>(smem);
-    case 1024: return batch_blocks_nt<T, 1024>(smem);
-    default: return batch_blocks_nt<T, 256>(smem);
+    case 512: return batch_max_blocks_nt<T, 512>(smem, cluster);
+    case 1024: return batch_max_blocks_nt<T, 1024>(smem, cluster);
+    default: return batch_max_blocks_nt<T, 256>(smem, cluster);
   }
 }
-template int batch_blocks_per_sm<double>(size_t, int);
-template int batch_blocks_per_sm<float>(size_t, int);
+template int batch_max_blocks<double>(size_t, int, int);
+template int batch_max_blocks<float>(size_t, int, int);
 
-template cudaError_t launch_batch<double>(const BArgs&, int, size_t, int, cudaStream_t);
-template cudaError_t launch_batch<float>(const BArgs&, int, size_t, int, cudaStream_t);
+template cudaError_t launch_batch<double>(const BArgs&, int, size_t, int, int, cudaStream_t);
+template cudaError_t launch_batch<float>(const BArgs&, int, size_t, int, int, cudaStream_t);
 
 }  // namespace homb

@@ -119,7 +119,9 @@ struct BTask {
 struct BArgs {
   const BTask* tasks;
   int ntasks;
-  int* counter;            // work queue head (zero before launch)
+  int* counter;            // queue head of the cooperative tasks (zero before launch)
+  int* counter2;           // queue head of the single-CTA tasks (zero before launch)
+  int ncoop;               // tasks [0, ncoop) are worked on by whole clusters
   const DevIncl* incl;
   const double2* tw64;
   const float2* tw32;
@@ -160,9 +162,12 @@ inline size_t batch_smem_bytes(int M0max, int M1max, int cap, int elem) {
   const size_t tw = ((size_t)(M0max + M1max) * (16 + elem) + 15) & ~(size_t)15;
   return tw + 2 * (size_t)cap * 16;
 }
-// threads per CTA: 256 (two CTAs per SM), 512 or 1024 (one CTA per SM)
-template <typename T> cudaError_t launch_batch(const BArgs& a, int nblocks, size_t smem, int threads, cudaStream_t s);
-template <typename T> int batch_blocks_per_sm(size_t smem, int threads);
+// threads per CTA: 256 (two CTAs per SM), 512 or 1024 (one CTA per SM); cluster: CTAs per
+// thread-block cluster (1, 2, 4 or 8; nblocks a multiple of it)
+template <typename T>
+cudaError_t launch_batch(const BArgs& a, int nblocks, size_t smem, int threads, int cluster, cudaStream_t s);
+// CTAs that can be resident at once on the device for a launch of this configuration
+template <typename T> int batch_max_blocks(size_t smem, int threads, int cluster);
 
 // launchers (return cudaGetLastError())
 template <typename T> cudaError_t launch_pencil(const PencilArgs& a, cudaStream_t s);

@@ -123,3 +123,46 @@ def test_benchmark_batch_properties(hb, solver):
 def test_batched_rejects_3d(hb, solver):
     with pytest.raises(hb.HombError):
         solver.batched([ms.cube_inclusion_3d(N=5)])
+
+
+@pytest.mark.parametrize("cluster", [2, 4, 8])
+@pytest.mark.parametrize("threads", [256, 1024])
+def test_cluster_cooperative_cells(hb, solver, refs, cluster, threads):
+    """The largest cells worked on by a whole thread-block cluster (every pass and
+    reduction split over its CTAs) give the oracle's bounds like single-CTA cells: FP64
+    within 1e-10 at tol 1e-12, also with ragged splits (cells of N 9, 13, 15, 23 mixed,
+    the cooperative ones N >= 13 here), and mixed precision within 1e-6."""
+    probs = small_batch()
+    try:
+        hb.binding.hom_set_batch_threads(solver.ctx, threads)
+        hb.binding.hom_set_batch_cluster(solver.ctx, cluster, 25)
+        out = solver.batched(probs, precision=hb.HOM_FP64, tol=1e-12)
+        assert (out["status"] == 0).all(), out["status"]
+        for i, ref in enumerate(refs):
+            for key in ("upper", "lower"):
+                assert rel(out[key][i], ref[key]) <= 1e-10, (i, key, rel(out[key][i], ref[key]))
+        mixed = solver.batched(probs, precision=hb.HOM_MIXED, tol=1e-6)
+        for i, ref in enumerate(refs):
+            for key in ("upper", "lower"):
+                assert rel(mixed[key][i], ref[key]) <= 1e-6, (i, key)
+            assert loewner_ge(mixed["upper"][i], mixed["lower"][i])
+    finally:
+        hb.binding.hom_set_batch_threads(solver.ctx, 0)
+        hb.binding.hom_set_batch_cluster(solver.ctx, 0, 0)
+
+
+def test_cluster_cooperative_benchmark_cells(hb, solver):
+    """Cluster-cooperative N = 113 and 203 cells of the benchmark batch equal the same
+    cells solved one CTA each (FP64, tol 1e-10: 1e-9 relative), with the graph replayed."""
+    probs = [ms.random_rectangles_2d(s) for s in range(24)]
+    base = solver.batched(probs, precision=hb.HOM_FP64, tol=1e-10)
+    try:
+        hb.binding.hom_set_batch_cluster(solver.ctx, 4, 225)
+        stream = torch.cuda.Stream()
+        for _ in range(2):
+            out = solver.batched(probs, precision=hb.HOM_FP64, tol=1e-10, graph=1, stream=stream.cuda_stream)
+        for i in range(len(probs)):
+            for key in ("upper", "lower"):
+                assert rel(out[key][i], base[key][i]) <= 1e-9, (i, key)
+    finally:
+        hb.binding.hom_set_batch_cluster(solver.ctx, 0, 0)
