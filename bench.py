@@ -439,7 +439,8 @@ def run_gpu(args):
 def batched_timings(hb, solver, dev, n=256, reps=3, n_seq=8):
     """The batched workload: n seeded random-rectangle 2D cells (N from {23, 63, 113, 203}),
     FP32 inner CG / FP64 bounds, tol 1e-4, one persistent launch replayed as a CUDA graph
-    after an autotuning pass; against plain FP64 hom_bounds one cell at a time on the same
+    after an autotuning pass (threads per CTA, chunk capacity, radix schedule, cluster size
+    for the largest cells); against plain FP64 hom_bounds one cell at a time on the same
     GPU (a sample of n_seq cells, extrapolated to n)."""
     import statistics as st_
     import torch
@@ -470,6 +471,7 @@ def batched_timings(hb, solver, dev, n=256, reps=3, n_seq=8):
     seq_ms = st_.mean(seq) * n
     return {"workload": f"{n} random-rectangle 2D cells, N from {{23,63,113,203}}, FP32 inner CG, FP64 bounds, tol {TOL:g}",
             "ms": ms_batch, "problems_per_s": n / (ms_batch * 1e-3), "launches": out["report"]["launches"],
+            "launch_config": out["report"]["config"],
             "max_iters": int(out["iters"].max()), "status_nonzero": int((out["status"] != 0).sum()),
             "sequential_fp64_ms_est": seq_ms, "speedup_vs_sequential_fp64": seq_ms / ms_batch,
             "sequential_note": f"plain FP64 hom_bounds per cell, mean of the first {n_seq} cells x {n}"}

@@ -128,6 +128,9 @@ typedef struct {
   int64_t launches;     /* CUDA kernels launched by the call                     */
   int64_t h2d_bytes;    /* host->device bytes copied by the call                 */
   int64_t d2h_bytes;    /* device->host bytes copied by the call                 */
+  int32_t batch_config[6]; /* hom_bounds_batched launch: threads per CTA, chunk
+                           capacity, radix schedule (1: 5/3, 2: composite), cluster
+                           size, smallest cooperative 2N-1, CTAs launched          */
 } hom_report;
 
 typedef struct hom_ctx hom_ctx;

@@ -47,7 +47,7 @@ class hom_opts(C.Structure):
 class hom_report(C.Structure):
     _fields_ = [("iters", (C.c_int32 * 3) * 2), ("resid", (C.c_double * 3) * 2), ("matvecs", C.c_int32),
                 ("status", (C.c_int32 * 3) * 2), ("ms_total", C.c_double), ("launches", C.c_int64),
-                ("h2d_bytes", C.c_int64), ("d2h_bytes", C.c_int64)]
+                ("h2d_bytes", C.c_int64), ("d2h_bytes", C.c_int64), ("batch_config", C.c_int32 * 6)]
 
 
 class hom_batch_io(C.Structure):
@@ -242,7 +242,9 @@ def hom_bounds_batched(ctx, problems, opts, d_ws, ws_bytes, stream=0, d_x0=None,
     return {"upper": np.array(up[:]).reshape(n, 2, 2), "lower": np.array(lo[:]).reshape(n, 2, 2),
             "status": np.array(stt[:]), "iters": np.array(its[:]).reshape(n, 2, 2), "code": code,
             "report": {"ms_total": rep.ms_total, "launches": rep.launches, "h2d_bytes": rep.h2d_bytes,
-                       "d2h_bytes": rep.d2h_bytes}}
+                       "d2h_bytes": rep.d2h_bytes,
+                       "config": dict(zip(("threads", "cap", "radix_schedule", "cluster", "coop_min_M", "ctas"),
+                                          list(rep.batch_config)))}}
 
 
 def hom_workspace_size(ctx, problem, opts):

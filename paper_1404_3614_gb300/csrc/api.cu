@@ -69,6 +69,7 @@ struct hom_ctx {
   struct Tuned { long long key; int cap, threads, sched, cluster, coopM; };
   std::vector<Tuned> tuned_cap;
   int batch_threads = 0;   // threads per batched CTA set by the caller (0: tuned / default)
+  int graph_launched[6] = {0, 0, 0, 0, 0, 0};   // launch configuration inside the batch graph
   int batch_cluster = 0;   // cluster size set by the caller (0: tuned / default)
   int batch_coopM = 0;     // with batch_cluster: cells at least this large are cooperative
 };
@@ -1370,6 +1371,7 @@ hom_status hom_bounds_batched(hom_ctx* ctx, int32_t n, const hom_problem* probs,
     const int g_ = std::min(bp.nslots_max, mx);
     return (g_ / cluster) * cluster;
   };
+  int launched[6] = {0, 0, 0, 0, 0, 0};   // threads, cap, schedule, cluster, coopM, CTAs
   auto enqueue = [&](int cap, int threads, int cluster, int coopM, int max_iter) -> hom_status {
     size_t smem = 0;
     int grid = grid_for(cap, threads, cluster, &smem);
@@ -1381,6 +1383,11 @@ hom_status hom_bounds_batched(hom_ctx* ctx, int32_t n, const hom_problem* probs,
     CK(h2d_copy(ctx, base + bp.o_tasks, ctx->pin_in, bp.in_bytes, st));
     CK(cudaMemsetAsync(base + bp.o_counter, 0, 2 * sizeof(int), st));
     const BArgs a = args_for(cap, max_iter, ncoop_for(cluster, coopM));
+    launched[0] = threads;
+    launched[1] = cap;
+    launched[3] = cluster;
+    launched[4] = cluster > 1 ? coopM : 0;
+    launched[5] = grid;
     if (f32) KL(launch_batch<float>(a, grid, smem, threads, cluster, st));
     else KL(launch_batch<double>(a, grid, smem, threads, cluster, st));
     CK(d2h_copy(ctx, ctx->pin_out, base + bp.o_energy, bp.out_bytes, st));
@@ -1492,10 +1499,12 @@ hom_status hom_bounds_batched(hom_ctx* ctx, int32_t n, const hom_problem* probs,
       ctx->graph = g;
       CK(cudaGraphInstantiate(&ctx->graph_exec, g, 0));
       ctx->graph_key = key;
+      for (int i = 0; i < 6; ++i) ctx->graph_launched[i] = launched[i];
     } else {
       ctx->h2d += bp.in_bytes;
       ctx->d2h += bp.out_bytes;
       ctx->launches += 1;
+      for (int i = 0; i < 6; ++i) launched[i] = ctx->graph_launched[i];
     }
     CK(cudaGraphLaunch(ctx->graph_exec, st));
   } else {
@@ -1551,6 +1560,8 @@ hom_status hom_bounds_batched(hom_ctx* ctx, int32_t n, const hom_problem* probs,
     rep->h2d_bytes = ctx->h2d;
     rep->d2h_bytes = ctx->d2h;
     rep->ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    launched[2] = sched == 0 ? (f32 ? 2 : 1) : sched;
+    for (int i = 0; i < 6; ++i) rep->batch_config[i] = launched[i];
   }
   if (worst == HOM_ERR_BREAKDOWN) ctx->err = "a batched solve broke down (see status[])";
   return worst == HOM_OK ? HOM_OK : HOM_WARN_NOT_CONVERGED;
