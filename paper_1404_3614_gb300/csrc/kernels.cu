@@ -121,7 +121,7 @@ __global__ void __launch_bounds__(kThreads) k_rhs(SpecArgs a, int side, int Nh, 
 template <typename T>
 __global__ void __launch_bounds__(kThreads) k_cg_update(cpx<T>* x, cpx<T>* r, const cpx<T>* p,
                                                          const cpx<T>* q, int C, long long field,
-                                                         int Nh, CgScalars* cg, double* partial,
+                                                         FastDiv fdNh, CgScalars* cg, double* partial,
                                                          int ld) {
   __shared__ double red[32];
   const int rhs = blockIdx.y;
@@ -138,7 +138,8 @@ __global__ void __launch_bounds__(kThreads) k_cg_update(cpx<T>* x, cpx<T>* r, co
     rv = mk<T>(fma(-al, qv.x, rv.x), fma(-al, qv.y, rv.y));
     x[base + e] = xv;
     r[base + e] = rv;
-    const double w = (e % Nh) == 0 ? 1.0 : 2.0;
+    const int ei = (int)e;   // < 2^31 elements per right-hand side (checked by the launcher)
+    const double w = ei - fdNh.div(ei) * (int)fdNh.d == 0 ? 1.0 : 2.0;
     acc += w * ((double)rv.x * rv.x + (double)rv.y * rv.y);
   }
   const double s = block_sum(acc, red);
@@ -264,7 +265,7 @@ __global__ void k_outer_check(CgScalars* cg, const double* partial, int ld, int 
 }
 
 __global__ void __launch_bounds__(kThreads) k_demote(const double2* r64, float2* r32, int C,
-                                                      long long field, int Nh, const CgScalars* outer,
+                                                      long long field, FastDiv fdNh, const CgScalars* outer,
                                                       double* partial, int ld) {
   __shared__ double red[32];
   const int rhs = blockIdx.y;
@@ -280,7 +281,8 @@ __global__ void __launch_bounds__(kThreads) k_demote(const double2* r64, float2*
       v = make_float2((float)w.x, (float)w.y);
     }
     r32[base + e] = v;
-    const double wt = (e % Nh) == 0 ? 1.0 : 2.0;
+    const int ei = (int)e;
+    const double wt = ei - fdNh.div(ei) * (int)fdNh.d == 0 ? 1.0 : 2.0;
     acc += wt * ((double)v.x * v.x + (double)v.y * v.y);
   }
   const double s = block_sum(acc, red);
@@ -405,10 +407,11 @@ template <typename T>
 cudaError_t launch_cg_update(void* x, void* r, const void* p, const void* q, int nrhs, int C,
                              long long field, int Nh, CgScalars* cg, double* partial, int nblk,
                              cudaStream_t s) {
+  if ((long long)C * field >= (1LL << 31)) return cudaErrorInvalidValue;
   dim3 grid(nblk, nrhs);
   k_cg_update<T><<<grid, kThreads, 0, s>>>(
       reinterpret_cast<cpx<T>*>(x), reinterpret_cast<cpx<T>*>(r), reinterpret_cast<const cpx<T>*>(p),
-      reinterpret_cast<const cpx<T>*>(q), C, field, Nh, cg, partial, nblk);
+      reinterpret_cast<const cpx<T>*>(q), C, field, FastDiv((uint32_t)Nh), cg, partial, nblk);
   return cudaGetLastError();
 }
 
@@ -424,8 +427,9 @@ cudaError_t launch_outer_check(CgScalars* cg, const double* partial, int ld, int
 }
 cudaError_t launch_demote(const double2* r64, float2* r32, int nrhs, int C, long long field, int Nh,
                           const CgScalars* outer, double* partial, int nblk, cudaStream_t s) {
+  if ((long long)C * field >= (1LL << 31)) return cudaErrorInvalidValue;
   dim3 grid(nblk, nrhs);
-  k_demote<<<grid, kThreads, 0, s>>>(r64, r32, C, field, Nh, outer, partial, nblk);
+  k_demote<<<grid, kThreads, 0, s>>>(r64, r32, C, field, FastDiv((uint32_t)Nh), outer, partial, nblk);
   return cudaGetLastError();
 }
 cudaError_t launch_promote_add(const float2* x32, double2* x64, long long n, cudaStream_t s) {

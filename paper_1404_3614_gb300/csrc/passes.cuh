@@ -37,6 +37,41 @@ __device__ __forceinline__ cpx<T>* fft_any(cpx<T>* a, cpx<T>* b, int G, const Ff
   else return fft_pencils<T>(a, b, G, plan.M, plan, W, dir);
 }
 
+// FP32 pencils of length 225 = 15 * 15 are transformed by warp-level in-register FFTs in
+// place (slab.cuh), with no ping-pong buffer (measured faster there; at 81 the shared-memory
+// Stockham passes stay ahead).
+template <typename T, int MT> constexpr int warp_fft_r() { return sizeof(T) == 4 && MT == 225 ? 15 : 0; }
+template <typename T> inline bool warp_fft_len(int M) { return sizeof(T) == 4 && M == 225; }
+
+template <typename T, int R>
+__device__ __forceinline__ void pencil_fft_inplace(cpx<T>* p, int l, const cpx<T>* Wt, int dir, bool on);
+
+// twiddles w_M^(l k) at [k][l] for the warp FFT of length R * R
+template <typename T, int R>
+__device__ __forceinline__ void stage_twiddles_kl(cpx<T>* Wt, const void* W) {
+  const cpx<T>* w = reinterpret_cast<const cpx<T>*>(W);
+  for (int t = threadIdx.x; t < R * R; t += blockDim.x) {
+    const int k = t / R;
+    Wt[t] = w[(t - k * R) * k];
+  }
+}
+
+// G contiguous pencils (stride R*R) in place, R lanes per pencil; ends with __syncthreads
+template <typename T, int R>
+__device__ __forceinline__ void fft_warp_all(cpx<T>* A, int G, const cpx<T>* Wt, int dir) {
+  constexpr int PW = 32 / R;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int sub = lane / R, l = lane - sub * R;
+  const bool act = sub < PW;
+  const int slots = (blockDim.x >> 5) * PW;
+  for (int g0 = 0; g0 < G; g0 += slots) {
+    const int g = g0 + warp * PW + sub;
+    const bool on = act && g < G;
+    pencil_fft_inplace<T, R>(A + (size_t)(on ? g : 0) * (R * R), l, Wt, dir, on);
+  }
+  __syncthreads();
+}
+
 // ---------------------------------------------------------------------------------
 // pencil pass along y or z (one component slab per CTA, XC contiguous positions)
 // ---------------------------------------------------------------------------------
@@ -53,7 +88,9 @@ __global__ void __launch_bounds__(kPassThreads) k_pencil(PencilArgs a) {
   if (a.cg != nullptr && !a.cg->active[rhs]) return;
   const int comp = (s / a.slabs_per_comp) % a.C;
   const int XC = min(a.XC, a.X - x0);
-  stage_twiddles<T>(Ws, a.W, M);
+  constexpr int WR = warp_fft_r<T, MT>();
+  if constexpr (WR > 0) stage_twiddles_kl<T, WR>(Ws, a.W);
+  else stage_twiddles<T>(Ws, a.W, M);
   const bool pad = a.dir > 0 && a.Pin != M;
   if (pad) {
     for (int t = threadIdx.x; t < XC * M; t += blockDim.x) A[t] = mk<T>(T(0), T(0));
@@ -79,7 +116,13 @@ __global__ void __launch_bounds__(kPassThreads) k_pencil(PencilArgs a) {
     A[xx * M + pos] = v;
   }
   __syncthreads();
-  cpx<T>* res = fft_any<T, MT>(A, B, XC, a.plan, Ws, a.dir);
+  cpx<T>* res;
+  if constexpr (WR > 0) {
+    fft_warp_all<T, WR>(A, XC, Ws, a.dir);
+    res = A;
+  } else {
+    res = fft_any<T, MT>(A, B, XC, a.plan, Ws, a.dir);
+  }
   cpx<T>* out = reinterpret_cast<cpx<T>*>(a.out) + (long long)s * a.out_slab;
   const bool trunc = a.dir < 0 && a.Pout != M;
   for (int t = threadIdx.x; t < a.Pout * a.XC; t += blockDim.x) {
@@ -100,14 +143,16 @@ __global__ void __launch_bounds__(kPassThreads) k_final(FinalArgs a) {
   const int M = MT > 0 ? MT : a.M;
   const int C = a.C;
   cpx<T>* Ws = reinterpret_cast<cpx<T>*>(smem);
+  constexpr int WR = warp_fft_r<T, MT>();
   cpx<T>* A = Ws + M;
-  cpx<T>* B = A + (size_t)C * a.XC * M;
-  double* red = reinterpret_cast<double*>(B + (size_t)C * a.XC * M);
+  cpx<T>* B = A + (size_t)C * a.XC * M;   // ping-pong half (not allocated for the warp FFT)
+  double* red = reinterpret_cast<double*>(WR > 0 ? B : B + (size_t)C * a.XC * M);
   const int rhs = blockIdx.y;
   if (a.cg != nullptr && !a.cg->active[rhs]) return;
   const int x0 = blockIdx.x * a.XC;
   const int XC = min(a.XC, a.X - x0);
-  stage_twiddles<T>(Ws, a.W, M);
+  if constexpr (WR > 0) stage_twiddles_kl<T, WR>(Ws, a.W);
+  else stage_twiddles<T>(Ws, a.W, M);
   const cpx<T>* in = reinterpret_cast<const cpx<T>*>(a.in) + (long long)rhs * C * a.in_comp;
   const int per = M * a.XC;
   for (int t = threadIdx.x; t < C * per; t += blockDim.x) {
@@ -119,7 +164,13 @@ __global__ void __launch_bounds__(kPassThreads) k_final(FinalArgs a) {
     A[(g * XC + xx) * M + p] = in[(long long)g * a.in_comp + (long long)p * a.X + x0 + xx];
   }
   __syncthreads();
-  cpx<T>* res = fft_any<T, MT>(A, B, C * XC, a.plan, Ws, -1);
+  cpx<T>* res;
+  if constexpr (WR > 0) {
+    fft_warp_all<T, WR>(A, C * XC, Ws, -1);
+    res = A;
+  } else {
+    res = fft_any<T, MT>(A, B, C * XC, a.plan, Ws, -1);
+  }
   cpx<T>* out = reinterpret_cast<cpx<T>*>(a.out) + (long long)rhs * C * a.out_comp;
   const cpx<T>* pdir = (a.cg && a.aux) ? reinterpret_cast<const cpx<T>*>(a.aux) + (long long)rhs * C * a.out_comp
                                        : nullptr;
@@ -411,7 +462,7 @@ static cudaError_t smem_attr(K kernel, size_t bytes, size_t* cache) {
 template <typename T> int pencil_xc(int M, int X, int C) {
   const size_t sz = sizeof(cpx<T>);
   const size_t fixed = M * sz + 512;
-  const size_t per = 2 * (size_t)C * M * sz;
+  const size_t per = (warp_fft_len<T>(M) ? 1 : 2) * (size_t)C * M * sz;
   long long xc = (long long)((kPassSmemBudget > fixed ? kPassSmemBudget - fixed : 0) / per);
   if (xc < 1) xc = (fixed + per <= kPassSmemMax) ? 1 : 0;
   if (xc > 32) xc = 32;
@@ -442,7 +493,8 @@ template <typename T> int xpass_yb(int M, int rpp, int planes) {
 }
 
 template <typename T, int MT> cudaError_t launch_pencil_m(PencilArgs a, cudaStream_t s) {
-  const size_t smem = (size_t)a.plan.M * sizeof(cpx<T>) * (1 + 2 * (size_t)a.XC);
+  const size_t bufs = warp_fft_r<T, MT>() > 0 ? 1 : 2;
+  const size_t smem = (size_t)a.plan.M * sizeof(cpx<T>) * (1 + bufs * (size_t)a.XC);
   static size_t cache[16] = {};
   cudaError_t e = smem_attr(k_pencil<T, MT>, smem, cache);
   if (e != cudaSuccess) return e;
@@ -452,7 +504,8 @@ template <typename T, int MT> cudaError_t launch_pencil_m(PencilArgs a, cudaStre
 }
 
 template <typename T, int MT> cudaError_t launch_final_m(FinalArgs a, cudaStream_t s) {
-  const size_t smem = (size_t)a.M * sizeof(cpx<T>) * (1 + 2 * (size_t)a.C * a.XC) + 32 * sizeof(double);
+  const size_t bufs = warp_fft_r<T, MT>() > 0 ? 1 : 2;
+  const size_t smem = (size_t)a.M * sizeof(cpx<T>) * (1 + bufs * (size_t)a.C * a.XC) + 32 * sizeof(double);
   static size_t cache[16] = {};
   cudaError_t e = smem_attr(k_final<T, MT>, smem, cache);
   if (e != cudaSuccess) return e;
