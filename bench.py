@@ -44,7 +44,7 @@ FP64_PEAK_TFLOPS = 1.25     # nominal GB300 FP64 (the recipe's table); a probe m
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one k_xpass<double, 81> launch
 # on the 3D N = 41 cube workload (3 fields, isotropic coefficient), from one ncu capture of
 # the build whose kernel sources hash to `sha256_16`; reported only while they still do.
-XPASS_TRAFFIC = {"sha256_16": "77596041bd40b489", "bytes": 24162304 + 32512,
+XPASS_TRAFFIC = {"sha256_16": "2850442042cdb8ba", "bytes": 24162304 + 29696,
                  "sources": ("common.cuh", "kernels.cuh", "passes.cuh", "passes_f64.cu"),
                  "capture": "profiles/xpass_f64_cube3d_N41.md"}
 
@@ -94,6 +94,24 @@ def run_learned(args):
                                        epochs=args.learned_epochs, batch=32, width=32, modes=12, layers=4,
                                        proj=128, tol=TOL, precision="mixed", solver=solver)
     print(json.dumps({"workload": "learned warm start, random-rectangle cells", **res}), flush=True)
+    solver.close()
+    return 0
+
+
+def run_batched_only(args):
+    """The batched workload alone (for kernel captures): `--batch-n` random-rectangle cells."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1404_3614_gb300 as hb
+    solver = hb.Bounds(0)
+    fixed = args.batch_threads > 0 or args.batch_cluster > 0
+    if args.batch_threads:
+        hb.binding.hom_set_batch_threads(solver.ctx, args.batch_threads)
+    if args.batch_cluster:
+        hb.binding.hom_set_batch_cluster(solver.ctx, args.batch_cluster, args.batch_coop_M)
+    res = batched_timings(hb, solver, torch.device("cuda", 0), n=args.batch_n, n_seq=2, autotune=0 if fixed else 1)
+    print(json.dumps({"batched": res}), flush=True)
     solver.close()
     return 0
 
@@ -436,7 +454,7 @@ def run_gpu(args):
     return 0
 
 
-def batched_timings(hb, solver, dev, n=256, reps=3, n_seq=8):
+def batched_timings(hb, solver, dev, n=256, reps=3, n_seq=8, autotune=1):
     """The batched workload: n seeded random-rectangle 2D cells (N from {23, 63, 113, 203}),
     FP32 inner CG / FP64 bounds, tol 1e-4, one persistent launch replayed as a CUDA graph
     after an autotuning pass (threads per CTA, chunk capacity, radix schedule, cluster size
@@ -447,7 +465,8 @@ def batched_timings(hb, solver, dev, n=256, reps=3, n_seq=8):
     import microstructures as ms
     probs = [ms.random_rectangles_2d(s) for s in range(n)]
     stream = torch.cuda.Stream(device=dev)
-    out = solver.batched(probs, precision=hb.HOM_MIXED, tol=TOL, autotune=1, graph=1, stream=stream.cuda_stream)
+    out = solver.batched(probs, precision=hb.HOM_MIXED, tol=TOL, autotune=autotune, graph=1,
+                         stream=stream.cuda_stream)
     times = []
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
     for _ in range(reps):
@@ -546,6 +565,11 @@ def main():
     ap.add_argument("--workload", default="cube3d_N41", choices=sorted(WORKLOADS))
     ap.add_argument("--matvec-only", action="store_true", help="operator applications only")
     ap.add_argument("--reps", type=int, default=20)
+    ap.add_argument("--batched-only", action="store_true", help="the batched workload only")
+    ap.add_argument("--batch-n", type=int, default=256, help="cells in the batched workload")
+    ap.add_argument("--batch-threads", type=int, default=0, help="fix the threads per CTA (no autotune)")
+    ap.add_argument("--batch-cluster", type=int, default=0, help="fix the cluster size (no autotune)")
+    ap.add_argument("--batch-coop-M", type=int, default=225, help="with --batch-cluster: cooperative 2N-1")
     ap.add_argument("--learned", action="store_true", help="learned warm-start workload only")
     ap.add_argument("--learned-N", type=int, default=63)
     ap.add_argument("--learned-train", type=int, default=20000)
@@ -558,6 +582,8 @@ def main():
         return run_reference(args)
     if args.matvec_only:
         return run_matvec_only(args)
+    if args.batched_only:
+        return run_batched_only(args)
     if args.learned:
         return run_learned(args)
     return run_gpu(args)
