@@ -47,7 +47,10 @@ class WarmStart:
         torch = self.torch
         out = torch.empty((len(problems), self.N, self.N, 1), dtype=torch.float32, device=self.dev)
         ws = torch.empty(1 << 22, dtype=torch.uint8, device=self.dev)
-        bd.hom_net_features(self.ctx, problems, out.data_ptr(), ws.data_ptr(), ws.numel())
+        chunk = 2048   # inclusion tables of 2048 cells fit the 4 MiB staging area
+        for s in range(0, len(problems), chunk):
+            part = problems[s:s + chunk]
+            bd.hom_net_features(self.ctx, part, out[s:s + len(part)].data_ptr(), ws.data_ptr(), ws.numel())
         out.mul_(1.0 / 3.0)
         return out
 
@@ -135,7 +138,7 @@ class WarmStart:
 
 def train_and_evaluate(N=63, n_train=20000, n_test=1024, epochs=20, batch=32, width=32, modes=12, layers=4,
                        proj=128, seed_train=1000, seed_test=100000, tol=1e-4, precision="mixed", lr=2e-3,
-                       gen_tol=1e-6, solver=None):
+                       gen_tol=1e-6, solver=None, tight_tol=1e-8):
     """The learned warm-start workload: random-rectangle cells on an N grid (the batched
     workload's distribution at one N). Returns a dict of measurements."""
     import torch
@@ -174,6 +177,11 @@ def train_and_evaluate(N=63, n_train=20000, n_test=1024, epochs=20, batch=32, wi
     warm, _ = ws.solve(test_probs, prec, tol, x0=x0)
     torch.cuda.synchronize()
     t_warm = time.perf_counter() - t0
+    # the same comparison at a tight tolerance, in FP64 (the FP32 inner CG of the batched
+    # mixed path stops near FP32 accuracy)
+    x0_64 = ws.grid_to_fields(pred, bd.HOM_FP64)
+    zero_t, _ = ws.solve(test_probs, bd.HOM_FP64, tight_tol)
+    warm_t, _ = ws.solve(test_probs, bd.HOM_FP64, tight_tol, x0=x0_64)
     # the network's field alone (no CG iteration) is a conforming field: a valid, looser bound
     net_only, _ = ws.solve(test_probs, prec, tol, x0=x0, max_iter=0)
     it_zero = zero["iters"].reshape(n_test, -1).sum(axis=1)
@@ -197,6 +205,9 @@ def train_and_evaluate(N=63, n_train=20000, n_test=1024, epochs=20, batch=32, wi
         "loss_first_epoch": hist[0] if hist else None, "loss_last_epoch": hist[-1] if hist else None,
         "iters_zero_mean": float(it_zero.mean()), "iters_warm_mean": float(it_warm.mean()),
         "iters_saved_frac": float(1.0 - it_warm.mean() / max(it_zero.mean(), 1e-300)),
+        "tight_tol": tight_tol,
+        "iters_zero_mean_tight": float(zero_t["iters"].reshape(n_test, -1).sum(axis=1).mean()),
+        "iters_warm_mean_tight": float(warm_t["iters"].reshape(n_test, -1).sum(axis=1).mean()),
         "time_zero_s": t_zero, "time_warm_s": t_warm, "time_data_s": t_data, "time_train_s": t_train,
         "time_geometry_s": t_probs,
         "max_rel_bound_diff": float(max(rel)), "ordering_ok": bool(ok),
