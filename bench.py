@@ -39,6 +39,7 @@ TOL = 1e-4
 # property of the problem (CG in exact arithmetic); measured by running the oracle's
 # own CG to completion, pinned by tests/test_bench_host.py.
 ORACLE_ITERS = {"primal": 46, "dual": 24}
+HBM_PEAK_GBS = 6782.8       # measured copy bandwidth of the GB300s (MEASURED_PEAKS.json)
 FP64_PEAK_TFLOPS = 1.25     # nominal GB300 FP64 (the recipe's table); a probe measured 1.256
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one k_xpass<double, 81> launch
@@ -395,6 +396,11 @@ def run_gpu(args):
 
     # one operator application (3 fields) per precision, through hom_matvec
     mv = matvec_timings(hb, solver, problem, dev, stream)
+    # the 225^3 operator of the 16-ball cell, where the HBM fraction is claimed
+    mv_large = None
+    if args.workload != "spheres3d_N113":
+        mv_large = matvec_timings(hb, solver, workload("spheres3d_N113"), dev, stream, reps=10)
+        mv_large["workload"] = WORKLOADS["spheres3d_N113"]
     batched = None if args.no_batched else batched_timings(hb, solver, dev)
 
     # roofline of the dominant kernel family
@@ -436,6 +442,7 @@ def run_gpu(args):
                           "speedup_vs_this": ms_step / alt_ms if alt_ms > 0 else None,
                           "upper_11": float(oo["upper"][0, 0]), "lower_11": float(oo["lower"][0, 0])},
         "matvec": mv,
+        "matvec_225": mv_large,
         "batched": batched,
         "kernel_families_ms_one_step": {k: v[1] for k, v in fam_ms.items()},
         "roofline": roof,
@@ -547,8 +554,9 @@ def matvec_timings(hb, solver, problem, dev, stream, reps=20, precisions=("fp64"
         flops = sum(family_flops_per_launch(problem, f, d) * (2 if f == "ypass" else 1)
                     for f in ("zpass", "ypass", "xpass", "final"))
         nbytes = matvec_bytes(problem, 8 if name == "fp64" else 4)
-        out[name] = {"ms": ms, "fft_tflops": flops / (ms * 1e-3) / 1e12, "fields": d,
-                     "model_bytes": nbytes, "model_gbs": nbytes / (ms * 1e-3) / 1e9}
+        gbs = nbytes / (ms * 1e-3) / 1e9
+        out[name] = {"ms": ms, "matvecs_per_s": 1e3 / ms, "fft_tflops": flops / (ms * 1e-3) / 1e12, "fields": d,
+                     "model_bytes": nbytes, "model_gbs": gbs, "model_hbm_frac": gbs / HBM_PEAK_GBS}
     return out
 
 

@@ -314,8 +314,9 @@ hom_status hom_matvec_noalloc(hom_ctx* ctx, const hom_problem* prob, int32_t sid
 /* The 3D operator with an isotropic coefficient and equal x and y transform lengths
  * M = R * R (R in 3, 5, 9, 15) fuses the inverse y transforms, the x row pass and the
  * forward y transforms into one pass over (rhs, component, z) slabs held in shared memory
- * (enable != 0, the default). enable = 0 runs them as three separate passes; the results
- * agree to rounding. Applies to later calls on this context. */
+ * (enable = 1, the default: warps per CTA chosen from the slab's shared memory; 4..24 in
+ * steps of 4 asks for that many warps where they fit). enable = 0 runs them as three separate
+ * passes; the results agree to rounding. Applies to later calls on this context. */
 hom_status hom_set_slab_pass(hom_ctx* ctx, int32_t enable);
 
 /* Threads per CTA of the persistent batched kernel: 256 (two CTAs per SM), 512 or 1024

@@ -65,6 +65,7 @@ struct hom_ctx {
   std::vector<CgGraph> cg_graphs;
   bool graphs_off = false;
   bool slab_on = true;   // fused y-x-y slab pass where it applies
+  int slab_warps = 0;     // warps per slab CTA chosen by the caller (0: automatic)
   std::vector<long long> graph_key;
   struct Tuned { long long key; int cap, threads, sched, cluster, coopM; };
   std::vector<Tuned> tuned_cap;
@@ -582,6 +583,7 @@ struct Runner {
       sl.in = T1; sl.out = T1; sl.coef = coef; sl.W = W(0); sl.cg = cg;
       sl.nrc = R * C; sl.C = C; sl.Mz = Mz; sl.M = Mx; sl.Ny = Ny; sl.Nh = Nh;
       sl.scale = 1.0 / (double)g.grid;
+      sl.warps = ctx->slab_warps;
       KL(launch_slab<T>(sl, st));
       fin = T1;
     } else {
@@ -1759,7 +1761,10 @@ hom_status hom_set_batch_cluster(hom_ctx* ctx, int32_t cluster, int32_t coop_min
 
 hom_status hom_set_slab_pass(hom_ctx* ctx, int32_t enable) {
   if (!ctx) return HOM_ERR_INVALID_ARG;
+  if (enable < 0 || (enable > 1 && (enable < 4 || enable > 24 || enable % 4)))
+    return fail(ctx, HOM_ERR_INVALID_ARG, "slab pass: 0 (off), 1 (automatic) or 4..24 warps in steps of 4");
   ctx->slab_on = enable != 0;
+  ctx->slab_warps = enable > 1 ? enable : 0;
   return HOM_OK;
 }
 

@@ -80,6 +80,7 @@ struct SlabArgs {
   const CgScalars* cg;  // skip right-hand sides that have converged (may be NULL)
   int nrc, C, Mz, M, Ny, Nh;
   double scale;         // 1 / |M|
+  int warps;            // warps per CTA, 0: automatic
 };
 
 struct DevIncl {

@@ -19,7 +19,7 @@
 
 namespace homb {
 
-constexpr int kSlabMaxThreads = 512;
+constexpr int kSlabMaxThreads = 768;
 
 // In-place FFT of one contiguous pencil of length R*R by the R lanes of a lane group
 // (lane index l < R). Every lane of the warp calls it (on = false: no memory access).
@@ -216,18 +216,36 @@ template <typename T> int slab_warps(int M, int Nh) {
   // leave 32 mod R lanes of every warp issuing FP64 work on zeros
   if (R == 0 || sizeof(T) == 8) return 0;
   const size_t elem = sizeof(cpx<T>);
-  // eight warps when at least two CTAs fit on an SM, else sixteen for latency hiding
+  // eight warps when at least two CTAs fit on an SM; else one CTA per SM with the fewest
+  // warps that reach the fewest rounds of lane-group tasks (two column rounds, weight 1
+  // each, plus row-pair rounds, weight 2.5), measured best at 225^3 (20 warps: 0.44 ms,
+  // 16: 0.47, 24: 0.47)
   if (2 * slab_smem_bytes(M, R, Nh, 8, elem) <= 220 * 1024) return 8;
-  if (slab_smem_bytes(M, R, Nh, 16, elem) <= 220 * 1024) return 16;
-  if (slab_smem_bytes(M, R, Nh, 8, elem) <= 220 * 1024) return 8;
-  return 0;
+  const int PW = 32 / R, npairs = (M + 1) / 2;
+  int best = 0;
+  double best_cost = 1e30;
+  for (int w = 8; w <= 24; w += 4) {
+    if (slab_smem_bytes(M, R, Nh, w, elem) > 220 * 1024) break;
+    const int slots = w * PW;
+    const double cost = 2.0 * ((Nh + slots - 1) / slots) + 2.5 * ((npairs + slots - 1) / slots);
+    if (cost < best_cost - 1e-9) {
+      best_cost = cost;
+      best = w;
+    }
+  }
+  return best;
 }
 
 template <typename T> cudaError_t launch_slab(const SlabArgs& a, cudaStream_t s) {
   if constexpr (sizeof(T) != 4) {
     return cudaErrorNotSupported;
   } else {
-    const int warps = slab_warps<T>(a.M, a.Nh);
+    int warps = slab_warps<T>(a.M, a.Nh);
+    if (warps && a.warps > 0) {   // a caller's choice, where it fits
+      const int r = a.M == 225 ? 15 : (a.M == 81 ? 9 : (a.M == 25 ? 5 : 3));
+      if (a.warps * 32 <= kSlabMaxThreads && slab_smem_bytes(a.M, r, a.Nh, a.warps, sizeof(cpx<T>)) <= 220 * 1024)
+        warps = a.warps;
+    }
     switch (warps ? a.M : 0) {
       case 9: return launch_slab_r<T, 3>(a, warps, s);
       case 25: return launch_slab_r<T, 5>(a, warps, s);
