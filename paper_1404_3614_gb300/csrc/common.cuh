@@ -360,21 +360,90 @@ __device__ __forceinline__ void cbfly(const cpx<T>* __restrict__ src, cpx<T>* __
   for (int q = 0; q < R; ++q) dst[base + q * Ns] = v[q];
 }
 
+// Radix-3 butterflies of a first stage whose middle inputs are all zero (a zero-padded
+// spectrum), and of a last stage whose middle outputs are not needed (a truncated one).
+template <typename T>
+__device__ __forceinline__ void dft3_mid_in0(cpx<T>* v, int dir) {   // v[1] == 0
+  const T h = T(0.5);
+  const T s3 = T(0.86602540378443864676372317075294);
+  const cpx<T> a = v[0], c = v[2];
+  const cpx<T> t2 = mk<T>(fma(-h, c.x, a.x), fma(-h, c.y, a.y));
+  const cpx<T> it3 = rot<T>(mk<T>(-s3 * c.x, -s3 * c.y), dir > 0 ? 1 : -1);
+  v[0] = add<T>(a, c);
+  v[1] = add<T>(t2, it3);
+  v[2] = sub<T>(t2, it3);
+}
+template <typename T>
+__device__ __forceinline__ void dft3_skip_out1(cpx<T>* v, int dir) {   // v[1] left undefined
+  const T h = T(0.5);
+  const T s3 = T(0.86602540378443864676372317075294);
+  const cpx<T> t1 = add<T>(v[1], v[2]);
+  const cpx<T> t2 = mk<T>(fma(-h, t1.x, v[0].x), fma(-h, t1.y, v[0].y));
+  const cpx<T> it3 = rot<T>(scl<T>(sub<T>(v[1], v[2]), s3), dir > 0 ? 1 : -1);
+  v[0] = add<T>(v[0], t1);
+  v[2] = sub<T>(t2, it3);
+}
+
+// prune bit 1: the first stage (radix 3, stride nb = M/3) reads only inputs j and j + 2 nb
+// (the inputs j + nb are zero padding); bit 2: the last stage (radix 3) writes only outputs
+// base and base + 2 Ns (the outputs base + Ns are truncated away). The caller checks that
+// the padding / truncation covers those positions.
 template <typename T, int M, int S, bool BIG>
-__device__ __forceinline__ cpx<T>* cfft_from(cpx<T>* a, cpx<T>* b, int G, const cpx<T>* W, int dir) {
+__device__ __forceinline__ cpx<T>* cfft_from(cpx<T>* a, cpx<T>* b, int G, const cpx<T>* W, int dir,
+                                             int prune = 0) {
   if constexpr (S >= cf_nstages(M, BIG)) {
     return a;
   } else {
     constexpr int R = cf_radix(M, S, BIG);
     constexpr int Ns = cf_ns(M, S, BIG);
     constexpr int nb = M / R;
+    constexpr bool last = S + 1 == cf_nstages(M, BIG);
+    if constexpr (R == 3 && S == 0 && !last) {
+      if (prune & 1) {
+        for (int t = threadIdx.x; t < G * nb; t += blockDim.x) {
+          const int g = t / nb;
+          const int j = t - g * nb;
+          const cpx<T>* src = a + g * M;
+          cpx<T> v[3] = {src[j], mk<T>(T(0), T(0)), src[j + 2 * nb]};
+          dft3_mid_in0<T>(v, dir);
+          cpx<T>* dst = b + g * M;
+#pragma unroll
+          for (int q = 0; q < 3; ++q) dst[3 * j + q] = v[q];   // Ns = 1: base = 3 j
+        }
+        __syncthreads();
+        return cfft_from<T, M, S + 1, BIG>(b, a, G, W, dir, prune);
+      }
+    }
+    if constexpr (R == 3 && last && S > 0) {
+      if (prune & 2) {
+        for (int t = threadIdx.x; t < G * nb; t += blockDim.x) {
+          const int g = t / nb;
+          const int j = t - g * nb;
+          const cpx<T>* src = a + g * M;
+          const int k = j % Ns;
+          cpx<T> v[3] = {src[j], src[j + nb], src[j + 2 * nb]};
+          if (k) {
+            constexpr int step = M / (Ns * R);
+            v[1] = mulc<T>(v[1], W[k * step], dir > 0);
+            v[2] = mulc<T>(v[2], W[2 * k * step], dir > 0);
+          }
+          dft3_skip_out1<T>(v, dir);
+          cpx<T>* dst = b + g * M;
+          const int base = (j / Ns) * Ns * R + k;
+          dst[base] = v[0];
+          dst[base + 2 * Ns] = v[2];
+        }
+        __syncthreads();
+        return b;
+      }
+    }
     for (int t = threadIdx.x; t < G * nb; t += blockDim.x) {
       const int g = t / nb;
       const int j = t - g * nb;
       cbfly<T, M, R, Ns>(a + g * M, b + g * M, j, W, dir);
     }
     __syncthreads();
-    return cfft_from<T, M, S + 1, BIG>(b, a, G, W, dir);
+    return cfft_from<T, M, S + 1, BIG>(b, a, G, W, dir, prune);
   }
 }
 
@@ -382,8 +451,15 @@ __device__ __forceinline__ cpx<T>* cfft_from(cpx<T>* a, cpx<T>* b, int G, const 
 // FP32 uses the composite register radices (fewer shared-memory passes); FP64 keeps
 // radices 3 and 5, which need the fewest FP64 operations.
 template <typename T, int M>
-__device__ __forceinline__ cpx<T>* cfft(cpx<T>* a, cpx<T>* b, int G, const cpx<T>* W, int dir) {
-  return cfft_from<T, M, 0, (sizeof(T) == 4)>(a, b, G, W, dir);
+__device__ __forceinline__ cpx<T>* cfft(cpx<T>* a, cpx<T>* b, int G, const cpx<T>* W, int dir, int prune = 0) {
+  return cfft_from<T, M, 0, (sizeof(T) == 4)>(a, b, G, W, dir, prune);
+}
+
+// Prune bits valid for a length-M transform whose spectrum is nonzero (inverse) or needed
+// (forward) only at [0, lo) and (M - lo, M): the middle third of a radix-3 first / last
+// stage, [M/3, 2M/3), must lie inside [lo, M - lo].
+__host__ __device__ inline bool prune3_ok(int M, int lo) {
+  return M % 3 == 0 && M / 3 >= lo && 2 * (M / 3) - 1 <= M - lo;
 }
 
 // Deterministic block sum of one double per thread (fixed tree order).

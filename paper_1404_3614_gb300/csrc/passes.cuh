@@ -32,8 +32,8 @@ __device__ __forceinline__ void stage_twiddles(cpx<T>* Ws, const void* W, int M)
 
 template <typename T, int MT>
 __device__ __forceinline__ cpx<T>* fft_any(cpx<T>* a, cpx<T>* b, int G, const FftPlan& plan,
-                                           const cpx<T>* W, int dir) {
-  if constexpr (MT > 0) return cfft<T, MT>(a, b, G, W, dir);
+                                           const cpx<T>* W, int dir, int prune = 0) {
+  if constexpr (MT > 0) return cfft<T, MT>(a, b, G, W, dir, prune);
   else return fft_pencils<T>(a, b, G, plan.M, plan, W, dir);
 }
 
@@ -121,7 +121,9 @@ __global__ void __launch_bounds__(kPassThreads) k_pencil(PencilArgs a) {
     fft_warp_all<T, WR>(A, XC, Ws, a.dir);
     res = A;
   } else {
-    res = fft_any<T, MT>(A, B, XC, a.plan, Ws, a.dir);
+    const bool trunc_ = a.dir < 0 && a.Pout != M;
+    const int prune = (pad && prune3_ok(M, half + 1) ? 1 : 0) | (trunc_ && prune3_ok(M, half + 1) ? 2 : 0);
+    res = fft_any<T, MT>(A, B, XC, a.plan, Ws, a.dir, prune);
   }
   cpx<T>* out = reinterpret_cast<cpx<T>*>(a.out) + (long long)s * a.out_slab;
   const bool trunc = a.dir < 0 && a.Pout != M;
@@ -169,7 +171,7 @@ __global__ void __launch_bounds__(kPassThreads) k_final(FinalArgs a) {
     fft_warp_all<T, WR>(A, C * XC, Ws, -1);
     res = A;
   } else {
-    res = fft_any<T, MT>(A, B, C * XC, a.plan, Ws, -1);
+    res = fft_any<T, MT>(A, B, C * XC, a.plan, Ws, -1, prune3_ok(M, (a.Nlog - 1) / 2 + 1) ? 2 : 0);
   }
   cpx<T>* out = reinterpret_cast<cpx<T>*>(a.out) + (long long)rhs * C * a.out_comp;
   const cpx<T>* pdir = (a.cg && a.aux) ? reinterpret_cast<const cpx<T>*>(a.aux) + (long long)rhs * C * a.out_comp
@@ -335,7 +337,7 @@ __global__ void __launch_bounds__(kPassThreads) k_xpass(XArgs a) {
     A[pp * M + k] = mk<T>(z[0].x - z[1].y, z[0].y + z[1].x);
   }
   __syncthreads();
-  cpx<T>* res = fft_any<T, MT>(A, B, npair, a.plan, Ws, +1);
+  cpx<T>* res = fft_any<T, MT>(A, B, npair, a.plan, Ws, +1, a.mode != 2 && prune3_ok(M, Nin) ? 1 : 0);
   cpx<T>* oth = res == A ? B : A;
   const T* coef = reinterpret_cast<const T*>(a.coef);
   const long long cstride = (long long)a.planes * M;
@@ -362,7 +364,7 @@ __global__ void __launch_bounds__(kPassThreads) k_xpass(XArgs a) {
         }
     }
     __syncthreads();
-    cpx<T>* r2 = fft_any<T, MT>(res, oth, npair, a.plan, Ws, -1);
+    cpx<T>* r2 = fft_any<T, MT>(res, oth, npair, a.plan, Ws, -1, prune3_ok(M, a.Nout) ? 2 : 0);
     cpx<T>* out = reinterpret_cast<cpx<T>*>(a.out);
     const int Nout = a.Nout;
     for (int t = threadIdx.x; t < nrow * Nout; t += blockDim.x) {
