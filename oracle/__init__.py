@@ -23,10 +23,16 @@ properties by FFT-based Galerkin method":
               the 2N-1 grid, naive (matrix) DFTs, pointwise coefficient, truncation,
               projection, conjugate gradients (Sec. 6.1) and the double-grid energy.
   bounds.py   upper / lower / mean / guaranteed error (Eq. approx_homog_with_error).
+  gani.py     GaNi (Def. GaNi, Cor. FD_GaNi): the coefficient sampled at the grid
+              points, the grid-quadrature Galerkin matrix, its minimisers, the GaNi
+              homogenized matrices and the bounds of the paper's algorithm (the
+              minimisers in the exactly integrated forms, Eq. GaNi_bounds).
+  fno.py      the learned warm start's Fourier-layer network in PyTorch float64.
 
-Every function is pinned by ``tests/test_oracle_pins.py`` against facts the paper
-and the mathematics fix (Voigt-Reuss, laminates, the 2D rotation identity,
-monotonicity in N, brute-force quadrature, ...).
+Every function is pinned by ``tests/test_oracle_pins.py``,
+``tests/test_oracle_gani_pins.py`` and ``tests/test_oracle_fno_pins.py`` against facts the
+paper and the mathematics fix (Voigt-Reuss, laminates, the 2D rotation identity,
+monotonicity in N, brute-force quadrature, odd-grid GaNi duality, ...).
 """
 from .fourier import (coefficient_hat_at, coefficient_hat_grid, freqs, projection,
                       topology_hat_at, phase_inverse)

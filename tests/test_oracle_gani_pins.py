@@ -1,0 +1,96 @@
+"""Pins of the GaNi oracle (oracle/gani.py) against what the paper and the mathematics fix.
+
+* Prop. FD_odd_problem: on odd grids the primal and dual GaNi homogenized matrices are
+  mutually inverse, A_{H,N} = B_{H,N}^{-1}.
+* Eq. GaNi_bounds: the exactly integrated energies of the GaNi minimisers bound the Galerkin
+  bounds from outside (the Galerkin minimisers minimise those energies over the same spaces).
+* A homogeneous cell gives A0 everywhere; N = 1 gives the sample at the origin and the
+  Voigt/Reuss bounds.
+* Discrete laminate: a coefficient that depends on x1 only gives the harmonic mean of the
+  samples along x1 and their arithmetic mean along x2.
+* The Fourier-basis GaNi matrix reproduces the grid quadrature of the definition for random
+  trigonometric polynomials evaluated at the grid points by direct sums.
+"""
+import numpy as np
+import pytest
+
+import microstructures as ms
+from oracle import dense, gani
+from oracle.fourier import frequency_grid
+
+CELLS = {
+    "square2d_N9": lambda: ms.square_inclusion_2d(N=9),
+    "aniso2d_N7": lambda: ms.random_anisotropic_2d(3, N=7),
+    "rect2d_N11": lambda: ms.random_rectangles_2d(4, N=11),
+    "paper_rho100_N15": lambda: ms.paper_square_2d(15, 100.0),
+    "aniso3d_N5": lambda: ms.random_anisotropic_3d(4, N=5),
+}
+
+
+def loewner_ge(A, B, tol=1e-12):
+    S = 0.5 * ((A - B) + (A - B).T)
+    return np.linalg.eigvalsh(S).min() >= -tol * max(1.0, np.abs(A).max())
+
+
+@pytest.mark.parametrize("name", list(CELLS))
+def test_odd_grid_duality(name):
+    out = gani.gani_bounds(CELLS[name]())
+    A, B = out["A_HN"], out["B_HN"]
+    assert np.abs(A - np.linalg.inv(B)).max() <= 1e-10 * np.abs(A).max()
+
+
+@pytest.mark.parametrize("name", list(CELLS))
+def test_gani_field_bounds_enclose_galerkin_bounds(name):
+    p = CELLS[name]()
+    g = gani.gani_bounds(p)
+    ga = dense.dense_bounds(p)
+    assert loewner_ge(g["upper"], ga["upper"])
+    assert loewner_ge(ga["lower"], g["lower"])
+    assert loewner_ge(g["upper"], g["lower"])
+
+
+def test_homogeneous_and_single_point():
+    A0 = np.array([[2.0, 0.3, 0.1], [0.3, 1.5, 0.2], [0.1, 0.2, 1.0]])
+    out = gani.gani_bounds(ms.homogeneous(3, 5, A0))
+    for key in ("A_HN", "upper", "lower"):
+        assert np.abs(out[key] - A0).max() < 1e-13
+    assert np.abs(np.linalg.inv(out["B_HN"]) - A0).max() < 1e-13
+    p = ms.random_anisotropic_2d(8, N=1)
+    out = gani.gani_bounds(p)
+    a0 = gani.sample_coefficient(p)[0, 0]
+    assert np.abs(out["A_HN"] - a0).max() < 1e-13
+    ref = dense.dense_bounds(p)        # N = 1: Voigt / Reuss from the exact integrals
+    assert np.abs(out["upper"] - ref["upper"]).max() < 1e-13
+    assert np.abs(out["lower"] - ref["lower"]).max() < 1e-13
+
+
+@pytest.mark.parametrize("N", [5, 9, 15])
+def test_discrete_laminate_means(N):
+    p = ms.laminate_2d(N, width=0.37, a_incl=7.0)
+    a = gani.sample_coefficient(p)[:, 0, 0, 0]             # depends on x1 only
+    assert np.allclose(gani.sample_coefficient(p)[..., 0, 0], a[:, None])
+    out = gani.gani_bounds(p)
+    assert abs(out["A_HN"][0, 0] - 1.0 / np.mean(1.0 / a)) < 1e-12
+    assert abs(out["A_HN"][1, 1] - np.mean(a)) < 1e-12
+    assert abs(out["A_HN"][0, 1]) < 1e-12
+
+
+def test_fourier_matrix_is_the_grid_quadrature():
+    p = ms.random_anisotropic_2d(5, N=7)
+    d = 2
+    N = tuple(int(n) for n in p.N)
+    Y = np.asarray(p.Y, dtype=np.float64)
+    rng = np.random.default_rng(0)
+    k = frequency_grid(N).reshape(-1, d)
+    x = gani.grid_points(p).reshape(-1, d)
+    A = gani.sample_coefficient(p).reshape(-1, d, d)
+    K = gani.gani_matrix(p, "primal")
+    for _ in range(3):
+        uh = rng.normal(size=(k.shape[0], d)) + 1j * rng.normal(size=(k.shape[0], d))
+        vh = rng.normal(size=(k.shape[0], d)) + 1j * rng.normal(size=(k.shape[0], d))
+        # u(x) = sum_k u_hat(k) exp(2 pi i k.x / Y), one grid point at a time
+        u = np.array([sum(uh[j] * np.exp(2j * np.pi * np.dot(k[j] / Y, xx)) for j in range(k.shape[0])) for xx in x])
+        v = np.array([sum(vh[j] * np.exp(2j * np.pi * np.dot(k[j] / Y, xx)) for j in range(k.shape[0])) for xx in x])
+        quad = sum(np.conj(v[i]) @ A[i] @ u[i] for i in range(x.shape[0])) / x.shape[0]
+        four = np.conj(vh.reshape(-1)) @ K @ uh.reshape(-1)
+        assert abs(quad - four) < 1e-11 * abs(quad)
