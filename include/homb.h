@@ -117,6 +117,12 @@ typedef struct {
                            (e_a + e^(a))], E = inv(upper) e_b, through the
                            double-grid operator of the primal coefficient. Any
                            start in J_N keeps the lower bound guaranteed.        */
+  int32_t discretization; /* hom_bounds: 0 Ga (CG with the exact double-grid operator);
+                           1 GaNi, the paper's algorithm (Sec. 6.2): CG on the N grid
+                           with the coefficient sampled at the grid points (Def.
+                           GaNi; a point on an inclusion boundary belongs to the
+                           matrix), then the double-grid energies of those
+                           minimisers give the bounds (Eq. GaNi_bounds). FP64 only.*/
 } hom_opts;
 
 typedef struct {
@@ -128,6 +134,8 @@ typedef struct {
   int64_t launches;     /* CUDA kernels launched by the call                     */
   int64_t h2d_bytes;    /* host->device bytes copied by the call                 */
   int64_t d2h_bytes;    /* device->host bytes copied by the call                 */
+  double gani[2][9];    /* hom_bounds with GaNi: the GaNi homogenized matrices
+                           A_{H,N} and B_{H,N} (Cor. FD_GaNi), d x d row-major    */
   int32_t batch_config[6]; /* hom_bounds_batched launch: threads per CTA, chunk
                            capacity, radix schedule (1: 5/3, 2: composite), cluster
                            size, smallest cooperative 2N-1, CTAs launched          */

@@ -41,13 +41,14 @@ class hom_problem(C.Structure):
 class hom_opts(C.Structure):
     _fields_ = [("precision", C.c_int32), ("max_iter", C.c_int32), ("tol", C.c_double),
                 ("check_every", C.c_int32), ("sides", C.c_int32), ("graph", C.c_int32),
-                ("autotune", C.c_int32), ("dual_start", C.c_int32)]
+                ("autotune", C.c_int32), ("dual_start", C.c_int32), ("discretization", C.c_int32)]
 
 
 class hom_report(C.Structure):
     _fields_ = [("iters", (C.c_int32 * 3) * 2), ("resid", (C.c_double * 3) * 2), ("matvecs", C.c_int32),
                 ("status", (C.c_int32 * 3) * 2), ("ms_total", C.c_double), ("launches", C.c_int64),
-                ("h2d_bytes", C.c_int64), ("d2h_bytes", C.c_int64), ("batch_config", C.c_int32 * 6)]
+                ("h2d_bytes", C.c_int64), ("d2h_bytes", C.c_int64), ("gani", (C.c_double * 9) * 2),
+                ("batch_config", C.c_int32 * 6)]
 
 
 class hom_batch_io(C.Structure):
@@ -199,10 +200,10 @@ def hom_problem_info(ctx, problem):
 
 
 def make_opts(precision=HOM_FP64, tol=1e-8, max_iter=10000, check_every=8, sides=3, graph=0, autotune=0,
-              dual_start=0):
+              dual_start=0, discretization=0):
     o = hom_opts()
     o.precision, o.tol, o.max_iter, o.check_every, o.sides = precision, tol, max_iter, check_every, sides
-    o.graph, o.autotune, o.dual_start = graph, autotune, dual_start
+    o.graph, o.autotune, o.dual_start, o.discretization = graph, autotune, dual_start, discretization
     return o
 
 
@@ -279,6 +280,9 @@ def hom_bounds(ctx, problem, opts, d_ws, ws_bytes, stream=0):
         "matvecs": rep.matvecs, "ms_total": rep.ms_total, "launches": rep.launches,
         "h2d_bytes": rep.h2d_bytes, "d2h_bytes": rep.d2h_bytes,
     }
+    if opts.discretization == 1:
+        out["gani_A"] = np.array(rep.gani[0][:d * d]).reshape(d, d)
+        out["gani_B"] = np.array(rep.gani[1][:d * d]).reshape(d, d)
     return out
 
 

@@ -409,6 +409,7 @@ struct Runner {
   unsigned char* base;
   cudaStream_t st;
   int R;
+  bool gani = false;   // GaNi: g is the N grid (M = N), coefficient sampled at the grid points
 
   template <typename X> X* at(size_t off) const { return reinterpret_cast<X*>(base + off); }
 
@@ -821,28 +822,44 @@ struct Runner {
     return HOM_OK;
   }
 
+  // GaNi coefficient: the side's coefficient sampled at the grid points (Def. GaNi)
+  hom_status sample_coefficient(int side, double* coef) {
+    Prof pr(ctx, "coef", st);
+    KL(launch_sample_coef(spec_args(side), coef, st));
+    return HOM_OK;
+  }
+
   template <typename T>
   hom_status solve_side(int side, const hom_opts& o, hom_report* rep, int* matvecs,
                         const double2* x0 = nullptr) {
     const size_t elem = sizeof(T) * 2;
     double* coef64 = at<double>(L.coef64);
-    CKS(build_coefficient(side, coef64));
+    if (gani) CKS(sample_coefficient(side, coef64));
+    else CKS(build_coefficient(side, coef64));
     const void* coefT = coef64;
     if (sizeof(T) == 4) {
       KL(launch_convert_d2f(coef64, at<float>(L.coef32), (long long)g.ncomp * g.grid, st));
       coefT = at<float>(L.coef32);
     }
     const size_t fb = (size_t)R * g.d * g.field * elem;
-    if (x0 && sizeof(T) == 8) CK(cudaMemcpyAsync(base + L.x, x0, fb, cudaMemcpyDeviceToDevice, st));
-    else CK(cudaMemsetAsync(base + L.x, 0, fb, st));
+    CK(cudaMemsetAsync(base + L.x, 0, fb, st));
     CK(cudaMemsetAsync(base + L.p, 0, fb, st));
     CgScalars* cg = at<CgScalars>(L.cg[side]);
     SpecArgs sa = spec_args(side);
     const int N3[3] = {g.N[0], g.N[1], g.N[2]};
-    KL(launch_rhs<T>(sa, side, R, g.Nh, N3, base + L.r, at<double>(L.partial), kVecBlocks, st));
+    if (gani) {
+      // b = -Gamma F_N (A_N E) (Eq. linear_system_primal with the GaNi matrix): the operator
+      // applied to the constant field E = e_r (x = 0 here), negated
+      CKS(matvec<T>(base + L.x, base + L.r, coefT, side + 1, nullptr, nullptr, nullptr, 2));
+      ++*matvecs;
+      KL(launch_negate_norm<T>(base + L.r, R, g.d, g.field, g.Nh, at<double>(L.partial), kVecBlocks, st));
+    } else {
+      KL(launch_rhs<T>(sa, side, R, g.Nh, N3, base + L.r, at<double>(L.partial), kVecBlocks, st));
+    }
     const double tol = o.tol > 0 ? o.tol : 1e-8;
     const int nfin = final_blocks(elem);
-    if (x0 && sizeof(T) == 8) {   // r0 = b - C x0 (in place over b), |r0|^2 partials
+    if (x0 && sizeof(T) == 8) {   // x = x0 (after b, which GaNi forms from x = 0); r0 = b - C x0
+      CK(cudaMemcpyAsync(base + L.x, x0, fb, cudaMemcpyDeviceToDevice, st));
       CKS(matvec<T>(base + L.x, base + L.r, coefT, side + 1, nullptr, nullptr, nullptr, 0, base + L.r));
       ++*matvecs;
       KL(launch_cg_init(cg, at<double>(L.partial), L.maxblk, nfin, R, tol * tol, 0.0, 0, st));
@@ -1200,6 +1217,20 @@ hom_status hom_problem_info(hom_ctx* ctx, const hom_problem* prob, int32_t* ncom
   return HOM_OK;
 }
 
+// the N-grid geometry of GaNi: transform lengths M = N, coefficient sampled on the N grid
+Geometry gani_geometry(const Geometry& g) {
+  Geometry n = g;
+  for (int a = 0; a < 3; ++a) n.M[a] = a < g.d ? g.N[a] : 1;
+  n.Nxs = (n.M[0] + 1) / 2;
+  n.planes = (long long)n.M[1] * n.M[2];
+  n.grid = n.planes * n.M[0];
+  n.spec = n.planes * n.Nxs;
+  for (int a = 0; a < 3; ++a) make_plan(n.M[a], n.plan[a]);
+  return n;
+}
+
+size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+
 hom_status hom_workspace_size(hom_ctx* ctx, const hom_problem* prob, const hom_opts* opts,
                               size_t* bytes) {
   if (!ctx || !opts || !bytes) return fail(ctx, HOM_ERR_INVALID_ARG, "NULL argument");
@@ -1207,6 +1238,7 @@ hom_status hom_workspace_size(hom_ctx* ctx, const hom_problem* prob, const hom_o
   CKS(build_geometry(ctx, prob, g));
   const size_t elem = opts->precision == HOM_MIXED ? 8 : 16;
   *bytes = make_layout(g, g.d, elem, 0).total;
+  if (opts->discretization == 1) *bytes = align256(*bytes) + make_layout(gani_geometry(g), g.d, 16, 0).total;
   return HOM_OK;
 }
 
@@ -1233,24 +1265,58 @@ hom_status hom_bounds(hom_ctx* ctx, const hom_problem* prob, const hom_opts* opt
   if (opts->precision != HOM_FP64 && opts->precision != HOM_MIXED)
     return fail(ctx, HOM_ERR_INVALID_ARG, "precision must be HOM_FP64 or HOM_MIXED");
   const size_t elem = opts->precision == HOM_MIXED ? 8 : 16;
+  if (opts->discretization != 0 && opts->discretization != 1)
+    return fail(ctx, HOM_ERR_INVALID_ARG, "discretization must be 0 (Ga) or 1 (GaNi)");
+  const bool gani = opts->discretization == 1;
+  if (gani && opts->precision != HOM_FP64) return fail(ctx, HOM_ERR_INVALID_ARG, "GaNi runs in FP64");
   Runner run{ctx, g, make_layout(g, g.d, elem, 0), static_cast<unsigned char*>(d_ws),
              static_cast<cudaStream_t>(stream), g.d};
-  if (!d_ws || ws_bytes < run.L.total) return fail(ctx, HOM_ERR_WORKSPACE, "workspace too small");
+  const Geometry gn = gani ? gani_geometry(g) : g;
+  const size_t gani_off = align256(run.L.total);
+  Runner rn{ctx, gn, gani ? make_layout(gn, g.d, 16, 0) : Layout{}, static_cast<unsigned char*>(d_ws) + gani_off,
+            static_cast<cudaStream_t>(stream), g.d};
+  rn.gani = true;
+  const size_t need = gani ? gani_off + rn.L.total : run.L.total;
+  if (!d_ws || ws_bytes < need) return fail(ctx, HOM_ERR_WORKSPACE, "workspace too small");
   if (reinterpret_cast<uintptr_t>(d_ws) % 256) return fail(ctx, HOM_ERR_INVALID_ARG, "workspace must be 256-byte aligned");
   if (rep) memset(rep, 0, sizeof *rep);
   CKS(run.upload_tables());
+  if (gani) CKS(rn.upload_tables());
   const int sides = opts->sides ? opts->sides : 3;
   int matvecs = 0;
   hom_status worst = HOM_OK;
   bool warm = false;
   for (int side = 0; side < 2; ++side) {
     if (!(sides & (1 << side))) continue;
+    if (gani) {
+      // the paper's algorithm (Sec. 6.2): GaNi minimisers on the N grid, then their exactly
+      // integrated energies on the double grid (Eq. GaNi_bounds)
+      double2* x0 = rn.at<double2>(rn.L.q);
+      if (side == 1 && (sides & 3) == 3 && opts->dual_start == 1) CKS(rn.dual_start(x0, &warm, &matvecs));
+      hom_status s = rn.solve_side<double>(side, *opts, rep, &matvecs, warm ? x0 : nullptr);
+      if (s < 0) return s;
+      if (s == HOM_WARN_NOT_CONVERGED) worst = s;
+      double* coef64 = run.at<double>(run.L.coef64);
+      CKS(run.build_coefficient(side, coef64));
+      CKS(run.energy(coef64, rn.at<double2>(rn.L.x64), 1, side));
+      continue;
+    }
     double2* x0 = elem == 16 ? run.at<double2>(run.L.q) : run.at<double2>(run.L.b64);
     if (side == 1 && (sides & 3) == 3 && opts->dual_start == 1) CKS(run.dual_start(x0, &warm, &matvecs));
     hom_status s = elem == 16 ? run.solve_side<double>(side, *opts, rep, &matvecs, warm ? x0 : nullptr)
                               : Runner_solve_mixed(run, side, *opts, rep, &matvecs, warm);
     if (s < 0) return s;
     if (s == HOM_WARN_NOT_CONVERGED) worst = s;
+  }
+  if (gani && rep) {   // the GaNi homogenized matrices A_{H,N}, B_{H,N} (Cor. FD_GaNi)
+    CK(d2h_copy(ctx, ctx->host_e, rn.at<double>(rn.L.eout), 18 * sizeof(double), run.st));
+    CK(cudaStreamSynchronize(run.st));
+    const double invN = 1.0 / (double)gn.grid;
+    for (int sd = 0; sd < 2; ++sd)
+      for (int i = 0; i < g.d; ++i)
+        for (int j = 0; j < g.d; ++j)
+          rep->gani[sd][g.d * i + j] =
+              0.5 * (ctx->host_e[9 * sd + g.d * i + j] + ctx->host_e[9 * sd + g.d * j + i]) * invN;
   }
   CK(d2h_copy(ctx, ctx->host_e, run.at<double>(run.L.eout), 18 * sizeof(double), run.st));
   CK(cudaStreamSynchronize(run.st));

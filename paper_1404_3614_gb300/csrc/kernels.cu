@@ -300,6 +300,63 @@ __global__ void k_promote_add(const float2* x32, double2* x64, long long n) {
   }
 }
 
+// GaNi coefficient (Def. GaNi, Eq. grid_points): the side's coefficient sampled at the grid
+// points x_k = k_a Y_a / N_a of the M = N grid (FFT storage order), packed symmetric
+// [q][j3][j2][j1]. A point on an inclusion boundary belongs to the matrix (strict
+// inequalities), with periodic images; the dual side samples the pointwise inverse.
+__global__ void k_sample_coef(SpecArgs a, double* coef) {
+  const long long grid = (long long)a.M[0] * a.M[1] * a.M[2];
+  for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < grid;
+       j += (long long)gridDim.x * blockDim.x) {
+    const int j1 = (int)(j % a.M[0]);
+    const int j2 = (int)((j / a.M[0]) % a.M[1]);
+    const int j3 = (int)(j / ((long long)a.M[0] * a.M[1]));
+    const int js[3] = {j1, j2, j3};
+    double x[3];
+    for (int c = 0; c < 3; ++c) x[c] = (double)sfreq(js[c], a.M[c]) / ((double)a.M[c] * a.invY[c]);
+    double v[6];
+    for (int q = 0; q < 6; ++q) v[q] = a.A0p[q];
+    for (int i = 0; i < a.nincl; ++i) {
+      const DevIncl& I = a.incl[i];
+      bool in = true;
+      double r2 = 0.0;
+      for (int c = 0; c < a.d; ++c) {
+        const double Yc = 1.0 / a.invY[c];
+        double dx = x[c] - I.c[c];
+        dx -= Yc * rint(dx * a.invY[c]);
+        if (I.shape == 0) in = in && fabs(dx) < 0.5 * I.h[c];
+        r2 += dx * dx;
+      }
+      if (I.shape != 0) in = sqrt(r2) < I.h[0];
+      if (in)
+        for (int q = 0; q < a.ncomp; ++q) v[q] = a.A0p[q] + I.dA[q];
+    }
+    for (int q = 0; q < a.ncomp; ++q) coef[q * grid + j] = v[q];
+  }
+}
+
+// r = -r over nrhs fields of C components, with the Hermitian-weighted |r|^2 partials
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_negate_norm(cpx<T>* r, int C, long long field, FastDiv fdNh,
+                                                          double* partial, int ld) {
+  __shared__ double red[32];
+  const int rhs = blockIdx.y;
+  const long long n = (long long)C * field;
+  const long long base = (long long)rhs * n;
+  double acc = 0.0;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
+       e += (long long)gridDim.x * blockDim.x) {
+    cpx<T> v = r[base + e];
+    v = mk<T>(-v.x, -v.y);
+    r[base + e] = v;
+    const int ei = (int)e;
+    const double w = ei - fdNh.div(ei) * (int)fdNh.d == 0 ? 1.0 : 2.0;
+    acc += w * ((double)v.x * v.x + (double)v.y * v.y);
+  }
+  const double s = block_sum(acc, red);
+  if (threadIdx.x == 0) partial[rhs * ld + blockIdx.x] = s;
+}
+
 // In place over nrhs FP64 fields of d components: u_b = sum_a c[b][a] (e_a + x_a), the
 // constant e_a sitting at k = 0 of component a (the superposition of Eq.
 // FD_superposition_odd_A).
@@ -470,6 +527,26 @@ cudaError_t launch_combine_fields(double2* x, int nrhs, int d, long long field, 
   k_combine_fields<<<(int)blocks, kThreads, 0, s>>>(x, nrhs, d, field, cc);
   return cudaGetLastError();
 }
+
+cudaError_t launch_sample_coef(const SpecArgs& a, double* coef, cudaStream_t s) {
+  const long long grid = (long long)a.M[0] * a.M[1] * a.M[2];
+  long long blocks = (grid + kThreads - 1) / kThreads;
+  if (blocks > 152 * 32) blocks = 152 * 32;
+  k_sample_coef<<<(int)blocks, kThreads, 0, s>>>(a, coef);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_negate_norm(void* r, int nrhs, int C, long long field, int Nh, double* partial, int nblk,
+                               cudaStream_t s) {
+  if ((long long)C * field >= (1LL << 31)) return cudaErrorInvalidValue;
+  dim3 grid(nblk, nrhs);
+  k_negate_norm<T><<<grid, kThreads, 0, s>>>(reinterpret_cast<cpx<T>*>(r), C, field, FastDiv((uint32_t)Nh), partial,
+                                             nblk);
+  return cudaGetLastError();
+}
+template cudaError_t launch_negate_norm<double>(void*, int, int, long long, int, double*, int, cudaStream_t);
+template cudaError_t launch_negate_norm<float>(void*, int, int, long long, int, double*, int, cudaStream_t);
 
 cudaError_t launch_energy_reduce(const double* partial, int nblk, int nrr, double* out,
                                  cudaStream_t s) {

@@ -209,6 +209,12 @@ cudaError_t launch_cg_alpha(CgScalars* cg, const double* partial, int ld, int nb
                             cudaStream_t s);
 cudaError_t launch_cg_beta(CgScalars* cg, const double* partial, int ld, int nblk, int nrhs,
                            cudaStream_t s);
+// GaNi coefficient sampled at the grid points of the M = N grid (a.M = N), packed symmetric
+cudaError_t launch_sample_coef(const SpecArgs& a, double* coef, cudaStream_t s);
+// r = -r with |r|^2 partials [nrhs][nblk]
+template <typename T>
+cudaError_t launch_negate_norm(void* r, int nrhs, int C, long long field, int Nh, double* partial, int nblk,
+                               cudaStream_t s);
 struct Coef3 { double v[9]; };   // 3 x 3 row-major coefficients passed by value
 // u_b = sum_a c[b*3+a] (e_a + x_a) in place over nrhs FP64 fields of d components
 cudaError_t launch_combine_fields(double2* x, int nrhs, int d, long long field, const double* c,

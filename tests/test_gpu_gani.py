@@ -1,0 +1,85 @@
+"""GaNi (the paper's algorithm, Sec. 6.2) through hom_bounds against the GaNi oracle.
+
+CG on the N grid with the coefficient sampled at the grid points, then the exactly
+integrated (double-grid) energies of its minimisers: the GaNi homogenized matrices
+A_{H,N}, B_{H,N} and the bounds match oracle/gani.py to 1e-10 relative (FP64); the GPU
+results keep the odd-grid duality A_{H,N} = B_{H,N}^{-1}; the dual start from the primal
+minimisers is exact for GaNi (Eq. FD_superposition_odd_A), so the dual CG needs almost no
+iterations.
+"""
+import numpy as np
+import pytest
+
+import microstructures as ms
+import oracle
+from oracle import gani
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+CELLS = {
+    "square2d_N9": lambda: ms.square_inclusion_2d(N=9),
+    "square2d_N15": lambda: ms.square_inclusion_2d(N=15),
+    "aniso2d_N7": lambda: ms.random_anisotropic_2d(3, N=7),
+    "rect2d_N11": lambda: ms.random_rectangles_2d(4, N=11),
+    "paper_rho100_N15": lambda: ms.paper_square_2d(15, 100.0),
+    "aniso3d_N5": lambda: ms.random_anisotropic_3d(4, N=5),
+    "cube3d_N9": lambda: ms.cube_inclusion_3d(N=9),
+    "spheres3d_N7": lambda: ms.random_spheres_3d(2, N=7, n_balls=6, phi=0.25, contrast=30.0),
+}
+
+
+@pytest.fixture(scope="module")
+def hb():
+    import paper_1404_3614_gb300 as hb
+    return hb
+
+
+@pytest.fixture(scope="module")
+def solver(hb):
+    s = hb.Bounds(0)
+    yield s
+    s.close()
+
+
+def rel(a, b):
+    return np.abs(a - b).max() / np.linalg.norm(b)
+
+
+@pytest.mark.parametrize("name", list(CELLS))
+def test_gani_matches_oracle(hb, solver, name):
+    p = CELLS[name]()
+    ref = gani.gani_bounds(p)
+    out = solver(p, precision=hb.HOM_FP64, tol=1e-12, discretization=1)
+    assert out["status"] == 0
+    assert rel(out["gani_A"], ref["A_HN"]) <= 1e-10
+    assert rel(out["gani_B"], ref["B_HN"]) <= 1e-10
+    for key in ("upper", "lower", "mean", "D"):
+        assert np.abs(out[key] - ref[key]).max() <= 1e-10 * np.linalg.norm(ref["upper"]), key
+    # odd-grid duality (Prop. FD_odd_problem) on the GPU results
+    assert rel(np.linalg.inv(out["gani_B"]), out["gani_A"]) <= 1e-9
+    # the GaNi-field bounds enclose the Galerkin bounds (both guaranteed)
+    ga = solver(p, precision=hb.HOM_FP64, tol=1e-12)
+    S = out["upper"] - ga["upper"]
+    assert np.linalg.eigvalsh(0.5 * (S + S.T)).min() >= -1e-10 * np.abs(ga["upper"]).max()
+    S = ga["lower"] - out["lower"]
+    assert np.linalg.eigvalsh(0.5 * (S + S.T)).min() >= -1e-10 * np.abs(ga["upper"]).max()
+
+
+@pytest.mark.parametrize("name", ["square2d_N15", "aniso2d_N7", "cube3d_N9", "aniso3d_N5"])
+def test_gani_dual_start_is_exact(hb, solver, name):
+    """For GaNi on odd grids the superposed primal minimisers are the dual minimisers, so
+    the dual CG started from them stops after a few iterations with the same bounds."""
+    p = CELLS[name]()
+    zero = solver(p, precision=hb.HOM_FP64, tol=1e-10, discretization=1)
+    warm = solver(p, precision=hb.HOM_FP64, tol=1e-10, discretization=1, dual_start=1)
+    iz, iw = max(zero["report"]["iters"][1]), max(warm["report"]["iters"][1])
+    print(name, "GaNi dual iterations from zero", iz, "from the primal minimisers", iw)
+    assert iw <= 3 and (iz <= 3 or iw < iz)
+    assert rel(warm["lower"], zero["lower"]) <= 1e-8
+    assert np.array_equal(warm["upper"], zero["upper"])
+
+
+def test_gani_rejects_mixed_precision(hb, solver):
+    with pytest.raises(hb.HombError):
+        solver(ms.square_inclusion_2d(N=9), precision=hb.HOM_MIXED, discretization=1)
