@@ -57,6 +57,10 @@ class Problem:
     N: np.ndarray              # (d,) odd grid sizes
     A0: np.ndarray             # (d, d) matrix phase
     inclusions: List[Inclusion]
+    # optional pixel image of an isotropic scalar coefficient, shape (P_1, ..., P_d): pixel
+    # (i_1, ..., i_d) covers prod_a (-Y_a/2 + i_a h_a, -Y_a/2 + (i_a + 1) h_a), h_a = Y_a / P_a,
+    # and holds the conductivity a (A = a I there). When set, A0 and inclusions are unused.
+    bitmap: np.ndarray = None
 
     @property
     def M(self) -> np.ndarray:
@@ -67,10 +71,16 @@ class Problem:
         N = np.broadcast_to(np.asarray(N, dtype=np.int64), (self.d,)).copy()
         return dataclasses.replace(self, N=N)
 
+    def is_bitmap(self) -> bool:
+        return self.bitmap is not None
+
     def volume_fraction(self) -> float:
         return sum(inc.volume() for inc in self.inclusions) / float(np.prod(self.Y))
 
     def is_isotropic(self) -> bool:
+        if self.bitmap is not None:
+            return True
+
         def iso(A):
             return np.allclose(A, A[0, 0] * np.eye(self.d), rtol=0, atol=0)
         return iso(self.A0) and all(iso(inc.A) for inc in self.inclusions)
@@ -288,3 +298,48 @@ def random_anisotropic_3d(seed: int, N=5, n_incl=2) -> Problem:
 
 def batch_rectangles_2d(seeds: Sequence[int], N=None) -> List[Problem]:
     return [random_rectangles_2d(s, N=N) for s in seeds]
+
+
+# ----------------------------------------------------------------------------------
+# pixel images (the paper's Sec. 7.3 workload type: a coefficient given per pixel)
+# ----------------------------------------------------------------------------------
+def bitmap_problem(bitmap, N=None, Y=1.0) -> Problem:
+    """A cell whose isotropic conductivity is the pixel image `bitmap` (values > 0).
+    N defaults to the image size (the grid points then sit at the pixel centres for odd
+    sizes)."""
+    b = np.ascontiguousarray(np.asarray(bitmap, dtype=np.float64))
+    d = b.ndim
+    if d not in (2, 3) or np.any(~(b > 0)):
+        raise ValueError("bitmap: 2D or 3D array of positive conductivities")
+    Nv = np.asarray(b.shape if N is None else np.broadcast_to(N, (d,)), dtype=np.int64)
+    Yv = _vec(Y, d)
+    return Problem(d, Yv, Nv.copy(), float(b.mean()) * np.eye(d), [], bitmap=b)
+
+
+def box_bitmap(P, lo, hi, a_in, a_out=1.0, d=2) -> np.ndarray:
+    """A P^d image holding a_in on the pixels [lo, hi) of every axis and a_out elsewhere."""
+    b = np.full((P,) * d, float(a_out))
+    b[tuple(slice(lo, hi) for _ in range(d))] = float(a_in)
+    return b
+
+
+def porous_bitmap_2d(seed: int, P=1199, porosity=0.45, r_min=0.01, r_max=0.04, a_solid=0.49,
+                     a_pore=0.029) -> np.ndarray:
+    """A synthetic porous two-phase P x P image standing in for a micrograph: pores are the
+    union of periodic disks (centres uniform, radii log-uniform in [r_min, r_max] of the cell),
+    added until the pore fraction reaches `porosity`; conductivities a_solid / a_pore (the
+    paper's Sec. 7.3 phase values)."""
+    rng = np.random.default_rng(seed)
+    c = (np.arange(P) + 0.5) / P - 0.5
+    X, Yg = np.meshgrid(c, c, indexing="ij")
+    pore = np.zeros((P, P), dtype=bool)
+    while pore.mean() < porosity:
+        cx, cy = rng.uniform(-0.5, 0.5, size=2)
+        r = math.exp(rng.uniform(math.log(r_min), math.log(r_max)))
+        dx = X - cx
+        dy = Yg - cy
+        dx -= np.round(dx)
+        dy -= np.round(dy)
+        pore |= dx * dx + dy * dy < r * r
+    return np.where(pore, a_pore, a_solid)
+

@@ -87,14 +87,38 @@ def _phase_increments(problem: Problem, side: str):
     raise ValueError(side)
 
 
+def bitmap_hat_at(problem: Problem, n: np.ndarray, side: str = "primal") -> np.ndarray:
+    """Fourier coefficient (Eq. FT_def) of a pixel image a(x) (or of 1/a for the dual) at
+    integer n [..., d]: every pixel is a box of sides h_a = Y_a/P_a centred at
+    c_a = -Y_a/2 + (i_a + 1/2) h_a (Remark "inclusion"), so
+      a_hat(n) = sum_i v_i prod_a (1/P_a) sinc(n_a/P_a) exp(-2 pi i n_a c_a / Y_a),
+    written as a sum over the pixels (no FFT). Returns a scalar per frequency."""
+    n = np.asarray(n, dtype=np.int64)
+    v = problem.bitmap if side == "primal" else 1.0 / problem.bitmap
+    Y = np.asarray(problem.Y, dtype=np.float64)
+    factors = []
+    for a in range(problem.d):
+        P = v.shape[a]
+        c = -0.5 * Y[a] + (np.arange(P) + 0.5) * (Y[a] / P)
+        na = n[..., a].astype(np.float64)
+        E = np.exp(-2j * np.pi * na[..., None] * c / Y[a])                      # [..., P]
+        factors.append(E * (np.sinc(na / P) / P)[..., None])
+    if problem.d == 2:
+        return np.einsum("...i,...j,ij->...", factors[0], factors[1], v)
+    return np.einsum("...i,...j,...k,ijk->...", factors[0], factors[1], factors[2], v)
+
+
 def coefficient_hat_at(problem: Problem, n: np.ndarray, side: str = "primal") -> np.ndarray:
     """A_hat(n) (or the coefficient of A^{-1}) at integer frequencies n [..., d] -> [..., d, d].
 
     Lemma bounds_for_matrix-inclusion: A_hat(n) = A0 delta_{n0}
-    + sum_j (A_j - A0) f_hat_j(n) phi_{-n}(x_j).
+    + sum_j (A_j - A0) f_hat_j(n) phi_{-n}(x_j); a pixel image is a sum of pixel boxes
+    (bitmap_hat_at) times the identity (the pointwise inverse for the dual).
     """
     n = np.asarray(n, dtype=np.int64)
     d = problem.d
+    if problem.bitmap is not None:
+        return bitmap_hat_at(problem, n, side)[..., None, None] * np.eye(d)
     C0, incr = _phase_increments(problem, side)
     out = np.zeros(n.shape[:-1] + (d, d), dtype=np.complex128)
     is0 = np.all(n == 0, axis=-1)

@@ -53,6 +53,13 @@ def sample_coefficient(problem: Problem, side: str = "primal") -> np.ndarray:
     d = problem.d
     Y = np.asarray(problem.Y, dtype=np.float64)
     x = grid_points(problem)
+    if problem.bitmap is not None:
+        # the pixel holding the grid point (pixel centres when N equals the image size)
+        b = problem.bitmap
+        idx = tuple(np.clip(np.floor((x[..., a] / Y[a] + 0.5) * b.shape[a]).astype(np.int64), 0, b.shape[a] - 1)
+                    for a in range(d))
+        A = b[idx][..., None, None] * np.eye(d)
+        return np.linalg.inv(A) if side == "dual" else A
     A = np.broadcast_to(np.asarray(problem.A0, dtype=np.float64), x.shape[:-1] + (d, d)).copy()
     for inc in problem.inclusions:
         A[_inside(inc, x, Y)] = np.asarray(inc.A, dtype=np.float64)
