@@ -67,6 +67,8 @@ WORKLOADS = {
     "cube3d_N41": "3D cube cell N=41^3 (double grid 81^3), contrast 100",
     "spheres3d_N113": "3D cell with 16 random balls, volume fraction 0.3, contrast 1000, N=113^3 (double grid 225^3), seed 0",
     "square2d_N23": "2D square inclusion side 0.6, a=1/10, N=23^2 (double grid 45^2)",
+    "porous2d_N1199": "2D synthetic porous pixel image 1199^2 (pores: union of random disks, fraction 0.45), "
+                      "a = 0.49 / 0.029, N = 1199 (double grid 2397^2)",
 }
 
 
@@ -78,6 +80,8 @@ def workload(name: str = "cube3d_N41"):
         return ms.random_spheres_3d(0, N=113)
     if name == "square2d_N23":
         return ms.square_inclusion_2d()
+    if name == "porous2d_N1199":
+        return ms.bitmap_problem(ms.porous_bitmap_2d(0, P=1199))
     raise ValueError(name)
 
 
@@ -428,6 +432,7 @@ def run_gpu(args):
         mv_large = matvec_timings(hb, solver, workload("spheres3d_N113"), dev, stream, reps=10)
         mv_large["workload"] = WORKLOADS["spheres3d_N113"]
     batched = None if args.no_batched else batched_timings(hb, solver, dev)
+    image = None if args.no_batched else image_timings(hb, solver, stream, flush)
 
     # roofline of the dominant kernel family
     nrhs = problem.d
@@ -471,6 +476,7 @@ def run_gpu(args):
         "matvec": mv,
         "matvec_225": mv_large,
         "batched": batched,
+        "image": image,
         "kernel_families_ms_one_step": {k: v[1] for k, v in fam_ms.items()},
         "roofline": roof,
         "clocks": clk.summary(),
@@ -528,6 +534,29 @@ def batched_timings(hb, solver, dev, n=256, reps=3, n_seq=8, autotune=1):
             "max_iters": int(out["iters"].max()), "status_nonzero": int((out["status"] != 0).sum()),
             "sequential_fp64_ms_est": seq_ms, "speedup_vs_sequential_fp64": seq_ms / ms_batch,
             "sequential_note": f"plain FP64 hom_bounds per cell, mean of the first {n_seq} cells x {n}"}
+
+
+def image_timings(hb, solver, stream, flush):
+    """The pixel-image workload (the paper's Sec. 7.3 type, synthetic stand-in): a 1199^2
+    porous two-phase image at N = 1199, tol 1e-4: Ga in FP64 and mixed, GaNi (the paper's
+    algorithm) with and without the dual start. One untimed call, then one timed call each."""
+    import torch
+    p = workload("porous2d_N1199")
+    out = {"workload": WORKLOADS["porous2d_N1199"]}
+    for name, kw in (("ga_fp64", {"precision": hb.HOM_FP64}), ("ga_mixed", {"precision": hb.HOM_MIXED}),
+                     ("gani_fp64", {"precision": hb.HOM_FP64, "discretization": 1}),
+                     ("gani_fp64_dual_start", {"precision": hb.HOM_FP64, "discretization": 1, "dual_start": 1})):
+        solver(p, tol=TOL, stream=stream.cuda_stream, **kw)
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        o = solver(p, tol=TOL, stream=stream.cuda_stream, **kw)
+        e1.record(stream)
+        e1.synchronize()
+        out[name] = {"ms": e0.elapsed_time(e1), "iters": o["report"]["iters"],
+                     "upper": o["upper"].tolist(), "lower": o["lower"].tolist()}
+    return out
 
 
 def matvec_bytes(problem, elem_bytes: int) -> float:

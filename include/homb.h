@@ -94,6 +94,18 @@ typedef struct {
   int32_t reserved;
   const hom_inclusion* incl;   /* host array [n_incl]; inclusions must not
                                   overlap (touching is allowed)                 */
+  const double* bitmap;        /* optional pixel image of an isotropic scalar
+                                  conductivity (A = a I), host array
+                                  [P_d]...[P_1] with the x index fastest; pixel
+                                  (i_1..i_d) covers prod_a (-Y_a/2 + i_a h_a,
+                                  -Y_a/2 + (i_a + 1) h_a), h_a = Y_a / P_a; values
+                                  finite and > 0. NULL: the inclusion model above.
+                                  With an image, n_incl must be 0 and A0 is unused;
+                                  its Fourier coefficients are those of a sum of
+                                  pixel boxes (Remark "inclusion"). Read during the
+                                  call only.                                     */
+  int32_t bitmap_n[3];         /* P_a, a < d (1 for unused axes)                 */
+  int32_t reserved2;
 } hom_problem;
 
 typedef struct {

@@ -35,7 +35,8 @@ class hom_inclusion(C.Structure):
 
 class hom_problem(C.Structure):
     _fields_ = [("d", C.c_int32), ("N", C.c_int32 * 3), ("Y", C.c_double * 3), ("A0", C.c_double * 9),
-                ("n_incl", C.c_int32), ("reserved", C.c_int32), ("incl", C.POINTER(hom_inclusion))]
+                ("n_incl", C.c_int32), ("reserved", C.c_int32), ("incl", C.POINTER(hom_inclusion)),
+                ("bitmap", C.POINTER(C.c_double)), ("bitmap_n", C.c_int32 * 3), ("reserved2", C.c_int32)]
 
 
 class hom_opts(C.Structure):
@@ -159,7 +160,19 @@ def problem_struct(problem):
     p.A0[:] = list(_mat3(problem.A0, d))
     p.n_incl = n
     p.incl = C.cast(arr, C.POINTER(hom_inclusion))
-    return p, arr
+    keep = [arr]
+    bm = getattr(problem, "bitmap", None)
+    if bm is not None:
+        # the ABI stores the x index fastest: the transpose of numpy's [i_1][i_2][(i_3)]
+        img = np.ascontiguousarray(np.asarray(bm, dtype=np.float64).T)
+        p.bitmap = img.ctypes.data_as(C.POINTER(C.c_double))
+        P = [1, 1, 1]
+        P[:d] = list(bm.shape)
+        p.bitmap_n[:] = P
+        keep.append(img)
+    else:
+        p.bitmap_n[:] = [1, 1, 1]
+    return p, keep
 
 
 def check(ctx, status, allow_warn=True):

@@ -136,6 +136,12 @@ struct Geometry {
   double A0[3][3];
   std::vector<hom_inclusion> incl;
   FftPlan plan[3];
+  // pixel image of an isotropic conductivity ([P2][P1] or [P3][P2][P1], x fastest), or empty
+  std::vector<double> bitmap;
+  int P[3] = {1, 1, 1};
+  FftPlan pplan[3];            // DFT plans of the image lengths
+  uint64_t bitmap_hash = 0;
+  long long npix() const { return (long long)P[0] * P[1] * P[2]; }
 };
 
 bool spd(const double* A, int d) {
@@ -218,10 +224,10 @@ void make_plan(int M, FftPlan& p) {
   p.nrad = 0;
   p.sched = 0;
   int m = M;
-  const int small[] = {5, 3, 7, 11, 13};
+  const int small[] = {5, 3, 7, 11, 13, 2};   // 2 only for image lengths (the double grid is odd)
   for (int r : small)
     while (m % r == 0 && p.nrad < kMaxRadices) { p.radix[p.nrad++] = r; m /= r; }
-  for (int r = 17; m > 1; r += 2)
+  for (int r = 17; m > 1 && r <= m; r += 2)
     while (m % r == 0 && p.nrad < kMaxRadices) { p.radix[p.nrad++] = r; m /= r; }
 }
 
@@ -242,11 +248,41 @@ hom_status build_geometry(hom_ctx* ctx, const hom_problem* P, Geometry& g) {
   }
   g.Nh = (g.N[0] + 1) / 2;
   g.Nxs = (g.M[0] + 1) / 2;
-  if (!spd(P->A0, g.d)) return fail(ctx, HOM_ERR_INVALID_ARG, "A0 is not symmetric positive definite");
+  if (P->bitmap) {
+    if (P->n_incl != 0) return fail(ctx, HOM_ERR_INVALID_ARG, "a pixel image excludes inclusions");
+    long long n = 1;
+    for (int a = 0; a < 3; ++a) {
+      g.P[a] = a < g.d ? P->bitmap_n[a] : 1;
+      if (g.P[a] < 1 || g.P[a] > 4096) return fail(ctx, HOM_ERR_INVALID_ARG, "image sizes must be in [1, 4096]");
+      n *= g.P[a];
+    }
+    if (n > (1LL << 27)) return fail(ctx, HOM_ERR_INVALID_ARG, "image too large (max 2^27 pixels)");
+    g.bitmap.assign(P->bitmap, P->bitmap + n);
+    uint64_t h = 1469598103934665603ull;   // FNV-1a over the bytes of the image
+    for (long long i = 0; i < n; ++i) {
+      if (!(g.bitmap[i] > 0) || !std::isfinite(g.bitmap[i]))
+        return fail(ctx, HOM_ERR_INVALID_ARG, "image values must be finite and > 0");
+      uint64_t bits;
+      memcpy(&bits, &g.bitmap[i], 8);
+      for (int k = 0; k < 8; ++k) {
+        h ^= (bits >> (8 * k)) & 0xff;
+        h *= 1099511628211ull;
+      }
+    }
+    g.bitmap_hash = h;
+    for (int a = 0; a < 3; ++a) make_plan(g.P[a], g.pplan[a]);
+    double mean = 0.0;
+    for (long long i = 0; i < n; ++i) mean += g.bitmap[i];
+    mean /= (double)n;
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 3; ++j) g.A0[i][j] = (i == j && i < g.d) ? mean : 0.0;
+  } else if (!spd(P->A0, g.d)) {
+    return fail(ctx, HOM_ERR_INVALID_ARG, "A0 is not symmetric positive definite");
+  }
   if (P->n_incl < 0 || (P->n_incl > 0 && !P->incl)) return fail(ctx, HOM_ERR_INVALID_ARG, "bad inclusion list");
   if (P->n_incl > 4096) return fail(ctx, HOM_ERR_INVALID_ARG, "too many inclusions (max 4096)");
   g.incl.assign(P->incl, P->incl + P->n_incl);
-  bool iso = isotropic(P->A0, g.d);
+  bool iso = P->bitmap ? true : isotropic(P->A0, g.d);
   double minY = g.Y[0];
   for (int a = 1; a < g.d; ++a) minY = std::min(minY, g.Y[a]);
   for (size_t j = 0; j < g.incl.size(); ++j) {
@@ -266,8 +302,9 @@ hom_status build_geometry(hom_ctx* ctx, const hom_problem* P, Geometry& g) {
       if (overlap(I, g.incl[k], g.Y, g.d)) return fail(ctx, HOM_ERR_INVALID_ARG, "inclusions overlap");
   }
   g.ncomp = iso ? 1 : g.d * (g.d + 1) / 2;
-  for (int i = 0; i < 3; ++i)
-    for (int j = 0; j < 3; ++j) g.A0[i][j] = P->A0[3 * i + j];
+  if (!P->bitmap)
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 3; ++j) g.A0[i][j] = P->A0[3 * i + j];
   g.field = (long long)g.Nh * g.N[1] * g.N[2];
   g.planes = (long long)g.M[1] * g.M[2];
   g.grid = g.planes * g.M[0];
@@ -288,6 +325,7 @@ void pack_sym(const double* A, int d, int ncomp, double* out) {  // A leading di
 struct Layout {
   size_t tw64[3], tw32[3], incl, phase, sinc, coef64, coef32, x, r, p, q, x64, b64, r64, t1, t2,
       cg[2], cgo[2], partial, epart, eout, total;
+  size_t bmp = 0, bmpD[2] = {0, 0}, bmptw[3] = {0, 0, 0};   // pixel image, its DFT buffers, twiddles
   int Mmax, maxblk, nblk_energy;
   size_t off = 0;
   size_t take(size_t bytes) {
@@ -315,6 +353,12 @@ Layout make_layout(const Geometry& g, int R, size_t elem, int mode) {
   L.incl = L.take(2 * ni * sizeof(DevIncl));
   L.phase = L.take(ni * 3 * L.Mmax * sizeof(double2));
   L.sinc = L.take(ni * 3 * L.Mmax * sizeof(double));
+  if (!g.bitmap.empty()) {
+    L.bmp = L.take((size_t)g.npix() * 8);
+    L.bmpD[0] = L.take((size_t)g.npix() * 16);
+    L.bmpD[1] = L.take((size_t)g.npix() * 16);
+    for (int a = 0; a < 3; ++a) L.bmptw[a] = L.take((size_t)g.P[a] * 16);
+  }
   const long long RC = (long long)R * g.d;
   const size_t spec_b = (size_t)g.ncomp * g.spec * 16;
   const size_t t1_b = g.d == 3 ? (size_t)RC * g.M[2] * g.N[1] * g.Nh * 16 : 0;
@@ -430,8 +474,21 @@ struct Runner {
     push(g.A0, sizeof g.A0);
     push(&g.ncomp, sizeof g.ncomp);
     if (!g.incl.empty()) push(g.incl.data(), g.incl.size() * sizeof(hom_inclusion));
+    if (!g.bitmap.empty()) {
+      push(&g.bitmap_hash, sizeof g.bitmap_hash);
+      push(g.P, sizeof g.P);
+    }
     if (key == ctx->tables_key) return HOM_OK;
     ctx->tables_key.clear();
+    if (!g.bitmap.empty()) {
+      CK(h2d_copy(ctx, base + L.bmp, g.bitmap.data(), (size_t)g.npix() * 8, st));
+      for (int a = 0; a < 3; ++a) {
+        std::vector<double2> w64;
+        std::vector<float2> w32;
+        twiddles(g.P[a], w64, w32);
+        CK(h2d_copy(ctx, base + L.bmptw[a], w64.data(), w64.size() * sizeof(double2), st));
+      }
+    }
     std::vector<double2> w64;
     std::vector<float2> w32;
     for (int a = 0; a < 3; ++a) {
@@ -498,6 +555,11 @@ struct Runner {
     else inv3(A0f, g.d, C0);
     pack_sym(C0, g.d, g.ncomp, a.A0p);
     a.incl = at<DevIncl>(L.incl) + side * g.incl.size();
+    if (!g.bitmap.empty()) {
+      a.bitmap = at<double>(L.bmp);
+      for (int k = 0; k < 3; ++k) a.P[k] = g.P[k];
+      a.invert = side;
+    }
     a.phase = at<double2>(L.phase);
     a.sinc = at<double>(L.sinc);
     a.Mmax = L.Mmax;
@@ -505,12 +567,40 @@ struct Runner {
   }
 
   // Double-grid coefficient of one side into `coef` (FP64, real). Uses t1/t2.
+  // Unnormalised DFT of the pixel image (or of 1 / a) into L.bmpD[0], layout [P3][P2][P1]:
+  // a transform along the contiguous axis, then a rotation that makes the next axis
+  // contiguous, three times.
+  hom_status bitmap_dft(int side) {
+    double2* D0 = at<double2>(L.bmpD[0]);
+    double2* D1 = at<double2>(L.bmpD[1]);
+    KL(launch_bitmap_load(at<double>(L.bmp), D0, g.npix(), side, st));
+    int P0 = g.P[0], P1 = g.P[1], P2 = g.P[2];
+    for (int step = 0; step < 3; ++step) {
+      if (P0 > 1) KL(launch_fft_batch<double>(D0, D0, P0, P1 * P2, -1, base + L.bmptw[step], g.pplan[step], st));
+      KL(launch_rotate3(D0, D1, P0, P1, P2, st));
+      std::swap(D0, D1);
+      const int t = P0;
+      P0 = P1;
+      P1 = P2;
+      P2 = t;
+    }
+    if (D0 != at<double2>(L.bmpD[0]))   // three swaps: the result is in bmpD[1]
+      CK(cudaMemcpyAsync(at<double2>(L.bmpD[0]), D0, (size_t)g.npix() * 16, cudaMemcpyDeviceToDevice, st));
+    return HOM_OK;
+  }
+
   hom_status build_coefficient(int side, double* coef) {
     Prof pr(ctx, "coef", st);
     SpecArgs sa = spec_args(side);
-    KL(launch_axis_tables(sa.nincl, g.d, g.M, L.Mmax, g.invY, sa.incl, at<double2>(L.phase), at<double>(L.sinc), st));
     double2* S = at<double2>(L.t1);
-    KL(launch_spectrum(sa, S, st));
+    if (!g.bitmap.empty()) {
+      CKS(bitmap_dft(side));
+      KL(launch_bitmap_spectrum(sa, at<double2>(L.bmpD[0]), S, st));
+    } else {
+      KL(launch_axis_tables(sa.nincl, g.d, g.M, L.Mmax, g.invY, sa.incl, at<double2>(L.phase), at<double>(L.sinc),
+                            st));
+      KL(launch_spectrum(sa, S, st));
+    }
     // 3D: z pass t1 -> t2, y pass t2 -> t1, rows from t1; 2D: y pass t1 -> t2, rows from t2
     const void* cur = S;
     void* nxt = at<void>(L.t2);
@@ -847,9 +937,10 @@ struct Runner {
     CgScalars* cg = at<CgScalars>(L.cg[side]);
     SpecArgs sa = spec_args(side);
     const int N3[3] = {g.N[0], g.N[1], g.N[2]};
-    if (gani) {
-      // b = -Gamma F_N (A_N E) (Eq. linear_system_primal with the GaNi matrix): the operator
-      // applied to the constant field E = e_r (x = 0 here), negated
+    if (gani || !g.bitmap.empty()) {
+      // b = -Gamma F (A E) (Eq. linear_system_primal; with the GaNi matrix for GaNi, with the
+      // double-grid coefficient for a pixel image): the operator applied to the constant
+      // field E = e_r (x = 0 here), negated
       CKS(matvec<T>(base + L.x, base + L.r, coefT, side + 1, nullptr, nullptr, nullptr, 2));
       ++*matvecs;
       KL(launch_negate_norm<T>(base + L.r, R, g.d, g.field, g.Nh, at<double>(L.partial), kVecBlocks, st));
@@ -935,14 +1026,27 @@ hom_status Runner_solve_mixed(Runner& run, int side, const hom_opts& o, hom_repo
   double* partial = run.at<double>(L.partial);
   const double tol = o.tol > 0 ? o.tol : 1e-8;
   const int nfin32 = run.final_blocks(8), nfin64 = run.final_blocks(16);
+  // b in FP64: closed form, or for a pixel image the operator applied to the constant
+  // field (x = 0 taken from `zero`), negated
+  auto form_rhs = [&](double2* zero) -> hom_status {
+    if (g.bitmap.empty()) {
+      KL(launch_rhs<double>(sa, side, R, g.Nh, N3, b64, partial, kVecBlocks, st));
+    } else {
+      CK(cudaMemsetAsync(zero, 0, n * sizeof(double2), st));
+      CKS(run.matvec<double>(zero, b64, coef64, side + 1, nullptr, nullptr, nullptr, 2));
+      ++*matvecs;
+      KL(launch_negate_norm<double>(b64, R, g.d, g.field, g.Nh, partial, kVecBlocks, st));
+    }
+    return HOM_OK;
+  };
   if (warm) {   // the start is in b64 (Runner::dual_start): x64 = start, r64 = b - C x64
     CK(cudaMemcpyAsync(x64, b64, n * sizeof(double2), cudaMemcpyDeviceToDevice, st));
-    KL(launch_rhs<double>(sa, side, R, g.Nh, N3, b64, partial, kVecBlocks, st));
+    CKS(form_rhs(r64));
     CKS(run.matvec<double>(x64, r64, coef64, side + 1, nullptr, nullptr, nullptr, 0, b64));
     ++*matvecs;
     KL(launch_cg_init(outer, partial, L.maxblk, nfin64, R, tol * tol, 0.0, 0, st));
   } else {
-    KL(launch_rhs<double>(sa, side, R, g.Nh, N3, b64, partial, kVecBlocks, st));
+    CKS(form_rhs(x64));
     KL(launch_cg_init(outer, partial, kVecBlocks, kVecBlocks, R, tol * tol, 0.0, 0, st));
     CK(cudaMemcpyAsync(r64, b64, n * sizeof(double2), cudaMemcpyDeviceToDevice, st));
     CK(cudaMemsetAsync(x64, 0, n * sizeof(double2), st));
@@ -1067,6 +1171,7 @@ hom_status build_batch(hom_ctx* ctx, int n, const hom_problem* probs, const hom_
     Geometry g;
     CKS(build_geometry(ctx, &probs[i], g));
     if (g.d != 2) return fail(ctx, HOM_ERR_INVALID_ARG, "hom_bounds_batched handles two-dimensional cells (d = 2)");
+    if (!g.bitmap.empty()) return fail(ctx, HOM_ERR_INVALID_ARG, "hom_bounds_batched takes inclusion cells, not images");
     double A0f[9], B0[9] = {};
     for (int a = 0; a < 3; ++a)
       for (int b = 0; b < 3; ++b) A0f[3 * a + b] = g.A0[a][b];
@@ -1664,6 +1769,9 @@ hom_status hom_rhs(hom_ctx* ctx, const hom_problem* prob, int32_t side, int32_t 
   Geometry g;
   CKS(build_geometry(ctx, prob, g));
   if (nrhs < 1 || nrhs > g.d) return fail(ctx, HOM_ERR_INVALID_ARG, "nrhs must be in [1, d]");
+  if (!g.bitmap.empty())
+    return fail(ctx, HOM_ERR_INVALID_ARG, "hom_rhs: a pixel image has no closed-form right-hand side "
+                                          "(apply hom_matvec to the constant field)");
   Runner run{ctx, g, make_layout(g, nrhs, 16, 1), static_cast<unsigned char*>(d_ws),
              static_cast<cudaStream_t>(stream), nrhs};
   if (!d_ws || ws_bytes < run.L.total) return fail(ctx, HOM_ERR_WORKSPACE, "workspace too small");
@@ -2004,6 +2112,7 @@ hom_status hom_net_features(hom_ctx* ctx, int32_t n, const hom_problem* probs, f
     Geometry g;
     CKS(build_geometry(ctx, &probs[i], g));
     if (g.d != 2) return fail(ctx, HOM_ERR_INVALID_ARG, "features are two-dimensional");
+    if (!g.bitmap.empty()) return fail(ctx, HOM_ERR_INVALID_ARG, "features take inclusion cells, not images");
     if (g.N[0] != g.N[1] || (N >= 0 && g.N[0] != N)) return fail(ctx, HOM_ERR_INVALID_ARG, "features need one square grid");
     N = g.N[0];
     basev[i] = (float)std::log10(0.5 * (g.A0[0][0] + g.A0[1][1]));

@@ -272,7 +272,7 @@ __device__ __forceinline__ void stage_bfly(const cpx<T>* __restrict__ src, cpx<T
   for (int q = 0; q < R; ++q) dst[base + q * Ns] = v[q];
 }
 
-// Runtime radix (any odd prime) straight from shared memory: output s of butterfly j,
+// Runtime radix (2 or a prime above 13) straight from shared memory: output s of butterfly j,
 // O(R) per output, so that a large prime radix spreads over R threads.
 template <typename T>
 __device__ void stage_out_generic(const cpx<T>* __restrict__ src, cpx<T>* __restrict__ dst,
@@ -305,7 +305,7 @@ __device__ cpx<T>* fft_pencils(cpx<T>* a, cpx<T>* b, int G, int ld, const FftPla
   for (int s = 0; s < plan.nrad; ++s) {
     const int R = plan.radix[s];
     const int nb = M / R;
-    if (R <= 13) {
+    if (R == 3 || R == 5 || R == 7 || R == 11 || R == 13) {
       const int total = G * nb;
       for (int t = threadIdx.x; t < total; t += blockDim.x) {
         const int g = t / nb;

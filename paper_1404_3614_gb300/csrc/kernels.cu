@@ -316,6 +316,17 @@ __global__ void k_sample_coef(SpecArgs a, double* coef) {
     for (int c = 0; c < 3; ++c) x[c] = (double)sfreq(js[c], a.M[c]) / ((double)a.M[c] * a.invY[c]);
     double v[6];
     for (int q = 0; q < 6; ++q) v[q] = a.A0p[q];
+    if (a.bitmap) {   // the pixel holding the grid point
+      long long idx = 0;
+      for (int c = a.d - 1; c >= 0; --c) {
+        int i = (int)floor((x[c] * a.invY[c] + 0.5) * a.P[c]);
+        i = i < 0 ? 0 : (i >= a.P[c] ? a.P[c] - 1 : i);
+        idx = idx * a.P[c] + i;
+      }
+      const double b = a.bitmap[idx];
+      coef[j] = a.invert ? 1.0 / b : b;
+      continue;
+    }
     for (int i = 0; i < a.nincl; ++i) {
       const DevIncl& I = a.incl[i];
       bool in = true;
@@ -332,6 +343,59 @@ __global__ void k_sample_coef(SpecArgs a, double* coef) {
         for (int q = 0; q < a.ncomp; ++q) v[q] = a.A0p[q] + I.dA[q];
     }
     for (int q = 0; q < a.ncomp; ++q) coef[q * grid + j] = v[q];
+  }
+}
+
+__global__ void k_bitmap_load(const double* bmp, double2* D, long long n, int invert) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    D[i] = make_double2(invert ? 1.0 / bmp[i] : bmp[i], 0.0);
+}
+
+__global__ void k_rotate3(const double2* in, double2* out, int P0, int P1, int P2) {
+  const long long n = (long long)P0 * P1 * P2;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const int a = (int)(i % P0);
+    const int b = (int)((i / P0) % P1);
+    const int c = (int)(i / ((long long)P0 * P1));
+    out[((long long)a * P2 + c) * P1 + b] = in[i];
+  }
+}
+
+// A_hat(n) = prod_a [(1/P_a) sinc(n_a/P_a) exp(i pi n_a (1 - 1/P_a))] D(n mod P): the pixel
+// boxes of side Y_a/P_a centred at -Y_a/2 + (i_a + 1/2) Y_a/P_a (Remark "inclusion")
+__global__ void k_bitmap_spectrum(SpecArgs a, const double2* D, double2* S) {
+  const long long n = (long long)a.len[0] * a.len[1] * a.len[2];
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+    const int i0 = (int)(e % a.len[0]);
+    const int i1 = (int)((e / a.len[0]) % a.len[1]);
+    const int i2 = (int)(e / ((long long)a.len[0] * a.len[1]));
+    const int ns[3] = {i0, sfreq(i1, a.Nmod[1]), sfreq(i2, a.Nmod[2])};
+    double re = 1.0, im = 0.0;
+    long long idx = 0;
+    for (int c = a.d - 1; c >= 0; --c) {
+      const int P = a.P[c];
+      int m = ns[c] % P;
+      if (m < 0) m += P;
+      idx = idx * P + m;
+    }
+    for (int c = 0; c < a.d; ++c) {
+      const int P = a.P[c];
+      const int nn = ns[c];
+      // sinc(n/P) and the phase pi n (P - 1)/P, arguments reduced to [0, 2) exactly
+      int r = nn % (2 * P);
+      if (r < 0) r += 2 * P;
+      const double sn = nn == 0 ? 1.0 : sinpi((double)r / P) / (M_PI * (double)nn / P);
+      long long q = ((long long)nn * (P - 1)) % (2LL * P);
+      if (q < 0) q += 2LL * P;
+      double ps, pc;
+      sincospi((double)q / P, &ps, &pc);
+      const double f = sn / P;
+      const double nre = (re * pc - im * ps) * f, nim = (re * ps + im * pc) * f;
+      re = nre;
+      im = nim;
+    }
+    const double2 dv = D[idx];
+    S[e] = make_double2(re * dv.x - im * dv.y, re * dv.y + im * dv.x);
   }
 }
 
@@ -533,6 +597,24 @@ cudaError_t launch_sample_coef(const SpecArgs& a, double* coef, cudaStream_t s) 
   long long blocks = (grid + kThreads - 1) / kThreads;
   if (blocks > 152 * 32) blocks = 152 * 32;
   k_sample_coef<<<(int)blocks, kThreads, 0, s>>>(a, coef);
+  return cudaGetLastError();
+}
+
+static int grid_blocks(long long n) {
+  long long blocks = (n + kThreads - 1) / kThreads;
+  if (blocks > 152 * 32) blocks = 152 * 32;
+  return (int)(blocks < 1 ? 1 : blocks);
+}
+cudaError_t launch_bitmap_load(const double* bmp, double2* D, long long n, int invert, cudaStream_t s) {
+  k_bitmap_load<<<grid_blocks(n), kThreads, 0, s>>>(bmp, D, n, invert);
+  return cudaGetLastError();
+}
+cudaError_t launch_rotate3(const double2* in, double2* out, int P0, int P1, int P2, cudaStream_t s) {
+  k_rotate3<<<grid_blocks((long long)P0 * P1 * P2), kThreads, 0, s>>>(in, out, P0, P1, P2);
+  return cudaGetLastError();
+}
+cudaError_t launch_bitmap_spectrum(const SpecArgs& a, const double2* D, double2* S, cudaStream_t s) {
+  k_bitmap_spectrum<<<grid_blocks((long long)a.len[0] * a.len[1] * a.len[2]), kThreads, 0, s>>>(a, D, S);
   return cudaGetLastError();
 }
 

@@ -103,6 +103,9 @@ struct SpecArgs {
   const double2* phase;   // [nincl][3][Mmax]
   const double* sinc;     // [nincl][3][Mmax]
   int Mmax;
+  const double* bitmap;   // pixel image ([P3][P2][P1], x fastest) or NULL
+  int P[3];
+  int invert;             // dual side of an image: 1 / a
 };
 
 // One batched 2D task: a (problem, side) pair solved entirely by one CTA of the
@@ -211,6 +214,13 @@ cudaError_t launch_cg_beta(CgScalars* cg, const double* partial, int ld, int nbl
                            cudaStream_t s);
 // GaNi coefficient sampled at the grid points of the M = N grid (a.M = N), packed symmetric
 cudaError_t launch_sample_coef(const SpecArgs& a, double* coef, cudaStream_t s);
+// pixel image: D = a (or 1 / a) as complex, n values
+cudaError_t launch_bitmap_load(const double* bmp, double2* D, long long n, int invert, cudaStream_t s);
+// out[a][c][b] = in[c][b][a] for an [P2][P1][P0] array (the next axis becomes contiguous)
+cudaError_t launch_rotate3(const double2* in, double2* out, int P0, int P1, int P2, cudaStream_t s);
+// spectrum of a pixel image on the half of Z_M (layout of launch_spectrum, one component) from
+// the unnormalised DFT D of the image values ([P3][P2][P1], x fastest)
+cudaError_t launch_bitmap_spectrum(const SpecArgs& a, const double2* D, double2* S, cudaStream_t s);
 // r = -r with |r|^2 partials [nrhs][nblk]
 template <typename T>
 cudaError_t launch_negate_norm(void* r, int nrhs, int C, long long field, int Nh, double* partial, int nblk,

@@ -63,7 +63,7 @@ PROBLEMS = {
 }
 
 
-@pytest.mark.parametrize("M", [1, 3, 5, 7, 9, 13, 15, 21, 37, 45, 73, 81, 125, 225, 405, 243, 343])
+@pytest.mark.parametrize("M", [1, 3, 5, 7, 9, 13, 15, 21, 37, 45, 73, 81, 125, 225, 405, 243, 343, 2, 8, 12, 34, 64])
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 def test_fft_matches_numpy(hb, ctx, M, prec):
     rng = np.random.default_rng(M)
