@@ -323,12 +323,25 @@ def box_bitmap(P, lo, hi, a_in, a_out=1.0, d=2) -> np.ndarray:
     return b
 
 
+def smooth_indicator_2d(f: np.ndarray) -> np.ndarray:
+    """The paper's local average of an image's characteristic function (Sec. 7.3): weights
+    4/16 at the pixel, 2/16 at its four edge neighbours and 1/16 at its four corner
+    neighbours, periodic."""
+    f = np.asarray(f, dtype=np.float64)
+    out = 4.0 * f
+    for s0, s1, w in ((1, 0, 2.0), (-1, 0, 2.0), (0, 1, 2.0), (0, -1, 2.0),
+                      (1, 1, 1.0), (-1, -1, 1.0), (-1, 1, 1.0), (1, -1, 1.0)):
+        out += w * np.roll(np.roll(f, s0, axis=0), s1, axis=1)
+    return out / 16.0
+
+
 def porous_bitmap_2d(seed: int, P=1199, porosity=0.45, r_min=0.01, r_max=0.04, a_solid=0.49,
-                     a_pore=0.029) -> np.ndarray:
+                     a_pore=0.029, smooth=False) -> np.ndarray:
     """A synthetic porous two-phase P x P image standing in for a micrograph: pores are the
     union of periodic disks (centres uniform, radii log-uniform in [r_min, r_max] of the cell),
     added until the pore fraction reaches `porosity`; conductivities a_solid / a_pore (the
-    paper's Sec. 7.3 phase values)."""
+    paper's Sec. 7.3 phase values); smooth=True applies smooth_indicator_2d to the solid
+    phase's characteristic function first."""
     rng = np.random.default_rng(seed)
     c = (np.arange(P) + 0.5) / P - 0.5
     X, Yg = np.meshgrid(c, c, indexing="ij")
@@ -341,5 +354,8 @@ def porous_bitmap_2d(seed: int, P=1199, porosity=0.45, r_min=0.01, r_max=0.04, a
         dx -= np.round(dx)
         dy -= np.round(dy)
         pore |= dx * dx + dy * dy < r * r
-    return np.where(pore, a_pore, a_solid)
+    solid = (~pore).astype(np.float64)
+    if smooth:
+        solid = smooth_indicator_2d(solid)
+    return a_pore + (a_solid - a_pore) * solid
 
