@@ -299,8 +299,10 @@ hom_status hom_energy(hom_ctx* ctx, const hom_problem* prob, int32_t nrhs,
                       int32_t add_constant, const void* d_coef, const void* d_x, double* W,
                       void* d_workspace, size_t workspace_bytes, void* stream);
 
-/* Batched 1D FFT of `howmany` contiguous complex sequences of odd length M
- * (any factorisation; radix-3/5 and generic odd-prime butterflies):
+/* Batched 1D FFT of `howmany` contiguous complex sequences of length M <= 4096
+ * (any factorisation; radix-3/5/7/11/13 butterflies, generic radix 2 and primes
+ * above 13 one output per thread; the double grid only needs odd lengths, images
+ * may be even):
  * out[j] = sum_k in[k] exp(dir * 2 pi i j k / M), dir = -1 (forward) or +1
  * (inverse), no normalisation. FP64 (double2) or FP32 (float2). */
 hom_status hom_fft(hom_ctx* ctx, int32_t M, int32_t precision, int32_t dir, int32_t howmany,

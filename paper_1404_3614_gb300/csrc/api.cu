@@ -1830,7 +1830,7 @@ hom_status hom_energy(hom_ctx* ctx, const hom_problem* prob, int32_t nrhs, int32
 hom_status hom_fft(hom_ctx* ctx, int32_t M, int32_t precision, int32_t dir, int32_t howmany,
                    const void* d_in, void* d_out, void* d_ws, size_t ws_bytes, void* stream) {
   if (!ctx || !d_in || !d_out || !d_ws) return fail(ctx, HOM_ERR_INVALID_ARG, "NULL argument");
-  if (M < 1 || M % 2 != 1 || M > 4095) return fail(ctx, HOM_ERR_INVALID_ARG, "M must be odd in [1, 4095]");
+  if (M < 1 || M > 4096) return fail(ctx, HOM_ERR_INVALID_ARG, "M must be in [1, 4096]");
   if (dir != 1 && dir != -1) return fail(ctx, HOM_ERR_INVALID_ARG, "dir must be +1 or -1");
   if (howmany < 0) return fail(ctx, HOM_ERR_INVALID_ARG, "howmany < 0");
   if (precision != HOM_FP64 && precision != HOM_FP32) return fail(ctx, HOM_ERR_INVALID_ARG, "precision");
