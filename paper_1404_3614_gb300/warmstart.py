@@ -21,8 +21,13 @@ import microstructures as ms
 from . import binding as bd
 
 
+def torch_cat(parts):
+    import torch
+    return torch.cat(parts, dim=-1)
+
+
 class WarmStart:
-    def __init__(self, solver, N, width=32, modes=12, layers=4, proj=128, batch=32, seed=0):
+    def __init__(self, solver, N, width=32, modes=12, layers=4, proj=128, batch=32, seed=0, energy=False):
         import torch
         self.torch = torch
         self.solver = solver
@@ -40,6 +45,7 @@ class WarmStart:
         self.grad = torch.zeros_like(self.params)
         self.ws = torch.empty(self.ws_bytes, dtype=torch.uint8, device=dev)
         self.step = 0
+        self.energy = energy   # train on sqrt(energy weight) * field, divide it out at inference
 
     # -- data -------------------------------------------------------------------------
     def features(self, problems):
@@ -53,6 +59,17 @@ class WarmStart:
             bd.hom_net_features(self.ctx, part, out[s:s + len(part)].data_ptr(), ws.data_ptr(), ws.numel())
         out.mul_(1.0 / 3.0)
         return out
+
+    @staticmethod
+    def energy_weights(x):
+        """sqrt of the pointwise energy weight of each output channel, [n, N, N, 8]: a(x) for
+        the primal correctors, 1/a(x) for the dual ones (features are log10(a)/3). The
+        energy norm of a field error is the a-weighted L2 norm (a(u, u) = (A u, u), no
+        derivative), so a plain MSE on sqrt(w) * field is the energy-norm error of the start."""
+        la = x[..., :1] * (3.0 * 2.302585092994046)   # ln a
+        primal = (0.5 * la).exp().expand(*x.shape[:-1], 4)
+        dual = (-0.5 * la).exp().expand(*x.shape[:-1], 4)
+        return torch_cat((primal, dual))
 
     @staticmethod
     def normalise_targets(y):
@@ -138,7 +155,7 @@ class WarmStart:
 
 def train_and_evaluate(N=63, n_train=20000, n_test=1024, epochs=20, batch=32, width=32, modes=12, layers=4,
                        proj=128, seed_train=1000, seed_test=100000, tol=1e-4, precision="mixed", lr=2e-3,
-                       gen_tol=1e-6, solver=None, tight_tol=1e-8):
+                       gen_tol=1e-6, solver=None, tight_tol=1e-8, energy=False):
     """The learned warm-start workload: random-rectangle cells on an N grid (the batched
     workload's distribution at one N). Returns a dict of measurements."""
     import torch
@@ -147,7 +164,7 @@ def train_and_evaluate(N=63, n_train=20000, n_test=1024, epochs=20, batch=32, wi
     if own:
         solver = hb.Bounds(0)
     prec = bd.HOM_MIXED if precision == "mixed" else bd.HOM_FP64
-    ws = WarmStart(solver, N, width, modes, layers, proj, batch, seed=seed_train)
+    ws = WarmStart(solver, N, width, modes, layers, proj, batch, seed=seed_train, energy=energy)
     t0 = time.perf_counter()
     train_probs = [ms.random_rectangles_2d(seed_train + i, N=N) for i in range(n_train)]
     test_probs = [ms.random_rectangles_2d(seed_test + i, N=N) for i in range(n_test)]
@@ -155,8 +172,11 @@ def train_and_evaluate(N=63, n_train=20000, n_test=1024, epochs=20, batch=32, wi
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     _, fields = ws.solve(train_probs, prec, gen_tol, want_fields=True)
-    y = WarmStart.normalise_targets(ws.fields_to_grid(fields))
     x = ws.features(train_probs)
+    y = ws.fields_to_grid(fields)
+    if energy:
+        y = y * WarmStart.energy_weights(x)
+    y = WarmStart.normalise_targets(y)
     torch.cuda.synchronize()
     t_data = time.perf_counter() - t0
     del fields
@@ -173,6 +193,8 @@ def train_and_evaluate(N=63, n_train=20000, n_test=1024, epochs=20, batch=32, wi
     t_zero = time.perf_counter() - t0
     t0 = time.perf_counter()
     pred = ws.predict(xt)
+    if energy:
+        pred = pred / WarmStart.energy_weights(xt)
     x0 = ws.grid_to_fields(pred, prec)
     warm, _ = ws.solve(test_probs, prec, tol, x0=x0)
     torch.cuda.synchronize()
@@ -200,7 +222,7 @@ def train_and_evaluate(N=63, n_train=20000, n_test=1024, epochs=20, batch=32, wi
     if own:
         solver.close()
     return {
-        "N": N, "n_train": n_train, "n_test": n_test, "epochs": epochs, "batch": batch,
+        "N": N, "n_train": n_train, "n_test": n_test, "epochs": epochs, "batch": batch, "energy_loss": energy,
         "network": {"width": width, "modes": modes, "layers": layers, "proj": proj, "params": ws.n_params},
         "loss_first_epoch": hist[0] if hist else None, "loss_last_epoch": hist[-1] if hist else None,
         "iters_zero_mean": float(it_zero.mean()), "iters_warm_mean": float(it_warm.mean()),
