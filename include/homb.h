@@ -174,6 +174,19 @@ hom_status hom_problem_info(hom_ctx* ctx, const hom_problem* prob, int32_t* ncom
 hom_status hom_workspace_size(hom_ctx* ctx, const hom_problem* prob, const hom_opts* opts,
                               size_t* bytes);
 
+/* Starting fields in / converged fields out for hom_bounds_io (device memory, complex
+ * FP64, layout [side 2][rhs d][comp d][Nz][Ny][(N1+1)/2], the half-spectrum layout of
+ * the fields with side 0 primal and 1 dual). A start is projected with Gamma (so any
+ * array gives a conforming field, Def. FD_projections) and scaled per right-hand side by
+ * the Rayleigh-Ritz factor s = (x.b)/(x.C x), which never gives a larger energy error than
+ * x = 0; CG then runs from it and the bounds stay guaranteed (Lemma bounds). The fields
+ * out are the FP64 re-projected CG fields the bounds were evaluated with. Either pointer
+ * may be NULL; not with GaNi. */
+typedef struct {
+  const void* d_x0;
+  void* d_fields;
+} hom_field_io;
+
 /* Whole pipeline (Algorithm of Sec. 6.2 with the exact double-grid operator in CG):
  * build both double-grid coefficients once, run d primal and d dual CG solves from
  * x0 = 0, re-project the fields in FP64 and evaluate the bound energies exactly on
@@ -185,6 +198,11 @@ hom_status hom_bounds(hom_ctx* ctx, const hom_problem* prob, const hom_opts* opt
                       void* d_workspace, size_t workspace_bytes, void* stream,
                       double* upper, double* lower, double* mean, double* D,
                       hom_report* rep);
+/* hom_bounds with starting and / or converged fields (hom_field_io; NULL: hom_bounds). */
+hom_status hom_bounds_io(hom_ctx* ctx, const hom_problem* prob, const hom_opts* opts,
+                         void* d_workspace, size_t workspace_bytes, void* stream,
+                         double* upper, double* lower, double* mean, double* D, hom_report* rep,
+                         const hom_field_io* io);
 
 /* Batched bounds for n two-dimensional cells of possibly different N, geometry and
  * phases, in ONE persistent kernel launch: each CTA takes (problem, side) tasks from an

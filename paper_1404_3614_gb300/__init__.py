@@ -43,17 +43,20 @@ class Bounds:
         return self.ws
 
     def __call__(self, problem, precision=HOM_FP64, tol=1e-8, max_iter=10000, check_every=8, sides=3,
-                 stream=None, graph=0, dual_start=0, discretization=0):
+                 stream=None, graph=0, dual_start=0, discretization=0, x0=None, fields=None):
         """hom_bounds on one problem; graph=-1 launches every CG kernel directly instead of
         replaying blocks of check_every iterations from captured CUDA graphs; dual_start=1
         starts the dual CG from the primal minimisers; discretization=1 runs GaNi (the
-        paper's algorithm: N-grid CG, double-grid bounds; adds gani_A, gani_B)."""
+        paper's algorithm: N-grid CG, double-grid bounds; adds gani_A, gani_B). x0 / fields:
+        optional complex128 device tensors [2, d, d, Nz, Ny, (N1+1)//2] of starting / converged
+        fields (a start is projected and scaled by Rayleigh-Ritz)."""
         opts = make_opts(precision, tol, max_iter, check_every, sides, graph, dual_start=dual_start,
                          discretization=discretization)
         nbytes = hom_workspace_size(self.ctx, problem, opts)
         ws = self.workspace(nbytes)
         s = stream if stream is not None else self.torch.cuda.current_stream(self.device).cuda_stream
-        return hom_bounds(self.ctx, problem, opts, ws.data_ptr(), ws.numel(), s)
+        return hom_bounds(self.ctx, problem, opts, ws.data_ptr(), ws.numel(), s,
+                          None if x0 is None else x0.data_ptr(), None if fields is None else fields.data_ptr())
 
     def batched(self, problems, precision=HOM_MIXED, tol=1e-4, max_iter=10000, graph=0, autotune=0,
                 stream=None, x0=None, fields=None):

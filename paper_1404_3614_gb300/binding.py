@@ -52,6 +52,10 @@ class hom_report(C.Structure):
                 ("batch_config", C.c_int32 * 6)]
 
 
+class hom_field_io(C.Structure):
+    _fields_ = [("d_x0", C.c_void_p), ("d_fields", C.c_void_p)]
+
+
 class hom_batch_io(C.Structure):
     _fields_ = [("d_x0", C.c_void_p), ("d_fields", C.c_void_p)]
 
@@ -81,6 +85,8 @@ def _load():
         "hom_problem_info": (i32, [vp, P(hom_problem), P(i32), P(i32), P(i64), P(i64)]),
         "hom_workspace_size": (i32, [vp, P(hom_problem), P(hom_opts), P(sz)]),
         "hom_bounds": (i32, [vp, P(hom_problem), P(hom_opts), vp, sz, vp, dp, dp, dp, dp, P(hom_report)]),
+        "hom_bounds_io": (i32, [vp, P(hom_problem), P(hom_opts), vp, sz, vp, dp, dp, dp, dp, P(hom_report),
+                                P(hom_field_io)]),
         "hom_step_workspace_size": (i32, [vp, P(hom_problem), i32, P(sz)]),
         "hom_batched_workspace_size": (i32, [vp, i32, P(hom_problem), P(hom_opts), P(sz)]),
         "hom_bounds_batched": (i32, [vp, i32, P(hom_problem), P(hom_opts), vp, sz, vp, dp, dp, P(i32), P(i32),
@@ -275,14 +281,20 @@ def hom_step_workspace_size(ctx, problem, nrhs):
     return n.value
 
 
-def hom_bounds(ctx, problem, opts, d_ws, ws_bytes, stream=0):
-    """Returns dict(upper, lower, mean, D, report, status) with d x d numpy arrays."""
+def hom_bounds(ctx, problem, opts, d_ws, ws_bytes, stream=0, d_x0=None, d_fields=None):
+    """Returns dict(upper, lower, mean, D, report, status) with d x d numpy arrays. d_x0 /
+    d_fields: optional device pointers to starting / converged fields (hom_bounds_io)."""
     p, keep = problem_struct(problem)
     d = int(problem.d)
     bufs = {k: (C.c_double * (d * d))() for k in ("upper", "lower", "mean", "D")}
     rep = hom_report()
-    st = lib.hom_bounds(ctx, C.byref(p), C.byref(opts), C.c_void_p(d_ws), ws_bytes, C.c_void_p(stream),
-                        bufs["upper"], bufs["lower"], bufs["mean"], bufs["D"], C.byref(rep))
+    if d_x0 is None and d_fields is None:
+        st = lib.hom_bounds(ctx, C.byref(p), C.byref(opts), C.c_void_p(d_ws), ws_bytes, C.c_void_p(stream),
+                            bufs["upper"], bufs["lower"], bufs["mean"], bufs["D"], C.byref(rep))
+    else:
+        io = hom_field_io(C.c_void_p(d_x0 or 0), C.c_void_p(d_fields or 0))
+        st = lib.hom_bounds_io(ctx, C.byref(p), C.byref(opts), C.c_void_p(d_ws), ws_bytes, C.c_void_p(stream),
+                               bufs["upper"], bufs["lower"], bufs["mean"], bufs["D"], C.byref(rep), C.byref(io))
     check(ctx, st)
     out = {k: np.array(v[:]).reshape(d, d) for k, v in bufs.items()}
     out["status"] = st

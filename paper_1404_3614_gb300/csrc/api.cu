@@ -326,6 +326,7 @@ struct Layout {
   size_t tw64[3], tw32[3], incl, phase, sinc, coef64, coef32, x, r, p, q, x64, b64, r64, t1, t2,
       cg[2], cgo[2], partial, epart, eout, total;
   size_t bmp = 0, bmpD[2] = {0, 0}, bmptw[3] = {0, 0, 0};   // pixel image, its DFT buffers, twiddles
+  size_t rrpart = 0;                                         // Rayleigh-Ritz partial sums
   int Mmax, maxblk, nblk_energy;
   size_t off = 0;
   size_t take(size_t bytes) {
@@ -385,6 +386,7 @@ Layout make_layout(const Geometry& g, int R, size_t elem, int mode) {
   const int xc = std::max(1, std::min(final_xc_elem(g, 16), final_xc_elem(g, 8)));
   L.maxblk = std::max(kVecBlocks, (X + xc - 1) / xc);
   L.partial = L.take((size_t)3 * L.maxblk * sizeof(double));
+  L.rrpart = L.take((size_t)6 * kVecBlocks * sizeof(double));
   L.nblk_energy = (int)g.planes;   // upper bound of the energy pass grid
   L.epart = L.take((size_t)L.nblk_energy * 9 * sizeof(double));
   L.eout = L.take(2 * 9 * sizeof(double));
@@ -921,7 +923,7 @@ struct Runner {
 
   template <typename T>
   hom_status solve_side(int side, const hom_opts& o, hom_report* rep, int* matvecs,
-                        const double2* x0 = nullptr) {
+                        const double2* x0 = nullptr, bool user_start = false) {
     const size_t elem = sizeof(T) * 2;
     double* coef64 = at<double>(L.coef64);
     if (gani) CKS(sample_coefficient(side, coef64));
@@ -949,7 +951,16 @@ struct Runner {
     }
     const double tol = o.tol > 0 ? o.tol : 1e-8;
     const int nfin = final_blocks(elem);
-    if (x0 && sizeof(T) == 8) {   // x = x0 (after b, which GaNi forms from x = 0); r0 = b - C x0
+    if (x0 && sizeof(T) == 8 && user_start) {
+      // a caller's start: x = s Gamma x0 with the Rayleigh-Ritz factor s = (x.b)/(x.C x) per
+      // right-hand side (never a larger energy error than x = 0), r = b - s C x
+      KL(launch_project_promote<double>(x0, at<double2>(L.x), R, g.d, g.N[1], g.N[2], g.Nh, g.invY, side, st));
+      CKS(matvec<T>(base + L.x, base + L.q, coefT, side + 1, nullptr, nullptr, nullptr, 0));
+      ++*matvecs;
+      KL(launch_rayleigh_ritz<double>(base + L.x, base + L.r, base + L.r, base + L.q, R, g.d, g.field, g.Nh,
+                                      at<double>(L.rrpart), at<double>(L.partial), kVecBlocks, st));
+      KL(launch_cg_init(cg, at<double>(L.partial), kVecBlocks, kVecBlocks, R, tol * tol, 0.0, 0, st));
+    } else if (x0 && sizeof(T) == 8) {   // x = x0 (after b, which GaNi forms from x = 0); r0 = b - C x0
       CK(cudaMemcpyAsync(base + L.x, x0, fb, cudaMemcpyDeviceToDevice, st));
       CKS(matvec<T>(base + L.x, base + L.r, coefT, side + 1, nullptr, nullptr, nullptr, 0, base + L.r));
       ++*matvecs;
@@ -1004,7 +1015,7 @@ struct Runner {
 // stops at |r64| <= tol |E| or when a step fails to halve |r64|; any field is a valid
 // conforming test field after the FP64 re-projection, so the bounds stay guaranteed.
 hom_status Runner_solve_mixed(Runner& run, int side, const hom_opts& o, hom_report* rep, int* matvecs,
-                              bool warm = false) {
+                              bool warm = false, bool user_start = false) {
   hom_ctx* ctx = run.ctx;
   const Geometry& g = run.g;
   const Layout& L = run.L;
@@ -1039,7 +1050,15 @@ hom_status Runner_solve_mixed(Runner& run, int side, const hom_opts& o, hom_repo
     }
     return HOM_OK;
   };
-  if (warm) {   // the start is in b64 (Runner::dual_start): x64 = start, r64 = b - C x64
+  if (warm && user_start) {   // a caller's start in b64: x64 = s Gamma start, r64 = b - s C x64
+    KL(launch_project_promote<double>(b64, x64, R, g.d, g.N[1], g.N[2], g.Nh, g.invY, side, st));
+    CKS(form_rhs(r64));
+    CKS(run.matvec<double>(x64, r64, coef64, side + 1, nullptr, nullptr, nullptr, 0));
+    ++*matvecs;
+    KL(launch_rayleigh_ritz<double>(x64, r64, b64, r64, R, g.d, g.field, g.Nh, run.at<double>(L.rrpart), partial,
+                                    kVecBlocks, st));
+    KL(launch_cg_init(outer, partial, kVecBlocks, kVecBlocks, R, tol * tol, 0.0, 0, st));
+  } else if (warm) {   // the start is in b64 (Runner::dual_start): x64 = start, r64 = b - C x64
     CK(cudaMemcpyAsync(x64, b64, n * sizeof(double2), cudaMemcpyDeviceToDevice, st));
     CKS(form_rhs(r64));
     CKS(run.matvec<double>(x64, r64, coef64, side + 1, nullptr, nullptr, nullptr, 0, b64));
@@ -1357,9 +1376,9 @@ hom_status hom_step_workspace_size(hom_ctx* ctx, const hom_problem* prob, int32_
   return HOM_OK;
 }
 
-hom_status hom_bounds(hom_ctx* ctx, const hom_problem* prob, const hom_opts* opts, void* d_ws,
-                      size_t ws_bytes, void* stream, double* upper, double* lower, double* mean,
-                      double* D, hom_report* rep) {
+static hom_status bounds_impl(hom_ctx* ctx, const hom_problem* prob, const hom_opts* opts, void* d_ws,
+                              size_t ws_bytes, void* stream, double* upper, double* lower, double* mean,
+                              double* D, hom_report* rep, const hom_field_io* io) {
   if (!ctx || !opts) return fail(ctx, HOM_ERR_INVALID_ARG, "NULL argument");
   const auto t0 = std::chrono::steady_clock::now();
   ctx->err.clear();
@@ -1374,6 +1393,8 @@ hom_status hom_bounds(hom_ctx* ctx, const hom_problem* prob, const hom_opts* opt
     return fail(ctx, HOM_ERR_INVALID_ARG, "discretization must be 0 (Ga) or 1 (GaNi)");
   const bool gani = opts->discretization == 1;
   if (gani && opts->precision != HOM_FP64) return fail(ctx, HOM_ERR_INVALID_ARG, "GaNi runs in FP64");
+  if (gani && io && (io->d_x0 || io->d_fields))
+    return fail(ctx, HOM_ERR_INVALID_ARG, "starting / output fields are for the Galerkin discretization");
   Runner run{ctx, g, make_layout(g, g.d, elem, 0), static_cast<unsigned char*>(d_ws),
              static_cast<cudaStream_t>(stream), g.d};
   const Geometry gn = gani ? gani_geometry(g) : g;
@@ -1406,12 +1427,28 @@ hom_status hom_bounds(hom_ctx* ctx, const hom_problem* prob, const hom_opts* opt
       CKS(run.energy(coef64, rn.at<double2>(rn.L.x64), 1, side));
       continue;
     }
+    const size_t side_bytes = (size_t)g.d * g.d * g.field * sizeof(double2);
     double2* x0 = elem == 16 ? run.at<double2>(run.L.q) : run.at<double2>(run.L.b64);
-    if (side == 1 && (sides & 3) == 3 && opts->dual_start == 1) CKS(run.dual_start(x0, &warm, &matvecs));
-    hom_status s = elem == 16 ? run.solve_side<double>(side, *opts, rep, &matvecs, warm ? x0 : nullptr)
-                              : Runner_solve_mixed(run, side, *opts, rep, &matvecs, warm);
+    const bool user = io && io->d_x0;
+    warm = false;
+    if (user) {
+      const unsigned char* src = static_cast<const unsigned char*>(io->d_x0) + side * side_bytes;
+      if (elem == 16) {
+        x0 = reinterpret_cast<double2*>(const_cast<unsigned char*>(src));
+      } else {
+        CK(cudaMemcpyAsync(x0, src, side_bytes, cudaMemcpyDeviceToDevice, run.st));
+      }
+      warm = true;
+    } else if (side == 1 && (sides & 3) == 3 && opts->dual_start == 1) {
+      CKS(run.dual_start(x0, &warm, &matvecs));
+    }
+    hom_status s = elem == 16 ? run.solve_side<double>(side, *opts, rep, &matvecs, warm ? x0 : nullptr, user)
+                              : Runner_solve_mixed(run, side, *opts, rep, &matvecs, warm, user);
     if (s < 0) return s;
     if (s == HOM_WARN_NOT_CONVERGED) worst = s;
+    if (io && io->d_fields)   // the re-projected FP64 fields of this side
+      CK(cudaMemcpyAsync(static_cast<unsigned char*>(io->d_fields) + side * side_bytes, run.at<double2>(run.L.x64),
+                         side_bytes, cudaMemcpyDeviceToDevice, run.st));
   }
   if (gani && rep) {   // the GaNi homogenized matrices A_{H,N}, B_{H,N} (Cor. FD_GaNi)
     CK(d2h_copy(ctx, ctx->host_e, rn.at<double>(rn.L.eout), 18 * sizeof(double), run.st));
@@ -1455,6 +1492,18 @@ hom_status hom_bounds(hom_ctx* ctx, const hom_problem* prob, const hom_opts* opt
     rep->ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   }
   return worst;
+}
+
+hom_status hom_bounds(hom_ctx* ctx, const hom_problem* prob, const hom_opts* opts, void* d_ws,
+                      size_t ws_bytes, void* stream, double* upper, double* lower, double* mean,
+                      double* D, hom_report* rep) {
+  return bounds_impl(ctx, prob, opts, d_ws, ws_bytes, stream, upper, lower, mean, D, rep, nullptr);
+}
+
+hom_status hom_bounds_io(hom_ctx* ctx, const hom_problem* prob, const hom_opts* opts, void* d_ws,
+                         size_t ws_bytes, void* stream, double* upper, double* lower, double* mean,
+                         double* D, hom_report* rep, const hom_field_io* io) {
+  return bounds_impl(ctx, prob, opts, d_ws, ws_bytes, stream, upper, lower, mean, D, rep, io);
 }
 
 hom_status hom_batched_workspace_size(hom_ctx* ctx, int32_t n, const hom_problem* probs, const hom_opts* opts,

@@ -399,6 +399,68 @@ __global__ void k_bitmap_spectrum(SpecArgs a, const double2* D, double2* S) {
   }
 }
 
+// Rayleigh-Ritz on span{x}: per right-hand side the partial sums of x.b and x.q (q = C x),
+// Hermitian weights, rows [rhs][2][nblk]
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_rr_dots(const cpx<T>* x, const cpx<T>* b, const cpx<T>* q, int C,
+                                                      long long field, FastDiv fdNh, double* part, int ld) {
+  __shared__ double red[32];
+  const int rhs = blockIdx.y;
+  const long long n = (long long)C * field;
+  const long long base = (long long)rhs * n;
+  double xb = 0.0, xq = 0.0;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int ei = (int)e;
+    const double w = ei - fdNh.div(ei) * (int)fdNh.d == 0 ? 1.0 : 2.0;
+    const cpx<T> xv = x[base + e], bv = b[base + e], qv = q[base + e];
+    xb += w * ((double)xv.x * bv.x + (double)xv.y * bv.y);
+    xq += w * ((double)xv.x * qv.x + (double)xv.y * qv.y);
+  }
+  const double s1 = block_sum(xb, red);
+  if (threadIdx.x == 0) part[(rhs * 2) * ld + blockIdx.x] = s1;
+  const double s2 = block_sum(xq, red);
+  if (threadIdx.x == 0) part[(rhs * 2 + 1) * ld + blockIdx.x] = s2;
+}
+
+// s = (x.b)/(x.Cx) (0 when x.Cx <= 0): x = s x, r = b - s q, |r|^2 partials
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_rr_apply(cpx<T>* x, cpx<T>* r, const cpx<T>* b, const cpx<T>* q, int C,
+                                                       long long field, FastDiv fdNh, const double* rrpart, int nblk,
+                                                       double* partial, int ld) {
+  __shared__ double red[32];
+  __shared__ double s_s;
+  const int rhs = blockIdx.y;
+  double a = 0.0, c = 0.0;
+  for (int i = threadIdx.x; i < nblk; i += blockDim.x) {
+    a += rrpart[(rhs * 2) * ld + i];
+    c += rrpart[(rhs * 2 + 1) * ld + i];
+  }
+  const double num = block_sum(a, red);
+  const double den = block_sum(c, red);
+  if (threadIdx.x == 0) {
+    const double sc = den > 0.0 ? num / den : 0.0;
+    s_s = isfinite(sc) ? sc : 0.0;
+  }
+  __syncthreads();
+  const T sr = T(s_s);
+  const long long n = (long long)C * field;
+  const long long base = (long long)rhs * n;
+  double acc = 0.0;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
+       e += (long long)gridDim.x * blockDim.x) {
+    const cpx<T> xv = x[base + e], bv = b[base + e], qv = q[base + e];
+    x[base + e] = mk<T>(sr * xv.x, sr * xv.y);
+    const cpx<T> rv = mk<T>(fma(-sr, qv.x, bv.x), fma(-sr, qv.y, bv.y));
+    r[base + e] = rv;
+    const int ei = (int)e;
+    const double w = ei - fdNh.div(ei) * (int)fdNh.d == 0 ? 1.0 : 2.0;
+    acc += w * ((double)rv.x * rv.x + (double)rv.y * rv.y);
+  }
+  const double s = block_sum(acc, red);
+  if (threadIdx.x == 0) partial[rhs * ld + blockIdx.x] = s;
+}
+
 // r = -r over nrhs fields of C components, with the Hermitian-weighted |r|^2 partials
 template <typename T>
 __global__ void __launch_bounds__(kThreads) k_negate_norm(cpx<T>* r, int C, long long field, FastDiv fdNh,
@@ -627,6 +689,21 @@ cudaError_t launch_negate_norm(void* r, int nrhs, int C, long long field, int Nh
                                              nblk);
   return cudaGetLastError();
 }
+template <typename T>
+cudaError_t launch_rayleigh_ritz(void* x, void* r, const void* b, const void* q, int nrhs, int C, long long field,
+                                 int Nh, double* rrpart, double* partial, int nblk, cudaStream_t s) {
+  if ((long long)C * field >= (1LL << 31)) return cudaErrorInvalidValue;
+  dim3 grid(nblk, nrhs);
+  const FastDiv fd((uint32_t)Nh);
+  k_rr_dots<T><<<grid, kThreads, 0, s>>>(reinterpret_cast<const cpx<T>*>(x), reinterpret_cast<const cpx<T>*>(b),
+                                         reinterpret_cast<const cpx<T>*>(q), C, field, fd, rrpart, nblk);
+  k_rr_apply<T><<<grid, kThreads, 0, s>>>(reinterpret_cast<cpx<T>*>(x), reinterpret_cast<cpx<T>*>(r),
+                                          reinterpret_cast<const cpx<T>*>(b), reinterpret_cast<const cpx<T>*>(q), C,
+                                          field, fd, rrpart, nblk, partial, nblk);
+  return cudaGetLastError();
+}
+template cudaError_t launch_rayleigh_ritz<double>(void*, void*, const void*, const void*, int, int, long long, int,
+                                                  double*, double*, int, cudaStream_t);
 template cudaError_t launch_negate_norm<double>(void*, int, int, long long, int, double*, int, cudaStream_t);
 template cudaError_t launch_negate_norm<float>(void*, int, int, long long, int, double*, int, cudaStream_t);
 

@@ -225,6 +225,11 @@ cudaError_t launch_bitmap_spectrum(const SpecArgs& a, const double2* D, double2*
 template <typename T>
 cudaError_t launch_negate_norm(void* r, int nrhs, int C, long long field, int Nh, double* partial, int nblk,
                                cudaStream_t s);
+// Rayleigh-Ritz on span{x} per right-hand side (q = C x given): s = (x.b)/(x.C x), x = s x,
+// r = b - s q (r may alias b), |r|^2 partials [nrhs][nblk]; rrpart holds [nrhs][2][nblk]
+template <typename T>
+cudaError_t launch_rayleigh_ritz(void* x, void* r, const void* b, const void* q, int nrhs, int C, long long field,
+                                 int Nh, double* rrpart, double* partial, int nblk, cudaStream_t s);
 struct Coef3 { double v[9]; };   // 3 x 3 row-major coefficients passed by value
 // u_b = sum_a c[b*3+a] (e_a + x_a) in place over nrhs FP64 fields of d components
 cudaError_t launch_combine_fields(double2* x, int nrhs, int d, long long field, const double* c,

@@ -230,3 +230,35 @@ def test_full_size_cube_bounds_properties(hb, solver):
     small = solver(p.with_N(21), precision=hb.HOM_FP64, tol=1e-8)
     assert out64["upper"][0, 0] <= small["upper"][0, 0] + 1e-9
     assert out64["lower"][0, 0] >= small["lower"][0, 0] - 1e-9
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("name", ["aniso3d_N5", "cube3d_N7", "square2d_N23", "spheres3d_N7"])
+def test_starting_fields_and_fields_out(hb, solver, name, prec):
+    """hom_bounds_io: the converged fields come back out; restarting from them (any scale:
+    Rayleigh-Ritz rescales the start) needs almost no iterations; a random start gives the
+    same converged bounds; all bounds stay guaranteed."""
+    precision = hb.HOM_FP64 if prec == "fp64" else hb.HOM_MIXED
+    tol = 1e-10 if prec == "fp64" else 1e-6
+    p = CASES[name]()
+    d = p.d
+    N = [int(n) for n in p.N] + [1] * (3 - d)
+    shape = (2, d, d, N[2], N[1], (N[0] + 1) // 2)
+    fields = torch.zeros(shape, dtype=torch.complex128, device="cuda")
+    ref = solver(p, precision=precision, tol=tol, fields=fields)
+    it0 = ref["report"]["iters"]
+    start = 3.0 * fields
+    again = solver(p, precision=precision, tol=tol, x0=start)
+    # FP64: within two iterations; mixed: the Rayleigh-Ritz factor of an inexact field is not
+    # exactly 1, so one short refinement may follow
+    limit = 2 if prec == "fp64" else max(2, 0.2 * max(max(r) for r in it0))
+    assert max(max(r) for r in again["report"]["iters"]) <= limit, (it0, again["report"]["iters"])
+    for key in ("upper", "lower"):
+        assert rel(again[key], ref[key]) <= (1e-9 if prec == "fp64" else 1e-6)
+    g = torch.Generator(device="cuda").manual_seed(3)
+    rnd = torch.randn(shape, dtype=torch.complex128, device="cuda", generator=g)
+    out = solver(p, precision=precision, tol=tol, x0=rnd)
+    dense = oracle.dense_bounds(p)
+    for key in ("upper", "lower"):
+        assert rel(out[key], dense[key]) <= (1e-9 if prec == "fp64" else 1e-6)
+    assert loewner_ge(out["upper"], dense["upper"], 1e-9) and loewner_ge(dense["lower"], out["lower"], 1e-9)
