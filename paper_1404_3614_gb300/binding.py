@@ -267,6 +267,11 @@ def hom_bounds_batched(ctx, problems, opts, d_ws, ws_bytes, stream=0, d_x0=None,
                                           list(rep.batch_config)))}}
 
 
+def hom_bounds_io(ctx, problem, opts, d_ws, ws_bytes, stream=0, d_x0=None, d_fields=None):
+    """hom_bounds with starting / converged fields (device pointers, see hom_field_io)."""
+    return hom_bounds(ctx, problem, opts, d_ws, ws_bytes, stream, d_x0, d_fields)
+
+
 def hom_workspace_size(ctx, problem, opts):
     p, keep = problem_struct(problem)
     n = C.c_size_t()
