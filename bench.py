@@ -103,6 +103,26 @@ def run_learned(args):
     return 0
 
 
+def run_learned3d(args):
+    """The 3D learned warm start: train on method-generated correctors of random-sphere cells
+    (16 balls, volume fraction 0.3, contrast 1000) at N = 41, then time the 3D sphere workload
+    (N = 113, seed 0) in mixed precision from zero and from the network's start (features,
+    forward and transform included), plus held-out N = 41 cells (one JSON line)."""
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1404_3614_gb300 as hb
+    from paper_1404_3614_gb300 import warmstart
+    solver = hb.Bounds(0)
+    res = warmstart.train_and_evaluate_3d(N_train=41, N_eval=113, n_train=args.learned_train3d,
+                                          n_test=args.learned_test3d, eval_seeds=(0, 1), epochs=args.learned_epochs3d,
+                                          batch=8, width=args.learned_width3d, modes=args.learned_modes3d, layers=4,
+                                          proj=64, tol=TOL, precision="mixed", solver=solver)
+    print(json.dumps({"workload": "3D learned warm start, random-sphere cells, trained at N=41, "
+                      "evaluated at N=113 (seed 0 = the 3D sphere workload)", **res}), flush=True)
+    solver.close()
+    return 0
+
+
 def run_batched_only(args):
     """The batched workload alone (for kernel captures): `--batch-n` random-rectangle cells."""
     import torch
@@ -645,6 +665,12 @@ def main():
     ap.add_argument("--learned-train", type=int, default=20000)
     ap.add_argument("--learned-test", type=int, default=1024)
     ap.add_argument("--learned-epochs", type=int, default=20)
+    ap.add_argument("--learned3d", action="store_true", help="3D learned warm-start workload only")
+    ap.add_argument("--learned-train3d", type=int, default=1000)
+    ap.add_argument("--learned-test3d", type=int, default=16)
+    ap.add_argument("--learned-epochs3d", type=int, default=30)
+    ap.add_argument("--learned-width3d", type=int, default=24)
+    ap.add_argument("--learned-modes3d", type=int, default=8)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -656,6 +682,8 @@ def main():
         return run_batched_only(args)
     if args.learned:
         return run_learned(args)
+    if args.learned3d:
+        return run_learned3d(args)
     return run_gpu(args)
 
 

@@ -233,17 +233,21 @@ hom_status hom_bounds_batched(hom_ctx* ctx, int32_t n, const hom_problem* probs,
                               void* stream, double* upper, double* lower, int32_t* status,
                               int32_t* iters, hom_report* rep, const hom_batch_io* io);
 
-/* ---- learned warm start: a 2D Fourier-layer network (no counterpart in the paper's
- * algorithm; the paper's guarantee makes any starting field admissible after projection).
+/* ---- learned warm start: a 2D or 3D Fourier-layer network (no counterpart in the paper's
+ * algorithm; the paper's guarantee makes any starting field admissible after projection,
+ * Lemma bounds and the remark after Eq. linear_system_dual).
  * Layers: lift (cin -> width), `layers` spectral layers keeping kx in [0, modes) and
- * ky in [-modes, modes) with per-mode complex channel mixing plus a 1x1 path and GELU,
- * projection width -> proj (GELU) -> cout. Every product is a BF16 tensor-core GEMM with
- * FP32 accumulation; parameters are FP32 (a flat array, layout fixed by the config).
- * Activations are channels-last [batch][N][N][ch] FP32. The network calls keep the DFT
- * bases at the front of their workspace between calls with the same workspace pointer
- * and grid: do not write into a network workspace between network calls. */
+ * ky (and kz in 3D) in [-modes, modes) with per-mode complex channel mixing plus a 1x1
+ * path and GELU, projection width -> proj (GELU) -> cout (cout <= proj). Every product is a
+ * BF16 tensor-core GEMM with FP32 accumulation; parameters are FP32 (a flat array, layout
+ * fixed by the config; spectral weights [re/im][kz][ky][kx][width][width]). Activations are
+ * channels-last [batch][(N)][N][N][ch] FP32. The spectral layers use 1/N^d-normalised
+ * inverse transforms, so one set of parameters runs on any grid with 2 modes <= N. The
+ * network calls keep the DFT bases at the front of their workspace between calls with the
+ * same workspace pointer and grid: do not write into a network workspace between network
+ * calls. d = 0 is read as 2. */
 typedef struct {
-  int32_t N, cin, width, modes, layers, proj, cout;
+  int32_t N, cin, width, modes, layers, proj, cout, d;
 } hom_net_config;
 
 /* number of parameters and workspace bytes for `batch` samples */
@@ -265,16 +269,23 @@ hom_status hom_net_train_step(hom_ctx* ctx, const hom_net_config* cfg, float* d_
                               float* d_v, float* d_grad, int32_t step, float lr, int32_t batch,
                               const float* d_in, const float* d_target, float* d_loss,
                               void* d_workspace, size_t workspace_bytes, void* stream);
-/* input features of n cells on their N grid: log10 of the mean diagonal phase value at
- * the grid points x_j = Y j / N, [n][N][N][1]; enqueue only (tables copied from host). */
+/* input features of n inclusion cells (all 2D or all 3D, one cubic grid N) on their N
+ * grid: log10 of the mean diagonal phase value at the grid points x_j = Y j / N,
+ * [n][(N)][N][N][1]; synchronises `stream` (tables staged from host). */
 hom_status hom_net_features(hom_ctx* ctx, int32_t n, const hom_problem* probs, float* d_features,
                             void* d_workspace, size_t workspace_bytes, void* stream);
-/* real N-grid fields [B][N][N][ch] <-> half spectra [B][ch][N][(N+1)/2] with the 1/N^2 of
- * Eq. DFT on the forward side; precision HOM_FP64 (double2) or HOM_FP32 (float2). */
-hom_status hom_grid_to_half(hom_ctx* ctx, int32_t N, int32_t batch, int32_t ch, const float* d_grid,
-                            void* d_half, int32_t precision, void* stream);
-hom_status hom_half_to_grid(hom_ctx* ctx, int32_t N, int32_t batch, int32_t ch, const void* d_half,
-                            float* d_grid, int32_t precision, void* stream);
+/* real N-grid fields [B][(N)][N][N][ch] <-> half spectra [B][ch][(N)][N][(N+1)/2] (the
+ * solver's field layout) with the 1/N^d of Eq. DFT on the forward side; d = 2 or 3, odd
+ * N <= 169; precision HOM_FP64 (double2) or HOM_FP32 (float2); sums in FP32 (the fields
+ * are network inputs and outputs). The 3D inverse needs a device scratch of
+ * hom_half_to_grid_workspace_size bytes (ignored in 2D, may be NULL there); enqueue only. */
+hom_status hom_grid_to_half(hom_ctx* ctx, int32_t d, int32_t N, int32_t batch, int32_t ch,
+                            const float* d_grid, void* d_half, int32_t precision, void* stream);
+hom_status hom_half_to_grid_workspace_size(hom_ctx* ctx, int32_t d, int32_t N, int32_t batch,
+                                           int32_t ch, size_t* bytes);
+hom_status hom_half_to_grid(hom_ctx* ctx, int32_t d, int32_t N, int32_t batch, int32_t ch,
+                            const void* d_half, float* d_grid, int32_t precision,
+                            void* d_workspace, size_t workspace_bytes, void* stream);
 /* the tensor-core GEMM: C = alpha op(A) op(B) + beta C (row-major FP32 in memory, BF16
  * products, FP32 accumulation); enqueue only. */
 hom_status hom_gemm_bf16(hom_ctx* ctx, int32_t M, int32_t N, int32_t K, const float* d_A, int32_t lda,

@@ -62,7 +62,7 @@ class hom_batch_io(C.Structure):
 
 class hom_net_config(C.Structure):
     _fields_ = [("N", C.c_int32), ("cin", C.c_int32), ("width", C.c_int32), ("modes", C.c_int32),
-                ("layers", C.c_int32), ("proj", C.c_int32), ("cout", C.c_int32)]
+                ("layers", C.c_int32), ("proj", C.c_int32), ("cout", C.c_int32), ("d", C.c_int32)]
 
 
 class HombError(RuntimeError):
@@ -98,8 +98,9 @@ def _load():
         "hom_net_train_step": (i32, [vp, P(hom_net_config), vp, vp, vp, vp, i32, C.c_float, i32, vp, vp, vp, vp,
                                      sz, vp]),
         "hom_net_features": (i32, [vp, i32, P(hom_problem), vp, vp, sz, vp]),
-        "hom_grid_to_half": (i32, [vp, i32, i32, i32, vp, vp, i32, vp]),
-        "hom_half_to_grid": (i32, [vp, i32, i32, i32, vp, vp, i32, vp]),
+        "hom_grid_to_half": (i32, [vp, i32, i32, i32, i32, vp, vp, i32, vp]),
+        "hom_half_to_grid_workspace_size": (i32, [vp, i32, i32, i32, i32, P(sz)]),
+        "hom_half_to_grid": (i32, [vp, i32, i32, i32, i32, vp, vp, i32, vp, sz, vp]),
         "hom_gemm_bf16": (i32, [vp, i32, i32, i32, vp, i32, i32, vp, i32, i32, vp, i32, C.c_float, C.c_float, vp]),
         "hom_coefficient": (i32, [vp, P(hom_problem), i32, i32, vp, vp, sz, vp]),
         "hom_rhs": (i32, [vp, P(hom_problem), i32, i32, i32, vp, vp, sz, vp]),
@@ -385,8 +386,8 @@ def hom_kernel_timing(ctx):
 # ------------------------------------------------------------------------------------
 # learned warm start
 # ------------------------------------------------------------------------------------
-def net_config(N, cin=1, width=32, modes=12, layers=4, proj=128, cout=8):
-    return hom_net_config(N, cin, width, modes, layers, proj, cout)
+def net_config(N, cin=1, width=32, modes=12, layers=4, proj=128, cout=8, d=2):
+    return hom_net_config(N, cin, width, modes, layers, proj, cout, d)
 
 
 def hom_net_sizes(ctx, cfg, batch):
@@ -427,14 +428,20 @@ def hom_net_features(ctx, problems, d_features, d_ws, ws_bytes, stream=0):
                                            ws_bytes, C.c_void_p(stream)))
 
 
-def hom_grid_to_half(ctx, N, batch, ch, d_grid, d_half, precision, stream=0):
-    return check(ctx, lib.hom_grid_to_half(ctx, N, batch, ch, C.c_void_p(d_grid), C.c_void_p(d_half), precision,
+def hom_grid_to_half(ctx, d, N, batch, ch, d_grid, d_half, precision, stream=0):
+    return check(ctx, lib.hom_grid_to_half(ctx, d, N, batch, ch, C.c_void_p(d_grid), C.c_void_p(d_half), precision,
                                            C.c_void_p(stream)))
 
 
-def hom_half_to_grid(ctx, N, batch, ch, d_half, d_grid, precision, stream=0):
-    return check(ctx, lib.hom_half_to_grid(ctx, N, batch, ch, C.c_void_p(d_half), C.c_void_p(d_grid), precision,
-                                           C.c_void_p(stream)))
+def hom_half_to_grid_workspace_size(ctx, d, N, batch, ch):
+    b = C.c_size_t()
+    check(ctx, lib.hom_half_to_grid_workspace_size(ctx, d, N, batch, ch, C.byref(b)))
+    return b.value
+
+
+def hom_half_to_grid(ctx, d, N, batch, ch, d_half, d_grid, precision, d_ws=0, ws_bytes=0, stream=0):
+    return check(ctx, lib.hom_half_to_grid(ctx, d, N, batch, ch, C.c_void_p(d_half), C.c_void_p(d_grid), precision,
+                                           C.c_void_p(d_ws), ws_bytes, C.c_void_p(stream)))
 
 
 def hom_gemm_bf16(ctx, M, N, K, d_A, lda, ta, d_B, ldb, tb, d_C, ldc, alpha=1.0, beta=0.0, stream=0):

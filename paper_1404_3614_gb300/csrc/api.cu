@@ -51,7 +51,7 @@ struct hom_ctx {
   cudaGraphExec_t graph_exec = nullptr;
   // network: DFT bases already uploaded to this workspace for this grid / mode count
   const void* net_bases_ws = nullptr;
-  int net_bases_N = 0, net_bases_modes = 0;
+  int net_bases_N = 0, net_bases_modes = 0, net_bases_d = 0;
   // single-problem paths: tables already at the front of this workspace for this problem
   std::vector<unsigned char> tables_key;
   // CG iteration blocks captured as graphs (private capture stream, replayed on the caller's)
@@ -968,7 +968,8 @@ struct Runner {
     } else {
       KL(launch_cg_init(cg, at<double>(L.partial), kVecBlocks, kVecBlocks, R, tol * tol, 0.0, 0, st));
     }
-    const int maxit = o.max_iter > 0 ? o.max_iter : 10000;
+    // with a caller's start, max_iter = 0 is taken literally: bounds of the projected start
+    const int maxit = o.max_iter > 0 ? o.max_iter : ((o.max_iter == 0 && x0 && user_start) ? 0 : 10000);
     const int every = o.check_every > 0 ? o.check_every : 8;
     // an initial poll avoids work when b = 0 (homogeneous cells)
     CK(d2h_copy(ctx, ctx->host_cg, cg, sizeof(CgScalars), st));
@@ -1070,7 +1071,7 @@ hom_status Runner_solve_mixed(Runner& run, int side, const hom_opts& o, hom_repo
     CK(cudaMemcpyAsync(r64, b64, n * sizeof(double2), cudaMemcpyDeviceToDevice, st));
     CK(cudaMemsetAsync(x64, 0, n * sizeof(double2), st));
   }
-  const int maxit = o.max_iter > 0 ? o.max_iter : 10000;
+  const int maxit = o.max_iter > 0 ? o.max_iter : ((o.max_iter == 0 && warm && user_start) ? 0 : 10000);
   const int every = o.check_every > 0 ? o.check_every : 8;
   const double eta = 1e-5;
   int used = 0;
@@ -2021,10 +2022,12 @@ hom_status hom_kernel_timing(hom_ctx* ctx, int64_t* launches, double* total_ms) 
 // ---- learned warm start ------------------------------------------------------------
 static hom_status net_cfg(hom_ctx* ctx, const hom_net_config* c, NetConfig* out) {
   if (!c) return fail(ctx, HOM_ERR_INVALID_ARG, "NULL config");
+  const int d = c->d == 0 ? 2 : c->d;
   if (c->N < 3 || c->N % 2 == 0 || c->N > 255 || c->cin < 1 || c->width < 1 || c->width > 256 || c->modes < 1 ||
-      2 * c->modes > c->N || c->layers < 1 || c->layers > 8 || c->proj < 1 || c->cout < 1)
+      2 * c->modes > c->N || c->layers < 1 || c->layers > 8 || c->proj < 1 || c->cout < 1 || c->cout > c->proj ||
+      (d != 2 && d != 3))
     return fail(ctx, HOM_ERR_INVALID_ARG, "invalid network configuration");
-  *out = NetConfig{c->N, c->cin, c->width, c->modes, c->layers, c->proj, c->cout};
+  *out = NetConfig{c->N, c->cin, c->width, c->modes, c->layers, c->proj, c->cout, d};
   return HOM_OK;
 }
 
@@ -2038,13 +2041,15 @@ static hom_status net_prepare(hom_ctx* ctx, const NetConfig& c, int batch, void*
   if (!d_ws || ws_bytes < net_ws_bytes(c, batch)) return fail(ctx, HOM_ERR_WORKSPACE, "workspace too small");
   float* b = static_cast<float*>(d_ws);
   ctx->tables_key.clear();
-  if (ctx->net_bases_ws != d_ws || ctx->net_bases_N != c.N || ctx->net_bases_modes != c.modes) {
+  if (ctx->net_bases_ws != d_ws || ctx->net_bases_N != c.N || ctx->net_bases_modes != c.modes ||
+      ctx->net_bases_d != c.d) {
     std::vector<float> hb((size_t)bases_floats(c));
     fill_bases(c, hb.data());
     CK(h2d_copy(ctx, b, hb.data(), hb.size() * sizeof(float), st));
     ctx->net_bases_ws = d_ws;
     ctx->net_bases_N = c.N;
     ctx->net_bases_modes = c.modes;
+    ctx->net_bases_d = c.d;
   }
   *bases = b;
   *rest = b + ((bases_floats(c) + 255) / 256) * 256;
@@ -2122,26 +2127,35 @@ hom_status hom_net_train_step(hom_ctx* ctx, const hom_net_config* cfg, float* d_
 namespace {
 struct FeatIncl {
   int shape;
-  float c[2], h[2], value;
+  float c[3], h[3], value;
 };
-__global__ void k_features(int n, int N, const int* offs, const FeatIncl* incl, const float* base_val,
+// one thread per grid point x_j = Y j / N of one cell (2D or 3D); strict membership with
+// periodic images, later inclusions overwrite earlier ones
+__global__ void k_features(int n, int d, int N, const int* offs, const FeatIncl* incl, const float* base_val,
                            const float* Y, float* out) {
-  const long long total = (long long)n * N * N;
+  const long long per = d == 3 ? (long long)N * N * N : (long long)N * N;
+  const long long total = (long long)n * per;
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
        t += (long long)gridDim.x * blockDim.x) {
-    const int p = (int)(t / ((long long)N * N));
-    const int j = (int)(t - (long long)p * N * N);
-    const int jy = j / N, jx = j - jy * N;
-    const float Yx = Y[2 * p], Yy = Y[2 * p + 1];
-    const float x = Yx * jx / N, y = Yy * jy / N;
+    const int p = (int)(t / per);
+    long long j = t - (long long)p * per;
+    int jx = (int)(j % N);
+    j /= N;
+    const int jy = (int)(j % N);
+    const int jz = (int)(j / N);
+    float x[3] = {Y[3 * p] * jx / N, Y[3 * p + 1] * jy / N, d == 3 ? Y[3 * p + 2] * jz / N : 0.f};
     float v = base_val[p];
     for (int k = offs[p]; k < offs[p + 1]; ++k) {
       const FeatIncl& I = incl[k];
-      float dx = x - I.c[0], dy = y - I.c[1];
-      dx -= Yx * rintf(dx / Yx);
-      dy -= Yy * rintf(dy / Yy);
-      const bool in = I.shape == 0 ? (fabsf(dx) < 0.5f * I.h[0] && fabsf(dy) < 0.5f * I.h[1])
-                                   : (dx * dx + dy * dy < I.h[0] * I.h[0]);
+      bool in = true;
+      float r2 = 0.f;
+      for (int a = 0; a < d; ++a) {
+        float dx = x[a] - I.c[a];
+        dx -= Y[3 * p + a] * rintf(dx / Y[3 * p + a]);
+        in = in && fabsf(dx) < 0.5f * I.h[a];
+        r2 += dx * dx;
+      }
+      if (I.shape != 0) in = r2 < I.h[0] * I.h[0];
       if (in) v = I.value;
     }
     out[t] = v;
@@ -2155,26 +2169,31 @@ hom_status hom_net_features(hom_ctx* ctx, int32_t n, const hom_problem* probs, f
   CKS(set_device(ctx));
   std::vector<int> offs(n + 1, 0);
   std::vector<FeatIncl> inc;
-  std::vector<float> basev(n), Y(2 * n);
-  int N = -1;
+  std::vector<float> basev(n), Y(3 * n);
+  int N = -1, d = -1;
   for (int i = 0; i < n; ++i) {
     Geometry g;
     CKS(build_geometry(ctx, &probs[i], g));
-    if (g.d != 2) return fail(ctx, HOM_ERR_INVALID_ARG, "features are two-dimensional");
     if (!g.bitmap.empty()) return fail(ctx, HOM_ERR_INVALID_ARG, "features take inclusion cells, not images");
-    if (g.N[0] != g.N[1] || (N >= 0 && g.N[0] != N)) return fail(ctx, HOM_ERR_INVALID_ARG, "features need one square grid");
+    if (d >= 0 && g.d != d) return fail(ctx, HOM_ERR_INVALID_ARG, "features need cells of one dimension");
+    d = g.d;
+    bool cubic = g.N[0] == g.N[1] && (d == 2 || g.N[2] == g.N[0]);
+    if (!cubic || (N >= 0 && g.N[0] != N)) return fail(ctx, HOM_ERR_INVALID_ARG, "features need one cubic grid");
     N = g.N[0];
-    basev[i] = (float)std::log10(0.5 * (g.A0[0][0] + g.A0[1][1]));
-    Y[2 * i] = (float)g.Y[0];
-    Y[2 * i + 1] = (float)g.Y[1];
+    double tr = 0.0;
+    for (int a = 0; a < d; ++a) tr += g.A0[a][a];
+    basev[i] = (float)std::log10(tr / d);
+    for (int a = 0; a < 3; ++a) Y[3 * i + a] = a < d ? (float)g.Y[a] : 1.f;
     for (const hom_inclusion& I : g.incl) {
       FeatIncl f;
       f.shape = I.shape == HOM_BOX ? 0 : 1;
-      f.c[0] = (float)I.center[0];
-      f.c[1] = (float)I.center[1];
-      f.h[0] = (float)I.size[0];
-      f.h[1] = (float)I.size[1];
-      f.value = (float)std::log10(0.5 * (I.A[0] + I.A[4]));
+      double itr = 0.0;
+      for (int a = 0; a < 3; ++a) {
+        f.c[a] = a < d ? (float)I.center[a] : 0.f;
+        f.h[a] = a < d ? (float)I.size[a] : 0.f;
+      }
+      for (int a = 0; a < d; ++a) itr += I.A[a * 3 + a];
+      f.value = (float)std::log10(itr / d);
       inc.push_back(f);
     }
     offs[i + 1] = (int)inc.size();
@@ -2199,9 +2218,9 @@ hom_status hom_net_features(hom_ctx* ctx, int32_t n, const hom_problem* probs, f
   CK(h2d_copy(ctx, p_inc.first, inc.data(), p_inc.second, st));
   CK(h2d_copy(ctx, p_base.first, basev.data(), p_base.second, st));
   CK(h2d_copy(ctx, p_Y.first, Y.data(), p_Y.second, st));
-  const long long total = (long long)n * N * N;
+  const long long total = (long long)n * N * N * (d == 3 ? N : 1);
   const int blocks = (int)std::min<long long>((total + 255) / 256, 152 * 16);
-  k_features<<<blocks, 256, 0, st>>>(n, N, static_cast<const int*>(p_offs.first), static_cast<const FeatIncl*>(p_inc.first),
+  k_features<<<blocks, 256, 0, st>>>(n, d, N, static_cast<const int*>(p_offs.first), static_cast<const FeatIncl*>(p_inc.first),
                                      static_cast<const float*>(p_base.first), static_cast<const float*>(p_Y.first),
                                      d_features);
   CK(cudaGetLastError());
@@ -2211,21 +2230,34 @@ hom_status hom_net_features(hom_ctx* ctx, int32_t n, const hom_problem* probs, f
   return HOM_OK;
 }
 
-hom_status hom_grid_to_half(hom_ctx* ctx, int32_t N, int32_t batch, int32_t ch, const float* d_grid, void* d_half,
-                            int32_t precision, void* stream) {
-  if (!ctx || N < 1 || N % 2 == 0 || N > 511 || batch < 1 || ch < 1 || !d_grid || !d_half)
-    return fail(ctx, HOM_ERR_INVALID_ARG, "bad argument");
+static bool half_args_ok(int32_t d, int32_t N, int32_t batch, int32_t ch) {
+  return (d == 2 || d == 3) && N >= 1 && N % 2 == 1 && N <= 169 && batch >= 1 && ch >= 1 &&
+         (long long)batch * ch * (d == 3 ? N : 1) < 0x7fffffffLL;
+}
+
+hom_status hom_grid_to_half(hom_ctx* ctx, int32_t d, int32_t N, int32_t batch, int32_t ch, const float* d_grid,
+                            void* d_half, int32_t precision, void* stream) {
+  if (!ctx || !half_args_ok(d, N, batch, ch) || !d_grid || !d_half) return fail(ctx, HOM_ERR_INVALID_ARG, "bad argument");
   CKS(set_device(ctx));
-  KL(grid_to_half(N, batch, ch, d_grid, d_half, precision == HOM_FP64 ? 1 : 0, static_cast<cudaStream_t>(stream)));
+  KL(grid_to_half(d, N, batch, ch, d_grid, d_half, precision == HOM_FP64 ? 1 : 0, static_cast<cudaStream_t>(stream)));
   return HOM_OK;
 }
 
-hom_status hom_half_to_grid(hom_ctx* ctx, int32_t N, int32_t batch, int32_t ch, const void* d_half, float* d_grid,
-                            int32_t precision, void* stream) {
-  if (!ctx || N < 1 || N % 2 == 0 || N > 511 || batch < 1 || ch < 1 || !d_grid || !d_half)
-    return fail(ctx, HOM_ERR_INVALID_ARG, "bad argument");
+hom_status hom_half_to_grid_workspace_size(hom_ctx* ctx, int32_t d, int32_t N, int32_t batch, int32_t ch,
+                                           size_t* bytes) {
+  if (!ctx || !half_args_ok(d, N, batch, ch) || !bytes) return fail(ctx, HOM_ERR_INVALID_ARG, "bad argument");
+  *bytes = d == 3 ? half3d_tmp_bytes(N, batch, ch) : 0;
+  return HOM_OK;
+}
+
+hom_status hom_half_to_grid(hom_ctx* ctx, int32_t d, int32_t N, int32_t batch, int32_t ch, const void* d_half,
+                            float* d_grid, int32_t precision, void* d_ws, size_t ws_bytes, void* stream) {
+  if (!ctx || !half_args_ok(d, N, batch, ch) || !d_grid || !d_half) return fail(ctx, HOM_ERR_INVALID_ARG, "bad argument");
+  if (d == 3 && (!d_ws || ws_bytes < half3d_tmp_bytes(N, batch, ch)))
+    return fail(ctx, HOM_ERR_WORKSPACE, "workspace too small");
   CKS(set_device(ctx));
-  KL(half_to_grid(N, batch, ch, d_half, d_grid, precision == HOM_FP64 ? 1 : 0, static_cast<cudaStream_t>(stream)));
+  KL(half_to_grid(d, N, batch, ch, d_half, d_grid, precision == HOM_FP64 ? 1 : 0, d_ws,
+                  static_cast<cudaStream_t>(stream)));
   return HOM_OK;
 }
 

@@ -1,9 +1,11 @@
-// Learned CG warm start: a 2D Fourier-layer network (lift, L spectral layers, projection)
-// trained and run with a BF16 tensor-core GEMM (mma.sync m16n8k16, FP32 accumulation).
+// Learned CG warm start: a 2D or 3D Fourier-layer network (lift, L spectral layers,
+// projection) trained and run with a BF16 tensor-core GEMM (mma.sync m16n8k16, FP32
+// accumulation).
 //
 // Every operation is a GEMM or an elementwise kernel:
 //   spectral layer  s = E_x [ H_y ( R_k ( G_y ( F_x v ) ) ) ]   (truncated DFTs as GEMMs
-//                   against DFT bases, per-mode complex channel mixing R_k), then
+//                   against DFT bases, per-mode complex channel mixing R_k; in 3D a
+//                   G_z / H_z pair sits inside G_y / H_y), then
 //   z = s + v W + b, v' = GELU(z) (no activation after the last layer);
 //   lift v0 = x W_l + b_l, projection out = GELU(v_L P1 + b1) P2 + b2.
 // The network output is a real field on the N grid; its DFT, projected by Gamma^E /
@@ -146,6 +148,18 @@ static thread_local long long g_split_floats = 0;
 
 cudaError_t gemm_bf16(const GemmArgs& g, cudaStream_t s) {
   if (g.M <= 0 || g.N <= 0 || g.batch <= 0) return cudaSuccess;
+  if ((g.M + GBM - 1) / GBM > 65535) {   // grid y is limited to 65535 tiles: chunks of rows
+    const int rows = 65535 * GBM;
+    for (int r0 = 0; r0 < g.M; r0 += rows) {
+      GemmArgs h = g;
+      h.M = std::min(rows, g.M - r0);
+      h.A = g.ta ? g.A + r0 : g.A + (long long)r0 * g.lda;
+      h.C = g.C + (long long)r0 * g.ldc;
+      const cudaError_t e = gemm_bf16(h, s);
+      if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+  }
   const int gm = (g.M + GBM - 1) / GBM, gn = (g.N + GBN - 1) / GBN;
   int ksplit = 1;
   const long long tiles = (long long)gm * gn * g.batch;
@@ -153,6 +167,17 @@ cudaError_t gemm_bf16(const GemmArgs& g, cudaStream_t s) {
     ksplit = (int)std::min<long long>(256, std::max<long long>(1, (304 + tiles - 1) / tiles));
     ksplit = std::min(ksplit, (g.K + 1023) / 1024);
     while (ksplit > 1 && (long long)ksplit * g.M * g.N * g.batch > g_split_floats) --ksplit;
+  }
+  if (ksplit == 1 && g.batch > 65535) {   // grid z is limited to 65535: chunks of batches
+    for (int b0 = 0; b0 < g.batch; b0 += 65535) {
+      GemmArgs h = g;
+      h.batch = std::min(65535, g.batch - b0);
+      h.A = g.A + (long long)b0 * g.sA;
+      h.B = g.B + (long long)b0 * g.sB;
+      h.C = g.C + (long long)b0 * g.sC;
+      k_gemm<<<dim3(gn, gm, h.batch), 128, 0, s>>>(h, 1, nullptr);
+    }
+    return cudaGetLastError();
   }
   dim3 grid(gn, gm, g.batch * ksplit);
   k_gemm<<<grid, 128, 0, s>>>(g, ksplit, g_split_ws);
@@ -265,15 +290,25 @@ static int eblocks(long long n) { return (int)std::min<long long>((n + 255) / 25
 // ---------------------------------------------------------------------------------
 // layout
 // ---------------------------------------------------------------------------------
+// kept modes of one spectral layer: K1^(d-1) * K
+static long long spectral_modes(const NetConfig& c) {
+  const long long K1 = 2 * c.modes;
+  return (c.d == 3 ? K1 * K1 : K1) * c.modes;
+}
+static long long ipow(long long b, int e) {
+  long long r = 1;
+  for (int i = 0; i < e; ++i) r *= b;
+  return r;
+}
+
 NetOffsets net_offsets(const NetConfig& c) {
   NetOffsets o{};
   long long off = 0;
   auto take = [&](long long n) { const long long r = off; off += n; return r; };
-  const int K1 = 2 * c.modes;
   o.lift_w = take((long long)c.cin * c.width);
   o.lift_b = take(c.width);
   for (int l = 0; l < c.layers; ++l) {
-    o.R[l] = take(2LL * K1 * c.modes * c.width * c.width);
+    o.R[l] = take(2LL * spectral_modes(c) * c.width * c.width);
     o.W[l] = take((long long)c.width * c.width);
     o.b[l] = take(c.width);
   }
@@ -292,7 +327,8 @@ long long bases_floats(const NetConfig& c) {
 
 // Fr, Fi [K x N]: e^{-2 pi i kx x / N}; Gc, Gs [K1 x N]: cos, sin of 2 pi ky y / N (ky in
 // 0..K-1, -K..-1); Hc, Hs [N x K1]: cos, sin of 2 pi ky y / N; Er, Ei [N x K]: the
-// half-spectrum inverse along x with weights c_kx (1, then 2) and 1/N^2.
+// half-spectrum inverse along x with weights c_kx (1, then 2) and 1/N^d. The z axis of the
+// 3D network uses the y bases (cubic grid).
 void fill_bases(const NetConfig& c, float* h) {
   const int N = c.N, K = c.modes, K1 = 2 * c.modes;
   const double tp = 6.283185307179586476925286766559;
@@ -310,7 +346,7 @@ void fill_bases(const NetConfig& c, float* h) {
       const double a = tp * k * x / N;
       Fr[k * N + x] = (float)std::cos(a);
       Fi[k * N + x] = (float)-std::sin(a);
-      const double w = (k == 0 ? 1.0 : 2.0) / ((double)N * N);
+      const double w = (k == 0 ? 1.0 : 2.0) / (double)ipow(N, c.d == 3 ? 3 : 2);
       Er[x * K + k] = (float)(w * std::cos(a));
       Ei[x * K + k] = (float)(-w * std::sin(a));
     }
@@ -324,17 +360,22 @@ void fill_bases(const NetConfig& c, float* h) {
     }
 }
 
+// Activations: v, z [P x W] per layer (P = B N^d grid points); x1 / z1 after the x DFT
+// [B][(z)][y][kx][W]; mr / mi (3D) after the y DFT [B][z][ky][kx][W]; x2[l] the kept
+// spectrum of layer l [B][(kz)][ky][kx][W] (saved for the weight gradient), y the mixed one.
 struct NetWs {
-  float *v[9], *z[8], *x1r, *x1i, *x2r[8], *x2i[8], *yr, *yi, *z1r, *z1i, *pz, *ph;
-  float *dv, *dz, *dx1r, *dx1i, *dx2r, *dx2i, *dyr, *dyi, *dz1r, *dz1i, *dh, *colpart, *lpart, *split;
+  float *v[9], *z[8], *x1r, *x1i, *x2r[8], *x2i[8], *yr, *yi, *z1r, *z1i, *mr, *mi, *pz, *ph;
+  float *dv, *dz, *dx1r, *dx1i, *dx2r, *dx2i, *dyr, *dyi, *dz1r, *dz1i, *dmr, *dmi, *dh, *colpart, *lpart, *split;
   long long split_floats;
 };
 
 // Carves the workspace; returns the number of floats used (pointers set when ws != null).
 static long long carve_n(const NetConfig& c, int B, float* ws, NetWs& w) {
   w = NetWs{};
-  const long long P = (long long)B * c.N * c.N, W = c.width, K = c.modes, K1 = 2 * c.modes;
-  const long long x1 = (long long)B * c.N * K * W, x2 = (long long)B * K1 * K * W;
+  const int d = c.d == 3 ? 3 : 2;
+  const long long P = (long long)B * ipow(c.N, d), W = c.width, K = c.modes, K1 = 2 * c.modes;
+  const long long x1 = (long long)B * ipow(c.N, d - 1) * K * W, x2 = (long long)B * spectral_modes(c) * W;
+  const long long xm = d == 3 ? (long long)B * c.N * K1 * K * W : 0;
   long long off = 0;
   auto take = [&](long long n) {
     float* r = ws ? ws + off : nullptr;
@@ -346,10 +387,12 @@ static long long carve_n(const NetConfig& c, int B, float* ws, NetWs& w) {
   w.x1r = take(x1); w.x1i = take(x1);
   for (int l = 0; l < c.layers; ++l) { w.x2r[l] = take(x2); w.x2i[l] = take(x2); }
   w.yr = take(x2); w.yi = take(x2); w.z1r = take(x1); w.z1i = take(x1);
+  if (xm) { w.mr = take(xm); w.mi = take(xm); }
   w.pz = take(P * c.proj); w.ph = take(P * c.proj);
   w.dv = take(P * W); w.dz = take(P * W);
   w.dx1r = take(x1); w.dx1i = take(x1); w.dx2r = take(x2); w.dx2i = take(x2);
   w.dyr = take(x2); w.dyi = take(x2); w.dz1r = take(x1); w.dz1i = take(x1);
+  if (xm) { w.dmr = take(xm); w.dmi = take(xm); }
   w.dh = take(P * c.proj);
   w.colpart = take(1024LL * std::max<long long>(c.proj, W));
   w.lpart = take(4096);
@@ -405,6 +448,45 @@ static Bases bases_of(const NetConfig& c, const float* b) {
   return r;
 }
 
+// Complex DFT along one axis on the kept modes, as four real GEMMs per batch item, with
+// bases Gc, Gs [K1 x Nn] and Hc, Hs [Nn x K1]; C columns per row, batch strides in floats.
+//   forward  O = G I:  Or = Gc Ir + Gs Ii,  Oi = Gc Ii - Gs Ir   (e^{-2 pi i k y / N})
+//   inverse  O = H I:  Or = Hc Ir - Hs Ii,  Oi = Hc Ii + Hs Ir   (e^{+2 pi i k y / N})
+struct Axis {
+  const Bases& bs;
+  int Nn, K1;
+  cudaStream_t s;
+  cudaError_t fwd(const float* ir, const float* ii, float* orr, float* oi, int C, long long sI, long long sO,
+                  int batch) const {
+    NCK(gemm_bf16(gemm(bs.Gc, ir, orr, K1, C, Nn, Nn, C, C, 0, 0, 0, sI, sO, batch, 1.f, 0.f), s));
+    NCK(gemm_bf16(gemm(bs.Gs, ii, orr, K1, C, Nn, Nn, C, C, 0, 0, 0, sI, sO, batch, 1.f, 1.f), s));
+    NCK(gemm_bf16(gemm(bs.Gc, ii, oi, K1, C, Nn, Nn, C, C, 0, 0, 0, sI, sO, batch, 1.f, 0.f), s));
+    return gemm_bf16(gemm(bs.Gs, ir, oi, K1, C, Nn, Nn, C, C, 0, 0, 0, sI, sO, batch, -1.f, 1.f), s);
+  }
+  cudaError_t inv(const float* ir, const float* ii, float* orr, float* oi, int C, long long sI, long long sO,
+                  int batch) const {
+    NCK(gemm_bf16(gemm(bs.Hc, ir, orr, Nn, C, K1, K1, C, C, 0, 0, 0, sI, sO, batch, 1.f, 0.f), s));
+    NCK(gemm_bf16(gemm(bs.Hs, ii, orr, Nn, C, K1, K1, C, C, 0, 0, 0, sI, sO, batch, -1.f, 1.f), s));
+    NCK(gemm_bf16(gemm(bs.Hc, ii, oi, Nn, C, K1, K1, C, C, 0, 0, 0, sI, sO, batch, 1.f, 0.f), s));
+    return gemm_bf16(gemm(bs.Hs, ir, oi, Nn, C, K1, K1, C, C, 0, 0, 0, sI, sO, batch, 1.f, 1.f), s);
+  }
+  // adjoints: dI = G^T dO (of fwd), dI = H^T dO (of inv); dO has stride sO, dI stride sI
+  cudaError_t fwd_adj(const float* dor, const float* doi, float* dir, float* dii, int C, long long sO,
+                      long long sI, int batch) const {
+    NCK(gemm_bf16(gemm(bs.Gc, dor, dir, Nn, C, K1, Nn, C, C, 1, 0, 0, sO, sI, batch, 1.f, 0.f), s));
+    NCK(gemm_bf16(gemm(bs.Gs, doi, dir, Nn, C, K1, Nn, C, C, 1, 0, 0, sO, sI, batch, -1.f, 1.f), s));
+    NCK(gemm_bf16(gemm(bs.Gs, dor, dii, Nn, C, K1, Nn, C, C, 1, 0, 0, sO, sI, batch, 1.f, 0.f), s));
+    return gemm_bf16(gemm(bs.Gc, doi, dii, Nn, C, K1, Nn, C, C, 1, 0, 0, sO, sI, batch, 1.f, 1.f), s);
+  }
+  cudaError_t inv_adj(const float* dor, const float* doi, float* dir, float* dii, int C, long long sO,
+                      long long sI, int batch) const {
+    NCK(gemm_bf16(gemm(bs.Hc, dor, dir, K1, C, Nn, K1, C, C, 1, 0, 0, sO, sI, batch, 1.f, 0.f), s));
+    NCK(gemm_bf16(gemm(bs.Hs, doi, dir, K1, C, Nn, K1, C, C, 1, 0, 0, sO, sI, batch, 1.f, 1.f), s));
+    NCK(gemm_bf16(gemm(bs.Hc, doi, dii, K1, C, Nn, K1, C, C, 1, 0, 0, sO, sI, batch, 1.f, 0.f), s));
+    return gemm_bf16(gemm(bs.Hs, dor, dii, K1, C, Nn, K1, C, C, 1, 0, 0, sO, sI, batch, -1.f, 1.f), s);
+  }
+};
+
 cudaError_t net_forward(const NetConfig& c, const float* prm, const float* bases, int B, const float* in, float* out,
                         float* ws, int train, cudaStream_t s) {
   (void)train;
@@ -413,38 +495,45 @@ cudaError_t net_forward(const NetConfig& c, const float* prm, const float* bases
   g_split_ws = w.split;
   g_split_floats = w.split_floats;
   const Bases bs = bases_of(c, bases);
+  const Axis ax{bs, c.N, 2 * c.modes, s};
+  const int d = c.d == 3 ? 3 : 2;
   const int N = c.N, W = c.width, K = c.modes, K1 = 2 * c.modes, KW = K * W;
-  const long long P = (long long)B * N * N;
-  const int BN = B * N;
+  const long long P = (long long)B * ipow(N, d);
+  const int BN = (int)(B * ipow(N, d - 1));   // rows of x transforms: (b, (z,) y)
+  const long long nmodes = spectral_modes(c);
   // lift
   NCK(gemm_bf16(gemm(in, prm + o.lift_w, w.v[0], (int)P, W, c.cin, c.cin, W, W, 0, 0, 0, 0, 0, 1, 1.f, 0.f), s));
   k_bias_act<<<eblocks(P * W), 256, 0, s>>>(w.v[0], prm + o.lift_b, w.v[0], P, W, 0);
   for (int l = 0; l < c.layers; ++l) {
     const float* v = w.v[l];
     const float* Rr = prm + o.R[l];
-    const float* Ri = Rr + (long long)K1 * K * W * W;
-    // (1) x DFT, per (b, y): [K x N] x [N x W]
+    const float* Ri = Rr + nmodes * W * W;
+    // (1) x DFT, per (b, (z,) y): [K x N] x [N x W]
     NCK(gemm_bf16(gemm(bs.Fr, v, w.x1r, K, W, N, N, W, W, 0, 0, 0, (long long)N * W, (long long)K * W, BN, 1.f, 0.f), s));
     NCK(gemm_bf16(gemm(bs.Fi, v, w.x1i, K, W, N, N, W, W, 0, 0, 0, (long long)N * W, (long long)K * W, BN, 1.f, 0.f), s));
-    // (2) y DFT, per b: X2r = Gc X1r + Gs X1i, X2i = Gc X1i - Gs X1r   ([K1 x N] x [N x KW])
+    // (2) y DFT per (b, (z)): [K1 x N] x [N x KW]; (2z) z DFT per b: [K1 x N] x [N x K1 KW]
     const long long sx1 = (long long)N * KW, sx2 = (long long)K1 * KW;
-    NCK(gemm_bf16(gemm(bs.Gc, w.x1r, w.x2r[l], K1, KW, N, N, KW, KW, 0, 0, 0, sx1, sx2, B, 1.f, 0.f), s));
-    NCK(gemm_bf16(gemm(bs.Gs, w.x1i, w.x2r[l], K1, KW, N, N, KW, KW, 0, 0, 0, sx1, sx2, B, 1.f, 1.f), s));
-    NCK(gemm_bf16(gemm(bs.Gc, w.x1i, w.x2i[l], K1, KW, N, N, KW, KW, 0, 0, 0, sx1, sx2, B, 1.f, 0.f), s));
-    NCK(gemm_bf16(gemm(bs.Gs, w.x1r, w.x2i[l], K1, KW, N, N, KW, KW, 0, 0, 0, sx1, sx2, B, -1.f, 1.f), s));
-    // (3) per mode m: Y = X2 R (complex), rows b (stride K1*K*W), batch over modes
-    const int nm = K1 * K;
+    if (d == 2) {
+      NCK(ax.fwd(w.x1r, w.x1i, w.x2r[l], w.x2i[l], KW, sx1, sx2, B));
+    } else {
+      NCK(ax.fwd(w.x1r, w.x1i, w.mr, w.mi, KW, sx1, sx2, B * N));
+      NCK(ax.fwd(w.mr, w.mi, w.x2r[l], w.x2i[l], K1 * KW, (long long)N * K1 * KW, (long long)K1 * K1 * KW, B));
+    }
+    // (3) per mode m: Y = X2 R (complex), rows b (stride nmodes*W), batch over modes
+    const int nm = (int)nmodes;
     const int ldm = nm * W;
     NCK(gemm_bf16(gemm(w.x2r[l], Rr, w.yr, B, W, W, ldm, W, ldm, 0, 0, W, (long long)W * W, W, nm, 1.f, 0.f), s));
     NCK(gemm_bf16(gemm(w.x2i[l], Ri, w.yr, B, W, W, ldm, W, ldm, 0, 0, W, (long long)W * W, W, nm, -1.f, 1.f), s));
     NCK(gemm_bf16(gemm(w.x2r[l], Ri, w.yi, B, W, W, ldm, W, ldm, 0, 0, W, (long long)W * W, W, nm, 1.f, 0.f), s));
     NCK(gemm_bf16(gemm(w.x2i[l], Rr, w.yi, B, W, W, ldm, W, ldm, 0, 0, W, (long long)W * W, W, nm, 1.f, 1.f), s));
-    // (4) inverse y, per b: Z1r = Hc Yr - Hs Yi, Z1i = Hc Yi + Hs Yr   ([N x K1] x [K1 x KW])
-    NCK(gemm_bf16(gemm(bs.Hc, w.yr, w.z1r, N, KW, K1, K1, KW, KW, 0, 0, 0, sx2, sx1, B, 1.f, 0.f), s));
-    NCK(gemm_bf16(gemm(bs.Hs, w.yi, w.z1r, N, KW, K1, K1, KW, KW, 0, 0, 0, sx2, sx1, B, -1.f, 1.f), s));
-    NCK(gemm_bf16(gemm(bs.Hc, w.yi, w.z1i, N, KW, K1, K1, KW, KW, 0, 0, 0, sx2, sx1, B, 1.f, 0.f), s));
-    NCK(gemm_bf16(gemm(bs.Hs, w.yr, w.z1i, N, KW, K1, K1, KW, KW, 0, 0, 0, sx2, sx1, B, 1.f, 1.f), s));
-    // (5) inverse x (half spectrum), per (b, y): s = Er Z1r + Ei Z1i   ([N x K] x [K x W]) into z
+    // (4) inverse (z then) y
+    if (d == 2) {
+      NCK(ax.inv(w.yr, w.yi, w.z1r, w.z1i, KW, sx2, sx1, B));
+    } else {
+      NCK(ax.inv(w.yr, w.yi, w.mr, w.mi, K1 * KW, (long long)K1 * K1 * KW, (long long)N * K1 * KW, B));
+      NCK(ax.inv(w.mr, w.mi, w.z1r, w.z1i, KW, sx2, sx1, B * N));
+    }
+    // (5) inverse x (half spectrum), per (b, (z,) y): s = Er Z1r + Ei Z1i   ([N x K] x [K x W]) into z
     NCK(gemm_bf16(gemm(bs.Er, w.z1r, w.z[l], N, W, K, K, W, W, 0, 0, 0, (long long)K * W, (long long)N * W, BN, 1.f, 0.f), s));
     NCK(gemm_bf16(gemm(bs.Ei, w.z1i, w.z[l], N, W, K, K, W, W, 0, 0, 0, (long long)K * W, (long long)N * W, BN, 1.f, 1.f), s));
     // (6) z += v W ; (7) bias + activation
@@ -455,8 +544,6 @@ cudaError_t net_forward(const NetConfig& c, const float* prm, const float* bases
   NCK(gemm_bf16(gemm(w.v[c.layers], prm + o.p1_w, w.pz, (int)P, c.proj, W, W, c.proj, c.proj, 0, 0, 0, 0, 0, 1, 1.f, 0.f), s));
   k_bias_act<<<eblocks(P * c.proj), 256, 0, s>>>(w.pz, prm + o.p1_b, w.ph, P, c.proj, 1);
   NCK(gemm_bf16(gemm(w.ph, prm + o.p2_w, out, (int)P, c.cout, c.proj, c.proj, c.cout, c.cout, 0, 0, 0, 0, 0, 1, 1.f, 0.f), s));
-  float* zero_z = nullptr;
-  (void)zero_z;
   k_bias_act<<<eblocks(P * c.cout), 256, 0, s>>>(out, prm + o.p2_b, out, P, c.cout, 0);
   g_split_ws = nullptr;
   g_split_floats = 0;
@@ -468,9 +555,12 @@ cudaError_t net_backward(const NetConfig& c, const float* prm, const float* base
   const NetOffsets o = net_offsets(c);
   NetWs w = carve(c, B, ws);
   const Bases bs = bases_of(c, bases);
+  const Axis ax{bs, c.N, 2 * c.modes, s};
+  const int d = c.d == 3 ? 3 : 2;
   const int N = c.N, W = c.width, K = c.modes, K1 = 2 * c.modes, KW = K * W;
-  const long long P = (long long)B * N * N;
-  const int BN = B * N;
+  const long long P = (long long)B * ipow(N, d);
+  const int BN = (int)(B * ipow(N, d - 1));
+  const long long nmodes = spectral_modes(c);
   // forward with the activations kept; output into dh's tail (reuse of pz for out is not possible)
   float* out = w.dh;   // [P x cout] fits in [P x proj]
   NCK(net_forward(c, prm, bases, B, in, out, ws, 1, s));
@@ -495,25 +585,27 @@ cudaError_t net_backward(const NetConfig& c, const float* prm, const float* base
   for (int l = c.layers - 1; l >= 0; --l) {
     const float* v = w.v[l];
     const float* Rr = prm + o.R[l];
-    const float* Ri = Rr + (long long)K1 * K * W * W;
+    const float* Ri = Rr + nmodes * W * W;
     float* dRr = grad + o.R[l];
-    float* dRi = dRr + (long long)K1 * K * W * W;
+    float* dRi = dRr + nmodes * W * W;
     if (l + 1 < c.layers) k_gelu_back<<<eblocks(P * W), 256, 0, s>>>(w.dv, w.z[l], w.dz, P * W);
     else NCK(cudaMemcpyAsync(w.dz, w.dv, P * W * sizeof(float), cudaMemcpyDeviceToDevice, s));
     NCK(colsum(w.dz, P, W, grad + o.b[l], w.colpart, s));
     NCK(gemm_bf16(gemm(v, w.dz, grad + o.W[l], W, W, (int)P, W, W, W, 1, 0, 0, 0, 0, 1, 1.f, 0.f), s));
     NCK(gemm_bf16(gemm(w.dz, prm + o.W[l], w.dv, (int)P, W, W, W, W, W, 0, 1, 0, 0, 0, 1, 1.f, 0.f), s));
-    // (5') dZ1 = E^T dz, per (b, y): [K x N] x [N x W]
+    // (5') dZ1 = E^T dz, per (b, (z,) y): [K x N] x [N x W]
     NCK(gemm_bf16(gemm(bs.Er, w.dz, w.dz1r, K, W, N, K, W, W, 1, 0, 0, (long long)N * W, (long long)K * W, BN, 1.f, 0.f), s));
     NCK(gemm_bf16(gemm(bs.Ei, w.dz, w.dz1i, K, W, N, K, W, W, 1, 0, 0, (long long)N * W, (long long)K * W, BN, 1.f, 0.f), s));
-    // (4') dYr = Hc^T dZ1r + Hs^T dZ1i ; dYi = Hc^T dZ1i - Hs^T dZ1r   ([K1 x N] x [N x KW])
+    // (4') adjoint of the inverse y (and then z) transform: dY = H^T dZ1
     const long long sx1 = (long long)N * KW, sx2 = (long long)K1 * KW;
-    NCK(gemm_bf16(gemm(bs.Hc, w.dz1r, w.dyr, K1, KW, N, K1, KW, KW, 1, 0, 0, sx1, sx2, B, 1.f, 0.f), s));
-    NCK(gemm_bf16(gemm(bs.Hs, w.dz1i, w.dyr, K1, KW, N, K1, KW, KW, 1, 0, 0, sx1, sx2, B, 1.f, 1.f), s));
-    NCK(gemm_bf16(gemm(bs.Hc, w.dz1i, w.dyi, K1, KW, N, K1, KW, KW, 1, 0, 0, sx1, sx2, B, 1.f, 0.f), s));
-    NCK(gemm_bf16(gemm(bs.Hs, w.dz1r, w.dyi, K1, KW, N, K1, KW, KW, 1, 0, 0, sx1, sx2, B, -1.f, 1.f), s));
+    if (d == 2) {
+      NCK(ax.inv_adj(w.dz1r, w.dz1i, w.dyr, w.dyi, KW, sx1, sx2, B));
+    } else {
+      NCK(ax.inv_adj(w.dz1r, w.dz1i, w.dmr, w.dmi, KW, sx1, sx2, B * N));
+      NCK(ax.inv_adj(w.dmr, w.dmi, w.dyr, w.dyi, K1 * KW, (long long)N * K1 * KW, (long long)K1 * K1 * KW, B));
+    }
     // (3') per mode: dRr = X2r^T dYr + X2i^T dYi ; dRi = X2r^T dYi - X2i^T dYr   ([W x B] x [B x W])
-    const int nm = K1 * K;
+    const int nm = (int)nmodes;
     const int ldm = nm * W;
     const long long WW = (long long)W * W;
     NCK(gemm_bf16(gemm(w.x2r[l], w.dyr, dRr, W, W, B, ldm, ldm, W, 1, 0, W, W, WW, nm, 1.f, 0.f), s));
@@ -525,12 +617,14 @@ cudaError_t net_backward(const NetConfig& c, const float* prm, const float* base
     NCK(gemm_bf16(gemm(w.dyi, Ri, w.dx2r, B, W, W, ldm, W, ldm, 0, 1, W, WW, W, nm, 1.f, 1.f), s));
     NCK(gemm_bf16(gemm(w.dyi, Rr, w.dx2i, B, W, W, ldm, W, ldm, 0, 1, W, WW, W, nm, 1.f, 0.f), s));
     NCK(gemm_bf16(gemm(w.dyr, Ri, w.dx2i, B, W, W, ldm, W, ldm, 0, 1, W, WW, W, nm, -1.f, 1.f), s));
-    // (2') dX1r = Gc^T dX2r - Gs^T dX2i ; dX1i = Gs^T dX2r + Gc^T dX2i   ([N x K1] x [K1 x KW])
-    NCK(gemm_bf16(gemm(bs.Gc, w.dx2r, w.dx1r, N, KW, K1, N, KW, KW, 1, 0, 0, sx2, sx1, B, 1.f, 0.f), s));
-    NCK(gemm_bf16(gemm(bs.Gs, w.dx2i, w.dx1r, N, KW, K1, N, KW, KW, 1, 0, 0, sx2, sx1, B, -1.f, 1.f), s));
-    NCK(gemm_bf16(gemm(bs.Gs, w.dx2r, w.dx1i, N, KW, K1, N, KW, KW, 1, 0, 0, sx2, sx1, B, 1.f, 0.f), s));
-    NCK(gemm_bf16(gemm(bs.Gc, w.dx2i, w.dx1i, N, KW, K1, N, KW, KW, 1, 0, 0, sx2, sx1, B, 1.f, 1.f), s));
-    // (1') dv += Fr^T dX1r + Fi^T dX1i, per (b, y): [N x K] x [K x W]
+    // (2') adjoint of the forward (z then) y transform: dX1 = G^T dX2
+    if (d == 2) {
+      NCK(ax.fwd_adj(w.dx2r, w.dx2i, w.dx1r, w.dx1i, KW, sx2, sx1, B));
+    } else {
+      NCK(ax.fwd_adj(w.dx2r, w.dx2i, w.dmr, w.dmi, K1 * KW, (long long)K1 * K1 * KW, (long long)N * K1 * KW, B));
+      NCK(ax.fwd_adj(w.dmr, w.dmi, w.dx1r, w.dx1i, KW, sx2, sx1, B * N));
+    }
+    // (1') dv += Fr^T dX1r + Fi^T dX1i, per (b, (z,) y): [N x K] x [K x W]
     NCK(gemm_bf16(gemm(bs.Fr, w.dx1r, w.dv, N, W, K, N, W, W, 1, 0, 0, (long long)K * W, (long long)N * W, BN, 1.f, 1.f), s));
     NCK(gemm_bf16(gemm(bs.Fi, w.dx1i, w.dv, N, W, K, N, W, W, 1, 0, 0, (long long)K * W, (long long)N * W, BN, 1.f, 1.f), s));
   }
@@ -555,13 +649,12 @@ cudaError_t init_params(const NetConfig& c, float* prm, unsigned long long seed,
     k_init<<<eblocks(n), 256, 0, s>>>(prm + off, n, -a, a, seed * 1315423911ULL + sd);
   };
   auto zero = [&](long long off, long long n) { k_fill<<<eblocks(n), 256, 0, s>>>(prm + off, n, 0.f); };
-  const int K1 = 2 * c.modes;
   uni(o.lift_w, (long long)c.cin * c.width, 1.f / sqrtf((float)c.cin), 1);
   zero(o.lift_b, c.width);
   for (int l = 0; l < c.layers; ++l) {
     const float sc = 1.f / (float)(c.width * c.width);
-    k_init<<<eblocks(2LL * K1 * c.modes * c.width * c.width), 256, 0, s>>>(
-        prm + o.R[l], 2LL * K1 * c.modes * c.width * c.width, 0.f, sc, seed * 2654435761ULL + 100 + l);
+    const long long nR = 2LL * spectral_modes(c) * c.width * c.width;
+    k_init<<<eblocks(nR), 256, 0, s>>>(prm + o.R[l], nR, 0.f, sc, seed * 2654435761ULL + 100 + l);
     uni(o.W[l], (long long)c.width * c.width, 1.f / sqrtf((float)c.width), 200 + l);
     zero(o.b[l], c.width);
   }
@@ -575,14 +668,18 @@ cudaError_t init_params(const NetConfig& c, float* prm, unsigned long long seed,
 // ---------------------------------------------------------------------------------
 // real N-grid fields <-> half spectra (direct DFT, one CTA per (sample, channel))
 // ---------------------------------------------------------------------------------
-__global__ void k_grid_to_half(int N, int ch, const float* grid, void* half, int fp64) {
+// One CTA per (slab, channel): the 2D DFT of an N x N slab by direct sums (rows, then
+// columns in FFT order). Slab s = b * Nz + z of grid [B][(Nz)][N][N][ch]; output at
+// [b][ch][z][ky][kx] of the half spectrum, times `scale`.
+__global__ void k_grid_to_half(int N, int ch, int Nz, const float* grid, void* half, int fp64, double scale) {
   extern __shared__ __align__(16) unsigned char sm[];
   float* u = reinterpret_cast<float*>(sm);                 // N*N
   float2* tw = reinterpret_cast<float2*>(u + N * N + (N * N & 1));   // N
   float2* R = tw + N;                                      // N * Nh
   const int Nh = (N + 1) / 2;
-  const int b = blockIdx.x / ch, c = blockIdx.x - (blockIdx.x / ch) * ch;
-  for (int i = threadIdx.x; i < N * N; i += blockDim.x) u[i] = grid[((long long)b * N * N + i) * ch + c];
+  const int sl = blockIdx.x / ch, c = blockIdx.x - (blockIdx.x / ch) * ch;
+  const int b = sl / Nz, z = sl - (sl / Nz) * Nz;
+  for (int i = threadIdx.x; i < N * N; i += blockDim.x) u[i] = grid[((long long)sl * N * N + i) * ch + c];
   for (int i = threadIdx.x; i < N; i += blockDim.x) {
     float sn, cs;
     sincospif(2.f * i / N, &sn, &cs);
@@ -603,7 +700,6 @@ __global__ void k_grid_to_half(int N, int ch, const float* grid, void* half, int
     R[t] = make_float2(re, im);
   }
   __syncthreads();
-  const double inv = 1.0 / ((double)N * N);
   for (int t = threadIdx.x; t < N * Nh; t += blockDim.x) {   // columns, FFT order ky
     const int i = t / Nh, kx = t - i * Nh;
     float re = 0.f, im = 0.f;
@@ -616,21 +712,24 @@ __global__ void k_grid_to_half(int N, int ch, const float* grid, void* half, int
       idx += i;
       if (idx >= N) idx -= N;
     }
-    const long long o = ((long long)(b * ch + c) * N + i) * Nh + kx;
-    if (fp64) reinterpret_cast<double2*>(half)[o] = make_double2(re * inv, im * inv);
-    else reinterpret_cast<float2*>(half)[o] = make_float2((float)(re * inv), (float)(im * inv));
+    const long long o = (((long long)(b * ch + c) * Nz + z) * N + i) * Nh + kx;
+    if (fp64) reinterpret_cast<double2*>(half)[o] = make_double2(re * scale, im * scale);
+    else reinterpret_cast<float2*>(half)[o] = make_float2((float)(re * scale), (float)(im * scale));
   }
 }
 
-__global__ void k_half_to_grid(int N, int ch, const void* half, float* grid, int fp64) {
+// One CTA per (slab, channel): the real N x N slab of a half spectrum [b][ch][z][ky][kx]
+// (columns inverse, then the Hermitian-weighted real inverse along x), no scaling.
+__global__ void k_half_to_grid(int N, int ch, int Nz, const void* half, float* grid, int fp64) {
   extern __shared__ __align__(16) unsigned char sm[];
   float2* H = reinterpret_cast<float2*>(sm);   // N * Nh
   const int Nh = (N + 1) / 2;
   float2* S = H + N * Nh;                       // N * Nh
   float2* tw = S + N * Nh;                      // N
-  const int b = blockIdx.x / ch, c = blockIdx.x - (blockIdx.x / ch) * ch;
+  const int sl = blockIdx.x / ch, c = blockIdx.x - (blockIdx.x / ch) * ch;
+  const int b = sl / Nz, z = sl - (sl / Nz) * Nz;
   for (int i = threadIdx.x; i < N * Nh; i += blockDim.x) {
-    const long long o = (long long)(b * ch + c) * N * Nh + i;
+    const long long o = ((long long)(b * ch + c) * Nz + z) * N * Nh + i;
     if (fp64) {
       const double2 v = reinterpret_cast<const double2*>(half)[o];
       H[i] = make_float2((float)v.x, (float)v.y);
@@ -670,23 +769,112 @@ __global__ void k_half_to_grid(int N, int ch, const void* half, float* grid, int
       idx += x;
       if (idx >= N) idx -= N;
     }
-    grid[((long long)b * N * N + t) * ch + c] = acc;
+    grid[((long long)sl * N * N + t) * ch + c] = acc;
   }
 }
 
-cudaError_t grid_to_half(int N, int B, int ch, const float* grid, void* half, int fp64, cudaStream_t s) {
+// DFT along z of columns of [bc][z][ky][kx] (N x N x Nh per bc): one CTA per (bc, ky,
+// block of kZB kx); the N x kZB block is staged in shared memory, so in == out is allowed.
+// sign -1: forward e^{-2 pi i kz z / N}; +1: inverse. Sums in FP32.
+constexpr int kZB = 32;
+__global__ void k_zdft(int N, const void* in, int fp64_in, void* out, int fp64_out, int sign) {
+  extern __shared__ __align__(16) unsigned char sm[];
+  float2* col = reinterpret_cast<float2*>(sm);   // N * kZB
+  float2* tw = col + N * kZB;                      // N
   const int Nh = (N + 1) / 2;
-  const size_t smem = (size_t)N * N * 4 + 8 + (size_t)N * 8 + (size_t)N * Nh * 8;
-  if (smem > 48 * 1024) cudaFuncSetAttribute(k_grid_to_half, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  k_grid_to_half<<<B * ch, 256, smem, s>>>(N, ch, grid, half, fp64);
+  const int nkb = (Nh + kZB - 1) / kZB;
+  const int kb = blockIdx.x % nkb;
+  const int ky = (blockIdx.x / nkb) % N;
+  const long long bc = blockIdx.x / ((long long)nkb * N);
+  const int kx0 = kb * kZB, nk = min(kZB, Nh - kx0);
+  const long long base = bc * N * N * Nh + (long long)ky * Nh + kx0;   // + z * N * Nh + j
+  for (int t = threadIdx.x; t < N * kZB; t += blockDim.x) {
+    const int z = t / kZB, j = t - z * kZB;
+    float2 v = make_float2(0.f, 0.f);
+    if (j < nk) {
+      const long long o = base + (long long)z * N * Nh + j;
+      if (fp64_in) {
+        const double2 dv = reinterpret_cast<const double2*>(in)[o];
+        v = make_float2((float)dv.x, (float)dv.y);
+      } else {
+        v = reinterpret_cast<const float2*>(in)[o];
+      }
+    }
+    col[t] = v;
+  }
+  for (int i = threadIdx.x; i < N; i += blockDim.x) {
+    float sn, cs;
+    sincospif(2.f * i / N, &sn, &cs);
+    tw[i] = make_float2(cs, (float)sign * sn);
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < N * kZB; t += blockDim.x) {
+    const int kz = t / kZB, j = t - kz * kZB;
+    if (j >= nk) continue;
+    float re = 0.f, im = 0.f;
+    int idx = 0;
+    for (int z = 0; z < N; ++z) {
+      const float2 w = tw[idx];
+      const float2 v = col[z * kZB + j];
+      re += v.x * w.x - v.y * w.y;
+      im += v.x * w.y + v.y * w.x;
+      idx += kz;
+      if (idx >= N) idx -= N;
+    }
+    const long long o = base + (long long)kz * N * Nh + j;
+    if (fp64_out) reinterpret_cast<double2*>(out)[o] = make_double2(re, im);
+    else reinterpret_cast<float2*>(out)[o] = make_float2(re, im);
+  }
+}
+
+static size_t g2h_smem(int N) {
+  const int Nh = (N + 1) / 2;
+  return (size_t)N * N * 4 + 8 + (size_t)N * 8 + (size_t)N * Nh * 8;
+}
+static size_t h2g_smem(int N) {
+  const int Nh = (N + 1) / 2;
+  return 2 * (size_t)N * Nh * 8 + (size_t)N * 8;
+}
+static size_t zdft_smem(int N) { return (size_t)N * kZB * 8 + (size_t)N * 8; }
+constexpr size_t kMaxSmem = 227 * 1024;
+
+static cudaError_t launch_zdft(int N, long long nbc, const void* in, int fp64_in, void* out, int fp64_out, int sign,
+                               cudaStream_t s) {
+  const size_t smem = zdft_smem(N);
+  if (smem > 48 * 1024) cudaFuncSetAttribute(k_zdft, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  const int Nh = (N + 1) / 2;
+  const long long blocks = nbc * N * ((Nh + kZB - 1) / kZB);
+  if (blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
+  k_zdft<<<(unsigned)blocks, 256, smem, s>>>(N, in, fp64_in, out, fp64_out, sign);
   return cudaGetLastError();
 }
 
-cudaError_t half_to_grid(int N, int B, int ch, const void* half, float* grid, int fp64, cudaStream_t s) {
-  const int Nh = (N + 1) / 2;
-  const size_t smem = 2 * (size_t)N * Nh * 8 + (size_t)N * 8;
+cudaError_t grid_to_half(int d, int N, int B, int ch, const float* grid, void* half, int fp64, cudaStream_t s) {
+  const size_t smem = g2h_smem(N);
+  if (smem > kMaxSmem || zdft_smem(N) > kMaxSmem) return cudaErrorInvalidValue;
+  if (smem > 48 * 1024) cudaFuncSetAttribute(k_grid_to_half, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  const int Nz = d == 3 ? N : 1;
+  const double scale = 1.0 / ((double)ipow(N, d == 3 ? 3 : 2));
+  k_grid_to_half<<<B * Nz * ch, 256, smem, s>>>(N, ch, Nz, grid, half, fp64, scale);
+  NCK(cudaGetLastError());
+  if (d == 3) return launch_zdft(N, (long long)B * ch, half, fp64, half, fp64, -1, s);
+  return cudaSuccess;
+}
+
+size_t half3d_tmp_bytes(int N, int B, int ch) { return (size_t)B * ch * N * N * ((N + 1) / 2) * 8; }
+
+cudaError_t half_to_grid(int d, int N, int B, int ch, const void* half, float* grid, int fp64, void* tmp,
+                         cudaStream_t s) {
+  const size_t smem = h2g_smem(N);
+  if (smem > kMaxSmem || zdft_smem(N) > kMaxSmem) return cudaErrorInvalidValue;
   if (smem > 48 * 1024) cudaFuncSetAttribute(k_half_to_grid, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  k_half_to_grid<<<B * ch, 256, smem, s>>>(N, ch, half, grid, fp64);
+  if (d == 3) {
+    if (!tmp) return cudaErrorInvalidValue;
+    NCK(launch_zdft(N, (long long)B * ch, half, fp64, tmp, 0, +1, s));
+    k_half_to_grid<<<B * N * ch, 256, smem, s>>>(N, ch, N, tmp, grid, 0);
+  } else {
+    k_half_to_grid<<<B * ch, 256, smem, s>>>(N, ch, 1, half, grid, fp64);
+  }
   return cudaGetLastError();
 }
 

@@ -1,4 +1,4 @@
-// Learned CG warm start: a 2D Fourier-layer network on the N-grid of one cell.
+// Learned CG warm start: a 2D or 3D Fourier-layer network on the N-grid of one cell.
 // Declarations shared by net.cu (kernels, orchestration) and api.cu (C ABI).
 #pragma once
 #include <cuda_runtime.h>
@@ -14,12 +14,13 @@ struct NetConfig {
   int layers;  // Fourier layers L
   int proj;    // projection hidden channels P
   int cout;    // output channels
+  int d;       // dimension: 2 (kx in [0, K), ky in [-K, K)) or 3 (also kz in [-K, K))
 };
 
 // offsets (floats) of the parameter tensors in the flat parameter array
 struct NetOffsets {
   long long lift_w, lift_b;
-  long long R[8], W[8], b[8];   // per layer: spectral weights (re then im), 1x1 weight, bias
+  long long R[8], W[8], b[8];   // per layer: spectral weights [re/im][kz][ky][kx][W][W], 1x1 weight, bias
   long long p1_w, p1_b, p2_w, p2_b;
   long long total;
 };
@@ -43,7 +44,7 @@ struct GemmArgs {
 };
 cudaError_t gemm_bf16(const GemmArgs& g, cudaStream_t s);
 
-// forward (keeps activations in ws for a backward when train != 0); out [B*N*N, cout]
+// forward (keeps activations in ws for a backward when train != 0); out [B*N^d, cout]
 cudaError_t net_forward(const NetConfig& c, const float* params, const float* bases, int B, const float* in,
                         float* out, float* ws, int train, cudaStream_t s);
 // loss = mean (out - target)^2 ; gradient of the parameters into grad (overwritten)
@@ -56,9 +57,12 @@ long long bases_floats(const NetConfig& c);
 void fill_bases(const NetConfig& c, float* host);
 cudaError_t init_params(const NetConfig& c, float* params, unsigned long long seed, cudaStream_t s);
 
-// real N-grid fields [B][N][N][ch] <-> half spectra [B][ch][N][Nh] (complex FP64/FP32), forward
-// with the 1/N^2 factor of Eq. DFT
-cudaError_t grid_to_half(int N, int B, int ch, const float* grid, void* half, int fp64, cudaStream_t s);
-cudaError_t half_to_grid(int N, int B, int ch, const void* half, float* grid, int fp64, cudaStream_t s);
+// real N-grid fields [B][(N)][N][N][ch] <-> half spectra [B][ch][(N)][N][Nh] (complex FP64/FP32),
+// forward with the 1/N^d factor of Eq. DFT. In 3D the forward runs in place along z; the
+// inverse needs `tmp` of half3d_tmp_bytes (unused in 2D).
+cudaError_t grid_to_half(int d, int N, int B, int ch, const float* grid, void* half, int fp64, cudaStream_t s);
+size_t half3d_tmp_bytes(int N, int B, int ch);
+cudaError_t half_to_grid(int d, int N, int B, int ch, const void* half, float* grid, int fp64, void* tmp,
+                         cudaStream_t s);
 
 }  // namespace homb

@@ -1,14 +1,16 @@
 """Learned CG warm start: data from the method, training and evaluation (driver).
 
-The heavy lifting is in the library: the batched solver produces the training fields
-(the converged primal and dual correctors of each cell), hom_net_features samples the
-cells on their N grid, hom_net_train_step runs forward, backward and Adam on the tensor
-cores, hom_net_forward predicts, hom_grid_to_half turns the prediction into half spectra
-and the batched solver starts CG from them after projecting with Gamma. Torch only holds
-device buffers and picks minibatch indices.
+The heavy lifting is in the library: the solver produces the training fields (the
+converged primal and dual correctors of each cell; the batched solver in 2D, hom_bounds_io
+per cell in 3D), hom_net_features samples the cells on their N grid, hom_net_train_step
+runs forward, backward and Adam on the tensor cores, hom_net_forward predicts,
+hom_grid_to_half turns the prediction into half spectra and the solver starts CG from them
+after projecting with Gamma and scaling by Rayleigh-Ritz. Torch only holds device buffers
+and picks minibatch indices.
 
-Channels of a field block (8): index side*4 + rhs*2 + component, for side 0 (primal
-corrector e^(rhs)) and 1 (dual corrector j^(rhs)), matching the solver's field pools.
+Channels of a field block (2 d^2): index (side * d + rhs) * d + component, for side 0
+(primal corrector e^(rhs)) and 1 (dual corrector j^(rhs)), matching the solver's field
+layout [side][rhs][comp][(z)][y][kx].
 """
 from __future__ import annotations
 
@@ -27,14 +29,18 @@ def torch_cat(parts):
 
 
 class WarmStart:
-    def __init__(self, solver, N, width=32, modes=12, layers=4, proj=128, batch=32, seed=0, energy=False):
+    def __init__(self, solver, N, width=32, modes=12, layers=4, proj=128, batch=32, seed=0, energy=False, d=2):
         import torch
         self.torch = torch
         self.solver = solver
         self.ctx = solver.ctx
         self.N = N
+        self.d = d
+        self.ch = 2 * d * d
+        self.grid = (N,) * d
         self.batch = batch
-        self.cfg = bd.net_config(N, 1, width, modes, layers, proj, 8)
+        self.arch = dict(width=width, modes=modes, layers=layers, proj=proj)
+        self.cfg = bd.net_config(N, 1, width, modes, layers, proj, self.ch, d)
         self.n_params, self.ws_bytes = bd.hom_net_sizes(self.ctx, self.cfg, batch)
         dev = f"cuda:{solver.device}"
         self.dev = dev
@@ -51,7 +57,7 @@ class WarmStart:
     def features(self, problems):
         """log10 of the phase value on the grid, divided by 3 (phase values span 1e-2..1e3)."""
         torch = self.torch
-        out = torch.empty((len(problems), self.N, self.N, 1), dtype=torch.float32, device=self.dev)
+        out = torch.empty((len(problems),) + self.grid + (1,), dtype=torch.float32, device=self.dev)
         ws = torch.empty(1 << 22, dtype=torch.uint8, device=self.dev)
         chunk = 2048   # inclusion tables of 2048 cells fit the 4 MiB staging area
         for s in range(0, len(problems), chunk):
@@ -62,13 +68,14 @@ class WarmStart:
 
     @staticmethod
     def energy_weights(x):
-        """sqrt of the pointwise energy weight of each output channel, [n, N, N, 8]: a(x) for
+        """sqrt of the pointwise energy weight of each output channel, [n, (N,) N, N, 2 d^2]: a(x) for
         the primal correctors, 1/a(x) for the dual ones (features are log10(a)/3). The
         energy norm of a field error is the a-weighted L2 norm (a(u, u) = (A u, u), no
         derivative), so a plain MSE on sqrt(w) * field is the energy-norm error of the start."""
         la = x[..., :1] * (3.0 * 2.302585092994046)   # ln a
-        primal = (0.5 * la).exp().expand(*x.shape[:-1], 4)
-        dual = (-0.5 * la).exp().expand(*x.shape[:-1], 4)
+        half = (x.dim() - 2) ** 2
+        primal = (0.5 * la).exp().expand(*x.shape[:-1], half)
+        dual = (-0.5 * la).exp().expand(*x.shape[:-1], half)
         return torch_cat((primal, dual))
 
     @staticmethod
@@ -76,35 +83,44 @@ class WarmStart:
         """Scale each (side, rhs) pair of channels of each cell to unit RMS: the network
         learns the shape of each corrector; the solver finds its scale (Rayleigh-Ritz on
         the start direction), so the magnitude need not be predicted."""
-        n = y.shape[0]
-        blocks = y.view(n, -1, 4, 2)
+        n, d = y.shape[0], y.dim() - 2
+        blocks = y.view(n, -1, 2 * d, d)
         rms = blocks.pow(2).mean(dim=(1, 3), keepdim=True).sqrt().clamp_min(1e-12)
         return (blocks / rms).view_as(y)
 
+    def field_shape(self, n):
+        d = self.d
+        return (n, 2, d, d) + self.grid[:-1] + ((self.N + 1) // 2,)
+
     def solve(self, problems, precision, tol, x0=None, want_fields=False, max_iter=10000):
+        """2D: one batched launch (complex64 fields in mixed precision)."""
         torch = self.torch
-        Nh = (self.N + 1) // 2
         cdt = torch.complex64 if precision == bd.HOM_MIXED else torch.complex128
-        fields = torch.empty((len(problems), 2, 2, 2, self.N, Nh), dtype=cdt, device=self.dev) if want_fields else None
+        fields = torch.empty(self.field_shape(len(problems)), dtype=cdt, device=self.dev) if want_fields else None
         out = self.solver.batched(problems, precision=precision, tol=tol, x0=x0, fields=fields, max_iter=max_iter)
         return out, fields
 
-    def fields_to_grid(self, fields):
+    def fields_to_grid(self, fields, out=None):
         torch = self.torch
         n = fields.shape[0]
-        grid = torch.empty((n, self.N, self.N, 8), dtype=torch.float32, device=self.dev)
+        grid = out if out is not None else torch.empty((n,) + self.grid + (self.ch,), dtype=torch.float32,
+                                                       device=self.dev)
         prec = bd.HOM_FP32 if fields.dtype == torch.complex64 else bd.HOM_FP64
-        bd.hom_half_to_grid(self.ctx, self.N, n, 8, fields.data_ptr(), grid.data_ptr(), prec)
+        nws = bd.hom_half_to_grid_workspace_size(self.ctx, self.d, self.N, n, self.ch)
+        ws = torch.empty(max(nws, 256), dtype=torch.uint8, device=self.dev)
+        bd.hom_half_to_grid(self.ctx, self.d, self.N, n, self.ch, fields.data_ptr(), grid.data_ptr(), prec,
+                            ws.data_ptr(), ws.numel())
         return grid
 
     def grid_to_fields(self, grid, precision):
+        """Half spectra of predicted grid fields: complex64 for the 2D batched mixed path,
+        complex128 otherwise (hom_bounds_io takes FP64 starts)."""
         torch = self.torch
         n = grid.shape[0]
-        Nh = (self.N + 1) // 2
-        cdt = torch.complex64 if precision == bd.HOM_MIXED else torch.complex128
-        half = torch.empty((n, 2, 2, 2, self.N, Nh), dtype=cdt, device=self.dev)
-        bd.hom_grid_to_half(self.ctx, self.N, n, 8, grid.data_ptr(), half.data_ptr(),
-                            bd.HOM_FP32 if precision == bd.HOM_MIXED else bd.HOM_FP64)
+        c64 = precision == bd.HOM_MIXED and self.d == 2
+        half = torch.empty(self.field_shape(n), dtype=torch.complex64 if c64 else torch.complex128, device=self.dev)
+        bd.hom_grid_to_half(self.ctx, self.d, self.N, n, self.ch, grid.data_ptr(), half.data_ptr(),
+                            bd.HOM_FP32 if c64 else bd.HOM_FP64)
         return half
 
     # -- training / inference -----------------------------------------------------------
@@ -141,9 +157,9 @@ class WarmStart:
         torch = self.torch
         n = x.shape[0]
         B = self.batch
-        out = torch.empty((n, self.N, self.N, 8), dtype=torch.float32, device=self.dev)
+        out = torch.empty((n,) + self.grid + (self.ch,), dtype=torch.float32, device=self.dev)
         xb = torch.zeros((B,) + tuple(x.shape[1:]), dtype=x.dtype, device=self.dev)
-        ob = torch.empty((B, self.N, self.N, 8), dtype=torch.float32, device=self.dev)
+        ob = torch.empty((B,) + self.grid + (self.ch,), dtype=torch.float32, device=self.dev)
         for s in range(0, n, B):
             m = min(B, n - s)
             xb[:m].copy_(x[s:s + m])
@@ -151,6 +167,33 @@ class WarmStart:
                                self.ws.data_ptr(), self.ws.numel())
             out[s:s + m].copy_(ob[:m])
         return out
+
+    def predict_on_grid(self, x, N):
+        """The trained network on another grid N (same parameters: the spectral weights
+        act on the kept modes, whose coefficients the 1/N^d-normalised transforms make
+        grid-independent), one cell at a time. x: [n, (N,) N, N, 1]."""
+        torch = self.torch
+        a = self.arch
+        cfg = bd.net_config(N, 1, a["width"], a["modes"], a["layers"], a["proj"], self.ch, self.d)
+        _, nws = bd.hom_net_sizes(self.ctx, cfg, 1)
+        if getattr(self, "_ws_grid", None) is None or self._ws_grid.numel() < nws:
+            self._ws_grid = torch.empty(nws, dtype=torch.uint8, device=self.dev)
+        n = x.shape[0]
+        out = torch.empty((n,) + (N,) * self.d + (self.ch,), dtype=torch.float32, device=self.dev)
+        for i in range(n):
+            xi = x[i:i + 1].contiguous()
+            bd.hom_net_forward(self.ctx, cfg, self.params.data_ptr(), 1, xi.data_ptr(), out[i:i + 1].data_ptr(),
+                               self._ws_grid.data_ptr(), self._ws_grid.numel())
+        return out
+
+    def with_grid(self, N):
+        """A view of this network for features / fields on grid N (shares the parameters)."""
+        other = object.__new__(WarmStart)
+        other.__dict__.update(self.__dict__)
+        other.N = N
+        other.grid = (N,) * self.d
+        other._ws_grid = None
+        return other
 
 
 def train_and_evaluate(N=63, n_train=20000, n_test=1024, epochs=20, batch=32, width=32, modes=12, layers=4,
@@ -234,4 +277,119 @@ def train_and_evaluate(N=63, n_train=20000, n_test=1024, epochs=20, batch=32, wi
         "time_geometry_s": t_probs,
         "max_rel_bound_diff": float(max(rel)), "ordering_ok": bool(ok),
         "net_only_gap_ratio_median": float(np.median(gap_net)),
+    }
+
+
+def _iters(out):
+    return int(np.asarray(out["report"]["iters"]).sum())
+
+
+def train_and_evaluate_3d(N_train=41, N_eval=113, n_train=1000, n_test=32, eval_seeds=(0,), epochs=30, batch=8,
+                          width=24, modes=8, layers=4, proj=64, seed_train=200000, seed_test=300000, tol=1e-4,
+                          precision="mixed", lr=2e-3, gen_tol=1e-6, solver=None, chunk=16, eval_tight_tol=None):
+    """The 3D learned warm start: random-sphere cells (16 equal balls, volume fraction 0.3,
+    contrast 1000), training fields generated by hom_bounds_io at N_train, evaluation on
+    held-out cells at N_train and on the cells `eval_seeds` at N_eval (seed 0 at N = 113 is
+    the 3D sphere workload), with and without the start. The warm timings include the
+    features, the network forward on the evaluation grid and the transform to half
+    spectra. Returns a dict of measurements."""
+    import torch
+    import paper_1404_3614_gb300 as hb
+    own = solver is None
+    if own:
+        solver = hb.Bounds(0)
+    prec = bd.HOM_MIXED if precision == "mixed" else bd.HOM_FP64
+    ws = WarmStart(solver, N_train, width, modes, layers, proj, batch, seed=seed_train, d=3)
+    t0 = time.perf_counter()
+    train_probs = [ms.random_spheres_3d(seed_train + i, N=N_train) for i in range(n_train)]
+    test_probs = [ms.random_spheres_3d(seed_test + i, N=N_train) for i in range(n_test)]
+    eval_probs = [ms.random_spheres_3d(s, N=N_eval) for s in eval_seeds]
+    t_probs = time.perf_counter() - t0
+    # training data: converged FP64 fields of each cell, chunks of `chunk` cells to the grid
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    y = torch.empty((n_train,) + ws.grid + (ws.ch,), dtype=torch.float32, device=ws.dev)
+    fb = torch.empty(ws.field_shape(chunk), dtype=torch.complex128, device=ws.dev)
+    gen_iters = []
+    for s in range(0, n_train, chunk):
+        m = min(chunk, n_train - s)
+        for i in range(m):
+            out = solver(train_probs[s + i], precision=prec, tol=gen_tol, fields=fb[i])
+            gen_iters.append(_iters(out))
+        ws.fields_to_grid(fb[:m], out=y[s:s + m])
+    del fb
+    x = ws.features(train_probs)
+    y = WarmStart.normalise_targets(y)
+    torch.cuda.synchronize()
+    t_data = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    hist = ws.train(x, y, epochs, lr=lr)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    del x, y
+
+    def compare(cells, wsg, tight=None):
+        rows = []
+        for p in cells:
+            solver(p, precision=prec, tol=tol)                      # warm-up (graphs, tables)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            zero = solver(p, precision=prec, tol=tol)
+            t_zero = time.perf_counter() - t0
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            xf = wsg.features([p])
+            pred = wsg.predict_on_grid(xf, wsg.N)
+            x0 = wsg.grid_to_fields(pred, bd.HOM_FP64)
+            torch.cuda.synchronize()
+            t_net = time.perf_counter() - t0
+            warm = solver(p, precision=prec, tol=tol, x0=x0)
+            t_warm = time.perf_counter() - t0
+            net_only = solver(p, precision=prec, tol=tol, x0=x0, max_iter=0)
+            S = warm["upper"] - warm["lower"]
+
+            def psd(M):
+                return bool(np.linalg.eigvalsh(0.5 * (M + M.T)).min() >= -1e-9 * np.abs(zero["upper"]).max())
+            row = {
+                "iters_zero": _iters(zero), "iters_warm": _iters(warm), "ms_zero": 1e3 * t_zero,
+                "ms_warm_total": 1e3 * t_warm, "ms_network": 1e3 * t_net,
+                "rel_bound_diff": float(max(np.abs(warm[k] - zero[k]).max() / np.linalg.norm(zero[k])
+                                            for k in ("upper", "lower"))),
+                "ordering_ok": psd(S),
+                # every bound of either run encloses the same A_H: the cross orderings hold too
+                "cross_ordering_ok": psd(warm["upper"] - zero["lower"]) and psd(zero["upper"] - warm["lower"]) and
+                psd(net_only["upper"] - zero["lower"]) and psd(zero["upper"] - net_only["lower"]),
+                "net_only_gap_ratio": float(np.trace(net_only["upper"] - net_only["lower"]) /
+                                            max(np.trace(zero["upper"] - zero["lower"]), 1e-300)),
+            }
+            if tight is not None:
+                zt = solver(p, precision=bd.HOM_FP64, tol=tight)
+                wt = solver(p, precision=bd.HOM_FP64, tol=tight, x0=x0)
+                row.update({"iters_zero_tight": _iters(zt), "iters_warm_tight": _iters(wt)})
+            rows.append(row)
+            del pred, x0
+        return rows
+
+    rows_test = compare(test_probs, ws)
+    rows_eval = compare(eval_probs, ws.with_grid(N_eval), eval_tight_tol)
+    if own:
+        solver.close()
+
+    def mean(rows, k):
+        return float(np.mean([r[k] for r in rows])) if rows else None
+
+    return {
+        "N_train": N_train, "N_eval": N_eval, "n_train": n_train, "n_test": n_test, "eval_seeds": list(eval_seeds),
+        "epochs": epochs, "batch": batch, "precision": precision, "tol": tol, "gen_tol": gen_tol,
+        "network": {"width": width, "modes": modes, "layers": layers, "proj": proj, "params": ws.n_params, "d": 3},
+        "loss_first_epoch": hist[0] if hist else None, "loss_last_epoch": hist[-1] if hist else None,
+        "gen_iters_mean": float(np.mean(gen_iters)),
+        "test_iters_zero_mean": mean(rows_test, "iters_zero"), "test_iters_warm_mean": mean(rows_test, "iters_warm"),
+        "test_ms_zero_mean": mean(rows_test, "ms_zero"), "test_ms_warm_mean": mean(rows_test, "ms_warm_total"),
+        "test_max_rel_bound_diff": float(max(r["rel_bound_diff"] for r in rows_test)) if rows_test else None,
+        "test_ordering_ok": all(r["ordering_ok"] and r["cross_ordering_ok"] for r in rows_test + rows_eval),
+        "test_net_only_gap_ratio_median": float(np.median([r["net_only_gap_ratio"] for r in rows_test]))
+        if rows_test else None,
+        "eval": rows_eval,
+        "time_geometry_s": t_probs, "time_data_s": t_data, "time_train_s": t_train,
     }

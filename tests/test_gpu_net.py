@@ -50,14 +50,39 @@ def test_grid_half_transforms(hb, ctx):
     grid = rng.normal(size=(B, N, N, ch))
     dgrid = torch.from_numpy(grid).float().cuda()
     half = torch.empty((B, ch, N, (N + 1) // 2), dtype=torch.complex128, device="cuda")
-    hb.binding.hom_grid_to_half(ctx, N, B, ch, dgrid.data_ptr(), half.data_ptr(), hb.HOM_FP64)
+    hb.binding.hom_grid_to_half(ctx, 2, N, B, ch, dgrid.data_ptr(), half.data_ptr(), hb.HOM_FP64)
     torch.cuda.synchronize()
     ref = np.fft.fft2(np.moveaxis(grid, -1, 1), axes=(2, 3)) / N ** 2       # [B, ch, y, x] -> [ky, kx]
     assert np.abs(half.cpu().numpy() - ref[..., :(N + 1) // 2]).max() < 2e-6
     back = torch.empty_like(dgrid)
-    hb.binding.hom_half_to_grid(ctx, N, B, ch, half.data_ptr(), back.data_ptr(), hb.HOM_FP64)
+    hb.binding.hom_half_to_grid(ctx, 2, N, B, ch, half.data_ptr(), back.data_ptr(), hb.HOM_FP64)
     torch.cuda.synchronize()
     assert np.abs(back.cpu().numpy() - grid).max() < 2e-5
+
+
+@pytest.mark.parametrize("N,prec", [(9, "fp64"), (15, "fp32"), (41, "fp64")])
+def test_grid_half_transforms_3d(hb, ctx, N, prec):
+    B, ch = 2, 3
+    rng = np.random.default_rng(N)
+    grid = rng.normal(size=(B, N, N, N, ch))
+    dgrid = torch.from_numpy(grid).float().cuda()
+    Nh = (N + 1) // 2
+    cdt, p = (torch.complex128, hb.HOM_FP64) if prec == "fp64" else (torch.complex64, hb.HOM_FP32)
+    half = torch.empty((B, ch, N, N, Nh), dtype=cdt, device="cuda")
+    hb.binding.hom_grid_to_half(ctx, 3, N, B, ch, dgrid.data_ptr(), half.data_ptr(), p)
+    torch.cuda.synchronize()
+    ref = np.fft.fftn(np.moveaxis(grid, -1, 1), axes=(2, 3, 4)) / N ** 3   # [B, ch, kz, ky, kx]
+    scale = np.abs(ref).max()
+    assert np.abs(half.cpu().numpy() - ref[..., :Nh]).max() < 2e-6 * N * scale
+    nws = hb.binding.hom_half_to_grid_workspace_size(ctx, 3, N, B, ch)
+    assert nws == B * ch * N * N * Nh * 8
+    ws = torch.empty(nws, dtype=torch.uint8, device="cuda")
+    back = torch.empty_like(dgrid)
+    hb.binding.hom_half_to_grid(ctx, 3, N, B, ch, half.data_ptr(), back.data_ptr(), p, ws.data_ptr(), nws)
+    torch.cuda.synchronize()
+    assert np.abs(back.cpu().numpy() - grid).max() < 1e-5 * N
+    with pytest.raises(hb.HombError):
+        hb.binding.hom_half_to_grid(ctx, 3, N, B, ch, half.data_ptr(), back.data_ptr(), p, ws.data_ptr(), nws - 8)
 
 
 def test_features_match_geometry(hb, ctx):
@@ -82,7 +107,29 @@ def test_features_match_geometry(hb, ctx):
         assert np.mean(np.abs(f[i] - ref) > 1e-5) < 0.02
 
 
+def test_features_3d_match_geometry(hb, ctx):
+    N = 13
+    probs = [ms.random_spheres_3d(s, N=N, n_balls=6, phi=0.25, contrast=30.0) for s in range(3)]
+    feat = torch.empty((3, N, N, N, 1), dtype=torch.float32, device="cuda")
+    ws = torch.empty(1 << 20, dtype=torch.uint8, device="cuda")
+    hb.binding.hom_net_features(ctx, probs, feat.data_ptr(), ws.data_ptr(), ws.numel())
+    f = feat.cpu().numpy()[..., 0]
+    j = np.arange(N) / N
+    Z, Y, X = np.meshgrid(j, j, j, indexing="ij")      # [z, y, x]
+    for i, p in enumerate(probs):
+        ref = np.full(X.shape, np.log10(np.trace(p.A0) / 3))
+        for inc in p.inclusions:
+            r2 = np.zeros_like(X)
+            for a, C_ in enumerate((X, Y, Z)):
+                dd = C_ - inc.center[a]
+                r2 += (dd - np.round(dd)) ** 2
+            ref = np.where(r2 < inc.size[0] ** 2, np.log10(np.trace(inc.A) / 3), ref)
+        # points exactly on an interface may fall either way in float32
+        assert np.mean(np.abs(f[i] - ref) > 1e-5) < 0.01
+
+
 CFG = dict(N=15, cin=1, width=8, modes=3, layers=2, proj=16, cout=8)
+CFG3 = dict(N=9, cin=1, width=6, modes=2, layers=2, proj=20, cout=18, d=3)
 
 
 def _net(hb, cfg, batch):
@@ -92,17 +139,21 @@ def _net(hb, cfg, batch):
     return ctx, c, npar, wsb
 
 
-def test_forward_and_gradient_match_cpu_reference(hb):
+@pytest.mark.parametrize("cfg", [CFG, CFG3], ids=["2d", "3d"])
+def test_forward_and_gradient_match_cpu_reference(hb, cfg):
     batch = 3
+    CFG = cfg
     ctx, c, npar, wsb = _net(hb, CFG, batch)
+    grid = (CFG["N"],) * CFG.get("d", 2)
     try:
         params = torch.empty(npar, dtype=torch.float32, device="cuda")
+        assert npar == fno.offsets(**CFG)["total"]
         hb.binding.hom_net_init(ctx, c, 7, params.data_ptr())
         g = torch.Generator().manual_seed(3)
-        x = torch.randn((batch, 15, 15, 1), generator=g, dtype=torch.float64)
-        t = torch.randn((batch, 15, 15, 8), generator=g, dtype=torch.float64) * 0.1
+        x = torch.randn((batch,) + grid + (1,), generator=g, dtype=torch.float64)
+        t = torch.randn((batch,) + grid + (CFG["cout"],), generator=g, dtype=torch.float64) * 0.1
         ws = torch.empty(wsb, dtype=torch.uint8, device="cuda")
-        out = torch.empty((batch, 15, 15, 8), dtype=torch.float32, device="cuda")
+        out = torch.empty((batch,) + grid + (CFG["cout"],), dtype=torch.float32, device="cuda")
         hb.binding.hom_net_forward(ctx, c, params.data_ptr(), batch, x.float().cuda().data_ptr(), out.data_ptr(),
                                    ws.data_ptr(), wsb)
         grad = torch.empty_like(params)
@@ -123,6 +174,29 @@ def test_forward_and_gradient_match_cpu_reference(hb):
             a, b = G[s:s + n], rgrad[s:s + n]
             scale = max(b.abs().max().item(), 1e-12)
             assert (a - b).abs().max().item() <= 5e-2 * scale, (name, (a - b).abs().max().item(), scale)
+    finally:
+        hb.hom_destroy(ctx)
+
+
+def test_forward_3d_large_batch_matches_single(hb):
+    """B * N^2 = 67240 rows of x transforms (above the 65535 grid limit, chunked): each
+    sample's output equals the output of the same sample run alone."""
+    cfg = dict(N=41, cin=1, width=4, modes=3, layers=1, proj=8, cout=2, d=3)
+    B, N = 40, 41
+    ctx, c, npar, wsb = _net(hb, cfg, B)
+    try:
+        params = torch.empty(npar, dtype=torch.float32, device="cuda")
+        hb.binding.hom_net_init(ctx, c, 5, params.data_ptr())
+        x = torch.randn((B, N, N, N, 1), generator=torch.Generator(device="cuda").manual_seed(2), device="cuda")
+        ws = torch.empty(wsb, dtype=torch.uint8, device="cuda")
+        out = torch.empty((B, N, N, N, 2), dtype=torch.float32, device="cuda")
+        hb.binding.hom_net_forward(ctx, c, params.data_ptr(), B, x.data_ptr(), out.data_ptr(), ws.data_ptr(), wsb)
+        one = torch.empty((1, N, N, N, 2), dtype=torch.float32, device="cuda")
+        for i in (0, 23, 39):
+            xi = x[i:i + 1].contiguous()
+            hb.binding.hom_net_forward(ctx, c, params.data_ptr(), 1, xi.data_ptr(), one.data_ptr(), ws.data_ptr(), wsb)
+            torch.cuda.synchronize()
+            assert (one[0] - out[i]).abs().max().item() <= 1e-5 * out[i].abs().max().item(), i
     finally:
         hb.hom_destroy(ctx)
 
@@ -168,3 +242,21 @@ def test_warm_start_gain_and_bounds(hb):
     assert res["max_rel_bound_diff"] < 2e-5, res
     assert res["ordering_ok"]
     assert res["net_only_gap_ratio_median"] >= 1.0 - 1e-6      # the network-only field is a looser valid bound
+
+
+def test_warm_start_3d_small(hb):
+    """The 3D warm start end to end on small grids: fields from hom_bounds_io at N = 15,
+    training, then starts on held-out N = 15 cells and on an N = 23 cell (the network runs
+    on a grid it was not trained on). Whatever the prediction, the bounds stay guaranteed:
+    each run's upper bound dominates every run's lower bound, the network-only field gives
+    a valid, looser bound."""
+    from paper_1404_3614_gb300 import warmstart
+    res = warmstart.train_and_evaluate_3d(N_train=15, N_eval=23, n_train=48, n_test=3, eval_seeds=(5,), epochs=6,
+                                          batch=4, width=8, modes=3, layers=2, proj=24, tol=1e-4, chunk=8)
+    print("3D warm start:", res["test_iters_zero_mean"], "->", res["test_iters_warm_mean"], "eval", res["eval"])
+    assert res["loss_last_epoch"] < res["loss_first_epoch"], res
+    assert res["test_ordering_ok"], res
+    assert res["test_max_rel_bound_diff"] < 1e-2, res
+    for r in res["eval"]:
+        assert r["net_only_gap_ratio"] >= 1.0 - 1e-6, r
+    assert res["test_net_only_gap_ratio_median"] >= 1.0 - 1e-6, res
