@@ -14,6 +14,15 @@ inequalities, as in Eq. S and Eq. S1 of the numerical examples), with periodic i
 Everything is dense and in the Fourier basis (tiny grids): for trigonometric polynomials on
 Z_N, a_N(u, v) = v_hat^H K_N u_hat with K_N[(l, a), (k, b)] = A_N_hat_ab(l - k mod N), the
 length-N DFT (1/|N| normalisation, Eq. DFT) of the samples.
+
+General (even) grids, Sec. "Fully discrete spaces --- general grids": the grid points are
+x_N^k for k in Z_N = {-N/2, ..., N/2 - 1} along an even axis, and the conforming spaces
+E_N = G^E_{N,0}[X_N], J_N = G^J_{N,0}[X_N] (Def. FD_proj_E, Def. FD_subspaces_E) carry no
+Nyquist frequency: their fields are trigonometric polynomials on the reduced set Z_N^r, which
+along an even axis is Z_{N-1}. The GaNi minimisers are searched there (Eq. FD_GaNi with the
+0-projections), the grid quadrature still runs over all N grid points, and the double-grid
+bounds of the minimisers are the exact Galerkin energies on Z_N^r. On odd grids nothing
+changes (Z_N^r = Z_N). Prop. FD_even_problem gives B_{H,N}^{-1} <= A_{H,N} in general.
 """
 from __future__ import annotations
 
@@ -28,11 +37,23 @@ from .dense import _galerkin_matrix, _projector
 from .fourier import freqs, frequency_grid
 
 
+def grid_indices(n: int) -> np.ndarray:
+    """Z_n in centred order for any n: -(n-1)/2 .. (n-1)/2 (odd), -n/2 .. n/2 - 1 (even)."""
+    lo = -(n // 2)
+    return np.arange(lo, lo + n, dtype=np.int64)
+
+
+def reduced_problem(problem: Problem) -> Problem:
+    """The same cell on the reduced frequency set Z_N^r: N_a - 1 along even axes."""
+    N = np.asarray(problem.N, dtype=np.int64)
+    return problem.with_N(np.where(N % 2 == 0, N - 1, N))
+
+
 def grid_points(problem: Problem) -> np.ndarray:
-    """x_N^k for k in Z_N, centred order, shape [*N, d] (Eq. grid_points)."""
+    """x_N^k for k in Z_N, centred order, shape [*N, d] (Eq. grid_points), odd or even N."""
     N = tuple(int(n) for n in problem.N)
     Y = np.asarray(problem.Y, dtype=np.float64)
-    k = frequency_grid(N)
+    k = np.stack(np.meshgrid(*[grid_indices(n) for n in N], indexing="ij"), axis=-1)
     return k * (Y / np.asarray(N, dtype=np.float64))
 
 
@@ -70,13 +91,13 @@ def sample_coefficient(problem: Problem, side: str = "primal") -> np.ndarray:
 
 def gani_matrix(problem: Problem, side: str) -> np.ndarray:
     """K_N[(l, a), (k, b)] = (1/|N|) sum_x A_N(x)_ab exp(-2 pi i (l - k) . x / Y) written out
-    as the grid sum (no FFT), l, k in Z_N."""
-    N = tuple(int(n) for n in problem.N)
+    as the grid sum over the N grid points (no FFT), l, k in the reduced set Z_N^r."""
     d = problem.d
     Y = np.asarray(problem.Y, dtype=np.float64)
     A = sample_coefficient(problem, side).reshape(-1, d, d)          # [npts, d, d]
     x = grid_points(problem).reshape(-1, d)                          # [npts, d]
-    k = frequency_grid(N).reshape(-1, d)                             # [nk, d]
+    Nr = tuple(int(n) for n in reduced_problem(problem).N)
+    k = frequency_grid(Nr).reshape(-1, d)                            # [nk, d]
     phase = np.exp(-2j * np.pi * (k / Y) @ x.T)                      # [nk, npts]: phi_{-k}(x)
     npts = x.shape[0]
     # K[(l, a), (k, b)] = (1/|N|) sum_x conj(phi_l(x)) A_ab(x) phi_k(x)
@@ -88,10 +109,11 @@ def gani_matrix(problem: Problem, side: str) -> np.ndarray:
 def gani_fields(problem: Problem, side: str):
     """GaNi minimisers X (columns a = 1..d, Fourier coefficients on Z_N), E0 and K_N."""
     K = gani_matrix(problem, side)
-    P = _projector(problem, side)
+    red = reduced_problem(problem)
+    P = _projector(red, side)
     d = problem.d
     nkd = K.shape[0]
-    k = frequency_grid(tuple(int(n) for n in problem.N)).reshape(-1, d)
+    k = frequency_grid(tuple(int(n) for n in red.N)).reshape(-1, d)
     k0 = int(np.flatnonzero(np.all(k == 0, axis=1))[0])
     E0 = np.zeros((nkd, d), dtype=np.complex128)
     for a in range(d):
@@ -111,7 +133,7 @@ def gani_bounds(problem: Problem) -> dict:
         X, E0, KN = gani_fields(problem, side)
         U = E0 + X
         out["A_HN" if side == "primal" else "B_HN"] = (U.conj().T @ KN @ U).real
-        W[side] = (U.conj().T @ _galerkin_matrix(problem, side) @ U).real
+        W[side] = (U.conj().T @ _galerkin_matrix(reduced_problem(problem), side) @ U).real
     b = assemble_bounds(W["primal"], W["dual"])
     out.update({key: b[key] for key in ("upper", "lower", "mean", "D")})
     return out

@@ -94,3 +94,112 @@ def test_fourier_matrix_is_the_grid_quadrature():
         quad = sum(np.conj(v[i]) @ A[i] @ u[i] for i in range(x.shape[0])) / x.shape[0]
         four = np.conj(vh.reshape(-1)) @ K @ uh.reshape(-1)
         assert abs(quad - four) < 1e-11 * abs(quad)
+
+
+# ---- general (even) grids -------------------------------------------------------------
+EVEN = {
+    "square2d_N8": lambda: ms.square_inclusion_2d(N=9).with_N(8),
+    "aniso2d_N6": lambda: ms.random_anisotropic_2d(3, N=7).with_N(6),
+    "rect2d_N6x5": lambda: ms.random_rectangles_2d(4, N=11).with_N((6, 5)),
+    "paper_rho100_N8": lambda: ms.paper_square_2d(15, 100.0).with_N(8),
+    "aniso3d_N4": lambda: ms.random_anisotropic_3d(4, N=5).with_N(4),
+    "spheres3d_N4x5x6": lambda: ms.random_spheres_3d(2, N=7, n_balls=6, phi=0.25, contrast=30.0).with_N((4, 5, 6)),
+}
+
+
+def real_space_gani(problem, side):
+    """A_{H,N} (primal) or B_{H,N} (dual) from the grid formulation of Eq. FD_GaNi written in
+    real space: e in X_N with e = G_{N,0} e and G_{N,0}[A (E + e)] = 0, where G_{N,0} =
+    F^-1 G_hat F (numpy FFTs) with G_hat zero at k = 0 and at the Nyquist frequencies
+    (Def. FD_proj_E). The dense system is assembled by applying the operator to unit
+    vectors; the energy is the grid mean of A (E + e) . (E + e)."""
+    d = problem.d
+    N = tuple(int(n) for n in problem.N)
+    Y = np.asarray(problem.Y, dtype=np.float64)
+    A = np.fft.ifftshift(gani.sample_coefficient(problem, side), axes=tuple(range(d)))   # [*N, d, d], x_j = Y j / N
+    k = np.stack(np.meshgrid(*[np.fft.fftfreq(n) * n for n in N], indexing="ij"), axis=-1)
+    xi = k / Y
+    n2 = np.sum(xi * xi, axis=-1)
+    nyq = np.zeros(N, dtype=bool)
+    for a in range(d):
+        if N[a] % 2 == 0:
+            nyq |= np.isclose(k[..., a], -N[a] / 2)
+    keep = (n2 > 0) & ~nyq
+    GE = np.where(keep[..., None, None], xi[..., :, None] * xi[..., None, :] / np.where(keep, n2, 1.0)[..., None, None], 0.0)
+    G = GE if side == "primal" else np.where(keep[..., None, None], np.eye(d) - GE, 0.0)
+    axes = tuple(range(d))
+
+    def proj(v):                                  # v [*N, d] real
+        vh = np.fft.fftn(v, axes=axes)
+        return np.real(np.fft.ifftn(np.einsum("...ab,...b->...a", G, vh), axes=axes))
+
+    npts = int(np.prod(N))
+    n = npts * d
+
+    def op(e):
+        e = e.reshape(N + (d,))
+        return (proj(np.einsum("...ab,...b->...a", A, proj(e))) + e - proj(e)).reshape(-1)
+
+    L = np.stack([op(np.eye(n)[:, j]) for j in range(n)], axis=1)
+    H = np.zeros((d, d))
+    U = []
+    for b in range(d):
+        E = np.zeros(N + (d,))
+        E[..., b] = 1.0
+        rhs = -proj(np.einsum("...ab,...b->...a", A, E)).reshape(-1)
+        U.append(E + np.linalg.solve(L, rhs).reshape(N + (d,)))
+    for a in range(d):
+        for b in range(d):
+            H[a, b] = np.mean(np.einsum("...a,...ab,...b->...", U[a], A, U[b]))
+    return H
+
+
+@pytest.mark.parametrize("name", list(EVEN))
+def test_even_grid_gani_equals_real_space_formulation(name):
+    p = EVEN[name]()
+    out = gani.gani_bounds(p)
+    for side, key in (("primal", "A_HN"), ("dual", "B_HN")):
+        ref = real_space_gani(p, side)
+        assert np.abs(out[key] - ref).max() <= 1e-10 * np.abs(ref).max(), (side, out[key], ref)
+
+
+@pytest.mark.parametrize("name", ["square2d_N9", "aniso2d_N7", "aniso3d_N5"])
+def test_real_space_formulation_on_odd_grids(name):
+    """The same real-space construction on odd grids (no Nyquist) gives the odd-grid oracle."""
+    p = CELLS[name]()
+    out = gani.gani_bounds(p)
+    assert np.abs(out["A_HN"] - real_space_gani(p, "primal")).max() <= 1e-10 * np.abs(out["A_HN"]).max()
+
+
+@pytest.mark.parametrize("name", list(EVEN))
+def test_even_grid_duality_inequality_and_enclosure(name):
+    """Prop. FD_even_problem: B_{H,N}^{-1} <= A_{H,N}; the GaNi minimisers live in the
+    Galerkin spaces of the reduced set Z_N^r = Z_{N-1}, so their double-grid bounds enclose
+    the Galerkin bounds on N - 1 (Eq. GaNi_bounds)."""
+    p = EVEN[name]()
+    out = gani.gani_bounds(p)
+    assert loewner_ge(out["A_HN"], np.linalg.inv(out["B_HN"]), 1e-10)
+    ga = dense.dense_bounds(gani.reduced_problem(p))
+    assert loewner_ge(out["upper"], ga["upper"], 1e-11)
+    assert loewner_ge(ga["lower"], out["lower"], 1e-11)
+    assert loewner_ge(out["upper"], out["lower"], 1e-11)
+
+
+def test_even_grid_duality_gap_is_real():
+    """On even grids the inequality of Prop. FD_even_problem is strict for a contrasted cell
+    (the odd-grid equality does not carry over)."""
+    out = gani.gani_bounds(EVEN["paper_rho100_N8"]())
+    gap = out["A_HN"] - np.linalg.inv(out["B_HN"])
+    assert np.linalg.eigvalsh(0.5 * (gap + gap.T)).max() > 1e-3 * np.abs(out["A_HN"]).max()
+
+
+def test_even_grid_points_and_homogeneous_cell():
+    p = ms.square_inclusion_2d(N=9).with_N((4, 6))
+    x = gani.grid_points(p)
+    assert np.allclose(x[:, 0, 0], np.array([-2, -1, 0, 1]) / 4.0)
+    assert np.allclose(x[0, :, 1], np.array([-3, -2, -1, 0, 1, 2]) / 6.0)
+    A0 = np.array([[2.0, 0.3], [0.3, 1.0]])
+    hom = ms.make_problem(2, 6, 1.0, A0, [])
+    out = gani.gani_bounds(hom)
+    for key in ("A_HN", "upper", "lower"):
+        assert np.abs(out[key] - A0).max() < 1e-13
