@@ -6,7 +6,8 @@
  * properties by FFT-based Galerkin method").
  *
  * The problem statement follows the paper:
- *   cell Y = prod_a (-Y_a/2, Y_a/2), odd grid N (Eq. N_odd), coefficient
+ *   cell Y = prod_a (-Y_a/2, Y_a/2), grid N (odd, Eq. N_odd, or general: see
+ *   hom_problem.N), coefficient
  *   A(x) = A0 + sum_j f_j(x - x_j) (A_j - A0)            (Eq. A_with_inclusions)
  *   with f_j the indicator of a box (Remark "inclusion") or a ball/disk;
  *   upper bound  A_up[a][b] = a(e_b + e^(b), e_a + e^(a)), e^(a) in E_N minimising
@@ -87,7 +88,17 @@ typedef struct {
 
 typedef struct {
   int32_t d;                   /* 2 or 3                                         */
-  int32_t N[3];                /* odd grid sizes N_a, a < d                      */
+  int32_t N[3];                /* grid sizes N_a >= 1, a < d. Odd grids (Eq. N_odd)
+                                  everywhere; even sizes (general grids, Sec. "Fully
+                                  discrete spaces --- general grids") in FP64
+                                  hom_bounds and the FP64 step-level calls only: the
+                                  conforming spaces E_N, J_N exclude the Nyquist
+                                  frequency k_a = -N_a/2 (Def. FD_proj_E), which every
+                                  field keeps at zero; the stored x frequencies are
+                                  0..(N_1+1)/2-1 in both cases. Ga on an even axis
+                                  then equals Ga on N_a - 1; GaNi samples the N_a
+                                  points and gives B_{H,N}^-1 <= A_{H,N} (Prop.
+                                  FD_even_problem).                                */
   double Y[3];                 /* cell side lengths Y_a > 0                      */
   double A0[9];                /* matrix phase, SPD, row-major, leading dim 3    */
   int32_t n_incl;              /* number of inclusions (may be 0)                */
@@ -286,6 +297,16 @@ hom_status hom_half_to_grid_workspace_size(hom_ctx* ctx, int32_t d, int32_t N, i
 hom_status hom_half_to_grid(hom_ctx* ctx, int32_t d, int32_t N, int32_t batch, int32_t ch,
                             const void* d_half, float* d_grid, int32_t precision,
                             void* d_workspace, size_t workspace_bytes, void* stream);
+/* Half-spectrum fields of one grid on another grid of the same dimension: `count` field
+ * components [Nz][Ny][(N1+1)/2] (e.g. count = 2 d d for a hom_field_io block) from grid
+ * N_from to grid N_to, out(k) = in(k) where N_from holds frequency k (Nyquist rows of even
+ * grids excluded) and 0 elsewhere. The coefficients do not depend on the grid (Eq. DFT), so
+ * this is the exact prolongation of a coarse trigonometric polynomial (the odd-grid spaces
+ * are nested) and the truncation P_N of a fine one. precision HOM_FP64 (double2) or HOM_FP32
+ * (float2); d_in and d_out must not overlap; enqueue only. */
+hom_status hom_resample_fields(hom_ctx* ctx, int32_t d, const int32_t N_from[3], const int32_t N_to[3],
+                               int64_t count, int32_t precision, const void* d_in, void* d_out,
+                               void* stream);
 /* the tensor-core GEMM: C = alpha op(A) op(B) + beta C (row-major FP32 in memory, BF16
  * products, FP32 accumulation); enqueue only. */
 hom_status hom_gemm_bf16(hom_ctx* ctx, int32_t M, int32_t N, int32_t K, const float* d_A, int32_t lda,

@@ -54,7 +54,7 @@ class Inclusion:
 class Problem:
     d: int
     Y: np.ndarray              # (d,) cell side lengths, cell = prod (-Y/2, Y/2)
-    N: np.ndarray              # (d,) odd grid sizes
+    N: np.ndarray              # (d,) grid sizes (odd; even sizes give the general grids)
     A0: np.ndarray             # (d, d) matrix phase
     inclusions: List[Inclusion]
     # optional pixel image of an isotropic scalar coefficient, shape (P_1, ..., P_d): pixel

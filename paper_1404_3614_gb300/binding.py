@@ -100,6 +100,7 @@ def _load():
         "hom_net_features": (i32, [vp, i32, P(hom_problem), vp, vp, sz, vp]),
         "hom_grid_to_half": (i32, [vp, i32, i32, i32, i32, vp, vp, i32, vp]),
         "hom_half_to_grid_workspace_size": (i32, [vp, i32, i32, i32, i32, P(sz)]),
+        "hom_resample_fields": (i32, [vp, i32, P(i32), P(i32), i64, i32, vp, vp, vp]),
         "hom_half_to_grid": (i32, [vp, i32, i32, i32, i32, vp, vp, i32, vp, sz, vp]),
         "hom_gemm_bf16": (i32, [vp, i32, i32, i32, vp, i32, i32, vp, i32, i32, vp, i32, C.c_float, C.c_float, vp]),
         "hom_coefficient": (i32, [vp, P(hom_problem), i32, i32, vp, vp, sz, vp]),
@@ -431,6 +432,13 @@ def hom_net_features(ctx, problems, d_features, d_ws, ws_bytes, stream=0):
 def hom_grid_to_half(ctx, d, N, batch, ch, d_grid, d_half, precision, stream=0):
     return check(ctx, lib.hom_grid_to_half(ctx, d, N, batch, ch, C.c_void_p(d_grid), C.c_void_p(d_half), precision,
                                            C.c_void_p(stream)))
+
+
+def hom_resample_fields(ctx, d, N_from, N_to, count, precision, d_in, d_out, stream=0):
+    f = (C.c_int32 * 3)(*(list(N_from) + [1] * (3 - len(N_from))))
+    t = (C.c_int32 * 3)(*(list(N_to) + [1] * (3 - len(N_to))))
+    return check(ctx, lib.hom_resample_fields(ctx, d, f, t, count, precision, C.c_void_p(d_in), C.c_void_p(d_out),
+                                              C.c_void_p(stream)))
 
 
 def hom_half_to_grid_workspace_size(ctx, d, N, batch, ch):

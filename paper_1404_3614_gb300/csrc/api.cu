@@ -124,7 +124,8 @@ struct Geometry {
   int d = 2;
   int N[3] = {1, 1, 1};
   int M[3] = {1, 1, 1};
-  int Nh = 1;       // (N1 + 1)/2
+  int Nh = 1;       // (N1 + 1)/2: the stored x frequencies 0..Nh-1 (an even N1 has no Nyquist column)
+  bool even = false;   // some axis has an even N (general grids, Def. FD_proj_E)
   int Nxs = 1;      // (M1 + 1)/2 = N1: half range of the coefficient spectrum
   double Y[3] = {1, 1, 1};
   double invY[3] = {1, 1, 1};
@@ -239,7 +240,8 @@ hom_status build_geometry(hom_ctx* ctx, const hom_problem* P, Geometry& g) {
     g.N[a] = a < g.d ? P->N[a] : 1;
     g.Y[a] = a < g.d ? P->Y[a] : 1.0;
     if (a < g.d) {
-      if (g.N[a] < 1 || g.N[a] % 2 != 1) return fail(ctx, HOM_ERR_INVALID_ARG, "grid sizes N must be odd and >= 1");
+      if (g.N[a] < 1) return fail(ctx, HOM_ERR_INVALID_ARG, "grid sizes N must be >= 1");
+      if (g.N[a] % 2 == 0) g.even = true;
       if (g.N[a] > 2049) return fail(ctx, HOM_ERR_INVALID_ARG, "grid size N too large (max 2049)");
       if (!(g.Y[a] > 0) || !std::isfinite(g.Y[a])) return fail(ctx, HOM_ERR_INVALID_ARG, "cell sizes Y must be > 0");
     }
@@ -1191,6 +1193,7 @@ hom_status build_batch(hom_ctx* ctx, int n, const hom_problem* probs, const hom_
     Geometry g;
     CKS(build_geometry(ctx, &probs[i], g));
     if (g.d != 2) return fail(ctx, HOM_ERR_INVALID_ARG, "hom_bounds_batched handles two-dimensional cells (d = 2)");
+    if (g.even) return fail(ctx, HOM_ERR_INVALID_ARG, "hom_bounds_batched handles odd grids");
     if (!g.bitmap.empty()) return fail(ctx, HOM_ERR_INVALID_ARG, "hom_bounds_batched takes inclusion cells, not images");
     double A0f[9], B0[9] = {};
     for (int a = 0; a < 3; ++a)
@@ -1394,6 +1397,7 @@ static hom_status bounds_impl(hom_ctx* ctx, const hom_problem* prob, const hom_o
     return fail(ctx, HOM_ERR_INVALID_ARG, "discretization must be 0 (Ga) or 1 (GaNi)");
   const bool gani = opts->discretization == 1;
   if (gani && opts->precision != HOM_FP64) return fail(ctx, HOM_ERR_INVALID_ARG, "GaNi runs in FP64");
+  if (g.even && opts->precision != HOM_FP64) return fail(ctx, HOM_ERR_INVALID_ARG, "even grids run in FP64");
   if (gani && io && (io->d_x0 || io->d_fields))
     return fail(ctx, HOM_ERR_INVALID_ARG, "starting / output fields are for the Galerkin discretization");
   Runner run{ctx, g, make_layout(g, g.d, elem, 0), static_cast<unsigned char*>(d_ws),
@@ -1798,6 +1802,7 @@ hom_status hom_coefficient(hom_ctx* ctx, const hom_problem* prob, int32_t side, 
   CKS(set_device(ctx));
   Geometry g;
   CKS(build_geometry(ctx, prob, g));
+  if (g.even && precision != HOM_FP64) return fail(ctx, HOM_ERR_INVALID_ARG, "even grids run in FP64");
   Runner run{ctx, g, make_layout(g, 1, 16, 1), static_cast<unsigned char*>(d_ws),
              static_cast<cudaStream_t>(stream), 1};
   if (!d_ws || ws_bytes < run.L.total) return fail(ctx, HOM_ERR_WORKSPACE, "workspace too small");
@@ -1818,6 +1823,7 @@ hom_status hom_rhs(hom_ctx* ctx, const hom_problem* prob, int32_t side, int32_t 
   CKS(set_device(ctx));
   Geometry g;
   CKS(build_geometry(ctx, prob, g));
+  if (g.even && precision != HOM_FP64) return fail(ctx, HOM_ERR_INVALID_ARG, "even grids run in FP64");
   if (nrhs < 1 || nrhs > g.d) return fail(ctx, HOM_ERR_INVALID_ARG, "nrhs must be in [1, d]");
   if (!g.bitmap.empty())
     return fail(ctx, HOM_ERR_INVALID_ARG, "hom_rhs: a pixel image has no closed-form right-hand side "
@@ -1847,6 +1853,7 @@ hom_status hom_matvec(hom_ctx* ctx, const hom_problem* prob, int32_t side, int32
   CKS(set_device(ctx));
   Geometry g;
   CKS(build_geometry(ctx, prob, g));
+  if (g.even && precision != HOM_FP64) return fail(ctx, HOM_ERR_INVALID_ARG, "even grids run in FP64");
   if (nrhs < 1 || nrhs > g.d) return fail(ctx, HOM_ERR_INVALID_ARG, "nrhs must be in [1, d]");
   Runner run{ctx, g, make_layout(g, nrhs, 16, 1), static_cast<unsigned char*>(d_ws),
              static_cast<cudaStream_t>(stream), nrhs};
@@ -1946,6 +1953,7 @@ hom_status hom_matvec_noalloc(hom_ctx* ctx, const hom_problem* prob, int32_t sid
   CKS(set_device(ctx));
   Geometry g;
   CKS(build_geometry(ctx, prob, g));
+  if (g.even && precision != HOM_FP64) return fail(ctx, HOM_ERR_INVALID_ARG, "even grids run in FP64");
   if (nrhs < 1 || nrhs > g.d) return fail(ctx, HOM_ERR_INVALID_ARG, "nrhs must be in [1, d]");
   const Layout L = make_layout(g, nrhs, 16, 1);
   if (L.total > (size_t)HOM_NOALLOC_SCRATCH_BYTES) {
@@ -2258,6 +2266,31 @@ hom_status hom_half_to_grid(hom_ctx* ctx, int32_t d, int32_t N, int32_t batch, i
   CKS(set_device(ctx));
   KL(half_to_grid(d, N, batch, ch, d_half, d_grid, precision == HOM_FP64 ? 1 : 0, d_ws,
                   static_cast<cudaStream_t>(stream)));
+  return HOM_OK;
+}
+
+hom_status hom_resample_fields(hom_ctx* ctx, int32_t d, const int32_t N_from[3], const int32_t N_to[3],
+                               int64_t count, int32_t precision, const void* d_in, void* d_out, void* stream) {
+  if (!ctx || !N_from || !N_to || !d_in || !d_out || count < 1 || (d != 2 && d != 3) ||
+      (precision != HOM_FP64 && precision != HOM_FP32))
+    return fail(ctx, HOM_ERR_INVALID_ARG, "bad argument");
+  long long nf = count, nt = count;
+  for (int a = 0; a < d; ++a) {
+    if (N_from[a] < 1 || N_to[a] < 1 || N_from[a] > 4096 || N_to[a] > 4096)
+      return fail(ctx, HOM_ERR_INVALID_ARG, "grid sizes must be in [1, 4096]");
+    nf *= a == 0 ? (N_from[0] + 1) / 2 : N_from[a];
+    nt *= a == 0 ? (N_to[0] + 1) / 2 : N_to[a];
+  }
+  const size_t el = precision == HOM_FP64 ? 16 : 8;
+  const char* pi = static_cast<const char*>(d_in);
+  const char* po = static_cast<const char*>(d_out);
+  if (pi < po + nt * el && po < pi + nf * el) return fail(ctx, HOM_ERR_INVALID_ARG, "d_in and d_out overlap");
+  CKS(set_device(ctx));
+  const int f[3] = {N_from[0], N_from[1], d == 3 ? N_from[2] : 1};
+  const int t[3] = {N_to[0], N_to[1], d == 3 ? N_to[2] : 1};
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (precision == HOM_FP64) KL(launch_resample<double>(d_in, d_out, count, d, f, t, st));
+  else KL(launch_resample<float>(d_in, d_out, count, d, f, t, st));
   return HOM_OK;
 }
 

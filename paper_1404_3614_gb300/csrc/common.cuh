@@ -479,6 +479,10 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
 
 // Frequency of storage index i in FFT order for odd length n.
 __device__ __forceinline__ int sfreq(int i, int n) { return i <= (n - 1) / 2 ? i : i - n; }
+// The Nyquist frequency k = -n/2 of an even axis: the conforming spaces E_N, J_N of general
+// grids exclude it (Def. FD_proj_E: G^E_{N,0}, G^J_{N,0} vanish there), so every N-grid
+// field keeps it at zero. Never true on odd axes.
+__device__ __forceinline__ bool nyquist(int k, int n) { return (n & 1) == 0 && k == -(n >> 1); }
 
 // Per-side CG scalars (device memory), one slot per right-hand side.
 struct CgScalars {

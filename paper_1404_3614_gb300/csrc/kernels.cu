@@ -100,9 +100,10 @@ __global__ void __launch_bounds__(kThreads) k_rhs(SpecArgs a, int side, int Nh, 
       dot.y += xi[c] * v[c].y;
     }
     const double w = kx == 0 ? 1.0 : 2.0;
+    const bool nyq = nyquist(ns[1], N1) || (a.d == 3 && nyquist(ns[2], N2));
     for (int c = 0; c < C; ++c) {
       double2 g = make_double2(0.0, 0.0);
-      if (n2 > 0.0) {
+      if (n2 > 0.0 && !nyq) {
         const double2 ge = make_double2(xi[c] * dot.x / n2, xi[c] * dot.y / n2);
         g = side == 0 ? ge : make_double2(v[c].x - ge.x, v[c].y - ge.y);
       }
@@ -528,9 +529,10 @@ __global__ void k_project_promote(const cpx<T>* x, double2* x64, int nrhs, int d
       dot.x += xi[c] * u[c].x;
       dot.y += xi[c] * u[c].y;
     }
+    const bool nyq = nyquist(ks[1], Ny) || (d == 3 && nyquist(ks[2], Nz));
     for (int c = 0; c < d; ++c) {
       double2 g = make_double2(0.0, 0.0);
-      if (n2 > 0.0) {
+      if (n2 > 0.0 && !nyq) {
         const double2 ge = make_double2(xi[c] * dot.x / n2, xi[c] * dot.y / n2);
         g = side == 0 ? ge : make_double2(u[c].x - ge.x, u[c].y - ge.y);
       }
@@ -642,6 +644,52 @@ cudaError_t launch_project_promote(const void* x, double2* x64, int nrhs, int d,
                                                         d, Ny, Nz, Nh, invY[0], invY[1], invY[2], side);
   return cudaGetLastError();
 }
+
+// Half-spectrum fields of one grid on another: out(k) = in(k) where the source grid holds
+// frequency k (Nyquist rows of even grids excluded), 0 elsewhere. Fourier coefficients of a
+// trigonometric polynomial do not depend on the grid (Eq. DFT with 1/|N|), so this is the
+// exact prolongation of a coarse field (E_N and J_N are nested for odd grids) and the
+// truncation P_N of a fine one. One thread per output element.
+template <typename T>
+__global__ void k_resample(const cpx<T>* in, cpx<T>* out, long long count, int d, int fx, int fy, int fz, int tx,
+                           int ty, int tz) {
+  const int tnh = (tx + 1) / 2, fnh = (fx + 1) / 2;
+  const long long tfield = (long long)tnh * ty * tz, ffield = (long long)fnh * fy * fz;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < count * tfield;
+       t += (long long)gridDim.x * blockDim.x) {
+    const long long f = t / tfield;
+    const long long e = t - f * tfield;
+    const int kx = (int)(e % tnh);
+    const int iy = (int)((e / tnh) % ty);
+    const int iz = (int)(e / ((long long)tnh * ty));
+    const int ky = sfreq(iy, ty), kz = d == 3 ? sfreq(iz, tz) : 0;
+    // the source holds k when |k| fits its reduced set (Nyquist rows excluded)
+    auto holds = [](int k, int n) { return k >= -((n - 1) / 2) && k <= (n - 1) / 2; };
+    const bool ok = kx < fnh && holds(ky, fy) && (d != 3 || holds(kz, fz)) && !nyquist(ky, ty) &&
+                    !(d == 3 && nyquist(kz, tz));
+    cpx<T> v = mk<T>(T(0), T(0));
+    if (ok) {
+      const int sy = ky < 0 ? ky + fy : ky, sz = kz < 0 ? kz + fz : kz;
+      v = in[f * ffield + ((long long)sz * fy + sy) * fnh + kx];
+    }
+    out[t] = v;
+  }
+}
+
+template <typename T>
+cudaError_t launch_resample(const void* in, void* out, long long count, int d, const int* from, const int* to,
+                            cudaStream_t s) {
+  const long long total = count * ((to[0] + 1) / 2) * (long long)to[1] * (d == 3 ? to[2] : 1);
+  long long blocks = (total + kThreads - 1) / kThreads;
+  if (blocks > 152 * 32) blocks = 152 * 32;
+  if (blocks < 1) blocks = 1;
+  k_resample<T><<<(int)blocks, kThreads, 0, s>>>(reinterpret_cast<const cpx<T>*>(in), reinterpret_cast<cpx<T>*>(out),
+                                                 count, d, from[0], from[1], d == 3 ? from[2] : 1, to[0], to[1],
+                                                 d == 3 ? to[2] : 1);
+  return cudaGetLastError();
+}
+template cudaError_t launch_resample<double>(const void*, void*, long long, int, const int*, const int*, cudaStream_t);
+template cudaError_t launch_resample<float>(const void*, void*, long long, int, const int*, const int*, cudaStream_t);
 
 cudaError_t launch_combine_fields(double2* x, int nrhs, int d, long long field, const double* c,
                                   cudaStream_t s) {

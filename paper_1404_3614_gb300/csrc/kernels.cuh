@@ -234,6 +234,10 @@ struct Coef3 { double v[9]; };   // 3 x 3 row-major coefficients passed by value
 // u_b = sum_a c[b*3+a] (e_a + x_a) in place over nrhs FP64 fields of d components
 cudaError_t launch_combine_fields(double2* x, int nrhs, int d, long long field, const double* c,
                                   cudaStream_t s);
+// half-spectrum fields [count][Nz][Ny][(Nx+1)/2] of grid `from` onto grid `to` (same d)
+template <typename T>
+cudaError_t launch_resample(const void* in, void* out, long long count, int d, const int* from, const int* to,
+                            cudaStream_t s);
 // x64 = Gamma (double) x_T (in place allowed for T = double)
 template <typename T>
 cudaError_t launch_project_promote(const void* x, double2* x64, int nrhs, int d, int Ny, int Nz,

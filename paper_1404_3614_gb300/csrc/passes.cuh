@@ -132,7 +132,8 @@ __global__ void __launch_bounds__(kPassThreads) k_pencil(PencilArgs a) {
     const int xx = t - i * a.XC;
     if (xx >= XC) continue;
     const int pos = trunc ? (i <= half ? i : i - a.Nlog + M) : i;
-    out[(long long)i * a.X + x0 + xx] = res[xx * M + pos];
+    // the Nyquist row of an even axis is not computed by a pruned last stage: zero it
+    out[(long long)i * a.X + x0 + xx] = trunc && nyquist(i - a.Nlog, a.Nlog) ? mk<T>(T(0), T(0)) : res[xx * M + pos];
   }
 }
 
@@ -199,8 +200,10 @@ __global__ void __launch_bounds__(kPassThreads) k_final(FinalArgs a) {
       kz = 0;
     }
     cpx<T> u[3];
+    // Nyquist rows of even axes are not computed by a pruned last stage: write zeros there
+    const bool nyq = nyquist(kl, a.Nlog) || (a.d == 3 && nyquist(ky, a.Ny));
 #pragma unroll
-    for (int c = 0; c < 3; ++c) u[c] = c < C ? res[(c * XC + xx) * M + pos] : mk<T>(T(0), T(0));
+    for (int c = 0; c < 3; ++c) u[c] = c < C && !nyq ? res[(c * XC + xx) * M + pos] : mk<T>(T(0), T(0));
     if (a.project) {
       const T xi[3] = {T(kx * a.invY[0]), T(ky * a.invY[1]), T(kz * a.invY[2])};
       T n2 = T(0);

@@ -286,13 +286,14 @@ def _iters(out):
 
 def train_and_evaluate_3d(N_train=41, N_eval=113, n_train=1000, n_test=32, eval_seeds=(0,), epochs=30, batch=8,
                           width=24, modes=8, layers=4, proj=64, seed_train=200000, seed_test=300000, tol=1e-4,
-                          precision="mixed", lr=2e-3, gen_tol=1e-6, solver=None, chunk=16, eval_tight_tol=None):
+                          precision="mixed", lr=2e-3, gen_tol=1e-6, solver=None, chunk=16, tight_tol=None):
     """The 3D learned warm start: random-sphere cells (16 equal balls, volume fraction 0.3,
     contrast 1000), training fields generated by hom_bounds_io at N_train, evaluation on
     held-out cells at N_train and on the cells `eval_seeds` at N_eval (seed 0 at N = 113 is
     the 3D sphere workload), with and without the start. The warm timings include the
     features, the network forward on the evaluation grid and the transform to half
-    spectra. Returns a dict of measurements."""
+    spectra. With tight_tol, the iterations from zero and from the start are also counted
+    at that tolerance (same precision). Returns a dict of measurements."""
     import torch
     import paper_1404_3614_gb300 as hb
     own = solver is None
@@ -328,7 +329,14 @@ def train_and_evaluate_3d(N_train=41, N_eval=113, n_train=1000, n_test=32, eval_
     t_train = time.perf_counter() - t0
     del x, y
 
-    def compare(cells, wsg, tight=None):
+    def coarse_start(p, fields_c):
+        """Half spectrum of the N_train field fields_c [1, 2, 3, 3, N, N, Nh] on p's grid."""
+        x0 = torch.zeros(ws.with_grid(int(p.N[0])).field_shape(1), dtype=torch.complex128, device=ws.dev)
+        bd.hom_resample_fields(solver.ctx, 3, (N_train,) * 3, tuple(int(n) for n in p.N), 2 * 9, bd.HOM_FP64,
+                               fields_c.data_ptr(), x0.data_ptr())
+        return x0
+
+    def compare(cells, wsg, tight=None, coarse=False):
         rows = []
         for p in cells:
             solver(p, precision=prec, tol=tol)                      # warm-up (graphs, tables)
@@ -363,15 +371,47 @@ def train_and_evaluate_3d(N_train=41, N_eval=113, n_train=1000, n_test=32, eval_
                                             max(np.trace(zero["upper"] - zero["lower"]), 1e-300)),
             }
             if tight is not None:
-                zt = solver(p, precision=bd.HOM_FP64, tol=tight)
-                wt = solver(p, precision=bd.HOM_FP64, tol=tight, x0=x0)
+                zt = solver(p, precision=prec, tol=tight)
+                wt = solver(p, precision=prec, tol=tight, x0=x0)
                 row.update({"iters_zero_tight": _iters(zt), "iters_warm_tight": _iters(wt)})
+            if coarse:
+                # (a) the network at its training grid on the cell sampled there, prolonged
+                # exactly to the fine grid (nested spaces); (b) the method's own coarse
+                # solution prolonged the same way (a non-learned reference start)
+                pc = p.with_N(N_train)
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                predc = ws.predict_on_grid(ws.features([pc]), N_train)
+                xc = coarse_start(p, ws.grid_to_fields(predc, bd.HOM_FP64))
+                cw = solver(p, precision=prec, tol=tol, x0=xc)
+                t_cw = time.perf_counter() - t0
+                cw_only = solver(p, precision=prec, tol=tol, x0=xc, max_iter=0)
+                fc = torch.empty(ws.field_shape(1), dtype=torch.complex128, device=ws.dev)
+                solver(pc, precision=prec, tol=tol)                 # warm-up of the coarse grid
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                solver(pc, precision=prec, tol=tol, fields=fc)
+                xs = coarse_start(p, fc)
+                cs = solver(p, precision=prec, tol=tol, x0=xs)
+                t_cs = time.perf_counter() - t0
+                row.update({
+                    "iters_coarse_net": _iters(cw), "ms_coarse_net_total": 1e3 * t_cw,
+                    "coarse_net_only_gap_ratio": float(np.trace(cw_only["upper"] - cw_only["lower"]) /
+                                                       max(np.trace(zero["upper"] - zero["lower"]), 1e-300)),
+                    "iters_coarse_solve": _iters(cs), "ms_coarse_solve_total": 1e3 * t_cs,
+                    "coarse_ordering_ok": psd(cw["upper"] - zero["lower"]) and psd(zero["upper"] - cw["lower"]) and
+                    psd(cs["upper"] - zero["lower"]) and psd(zero["upper"] - cs["lower"]),
+                })
+                if tight is not None:
+                    row.update({"iters_coarse_net_tight": _iters(solver(p, precision=prec, tol=tight, x0=xc)),
+                                "iters_coarse_solve_tight": _iters(solver(p, precision=prec, tol=tight, x0=xs))})
+                del predc, xc, xs, fc
             rows.append(row)
             del pred, x0
         return rows
 
-    rows_test = compare(test_probs, ws)
-    rows_eval = compare(eval_probs, ws.with_grid(N_eval), eval_tight_tol)
+    rows_test = compare(test_probs, ws, tight_tol)
+    rows_eval = compare(eval_probs, ws.with_grid(N_eval), tight_tol, coarse=N_eval != N_train)
     if own:
         solver.close()
 
@@ -386,8 +426,12 @@ def train_and_evaluate_3d(N_train=41, N_eval=113, n_train=1000, n_test=32, eval_
         "gen_iters_mean": float(np.mean(gen_iters)),
         "test_iters_zero_mean": mean(rows_test, "iters_zero"), "test_iters_warm_mean": mean(rows_test, "iters_warm"),
         "test_ms_zero_mean": mean(rows_test, "ms_zero"), "test_ms_warm_mean": mean(rows_test, "ms_warm_total"),
+        "tight_tol": tight_tol,
+        "test_iters_zero_tight_mean": mean(rows_test, "iters_zero_tight") if tight_tol else None,
+        "test_iters_warm_tight_mean": mean(rows_test, "iters_warm_tight") if tight_tol else None,
         "test_max_rel_bound_diff": float(max(r["rel_bound_diff"] for r in rows_test)) if rows_test else None,
-        "test_ordering_ok": all(r["ordering_ok"] and r["cross_ordering_ok"] for r in rows_test + rows_eval),
+        "test_ordering_ok": all(r["ordering_ok"] and r["cross_ordering_ok"] and r.get("coarse_ordering_ok", True)
+                                for r in rows_test + rows_eval),
         "test_net_only_gap_ratio_median": float(np.median([r["net_only_gap_ratio"] for r in rows_test]))
         if rows_test else None,
         "eval": rows_eval,

@@ -83,3 +83,52 @@ def test_gani_dual_start_is_exact(hb, solver, name):
 def test_gani_rejects_mixed_precision(hb, solver):
     with pytest.raises(hb.HombError):
         solver(ms.square_inclusion_2d(N=9), precision=hb.HOM_MIXED, discretization=1)
+
+
+# ---- general (even) grids -------------------------------------------------------------
+EVEN = {
+    "square2d_N8": lambda: ms.square_inclusion_2d(N=9).with_N(8),
+    "aniso2d_N6": lambda: ms.random_anisotropic_2d(3, N=7).with_N(6),
+    "rect2d_N6x5": lambda: ms.random_rectangles_2d(4, N=11).with_N((6, 5)),
+    "paper_rho100_N16": lambda: ms.paper_square_2d(15, 100.0).with_N(16),
+    "paper_rho1000_N10": lambda: ms.paper_square_2d(15, 1000.0).with_N(10),
+    "aniso3d_N4": lambda: ms.random_anisotropic_3d(4, N=5).with_N(4),
+    "spheres3d_N4x5x6": lambda: ms.random_spheres_3d(2, N=7, n_balls=6, phi=0.25, contrast=30.0).with_N((4, 5, 6)),
+    "cube3d_N8": lambda: ms.cube_inclusion_3d(N=9).with_N(8),
+}
+
+
+@pytest.mark.parametrize("name", list(EVEN))
+def test_even_grid_gani_matches_oracle(hb, solver, name):
+    """GaNi on general grids (Nyquist-free conforming spaces, Def. FD_proj_E): the GaNi
+    matrices and the double-grid bounds of their minimisers match the oracle; the GPU
+    results keep B_{H,N}^{-1} <= A_{H,N} (Prop. FD_even_problem)."""
+    p = EVEN[name]()
+    ref = gani.gani_bounds(p)
+    out = solver(p, precision=hb.HOM_FP64, tol=1e-12, discretization=1)
+    assert out["status"] == 0
+    assert rel(out["gani_A"], ref["A_HN"]) <= 1e-10, (out["gani_A"], ref["A_HN"])
+    assert rel(out["gani_B"], ref["B_HN"]) <= 1e-10
+    for key in ("upper", "lower", "mean", "D"):
+        assert np.abs(out[key] - ref[key]).max() <= 1e-10 * np.linalg.norm(ref["upper"]), key
+    S = out["gani_A"] - np.linalg.inv(out["gani_B"])
+    assert np.linalg.eigvalsh(0.5 * (S + S.T)).min() >= -1e-10 * np.abs(out["gani_A"]).max()
+
+
+@pytest.mark.parametrize("name", ["square2d_N8", "rect2d_N6x5", "aniso3d_N4", "cube3d_N8"])
+def test_even_grid_galerkin_is_the_reduced_grid(hb, solver, name):
+    """The conforming Galerkin spaces of an even grid exclude the Nyquist frequency, so they
+    are the spaces of the odd grid N - 1 along that axis: the same bounds."""
+    p = EVEN[name]()
+    ev = solver(p, precision=hb.HOM_FP64, tol=1e-12)
+    od = solver(gani.reduced_problem(p), precision=hb.HOM_FP64, tol=1e-12)
+    for key in ("upper", "lower"):
+        assert rel(ev[key], od[key]) <= 1e-11, key
+
+
+def test_even_grid_rejections(hb, solver):
+    p = EVEN["square2d_N8"]()
+    with pytest.raises(hb.HombError):
+        solver(p, precision=hb.HOM_MIXED)
+    with pytest.raises(hb.HombError):
+        solver.batched([p])

@@ -174,10 +174,18 @@ def test_energy_matches_oracle(hb, ctx, name, add_constant):
 
 
 def test_invalid_inputs_rejected(hb, ctx):
-    p = ms.square_inclusion_2d(N=8)
+    p = ms.square_inclusion_2d(N=5).with_N(0)
     with pytest.raises(hb.HombError) as e:
         hb.hom_problem_info(ctx, p)
     assert e.value.status == hb.binding.HOM_ERR_INVALID_ARG
+    # even grids are general grids: FP64 only
+    p8 = ms.square_inclusion_2d(N=8)
+    hb.hom_problem_info(ctx, p8)
+    nws = hb.hom_step_workspace_size(ctx, p8, 2)
+    wsb = torch.empty(nws, dtype=torch.uint8, device="cuda")
+    b = torch.empty((2, 2, 8, 4), dtype=torch.complex64, device="cuda")
+    with pytest.raises(hb.HombError):
+        hb.hom_rhs(ctx, p8, 0, hb.HOM_FP32, 2, b.data_ptr(), wsb.data_ptr(), nws)
     q = ms.make_problem(2, 5, 1.0, 1.0, [ms.box(0.0, 0.4, 2.0, 2), ms.box(0.1, 0.4, 3.0, 2)])
     with pytest.raises(hb.HombError):
         hb.hom_problem_info(ctx, q)

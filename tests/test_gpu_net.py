@@ -260,3 +260,45 @@ def test_warm_start_3d_small(hb):
     for r in res["eval"]:
         assert r["net_only_gap_ratio"] >= 1.0 - 1e-6, r
     assert res["test_net_only_gap_ratio_median"] >= 1.0 - 1e-6, res
+
+
+def _resample_ref(x, d, nf, nt):
+    """out(k) = in(k) for k held by grid nf (no Nyquist rows), else 0; numpy loops."""
+    def sf(i, n):
+        return i if i <= (n - 1) // 2 else i - n
+
+    def holds(k, n):
+        return -((n - 1) // 2) <= k <= (n - 1) // 2
+    count = x.shape[0]
+    tz = nt[2] if d == 3 else 1
+    fz = nf[2] if d == 3 else 1
+    out = np.zeros((count, tz, nt[1], (nt[0] + 1) // 2), dtype=x.dtype)
+    xi = x.reshape(count, fz, nf[1], (nf[0] + 1) // 2)
+    for iz in range(tz):
+        kz = sf(iz, tz) if d == 3 else 0
+        for iy in range(nt[1]):
+            ky = sf(iy, nt[1])
+            for kx in range((nt[0] + 1) // 2):
+                nyq = (nt[1] % 2 == 0 and ky == -nt[1] // 2) or (d == 3 and tz % 2 == 0 and kz == -tz // 2)
+                if kx < (nf[0] + 1) // 2 and holds(ky, nf[1]) and (d != 3 or holds(kz, fz)) and not nyq:
+                    out[:, iz, iy, kx] = xi[:, kz % fz, ky % nf[1], kx]
+    return out
+
+
+@pytest.mark.parametrize("d,nf,nt,prec", [(3, (9, 9, 9), (15, 13, 11), "fp64"), (3, (15, 13, 11), (9, 9, 9), "fp32"),
+                                          (2, (8, 8), (11, 11), "fp64"), (2, (11, 9), (6, 10), "fp64")])
+def test_resample_fields(hb, ctx, d, nf, nt, prec):
+    rng = np.random.default_rng(sum(nf) + sum(nt))
+    count = 4
+    shape_f = (count,) + ((nf[2],) if d == 3 else ()) + (nf[1], (nf[0] + 1) // 2)
+    x = rng.normal(size=shape_f) + 1j * rng.normal(size=shape_f)
+    cdt, p = (torch.complex128, hb.HOM_FP64) if prec == "fp64" else (torch.complex64, hb.HOM_FP32)
+    dx = torch.from_numpy(x).to(cdt).cuda()
+    shape_t = (count,) + ((nt[2],) if d == 3 else ()) + (nt[1], (nt[0] + 1) // 2)
+    out = torch.full(shape_t, 7.0, dtype=cdt, device="cuda")
+    hb.binding.hom_resample_fields(ctx, d, nf, nt, count, p, dx.data_ptr(), out.data_ptr())
+    torch.cuda.synchronize()
+    ref = _resample_ref(dx.cpu().numpy(), d, nf, nt)
+    assert np.array_equal(out.cpu().numpy().reshape(ref.shape), ref)
+    with pytest.raises(hb.HombError):
+        hb.binding.hom_resample_fields(ctx, d, nf, nt, count, p, dx.data_ptr(), dx.data_ptr())
