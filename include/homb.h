@@ -63,11 +63,15 @@ typedef enum {
   HOM_WARN_NOT_CONVERGED = 1,  /* max_iter reached: the returned bounds are still
                                   guaranteed (any conforming field gives a bound,
                                   Lemma bounds), only looser                      */
-  HOM_ERR_INVALID_ARG = -1,    /* even N, d not 2/3, non-SPD phase, overlapping or
-                                  oversized inclusion, NULL pointer, bad sizes    */
+  HOM_ERR_INVALID_ARG = -1,    /* N < 1, even N where only odd grids run, d not
+                                  2/3, non-SPD phase, overlapping or oversized
+                                  inclusion, NULL pointer, bad sizes              */
   HOM_ERR_BREAKDOWN = -2,      /* CG breakdown: NaN/Inf or p.Cp <= 0              */
   HOM_ERR_CUDA = -3,           /* a CUDA runtime call failed (see hom_last_error) */
   HOM_ERR_WORKSPACE = -4,      /* workspace smaller than hom_workspace_size      */
+  HOM_ERR_TIMEOUT = -5,        /* a bounded device wait gave up (the tensor-core
+                                  GEMM's completion barrier); the context stays
+                                  usable                                          */
   HOM_ERR_NOT_SPD_RESULT = -6  /* dual energy matrix not invertible              */
 } hom_status;
 
@@ -308,7 +312,8 @@ hom_status hom_resample_fields(hom_ctx* ctx, int32_t d, const int32_t N_from[3],
                                int64_t count, int32_t precision, const void* d_in, void* d_out,
                                void* stream);
 /* the tensor-core GEMM: C = alpha op(A) op(B) + beta C (row-major FP32 in memory, BF16
- * products, FP32 accumulation); enqueue only. */
+ * products on tcgen05.mma, FP32 accumulation in tensor memory); enqueue only. A wait that
+ * gives up is reported by the next hom_net_gradient as HOM_ERR_TIMEOUT. */
 hom_status hom_gemm_bf16(hom_ctx* ctx, int32_t M, int32_t N, int32_t K, const float* d_A, int32_t lda,
                          int32_t transA, const float* d_B, int32_t ldb, int32_t transB, float* d_C,
                          int32_t ldc, float alpha, float beta, void* stream);

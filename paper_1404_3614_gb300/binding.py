@@ -21,6 +21,7 @@ HOM_ERR_INVALID_ARG = -1
 HOM_ERR_BREAKDOWN = -2
 HOM_ERR_CUDA = -3
 HOM_ERR_WORKSPACE = -4
+HOM_ERR_TIMEOUT = -5
 HOM_ERR_NOT_SPD_RESULT = -6
 
 HOM_BOX, HOM_BALL = 0, 1

@@ -2111,6 +2111,7 @@ hom_status hom_net_gradient(hom_ctx* ctx, const hom_net_config* cfg, const float
   float h = 0.f;
   CK(d2h_copy(ctx, &h, dloss, sizeof(float), st));
   CK(cudaStreamSynchronize(st));
+  if (gemm_timeouts() != 0) return fail(ctx, HOM_ERR_TIMEOUT, "tensor-core GEMM completion wait timed out");
   if (loss) *loss = h;
   return HOM_OK;
 }

@@ -1,6 +1,6 @@
 // Learned CG warm start: a 2D or 3D Fourier-layer network (lift, L spectral layers,
-// projection) trained and run with a BF16 tensor-core GEMM (mma.sync m16n8k16, FP32
-// accumulation).
+// projection) trained and run with a BF16 tensor-core GEMM (tcgen05.mma, FP32 accumulation
+// in tensor memory).
 //
 // Every operation is a GEMM or an elementwise kernel:
 //   spectral layer  s = E_x [ H_y ( R_k ( G_y ( F_x v ) ) ) ]   (truncated DFTs as GEMMs
@@ -23,100 +23,182 @@
 namespace homb {
 
 // ---------------------------------------------------------------------------------
-// BF16 tensor-core GEMM (mma.sync.m16n8k16, FP32 accumulate)
+// BF16 tensor-core GEMM on the 5th-generation tensor cores (tcgen05.mma, FP32 accumulators
+// in tensor memory)
+//
+// One CTA of 128 threads computes a 128 x 64 tile of C. Per K chunk of 64, all threads read
+// the FP32 operands, round them to BF16 and store them in shared memory in the canonical
+// K-major, non-swizzled layout: 8-row x 16-byte core matrices, the M (or N) groups of a
+// core column 128 bytes apart, the K core columns 16 (or 8) core matrices apart. One thread
+// then issues four tcgen05.mma (K = 16 each) into a 128-lane x 64-column FP32 accumulator in
+// tensor memory and commits them to an mbarrier; the CTA waits on it (bounded) before the
+// next chunk overwrites the tiles. The epilogue reads the accumulator with tcgen05.ld
+// (warp w owns lanes 32w..32w+31 = rows) and applies alpha / beta, or writes split-K partials.
 // ---------------------------------------------------------------------------------
-constexpr int GBM = 64, GBN = 64, GBK = 32, GPAD = 8;
+constexpr int TBM = 128, TBN = 64, TBK = 64;
+constexpr int kTmemCols = 64;                       // power of two >= 32
+constexpr int kTileABytes = TBM * TBK * 2, kTileBBytes = TBN * TBK * 2;
+// 40 KB of dynamic shared memory: at most 5 CTAs per SM, 5 x 64 <= 512 TMEM columns, so an
+// allocation never waits on a CTA that is not running
+constexpr int kGemmSmem = 40 * 1024;
+constexpr long long kMbarSpinLimit = 1LL << 22;
 
-__device__ __forceinline__ uint32_t ld_pair(const __nv_bfloat16* p) {
-  return *reinterpret_cast<const uint32_t*>(p);
+__device__ int g_gemm_timeout = 0;   // set when an mbarrier wait gave up
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+// shared-memory matrix descriptor: start address, leading (K-direction core) and stride
+// (M/N-direction core) byte offsets, fixed 0b001 at bits 46-48, no swizzle
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = (uint64_t)((addr >> 4) & 0x3FFF);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
+  d |= (uint64_t)1 << 46;
+  return d;
+}
+
+// instruction descriptor, kind::f16: D F32, A and B BF16, both K-major, N >> 3, M >> 4
+__host__ __device__ constexpr uint32_t mma_idesc(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
+  __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+  return *reinterpret_cast<uint32_t*>(&h);
+}
+
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t phase) {
+  for (long long it = 0; it < kMbarSpinLimit; ++it) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(mbar), "r"(phase)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
 }
 
 __global__ void __launch_bounds__(128) k_gemm(GemmArgs g, int ksplit, float* partial) {
-  __shared__ __align__(16) __nv_bfloat16 As[GBM][GBK + GPAD];
-  __shared__ __align__(16) __nv_bfloat16 Bs[GBN][GBK + GPAD];
+  extern __shared__ __align__(1024) unsigned char smem[];
+  unsigned char* sA = smem;                                 // [TBK/8][TBM/8][8][16 B]
+  unsigned char* sB = smem + kTileABytes;                   // [TBK/8][TBN/8][8][16 B]
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + kTileABytes + kTileBBytes);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 1);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int bz = blockIdx.z / ksplit;
   const int ks = blockIdx.z - bz * ksplit;
   const float* A = g.A + (long long)bz * g.sA;
   const float* B = g.B + (long long)bz * g.sB;
-  const int m0 = blockIdx.y * GBM, n0 = blockIdx.x * GBN;
-  const int kchunk = ((g.K + ksplit - 1) / ksplit + GBK - 1) / GBK * GBK;
+  const int m0 = blockIdx.y * TBM, n0 = blockIdx.x * TBN;
+  const int kchunk = ((g.K + ksplit - 1) / ksplit + TBK - 1) / TBK * TBK;
   const int kbeg = ks * kchunk;
   const int kend = min(g.K, kbeg + kchunk);
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int wm = warp >> 1, wn = warp & 1;
-  const int grp = lane >> 2, tig = lane & 3;
-  float acc[2][4][4];
-#pragma unroll
-  for (int i = 0; i < 2; ++i)
-#pragma unroll
-    for (int j = 0; j < 4; ++j)
-#pragma unroll
-      for (int q = 0; q < 4; ++q) acc[i][j][q] = 0.f;
-  for (int k0 = kbeg; k0 < kend; k0 += GBK) {
-    // A tile (m, k): contiguous along k when not transposed, along m when transposed
-    for (int idx = threadIdx.x; idx < GBM * GBK; idx += blockDim.x) {
-      int r, kk;
-      if (!g.ta) { r = idx / GBK; kk = idx - r * GBK; }
-      else { kk = idx / GBM; r = idx - kk * GBM; }
-      const int gm = m0 + r, gk = k0 + kk;
-      float v = 0.f;
-      if (gm < g.M && gk < kend) v = g.ta ? A[(long long)gk * g.lda + gm] : A[(long long)gm * g.lda + gk];
-      As[r][kk] = __float2bfloat16_rn(v);
-    }
-    // B tile stored n-major (n, k)
-    for (int idx = threadIdx.x; idx < GBN * GBK; idx += blockDim.x) {
-      int n, kk;
-      if (!g.tb) { kk = idx / GBN; n = idx - kk * GBN; }
-      else { n = idx / GBK; kk = idx - n * GBK; }
-      const int gn = n0 + n, gk = k0 + kk;
-      float v = 0.f;
-      if (gn < g.N && gk < kend) v = g.tb ? B[(long long)gn * g.ldb + gk] : B[(long long)gk * g.ldb + gn];
-      Bs[n][kk] = __float2bfloat16_rn(v);
-    }
-    __syncthreads();
-#pragma unroll
-    for (int kk = 0; kk < GBK; kk += 16) {
-      uint32_t a[2][4], b[4][2];
-#pragma unroll
-      for (int mt = 0; mt < 2; ++mt) {
-        const int r = wm * 32 + mt * 16 + grp;
-        a[mt][0] = ld_pair(&As[r][kk + tig * 2]);
-        a[mt][1] = ld_pair(&As[r + 8][kk + tig * 2]);
-        a[mt][2] = ld_pair(&As[r][kk + 8 + tig * 2]);
-        a[mt][3] = ld_pair(&As[r + 8][kk + 8 + tig * 2]);
-      }
-#pragma unroll
-      for (int nt = 0; nt < 4; ++nt) {
-        const int n = wn * 32 + nt * 8 + grp;
-        b[nt][0] = ld_pair(&Bs[n][kk + tig * 2]);
-        b[nt][1] = ld_pair(&Bs[n][kk + 8 + tig * 2]);
-      }
-#pragma unroll
-      for (int mt = 0; mt < 2; ++mt)
-#pragma unroll
-        for (int nt = 0; nt < 4; ++nt)
-          asm volatile(
-              "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-              "{%0,%1,%2,%3};\n"
-              : "+f"(acc[mt][nt][0]), "+f"(acc[mt][nt][1]), "+f"(acc[mt][nt][2]), "+f"(acc[mt][nt][3])
-              : "r"(a[mt][0]), "r"(a[mt][1]), "r"(a[mt][2]), "r"(a[mt][3]), "r"(b[nt][0]), "r"(b[nt][1]));
-    }
-    __syncthreads();
+  const uint32_t mbar_a = smem_u32(mbar);
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
+                 "r"(kTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
-  // epilogue: direct (ksplit == 1) or partial sums per split
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mbar_a) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tslot;
+  constexpr uint32_t idesc = mma_idesc(TBM, TBN);
+  uint32_t phase = 0;
+  bool ok = true;
+  for (int k0 = kbeg; k0 < kend && ok; k0 += TBK) {
+    // A tile: 8-element K runs of one row per store (16 bytes = one core-matrix row)
+    for (int c = tid; c < TBM * (TBK / 8); c += 128) {
+      int r, kc;
+      if (!g.ta) { r = c >> 3; kc = c & 7; }
+      else { r = c & (TBM - 1); kc = c / TBM; }
+      const int gm = m0 + r;
+      float v[8];
 #pragma unroll
-  for (int mt = 0; mt < 2; ++mt)
+      for (int j = 0; j < 8; ++j) {
+        const int gk = k0 + kc * 8 + j;
+        v[j] = 0.f;
+        if (gm < g.M && gk < kend) v[j] = g.ta ? A[(long long)gk * g.lda + gm] : A[(long long)gm * g.lda + gk];
+      }
+      const uint4 q = make_uint4(pack_bf16(v[0], v[1]), pack_bf16(v[2], v[3]), pack_bf16(v[4], v[5]),
+                                 pack_bf16(v[6], v[7]));
+      *reinterpret_cast<uint4*>(sA + ((kc * (TBM / 8) + (r >> 3)) * 8 + (r & 7)) * 16) = q;
+    }
+    // B tile, stored N x K (K-major)
+    for (int c = tid; c < TBN * (TBK / 8); c += 128) {
+      int n, kc;
+      if (g.tb) { n = c >> 3; kc = c & 7; }
+      else { n = c & (TBN - 1); kc = c / TBN; }
+      const int gn = n0 + n;
+      float v[8];
 #pragma unroll
-    for (int nt = 0; nt < 4; ++nt)
+      for (int j = 0; j < 8; ++j) {
+        const int gk = k0 + kc * 8 + j;
+        v[j] = 0.f;
+        if (gn < g.N && gk < kend) v[j] = g.tb ? B[(long long)gn * g.ldb + gk] : B[(long long)gk * g.ldb + gn];
+      }
+      const uint4 q = make_uint4(pack_bf16(v[0], v[1]), pack_bf16(v[2], v[3]), pack_bf16(v[4], v[5]),
+                                 pack_bf16(v[6], v[7]));
+      *reinterpret_cast<uint4*>(sB + ((kc * (TBN / 8) + (n >> 3)) * 8 + (n & 7)) * 16) = q;
+    }
+    // make the generic-proxy stores visible to the tensor core (async proxy)
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    if (tid == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 #pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const int row = m0 + wm * 32 + mt * 16 + grp + h * 8;
-        if (row >= g.M) continue;
+      for (int s = 0; s < TBK / 16; ++s) {
+        const uint64_t ad = smem_desc(smem_u32(sA) + s * 2 * (TBM / 8) * 128, (TBM / 8) * 128, 128);
+        const uint64_t bd = smem_desc(smem_u32(sB) + s * 2 * (TBN / 8) * 128, (TBN / 8) * 128, 128);
+        const uint32_t acc = (k0 > kbeg || s > 0) ? 1u : 0u;
+        asm volatile(
+            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+            " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+            "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+            : "memory");
+      }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar_a)
+                   : "memory");
+    }
+    ok = mbar_wait(mbar_a, phase);
+    phase ^= 1u;
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  }
+  if (!ok) {
+    // give the committed MMAs a second bounded chance before the accumulator is freed
+    if (tid == 0) atomicExch(&g_gemm_timeout, 1);
+    mbar_wait(mbar_a, phase ^ 1u);
+  } else {
+    // epilogue: warp w reads rows 32w + lane, 16 columns per tcgen05.ld (zeros when this
+    // split has no K range: nothing was accumulated)
+    const bool have = kend > kbeg;
+    const int row = m0 + warp * 32 + lane;
 #pragma unroll
-        for (int c = 0; c < 2; ++c) {
-          const int col = n0 + wn * 32 + nt * 8 + tig * 2 + c;
+    for (int c0 = 0; c0 < TBN; c0 += 16) {
+      uint32_t r[16];
+#pragma unroll
+      for (int j = 0; j < 16; ++j) r[j] = 0u;
+      if (have) asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+          : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+            "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+          : "r"(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0));
+      if (have) asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      if (row < g.M) {
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          const int col = n0 + c0 + j;
           if (col >= g.N) continue;
-          const float v = acc[mt][nt][h * 2 + c];
+          const float v = __uint_as_float(r[j]);
           if (ksplit == 1) {
             float* C = g.C + (long long)bz * g.sC + (long long)row * g.ldc + col;
             *C = g.beta == 0.f ? g.alpha * v : g.alpha * v + g.beta * *C;
@@ -125,6 +207,12 @@ __global__ void __launch_bounds__(128) k_gemm(GemmArgs g, int ksplit, float* par
           }
         }
       }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
 }
 
 __global__ void k_gemm_reduce(GemmArgs g, int ksplit, const float* partial) {
@@ -142,14 +230,21 @@ __global__ void k_gemm_reduce(GemmArgs g, int ksplit, const float* partial) {
   }
 }
 
+int gemm_timeouts() {
+  int h = 0, z = 0;
+  if (cudaMemcpyFromSymbol(&h, g_gemm_timeout, sizeof(int)) != cudaSuccess) return -1;
+  if (h) cudaMemcpyToSymbol(g_gemm_timeout, &z, sizeof(int));
+  return h;
+}
+
 // split-K scratch, owned by the caller through net_workspace: set per call
 static thread_local float* g_split_ws = nullptr;
 static thread_local long long g_split_floats = 0;
 
 cudaError_t gemm_bf16(const GemmArgs& g, cudaStream_t s) {
   if (g.M <= 0 || g.N <= 0 || g.batch <= 0) return cudaSuccess;
-  if ((g.M + GBM - 1) / GBM > 65535) {   // grid y is limited to 65535 tiles: chunks of rows
-    const int rows = 65535 * GBM;
+  if ((g.M + TBM - 1) / TBM > 65535) {   // grid y is limited to 65535 tiles: chunks of rows
+    const int rows = 65535 * TBM;
     for (int r0 = 0; r0 < g.M; r0 += rows) {
       GemmArgs h = g;
       h.M = std::min(rows, g.M - r0);
@@ -160,7 +255,7 @@ cudaError_t gemm_bf16(const GemmArgs& g, cudaStream_t s) {
     }
     return cudaSuccess;
   }
-  const int gm = (g.M + GBM - 1) / GBM, gn = (g.N + GBN - 1) / GBN;
+  const int gm = (g.M + TBM - 1) / TBM, gn = (g.N + TBN - 1) / TBN;
   int ksplit = 1;
   const long long tiles = (long long)gm * gn * g.batch;
   if (tiles < 152 && g.K > 2048 && g_split_ws) {
@@ -175,12 +270,12 @@ cudaError_t gemm_bf16(const GemmArgs& g, cudaStream_t s) {
       h.A = g.A + (long long)b0 * g.sA;
       h.B = g.B + (long long)b0 * g.sB;
       h.C = g.C + (long long)b0 * g.sC;
-      k_gemm<<<dim3(gn, gm, h.batch), 128, 0, s>>>(h, 1, nullptr);
+      k_gemm<<<dim3(gn, gm, h.batch), 128, kGemmSmem, s>>>(h, 1, nullptr);
     }
     return cudaGetLastError();
   }
   dim3 grid(gn, gm, g.batch * ksplit);
-  k_gemm<<<grid, 128, 0, s>>>(g, ksplit, g_split_ws);
+  k_gemm<<<grid, 128, kGemmSmem, s>>>(g, ksplit, g_split_ws);
   if (ksplit > 1) {
     const long long total = (long long)g.M * g.N * g.batch;
     const int blocks = (int)std::min<long long>((total + 255) / 256, 152 * 8);

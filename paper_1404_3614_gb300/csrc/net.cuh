@@ -28,8 +28,9 @@ struct NetOffsets {
 NetOffsets net_offsets(const NetConfig& c);
 long long net_workspace_floats(const NetConfig& c, int batch);
 
-// GEMM on the tensor cores: C[b] = alpha * op(A[b]) op(B[b]) + beta * C[b]; A, B, C FP32 in
-// memory, rounded to BF16 when staged, FP32 accumulation. op = transpose when ta/tb.
+// GEMM on the tensor cores (tcgen05.mma, accumulators in tensor memory): C[b] = alpha *
+// op(A[b]) op(B[b]) + beta * C[b]; A, B, C FP32 in memory, rounded to BF16 when staged,
+// FP32 accumulation. op = transpose when ta/tb.
 // A is M x K (row-major with lda) or K x M when ta; B is K x N (ldb) or N x K when tb.
 struct GemmArgs {
   const float* A;
@@ -43,6 +44,9 @@ struct GemmArgs {
   float alpha, beta;
 };
 cudaError_t gemm_bf16(const GemmArgs& g, cudaStream_t s);
+// 1 if a GEMM's bounded wait on its tensor-core completion barrier gave up since the last
+// call (the flag is then cleared), 0 otherwise, -1 if it could not be read. Synchronous.
+int gemm_timeouts();
 
 // forward (keeps activations in ws for a backward when train != 0); out [B*N^d, cout]
 cudaError_t net_forward(const NetConfig& c, const float* params, const float* bases, int B, const float* in,
