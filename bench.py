@@ -45,7 +45,7 @@ FP64_PEAK_TFLOPS = 1.25     # nominal GB300 FP64 (the recipe's table); a probe m
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one k_xpass<double, 81> launch
 # on the 3D N = 41 cube workload (3 fields, isotropic coefficient), from one ncu capture of
 # the build whose kernel sources hash to `sha256_16`; reported only while they still do.
-XPASS_TRAFFIC = {"sha256_16": "5c8136f2de48829d", "bytes": 24164608 + 27648,
+XPASS_TRAFFIC = {"sha256_16": "620b49afa3f0a3e2", "bytes": 24164352 + 28672,
                  "sources": ("common.cuh", "kernels.cuh", "passes.cuh", "passes_f64.cu"),
                  "capture": "profiles/xpass_f64_cube3d_N41.md"}
 
@@ -116,7 +116,7 @@ def run_learned3d(args):
     res = warmstart.train_and_evaluate_3d(N_train=41, N_eval=113, n_train=args.learned_train3d,
                                           n_test=args.learned_test3d, eval_seeds=(0, 1), epochs=args.learned_epochs3d,
                                           batch=8, width=args.learned_width3d, modes=args.learned_modes3d, layers=4,
-                                          proj=64, tol=TOL, precision="mixed", solver=solver)
+                                          proj=64, tol=TOL, precision="mixed", solver=solver, tight_tol=1e-6)
     print(json.dumps({"workload": "3D learned warm start, random-sphere cells, trained at N=41, "
                       "evaluated at N=113 (seed 0 = the 3D sphere workload)", **res}), flush=True)
     solver.close()
@@ -154,6 +154,46 @@ def run_matvec_only(args):
                         precisions=(args.precision,) if args.precision != "mixed" else ("fp32",))
     print(json.dumps({"workload": WORKLOADS[args.workload], "matvec": mv}), flush=True)
     solver.close()
+    return 0
+
+
+def run_gemm_only(args):
+    """The network's tensor-core GEMM alone (for kernel captures and its roofline): a 1x1
+    channel-mixing layer of the 3D network, C = A B with A [M x K] FP32 (M = 2^20 grid points,
+    4 MiB per channel column, larger than L2 at K = 64), B [K x N], `--reps` timed launches."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1404_3614_gb300 as hb
+    M, N, K = 1 << 20, 64, 64
+    g = torch.Generator(device="cuda").manual_seed(0)
+    A = torch.randn((M, K), generator=g, device="cuda")
+    B = torch.randn((K, N), generator=g, device="cuda")
+    C = torch.empty((M, N), device="cuda")
+    ctx = hb.hom_create(0)
+    stream = torch.cuda.current_stream().cuda_stream
+
+    def run():
+        hb.binding.hom_gemm_bf16(ctx, M, N, K, A.data_ptr(), K, 0, B.data_ptr(), N, 0, C.data_ptr(), N, 1.0, 0.0,
+                                 stream)
+    for _ in range(3):
+        run()
+    torch.cuda.synchronize()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    ev[0].record()
+    for _ in range(args.reps):
+        run()
+    ev[1].record()
+    torch.cuda.synchronize()
+    ms = ev[0].elapsed_time(ev[1]) / args.reps
+    ref = (A[:4096].bfloat16().double() @ B.bfloat16().double())
+    err = float((C[:4096].double() - ref).abs().max() / ref.abs().max())
+    hb.hom_destroy(ctx)
+    flops = 2.0 * M * N * K
+    byt = 4.0 * (M * K + K * N + M * N)
+    print(json.dumps({"gemm": {"M": M, "N": N, "K": K, "ms": ms, "tflops": flops / ms / 1e9,
+                               "gbs": byt / ms / 1e6, "hbm_frac": byt / ms / 1e6 / HBM_PEAK_GBS,
+                               "max_rel_err_vs_bf16_products": err}}), flush=True)
     return 0
 
 
@@ -666,6 +706,7 @@ def main():
     ap.add_argument("--learned-test", type=int, default=1024)
     ap.add_argument("--learned-epochs", type=int, default=20)
     ap.add_argument("--learned3d", action="store_true", help="3D learned warm-start workload only")
+    ap.add_argument("--gemm-only", action="store_true", help="the network's tensor-core GEMM alone")
     ap.add_argument("--learned-train3d", type=int, default=1000)
     ap.add_argument("--learned-test3d", type=int, default=16)
     ap.add_argument("--learned-epochs3d", type=int, default=30)
@@ -684,6 +725,8 @@ def main():
         return run_learned(args)
     if args.learned3d:
         return run_learned3d(args)
+    if args.gemm_only:
+        return run_gemm_only(args)
     return run_gpu(args)
 
 
