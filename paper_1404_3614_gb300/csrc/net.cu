@@ -38,9 +38,10 @@ namespace homb {
 constexpr int TBM = 128, TBN = 64, TBK = 64;
 constexpr int kTmemCols = 64;                       // power of two >= 32
 constexpr int kTileABytes = TBM * TBK * 2, kTileBBytes = TBN * TBK * 2;
-// 40 KB of dynamic shared memory: at most 5 CTAs per SM, 5 x 64 <= 512 TMEM columns, so an
-// allocation never waits on a CTA that is not running
-constexpr int kGemmSmem = 40 * 1024;
+// 26 KB of dynamic shared memory: at most 8 CTAs per SM (228 KB), 8 x 64 = 512 TMEM columns,
+// so an allocation never waits on a CTA that is not running
+constexpr int kGemmSmem = 26 * 1024;
+static_assert(kTileABytes + kTileBBytes + 16 <= kGemmSmem, "GEMM tiles exceed the shared-memory request");
 constexpr long long kMbarSpinLimit = 1LL << 22;
 
 __device__ int g_gemm_timeout = 0;   // set when an mbarrier wait gave up
@@ -123,11 +124,18 @@ __global__ void __launch_bounds__(128) k_gemm(GemmArgs g, int ksplit, float* par
       else { r = c & (TBM - 1); kc = c / TBM; }
       const int gm = m0 + r;
       float v[8];
+      const int gk0 = k0 + kc * 8;
+      if (g.vecA && gm < g.M && gk0 + 8 <= kend) {   // two 16-byte loads along K
+        const float4* p = reinterpret_cast<const float4*>(A + (long long)gm * g.lda + gk0);
+        const float4 lo = __ldg(p), hi = __ldg(p + 1);
+        v[0] = lo.x; v[1] = lo.y; v[2] = lo.z; v[3] = lo.w; v[4] = hi.x; v[5] = hi.y; v[6] = hi.z; v[7] = hi.w;
+      } else {
 #pragma unroll
-      for (int j = 0; j < 8; ++j) {
-        const int gk = k0 + kc * 8 + j;
-        v[j] = 0.f;
-        if (gm < g.M && gk < kend) v[j] = g.ta ? A[(long long)gk * g.lda + gm] : A[(long long)gm * g.lda + gk];
+        for (int j = 0; j < 8; ++j) {
+          const int gk = gk0 + j;
+          v[j] = 0.f;
+          if (gm < g.M && gk < kend) v[j] = g.ta ? A[(long long)gk * g.lda + gm] : A[(long long)gm * g.lda + gk];
+        }
       }
       const uint4 q = make_uint4(pack_bf16(v[0], v[1]), pack_bf16(v[2], v[3]), pack_bf16(v[4], v[5]),
                                  pack_bf16(v[6], v[7]));
@@ -194,16 +202,30 @@ __global__ void __launch_bounds__(128) k_gemm(GemmArgs g, int ksplit, float* par
           : "r"(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0));
       if (have) asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
       if (row < g.M) {
+        if (ksplit == 1 && g.vecC && n0 + c0 + 16 <= g.N) {   // four 16-byte stores
+          float4* C = reinterpret_cast<float4*>(g.C + (long long)bz * g.sC + (long long)row * g.ldc + n0 + c0);
 #pragma unroll
-        for (int j = 0; j < 16; ++j) {
-          const int col = n0 + c0 + j;
-          if (col >= g.N) continue;
-          const float v = __uint_as_float(r[j]);
-          if (ksplit == 1) {
-            float* C = g.C + (long long)bz * g.sC + (long long)row * g.ldc + col;
-            *C = g.beta == 0.f ? g.alpha * v : g.alpha * v + g.beta * *C;
-          } else {
-            partial[(((long long)ks * g.batch + bz) * g.M + row) * g.N + col] = v;
+          for (int q = 0; q < 4; ++q) {
+            float4 o = make_float4(g.alpha * __uint_as_float(r[4 * q]), g.alpha * __uint_as_float(r[4 * q + 1]),
+                                   g.alpha * __uint_as_float(r[4 * q + 2]), g.alpha * __uint_as_float(r[4 * q + 3]));
+            if (g.beta != 0.f) {
+              const float4 c = C[q];
+              o.x += g.beta * c.x; o.y += g.beta * c.y; o.z += g.beta * c.z; o.w += g.beta * c.w;
+            }
+            C[q] = o;
+          }
+        } else {
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            const int col = n0 + c0 + j;
+            if (col >= g.N) continue;
+            const float v = __uint_as_float(r[j]);
+            if (ksplit == 1) {
+              float* C = g.C + (long long)bz * g.sC + (long long)row * g.ldc + col;
+              *C = g.beta == 0.f ? g.alpha * v : g.alpha * v + g.beta * *C;
+            } else {
+              partial[(((long long)ks * g.batch + bz) * g.M + row) * g.N + col] = v;
+            }
           }
         }
       }
@@ -241,8 +263,12 @@ int gemm_timeouts() {
 static thread_local float* g_split_ws = nullptr;
 static thread_local long long g_split_floats = 0;
 
-cudaError_t gemm_bf16(const GemmArgs& g, cudaStream_t s) {
-  if (g.M <= 0 || g.N <= 0 || g.batch <= 0) return cudaSuccess;
+cudaError_t gemm_bf16(const GemmArgs& g0, cudaStream_t s) {
+  if (g0.M <= 0 || g0.N <= 0 || g0.batch <= 0) return cudaSuccess;
+  GemmArgs g = g0;
+  auto al16 = [](const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; };
+  g.vecA = !g.ta && g.lda % 4 == 0 && g.sA % 4 == 0 && al16(g.A);
+  g.vecC = g.ldc % 4 == 0 && g.sC % 4 == 0 && al16(g.C);
   if ((g.M + TBM - 1) / TBM > 65535) {   // grid y is limited to 65535 tiles: chunks of rows
     const int rows = 65535 * TBM;
     for (int r0 = 0; r0 < g.M; r0 += rows) {

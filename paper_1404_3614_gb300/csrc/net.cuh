@@ -42,6 +42,7 @@ struct GemmArgs {
   long long sA, sB, sC;   // batch strides
   int batch;
   float alpha, beta;
+  int vecA, vecC;         // set by gemm_bf16: 16-byte vector loads of A rows / stores of C rows
 };
 cudaError_t gemm_bf16(const GemmArgs& g, cudaStream_t s);
 // 1 if a GEMM's bounded wait on its tensor-core completion barrier gave up since the last
