@@ -61,6 +61,10 @@ class Problem:
     # (i_1, ..., i_d) covers prod_a (-Y_a/2 + i_a h_a, -Y_a/2 + (i_a + 1) h_a), h_a = Y_a / P_a,
     # and holds the conductivity a (A = a I there). When set, A0 and inclusions are unused.
     bitmap: np.ndarray = None
+    # where GaNi samples a grid point lying exactly on an inclusion boundary: False puts it in
+    # the matrix (strict membership, the paper's Eq. S and S1), True in the inclusion
+    # (non-strict, Eq. S2). Galerkin with exact integration does not depend on it.
+    closed: bool = False
 
     @property
     def M(self) -> np.ndarray:
@@ -128,6 +132,13 @@ def cube_inclusion_3d(N=41, side=0.5, a_matrix=1.0, a_incl=100.0) -> Problem:
 def paper_square_2d(N, rho) -> Problem:
     """Cell (-1, 1)^2 with A = (1 + rho f) I and f the indicator of |x_a| < 3/5 (Sec. 7)."""
     return make_problem(2, N, 2.0, 1.0, [box(0.0, 1.2, 1.0 + rho, 2)])
+
+
+def paper_square_even_2d(N, rho, closed=False) -> Problem:
+    """Cell (-1, 1)^2 with A = (1 + rho f) I and f the indicator of |x_a| < 3/4 (Eq. S1,
+    closed=False) or |x_a| <= 3/4 (Eq. S2, closed=True), the even-grid cells of Sec. 7."""
+    p = make_problem(2, N, 2.0, 1.0, [box(0.0, 1.5, 1.0 + rho, 2)])
+    return dataclasses.replace(p, closed=bool(closed))
 
 
 def laminate_2d(N, width=0.4, a_matrix=1.0, a_incl=10.0, Y=1.0) -> Problem:

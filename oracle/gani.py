@@ -9,7 +9,8 @@ paper's algorithm (Sec. 6.2, steps (i)-(iii), Eq. GaNi_bounds) evaluate the GaNi
 in the exactly integrated (double-grid) forms of Lemma double-grid.
 
 Sampling reading: a grid point on an inclusion's boundary belongs to the matrix (strict
-inequalities, as in Eq. S and Eq. S1 of the numerical examples), with periodic images.
+inequalities, as in Eq. S and Eq. S1 of the numerical examples), with periodic images; a
+problem marked `closed` puts it in the inclusion (non-strict, Eq. S2).
 
 Everything is dense and in the Fourier basis (tiny grids): for trigonometric polynomials on
 Z_N, a_N(u, v) = v_hat^H K_N u_hat with K_N[(l, a), (k, b)] = A_N_hat_ab(l - k mod N), the
@@ -57,16 +58,18 @@ def grid_points(problem: Problem) -> np.ndarray:
     return k * (Y / np.asarray(N, dtype=np.float64))
 
 
-def _inside(inc, x: np.ndarray, Y: np.ndarray) -> np.ndarray:
-    """Strict membership of the points x [..., d] in the inclusion (periodic images)."""
+def _inside(inc, x: np.ndarray, Y: np.ndarray, closed: bool = False) -> np.ndarray:
+    """Membership of the points x [..., d] in the inclusion (periodic images): strict, or
+    non-strict when `closed`."""
     dx = x - np.asarray(inc.center, dtype=np.float64)
     dx = dx - Y * np.round(dx / Y)
+    lt = np.less_equal if closed else np.less
     if inc.shape == BOX:
         ins = np.ones(x.shape[:-1], dtype=bool)
         for a in range(x.shape[-1]):
-            ins &= np.abs(dx[..., a]) < 0.5 * inc.size[a]
+            ins &= lt(np.abs(dx[..., a]), 0.5 * inc.size[a])
         return ins
-    return np.sqrt(np.sum(dx * dx, axis=-1)) < inc.size[0]
+    return lt(np.sqrt(np.sum(dx * dx, axis=-1)), inc.size[0])
 
 
 def sample_coefficient(problem: Problem, side: str = "primal") -> np.ndarray:
@@ -83,7 +86,7 @@ def sample_coefficient(problem: Problem, side: str = "primal") -> np.ndarray:
         return np.linalg.inv(A) if side == "dual" else A
     A = np.broadcast_to(np.asarray(problem.A0, dtype=np.float64), x.shape[:-1] + (d, d)).copy()
     for inc in problem.inclusions:
-        A[_inside(inc, x, Y)] = np.asarray(inc.A, dtype=np.float64)
+        A[_inside(inc, x, Y, bool(getattr(problem, "closed", False)))] = np.asarray(inc.A, dtype=np.float64)
     if side == "dual":
         A = np.linalg.inv(A)
     return A

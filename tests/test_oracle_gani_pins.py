@@ -203,3 +203,23 @@ def test_even_grid_points_and_homogeneous_cell():
     out = gani.gani_bounds(hom)
     for key in ("A_HN", "upper", "lower"):
         assert np.abs(out[key] - A0).max() < 1e-13
+
+
+def test_closed_and_open_inclusions_on_even_grids():
+    """The paper's S1 (|x| < 3/4) and S2 (|x| <= 3/4) cells: on grids whose points avoid the
+    interface (N = 4: x in {-1, -1/2, 0, 1/2}) they are the same GaNi problem; for N = 8 the
+    points x = +-3/4 lie on it, S2 puts them in the inclusion, so its GaNi homogenized matrix
+    is larger (Loewner order: more stiff samples) and both keep B^-1 <= A. The Galerkin bounds
+    do not depend on the choice."""
+    for rho in (10.0, 1000.0):
+        s1, s2 = ms.paper_square_even_2d(4, rho), ms.paper_square_even_2d(4, rho, closed=True)
+        a, b = gani.gani_bounds(s1), gani.gani_bounds(s2)
+        assert np.abs(a["A_HN"] - b["A_HN"]).max() < 1e-13
+        s1, s2 = ms.paper_square_even_2d(8, rho), ms.paper_square_even_2d(8, rho, closed=True)
+        assert gani.sample_coefficient(s2)[..., 0, 0].sum() > gani.sample_coefficient(s1)[..., 0, 0].sum()
+        a, b = gani.gani_bounds(s1), gani.gani_bounds(s2)
+        assert b["A_HN"][0, 0] > a["A_HN"][0, 0] * (1 + 1e-3)
+        for o in (a, b):
+            assert loewner_ge(o["A_HN"], np.linalg.inv(o["B_HN"]), 1e-10)
+        g1, g2 = dense.dense_bounds(s1.with_N(7)), dense.dense_bounds(s2.with_N(7))
+        assert np.abs(g1["upper"] - g2["upper"]).max() < 1e-13
