@@ -120,7 +120,10 @@ typedef struct {
                                   pixel boxes (Remark "inclusion"). Read during the
                                   call only.                                     */
   int32_t bitmap_n[3];         /* P_a, a < d (1 for unused axes)                 */
-  int32_t reserved2;
+  int32_t closed;               /* GaNi sampling of a grid point exactly on an
+                                  inclusion boundary: 0 matrix (strict membership,
+                                  the paper's Eq. S, S1), 1 inclusion (Eq. S2). The
+                                  Galerkin discretization does not depend on it.  */
 } hom_problem;
 
 typedef struct {

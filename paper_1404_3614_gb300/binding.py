@@ -37,7 +37,7 @@ class hom_inclusion(C.Structure):
 class hom_problem(C.Structure):
     _fields_ = [("d", C.c_int32), ("N", C.c_int32 * 3), ("Y", C.c_double * 3), ("A0", C.c_double * 9),
                 ("n_incl", C.c_int32), ("reserved", C.c_int32), ("incl", C.POINTER(hom_inclusion)),
-                ("bitmap", C.POINTER(C.c_double)), ("bitmap_n", C.c_int32 * 3), ("reserved2", C.c_int32)]
+                ("bitmap", C.POINTER(C.c_double)), ("bitmap_n", C.c_int32 * 3), ("closed", C.c_int32)]
 
 
 class hom_opts(C.Structure):
@@ -181,6 +181,7 @@ def problem_struct(problem):
         keep.append(img)
     else:
         p.bitmap_n[:] = [1, 1, 1]
+    p.closed = 1 if getattr(problem, "closed", False) else 0
     return p, keep
 
 

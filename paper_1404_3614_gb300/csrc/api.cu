@@ -142,6 +142,7 @@ struct Geometry {
   int P[3] = {1, 1, 1};
   FftPlan pplan[3];            // DFT plans of the image lengths
   uint64_t bitmap_hash = 0;
+  int closed = 0;              // GaNi: boundary grid points belong to the inclusion (Eq. S2)
   long long npix() const { return (long long)P[0] * P[1] * P[2]; }
 };
 
@@ -250,6 +251,8 @@ hom_status build_geometry(hom_ctx* ctx, const hom_problem* P, Geometry& g) {
   }
   g.Nh = (g.N[0] + 1) / 2;
   g.Nxs = (g.M[0] + 1) / 2;
+  if (P->closed != 0 && P->closed != 1) return fail(ctx, HOM_ERR_INVALID_ARG, "closed must be 0 or 1");
+  g.closed = P->closed;
   if (P->bitmap) {
     if (P->n_incl != 0) return fail(ctx, HOM_ERR_INVALID_ARG, "a pixel image excludes inclusions");
     long long n = 1;
@@ -477,6 +480,7 @@ struct Runner {
     push(g.Y, sizeof g.Y);
     push(g.A0, sizeof g.A0);
     push(&g.ncomp, sizeof g.ncomp);
+    push(&g.closed, sizeof g.closed);
     if (!g.incl.empty()) push(g.incl.data(), g.incl.size() * sizeof(hom_inclusion));
     if (!g.bitmap.empty()) {
       push(&g.bitmap_hash, sizeof g.bitmap_hash);
@@ -552,6 +556,7 @@ struct Runner {
     a.Nmod[1] = g.M[1];
     a.Nmod[2] = g.M[2];
     a.invVol = 1.0 / (g.Y[0] * g.Y[1] * g.Y[2]);
+    a.closed = g.closed;
     double C0[9], A0f[9];
     for (int i = 0; i < 3; ++i)
       for (int j = 0; j < 3; ++j) A0f[3 * i + j] = g.A0[i][j];

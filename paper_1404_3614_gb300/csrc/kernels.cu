@@ -304,7 +304,8 @@ __global__ void k_promote_add(const float2* x32, double2* x64, long long n) {
 // GaNi coefficient (Def. GaNi, Eq. grid_points): the side's coefficient sampled at the grid
 // points x_k = k_a Y_a / N_a of the M = N grid (FFT storage order), packed symmetric
 // [q][j3][j2][j1]. A point on an inclusion boundary belongs to the matrix (strict
-// inequalities), with periodic images; the dual side samples the pointwise inverse.
+// inequalities, Eq. S1), or to the inclusion when the problem is closed (Eq. S2), with
+// periodic images; the dual side samples the pointwise inverse.
 __global__ void k_sample_coef(SpecArgs a, double* coef) {
   const long long grid = (long long)a.M[0] * a.M[1] * a.M[2];
   for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < grid;
@@ -336,10 +337,10 @@ __global__ void k_sample_coef(SpecArgs a, double* coef) {
         const double Yc = 1.0 / a.invY[c];
         double dx = x[c] - I.c[c];
         dx -= Yc * rint(dx * a.invY[c]);
-        if (I.shape == 0) in = in && fabs(dx) < 0.5 * I.h[c];
+        if (I.shape == 0) in = in && (a.closed ? fabs(dx) <= 0.5 * I.h[c] : fabs(dx) < 0.5 * I.h[c]);
         r2 += dx * dx;
       }
-      if (I.shape != 0) in = sqrt(r2) < I.h[0];
+      if (I.shape != 0) in = a.closed ? sqrt(r2) <= I.h[0] : sqrt(r2) < I.h[0];
       if (in)
         for (int q = 0; q < a.ncomp; ++q) v[q] = a.A0p[q] + I.dA[q];
     }

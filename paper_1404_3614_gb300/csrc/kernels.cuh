@@ -106,6 +106,7 @@ struct SpecArgs {
   const double* bitmap;   // pixel image ([P3][P2][P1], x fastest) or NULL
   int P[3];
   int invert;             // dual side of an image: 1 / a
+  int closed;             // GaNi sampling: boundary points belong to the inclusion
 };
 
 // One batched 2D task: a (problem, side) pair solved entirely by one CTA of the

@@ -132,3 +132,24 @@ def test_even_grid_rejections(hb, solver):
         solver(p, precision=hb.HOM_MIXED)
     with pytest.raises(hb.HombError):
         solver.batched([p])
+
+
+@pytest.mark.parametrize("N", [8, 16])
+@pytest.mark.parametrize("rho", [10.0, 1000.0])
+def test_paper_even_cells_s1_s2(hb, solver, N, rho):
+    """The paper's even-grid cells S1 (|x| < 3/4) and S2 (|x| <= 3/4) under GaNi: both match
+    the oracle; their GaNi matrices differ (interface points at x = +-3/4), the Galerkin
+    bounds of the two descriptions are the same."""
+    out = {}
+    for closed in (False, True):
+        p = ms.paper_square_even_2d(N, rho, closed=closed)
+        ref = gani.gani_bounds(p)
+        o = solver(p, precision=hb.HOM_FP64, tol=1e-12, discretization=1)
+        assert rel(o["gani_A"], ref["A_HN"]) <= 1e-10
+        assert rel(o["gani_B"], ref["B_HN"]) <= 1e-10
+        for key in ("upper", "lower"):
+            assert rel(o[key], ref[key]) <= 1e-10, key
+        out[closed] = o
+    assert out[True]["gani_A"][0, 0] > out[False]["gani_A"][0, 0] * (1 + 1e-4)
+    ga = [solver(ms.paper_square_even_2d(N, rho, closed=c), precision=hb.HOM_FP64, tol=1e-12) for c in (False, True)]
+    assert rel(ga[0]["upper"], ga[1]["upper"]) <= 1e-12
