@@ -153,3 +153,19 @@ def test_paper_even_cells_s1_s2(hb, solver, N, rho):
     assert out[True]["gani_A"][0, 0] > out[False]["gani_A"][0, 0] * (1 + 1e-4)
     ga = [solver(ms.paper_square_even_2d(N, rho, closed=c), precision=hb.HOM_FP64, tol=1e-12) for c in (False, True)]
     assert rel(ga[0]["upper"], ga[1]["upper"]) <= 1e-12
+
+
+def test_paper_even_grid_bounds_at_n1024(hb, solver):
+    """The GaNi-field bounds of the paper's even-grid cells S1 and S2 at n = 1024, rho = 10^3
+    against the values the paper's source keeps beside Fig. even_comparison (golden file,
+    with its citation and reading): agreement to 1e-7 relative at CG tolerance 1e-8."""
+    import json
+    import os
+    gold = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_even_grid_bounds_n1024.json")))
+    for cell, closed in (("S1", False), ("S2", True)):
+        p = ms.paper_square_even_2d(gold["n"], gold["rho"], closed=closed)
+        out = solver(p, precision=hb.HOM_FP64, tol=1e-8, discretization=1)
+        for key in ("upper", "lower"):
+            ref = gold[f"{cell}_{key}"]
+            assert abs(out[key][0, 0] - ref) <= 1e-7 * ref, (cell, key, out[key][0, 0], ref)
+            assert abs(out[key][0, 1]) <= 1e-9 * ref and abs(out[key][1, 1] - out[key][0, 0]) <= 1e-9 * ref
