@@ -157,6 +157,36 @@ def run_matvec_only(args):
     return 0
 
 
+def run_paper_grids(args):
+    """The paper's square-inclusion study (Sec. 7, Eqs. S, S1, S2): for each contrast, the
+    Galerkin (exact integration) bounds, the GaNi homogenized matrices A_{H,N}, B_{H,N}^{-1}
+    and the bounds of the GaNi fields, on odd grids n = 5 3^j (cell S) and on even grids
+    n = 2^j (cells S1 and S2). FP64, tol 1e-8. One JSON line per (cell, contrast, n)."""
+    import numpy as np
+    import __graft_entry__
+    __graft_entry__.build()
+    import microstructures as ms
+    import paper_1404_3614_gb300 as hb
+    solver = hb.Bounds(0)
+    cases = [("S", False, n) for n in (5, 15, 45, 135, 405)] + \
+            [(c, c == "S2", n) for n in (4, 8, 16, 32, 64, 128, 256, 512) for c in ("S1", "S2")]
+    for rho in (10.0, 1000.0):
+        for cell, closed, n in cases:
+            p = ms.paper_square_2d(n, rho) if cell == "S" else ms.paper_square_even_2d(n, rho, closed=closed)
+            t0 = time.perf_counter()
+            ga = solver(p, precision=hb.HOM_FP64, tol=1e-8)
+            gn = solver(p, precision=hb.HOM_FP64, tol=1e-8, discretization=1)
+            print(json.dumps({"cell": cell, "rho": rho, "n": n,
+                              "ga_upper": ga["upper"][0, 0], "ga_lower": ga["lower"][0, 0],
+                              "gani_A": gn["gani_A"][0, 0], "gani_invB": float(np.linalg.inv(gn["gani_B"])[0, 0]),
+                              "gani_upper": gn["upper"][0, 0], "gani_lower": gn["lower"][0, 0],
+                              "iters_ga": int(np.asarray(ga["report"]["iters"]).sum()),
+                              "iters_gani": int(np.asarray(gn["report"]["iters"]).sum()),
+                              "s": time.perf_counter() - t0}), flush=True)
+    solver.close()
+    return 0
+
+
 def run_gemm_only(args):
     """The network's tensor-core GEMM alone (for kernel captures and its roofline): a 1x1
     channel-mixing layer of the 3D network, C = A B with A [M x K] FP32 (M = 2^20 grid points,
@@ -707,6 +737,8 @@ def main():
     ap.add_argument("--learned-epochs", type=int, default=20)
     ap.add_argument("--learned3d", action="store_true", help="3D learned warm-start workload only")
     ap.add_argument("--gemm-only", action="store_true", help="the network's tensor-core GEMM alone")
+    ap.add_argument("--paper-grids", action="store_true",
+                    help="the paper's square-inclusion study on odd and even grids (Ga and GaNi)")
     ap.add_argument("--learned-train3d", type=int, default=1000)
     ap.add_argument("--learned-test3d", type=int, default=16)
     ap.add_argument("--learned-epochs3d", type=int, default=30)
@@ -727,6 +759,8 @@ def main():
         return run_learned3d(args)
     if args.gemm_only:
         return run_gemm_only(args)
+    if args.paper_grids:
+        return run_paper_grids(args)
     return run_gpu(args)
 
 
