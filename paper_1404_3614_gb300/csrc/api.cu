@@ -233,7 +233,24 @@ void make_plan(int M, FftPlan& p) {
     while (m % r == 0 && p.nrad < kMaxRadices) { p.radix[p.nrad++] = r; m /= r; }
 }
 
-hom_status build_geometry(hom_ctx* ctx, const hom_problem* P, Geometry& g) {
+// Smallest odd M >= m whose prime factors are all radices with butterflies (3, 5, 7, 11,
+// 13). The double-grid quadrature (Lemma double-grid) stays exact on any odd M >= 2N - 1:
+// the Galerkin entries need A_hat(k - j) for |k - j| <= N - 1, all inside Z_M without
+// aliasing, and the grid of M points integrates A_M u v exactly. A length like 809 (prime)
+// would otherwise run as one O(M^2) generic radix.
+int smooth_odd_at_least(int m) {
+  for (int c = m | 1;; c += 2) {
+    int r = c;
+    for (int p : {3, 5, 7, 11, 13})
+      while (r % p == 0) r /= p;
+    if (r == 1) return c;
+  }
+}
+
+// smooth_M: the whole-pipeline calls (hom_bounds, hom_bounds_batched) take the smallest
+// smooth odd double grid >= 2N - 1; the step-level calls keep M = 2N - 1 (their coefficient
+// and grid layouts are part of the ABI).
+hom_status build_geometry(hom_ctx* ctx, const hom_problem* P, Geometry& g, bool smooth_M = false) {
   if (!P) return fail(ctx, HOM_ERR_INVALID_ARG, "problem is NULL");
   if (P->d != 2 && P->d != 3) return fail(ctx, HOM_ERR_INVALID_ARG, "d must be 2 or 3");
   g.d = P->d;
@@ -247,6 +264,7 @@ hom_status build_geometry(hom_ctx* ctx, const hom_problem* P, Geometry& g) {
       if (!(g.Y[a] > 0) || !std::isfinite(g.Y[a])) return fail(ctx, HOM_ERR_INVALID_ARG, "cell sizes Y must be > 0");
     }
     g.M[a] = 2 * g.N[a] - 1;
+    if (smooth_M && a < g.d) g.M[a] = smooth_odd_at_least(g.M[a]);
     g.invY[a] = 1.0 / g.Y[a];
   }
   g.Nh = (g.N[0] + 1) / 2;
@@ -1196,7 +1214,7 @@ hom_status build_batch(hom_ctx* ctx, int n, const hom_problem* probs, const hom_
   };
   for (int i = 0; i < n; ++i) {
     Geometry g;
-    CKS(build_geometry(ctx, &probs[i], g));
+    CKS(build_geometry(ctx, &probs[i], g, true));
     if (g.d != 2) return fail(ctx, HOM_ERR_INVALID_ARG, "hom_bounds_batched handles two-dimensional cells (d = 2)");
     if (g.even) return fail(ctx, HOM_ERR_INVALID_ARG, "hom_bounds_batched handles odd grids");
     if (!g.bitmap.empty()) return fail(ctx, HOM_ERR_INVALID_ARG, "hom_bounds_batched takes inclusion cells, not images");
@@ -1368,7 +1386,7 @@ hom_status hom_workspace_size(hom_ctx* ctx, const hom_problem* prob, const hom_o
                               size_t* bytes) {
   if (!ctx || !opts || !bytes) return fail(ctx, HOM_ERR_INVALID_ARG, "NULL argument");
   Geometry g;
-  CKS(build_geometry(ctx, prob, g));
+  CKS(build_geometry(ctx, prob, g, true));
   const size_t elem = opts->precision == HOM_MIXED ? 8 : 16;
   *bytes = make_layout(g, g.d, elem, 0).total;
   if (opts->discretization == 1) *bytes = align256(*bytes) + make_layout(gani_geometry(g), g.d, 16, 0).total;
@@ -1394,7 +1412,7 @@ static hom_status bounds_impl(hom_ctx* ctx, const hom_problem* prob, const hom_o
   ctx->launches = ctx->h2d = ctx->d2h = 0;
   CKS(set_device(ctx));
   Geometry g;
-  CKS(build_geometry(ctx, prob, g));
+  CKS(build_geometry(ctx, prob, g, true));
   if (opts->precision != HOM_FP64 && opts->precision != HOM_MIXED)
     return fail(ctx, HOM_ERR_INVALID_ARG, "precision must be HOM_FP64 or HOM_MIXED");
   const size_t elem = opts->precision == HOM_MIXED ? 8 : 16;
