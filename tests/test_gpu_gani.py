@@ -168,4 +168,5 @@ def test_paper_even_grid_bounds_at_n1024(hb, solver):
         for key in ("upper", "lower"):
             ref = gold[f"{cell}_{key}"]
             assert abs(out[key][0, 0] - ref) <= 1e-7 * ref, (cell, key, out[key][0, 0], ref)
-            assert abs(out[key][0, 1]) <= 1e-9 * ref and abs(out[key][1, 1] - out[key][0, 0]) <= 1e-9 * ref
+            # isotropic cell: the second right-hand side gives the same value to the CG tolerance
+            assert abs(out[key][0, 1]) <= 1e-9 * ref and abs(out[key][1, 1] - out[key][0, 0]) <= 1e-7 * ref
