@@ -143,6 +143,11 @@ struct Geometry {
   FftPlan pplan[3];            // DFT plans of the image lengths
   uint64_t bitmap_hash = 0;
   int closed = 0;              // GaNi: boundary grid points belong to the inclusion (Eq. S2)
+  // GaNi on the double grid (an N without a fast FFT length): the GaNi matrix as the Galerkin
+  // operator of the periodized sample spectrum; nplan are the N-point DFT plans of the samples
+  bool gani_dg = false;
+  FftPlan nplan[3];
+  long long nsamp() const { return (long long)N[0] * N[1] * N[2]; }
   long long npix() const { return (long long)P[0] * P[1] * P[2]; }
 };
 
@@ -350,6 +355,7 @@ struct Layout {
       cg[2], cgo[2], partial, epart, eout, total;
   size_t bmp = 0, bmpD[2] = {0, 0}, bmptw[3] = {0, 0, 0};   // pixel image, its DFT buffers, twiddles
   size_t rrpart = 0;                                         // Rayleigh-Ritz partial sums
+  size_t gs = 0, gD[2] = {0, 0}, gtw[3] = {0, 0, 0};         // GaNi samples, their DFT, twiddles
   int Mmax, maxblk, nblk_energy;
   size_t off = 0;
   size_t take(size_t bytes) {
@@ -382,6 +388,12 @@ Layout make_layout(const Geometry& g, int R, size_t elem, int mode) {
     L.bmpD[0] = L.take((size_t)g.npix() * 16);
     L.bmpD[1] = L.take((size_t)g.npix() * 16);
     for (int a = 0; a < 3; ++a) L.bmptw[a] = L.take((size_t)g.P[a] * 16);
+  }
+  if (g.gani_dg) {
+    L.gs = L.take((size_t)g.ncomp * g.nsamp() * 8);
+    L.gD[0] = L.take((size_t)g.nsamp() * 16);
+    L.gD[1] = L.take((size_t)g.nsamp() * 16);
+    for (int a = 0; a < 3; ++a) L.gtw[a] = L.take((size_t)g.N[a] * 16);
   }
   const long long RC = (long long)R * g.d;
   const size_t spec_b = (size_t)g.ncomp * g.spec * 16;
@@ -499,6 +511,8 @@ struct Runner {
     push(g.A0, sizeof g.A0);
     push(&g.ncomp, sizeof g.ncomp);
     push(&g.closed, sizeof g.closed);
+    push(&g.gani_dg, sizeof g.gani_dg);
+    push(g.M, sizeof g.M);
     if (!g.incl.empty()) push(g.incl.data(), g.incl.size() * sizeof(hom_inclusion));
     if (!g.bitmap.empty()) {
       push(&g.bitmap_hash, sizeof g.bitmap_hash);
@@ -515,6 +529,13 @@ struct Runner {
         CK(h2d_copy(ctx, base + L.bmptw[a], w64.data(), w64.size() * sizeof(double2), st));
       }
     }
+    if (g.gani_dg)
+      for (int a = 0; a < 3; ++a) {
+        std::vector<double2> w64;
+        std::vector<float2> w32;
+        twiddles(g.N[a], w64, w32);
+        CK(h2d_copy(ctx, base + L.gtw[a], w64.data(), w64.size() * sizeof(double2), st));
+      }
     std::vector<double2> w64;
     std::vector<float2> w32;
     for (int a = 0; a < 3; ++a) {
@@ -597,13 +618,14 @@ struct Runner {
   // Unnormalised DFT of the pixel image (or of 1 / a) into L.bmpD[0], layout [P3][P2][P1]:
   // a transform along the contiguous axis, then a rotation that makes the next axis
   // contiguous, three times.
-  hom_status bitmap_dft(int side) {
-    double2* D0 = at<double2>(L.bmpD[0]);
-    double2* D1 = at<double2>(L.bmpD[1]);
-    KL(launch_bitmap_load(at<double>(L.bmp), D0, g.npix(), side, st));
-    int P0 = g.P[0], P1 = g.P[1], P2 = g.P[2];
+  // Unnormalised forward DFT of a [P2][P1][P0] complex grid (x fastest) in place in D0:
+  // along x, then two axis rotations with the next axis' DFT, a third rotation back.
+  hom_status dft3(double2* D0, double2* D1, const int* P, const FftPlan* plans, const size_t* tw) {
+    double2* const out = D0;
+    int P0 = P[0], P1 = P[1], P2 = P[2];
+    const long long n = (long long)P0 * P1 * P2;
     for (int step = 0; step < 3; ++step) {
-      if (P0 > 1) KL(launch_fft_batch<double>(D0, D0, P0, P1 * P2, -1, base + L.bmptw[step], g.pplan[step], st));
+      if (P0 > 1) KL(launch_fft_batch<double>(D0, D0, P0, P1 * P2, -1, base + tw[step], plans[step], st));
       KL(launch_rotate3(D0, D1, P0, P1, P2, st));
       std::swap(D0, D1);
       const int t = P0;
@@ -611,9 +633,14 @@ struct Runner {
       P1 = P2;
       P2 = t;
     }
-    if (D0 != at<double2>(L.bmpD[0]))   // three swaps: the result is in bmpD[1]
-      CK(cudaMemcpyAsync(at<double2>(L.bmpD[0]), D0, (size_t)g.npix() * 16, cudaMemcpyDeviceToDevice, st));
+    if (D0 != out)   // three swaps: the result is in the other buffer
+      CK(cudaMemcpyAsync(out, D0, (size_t)n * 16, cudaMemcpyDeviceToDevice, st));
     return HOM_OK;
+  }
+
+  hom_status bitmap_dft(int side) {
+    KL(launch_bitmap_load(at<double>(L.bmp), at<double2>(L.bmpD[0]), g.npix(), side, st));
+    return dft3(at<double2>(L.bmpD[0]), at<double2>(L.bmpD[1]), g.P, g.pplan, L.bmptw);
   }
 
   hom_status build_coefficient(int side, double* coef) {
@@ -628,6 +655,34 @@ struct Runner {
                             st));
       KL(launch_spectrum(sa, S, st));
     }
+    return coefficient_from_spectrum(coef);
+  }
+
+  // GaNi matrix on the double grid: K_N[l, k] = A_hat_N(l - k mod N) (Lemma FD_of_GaNi) with
+  // A_hat_N the N-point DFT (1/|N|) of the grid samples; for |l - k| <= N - 1 and an odd
+  // M >= 2N - 1 these are the Galerkin entries of the coefficient whose spectrum on Z_M is
+  // the N-periodic extension of A_hat_N, so the double-grid passes apply the GaNi operator
+  // exactly, with fast lengths M even when N is prime.
+  hom_status gani_coefficient_dg(int side, double* coef) {
+    Prof pr(ctx, "coef", st);
+    SpecArgs sn = spec_args(side);
+    for (int k = 0; k < 3; ++k) sn.M[k] = k < g.d ? g.N[k] : 1;
+    KL(launch_sample_coef(sn, at<double>(L.gs), st));
+    const SpecArgs sa = spec_args(side);
+    double2* S = at<double2>(L.t1);
+    const long long total = (long long)sa.len[0] * sa.len[1] * sa.len[2];
+    const double scale = 1.0 / (double)g.nsamp();
+    for (int q = 0; q < g.ncomp; ++q) {
+      KL(launch_bitmap_load(at<double>(L.gs) + q * g.nsamp(), at<double2>(L.gD[0]), g.nsamp(), 0, st));
+      CKS(dft3(at<double2>(L.gD[0]), at<double2>(L.gD[1]), g.N, g.nplan, L.gtw));
+      KL(launch_periodic_spectrum(sa, at<double2>(L.gD[0]), S + q * total, g.N, scale, st));
+    }
+    return coefficient_from_spectrum(coef);
+  }
+
+  // A_M(x) = sum over Z_M of the half spectrum in t1 (inverse passes z, y, then the rows)
+  hom_status coefficient_from_spectrum(double* coef) {
+    double2* S = at<double2>(L.t1);
     // 3D: z pass t1 -> t2, y pass t2 -> t1, rows from t1; 2D: y pass t1 -> t2, rows from t2
     const void* cur = S;
     void* nxt = at<void>(L.t2);
@@ -941,6 +996,7 @@ struct Runner {
 
   // GaNi coefficient: the side's coefficient sampled at the grid points (Def. GaNi)
   hom_status sample_coefficient(int side, double* coef) {
+    if (g.gani_dg) return gani_coefficient_dg(side, coef);
     Prof pr(ctx, "coef", st);
     KL(launch_sample_coef(spec_args(side), coef, st));
     return HOM_OK;
@@ -1369,8 +1425,22 @@ hom_status hom_problem_info(hom_ctx* ctx, const hom_problem* prob, int32_t* ncom
 }
 
 // the N-grid geometry of GaNi: transform lengths M = N, coefficient sampled on the N grid
+// GaNi geometry: the N grid itself when every N_a factors into radices 2, 3, 5, 7, 11, 13;
+// else the (smooth) double grid of g with the GaNi matrix built as a periodized spectrum
 Geometry gani_geometry(const Geometry& g) {
   Geometry n = g;
+  bool fast = true;
+  for (int a = 0; a < g.d; ++a) {
+    int r = g.N[a];
+    for (int p : {2, 3, 5, 7, 11, 13})
+      while (r % p == 0) r /= p;
+    fast = fast && r == 1;
+  }
+  if (!fast) {
+    n.gani_dg = true;
+    for (int a = 0; a < 3; ++a) make_plan(a < g.d ? g.N[a] : 1, n.nplan[a]);
+    return n;
+  }
   for (int a = 0; a < 3; ++a) n.M[a] = a < g.d ? g.N[a] : 1;
   n.Nxs = (n.M[0] + 1) / 2;
   n.planes = (long long)n.M[1] * n.M[2];

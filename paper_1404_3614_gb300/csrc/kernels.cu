@@ -401,6 +401,27 @@ __global__ void k_bitmap_spectrum(SpecArgs a, const double2* D, double2* S) {
   }
 }
 
+// Half spectrum on Z_M (layout of k_spectrum) of the N-periodic extension of a DFT D of
+// N-grid samples ([N2][N1][N0], x fastest): S(n) = scale * D(n mod N).
+__global__ void k_periodic_spectrum(SpecArgs a, const double2* D, double2* S, int N0, int N1, int N2, double scale) {
+  const long long n = (long long)a.len[0] * a.len[1] * a.len[2];
+  const int Nn[3] = {N0, N1, N2};
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+    const int i0 = (int)(e % a.len[0]);
+    const int i1 = (int)((e / a.len[0]) % a.len[1]);
+    const int i2 = (int)(e / ((long long)a.len[0] * a.len[1]));
+    const int ns[3] = {i0, sfreq(i1, a.Nmod[1]), sfreq(i2, a.Nmod[2])};
+    long long idx = 0;
+    for (int c = a.d - 1; c >= 0; --c) {
+      int m = ns[c] % Nn[c];
+      if (m < 0) m += Nn[c];
+      idx = idx * Nn[c] + m;
+    }
+    const double2 dv = D[idx];
+    S[e] = make_double2(scale * dv.x, scale * dv.y);
+  }
+}
+
 // Rayleigh-Ritz on span{x}: per right-hand side the partial sums of x.b and x.q (q = C x),
 // Hermitian weights, rows [rhs][2][nblk]
 template <typename T>
@@ -724,6 +745,13 @@ cudaError_t launch_rotate3(const double2* in, double2* out, int P0, int P1, int 
   k_rotate3<<<grid_blocks((long long)P0 * P1 * P2), kThreads, 0, s>>>(in, out, P0, P1, P2);
   return cudaGetLastError();
 }
+cudaError_t launch_periodic_spectrum(const SpecArgs& a, const double2* D, double2* S, const int* N, double scale,
+                                     cudaStream_t s) {
+  const long long n = (long long)a.len[0] * a.len[1] * a.len[2];
+  k_periodic_spectrum<<<grid_blocks(n), kThreads, 0, s>>>(a, D, S, N[0], N[1], N[2], scale);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_bitmap_spectrum(const SpecArgs& a, const double2* D, double2* S, cudaStream_t s) {
   k_bitmap_spectrum<<<grid_blocks((long long)a.len[0] * a.len[1] * a.len[2]), kThreads, 0, s>>>(a, D, S);
   return cudaGetLastError();

@@ -222,6 +222,9 @@ cudaError_t launch_rotate3(const double2* in, double2* out, int P0, int P1, int 
 // spectrum of a pixel image on the half of Z_M (layout of launch_spectrum, one component) from
 // the unnormalised DFT D of the image values ([P3][P2][P1], x fastest)
 cudaError_t launch_bitmap_spectrum(const SpecArgs& a, const double2* D, double2* S, cudaStream_t s);
+// S(n) = scale * D(n mod N) on the half of Z_M (N-periodic extension of an N-point DFT)
+cudaError_t launch_periodic_spectrum(const SpecArgs& a, const double2* D, double2* S, const int* N, double scale,
+                                     cudaStream_t s);
 // r = -r with |r|^2 partials [nrhs][nblk]
 template <typename T>
 cudaError_t launch_negate_norm(void* r, int nrhs, int C, long long field, int Nh, double* partial, int nblk,

@@ -170,3 +170,31 @@ def test_paper_even_grid_bounds_at_n1024(hb, solver):
             assert abs(out[key][0, 0] - ref) <= 1e-7 * ref, (cell, key, out[key][0, 0], ref)
             # isotropic cell: the second right-hand side gives the same value to the CG tolerance
             assert abs(out[key][0, 1]) <= 1e-9 * ref and abs(out[key][1, 1] - out[key][0, 0]) <= 1e-7 * ref
+
+
+# GaNi for grids without a fast FFT length (a prime factor above 13): the GaNi matrix is
+# applied on the smooth double grid as the Galerkin operator of the N-periodic sample spectrum
+PRIME = {
+    "square2d_N17": lambda: ms.square_inclusion_2d(N=17),
+    "aniso2d_N19x9": lambda: ms.random_anisotropic_2d(3, N=7).with_N((19, 9)),
+    "rect2d_N34x5": lambda: ms.random_rectangles_2d(4, N=11).with_N((34, 5)),
+    "paper_rho100_N17": lambda: ms.paper_square_2d(17, 100.0),
+    "aniso3d_N3x5x17": lambda: ms.random_anisotropic_3d(4, N=5).with_N((3, 5, 17)),
+    "image_P17_N17": lambda: ms.bitmap_problem(np.where(np.random.default_rng(9).uniform(size=(17, 17)) < 0.4,
+                                                        0.029, 0.49)),
+}
+
+
+@pytest.mark.parametrize("name", list(PRIME))
+def test_gani_prime_lengths_match_oracle(hb, solver, name):
+    p = PRIME[name]()
+    ref = gani.gani_bounds(p)
+    out = solver(p, precision=hb.HOM_FP64, tol=1e-12, discretization=1)
+    assert rel(out["gani_A"], ref["A_HN"]) <= 1e-10, (out["gani_A"], ref["A_HN"])
+    assert rel(out["gani_B"], ref["B_HN"]) <= 1e-10
+    for key in ("upper", "lower"):
+        assert rel(out[key], ref[key]) <= 1e-10, key
+    if all(int(n) % 2 for n in p.N):
+        assert rel(np.linalg.inv(out["gani_B"]), out["gani_A"]) <= 1e-9
+    warm = solver(p, precision=hb.HOM_FP64, tol=1e-10, discretization=1, dual_start=1)
+    assert rel(warm["lower"], out["lower"]) <= 1e-8
