@@ -45,7 +45,7 @@ FP64_PEAK_TFLOPS = 1.25     # nominal GB300 FP64 (the recipe's table); a probe m
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one k_xpass<double, 81> launch
 # on the 3D N = 41 cube workload (3 fields, isotropic coefficient), from one ncu capture of
 # the build whose kernel sources hash to `sha256_16`; reported only while they still do.
-XPASS_TRAFFIC = {"sha256_16": "620b49afa3f0a3e2", "bytes": 24164352 + 28672,
+XPASS_TRAFFIC = {"sha256_16": "1aec6da91d95b115", "bytes": 24164864 + 35840, "fp64_pipe_active": 0.8375,
                  "sources": ("common.cuh", "kernels.cuh", "passes.cuh", "passes_f64.cu"),
                  "capture": "profiles/xpass_f64_cube3d_N41.md"}
 
@@ -542,6 +542,10 @@ def run_gpu(args):
             roof["traffic_note"] = ("ncu DRAM bytes per launch (" + XPASS_TRAFFIC["capture"] + "): the "
                                     "input fields and coefficient are read once; the in-place output "
                                     "stays in L2 during the launch")
+            # the same capture: the FP64 pipe is busy this fraction of the active cycles; the
+            # conventional 5 M log2 M flop count undercounts an add-heavy radix-3 FFT, so frac
+            # reads well below the pipe's own occupancy
+            roof["fp64_pipe_active_ncu"] = XPASS_TRAFFIC["fp64_pipe_active"]
 
     line = {
         "metric": METRIC, "value": ms_step, "unit": "ms", "n_gpus": world, "steps": args.steps,
