@@ -116,7 +116,7 @@ def run_learned3d(args):
     res = warmstart.train_and_evaluate_3d(N_train=41, N_eval=113, n_train=args.learned_train3d,
                                           n_test=args.learned_test3d, eval_seeds=(0, 1), epochs=args.learned_epochs3d,
                                           batch=8, width=args.learned_width3d, modes=args.learned_modes3d, layers=4,
-                                          proj=64, tol=TOL, precision="mixed", solver=solver, tight_tol=1e-6)
+                                          proj=64, tol=TOL, precision="mixed", solver=solver, tight_tol=1e-8)
     print(json.dumps({"workload": "3D learned warm start, random-sphere cells, trained at N=41, "
                       "evaluated at N=113 (seed 0 = the 3D sphere workload)", **res}), flush=True)
     solver.close()
