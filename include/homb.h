@@ -151,8 +151,12 @@ typedef struct {
                            1 GaNi, the paper's algorithm (Sec. 6.2): CG on the N grid
                            with the coefficient sampled at the grid points (Def.
                            GaNi; a point on an inclusion boundary belongs to the
-                           matrix), then the double-grid energies of those
-                           minimisers give the bounds (Eq. GaNi_bounds). FP64 only.*/
+                           matrix unless hom_problem.closed), then the double-grid
+                           energies of those minimisers give the bounds (Eq.
+                           GaNi_bounds). When an N_a has a prime factor above 13 the
+                           GaNi matrix is applied on the double grid instead (the
+                           same operator, fast FFT lengths). FP64 or mixed; no
+                           starting / output fields.                             */
 } hom_opts;
 
 typedef struct {

@@ -1105,7 +1105,8 @@ hom_status Runner_solve_mixed(Runner& run, int side, const hom_opts& o, hom_repo
   cudaStream_t st = run.st;
   unsigned char* base = run.base;
   double* coef64 = run.at<double>(L.coef64);
-  CKS(run.build_coefficient(side, coef64));
+  if (run.gani) CKS(run.sample_coefficient(side, coef64));
+  else CKS(run.build_coefficient(side, coef64));
   KL(launch_convert_d2f(coef64, run.at<float>(L.coef32), (long long)g.ncomp * g.grid, st));
   const float* coef32 = run.at<float>(L.coef32);
   const long long n = (long long)R * g.d * g.field;
@@ -1119,10 +1120,10 @@ hom_status Runner_solve_mixed(Runner& run, int side, const hom_opts& o, hom_repo
   double* partial = run.at<double>(L.partial);
   const double tol = o.tol > 0 ? o.tol : 1e-8;
   const int nfin32 = run.final_blocks(8), nfin64 = run.final_blocks(16);
-  // b in FP64: closed form, or for a pixel image the operator applied to the constant
-  // field (x = 0 taken from `zero`), negated
+  // b in FP64: closed form, or for a pixel image and for GaNi the operator applied to the
+  // constant field (x = 0 taken from `zero`), negated
   auto form_rhs = [&](double2* zero) -> hom_status {
-    if (g.bitmap.empty()) {
+    if (g.bitmap.empty() && !run.gani) {
       KL(launch_rhs<double>(sa, side, R, g.Nh, N3, b64, partial, kVecBlocks, st));
     } else {
       CK(cudaMemsetAsync(zero, 0, n * sizeof(double2), st));
@@ -1459,7 +1460,7 @@ hom_status hom_workspace_size(hom_ctx* ctx, const hom_problem* prob, const hom_o
   CKS(build_geometry(ctx, prob, g, true));
   const size_t elem = opts->precision == HOM_MIXED ? 8 : 16;
   *bytes = make_layout(g, g.d, elem, 0).total;
-  if (opts->discretization == 1) *bytes = align256(*bytes) + make_layout(gani_geometry(g), g.d, 16, 0).total;
+  if (opts->discretization == 1) *bytes = align256(*bytes) + make_layout(gani_geometry(g), g.d, elem, 0).total;
   return HOM_OK;
 }
 
@@ -1489,7 +1490,6 @@ static hom_status bounds_impl(hom_ctx* ctx, const hom_problem* prob, const hom_o
   if (opts->discretization != 0 && opts->discretization != 1)
     return fail(ctx, HOM_ERR_INVALID_ARG, "discretization must be 0 (Ga) or 1 (GaNi)");
   const bool gani = opts->discretization == 1;
-  if (gani && opts->precision != HOM_FP64) return fail(ctx, HOM_ERR_INVALID_ARG, "GaNi runs in FP64");
   if (g.even && opts->precision != HOM_FP64) return fail(ctx, HOM_ERR_INVALID_ARG, "even grids run in FP64");
   if (gani && io && (io->d_x0 || io->d_fields))
     return fail(ctx, HOM_ERR_INVALID_ARG, "starting / output fields are for the Galerkin discretization");
@@ -1497,7 +1497,7 @@ static hom_status bounds_impl(hom_ctx* ctx, const hom_problem* prob, const hom_o
              static_cast<cudaStream_t>(stream), g.d};
   const Geometry gn = gani ? gani_geometry(g) : g;
   const size_t gani_off = align256(run.L.total);
-  Runner rn{ctx, gn, gani ? make_layout(gn, g.d, 16, 0) : Layout{}, static_cast<unsigned char*>(d_ws) + gani_off,
+  Runner rn{ctx, gn, gani ? make_layout(gn, g.d, elem, 0) : Layout{}, static_cast<unsigned char*>(d_ws) + gani_off,
             static_cast<cudaStream_t>(stream), g.d};
   rn.gani = true;
   const size_t need = gani ? gani_off + rn.L.total : run.L.total;
@@ -1515,9 +1515,10 @@ static hom_status bounds_impl(hom_ctx* ctx, const hom_problem* prob, const hom_o
     if (gani) {
       // the paper's algorithm (Sec. 6.2): GaNi minimisers on the N grid, then their exactly
       // integrated energies on the double grid (Eq. GaNi_bounds)
-      double2* x0 = rn.at<double2>(rn.L.q);
+      double2* x0 = elem == 16 ? rn.at<double2>(rn.L.q) : rn.at<double2>(rn.L.b64);
       if (side == 1 && (sides & 3) == 3 && opts->dual_start == 1) CKS(rn.dual_start(x0, &warm, &matvecs));
-      hom_status s = rn.solve_side<double>(side, *opts, rep, &matvecs, warm ? x0 : nullptr);
+      hom_status s = elem == 16 ? rn.solve_side<double>(side, *opts, rep, &matvecs, warm ? x0 : nullptr)
+                                : Runner_solve_mixed(rn, side, *opts, rep, &matvecs, warm, false);
       if (s < 0) return s;
       if (s == HOM_WARN_NOT_CONVERGED) worst = s;
       double* coef64 = run.at<double>(run.L.coef64);

@@ -80,9 +80,34 @@ def test_gani_dual_start_is_exact(hb, solver, name):
     assert np.array_equal(warm["upper"], zero["upper"])
 
 
-def test_gani_rejects_mixed_precision(hb, solver):
+@pytest.mark.parametrize("name", ["square2d_N15", "aniso2d_N7", "cube3d_N9", "spheres3d_N7", "paper_rho100_N15"])
+def test_gani_mixed_precision(hb, solver, name):
+    """GaNi with the FP32 inner CG and FP64 refinement, GaNi matrices and bounds: within 1e-6
+    of the oracle; with the dual start too."""
+    p = CELLS[name]()
+    ref = gani.gani_bounds(p)
+    out = solver(p, precision=hb.HOM_MIXED, tol=1e-7, discretization=1)
+    assert rel(out["gani_A"], ref["A_HN"]) <= 1e-6
+    assert rel(out["gani_B"], ref["B_HN"]) <= 1e-6
+    for key in ("upper", "lower"):
+        assert rel(out[key], ref[key]) <= 1e-6, key
+    warm = solver(p, precision=hb.HOM_MIXED, tol=1e-7, discretization=1, dual_start=1)
+    assert rel(warm["lower"], ref["lower"]) <= 1e-6
+
+
+@pytest.mark.parametrize("name", ["square2d_N17", "aniso3d_N3x5x17"])
+def test_gani_mixed_precision_prime_lengths(hb, solver, name):
+    p = PRIME[name]()
+    ref = gani.gani_bounds(p)
+    out = solver(p, precision=hb.HOM_MIXED, tol=1e-7, discretization=1)
+    assert rel(out["gani_A"], ref["A_HN"]) <= 1e-6
+    for key in ("upper", "lower"):
+        assert rel(out[key], ref[key]) <= 1e-6, key
+
+
+def test_gani_mixed_rejects_even_grids(hb, solver):
     with pytest.raises(hb.HombError):
-        solver(ms.square_inclusion_2d(N=9), precision=hb.HOM_MIXED, discretization=1)
+        solver(ms.square_inclusion_2d(N=9).with_N(8), precision=hb.HOM_MIXED, discretization=1)
 
 
 # ---- general (even) grids -------------------------------------------------------------
