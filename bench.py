@@ -463,16 +463,27 @@ def run_gpu(args):
     ms_step = statistics.mean(times)
     ms_step = max_over_ranks(ms_step, world, dev)
 
-    # end to end through the public API: host problem in, host bounds out, wall clock
+    # end to end through the public API: host problem in, host bounds out, wall clock. Two
+    # workspaces alternate, as for two requests in flight, so every step uploads its problem
+    # tables (inclusions, twiddles) from the host again instead of finding them resident.
+    opts_e2e = hb.make_opts(prec, TOL)
+    nbytes = hb.hom_workspace_size(solver.ctx, problem, opts_e2e)
+    wss = [torch.empty(nbytes, dtype=torch.uint8, device=dev) for _ in range(2)]
+
+    def step_e2e(i):
+        return hb.hom_bounds(solver.ctx, problem, opts_e2e, wss[i % 2].data_ptr(), nbytes, s_ptr)
+    for i in range(2 * args.warmup):
+        step_e2e(i)
     e2e = []
-    for _ in range(max(3, args.steps // 2)):
+    for i in range(max(4, args.steps // 2)):
         flush.zero_()
         torch.cuda.synchronize()
         t = time.perf_counter()
-        o = step(prec)
+        o = step_e2e(i)
         e2e.append((time.perf_counter() - t) * 1e3)
     e2e_ms = max_over_ranks(statistics.mean(e2e), world, dev)
     rep = o["report"]
+    del wss
 
     # the other precision on the same workload (plain FP64 vs mixed)
     other = hb.HOM_MIXED if prec == hb.HOM_FP64 else hb.HOM_FP64
@@ -565,7 +576,8 @@ def run_gpu(args):
         "gpu_launches": launches,
         "e2e": {"value": e2e_ms, "unit": "ms", "h2d_bytes_per_step": rep["h2d_bytes"],
                 "d2h_bytes_per_step": rep["d2h_bytes"],
-                "note": "hom_bounds wall clock: host problem in, host bounds out"},
+                "note": "hom_bounds wall clock: host problem in (tables uploaded every step, two workspaces "
+                        "alternating), host bounds out"},
         "alt_precision": {"precision": "mixed" if other == hb.HOM_MIXED else "fp64", "ms": alt_ms,
                           "speedup_vs_this": ms_step / alt_ms if alt_ms > 0 else None,
                           "upper_11": float(oo["upper"][0, 0]), "lower_11": float(oo["lower"][0, 0])},
