@@ -395,6 +395,9 @@ hom_status hom_matvec_noalloc(hom_ctx* ctx, const hom_problem* prob, int32_t sid
                               int32_t precision, int32_t project, int32_t nrhs,
                               const void* d_coef, const void* d_in, void* d_out, void* stream);
 
+/* Tuning: pencils per CTA of the operator's y passes and planes per CTA of its row pass
+ * (0: automatic, the shared-memory budget's maximum; larger requests are capped to it). */
+hom_status hom_set_pass_chunks(hom_ctx* ctx, int32_t ypass_pencils, int32_t xpass_planes);
 /* The 3D operator with an isotropic coefficient and equal x and y transform lengths
  * M = R * R (R in 3, 5, 9, 15) fuses the inverse y transforms, the x row pass and the
  * forward y transforms into one pass over (rhs, component, z) slabs held in shared memory

@@ -110,6 +110,7 @@ def _load():
         "hom_energy": (i32, [vp, P(hom_problem), i32, i32, vp, vp, dp, vp, sz, vp]),
         "hom_fft": (i32, [vp, i32, i32, i32, i32, vp, vp, vp, sz, vp]),
         "hom_matvec_noalloc": (i32, [vp, P(hom_problem), i32, i32, i32, i32, vp, vp, vp, vp]),
+        "hom_set_pass_chunks": (i32, [vp, i32, i32]),
         "hom_set_slab_pass": (i32, [vp, i32]),
         "hom_set_batch_threads": (i32, [vp, i32]),
         "hom_set_batch_cluster": (i32, [vp, i32, i32]),
@@ -369,6 +370,11 @@ def hom_set_batch_threads(ctx, threads):
 
 def hom_set_batch_cluster(ctx, cluster, coop_min_M=0):
     return check(ctx, lib.hom_set_batch_cluster(ctx, int(cluster), int(coop_min_M)))
+
+
+def hom_set_pass_chunks(ctx, ypass_pencils=0, xpass_planes=0):
+    """Pencils per CTA of the operator's y passes and planes per CTA of its row pass (0: auto)."""
+    return check(ctx, lib.hom_set_pass_chunks(ctx, ypass_pencils, xpass_planes))
 
 
 def hom_set_slab_pass(ctx, enable):

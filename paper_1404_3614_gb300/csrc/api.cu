@@ -66,6 +66,8 @@ struct hom_ctx {
   bool graphs_off = false;
   bool slab_on = true;   // fused y-x-y slab pass where it applies
   int slab_warps = 0;     // warps per slab CTA chosen by the caller (0: automatic)
+  int ypass_xc = 0;       // pencils per CTA of the operator's y passes (0: automatic)
+  int xpass_yb = 0;       // planes per CTA of the operator's row pass (0: automatic)
   std::vector<long long> graph_key;
   struct Tuned { long long key; int cap, threads, sched, cluster, coopM; };
   std::vector<Tuned> tuned_cap;
@@ -483,6 +485,11 @@ struct Prof {
   }
 };
 
+// a caller's chunk size (hom_set_pass_chunks) within the shared-memory maximum
+static int chunk(int automatic, int requested) {
+  return requested > 0 && automatic > 0 ? std::min(automatic, requested) : automatic;
+}
+
 struct Runner {
   hom_ctx* ctx;
   const Geometry& g;
@@ -765,7 +772,7 @@ struct Runner {
       PencilArgs y{};
       y.in = ycur; y.out = T2; y.aux = g.d == 3 ? nullptr : r_aux;
       y.in_slab = (long long)Ny * Nh; y.out_slab = (long long)My * Nh;
-      y.nslab = R * C * Mz; y.X = Nh; y.XC = pencil_xc<T>(My, Nh, 1);
+      y.nslab = R * C * Mz; y.X = Nh; y.XC = chunk(pencil_xc<T>(My, Nh, 1), ctx->ypass_xc);
       y.Pin = Ny; y.Pout = My; y.Nlog = Ny; y.dir = +1;
       y.slabs_per_rhs = C * Mz; y.slabs_per_comp = Mz; y.C = C;
       y.prologue = g.d == 3 ? 0 : prologue;
@@ -777,7 +784,7 @@ struct Runner {
       Prof pr(ctx, "xpass", st);
       XArgs x{};
       x.in = T2; x.out = T2; x.coef = coef; x.mode = 0;
-      x.planes = (int)g.planes; x.YB = xpass_yb<T>(Mx, C, (int)g.planes);
+      x.planes = (int)g.planes; x.YB = chunk(xpass_yb<T>(Mx, C, (int)g.planes), ctx->xpass_yb);
       x.Nin = Nh; x.Nout = Nh; x.M = Mx; x.R = R; x.C = C; x.ncomp = g.ncomp; x.d = g.d;
       x.comp_stride = g.planes * Nh; x.scale = 1.0 / (double)g.grid;
       x.W = W(0); x.plan = g.plan[0]; x.cg = cg; x.partial = nullptr;
@@ -789,7 +796,7 @@ struct Runner {
       PencilArgs y{};
       y.in = T2; y.out = T1; y.aux = nullptr;
       y.in_slab = (long long)My * Nh; y.out_slab = (long long)Ny * Nh;
-      y.nslab = R * C * Mz; y.X = Nh; y.XC = pencil_xc<T>(My, Nh, 1);
+      y.nslab = R * C * Mz; y.X = Nh; y.XC = chunk(pencil_xc<T>(My, Nh, 1), ctx->ypass_xc);
       y.Pin = My; y.Pout = Ny; y.Nlog = Ny; y.dir = -1;
       y.slabs_per_rhs = C * Mz; y.slabs_per_comp = Mz; y.C = C; y.prologue = 0;
       y.W = W(1); y.plan = g.plan[1]; y.cg = cg;
@@ -889,8 +896,9 @@ struct Runner {
       return HOM_OK;
     }
     std::vector<unsigned char> key = ctx->tables_key;
-    const long long extra[8] = {(long long)side, (long long)sizeof(T), K, (long long)(uintptr_t)coefT,
-                                (long long)(uintptr_t)cg, (long long)L.total, R, nfin};
+    const long long extra[10] = {(long long)side, (long long)sizeof(T), K, (long long)(uintptr_t)coefT,
+                                 (long long)(uintptr_t)cg, (long long)L.total, R, nfin, ctx->ypass_xc,
+                                 ctx->xpass_yb};
     const unsigned char* eb = reinterpret_cast<const unsigned char*>(extra);
     key.insert(key.end(), eb, eb + sizeof extra);
     key.insert(key.end(), ctx->prof_family.begin(), ctx->prof_family.end());
@@ -2091,6 +2099,14 @@ hom_status hom_set_slab_pass(hom_ctx* ctx, int32_t enable) {
     return fail(ctx, HOM_ERR_INVALID_ARG, "slab pass: 0 (off), 1 (automatic) or 4..24 warps in steps of 4");
   ctx->slab_on = enable != 0;
   ctx->slab_warps = enable > 1 ? enable : 0;
+  return HOM_OK;
+}
+
+hom_status hom_set_pass_chunks(hom_ctx* ctx, int32_t ypass_pencils, int32_t xpass_planes) {
+  if (!ctx) return HOM_ERR_INVALID_ARG;
+  if (ypass_pencils < 0 || xpass_planes < 0) return fail(ctx, HOM_ERR_INVALID_ARG, "chunk sizes must be >= 0");
+  ctx->ypass_xc = ypass_pencils;
+  ctx->xpass_yb = xpass_planes;
   return HOM_OK;
 }
 
