@@ -476,6 +476,26 @@ template <typename T> int pencil_xc(int M, int X, int C) {
     const long long nch = (X + xc - 1) / xc;
     xc = (X + nch - 1) / nch;
   }
+  if (xc > 1 && !warp_fft_len<T>(M)) {
+    // among balanced chunk sizes, the fewest thread rounds per radix stage over all chunks
+    // (each CTA does xc * C * M / r butterflies per stage on kPassThreads threads, r the
+    // smallest radix), plus half a round of fixed work per CTA; ties keep the larger chunk
+    int r = 2;
+    while (r < M && M % r) ++r;
+    const long long bfl = (long long)(M / r) * C;
+    double best = 1e300;
+    long long bx = xc;
+    for (long long c = xc; c >= 1; --c) {
+      const long long nch = (X + c - 1) / c;
+      if ((X + nch - 1) / nch != c) continue;
+      const double cost = (double)nch * ((double)((c * bfl + kPassThreads - 1) / kPassThreads) + 0.5);
+      if (cost < best - 1e-9) {
+        best = cost;
+        bx = c;
+      }
+    }
+    xc = bx;
+  }
   return (int)xc;
 }
 
