@@ -42,6 +42,8 @@ constexpr int kTileABytes = TBM * TBK * 2, kTileBBytes = TBN * TBK * 2;
 // so an allocation never waits on a CTA that is not running
 constexpr int kGemmSmem = 26 * 1024;
 static_assert(kTileABytes + kTileBBytes + 16 <= kGemmSmem, "GEMM tiles exceed the shared-memory request");
+static_assert(TBM * 36 * 4 <= kTileABytes + kTileBBytes, "the result staging must fit in the operand tiles");
+static_assert(TBN % 32 == 0, "the staged epilogue works in 32-column halves");
 constexpr long long kMbarSpinLimit = 1LL << 22;
 
 __device__ int g_gemm_timeout = 0;   // set when an mbarrier wait gave up
@@ -177,7 +179,7 @@ __global__ void __launch_bounds__(128) k_gemm(GemmArgs g, int ksplit, float* par
       asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar_a)
                    : "memory");
     }
-    ok = mbar_wait(mbar_a, phase);
+    ok = __syncthreads_and(mbar_wait(mbar_a, phase) ? 1 : 0) != 0;   // one verdict for the CTA
     phase ^= 1u;
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   }
@@ -185,6 +187,54 @@ __global__ void __launch_bounds__(128) k_gemm(GemmArgs g, int ksplit, float* par
     // give the committed MMAs a second bounded chance before the accumulator is freed
     if (tid == 0) atomicExch(&g_gemm_timeout, 1);
     mbar_wait(mbar_a, phase ^ 1u);
+  } else if (ksplit == 1 && g.vecC) {
+    // epilogue through shared memory (the operand tiles are free: the MMAs have completed):
+    // per 32-column half, each warp writes its 32 accumulator rows, then the CTA stores whole
+    // 128-byte row segments (8 threads per row, 16-byte accesses); row stride 36 floats keeps
+    // both phases free of bank conflicts
+    const bool have = kend > kbeg;
+    float* Cs = reinterpret_cast<float*>(smem);
+    const int lrow = warp * 32 + lane;
+    for (int h = 0; h < TBN / 32; ++h) {
+#pragma unroll
+      for (int c = 0; c < 32; c += 16) {
+        uint32_t r[16];
+#pragma unroll
+        for (int j = 0; j < 16; ++j) r[j] = 0u;
+        if (have) asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+              "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+            : "r"(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(h * 32 + c)));
+        if (have) asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        float4* dst = reinterpret_cast<float4*>(Cs + lrow * 36 + c);
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          dst[q] = make_float4(__uint_as_float(r[4 * q]), __uint_as_float(r[4 * q + 1]),
+                               __uint_as_float(r[4 * q + 2]), __uint_as_float(r[4 * q + 3]));
+      }
+      __syncthreads();
+      for (int idx = tid; idx < TBM * 8; idx += 128) {
+        const int rr = idx >> 3, q = idx & 7;
+        const int row = m0 + rr, col = n0 + h * 32 + 4 * q;
+        if (row >= g.M || col >= g.N) continue;
+        const float4 v = *reinterpret_cast<const float4*>(Cs + rr * 36 + 4 * q);
+        float* C = g.C + (long long)bz * g.sC + (long long)row * g.ldc + col;
+        if (col + 4 <= g.N) {
+          float4 o = make_float4(g.alpha * v.x, g.alpha * v.y, g.alpha * v.z, g.alpha * v.w);
+          if (g.beta != 0.f) {
+            const float4 c4 = *reinterpret_cast<const float4*>(C);
+            o.x += g.beta * c4.x; o.y += g.beta * c4.y; o.z += g.beta * c4.z; o.w += g.beta * c4.w;
+          }
+          *reinterpret_cast<float4*>(C) = o;
+        } else {
+          const float vv[4] = {v.x, v.y, v.z, v.w};
+          for (int e = 0; e < 4 && col + e < g.N; ++e)
+            C[e] = g.beta == 0.f ? g.alpha * vv[e] : g.alpha * vv[e] + g.beta * C[e];
+        }
+      }
+      __syncthreads();
+    }
   } else {
     // epilogue: warp w reads rows 32w + lane, 16 columns per tcgen05.ld (zeros when this
     // split has no K range: nothing was accumulated)
@@ -202,30 +252,16 @@ __global__ void __launch_bounds__(128) k_gemm(GemmArgs g, int ksplit, float* par
           : "r"(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0));
       if (have) asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
       if (row < g.M) {
-        if (ksplit == 1 && g.vecC && n0 + c0 + 16 <= g.N) {   // four 16-byte stores
-          float4* C = reinterpret_cast<float4*>(g.C + (long long)bz * g.sC + (long long)row * g.ldc + n0 + c0);
 #pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            float4 o = make_float4(g.alpha * __uint_as_float(r[4 * q]), g.alpha * __uint_as_float(r[4 * q + 1]),
-                                   g.alpha * __uint_as_float(r[4 * q + 2]), g.alpha * __uint_as_float(r[4 * q + 3]));
-            if (g.beta != 0.f) {
-              const float4 c = C[q];
-              o.x += g.beta * c.x; o.y += g.beta * c.y; o.z += g.beta * c.z; o.w += g.beta * c.w;
-            }
-            C[q] = o;
-          }
-        } else {
-#pragma unroll
-          for (int j = 0; j < 16; ++j) {
-            const int col = n0 + c0 + j;
-            if (col >= g.N) continue;
-            const float v = __uint_as_float(r[j]);
-            if (ksplit == 1) {
-              float* C = g.C + (long long)bz * g.sC + (long long)row * g.ldc + col;
-              *C = g.beta == 0.f ? g.alpha * v : g.alpha * v + g.beta * *C;
-            } else {
-              partial[(((long long)ks * g.batch + bz) * g.M + row) * g.N + col] = v;
-            }
+        for (int j = 0; j < 16; ++j) {
+          const int col = n0 + c0 + j;
+          if (col >= g.N) continue;
+          const float v = __uint_as_float(r[j]);
+          if (ksplit == 1) {
+            float* C = g.C + (long long)bz * g.sC + (long long)row * g.ldc + col;
+            *C = g.beta == 0.f ? g.alpha * v : g.alpha * v + g.beta * *C;
+          } else {
+            partial[(((long long)ks * g.batch + bz) * g.M + row) * g.N + col] = v;
           }
         }
       }
