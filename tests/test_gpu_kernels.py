@@ -237,3 +237,36 @@ def test_slab_pass_matches_separate_passes(hb, ctx, N, prec):
             assert relerr(out[side, 1], out[side, 0]) < tol, (N, prec, side, relerr(out[side, 1], out[side, 0]))
     finally:
         hb.hom_set_slab_pass(ctx, 1)
+
+
+@pytest.mark.parametrize("N,prec", [(41, "fp64"), (23, "fp64"), (41, "fp32")])
+def test_pass_chunks_do_not_change_the_operator(hb, ctx, N, prec):
+    """hom_set_pass_chunks only regroups pencils and planes into CTAs: every pencil is
+    transformed by the same arithmetic, so the operator output is bitwise the same."""
+    p = ms.random_spheres_3d(3, N=N, n_balls=5, phi=0.2, contrast=100.0)
+    d = 3
+    rng = np.random.default_rng([zlib.crc32(b"chunks"), N])
+    info = hb.hom_problem_info(ctx, p)
+    nws = hb.hom_step_workspace_size(ctx, p, d)
+    ws = torch.empty(nws, dtype=torch.uint8, device="cuda")
+    precision = hb.HOM_FP64 if prec == "fp64" else hb.HOM_FP32
+    cdt = torch.complex128 if prec == "fp64" else torch.complex64
+    rdt = torch.float64 if prec == "fp64" else torch.float32
+    Nh = (N + 1) // 2
+    x = torch.from_numpy(rng.normal(size=(d, d, N, N, Nh)) + 1j * rng.normal(size=(d, d, N, N, Nh))).to(cdt).cuda()
+    coef = torch.empty((info["ncomp"],) + tuple(info["M"][:d][::-1]), dtype=rdt, device="cuda")
+    hb.hom_coefficient(ctx, p, 0, precision, coef.data_ptr(), ws.data_ptr(), nws)
+    outs = []
+    try:
+        for yc, yb in ((0, 0), (1, 1), (3, 5), (7, 10), (100, 100)):
+            hb.binding.hom_set_pass_chunks(ctx, yc, yb)
+            y = torch.zeros_like(x)
+            hb.hom_matvec(ctx, p, 0, precision, 1, d, coef.data_ptr(), x.data_ptr(), y.data_ptr(), ws.data_ptr(), nws)
+            torch.cuda.synchronize()
+            outs.append(y.cpu().numpy())
+        for o in outs[1:]:
+            assert np.array_equal(o, outs[0])
+        with pytest.raises(hb.HombError):
+            hb.binding.hom_set_pass_chunks(ctx, -1, 0)
+    finally:
+        hb.binding.hom_set_pass_chunks(ctx, 0, 0)
