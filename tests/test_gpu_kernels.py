@@ -241,8 +241,9 @@ def test_slab_pass_matches_separate_passes(hb, ctx, N, prec):
 
 @pytest.mark.parametrize("N,prec", [(41, "fp64"), (23, "fp64"), (41, "fp32")])
 def test_pass_chunks_do_not_change_the_operator(hb, ctx, N, prec):
-    """hom_set_pass_chunks only regroups pencils and planes into CTAs: every pencil is
-    transformed by the same arithmetic, so the operator output is bitwise the same."""
+    """hom_set_pass_chunks only regroups pencils and planes into CTAs. The y-pass pencils keep
+    their arithmetic; the row pass packs two real rows per complex FFT, and the partner row
+    changes with the plane count, so results agree to rounding (1e-13 FP64, 2e-6 FP32)."""
     p = ms.random_spheres_3d(3, N=N, n_balls=5, phi=0.2, contrast=100.0)
     d = 3
     rng = np.random.default_rng([zlib.crc32(b"chunks"), N])
@@ -264,8 +265,9 @@ def test_pass_chunks_do_not_change_the_operator(hb, ctx, N, prec):
             hb.hom_matvec(ctx, p, 0, precision, 1, d, coef.data_ptr(), x.data_ptr(), y.data_ptr(), ws.data_ptr(), nws)
             torch.cuda.synchronize()
             outs.append(y.cpu().numpy())
+        tol = 1e-13 if prec == "fp64" else 2e-6
         for o in outs[1:]:
-            assert np.array_equal(o, outs[0])
+            assert relerr(o, outs[0]) < tol
         with pytest.raises(hb.HombError):
             hb.binding.hom_set_pass_chunks(ctx, -1, 0)
     finally:
