@@ -173,6 +173,12 @@ typedef struct {
   int32_t batch_config[6]; /* hom_bounds_batched launch: threads per CTA, chunk
                            capacity, radix schedule (1: 5/3, 2: composite), cluster
                            size, smallest cooperative 2N-1, CTAs launched          */
+  double elem_lo[9];    /* hom_bounds with both sides: intervals [elem_lo, elem_hi]
+                           for each entry of A_H, d x d row-major (Lemma bounds):
+                           diagonal [lower_aa, upper_aa] (Eq. estimate_diagonal),
+                           off-diagonal mean_ab -+ (D_aa + D_bb) (Eq.
+                           estimate_nondiagonal)                                 */
+  double elem_hi[9];
 } hom_report;
 
 typedef struct hom_ctx hom_ctx;

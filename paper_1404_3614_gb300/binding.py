@@ -50,7 +50,7 @@ class hom_report(C.Structure):
     _fields_ = [("iters", (C.c_int32 * 3) * 2), ("resid", (C.c_double * 3) * 2), ("matvecs", C.c_int32),
                 ("status", (C.c_int32 * 3) * 2), ("ms_total", C.c_double), ("launches", C.c_int64),
                 ("h2d_bytes", C.c_int64), ("d2h_bytes", C.c_int64), ("gani", (C.c_double * 9) * 2),
-                ("batch_config", C.c_int32 * 6)]
+                ("batch_config", C.c_int32 * 6), ("elem_lo", C.c_double * 9), ("elem_hi", C.c_double * 9)]
 
 
 class hom_field_io(C.Structure):
@@ -318,6 +318,9 @@ def hom_bounds(ctx, problem, opts, d_ws, ws_bytes, stream=0, d_x0=None, d_fields
     if opts.discretization == 1:
         out["gani_A"] = np.array(rep.gani[0][:d * d]).reshape(d, d)
         out["gani_B"] = np.array(rep.gani[1][:d * d]).reshape(d, d)
+    if (opts.sides or 3) & 3 == 3:
+        out["elem_lo"] = np.array(rep.elem_lo[:d * d]).reshape(d, d)
+        out["elem_hi"] = np.array(rep.elem_hi[:d * d]).reshape(d, d)
     return out
 
 

@@ -1590,6 +1590,20 @@ static hom_status bounds_impl(hom_ctx* ctx, const hom_problem* prob, const hom_o
       if (mean) mean[i] = 0.5 * (Au[i] + Lo[i]);
       if (D) D[i] = 0.5 * (Au[i] - Lo[i]);
     }
+    if (rep)   // entry intervals of A_H (Lemma bounds, Eqs. estimate_diagonal, estimate_nondiagonal)
+      for (int a = 0; a < d; ++a)
+        for (int b = 0; b < d; ++b) {
+          const int i = a * d + b;
+          if (a == b) {
+            rep->elem_lo[i] = Lo[i];
+            rep->elem_hi[i] = Au[i];
+          } else {
+            const double m = 0.5 * (Au[i] + Lo[i]);
+            const double r = 0.5 * (Au[a * d + a] - Lo[a * d + a]) + 0.5 * (Au[b * d + b] - Lo[b * d + b]);
+            rep->elem_lo[i] = m - r;
+            rep->elem_hi[i] = m + r;
+          }
+        }
   }
   if (rep) {
     rep->launches = ctx->launches;

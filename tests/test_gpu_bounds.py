@@ -262,3 +262,24 @@ def test_starting_fields_and_fields_out(hb, solver, name, prec):
     for key in ("upper", "lower"):
         assert rel(out[key], dense[key]) <= (1e-9 if prec == "fp64" else 1e-6)
     assert loewner_ge(out["upper"], dense["upper"], 1e-9) and loewner_ge(dense["lower"], out["lower"], 1e-9)
+
+
+@pytest.mark.parametrize("N", [5, 9])
+def test_element_bounds_match_oracle_and_contain_the_laminate(hb, N):
+    """Entry intervals of A_H (Lemma bounds): equal to the oracle's, and they contain the exact
+    homogenized tensor of an anisotropic laminate (closed form)."""
+    import sys
+    import os
+    sys.path.insert(0, os.path.dirname(__file__))
+    from test_oracle_pins import _anisotropic_laminate, _laminate_exact
+    p, A0, A1, w = _anisotropic_laminate(N)
+    ref = oracle.dense_bounds(p)
+    s = hb.Bounds(0)
+    try:
+        out = s(p, precision=hb.HOM_FP64, tol=1e-12)
+    finally:
+        s.close()
+    for key in ("elem_lo", "elem_hi"):
+        assert np.abs(out[key] - ref[key]).max() <= 1e-10 * np.abs(ref["upper"]).max(), key
+    exact = _laminate_exact(A0, A1, w)
+    assert np.all(out["elem_lo"] <= exact + 1e-12) and np.all(exact <= out["elem_hi"] + 1e-12)
