@@ -107,12 +107,14 @@ EVEN = {
 }
 
 
-def real_space_gani(problem, side):
+def real_space_gani(problem, side, nyquist="zero"):
     """A_{H,N} (primal) or B_{H,N} (dual) from the grid formulation of Eq. FD_GaNi written in
     real space: e in X_N with e = G_{N,0} e and G_{N,0}[A (E + e)] = 0, where G_{N,0} =
     F^-1 G_hat F (numpy FFTs) with G_hat zero at k = 0 and at the Nyquist frequencies
-    (Def. FD_proj_E). The dense system is assembled by applying the operator to unit
-    vectors; the energy is the grid mean of A (E + e) . (E + e)."""
+    (Def. FD_proj_E). nyquist="identity" takes G_{N,I} instead (identity at the Nyquist
+    frequencies): the enlarged spaces E_N^app, J_N^app of Eq. FD_GaNi_tilde. The dense system
+    is assembled by applying the operator to unit vectors; the energy is the grid mean of
+    A (E + e) . (E + e)."""
     d = problem.d
     N = tuple(int(n) for n in problem.N)
     Y = np.asarray(problem.Y, dtype=np.float64)
@@ -127,6 +129,8 @@ def real_space_gani(problem, side):
     keep = (n2 > 0) & ~nyq
     GE = np.where(keep[..., None, None], xi[..., :, None] * xi[..., None, :] / np.where(keep, n2, 1.0)[..., None, None], 0.0)
     G = GE if side == "primal" else np.where(keep[..., None, None], np.eye(d) - GE, 0.0)
+    if nyquist == "identity":
+        G = np.where(nyq[..., None, None], np.eye(d), G)
     axes = tuple(range(d))
 
     def proj(v):                                  # v [*N, d] real
@@ -223,3 +227,19 @@ def test_closed_and_open_inclusions_on_even_grids():
             assert loewner_ge(o["A_HN"], np.linalg.inv(o["B_HN"]), 1e-10)
         g1, g2 = dense.dense_bounds(s1.with_N(7)), dense.dense_bounds(s2.with_N(7))
         assert np.abs(g1["upper"] - g2["upper"]).max() < 1e-13
+
+
+@pytest.mark.parametrize("name", ["square2d_N8", "aniso2d_N6", "rect2d_N6x5", "paper_rho100_N8", "aniso3d_N4"])
+def test_even_grid_duality_with_the_enlarged_spaces(name):
+    """Prop. FD_even_problem (i): on general grids the GaNi matrices are dual to the problems on
+    the enlarged spaces E_N^app, J_N^app (projections G_{N,I}, identity at the Nyquist
+    frequencies, Eq. FD_GaNi_tilde): A_{H,N} = B~_{H,N}^{-1} and B_{H,N}^{-1} = A~_{H,N}. The
+    enlarged problems are computed by the independent real-space construction; A_{H,N} and
+    B_{H,N} come from the oracle."""
+    p = EVEN[name]()
+    out = gani.gani_bounds(p)
+    Bt = real_space_gani(p, "dual", nyquist="identity")
+    At = real_space_gani(p, "primal", nyquist="identity")
+    A, B = out["A_HN"], out["B_HN"]
+    assert np.abs(A - np.linalg.inv(Bt)).max() <= 1e-10 * np.abs(A).max()
+    assert np.abs(np.linalg.inv(B) - At).max() <= 1e-10 * np.abs(At).max()
