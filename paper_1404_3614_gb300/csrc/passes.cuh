@@ -99,21 +99,45 @@ __global__ void __launch_bounds__(kPassThreads) k_pencil(PencilArgs a) {
   cpx<T>* pin = const_cast<cpx<T>*>(reinterpret_cast<const cpx<T>*>(a.in)) + (long long)s * a.in_slab;
   const T beta = a.prologue == 1 ? T(a.cg->beta[rhs]) : T(0);
   const int half = (a.Nlog - 1) / 2;
-  for (int t = threadIdx.x; t < a.Pin * a.XC; t += blockDim.x) {
-    const int p = a.fd_XC.div(t);
-    const int xx = t - p * a.XC;
-    if (xx >= XC) continue;
-    const long long gi = (long long)p * a.X + x0 + xx;
-    cpx<T> v = pin[gi];
-    if (a.prologue == 1) {
-      const cpx<T> r = reinterpret_cast<const cpx<T>*>(a.aux)[(long long)s * a.in_slab + gi];
-      v = mk<T>(fma(beta, v.x, r.x), fma(beta, v.y, r.y));
-      pin[gi] = v;
-    } else if (a.prologue == 2) {
-      if (comp == rhs && p == 0 && x0 + xx == 0) v.x += T(1);
+  // FP32 on long pencils: four independent loads per thread in flight before their
+  // shared-memory stores (the stores may alias the loads for the compiler, which would
+  // otherwise serialise them); FP64 is bound by its arithmetic pipe and short FP32 pencils
+  // by occupancy: they keep one load (and their registers)
+  constexpr int U = sizeof(T) == 4 && (MT == 0 || MT >= 125) ? 4 : 1;
+  const int nload = a.Pin * a.XC;
+  for (int t0 = threadIdx.x; t0 < nload; t0 += U * blockDim.x) {
+    cpx<T> v[U], r[U];
+    long long gi[U];
+    int p[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int t = t0 + u * (int)blockDim.x;
+      p[u] = -1;
+      if (t < nload) {
+        const int pp = a.fd_XC.div(t);
+        const int xx = t - pp * a.XC;
+        if (xx < XC) {
+          p[u] = pp;
+          gi[u] = (long long)pp * a.X + x0 + xx;
+          v[u] = pin[gi[u]];
+          if (a.prologue == 1) r[u] = reinterpret_cast<const cpx<T>*>(a.aux)[(long long)s * a.in_slab + gi[u]];
+        }
+      }
     }
-    const int pos = pad ? (p <= half ? p : p - a.Nlog + M) : p;
-    A[xx * M + pos] = v;
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      if (p[u] < 0) continue;
+      const int xx = (int)(gi[u] - (long long)p[u] * a.X - x0);
+      cpx<T> w = v[u];
+      if (a.prologue == 1) {
+        w = mk<T>(fma(beta, w.x, r[u].x), fma(beta, w.y, r[u].y));
+        pin[gi[u]] = w;
+      } else if (a.prologue == 2) {
+        if (comp == rhs && p[u] == 0 && x0 + xx == 0) w.x += T(1);
+      }
+      const int pos = pad ? (p[u] <= half ? p[u] : p[u] - a.Nlog + M) : p[u];
+      A[xx * M + pos] = w;
+    }
   }
   __syncthreads();
   cpx<T>* res;
@@ -158,13 +182,30 @@ __global__ void __launch_bounds__(kPassThreads) k_final(FinalArgs a) {
   else stage_twiddles<T>(Ws, a.W, M);
   const cpx<T>* in = reinterpret_cast<const cpx<T>*>(a.in) + (long long)rhs * C * a.in_comp;
   const int per = M * a.XC;
-  for (int t = threadIdx.x; t < C * per; t += blockDim.x) {
-    const int g = a.fd_per.div(t);
-    const int rem = t - g * per;
-    const int p = a.fd_XC.div(rem);
-    const int xx = rem - p * a.XC;
-    if (xx >= XC) continue;
-    A[(g * XC + xx) * M + p] = in[(long long)g * a.in_comp + (long long)p * a.X + x0 + xx];
+  // FP32 on long pencils: four independent read-only loads per thread in flight before their
+  // shared-memory stores; FP64 and short FP32 pencils keep one
+  constexpr int U = sizeof(T) == 4 && (MT == 0 || MT >= 125) ? 4 : 1;
+  for (int t0 = threadIdx.x; t0 < C * per; t0 += U * blockDim.x) {
+    cpx<T> v[U];
+    int dst[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int t = t0 + u * (int)blockDim.x;
+      dst[u] = -1;
+      if (t < C * per) {
+        const int g = a.fd_per.div(t);
+        const int rem = t - g * per;
+        const int p = a.fd_XC.div(rem);
+        const int xx = rem - p * a.XC;
+        if (xx < XC) {
+          dst[u] = (g * XC + xx) * M + p;
+          v[u] = __ldg(in + (long long)g * a.in_comp + (long long)p * a.X + x0 + xx);
+        }
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (dst[u] >= 0) A[dst[u]] = v[u];
   }
   __syncthreads();
   cpx<T>* res;
