@@ -240,6 +240,16 @@ __global__ void __launch_bounds__(kPassThreads) k_final(FinalArgs a) {
       ky = kl;
       kz = 0;
     }
+    const long long oi = (long long)i * a.X + x;
+    // FP32: the CG direction p is fetched first, so that its latency overlaps the projection
+    // (issued after the stores below, the loads would wait for them); FP64, bound by its
+    // arithmetic pipe, keeps its registers and loads p after the stores
+    cpx<T> pv[3];
+    if constexpr (sizeof(T) == 4) {
+#pragma unroll
+      for (int c = 0; c < 3; ++c)
+        pv[c] = pdir && c < C ? __ldg(pdir + (long long)c * a.out_comp + oi) : mk<T>(T(0), T(0));
+    }
     cpx<T> u[3];
     // Nyquist rows of even axes are not computed by a pruned last stage: write zeros there
     const bool nyq = nyquist(kl, a.Nlog) || (a.d == 3 && nyquist(ky, a.Ny));
@@ -268,7 +278,6 @@ __global__ void __launch_bounds__(kPassThreads) k_final(FinalArgs a) {
           }
       }
     }
-    const long long oi = (long long)i * a.X + x;
     if (bsub) {
       double sq = 0.0;
 #pragma unroll
@@ -287,8 +296,8 @@ __global__ void __launch_bounds__(kPassThreads) k_final(FinalArgs a) {
 #pragma unroll
       for (int c = 0; c < 3; ++c)
         if (c < C) {
-          const cpx<T> pv = pdir[(long long)c * a.out_comp + oi];
-          sq += (double)pv.x * (double)u[c].x + (double)pv.y * (double)u[c].y;
+          if constexpr (sizeof(T) != 4) pv[c] = pdir[(long long)c * a.out_comp + oi];
+          sq += (double)pv[c].x * (double)u[c].x + (double)pv[c].y * (double)u[c].y;
         }
       acc += (kx == 0 ? 1.0 : 2.0) * sq;
     }
