@@ -1,4 +1,4 @@
-"""Learned CG warm start: data from the method, training and evaluation (driver).
+"""Learned CG warm start: data from the method, training and evaluation.
 
 The heavy lifting is in the library: the solver produces the training fields (the
 converged primal and dual correctors of each cell; the batched solver in 2D, hom_bounds_io
