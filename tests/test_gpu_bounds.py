@@ -283,3 +283,39 @@ def test_element_bounds_match_oracle_and_contain_the_laminate(hb, N):
         assert np.abs(out[key] - ref[key]).max() <= 1e-10 * np.abs(ref["upper"]).max(), key
     exact = _laminate_exact(A0, A1, w)
     assert np.all(out["elem_lo"] <= exact + 1e-12) and np.all(exact <= out["elem_hi"] + 1e-12)
+
+
+def test_full_size_spheres_matvec_sampled_rows(hb):
+    """The 3D 16-ball cell at N = 113 (double grid 225^3), the mixed-precision workload: rows
+    of the FP64 and FP32 operators at full size against the oracle's one-by-one rows
+    (Lemma Ga_full), 1e-11 (FP64) and 2e-6 (FP32) relative to the largest entry."""
+    p = ms.random_spheres_3d(0)
+    d = 3
+    N = tuple(int(n) for n in p.N)
+    ctx = hb.hom_create(0)
+    try:
+        rng = np.random.default_rng(7)
+        info = hb.hom_problem_info(ctx, p)
+        nws = hb.hom_step_workspace_size(ctx, p, d)
+        ws = torch.empty(nws, dtype=torch.uint8, device="cuda")
+        fields = [random_real_field(rng, d, N) for _ in range(d)]
+        uin = np.stack([full_to_half(u, d) for u in fields])
+        cases = {0: np.array([[0, 0, 0], [1, -2, 3], [56, -56, 10]]), 1: np.array([[5, 0, -1], [-40, 33, 56]])}
+        for side, ls in cases.items():
+            rows = matfree.matvec_sampled(p, "primal" if side == 0 else "dual", fields[0], ls)
+            for prec, cdt, rdt, tol in ((hb.HOM_FP64, torch.complex128, torch.float64, 1e-11),
+                                        (hb.HOM_FP32, torch.complex64, torch.float32, 2e-6)):
+                coef = torch.empty((info["ncomp"],) + tuple(info["M"][::-1]), dtype=rdt, device="cuda")
+                hb.hom_coefficient(ctx, p, side, prec, coef.data_ptr(), ws.data_ptr(), nws)
+                x = torch.from_numpy(uin).to(cdt).cuda()
+                out = torch.zeros_like(x)
+                hb.hom_matvec(ctx, p, side, prec, 1, d, coef.data_ptr(), x.data_ptr(), out.data_ptr(),
+                              ws.data_ptr(), nws)
+                full = half_to_full(out.cpu().numpy().astype(np.complex128)[0], d, N[0])
+                scale = max(1.0, np.abs(rows).max())
+                for i, l in enumerate(ls):
+                    idx = tuple(l + (np.array(N) - 1) // 2)
+                    v = full[(slice(None),) + idx]
+                    assert np.abs(v - rows[i]).max() <= tol * scale, (side, prec, l, v, rows[i])
+    finally:
+        hb.hom_destroy(ctx)
