@@ -102,9 +102,9 @@ typedef struct {
                                   0..(N_1+1)/2-1 in both cases. Ga on an even axis
                                   then equals Ga on N_a - 1; GaNi samples the N_a
                                   points and gives B_{H,N}^-1 <= A_{H,N} (Prop.
-                                  FD_even_problem). Sizes: N_a <= 2049; a pass keeps
-                                  d + 1 pencils of the double-grid length in 220 KB
-                                  of shared memory, so FP64 runs 2D grids up to
+                                  FD_even_problem). Sizes: N_a <= 2049; the last pass
+                                  keeps 2 d + 1 pencils of the double-grid length in
+                                  220 KB of shared memory, so FP64 runs 2D grids up to
                                   N ~ 1400 and 3D up to N ~ 1000 (larger ones return
                                   HOM_ERR_INVALID_ARG).                            */
   double Y[3];                 /* cell side lengths Y_a > 0                      */
