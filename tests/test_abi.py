@@ -52,6 +52,41 @@ def test_struct_layouts_match_header(libpath):
     assert ctypes.sizeof(bd.hom_opts) == 4 + 4 + 8 + 4 + 4 + 4 + 4 + 4 + 4
 
 
+def test_struct_layouts_match_a_c_compiler(libpath, tmp_path):
+    """Every struct of the header, compiled by the host C compiler: its size and the offset of
+    each field equal the ctypes mirror in the binding (the binding cannot drift from the ABI)."""
+    import shutil
+    import subprocess
+    import paper_1404_3614_gb300.binding as bd
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    structs = {"hom_inclusion": bd.hom_inclusion, "hom_problem": bd.hom_problem, "hom_opts": bd.hom_opts,
+               "hom_report": bd.hom_report, "hom_field_io": bd.hom_field_io, "hom_batch_io": bd.hom_batch_io,
+               "hom_net_config": bd.hom_net_config}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "homb.h"', "int main(void) {"]
+    for name, cls in structs.items():
+        lines.append(f'  printf("{name} @sizeof %zu\\n", sizeof({name}));')
+        for fname, _ in cls._fields_:
+            lines.append(f'  printf("{name} {fname} %zu\\n", offsetof({name}, {fname}));')
+    lines.append("  return 0;\n}")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    inc = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
+    subprocess.run([cc, "-std=c11", "-I", inc, str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {}
+    for line in out:
+        parts = line.split()
+        if len(parts) == 3:
+            got[(parts[0], parts[1])] = int(parts[2])
+    for name, cls in structs.items():
+        assert got[(name, "@sizeof")] == ctypes.sizeof(cls), name
+        for fname, _ in cls._fields_:
+            assert got[(name, fname)] == getattr(cls, fname).offset, (name, fname)
+
+
 def test_create_without_gpu_fails_cleanly(libpath):
     import torch
     if torch.cuda.is_available():
