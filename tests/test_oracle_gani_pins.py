@@ -243,3 +243,18 @@ def test_even_grid_duality_with_the_enlarged_spaces(name):
     A, B = out["A_HN"], out["B_HN"]
     assert np.abs(A - np.linalg.inv(Bt)).max() <= 1e-10 * np.abs(A).max()
     assert np.abs(np.linalg.inv(B) - At).max() <= 1e-10 * np.abs(At).max()
+
+
+@pytest.mark.parametrize("name", ["square2d_N9", "aniso2d_N7", "rect2d_N11", "aniso3d_N5"])
+def test_odd_grid_dual_fields_from_the_primal_ones(name):
+    """Eq. FD_superposition_odd_A: on odd grids the dual GaNi fields follow from the primal ones
+    pointwise, e_b + j^(b) = A_N sum_a E_a (e_a + e^(a)) with E = B_{H,N} e_b. In the Fourier
+    basis the grid product with A_N is the GaNi matrix K_N (exact on Z_N), so the dual fields
+    of the oracle equal K_N U E column by column."""
+    p = CELLS[name]()
+    Xp, E0, Kp = gani.gani_fields(p, "primal")
+    Xd, _, _ = gani.gani_fields(p, "dual")
+    Up, Ud = E0 + Xp, E0 + Xd
+    B = (Ud.conj().T @ gani.gani_matrix(p, "dual") @ Ud).real
+    J = Kp @ Up @ B                      # column b: A_N sum_a (B e_b)_a (e_a + e^(a))
+    assert np.abs(J - Ud).max() <= 1e-10 * np.abs(Ud).max()
