@@ -94,8 +94,8 @@ typedef struct {
   int32_t d;                   /* 2 or 3                                         */
   int32_t N[3];                /* grid sizes N_a >= 1, a < d. Odd grids (Eq. N_odd)
                                   everywhere; even sizes (general grids, Sec. "Fully
-                                  discrete spaces --- general grids") in FP64
-                                  hom_bounds and the FP64 step-level calls only: the
+                                  discrete spaces --- general grids") in hom_bounds
+                                  (FP64 and mixed) and the FP64 step-level calls: the
                                   conforming spaces E_N, J_N exclude the Nyquist
                                   frequency k_a = -N_a/2 (Def. FD_proj_E), which every
                                   field keeps at zero; the stored x frequencies are

@@ -1498,7 +1498,6 @@ static hom_status bounds_impl(hom_ctx* ctx, const hom_problem* prob, const hom_o
   if (opts->discretization != 0 && opts->discretization != 1)
     return fail(ctx, HOM_ERR_INVALID_ARG, "discretization must be 0 (Ga) or 1 (GaNi)");
   const bool gani = opts->discretization == 1;
-  if (g.even && opts->precision != HOM_FP64) return fail(ctx, HOM_ERR_INVALID_ARG, "even grids run in FP64");
   if (gani && io && (io->d_x0 || io->d_fields))
     return fail(ctx, HOM_ERR_INVALID_ARG, "starting / output fields are for the Galerkin discretization");
   Runner run{ctx, g, make_layout(g, g.d, elem, 0), static_cast<unsigned char*>(d_ws),
