@@ -105,10 +105,6 @@ def test_gani_mixed_precision_prime_lengths(hb, solver, name):
         assert rel(out[key], ref[key]) <= 1e-6, key
 
 
-def test_gani_mixed_rejects_even_grids(hb, solver):
-    with pytest.raises(hb.HombError):
-        solver(ms.square_inclusion_2d(N=9).with_N(8), precision=hb.HOM_MIXED, discretization=1)
-
 
 # ---- general (even) grids -------------------------------------------------------------
 EVEN = {
