@@ -102,11 +102,16 @@ typedef struct {
                                   0..(N_1+1)/2-1 in both cases. Ga on an even axis
                                   then equals Ga on N_a - 1; GaNi samples the N_a
                                   points and gives B_{H,N}^-1 <= A_{H,N} (Prop.
-                                  FD_even_problem). Sizes: N_a <= 2049; the last pass
-                                  keeps 2 d + 1 pencils of the double-grid length in
-                                  220 KB of shared memory, so FP64 runs 2D grids up to
-                                  N ~ 1400 and 3D up to N ~ 1000 (larger ones return
-                                  HOM_ERR_INVALID_ARG).                            */
+                                  FD_even_problem). Sizes: N_a <= 2049. Each FP64
+                                  pass keeps one pencil or plane of rows of the
+                                  double-grid length M_a in 220 KB of shared memory.
+                                  hom_bounds' energy pass holds the d^2 rows of a
+                                  plane: N_a <= 1348 in 2D (M = 2695) and 613 in 3D
+                                  (M = 1225), checked by hom_workspace_size and
+                                  hom_bounds before any work. The step-level operator
+                                  (M = 2N - 1, 2 d + 1 pencils in its last pass) takes
+                                  N <= 1405 in 2D and 1003 in 3D in FP64. Larger
+                                  grids return HOM_ERR_INVALID_ARG.                */
   double Y[3];                 /* cell side lengths Y_a > 0                      */
   double A0[9];                /* matrix phase, SPD, row-major, leading dim 3    */
   int32_t n_incl;              /* number of inclusions (may be 0)                */

@@ -1461,11 +1461,29 @@ Geometry gani_geometry(const Geometry& g) {
 
 size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 
+// Every shared-memory pass of the FP64 pipeline holds at least one pencil (the y and z
+// transforms; the last pass with its d components) or one plane of rows (the x pass: one
+// c2r row, d operator rows, and the energy pass's d^2 rows). Checked before any work, so
+// that an oversize grid fails at once instead of at its first energy evaluation. The FP32
+// passes of the mixed path are half the size and fit whenever these do.
+static hom_status check_pass_fit(hom_ctx* ctx, const Geometry& g, bool energy) {
+  bool ok = xpass_yb<double>(g.M[0], 1, 1) >= 1 && xpass_yb<double>(g.M[0], g.d, 1) >= 1 &&
+            pencil_xc<double>(g.M[g.d - 1], 1, g.d) >= 1;
+  if (energy) ok = ok && xpass_yb<double>(g.M[0], g.d * g.d, 1) >= 1;
+  for (int a = 1; a < g.d; ++a) ok = ok && pencil_xc<double>(g.M[a], 1, 1) >= 1;
+  if (!ok)
+    return fail(ctx, HOM_ERR_INVALID_ARG,
+                "grid too large for the shared-memory FFT (a pass cannot hold one pencil or plane of rows)");
+  return HOM_OK;
+}
+
 hom_status hom_workspace_size(hom_ctx* ctx, const hom_problem* prob, const hom_opts* opts,
                               size_t* bytes) {
   if (!ctx || !opts || !bytes) return fail(ctx, HOM_ERR_INVALID_ARG, "NULL argument");
   Geometry g;
   CKS(build_geometry(ctx, prob, g, true));
+  CKS(check_pass_fit(ctx, g, true));
+  if (opts->discretization == 1) CKS(check_pass_fit(ctx, gani_geometry(g), false));
   const size_t elem = opts->precision == HOM_MIXED ? 8 : 16;
   *bytes = make_layout(g, g.d, elem, 0).total;
   if (opts->discretization == 1) *bytes = align256(*bytes) + make_layout(gani_geometry(g), g.d, elem, 0).total;
@@ -1500,6 +1518,8 @@ static hom_status bounds_impl(hom_ctx* ctx, const hom_problem* prob, const hom_o
   const bool gani = opts->discretization == 1;
   if (gani && io && (io->d_x0 || io->d_fields))
     return fail(ctx, HOM_ERR_INVALID_ARG, "starting / output fields are for the Galerkin discretization");
+  CKS(check_pass_fit(ctx, g, true));
+  if (gani) CKS(check_pass_fit(ctx, gani_geometry(g), false));
   Runner run{ctx, g, make_layout(g, g.d, elem, 0), static_cast<unsigned char*>(d_ws),
              static_cast<cudaStream_t>(stream), g.d};
   const Geometry gn = gani ? gani_geometry(g) : g;

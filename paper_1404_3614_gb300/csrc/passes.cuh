@@ -552,7 +552,8 @@ template <typename T> int pencil_xc(int M, int X, int C) {
 template <typename T> int xpass_yb(int M, int rpp, int planes) {
   const size_t sz = sizeof(cpx<T>);
   const size_t fixed = M * sz + 512;
-  const long long npmax = (long long)((kPassSmemBudget - fixed) / (2 * (size_t)(M + 1) * sz));
+  const long long npmax =
+      kPassSmemBudget > fixed ? (long long)((kPassSmemBudget - fixed) / (2 * (size_t)(M + 1) * sz)) : 0;
   long long yb = (2 * npmax) / rpp;
   if (yb < 1) {
     const size_t need = fixed + 2 * (size_t)((rpp + 1) / 2) * (M + 1) * sz;

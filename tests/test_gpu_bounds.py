@@ -319,3 +319,39 @@ def test_full_size_spheres_matvec_sampled_rows(hb):
                     assert np.abs(v - rows[i]).max() <= tol * scale, (side, prec, l, v, rows[i])
     finally:
         hb.hom_destroy(ctx)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_laminate_at_the_largest_2d_grid(hb, solver, precision):
+    """The largest 2D grid hom_bounds takes: N = 1348 (double grid 2695 = 5 * 7^2 * 11, whose
+    FP64 energy pass holds the four rows of a plane in 220 KB). The laminate's closed forms
+    hold at every N (layers normal to x1: upper[1,1] is the arithmetic mean and lower[0,0] the
+    harmonic mean, exactly; the other diagonal entries are strict bounds)."""
+    import json
+    import os
+    g = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "laminate_2d.json")))
+    p = ms.laminate_2d(1348, width=g["width"], a_matrix=g["a_matrix"], a_incl=g["a_incl"])
+    prec = hb.HOM_FP64 if precision == "fp64" else hb.HOM_MIXED
+    out = solver(p, precision=prec, tol=1e-6)
+    up, lo = np.asarray(out["upper"]), np.asarray(out["lower"])
+    assert up[1, 1] == pytest.approx(g["arithmetic"], rel=1e-10)
+    assert lo[0, 0] == pytest.approx(g["harmonic"], rel=1e-10)
+    assert abs(up[0, 1]) < 1e-10 and abs(lo[0, 1]) < 1e-10
+    assert up[0, 0] > g["harmonic"] and lo[1, 1] < g["arithmetic"]
+    assert loewner_ge(up, lo)
+
+
+def test_oversize_grids_rejected_before_any_work(hb, solver):
+    """One step past the largest grids (2D N = 1349: double grid 2835; 3D N = 615: 1287) the
+    energy pass cannot hold a plane of rows: hom_workspace_size refuses with
+    HOM_ERR_INVALID_ARG, so no workspace is ever allocated; the largest grids are accepted."""
+    ctx = solver.ctx
+    for prec in (hb.HOM_FP64, hb.HOM_MIXED):
+        opts = hb.make_opts(precision=prec)
+        assert hb.hom_workspace_size(ctx, ms.laminate_2d(1348), opts) > 0
+        assert hb.hom_workspace_size(ctx, ms.cube_inclusion_3d(N=613), opts) > 0
+        for p in (ms.laminate_2d(1349), ms.laminate_2d(1350), ms.cube_inclusion_3d(N=615)):
+            with pytest.raises(hb.HombError) as e:
+                hb.hom_workspace_size(ctx, p, opts)
+            assert e.value.status == hb.binding.HOM_ERR_INVALID_ARG
+            assert "too large" in str(e.value)
