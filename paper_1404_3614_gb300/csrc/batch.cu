@@ -9,6 +9,7 @@
 // upper_lower_bounds). No grid-wide synchronisation and no waits between CTAs: each
 // task is independent. Data live in a per-CTA global scratch slot (L2-resident for the
 // small grids) and pass through shared memory in chunks of FFT pencils.
+#include <atomic>
 #include <cooperative_groups.h>
 #include <math.h>
 
@@ -798,14 +799,16 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 2 : 1) k_batch(BArgs a) {
 
 template <typename T, int NT>
 cudaError_t launch_batch_nt(const BArgs& a, int nblocks, size_t smem, int cluster, cudaStream_t s) {
-  static size_t cache[16] = {};
+  static std::atomic<size_t> cache[16] = {};   // shared by every context: atomic
   int dev = 0;
   cudaGetDevice(&dev);
   dev &= 15;
-  if (smem > 48 * 1024 && cache[dev] < smem) {
+  if (smem > 48 * 1024 && cache[dev].load(std::memory_order_relaxed) < smem) {
     const cudaError_t e = cudaFuncSetAttribute(k_batch<T, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    cache[dev] = smem;
+    size_t cur = cache[dev].load(std::memory_order_relaxed);
+    while (cur < smem && !cache[dev].compare_exchange_weak(cur, smem, std::memory_order_relaxed)) {
+    }
   }
   if (cluster <= 1) {
     k_batch<T, NT><<<nblocks, NT, smem, s>>>(a);

@@ -199,7 +199,7 @@ inline size_t slab_smem_bytes(int M, int R, int Nh, int warps, size_t elem) {
 
 template <typename T, int R> cudaError_t launch_slab_r(const SlabArgs& a, int warps, cudaStream_t s) {
   const size_t smem = slab_smem_bytes(R * R, R, a.Nh, warps, sizeof(cpx<T>));
-  static size_t cache[16] = {};
+  static std::atomic<size_t> cache[16] = {};
   cudaError_t e = smem_attr(k_slab<T, R>, smem, cache);
   if (e != cudaSuccess) return e;
   k_slab<T, R><<<a.nrc * a.Mz, warps * 32, smem, s>>>(a);

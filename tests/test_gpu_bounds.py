@@ -355,3 +355,52 @@ def test_oversize_grids_rejected_before_any_work(hb, solver):
                 hb.hom_workspace_size(ctx, p, opts)
             assert e.value.status == hb.binding.HOM_ERR_INVALID_ARG
             assert "too large" in str(e.value)
+
+
+def test_one_context_per_thread(hb):
+    """Contexts are independent: two host threads, each with its own context and stream,
+    solve at the same time (ctypes releases the interpreter lock during the calls; graph
+    captures are thread-local) and reproduce the results of the same solves run one after
+    the other."""
+    import threading
+    cells = [ms.square_inclusion_2d(N=23), ms.cube_inclusion_3d(N=9)]
+    precs = [hb.HOM_FP64, hb.HOM_MIXED]
+    ref = {}
+    s0 = hb.Bounds(0)
+    try:
+        for i, p in enumerate(cells):
+            for prec in precs:
+                o = s0(p, precision=prec, tol=1e-8)
+                ref[i, prec] = (np.asarray(o["upper"]), np.asarray(o["lower"]))
+    finally:
+        s0.close()
+    errors, got = [], {}
+
+    def work(i):
+        try:
+            s = hb.Bounds(0)
+            st = torch.cuda.Stream()
+            try:
+                with torch.cuda.stream(st):
+                    for rep in range(3):
+                        for prec in precs:
+                            o = s(cells[i], precision=prec, tol=1e-8)
+                            got[i, prec, rep] = (np.asarray(o["upper"]), np.asarray(o["lower"]))
+            finally:
+                st.synchronize()
+                s.close()
+        except Exception as e:  # reported by the main thread
+            errors.append(repr(e))
+
+    threads = [threading.Thread(target=work, args=(i,)) for i in range(len(cells))]
+    for t in threads:
+        t.start()
+    for t in threads:
+        t.join(timeout=600)
+    assert not any(t.is_alive() for t in threads)
+    assert not errors, errors
+    assert len(got) == len(cells) * len(precs) * 3
+    for (i, prec, rep), (up, lo) in got.items():
+        ru, rl = ref[i, prec]
+        assert np.abs(up - ru).max() <= 1e-12 * np.abs(ru).max(), (i, prec, rep)
+        assert np.abs(lo - rl).max() <= 1e-12 * np.abs(rl).max(), (i, prec, rep)
