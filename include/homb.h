@@ -63,7 +63,8 @@ typedef enum {
   HOM_WARN_NOT_CONVERGED = 1,  /* max_iter reached: the returned bounds are still
                                   guaranteed (any conforming field gives a bound,
                                   Lemma bounds), only looser                      */
-  HOM_ERR_INVALID_ARG = -1,    /* N < 1, even N where only odd grids run, d not
+  HOM_ERR_INVALID_ARG = -1,    /* N < 1, even N where only odd grids run, a grid
+                                  too large for the shared-memory passes, d not
                                   2/3, non-SPD phase, overlapping or oversized
                                   inclusion, NULL pointer, bad sizes              */
   HOM_ERR_BREAKDOWN = -2,      /* CG breakdown: NaN/Inf or p.Cp <= 0              */
