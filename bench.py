@@ -187,6 +187,39 @@ def run_paper_grids(args):
     return 0
 
 
+def run_even_grids(args):
+    """The paper's even-grid cells S1/S2 (Sec. 7.2, Eqs. S1, S2) at n = 512 and 1024,
+    rho = 10 and 10^3, tol 1e-8: Ga and GaNi in FP64 and in mixed precision. Each solve is
+    timed on its second call (the first builds plans and captures graphs); one JSON line per
+    (cell, rho, n, precision) with the bounds, so the precisions can be compared."""
+    import numpy as np
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import microstructures as ms
+    import paper_1404_3614_gb300 as hb
+    solver = hb.Bounds(0)
+    for n in (512, 1024):
+        for rho in (10.0, 1000.0):
+            for cell in ("S1", "S2"):
+                p = ms.paper_square_even_2d(n, rho, closed=cell == "S2")
+                for pname, prec in (("fp64", hb.HOM_FP64), ("mixed", hb.HOM_MIXED)):
+                    line = {"cell": cell, "rho": rho, "n": n, "precision": pname, "tol": 1e-8}
+                    for disc, tag in ((0, "ga"), (1, "gani")):
+                        solver(p, precision=prec, tol=1e-8, discretization=disc)
+                        torch.cuda.synchronize()
+                        t0 = time.perf_counter()
+                        o = solver(p, precision=prec, tol=1e-8, discretization=disc)
+                        torch.cuda.synchronize()
+                        line[tag + "_s"] = time.perf_counter() - t0
+                        line[tag + "_upper"] = float(o["upper"][0, 0])
+                        line[tag + "_lower"] = float(o["lower"][0, 0])
+                        line[tag + "_iters"] = int(np.asarray(o["report"]["iters"]).sum())
+                    print(json.dumps(line), flush=True)
+    solver.close()
+    return 0
+
+
 def run_gemm_only(args):
     """The network's tensor-core GEMM alone (for kernel captures and its roofline): a 1x1
     channel-mixing layer of the 3D network, C = A B with A [M x K] FP32 (M = 2^20 grid points,
@@ -758,6 +791,8 @@ def main():
     ap.add_argument("--gemm-only", action="store_true", help="the network's tensor-core GEMM alone")
     ap.add_argument("--paper-grids", action="store_true",
                     help="the paper's square-inclusion study on odd and even grids (Ga and GaNi)")
+    ap.add_argument("--even-grids", action="store_true",
+                    help="the paper's even-grid cells S1/S2 at n = 512, 1024: Ga and GaNi, FP64 and mixed")
     ap.add_argument("--learned-train3d", type=int, default=1000)
     ap.add_argument("--learned-test3d", type=int, default=16)
     ap.add_argument("--learned-epochs3d", type=int, default=30)
@@ -780,6 +815,8 @@ def main():
         return run_gemm_only(args)
     if args.paper_grids:
         return run_paper_grids(args)
+    if args.even_grids:
+        return run_even_grids(args)
     return run_gpu(args)
 
 
