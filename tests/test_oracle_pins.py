@@ -412,18 +412,21 @@ def test_element_bounds_contain_exact_anisotropic_laminate(N):
     assert abs(hi[0, 1] - lo[0, 1] - 2 * (D[0, 0] + D[1, 1])) < 1e-13
 
 
-def test_mean_and_error_matrix_reproduce_the_papers_printed_values():
-    """Eq. approx_homog_with_error on the paper's own numbers (Sec. 7.3, Eqs. flyash_orig_bounds
-    and flyash_orig_mean). The oracle forms the mean and the guaranteed error matrix D from the
-    printed upper bound and inverse dual bound. They equal the printed mean and D to the printing
-    precision: inputs and outputs are rounded to 7 decimals, so they are at most 1e-7 apart. A
-    D without the factor 1/2, or a mean of the dual energies instead of their inverse, fails."""
+@pytest.mark.parametrize("which", ["original", "smoothed"])
+def test_mean_and_error_matrix_reproduce_the_papers_printed_values(which):
+    """Eq. approx_homog_with_error on the paper's own numbers (Sec. 7.3: Eqs. flyash_orig_bounds
+    and flyash_orig_mean, Eqs. flyash_smooth_bounds and flyash_smooth_mean). The oracle forms the
+    mean and the guaranteed error matrix D from the printed upper bound and inverse dual bound.
+    They equal the printed mean and D to the printing precision: inputs and outputs are rounded
+    to 7 decimals, so they are at most 1e-7 apart. A D without the factor 1/2, or a mean of the
+    dual energies instead of their inverse, fails."""
     from oracle import bounds
     g = json.load(open(os.path.join(GOLDEN, "paper_flyash_printed_matrices.json")))
-    up, lo = np.array(g["upper"]), np.array(g["lower"])
+    m = g["sets"][which]
+    up, lo = np.array(m["upper"]), np.array(m["lower"])
     out = bounds.assemble_bounds(up, np.linalg.inv(lo))
     tol = 10.0 ** -g["decimals"] + 1e-12
-    assert np.abs(out["mean"] - np.array(g["mean"])).max() <= tol
-    assert np.abs(out["D"] - np.array(g["D"])).max() <= tol
+    assert np.abs(out["mean"] - np.array(m["mean"])).max() <= tol
+    assert np.abs(out["D"] - np.array(m["D"])).max() <= tol
     # which printed matrix is the upper bound: upper - lower is positive definite
     assert np.linalg.eigvalsh(up - lo).min() > 0
