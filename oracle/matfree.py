@@ -99,10 +99,11 @@ class MatFreeOperator:
         return W
 
 
-def cg_solve(op: MatFreeOperator, E, tol: float = 1e-10, maxiter: int = 10000, x0=None):
+def cg_solve(op: MatFreeOperator, E, tol: float = 1e-10, maxiter: int = 10000, x0=None, history=None):
     """CG on C x = b, b = -Gamma P F A F^{-1} E (Eq. linear_system_primal / _dual, double-grid C).
 
-    Returns (x_hat, iterations, final recursive residual norm / ||E||).
+    Returns (x_hat, iterations, final recursive residual norm / ||E||). A list given as
+    `history` receives the relative residual after each iteration (index 0: the start).
     """
     Ef = op.constant_field(E)
     normE = float(np.linalg.norm(np.asarray(E, dtype=np.float64)))
@@ -116,6 +117,8 @@ def cg_solve(op: MatFreeOperator, E, tol: float = 1e-10, maxiter: int = 10000, x
     p = r.copy()
     rr = inner(r, r)
     it = 0
+    if history is not None:
+        history.append(float(np.sqrt(rr)) / normE)
     while np.sqrt(rr) > tol * normE and it < maxiter:
         q = op.apply(p)
         alpha = rr / inner(p, q)
@@ -125,6 +128,8 @@ def cg_solve(op: MatFreeOperator, E, tol: float = 1e-10, maxiter: int = 10000, x
         p = r + (rr_new / rr) * p
         rr = rr_new
         it += 1
+        if history is not None:
+            history.append(float(np.sqrt(rr)) / normE)
     return x, it, float(np.sqrt(rr)) / normE
 
 
