@@ -693,7 +693,7 @@ def image_timings(hb, solver, stream, flush):
                      ("smoothed_gani_fp64", {"precision": hb.HOM_FP64, "discretization": 1})):
         if name.startswith("smoothed") and "smoothed_image" not in out:
             out["smoothed_image"] = "the same image with the paper's 4/2/1 local average of the solid phase"
-            p = ms.bitmap_problem(ms.porous_bitmap_2d(0, P=1199, smooth=True))
+            p = ms.bitmap_problem(ms.porous_bitmap_2d(0, P=1199), smooth=True)
         solver(p, tol=TOL, stream=stream.cuda_stream, **kw)
         flush.zero_()
         e0 = torch.cuda.Event(enable_timing=True)

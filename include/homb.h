@@ -134,6 +134,15 @@ typedef struct {
                                   inclusion boundary: 0 matrix (strict membership,
                                   the paper's Eq. S, S1), 1 inclusion (Eq. S2). The
                                   Galerkin discretization does not depend on it.  */
+  int32_t smooth;              /* pixel images only (else 0): 1 replaces the image by
+                                  the paper's local average (Sec. 7.3) before the
+                                  coefficient is formed: weight 4/16 for the pixel,
+                                  2/16 for each edge neighbour, 1/16 for each corner
+                                  neighbour, periodic; a 3D image takes weights
+                                  1/2, 1/4, 1/4 along every axis, multiplied. The
+                                  primal coefficient is smoothed; the dual side
+                                  inverts the smoothed values. Done on the device
+                                  when the image is uploaded.                    */
 } hom_problem;
 
 typedef struct {
@@ -443,6 +452,12 @@ hom_status hom_set_batch_cluster(hom_ctx* ctx, int32_t cluster, int32_t coop_min
  * last hom_profile_kernel call (synchronises the events). Inside the CG iteration
  * graphs of hom_bounds the events are event-record nodes of the graph; each replay
  * of a graph holding them is waited for and its pairs summed before the call goes on. */
+/* Measured FMA rate of this GPU (no counterpart in the paper; a measurement aid):
+ * precision HOM_FP32 or HOM_FP64; runs 8 independent FMA chains per thread on 4 CTAs
+ * of 512 threads per SM on `stream`, best of 5 timed launches after one warm-up, and
+ * returns the rate in TFLOP/s (one FMA = 2 flops) in *tflops. The denominator of the
+ * ALU-bound rooflines of the FFT passes. Uses no memory beyond a static 8-byte sink. */
+hom_status hom_peak_probe(hom_ctx* ctx, int32_t precision, void* stream, double* tflops);
 hom_status hom_profile_kernel(hom_ctx* ctx, const char* name);
 hom_status hom_kernel_timing(hom_ctx* ctx, int64_t* launches, double* total_ms);
 

@@ -65,6 +65,10 @@ class Problem:
     # the matrix (strict membership, the paper's Eq. S and S1), True in the inclusion
     # (non-strict, Eq. S2). Galerkin with exact integration does not depend on it.
     closed: bool = False
+    # pixel images only: True asks for the paper's local average of the image (Sec. 7.3)
+    # before the coefficient is formed; a flag of the problem statement, applied by the
+    # solver (and independently by the oracle), never by this module
+    smooth: bool = False
 
     @property
     def M(self) -> np.ndarray:
@@ -314,17 +318,18 @@ def batch_rectangles_2d(seeds: Sequence[int], N=None) -> List[Problem]:
 # ----------------------------------------------------------------------------------
 # pixel images (the paper's Sec. 7.3 workload type: a coefficient given per pixel)
 # ----------------------------------------------------------------------------------
-def bitmap_problem(bitmap, N=None, Y=1.0) -> Problem:
+def bitmap_problem(bitmap, N=None, Y=1.0, smooth=False) -> Problem:
     """A cell whose isotropic conductivity is the pixel image `bitmap` (values > 0).
     N defaults to the image size (the grid points then sit at the pixel centres for odd
-    sizes)."""
+    sizes). smooth=True asks the solver to replace the image by the paper's local
+    average (Sec. 7.3) first; the image itself is stored raw."""
     b = np.ascontiguousarray(np.asarray(bitmap, dtype=np.float64))
     d = b.ndim
     if d not in (2, 3) or np.any(~(b > 0)):
         raise ValueError("bitmap: 2D or 3D array of positive conductivities")
     Nv = np.asarray(b.shape if N is None else np.broadcast_to(N, (d,)), dtype=np.int64)
     Yv = _vec(Y, d)
-    return Problem(d, Yv, Nv.copy(), float(b.mean()) * np.eye(d), [], bitmap=b)
+    return Problem(d, Yv, Nv.copy(), float(b.mean()) * np.eye(d), [], bitmap=b, smooth=bool(smooth))
 
 
 def box_bitmap(P, lo, hi, a_in, a_out=1.0, d=2) -> np.ndarray:
@@ -334,25 +339,13 @@ def box_bitmap(P, lo, hi, a_in, a_out=1.0, d=2) -> np.ndarray:
     return b
 
 
-def smooth_indicator_2d(f: np.ndarray) -> np.ndarray:
-    """The paper's local average of an image's characteristic function (Sec. 7.3): weights
-    4/16 at the pixel, 2/16 at its four edge neighbours and 1/16 at its four corner
-    neighbours, periodic."""
-    f = np.asarray(f, dtype=np.float64)
-    out = 4.0 * f
-    for s0, s1, w in ((1, 0, 2.0), (-1, 0, 2.0), (0, 1, 2.0), (0, -1, 2.0),
-                      (1, 1, 1.0), (-1, -1, 1.0), (-1, 1, 1.0), (1, -1, 1.0)):
-        out += w * np.roll(np.roll(f, s0, axis=0), s1, axis=1)
-    return out / 16.0
-
-
 def porous_bitmap_2d(seed: int, P=1199, porosity=0.45, r_min=0.01, r_max=0.04, a_solid=0.49,
-                     a_pore=0.029, smooth=False) -> np.ndarray:
+                     a_pore=0.029) -> np.ndarray:
     """A synthetic porous two-phase P x P image standing in for a micrograph: pores are the
     union of periodic disks (centres uniform, radii log-uniform in [r_min, r_max] of the cell),
     added until the pore fraction reaches `porosity`; conductivities a_solid / a_pore (the
-    paper's Sec. 7.3 phase values); smooth=True applies smooth_indicator_2d to the solid
-    phase's characteristic function first."""
+    paper's Sec. 7.3 phase values). The raw image: the paper's smoothing is a flag of the
+    problem (bitmap_problem(..., smooth=True)), applied by the solver."""
     rng = np.random.default_rng(seed)
     c = (np.arange(P) + 0.5) / P - 0.5
     X, Yg = np.meshgrid(c, c, indexing="ij")
@@ -366,7 +359,5 @@ def porous_bitmap_2d(seed: int, P=1199, porosity=0.45, r_min=0.01, r_max=0.04, a
         dy -= np.round(dy)
         pore |= dx * dx + dy * dy < r * r
     solid = (~pore).astype(np.float64)
-    if smooth:
-        solid = smooth_indicator_2d(solid)
     return a_pore + (a_solid - a_pore) * solid
 

@@ -28,6 +28,8 @@ properties by FFT-based Galerkin method":
               homogenized matrices and the bounds of the paper's algorithm (the
               minimisers in the exactly integrated forms, Eq. GaNi_bounds).
   fno.py      the learned warm start's Fourier-layer network in PyTorch float64.
+  image.py    pixel-image values, with the paper's optional 4/2/1 local average
+              (Sec. 7.3) written as circulant-matrix products.
 
 Every function is pinned by ``tests/test_oracle_pins.py``,
 ``tests/test_oracle_gani_pins.py`` and ``tests/test_oracle_fno_pins.py`` against facts the
@@ -39,9 +41,11 @@ from .fourier import (coefficient_hat_at, coefficient_hat_grid, freqs, projectio
 from .dense import dense_bounds, dense_energy_matrix, dense_fields
 from .matfree import (MatFreeOperator, cg_solve, matfree_bounds, matvec_sampled)
 from .bounds import assemble_bounds
+from .image import image_values, smoothed_image, smoothing_matrix
 
 __all__ = [
     "coefficient_hat_at", "coefficient_hat_grid", "freqs", "projection", "topology_hat_at",
     "phase_inverse", "dense_bounds", "dense_energy_matrix", "dense_fields", "MatFreeOperator",
-    "cg_solve", "matfree_bounds", "matvec_sampled", "assemble_bounds",
+    "cg_solve", "matfree_bounds", "matvec_sampled", "assemble_bounds", "image_values",
+    "smoothed_image", "smoothing_matrix",
 ]

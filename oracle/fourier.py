@@ -12,6 +12,8 @@ from scipy import special
 
 from microstructures import BALL, BOX, Problem
 
+from .image import image_values
+
 
 def freqs(n: int) -> np.ndarray:
     """Z_n for odd n, centred order (Eq. index_sets; the reduced and full sets agree)."""
@@ -94,7 +96,8 @@ def bitmap_hat_at(problem: Problem, n: np.ndarray, side: str = "primal") -> np.n
       a_hat(n) = sum_i v_i prod_a (1/P_a) sinc(n_a/P_a) exp(-2 pi i n_a c_a / Y_a),
     written as a sum over the pixels (no FFT). Returns a scalar per frequency."""
     n = np.asarray(n, dtype=np.int64)
-    v = problem.bitmap if side == "primal" else 1.0 / problem.bitmap
+    img = image_values(problem)
+    v = img if side == "primal" else 1.0 / img
     Y = np.asarray(problem.Y, dtype=np.float64)
     factors = []
     for a in range(problem.d):

@@ -36,6 +36,7 @@ from microstructures import BOX, Problem
 from .bounds import assemble_bounds
 from .dense import _galerkin_matrix, _projector
 from .fourier import freqs, frequency_grid
+from .image import image_values
 
 
 def grid_indices(n: int) -> np.ndarray:
@@ -79,7 +80,7 @@ def sample_coefficient(problem: Problem, side: str = "primal") -> np.ndarray:
     x = grid_points(problem)
     if problem.bitmap is not None:
         # the pixel holding the grid point (pixel centres when N equals the image size)
-        b = problem.bitmap
+        b = image_values(problem)
         idx = tuple(np.clip(np.floor((x[..., a] / Y[a] + 0.5) * b.shape[a]).astype(np.int64), 0, b.shape[a] - 1)
                     for a in range(d))
         A = b[idx][..., None, None] * np.eye(d)

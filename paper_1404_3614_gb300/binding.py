@@ -37,7 +37,8 @@ class hom_inclusion(C.Structure):
 class hom_problem(C.Structure):
     _fields_ = [("d", C.c_int32), ("N", C.c_int32 * 3), ("Y", C.c_double * 3), ("A0", C.c_double * 9),
                 ("n_incl", C.c_int32), ("reserved", C.c_int32), ("incl", C.POINTER(hom_inclusion)),
-                ("bitmap", C.POINTER(C.c_double)), ("bitmap_n", C.c_int32 * 3), ("closed", C.c_int32)]
+                ("bitmap", C.POINTER(C.c_double)), ("bitmap_n", C.c_int32 * 3), ("closed", C.c_int32),
+                ("smooth", C.c_int32)]
 
 
 class hom_opts(C.Structure):
@@ -116,6 +117,7 @@ def _load():
         "hom_set_batch_cluster": (i32, [vp, i32, i32]),
         "hom_profile_kernel": (i32, [vp, C.c_char_p]),
         "hom_kernel_timing": (i32, [vp, P(i64), dp]),
+        "hom_peak_probe": (i32, [vp, i32, vp, dp]),
     }
     for name, (res, args) in sigs.items():
         fn = getattr(lib, name)
@@ -183,6 +185,7 @@ def problem_struct(problem):
     else:
         p.bitmap_n[:] = [1, 1, 1]
     p.closed = 1 if getattr(problem, "closed", False) else 0
+    p.smooth = 1 if getattr(problem, "smooth", False) else 0
     return p, keep
 
 
@@ -393,6 +396,13 @@ def hom_kernel_timing(ctx):
     ms = C.c_double()
     check(ctx, lib.hom_kernel_timing(ctx, C.byref(n), C.byref(ms)))
     return n.value, ms.value
+
+
+def hom_peak_probe(ctx, precision, stream=0):
+    """Measured FMA rate (TFLOP/s) of this GPU in HOM_FP32 or HOM_FP64."""
+    t = C.c_double()
+    check(ctx, lib.hom_peak_probe(ctx, precision, stream, C.byref(t)))
+    return t.value
 
 
 # ------------------------------------------------------------------------------------

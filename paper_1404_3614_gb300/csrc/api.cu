@@ -144,6 +144,7 @@ struct Geometry {
   int P[3] = {1, 1, 1};
   FftPlan pplan[3];            // DFT plans of the image lengths
   uint64_t bitmap_hash = 0;
+  int smooth = 0;              // replace the image by its local average (Sec. 7.3) on the device
   int closed = 0;              // GaNi: boundary grid points belong to the inclusion (Eq. S2)
   // GaNi on the double grid (an N without a fast FFT length): the GaNi matrix as the Galerkin
   // operator of the periodized sample spectrum; nplan are the N-point DFT plans of the samples
@@ -278,6 +279,9 @@ hom_status build_geometry(hom_ctx* ctx, const hom_problem* P, Geometry& g, bool 
   g.Nxs = (g.M[0] + 1) / 2;
   if (P->closed != 0 && P->closed != 1) return fail(ctx, HOM_ERR_INVALID_ARG, "closed must be 0 or 1");
   g.closed = P->closed;
+  if (P->smooth != 0 && P->smooth != 1) return fail(ctx, HOM_ERR_INVALID_ARG, "smooth must be 0 or 1");
+  if (P->smooth && !P->bitmap) return fail(ctx, HOM_ERR_INVALID_ARG, "smooth applies to pixel images only");
+  g.smooth = P->smooth;
   if (P->bitmap) {
     if (P->n_incl != 0) return fail(ctx, HOM_ERR_INVALID_ARG, "a pixel image excludes inclusions");
     long long n = 1;
@@ -524,11 +528,17 @@ struct Runner {
     if (!g.bitmap.empty()) {
       push(&g.bitmap_hash, sizeof g.bitmap_hash);
       push(g.P, sizeof g.P);
+      push(&g.smooth, sizeof g.smooth);
     }
     if (key == ctx->tables_key) return HOM_OK;
     ctx->tables_key.clear();
     if (!g.bitmap.empty()) {
-      CK(h2d_copy(ctx, base + L.bmp, g.bitmap.data(), (size_t)g.npix() * 8, st));
+      if (g.smooth) {   // raw image into the DFT scratch, its local average into the image slot
+        CK(h2d_copy(ctx, base + L.bmpD[1], g.bitmap.data(), (size_t)g.npix() * 8, st));
+        KL(launch_bitmap_smooth(at<double>(L.bmpD[1]), at<double>(L.bmp), g.d, g.P, st));
+      } else {
+        CK(h2d_copy(ctx, base + L.bmp, g.bitmap.data(), (size_t)g.npix() * 8, st));
+      }
       for (int a = 0; a < 3; ++a) {
         std::vector<double2> w64;
         std::vector<float2> w32;
@@ -2149,6 +2159,41 @@ hom_status hom_profile_kernel(hom_ctx* ctx, const char* name) {
   ctx->ev_used = 0;
   ctx->graph_prof_ms = 0;
   ctx->graph_prof_n = 0;
+  return HOM_OK;
+}
+
+hom_status hom_peak_probe(hom_ctx* ctx, int32_t precision, void* stream, double* tflops) {
+  if (!ctx || !tflops || (precision != HOM_FP64 && precision != HOM_FP32))
+    return fail(ctx, HOM_ERR_INVALID_ARG, "hom_peak_probe: precision HOM_FP64 or HOM_FP32, tflops not NULL");
+  CKS(set_device(ctx));
+  const cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int fp64 = precision == HOM_FP64;
+  // 4 CTAs of 512 threads per SM; FP64 issues about 1/64 of the FP32 rate, so fewer steps
+  const int blocks = 4 * device_sms(ctx->device);
+  const int iters = fp64 ? 2048 : 65536;
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  double best = 1e30;
+  hom_status s = HOM_OK;
+  for (int rep = 0; rep < 6 && s == HOM_OK; ++rep) {
+    cudaError_t e = cudaEventRecord(e0, st);
+    if (e == cudaSuccess) e = launch_fma_probe(fp64, blocks, iters, st);
+    if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    float ms = 0;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    if (e != cudaSuccess) {
+      s = fail(ctx, HOM_ERR_CUDA, std::string("hom_peak_probe: ") + cudaGetErrorString(e));
+    } else if (rep > 0) {   // the first launch warms up clocks and caches
+      best = std::min(best, (double)ms);
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (s != HOM_OK) return s;
+  const double flops = 2.0 * 8.0 * (double)iters * (double)blocks * 512.0;
+  *tflops = flops / (best * 1e-3) / 1e12;
   return HOM_OK;
 }
 

@@ -353,6 +353,34 @@ __global__ void k_bitmap_load(const double* bmp, double2* D, long long n, int in
     D[i] = make_double2(invert ? 1.0 / bmp[i] : bmp[i], 0.0);
 }
 
+// The image's local average of Sec. 7.3: weight 1/2 for the pixel and 1/4 for each of its
+// two periodic neighbours along every axis, multiplied over the axes (in 2D: 4/16 the
+// pixel, 2/16 the edge neighbours, 1/16 the corners; 3D images take the same per-axis
+// weights). One output pixel per thread, summed in FP64.
+__global__ void k_bitmap_smooth(const double* __restrict__ raw, double* __restrict__ out, int d, int P0, int P1,
+                                int P2) {
+  const long long n = (long long)P0 * P1 * P2;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+    const int i0 = (int)(e % P0);
+    const int i1 = (int)((e / P0) % P1);
+    const int i2 = (int)(e / ((long long)P0 * P1));
+    const int r2 = d == 3 ? 1 : 0;
+    double acc = 0.0;
+    for (int o2 = -r2; o2 <= r2; ++o2) {
+      const int j2 = (i2 + o2 + P2) % P2;
+      const double w2 = d == 3 ? (o2 == 0 ? 0.5 : 0.25) : 1.0;
+      for (int o1 = -1; o1 <= 1; ++o1) {
+        const int j1 = (i1 + o1 + P1) % P1;
+        const double w1 = o1 == 0 ? 0.5 : 0.25;
+        const double* row = raw + ((long long)j2 * P1 + j1) * P0;
+        const double s = 0.25 * row[(i0 + P0 - 1) % P0] + 0.5 * row[i0] + 0.25 * row[(i0 + 1) % P0];
+        acc += (w2 * w1) * s;
+      }
+    }
+    out[e] = acc;
+  }
+}
+
 __global__ void k_rotate3(const double2* in, double2* out, int P0, int P1, int P2) {
   const long long n = (long long)P0 * P1 * P2;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
@@ -739,6 +767,11 @@ static int grid_blocks(long long n) {
 }
 cudaError_t launch_bitmap_load(const double* bmp, double2* D, long long n, int invert, cudaStream_t s) {
   k_bitmap_load<<<grid_blocks(n), kThreads, 0, s>>>(bmp, D, n, invert);
+  return cudaGetLastError();
+}
+cudaError_t launch_bitmap_smooth(const double* raw, double* out, int d, const int P[3], cudaStream_t s) {
+  const long long n = (long long)P[0] * P[1] * P[2];
+  k_bitmap_smooth<<<grid_blocks(n), kThreads, 0, s>>>(raw, out, d, P[0], P[1], P[2]);
   return cudaGetLastError();
 }
 cudaError_t launch_rotate3(const double2* in, double2* out, int P0, int P1, int P2, cudaStream_t s) {

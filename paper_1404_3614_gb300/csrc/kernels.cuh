@@ -217,6 +217,10 @@ cudaError_t launch_cg_beta(CgScalars* cg, const double* partial, int ld, int nbl
 cudaError_t launch_sample_coef(const SpecArgs& a, double* coef, cudaStream_t s);
 // pixel image: D = a (or 1 / a) as complex, n values
 cudaError_t launch_bitmap_load(const double* bmp, double2* D, long long n, int invert, cudaStream_t s);
+// FMA-rate probe: `blocks` CTAs of 512 threads, 8 chains x `iters` FMAs per thread
+cudaError_t launch_fma_probe(int precision_fp64, int blocks, int iters, cudaStream_t s);
+// the local average of a pixel image (Sec. 7.3), periodic, out-of-place
+cudaError_t launch_bitmap_smooth(const double* raw, double* out, int d, const int P[3], cudaStream_t s);
 // out[a][c][b] = in[c][b][a] for an [P2][P1][P0] array (the next axis becomes contiguous)
 cudaError_t launch_rotate3(const double2* in, double2* out, int P0, int P1, int P2, cudaStream_t s);
 // spectrum of a pixel image on the half of Z_M (layout of launch_spectrum, one component) from

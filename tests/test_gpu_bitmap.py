@@ -5,7 +5,9 @@ centring phase) and zero-padded to the double grid; the right-hand side is the o
 applied to the constant field. Parity against the oracle (which sums the pixel boxes
 directly): the double-grid coefficient to 1e-12, FP64 bounds to 1e-10, mixed to 1e-6, GaNi
 on the image grid to 1e-10; images of odd and even size, N equal to and different from the
-image size, 2D and 3D.
+image size, 2D and 3D. The paper's local average of the image (Sec. 7.3) is a flag of the
+problem: the library smooths the uploaded image on the device, the oracle by its own
+circulant-matrix products (oracle/image.py); both start from the same raw image.
 """
 import numpy as np
 import pytest
@@ -33,6 +35,9 @@ CELLS = {
     "rect_cell_P7x5_N7x5": lambda: ms.bitmap_problem(two_phase(4, (7, 5)), N=(7, 5), Y=(1.0, 0.6)),
     "image3d_P5_N5": lambda: ms.bitmap_problem(two_phase(5, (5, 5, 5)), N=5),
     "image3d_P4_N7": lambda: ms.bitmap_problem(two_phase(6, (4, 4, 4), a=(3.0, 0.5)), N=7),
+    "smoothed_P9_N9": lambda: ms.bitmap_problem(two_phase(7, (9, 9)), smooth=True),
+    "smoothed_P10x7_N5x7": lambda: ms.bitmap_problem(two_phase(8, (10, 7)), N=(5, 7), Y=(1.0, 0.7), smooth=True),
+    "smoothed3d_P5_N5": lambda: ms.bitmap_problem(two_phase(9, (5, 5, 5), a=(3.0, 0.5)), N=5, smooth=True),
 }
 
 
@@ -84,7 +89,8 @@ def test_image_bounds_match_dense_oracle(hb, solver, name):
         assert rel(mixed[key], ref[key]) <= 1e-6, (key, rel(mixed[key], ref[key]))
 
 
-@pytest.mark.parametrize("name", ["two_phase_P9_N9", "rect_cell_P7x5_N7x5", "image3d_P5_N5", "two_phase_P9_N5"])
+@pytest.mark.parametrize("name", ["two_phase_P9_N9", "rect_cell_P7x5_N7x5", "image3d_P5_N5", "two_phase_P9_N5",
+                                  "smoothed_P9_N9", "smoothed3d_P5_N5"])
 def test_image_gani_matches_oracle(hb, solver, name):
     p = CELLS[name]()
     ref = gani.gani_bounds(p)
@@ -102,6 +108,30 @@ def test_porous_image_against_double_grid_cg_oracle(hb, solver):
     out = solver(p, precision=hb.HOM_FP64, tol=1e-11)
     for key in ("upper", "lower"):
         assert rel(out[key], ref[key]) <= 1e-9, (key, rel(out[key], ref[key]))
+
+
+def test_smoothed_porous_image_against_double_grid_cg_oracle(hb, solver):
+    """The same kind of 63 x 63 porous image with the paper's smoothing applied by the library
+    (FP64 and mixed) against O2 on the oracle's own smoothing of the raw image; the smoothing
+    moves the bounds by far more than the tolerance."""
+    img = ms.porous_bitmap_2d(8, P=63, r_min=0.03, r_max=0.1)
+    p = ms.bitmap_problem(img, smooth=True)
+    ref = oracle.matfree_bounds(p, tol=1e-11)
+    out = solver(p, precision=hb.HOM_FP64, tol=1e-11)
+    mixed = solver(p, precision=hb.HOM_MIXED, tol=1e-8)
+    raw = solver(ms.bitmap_problem(img), precision=hb.HOM_FP64, tol=1e-11)
+    for key in ("upper", "lower"):
+        assert rel(out[key], ref[key]) <= 1e-9, (key, rel(out[key], ref[key]))
+        assert rel(mixed[key], ref[key]) <= 1e-6, (key, rel(mixed[key], ref[key]))
+        assert rel(raw[key], ref[key]) > 1e-4
+
+
+def test_smoothing_needs_an_image(hb, solver):
+    p = ms.square_inclusion_2d(N=9)
+    import dataclasses
+    with pytest.raises(hb.HombError) as e:
+        solver(dataclasses.replace(p, smooth=True), precision=hb.HOM_FP64)
+    assert e.value.status == hb.binding.HOM_ERR_INVALID_ARG
 
 
 def test_image_rejected_where_not_supported(hb, solver):

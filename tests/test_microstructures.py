@@ -62,14 +62,10 @@ def test_overlap_rules():
     assert not ms.inclusions_overlap(d1, ms.box([0.35, 0.0], [0.2, 0.2], 2.0, 2), Y)
 
 
-def test_image_smoothing_and_porous_image():
-    f = np.zeros((7, 7))
-    f[0, 0] = 1.0
-    g = ms.smooth_indicator_2d(f)
-    assert abs(g.sum() - 1.0) < 1e-15 and abs(g[0, 0] - 0.25) < 1e-15
-    assert abs(g[1, 0] - 0.125) < 1e-15 and abs(g[-1, -1] - 0.0625) < 1e-15 and g[3, 3] == 0.0
-    assert np.allclose(ms.smooth_indicator_2d(np.full((5, 5), 0.3)), 0.3)
+def test_porous_image_is_raw_and_smoothing_is_a_flag():
     b = ms.porous_bitmap_2d(1, P=101, porosity=0.4)
     assert set(np.unique(b)) <= {0.029, 0.49} and abs((b == 0.029).mean() - 0.4) < 0.05
-    bs = ms.porous_bitmap_2d(1, P=101, porosity=0.4, smooth=True)
-    assert bs.min() >= 0.029 - 1e-15 and bs.max() <= 0.49 + 1e-15 and abs(bs.mean() - b.mean()) < 1e-12
+    p = ms.bitmap_problem(b, smooth=True)
+    assert p.smooth and np.array_equal(p.bitmap, b)       # the image is stored unsmoothed
+    assert not ms.bitmap_problem(b).smooth
+    assert not hasattr(ms, "smooth_indicator_2d")         # no method step in the input module
