@@ -1,19 +1,21 @@
 #!/usr/bin/env python
-"""Benchmark: time to guaranteed bounds on the 3D cube cell, N = 41^3 (double grid 81^3).
+"""Benchmark: time to guaranteed bounds on the 3D cell with 16 random balls, N = 113^3.
 
-One step = one hom_bounds call = the whole hot path: both double-grid coefficients
-built from the closed-form inclusion coefficients, 3 primal and 3 dual CG solves (E =
-e1, e2, e3) to a relative residual of 1e-4, FP64 re-projection and the exact
-double-grid bound energies, upper and inv(lower) on the host.
+One step = one hom_bounds call = the whole hot path: both double-grid coefficients built
+from the closed-form ball coefficients, 3 primal and 3 dual CG solves (E = e1, e2, e3) to a
+relative residual of 1e-4 with FP32 inner CG and FP64 outer refinement, FP64 re-projection
+and the exact double-grid bound energies, upper and inv(lower) on the host.
 
-Prints one JSON line (rank 0). Default: 1 GPU, plain FP64 CG (the workload's stated
-precision), 10 timed steps after 3 warm-up steps, L2 flushed between steps. Extra
-keys report the mixed-precision path (FP32 inner CG, FP64 outer) on the same
-workload and single-matvec timings. ``--impl reference`` times the CPU oracle
-instead (the reference arm of this comparison).
+Prints one JSON line (rank 0). Default: 1 GPU, mixed precision (the workload's stated
+"FP32 inner CG with FP64 bounds"), 10 timed steps after 3 warm-up steps, L2 flushed between
+steps. The same line carries plain FP64 CG on the same cell (the "vs plain FP64 CG" part of
+the metric), the roofline of the dominant kernel (the fused FP32 slab pass of the operator,
+against the measured HBM bandwidth), the measured FMA peaks, the 3D cube cell, the 256-cell
+batched launch against all 256 cells solved one by one in FP64, and the CPU oracle timed on
+a bounded sample. ``--impl reference`` times the CPU oracle instead (the reference arm).
 
-Multi-GPU: independent replicas (the path does not shard): under torchrun each rank
-runs the same workload on its own GPU; timing is max over ranks.
+Multi-GPU: independent replicas (the path does not shard): under torchrun each rank runs the
+same workload on its own GPU; timing is max over ranks.
 """
 from __future__ import annotations
 
@@ -31,48 +33,65 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "time to bounds at 1e-4 rel. residual; matvec HBM GB/s; vs plain FP64 CG"
-WORKLOAD = ("3D d=3, N=41^3 (double grid 81^3), centred cube inclusion side 0.5, contrast 100 "
-            "(a=1 matrix, a=100 inclusion), plain CG, primal and dual bounds for E=e1,e2,e3, "
-            "stop at ||r|| <= 1e-4 ||E||")
+WORKLOAD = ("3D d=3, N=113^3 (double grid 225^3), 16 random non-overlapping balls (seed 0), volume "
+            "fraction 0.3, contrast 1000 (a=1 matrix, a=1000 balls), FP32 inner CG with FP64 refinement, "
+            "re-projection and bounds, primal and dual bounds for E=e1,e2,e3, stop at ||r|| <= 1e-4 ||E||")
+CUBE_WORKLOAD = ("3D d=3, N=41^3 (double grid 81^3), centred cube inclusion side 0.5, contrast 100 "
+                 "(a=1 matrix, a=100 inclusion), plain FP64 CG")
 TOL = 1e-4
-# FP64 CG iterations of this workload at 1e-4 (primal, dual), per right-hand side: a
-# property of the problem (CG in exact arithmetic); measured by running the oracle's
-# own CG to completion, pinned by tests/test_bench_host.py.
+# FP64 CG iterations of the cube cell at 1e-4 (primal, dual), per right-hand side: a property
+# of the problem (CG in exact arithmetic), from the oracle's own CG, pinned by
+# tests/test_bench_host.py.
 ORACLE_ITERS = {"primal": 46, "dual": 24}
-HBM_PEAK_GBS = 6782.8       # measured copy bandwidth of the GB300s (MEASURED_PEAKS.json)
-FP64_PEAK_TFLOPS = 1.25     # nominal GB300 FP64 (the recipe's table); a probe measured 1.256
-
-# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one k_xpass<double, 81> launch
-# on the 3D N = 41 cube workload (3 fields, isotropic coefficient), from one ncu capture of
-# the build whose kernel sources hash to `sha256_16`; reported only while they still do.
-XPASS_TRAFFIC = {"sha256_16": "e18ef698bd254de5", "bytes": 24164352 + 26368, "fp64_pipe_active": 0.8375,
-                 "sources": ("common.cuh", "kernels.cuh", "passes.cuh", "passes_f64.cu"),
-                 "capture": "profiles/xpass_f64_cube3d_N41.md"}
+GOLDEN = os.path.join(ROOT, "tests", "golden", "fullsize_bounds.json")
+FALLBACK_HBM_GBS = 6800.0     # used only when MEASURED_PEAKS.json is absent ("of fallback")
 
 
-def xpass_traffic(workload_name, precision):
-    """Per-launch DRAM traffic of the FP64 row pass, or None once the kernel has changed."""
+def measured_peaks():
+    """The measured peaks of the GB300s (copy bandwidth, bf16 GEMM)."""
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return {"hbm_gbs": float(d["hbm_gbs"]), "source": "of measured (MEASURED_PEAKS.json)"}
+    except Exception:
+        return {"hbm_gbs": FALLBACK_HBM_GBS, "source": "of fallback (recipe: 6.8 TB/s)"}
+
+
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one k_slab<float, 15> launch on
+# the 16-ball cell (9 fields, 3 right-hand sides), from one ncu capture of the build whose
+# kernel sources hash to `sha256_16`; reported only while they still do.
+SLAB_TRAFFIC = {"sha256_16": None, "bytes": None, "sources": ("common.cuh", "kernels.cuh", "slab.cuh"),
+                "capture": "profiles/slab_f32_spheres3d_N113.md"}
+
+
+def source_hash(files) -> str:
     import hashlib
-    if workload_name != "cube3d_N41" or precision != "fp64":
-        return None
     h = hashlib.sha256()
-    src = os.path.join(os.path.dirname(os.path.abspath(__file__)), "paper_1404_3614_gb300", "csrc")
-    for f in XPASS_TRAFFIC["sources"]:
+    src = os.path.join(ROOT, "paper_1404_3614_gb300", "csrc")
+    for f in files:
         with open(os.path.join(src, f), "rb") as fh:
             h.update(fh.read())
-    return XPASS_TRAFFIC["bytes"] if h.hexdigest()[:16] == XPASS_TRAFFIC["sha256_16"] else None
+    return h.hexdigest()[:16]
+
+
+def slab_traffic():
+    """Per-launch DRAM traffic of the slab pass from ncu, or None once the kernel has changed."""
+    if SLAB_TRAFFIC["sha256_16"] is None:
+        return None
+    return SLAB_TRAFFIC["bytes"] if source_hash(SLAB_TRAFFIC["sources"]) == SLAB_TRAFFIC["sha256_16"] else None
 
 
 WORKLOADS = {
-    "cube3d_N41": "3D cube cell N=41^3 (double grid 81^3), contrast 100",
     "spheres3d_N113": "3D cell with 16 random balls, volume fraction 0.3, contrast 1000, N=113^3 (double grid 225^3), seed 0",
+    "cube3d_N41": "3D cube cell N=41^3 (double grid 81^3), contrast 100",
     "square2d_N23": "2D square inclusion side 0.6, a=1/10, N=23^2 (double grid 45^2)",
     "porous2d_N1199": "2D synthetic porous pixel image 1199^2 (pores: union of random disks, fraction 0.45), "
                       "a = 0.49 / 0.029, N = 1199 (double grid 2397^2)",
 }
 
 
-def workload(name: str = "cube3d_N41"):
+def workload(name: str = "spheres3d_N113"):
     import microstructures as ms
     if name == "cube3d_N41":
         return ms.cube_inclusion_3d()
@@ -83,6 +102,17 @@ def workload(name: str = "cube3d_N41"):
     if name == "porous2d_N1199":
         return ms.bitmap_problem(ms.porous_bitmap_2d(0, P=1199))
     raise ValueError(name)
+
+
+def oracle_iters_c5():
+    """CG iterations per right-hand side to 1e-4 of the 16-ball cell, read off the residual
+    history of the oracle's own CG (tests/golden/make_fullsize_goldens.py); None if absent."""
+    try:
+        with open(GOLDEN) as f:
+            it = json.load(f)["spheres3d_N113"]["iters_to_1e-4"]
+        return {"primal": it[0], "dual": it[1]}
+    except Exception:
+        return None
 
 
 def run_learned(args):
@@ -135,7 +165,7 @@ def run_batched_only(args):
         hb.binding.hom_set_batch_threads(solver.ctx, args.batch_threads)
     if args.batch_cluster:
         hb.binding.hom_set_batch_cluster(solver.ctx, args.batch_cluster, args.batch_coop_M)
-    res = batched_timings(hb, solver, torch.device("cuda", 0), n=args.batch_n, n_seq=2, autotune=0 if fixed else 1)
+    res = batched_timings(hb, solver, torch.device("cuda", 0), n=args.batch_n, autotune=0 if fixed else 1)
     print(json.dumps({"batched": res}), flush=True)
     solver.close()
     return 0
@@ -255,7 +285,7 @@ def run_gemm_only(args):
     flops = 2.0 * M * N * K
     byt = 4.0 * (M * K + K * N + M * N)
     print(json.dumps({"gemm": {"M": M, "N": N, "K": K, "ms": ms, "tflops": flops / ms / 1e9,
-                               "gbs": byt / ms / 1e6, "hbm_frac": byt / ms / 1e6 / HBM_PEAK_GBS,
+                               "gbs": byt / ms / 1e6, "hbm_frac": byt / ms / 1e6 / measured_peaks()["hbm_gbs"],
                                "max_rel_err_vs_bf16_products": err}}), flush=True)
     return 0
 
@@ -370,23 +400,39 @@ def family_flops_per_launch(problem, family: str, nrhs: int) -> float:
 # ------------------------------------------------------------------------------------
 # CPU oracle leg
 # ------------------------------------------------------------------------------------
-def oracle_sample(problem, iters, n_matvec: int):
+def oracle_sample(problem, iters, n_matvec: int = 2, n_slabs: int = 8):
     """Time the oracle on a bounded sample and extrapolate to one full time to bounds.
 
-    Sample: both double-grid coefficient builds (naive inverse DFT) + n_matvec
-    double-grid matvecs per side on one right-hand side. Estimate: coefficient builds
-    + (iters_side x d) matvecs per side + d/2 matvec-equivalents per side for the energies.
+    The oracle: O2 (matrix DFTs) for grids up to 81 points per axis, O3 (the same steps with
+    library FFTs, pinned to O2) beyond. Sample per side: the closed-form coefficient of
+    `n_slabs` of the M first-axis slabs of Z_M (O3; O2 builds it whole), one inverse FFT of
+    the whole grid, and `n_matvec` operator applications on one right-hand side. Estimate per
+    side: the coefficient (slabs scaled to M) + (iters x d + d for the right-hand sides + d for
+    the energies) matvecs, with iters the CG iteration counts per right-hand side.
     """
     import numpy as np
-    from oracle import matfree
+    from oracle import fftcg, matfree
     d = problem.d
-    total = 0.0
-    t_coef = 0.0
-    t_mv = {}
+    M = [2 * int(n) - 1 for n in problem.N]
+    use_o3 = max(M) > 81
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    t_coef, t_mv = {}, {}
     for side in ("primal", "dual"):
         t = time.perf_counter()
-        op = matfree.MatFreeOperator(problem, side)
-        t_coef += time.perf_counter() - t
+        if use_o3:
+            import scipy.fft as sfft
+            for i0 in range(n_slabs):
+                fftcg.coefficient_slab(problem, side, M, i0)
+            t_slab = (time.perf_counter() - t) / n_slabs
+            t = time.perf_counter()
+            grid = sfft.ifftn(np.zeros(M, dtype=np.complex128), workers=cores).real
+            t_coef[side] = t_slab * M[0] + (time.perf_counter() - t)
+            # the operator with a stand-in coefficient of the same shape: a matvec costs the
+            # same whatever the values
+            op = fftcg.FFTOperator(problem, side, workers=cores, A_grid=grid + 1.0)
+        else:
+            op = matfree.MatFreeOperator(problem, side)
+            t_coef[side] = time.perf_counter() - t
         u = op.constant_field(np.eye(d)[0])
         u = op.apply(u)
         t = time.perf_counter()
@@ -394,34 +440,51 @@ def oracle_sample(problem, iters, n_matvec: int):
             u = op.apply(u)
             u /= max(np.abs(u).max(), 1e-300)
         t_mv[side] = (time.perf_counter() - t) / n_matvec
+    total = sum(t_coef.values())
     for side in ("primal", "dual"):
-        total += (iters[side] * d + 0.5 * d) * t_mv[side]
-    est = (t_coef + total) * 1e3
-    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
-    threads = int(os.environ.get("OPENBLAS_NUM_THREADS", os.environ.get("OMP_NUM_THREADS", cores)))
-    sample = (f"oracle O2 (naive-DFT double-grid CG, numpy fp64): both coefficient builds + {n_matvec} "
-              f"matvecs per side on one RHS, timed; extrapolated with {iters['primal']}/{iters['dual']} "
-              f"CG iterations x {d} RHS per side + d/2 matvecs per side for the energies")
-    return est, {"value": est, "unit": "ms", "cores": min(threads, cores), "kind": "oracle", "sample": sample,
-                 "matvec_ms": {k: v * 1e3 for k, v in t_mv.items()}, "coef_ms": t_coef * 1e3}
+        it = iters[side]
+        total += (sum(it) if isinstance(it, (list, tuple)) else it * d) * t_mv[side] + 2 * d * t_mv[side]
+    est = total * 1e3
+    which = "O3 (library-FFT double-grid CG, scipy.fft, numpy fp64)" if use_o3 else \
+        "O2 (matrix-DFT double-grid CG, numpy fp64)"
+    sample = (f"oracle {which}: per side the closed-form coefficient of "
+              f"{n_slabs if use_o3 else M[0]} of {M[0]} slabs and {n_matvec} matvecs on one RHS, timed; "
+              f"extrapolated with the CG iteration counts {iters} + 2d matvecs per side (right-hand sides, "
+              f"energies)")
+    return est, {"value": est, "unit": "ms", "cores": cores, "kind": "oracle", "sample": sample,
+                 "extrapolated": True, "matvec_ms": {k: v * 1e3 for k, v in t_mv.items()},
+                 "coef_ms": {k: v * 1e3 for k, v in t_coef.items()}}
+
+
+def reference_iters(problem, name):
+    if name == "spheres3d_N113":
+        it = oracle_iters_c5()
+        if it is not None:
+            return it
+        # not yet in the golden file: the GPU FP64 counts of this cell (primal, dual per rhs)
+        return {"primal": [176, 176, 176], "dual": [49, 51, 49]}
+    return dict(ORACLE_ITERS)
 
 
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
         return 0
-    problem = workload()
+    problem = workload(args.workload)
+    iters = reference_iters(problem, args.workload)
     vals = []
     info = None
     for i in range(args.warmup + args.steps):
-        v, info = oracle_sample(problem, ORACLE_ITERS, n_matvec=max(2, args.ref_matvecs // 3))
+        v, info = oracle_sample(problem, iters, n_matvec=1 if i < args.warmup else 2, n_slabs=4)
         if i >= args.warmup:
             vals.append(v)
     value = statistics.mean(vals)
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "ms", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": value, "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "impl": "CPU oracle (naive DFT double-grid CG)"},
+            "config": {"workload": WORKLOAD if args.workload == "spheres3d_N113" else WORKLOADS[args.workload],
+                       "impl": "CPU oracle (double-grid CG, FP64), bounded sample, extrapolated"},
+            "extrapolated": True,
             "cpu_baseline": info, "e2e": {"value": value, "unit": "ms", "h2d_bytes_per_step": 0,
                                           "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -431,6 +494,23 @@ def run_reference(args):
 # ------------------------------------------------------------------------------------
 # GPU leg
 # ------------------------------------------------------------------------------------
+def timed_steps(stream, flush, fn, n):
+    """n calls of fn, each bracketed by CUDA events on `stream`, L2 flushed before each
+    (outside the events); returns the per-call device times (ms) and the last result."""
+    import torch
+    ts, out = [], None
+    for _ in range(n):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        out = fn()
+        e1.record(stream)
+        e1.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    return ts, out
+
+
 def run_gpu(args):
     import numpy as np
     import torch
@@ -451,50 +531,26 @@ def run_gpu(args):
     stream = torch.cuda.current_stream(dev)
     s_ptr = stream.cuda_stream
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)   # > L2 (129 MB)
+    peaks = measured_peaks()
 
-    def step(precision):
-        return solver(problem, precision=precision, tol=TOL, stream=s_ptr)
+    def step(precision, p=problem):
+        return solver(p, precision=precision, tol=TOL, stream=s_ptr)
 
     for _ in range(args.warmup):
         out = step(prec)
     torch.cuda.synchronize()
 
-    # dominant kernel family: one untimed profiled step per family
-    fam_ms = {}
-    for fam in ("slab", "xpass", "ypass", "zpass", "final", "cg", "coef", "energy"):
-        hb.hom_profile_kernel(solver.ctx, fam)
-        step(prec)
-        n, ms = hb.hom_kernel_timing(solver.ctx)
-        fam_ms[fam] = (n, ms)
-    hb.hom_profile_kernel(solver.ctx, "")
-    dom = max(fam_ms, key=lambda f: fam_ms[f][1])
-
-    # timed region: K steps, device time by CUDA events on the launching stream,
-    # L2 flushed between steps (outside the events), dominant family timed live
-    hb.hom_profile_kernel(solver.ctx, dom)
-    times = []
-    launches = 0
+    # timed region: K steps, device time by CUDA events on the launching stream, L2 flushed
+    # between steps (outside the events), no per-kernel instrumentation
     reports = []
     barrier(world)
     torch.cuda.synchronize()
     with ClockSampler(local) as clk:
-        for _ in range(args.steps):
-            flush.zero_()
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            out = step(prec)
-            e1.record(stream)
-            e1.synchronize()
-            times.append(e0.elapsed_time(e1))
-            reports.append(out["report"])
-            launches += out["report"]["launches"]
+        times, out = timed_steps(stream, flush, lambda: step(prec), args.steps)
     torch.cuda.synchronize()
     barrier(world)
-    dom_n, dom_ms = hb.hom_kernel_timing(solver.ctx)
-    hb.hom_profile_kernel(solver.ctx, "")
-    ms_step = statistics.mean(times)
-    ms_step = max_over_ranks(ms_step, world, dev)
+    launches = out["report"]["launches"] * args.steps
+    ms_step = max_over_ranks(statistics.mean(times), world, dev)
 
     # end to end through the public API: host problem in, host bounds out, wall clock. Two
     # workspaces alternate, as for two requests in flight, so every step uploads its problem
@@ -505,7 +561,7 @@ def run_gpu(args):
 
     def step_e2e(i):
         return hb.hom_bounds(solver.ctx, problem, opts_e2e, wss[i % 2].data_ptr(), nbytes, s_ptr)
-    for i in range(2 * args.warmup):
+    for i in range(2):
         step_e2e(i)
     e2e = []
     for i in range(max(4, args.steps // 2)):
@@ -518,115 +574,30 @@ def run_gpu(args):
     rep = o["report"]
     del wss
 
-    # the other precision on the same workload (plain FP64 vs mixed)
-    other = hb.HOM_MIXED if prec == hb.HOM_FP64 else hb.HOM_FP64
-    alt = []
-    for _ in range(max(3, args.steps // 2)):
-        flush.zero_()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        oo = step(other)
-        e1.record(stream)
-        e1.synchronize()
-        alt.append(e0.elapsed_time(e1))
-    alt_ms = statistics.mean(alt)
-
-    # variants of the method on the same workload (FP64, same tolerance): the dual CG started
-    # from the primal minimisers, and GaNi (the paper's algorithm: N-grid CG, double-grid
-    # bounds) from zero and with the dual start, which is exact for GaNi on odd grids
-    def timed(**kw):
-        ts, o_ = [], None
-        for _ in range(3):
-            flush.zero_()
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            o_ = solver(problem, tol=TOL, stream=s_ptr, **kw)
-            e1.record(stream)
-            e1.synchronize()
-            ts.append(e0.elapsed_time(e1))
-        return statistics.mean(ts), o_
-    variants = {}
-    F64, MIX = {"precision": hb.HOM_FP64}, {"precision": hb.HOM_MIXED}
-    for name, kw in (("dual_start", {"dual_start": 1, **F64}), ("gani", {"discretization": 1, **F64}),
-                     ("gani_dual_start", {"discretization": 1, "dual_start": 1, **F64}),
-                     ("gani_mixed", {"discretization": 1, **MIX}),
-                     ("gani_mixed_dual_start", {"discretization": 1, "dual_start": 1, **MIX})):
-        timed(**kw)   # untimed first call (graph capture, tables)
-        ms_v, o_v = timed(**kw)
-        variants[name] = {"ms": ms_v, "iters": o_v["report"]["iters"], "upper_11": float(o_v["upper"][0, 0]),
-                          "lower_11": float(o_v["lower"][0, 0])}
-        if "gani_A" in o_v:
-            variants[name]["gani_A_11"] = float(o_v["gani_A"][0, 0])
-            variants[name]["gani_invB_11"] = float(np.linalg.inv(o_v["gani_B"])[0, 0])
-
-    # one operator application (3 fields) per precision, through hom_matvec
-    mv = matvec_timings(hb, solver, problem, dev, stream)
-    # the 225^3 operator of the 16-ball cell, where the HBM fraction is claimed
-    mv_large = None
-    if args.workload != "spheres3d_N113":
-        mv_large = matvec_timings(hb, solver, workload("spheres3d_N113"), dev, stream, reps=10)
-        mv_large["workload"] = WORKLOADS["spheres3d_N113"]
-    batched = None if args.no_batched else batched_timings(hb, solver, dev)
-    image = None if args.no_batched else image_timings(hb, solver, stream, flush)
-
-    # roofline of the dominant kernel family
-    nrhs = problem.d
-    per_launch_ms = dom_ms / max(dom_n, 1)
-    flops = family_flops_per_launch(problem, dom, nrhs)
-    roof = None
-    if flops > 0 and per_launch_ms > 0:
-        achieved = flops / (per_launch_ms * 1e-3) / 1e12
-        roof = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
-                "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
-                "traffic": xpass_traffic(args.workload, args.precision) if dom == "xpass" else None,
-                "flops_per_launch": flops, "launches": dom_n, "avg_launch_ms": per_launch_ms,
-                "peak_note": "FP64 nominal 1.25 TFLOP/s (recipe table); FMA probe measured 1.256"}
-        if prec != hb.HOM_FP64:
-            roof["note"] = "mixed: dominant family mixes FP32 inner and FP64 outer launches"
-        if roof["traffic"] is not None:
-            roof["traffic_note"] = ("ncu DRAM bytes per launch (" + XPASS_TRAFFIC["capture"] + "): the "
-                                    "input fields and coefficient are read once; the in-place output "
-                                    "stays in L2 during the launch")
-            # the same capture: the FP64 pipe is busy this fraction of the active cycles; the
-            # conventional 5 M log2 M flop count undercounts an add-heavy radix-3 FFT, so frac
-            # reads well below the pipe's own occupancy
-            roof["fp64_pipe_active_ncu"] = XPASS_TRAFFIC["fp64_pipe_active"]
-
     line = {
         "metric": METRIC, "value": ms_step, "unit": "ms", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": False, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64" if prec == hb.HOM_FP64 else "f32+f64",
-        "data": "synthetic",
-        "config": {"workload": WORKLOAD if args.workload == "cube3d_N41" else WORKLOADS[args.workload],
+        "vs_baseline": None, "dtype": "f64" if prec == hb.HOM_FP64 else "f32+f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD if args.workload == "spheres3d_N113" else WORKLOADS[args.workload],
                    "precision": args.precision, "tol": TOL,
                    "l2": "flushed between steps (256 MiB write, outside the timed region)",
                    "launch": "CG iterations in blocks of 8 replayed from captured CUDA graphs",
                    "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
-        "bounds": {"upper_11": float(out["upper"][0, 0]), "lower_11": float(out["lower"][0, 0])},
-        "iters": reports[-1]["iters"], "matvecs": reports[-1]["matvecs"],
+        "bounds": {"upper": out["upper"].tolist(), "lower": out["lower"].tolist()},
+        "iters": out["report"]["iters"], "matvecs": out["report"]["matvecs"],
         "gpu_launches": launches,
         "e2e": {"value": e2e_ms, "unit": "ms", "h2d_bytes_per_step": rep["h2d_bytes"],
                 "d2h_bytes_per_step": rep["d2h_bytes"],
                 "note": "hom_bounds wall clock: host problem in (tables uploaded every step, two workspaces "
                         "alternating), host bounds out"},
-        "alt_precision": {"precision": "mixed" if other == hb.HOM_MIXED else "fp64", "ms": alt_ms,
-                          "speedup_vs_this": ms_step / alt_ms if alt_ms > 0 else None,
-                          "upper_11": float(oo["upper"][0, 0]), "lower_11": float(oo["lower"][0, 0])},
-        "variants": variants,
-        "matvec": mv,
-        "matvec_225": mv_large,
-        "batched": batched,
-        "image": image,
-        "kernel_families_ms_one_step": {k: v[1] for k, v in fam_ms.items()},
-        "roofline": roof,
         "clocks": clk.summary(),
     }
+    if rank == 0 and not args.headline_only:
+        line.update(extras(args, hb, solver, problem, prec, dev, stream, flush, peaks, ms_step))
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        iters = {"primal": max(reports[-1]["iters"][0]), "dual": max(reports[-1]["iters"][1])}
-        _, info = oracle_sample(problem, iters, n_matvec=args.ref_matvecs)
+        _, info = oracle_sample(problem, reference_iters(problem, args.workload))
         line["cpu_baseline"] = info
+    barrier(world)
     if rank == 0:
         print(json.dumps(line), flush=True)
     solver.close()
@@ -636,12 +607,81 @@ def run_gpu(args):
     return 0
 
 
-def batched_timings(hb, solver, dev, n=256, reps=3, n_seq=8, autotune=1):
+def extras(args, hb, solver, problem, prec, dev, stream, flush, peaks, ms_step):
+    """Everything the line reports beside the headline (rank 0, after the timed region)."""
+    import numpy as np
+    s_ptr = stream.cuda_stream
+    res = {}
+    # plain FP64 CG on the same cell (the metric's comparison)
+    other = hb.HOM_FP64 if prec == hb.HOM_MIXED else hb.HOM_MIXED
+    solver(problem, precision=other, tol=TOL, stream=s_ptr)
+    ts, oo = timed_steps(stream, flush, lambda: solver(problem, precision=other, tol=TOL, stream=s_ptr),
+                         args.fp64_steps)
+    res["alt_precision"] = {"precision": "fp64" if other == hb.HOM_FP64 else "mixed", "ms": statistics.mean(ts),
+                            "steps": len(ts), "iters": oo["report"]["iters"],
+                            "upper": oo["upper"].tolist(), "lower": oo["lower"].tolist()}
+    if other == hb.HOM_FP64:
+        res["alt_precision"]["mixed_speedup_vs_fp64"] = statistics.mean(ts) / ms_step
+    # kernel families of one step (separate, instrumented steps: the timed steps carry no events)
+    fam_ms = {}
+    for fam in ("slab", "xpass", "ypass", "zpass", "final", "cg", "coef", "energy"):
+        hb.hom_profile_kernel(solver.ctx, fam)
+        solver(problem, precision=prec, tol=TOL, stream=s_ptr)
+        n, ms = hb.hom_kernel_timing(solver.ctx)
+        fam_ms[fam] = {"launches": n, "ms": ms}
+    hb.hom_profile_kernel(solver.ctx, "")
+    res["kernel_families_one_step"] = fam_ms
+    # the operator: one application on d fields per precision; the slab pass timed per launch
+    mv = matvec_timings(hb, solver, problem, dev, stream, reps=20, profile="slab")
+    res["matvec"] = mv
+    # measured FMA peaks (the denominators of the ALU-bound passes)
+    p32 = hb.binding.hom_peak_probe(solver.ctx, hb.HOM_FP32, s_ptr)
+    p64 = hb.binding.hom_peak_probe(solver.ctx, hb.HOM_FP64, s_ptr)
+    res["fma_peaks_tflops"] = {"fp32": p32, "fp64": p64, "how": "hom_peak_probe: 8 FMA chains per thread, "
+                               "4 x 512 threads per SM, best of 5"}
+    # roofline of the dominant kernel of the step
+    dom = max(fam_ms, key=lambda f: fam_ms[f]["ms"])
+    res["dominant_family"] = dom
+    f32 = mv.get("fp32", {})
+    if problem.d == 3 and f32.get("profiled_launch_ms"):
+        byt = slab_model_bytes(problem, 4, problem.d)
+        ms_l = f32["profiled_launch_ms"]
+        achieved = byt / (ms_l * 1e-3) / 1e9
+        res["roofline"] = {
+            "bound": "hbm", "kernel": "k_slab<float,15>", "achieved": achieved, "peak": peaks["hbm_gbs"],
+            "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": slab_traffic(),
+            "algorithmic_bytes_per_launch": byt, "avg_launch_ms": ms_l, "launches_timed": f32["profiled_launches"],
+            "peak_note": peaks["source"],
+            "bytes_note": "passes 2-4 of the unfused 5-pass operator model (inverse y with padding, x rows with "
+                          "the coefficient, forward y with truncation) for 9 field components + one coefficient "
+                          "read per right-hand side; the fused kernel keeps the double-grid slab on chip, so "
+                          "its DRAM traffic is far below these bytes",
+            "fft_tflops": slab_flops(problem, problem.d) / (ms_l * 1e-3) / 1e12,
+            "fp32_fma_peak_tflops": p32,
+            "operator_3field_ms": f32["ms"], "operator_model_frac": f32["model_hbm_frac"]}
+    # the 3D cube cell (FP64 plain CG and mixed)
+    if not args.no_cube:
+        cube = workload("cube3d_N41")
+        cres = {"workload": CUBE_WORKLOAD}
+        for name, pr in (("fp64", hb.HOM_FP64), ("mixed", hb.HOM_MIXED)):
+            solver(cube, precision=pr, tol=TOL, stream=s_ptr)
+            ts, oc = timed_steps(stream, flush, lambda: solver(cube, precision=pr, tol=TOL, stream=s_ptr), 5)
+            cres[name] = {"ms": statistics.mean(ts), "iters": oc["report"]["iters"],
+                          "upper_11": float(oc["upper"][0, 0]), "lower_11": float(oc["lower"][0, 0])}
+        res["cube3d_N41"] = cres
+    if not args.no_batched:
+        res["batched"] = batched_timings(hb, solver, dev)
+    if args.image:
+        res["image"] = image_timings(hb, solver, stream, flush)
+    return res
+
+
+def batched_timings(hb, solver, dev, n=256, reps=3, autotune=1):
     """The batched workload: n seeded random-rectangle 2D cells (N from {23, 63, 113, 203}),
     FP32 inner CG / FP64 bounds, tol 1e-4, one persistent launch replayed as a CUDA graph
     after an autotuning pass (threads per CTA, chunk capacity, radix schedule, cluster size
     for the largest cells); against plain FP64 hom_bounds one cell at a time on the same
-    GPU (a sample of n_seq cells, extrapolated to n)."""
+    GPU, all n cells, wall clock."""
     import statistics as st_
     import torch
     import microstructures as ms
@@ -663,19 +703,20 @@ def batched_timings(hb, solver, dev, n=256, reps=3, n_seq=8, autotune=1):
         e1.synchronize()
         times.append(e0.elapsed_time(e1))
     ms_batch = st_.mean(times)
-    seq = []
-    for p in probs[:n_seq]:
-        torch.cuda.synchronize()
-        t = time.perf_counter()
+    for p in probs[:4]:                      # warm: plans and graphs of the four grid sizes
         solver(p, precision=hb.HOM_FP64, tol=TOL)
-        seq.append((time.perf_counter() - t) * 1e3)
-    seq_ms = st_.mean(seq) * n
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    for p in probs:
+        solver(p, precision=hb.HOM_FP64, tol=TOL)
+    torch.cuda.synchronize()
+    seq_ms = (time.perf_counter() - t) * 1e3
     return {"workload": f"{n} random-rectangle 2D cells, N from {{23,63,113,203}}, FP32 inner CG, FP64 bounds, tol {TOL:g}",
             "ms": ms_batch, "problems_per_s": n / (ms_batch * 1e-3), "launches": out["report"]["launches"],
             "launch_config": out["report"]["config"],
             "max_iters": int(out["iters"].max()), "status_nonzero": int((out["status"] != 0).sum()),
-            "sequential_fp64_ms_est": seq_ms, "speedup_vs_sequential_fp64": seq_ms / ms_batch,
-            "sequential_note": f"plain FP64 hom_bounds per cell, mean of the first {n_seq} cells x {n}"}
+            "sequential_fp64_ms": seq_ms, "speedup_vs_sequential_fp64": seq_ms / ms_batch,
+            "sequential_note": f"plain FP64 hom_bounds per cell, all {n} cells one after another, wall clock"}
 
 
 def image_timings(hb, solver, stream, flush):
@@ -725,8 +766,25 @@ def matvec_bytes(problem, elem_bytes: int) -> float:
     return fields * per * cplx + coef
 
 
-def matvec_timings(hb, solver, problem, dev, stream, reps=20, precisions=("fp64", "fp32")):
-    """Device time of one operator application on d fields, FP64 and FP32."""
+def slab_model_bytes(problem, elem_bytes: int, nrhs: int) -> float:
+    """Algorithmic bytes of one slab launch (3D): passes 2-4 of the operator model (inverse y
+    with zero padding, x rows with the coefficient, forward y with truncation) for nrhs x d
+    field components, each pass reading and writing its input and output once, plus one
+    coefficient read per right-hand side."""
+    N = [int(n) for n in problem.N]
+    M = [2 * n - 1 for n in N]
+    Nh = (N[0] + 1) // 2
+    per = Nh * (2 * M[2] * N[1] + 4 * M[2] * M[1])
+    return nrhs * problem.d * per * 2 * elem_bytes + nrhs * M[0] * M[1] * M[2] * elem_bytes
+
+
+def slab_flops(problem, nrhs: int) -> float:
+    return family_flops_per_launch(problem, "slab", nrhs)
+
+
+def matvec_timings(hb, solver, problem, dev, stream, reps=20, precisions=("fp64", "fp32"), profile=None):
+    """Device time of one operator application on d fields, FP64 and FP32; with `profile`
+    a kernel family, its launches are timed too (in separate, instrumented applications)."""
     import torch
     ctx = solver.ctx
     info = hb.hom_problem_info(ctx, problem)
@@ -743,25 +801,57 @@ def matvec_timings(hb, solver, problem, dev, stream, reps=20, precisions=("fp64"
         hb.hom_coefficient(ctx, problem, 0, prec, coef.data_ptr(), ws.data_ptr(), nws, stream.cuda_stream)
         x = torch.randn(shape, dtype=cdt, device=dev)
         y = torch.empty_like(x)
-        for _ in range(3):
+
+        def apply():
             hb.hom_matvec(ctx, problem, 0, prec, 1, d, coef.data_ptr(), x.data_ptr(), y.data_ptr(),
                           ws.data_ptr(), nws, stream.cuda_stream)
+        for _ in range(3):
+            apply()
+        n_rep = reps if name == "fp32" else max(3, reps // 6)
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        for _ in range(reps):
-            hb.hom_matvec(ctx, problem, 0, prec, 1, d, coef.data_ptr(), x.data_ptr(), y.data_ptr(),
-                          ws.data_ptr(), nws, stream.cuda_stream)
+        for _ in range(n_rep):
+            apply()
         e1.record(stream)
         e1.synchronize()
-        ms = e0.elapsed_time(e1) / reps
+        ms = e0.elapsed_time(e1) / n_rep
         flops = sum(family_flops_per_launch(problem, f, d) * (2 if f == "ypass" else 1)
                     for f in ("zpass", "ypass", "xpass", "final"))
         nbytes = matvec_bytes(problem, 8 if name == "fp64" else 4)
         gbs = nbytes / (ms * 1e-3) / 1e9
+        hbm = measured_peaks()["hbm_gbs"]
         out[name] = {"ms": ms, "matvecs_per_s": 1e3 / ms, "fft_tflops": flops / (ms * 1e-3) / 1e12, "fields": d,
-                     "model_bytes": nbytes, "model_gbs": gbs, "model_hbm_frac": gbs / HBM_PEAK_GBS}
+                     "model_bytes": nbytes, "model_gbs": gbs, "model_hbm_frac": gbs / hbm}
+        if profile:
+            hb.hom_profile_kernel(ctx, profile)
+            for _ in range(n_rep):
+                apply()
+            torch.cuda.synchronize()
+            n, tot = hb.hom_kernel_timing(ctx)
+            hb.hom_profile_kernel(ctx, "")
+            if n:
+                out[name]["profiled_family"] = profile
+                out[name]["profiled_launches"] = n
+                out[name]["profiled_launch_ms"] = tot / n
     return out
+
+
+def run_peak_probe(args):
+    """The FMA peak probe alone, with the clocks sampled while it runs."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1404_3614_gb300 as hb
+    ctx = hb.hom_create(0)
+    s = torch.cuda.current_stream().cuda_stream
+    with ClockSampler(0) as clk:
+        r = {"fp32_tflops": [hb.binding.hom_peak_probe(ctx, hb.HOM_FP32, s) for _ in range(5)],
+             "fp64_tflops": [hb.binding.hom_peak_probe(ctx, hb.HOM_FP64, s) for _ in range(5)]}
+    hb.hom_destroy(ctx)
+    r["clocks"] = clk.summary()
+    print(json.dumps({"fma_peak_probe": r}), flush=True)
+    return 0
 
 
 def main():
@@ -770,11 +860,14 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
-    ap.add_argument("--ref-matvecs", type=int, default=20)
+    ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed"])
+    ap.add_argument("--fp64-steps", type=int, default=2, help="timed steps of the other precision")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
-    ap.add_argument("--workload", default="cube3d_N41", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-cube", action="store_true")
+    ap.add_argument("--image", action="store_true", help="add the 1199^2 pixel-image timings")
+    ap.add_argument("--headline-only", action="store_true", help="only the timed steps and e2e")
+    ap.add_argument("--workload", default="spheres3d_N113", choices=sorted(WORKLOADS))
     ap.add_argument("--matvec-only", action="store_true", help="operator applications only")
     ap.add_argument("--reps", type=int, default=20)
     ap.add_argument("--batched-only", action="store_true", help="the batched workload only")
@@ -789,6 +882,7 @@ def main():
     ap.add_argument("--learned-epochs", type=int, default=20)
     ap.add_argument("--learned3d", action="store_true", help="3D learned warm-start workload only")
     ap.add_argument("--gemm-only", action="store_true", help="the network's tensor-core GEMM alone")
+    ap.add_argument("--peak-probe", action="store_true", help="the FMA peak probe alone, with clocks")
     ap.add_argument("--paper-grids", action="store_true",
                     help="the paper's square-inclusion study on odd and even grids (Ga and GaNi)")
     ap.add_argument("--even-grids", action="store_true",
@@ -813,6 +907,8 @@ def main():
         return run_learned3d(args)
     if args.gemm_only:
         return run_gemm_only(args)
+    if args.peak_probe:
+        return run_peak_probe(args)
     if args.paper_grids:
         return run_paper_grids(args)
     if args.even_grids:

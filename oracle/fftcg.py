@@ -32,10 +32,23 @@ def default_workers() -> int:
     return len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
 
 
-class FFTOperator:
-    """Double-grid Galerkin operator of one side, FFT-based (same interface as O2's)."""
+def coefficient_slab(problem: Problem, side: str, M, i0: int) -> np.ndarray:
+    """A_hat(n) for the frequencies with first index i0 (FFT order) of Z_M: the scalar for
+    isotropic problems ([*M[1:]]), else [d, d, *M[1:]] (Lemma bounds_for_matrix-inclusion)."""
+    kf = [np.fft.fftfreq(m, 1.0 / m).round().astype(np.int64) for m in M]
+    rest = np.stack(np.meshgrid(*kf[1:], indexing="ij"), axis=-1)             # [*M[1:], d-1]
+    n = np.concatenate([np.full(rest.shape[:-1] + (1,), kf[0][i0]), rest], axis=-1)
+    c = coefficient_hat_at(problem, n, side)                                   # [*M[1:], d, d]
+    if problem.is_isotropic():
+        return c[..., 0, 0]
+    return np.moveaxis(c, (-2, -1), (0, 1))
 
-    def __init__(self, problem: Problem, side: str, workers: int = None):
+
+class FFTOperator:
+    """Double-grid Galerkin operator of one side, FFT-based (same interface as O2's). A caller
+    that already holds the double-grid coefficient passes it as A_grid (FFT order)."""
+
+    def __init__(self, problem: Problem, side: str, workers: int = None, A_grid: np.ndarray = None):
         self.problem = problem
         self.side = side
         self.d = d = problem.d
@@ -46,22 +59,18 @@ class FFTOperator:
         # FFT-order position of every k in Z_N inside a length-M axis
         self.pos = [np.mod(freqs(n), m) for n, m in zip(self.N, self.M)]
         self.iso = problem.is_isotropic()
-        # A_hat on Z_M (FFT order), built slab by slab along the first axis
-        kf = [np.fft.fftfreq(m, 1.0 / m).round().astype(np.int64) for m in self.M]
-        shape = (self.M if self.iso else (d, d) + self.M)
-        Ahat = np.zeros(shape, dtype=np.complex128)
-        rest = np.stack(np.meshgrid(*kf[1:], indexing="ij"), axis=-1)         # [*M[1:], d-1]
-        for i0, k0 in enumerate(kf[0]):
-            n = np.concatenate([np.full(rest.shape[:-1] + (1,), k0), rest], axis=-1)
-            c = coefficient_hat_at(problem, n, side)                           # [*M[1:], d, d]
-            if self.iso:
-                Ahat[i0] = c[..., 0, 0]
-            else:
-                Ahat[:, :, i0] = np.moveaxis(c, (-2, -1), (0, 1))
-        gaxes = tuple(range(d)) if self.iso else tuple(range(2, d + 2))
-        A = sfft.ifftn(Ahat, axes=gaxes, workers=self.workers) * float(np.prod(self.M))
-        self.coef_imag_max = float(np.max(np.abs(A.imag)))
-        self.A_grid = A.real.copy()             # [*M] (isotropic: A = a I) or [d, d, *M]
+        if A_grid is None:
+            Ahat = np.zeros(self.M if self.iso else (d, d) + self.M, dtype=np.complex128)
+            for i0 in range(self.M[0]):
+                if self.iso:
+                    Ahat[i0] = coefficient_slab(problem, side, self.M, i0)
+                else:
+                    Ahat[:, :, i0] = coefficient_slab(problem, side, self.M, i0)
+            gaxes = tuple(range(d)) if self.iso else tuple(range(2, d + 2))
+            A = sfft.ifftn(Ahat, axes=gaxes, workers=self.workers) * float(np.prod(self.M))
+            self.coef_imag_max = float(np.max(np.abs(A.imag)))
+            A_grid = A.real.copy()
+        self.A_grid = A_grid                    # [*M] (isotropic: A = a I) or [d, d, *M]
         self.G = projection(self.N, problem.Y, side)                           # [d, d, *N]
 
     def _pad(self, u_hat):

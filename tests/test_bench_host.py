@@ -13,8 +13,8 @@ from oracle import matfree
 
 
 def test_oracle_iteration_counts_pinned():
-    """bench.ORACLE_ITERS are the oracle CG's own iteration counts at 1e-4 (E = e1)."""
-    p = bench.workload()
+    """bench.ORACLE_ITERS are the oracle CG's own iteration counts at 1e-4 on the cube cell (E = e1)."""
+    p = bench.workload("cube3d_N41")
     for side in ("primal", "dual"):
         op = matfree.MatFreeOperator(p, side)
         _, it, res = matfree.cg_solve(op, [1.0, 0.0, 0.0], tol=bench.TOL)
@@ -22,11 +22,29 @@ def test_oracle_iteration_counts_pinned():
 
 
 def test_traffic_reported_only_for_the_captured_kernel(monkeypatch):
-    """The ncu DRAM figure is tied to the row-pass sources it was captured on."""
-    assert bench.xpass_traffic("spheres3d_N113", "fp64") is None
-    assert bench.xpass_traffic("cube3d_N41", "mixed") is None
-    monkeypatch.setitem(bench.XPASS_TRAFFIC, "sha256_16", "0" * 16)
-    assert bench.xpass_traffic("cube3d_N41", "fp64") is None
+    """The ncu DRAM figure is tied to the slab-pass sources it was captured on."""
+    monkeypatch.setitem(bench.SLAB_TRAFFIC, "sha256_16", "0" * 16)
+    monkeypatch.setitem(bench.SLAB_TRAFFIC, "bytes", 123)
+    assert bench.slab_traffic() is None
+    monkeypatch.setitem(bench.SLAB_TRAFFIC, "sha256_16", bench.source_hash(bench.SLAB_TRAFFIC["sources"]))
+    assert bench.slab_traffic() == 123
+
+
+def test_slab_byte_model():
+    """Passes 2-4 of the 5-pass model on the 16-ball cell (N = 113, M = 225, Nh = 57), 9 FP32
+    field components and 3 coefficient reads."""
+    p = bench.workload("spheres3d_N113")
+    want = 9 * 57 * (2 * 225 * 113 + 4 * 225 * 225) * 8 + 3 * 225 ** 3 * 4
+    assert bench.slab_model_bytes(p, 4, 3) == want
+    # with passes 1 and 5 (the z transforms) it is the whole-operator model
+    z = 9 * 57 * (2 * 113 * 113 + 2 * 225 * 113) * 8
+    assert bench.matvec_bytes(p, 4) == want + z
+
+
+def test_oracle_sample_extrapolates_a_bounded_sample():
+    p = ms.cube_inclusion_3d(N=9)
+    est, info = bench.oracle_sample(p, {"primal": 5, "dual": 3}, n_matvec=1)
+    assert est > 0 and info["extrapolated"] and info["kind"] == "oracle" and info["cores"] >= 1
 
 
 def test_flop_model():
