@@ -13,6 +13,7 @@
 #include <cooperative_groups.h>
 #include <math.h>
 
+#include "attr.cuh"
 #include "kernels.cuh"
 #include "spectrum.cuh"
 
@@ -799,17 +800,9 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 2 : 1) k_batch(BArgs a) {
 
 template <typename T, int NT>
 cudaError_t launch_batch_nt(const BArgs& a, int nblocks, size_t smem, int cluster, cudaStream_t s) {
-  static std::atomic<size_t> cache[16] = {};   // shared by every context: atomic
-  int dev = 0;
-  cudaGetDevice(&dev);
-  dev &= 15;
-  if (smem > 48 * 1024 && cache[dev].load(std::memory_order_relaxed) < smem) {
-    const cudaError_t e = cudaFuncSetAttribute(k_batch<T, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    size_t cur = cache[dev].load(std::memory_order_relaxed);
-    while (cur < smem && !cache[dev].compare_exchange_weak(cur, smem, std::memory_order_relaxed)) {
-    }
-  }
+  static std::atomic<int> cache[kAttrDevices] = {};
+  const cudaError_t e = smem_attr(k_batch<T, NT>, smem, cache);
+  if (e != cudaSuccess) return e;
   if (cluster <= 1) {
     k_batch<T, NT><<<nblocks, NT, smem, s>>>(a);
     return cudaGetLastError();
@@ -842,7 +835,8 @@ cudaError_t launch_batch(const BArgs& a, int nblocks, size_t smem, int threads, 
 }
 
 template <typename T, int NT> int batch_max_blocks_nt(size_t smem, int cluster) {
-  if (smem > 48 * 1024) cudaFuncSetAttribute(k_batch<T, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  static std::atomic<int> cache[kAttrDevices] = {};
+  if (smem_attr(k_batch<T, NT>, smem, cache) != cudaSuccess) return 0;
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) sms = 1;

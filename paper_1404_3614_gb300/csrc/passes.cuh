@@ -12,6 +12,7 @@
 #pragma once
 #include <atomic>
 
+#include "attr.cuh"
 #include "kernels.cuh"
 
 namespace homb {
@@ -503,25 +504,6 @@ __global__ void __launch_bounds__(kPassThreads) k_fft_batch(const cpx<T>* in, cp
 // ---------------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------------
-// Raise the dynamic shared-memory limit of one kernel instantiation once per device. The
-// cache is shared by every context (one per host thread), hence atomic; two threads that
-// race here both set the attribute, which is harmless.
-template <typename K>
-static cudaError_t smem_attr(K kernel, size_t bytes, std::atomic<size_t>* cache) {
-  if (bytes <= 48 * 1024) return cudaSuccess;
-  int dev = 0;
-  cudaGetDevice(&dev);
-  dev &= 15;
-  if (cache[dev].load(std::memory_order_relaxed) >= bytes) return cudaSuccess;
-  const cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-  if (e == cudaSuccess) {
-    size_t cur = cache[dev].load(std::memory_order_relaxed);
-    while (cur < bytes && !cache[dev].compare_exchange_weak(cur, bytes, std::memory_order_relaxed)) {
-    }
-  }
-  return e;
-}
-
 template <typename T> int pencil_xc(int M, int X, int C) {
   const size_t sz = sizeof(cpx<T>);
   const size_t fixed = M * sz + 512;
@@ -579,7 +561,7 @@ template <typename T> int xpass_yb(int M, int rpp, int planes) {
 template <typename T, int MT> cudaError_t launch_pencil_m(PencilArgs a, cudaStream_t s) {
   const size_t bufs = warp_fft_r<T, MT>() > 0 ? 1 : 2;
   const size_t smem = (size_t)a.plan.M * sizeof(cpx<T>) * (1 + bufs * (size_t)a.XC);
-  static std::atomic<size_t> cache[16] = {};
+  static std::atomic<int> cache[kAttrDevices] = {};
   cudaError_t e = smem_attr(k_pencil<T, MT>, smem, cache);
   if (e != cudaSuccess) return e;
   dim3 grid((a.X + a.XC - 1) / a.XC, a.nslab);
@@ -590,7 +572,7 @@ template <typename T, int MT> cudaError_t launch_pencil_m(PencilArgs a, cudaStre
 template <typename T, int MT> cudaError_t launch_final_m(FinalArgs a, cudaStream_t s) {
   const size_t bufs = warp_fft_r<T, MT>() > 0 ? 1 : 2;
   const size_t smem = (size_t)a.M * sizeof(cpx<T>) * (1 + bufs * (size_t)a.C * a.XC) + 32 * sizeof(double);
-  static std::atomic<size_t> cache[16] = {};
+  static std::atomic<int> cache[kAttrDevices] = {};
   cudaError_t e = smem_attr(k_final<T, MT>, smem, cache);
   if (e != cudaSuccess) return e;
   dim3 grid((a.X + a.XC - 1) / a.XC, a.nrhs);
@@ -603,7 +585,7 @@ template <typename T, int MT> cudaError_t launch_xpass_m(XArgs a, int grid_y, cu
   const int npair = (a.YB * rpp + 1) / 2;
   const size_t smem = (size_t)a.M * sizeof(cpx<T>) + 2 * (size_t)npair * (a.M + 1) * sizeof(cpx<T>) +
                       32 * sizeof(double);
-  static std::atomic<size_t> cache[16] = {};
+  static std::atomic<int> cache[kAttrDevices] = {};
   cudaError_t e = smem_attr(k_xpass<T, MT>, smem, cache);
   if (e != cudaSuccess) return e;
   dim3 grid((a.planes + a.YB - 1) / a.YB, grid_y);
@@ -615,7 +597,7 @@ template <typename T, int MT>
 cudaError_t launch_fft_batch_m(const void* in, void* out, int M, int howmany, int dir, const void* W,
                                const FftPlan& plan, int G, cudaStream_t s) {
   const size_t smem = (size_t)M * sizeof(cpx<T>) * (1 + 2 * (size_t)G);
-  static std::atomic<size_t> cache[16] = {};
+  static std::atomic<int> cache[kAttrDevices] = {};
   cudaError_t e = smem_attr(k_fft_batch<T, MT>, smem, cache);
   if (e != cudaSuccess) return e;
   const int blocks = (howmany + G - 1) / G;
