@@ -18,6 +18,7 @@
 #include <cmath>
 #include <vector>
 
+#include "attr.cuh"
 #include "net.cuh"
 
 namespace homb {
@@ -46,7 +47,7 @@ static_assert(TBM * 36 * 4 <= kTileABytes + kTileBBytes, "the result staging mus
 static_assert(TBN % 32 == 0, "the staged epilogue works in 32-column halves");
 constexpr long long kMbarSpinLimit = 1LL << 22;
 
-__device__ int g_gemm_timeout = 0;   // set when an mbarrier wait gave up
+__device__ int g_gemm_timeout[kGemmFlagSlots];   // per context: set when an mbarrier wait gave up
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -72,14 +73,25 @@ __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
   return *reinterpret_cast<uint32_t*>(&h);
 }
 
-__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t phase) {
-  for (long long it = 0; it < kMbarSpinLimit; ++it) {
+// Bounded wait for the phase `phase` of an mbarrier: at most `limit` polls. A limit below
+// the default uses the non-blocking test (a test aid: the wait then gives up at once);
+// otherwise the potentially blocking try_wait.
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t phase, long long limit = kMbarSpinLimit) {
+  const bool quick = limit < kMbarSpinLimit;
+  for (long long it = 0; it < limit; ++it) {
     uint32_t done;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(done)
-        : "r"(mbar), "r"(phase)
-        : "memory");
+    if (quick)
+      asm volatile(
+          "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+          : "=r"(done)
+          : "r"(mbar), "r"(phase)
+          : "memory");
+    else
+      asm volatile(
+          "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+          : "=r"(done)
+          : "r"(mbar), "r"(phase)
+          : "memory");
     if (done) return true;
   }
   return false;
@@ -179,13 +191,14 @@ __global__ void __launch_bounds__(128) k_gemm(GemmArgs g, int ksplit, float* par
       asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar_a)
                    : "memory");
     }
-    ok = __syncthreads_and(mbar_wait(mbar_a, phase) ? 1 : 0) != 0;   // one verdict for the CTA
+    ok = __syncthreads_and(mbar_wait(mbar_a, phase, g.spin) ? 1 : 0) != 0;   // one verdict for the CTA
     phase ^= 1u;
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   }
   if (!ok) {
-    // give the committed MMAs a second bounded chance before the accumulator is freed
-    if (tid == 0) atomicExch(&g_gemm_timeout, 1);
+    // drain: wait (with the default bound, whatever the first limit was) for the committed
+    // MMAs before the accumulator is freed
+    if (tid == 0) atomicExch(&g_gemm_timeout[g.slot], 1);
     mbar_wait(mbar_a, phase ^ 1u);
   } else if (ksplit == 1 && g.vecC) {
     // epilogue through shared memory (the operand tiles are free: the MMAs have completed):
@@ -288,11 +301,26 @@ __global__ void k_gemm_reduce(GemmArgs g, int ksplit, const float* partial) {
   }
 }
 
-int gemm_timeouts() {
-  int h = 0, z = 0;
-  if (cudaMemcpyFromSymbol(&h, g_gemm_timeout, sizeof(int)) != cudaSuccess) return -1;
-  if (h) cudaMemcpyToSymbol(g_gemm_timeout, &z, sizeof(int));
-  return h;
+static thread_local int g_ctx_slot = 0;
+static thread_local long long g_ctx_spin = 0;
+
+void gemm_set_context(int slot, long long spin) {
+  g_ctx_slot = ((slot % kGemmFlagSlots) + kGemmFlagSlots) % kGemmFlagSlots;
+  g_ctx_spin = spin;
+}
+
+cudaError_t gemm_timeout_clear(int slot, cudaStream_t s) {
+  int* base = nullptr;
+  cudaError_t e = cudaGetSymbolAddress((void**)&base, g_gemm_timeout);
+  if (e != cudaSuccess) return e;
+  return cudaMemsetAsync(base + (slot % kGemmFlagSlots), 0, sizeof(int), s);
+}
+
+cudaError_t gemm_timeout_read(int slot, int* host_flag, cudaStream_t s) {
+  int* base = nullptr;
+  cudaError_t e = cudaGetSymbolAddress((void**)&base, g_gemm_timeout);
+  if (e != cudaSuccess) return e;
+  return cudaMemcpyAsync(host_flag, base + (slot % kGemmFlagSlots), sizeof(int), cudaMemcpyDeviceToHost, s);
 }
 
 // split-K scratch, owned by the caller through net_workspace: set per call
@@ -302,6 +330,8 @@ static thread_local long long g_split_floats = 0;
 cudaError_t gemm_bf16(const GemmArgs& g0, cudaStream_t s) {
   if (g0.M <= 0 || g0.N <= 0 || g0.batch <= 0) return cudaSuccess;
   GemmArgs g = g0;
+  g.slot = g_ctx_slot;
+  g.spin = g_ctx_spin > 0 ? g_ctx_spin : kMbarSpinLimit;
   auto al16 = [](const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; };
   g.vecA = !g.ta && g.lda % 4 == 0 && g.sA % 4 == 0 && al16(g.A);
   g.vecC = g.ldc % 4 == 0 && g.sC % 4 == 0 && al16(g.C);
@@ -793,6 +823,47 @@ cudaError_t net_backward(const NetConfig& c, const float* prm, const float* base
   return cudaGetLastError();
 }
 
+// Training targets: each group of `group` consecutive channels of one sample scaled to unit
+// RMS over all its grid points and channels (the RMS clamped below at 1e-12). One CTA per
+// (sample, group): an FP64 block sum of squares, then the scaling.
+__global__ void k_normalise_groups(float* grid, long long pts, int ch, int group) {
+  const int ngroups = ch / group;
+  const int sample = blockIdx.x / ngroups;
+  const int gi = blockIdx.x - sample * ngroups;
+  float* base = grid + (long long)sample * pts * ch + (long long)gi * group;
+  const long long total = pts * group;
+  double acc = 0.0;
+  for (long long t = threadIdx.x; t < total; t += blockDim.x) {
+    const long long pt = t / group;
+    const float v = base[pt * ch + (t - pt * group)];
+    acc += (double)v * v;
+  }
+  __shared__ double red[32];
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double v = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (threadIdx.x == 0) red[0] = v;
+  }
+  __syncthreads();
+  const double rms = fmax(sqrt(red[0] / (double)total), 1e-12);
+  const float inv = (float)(1.0 / rms);
+  for (long long t = threadIdx.x; t < total; t += blockDim.x) {
+    const long long pt = t / group;
+    base[pt * ch + (t - pt * group)] *= inv;
+  }
+}
+
+cudaError_t normalise_groups(float* grid, int n, long long pts, int ch, int group, cudaStream_t s) {
+  if (n < 1 || group < 1 || ch % group) return cudaErrorInvalidValue;
+  const long long blocks = (long long)n * (ch / group);
+  if (blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
+  k_normalise_groups<<<(unsigned)blocks, 256, 0, s>>>(grid, pts, ch, group);
+  return cudaGetLastError();
+}
+
 cudaError_t adam_step(float* p, const float* g, float* m, float* v, long long n, float lr, float b1, float b2,
                       float eps, int step, cudaStream_t s) {
   const float c1 = 1.f - powf(b1, (float)step), c2 = 1.f - powf(b2, (float)step);
@@ -998,7 +1069,11 @@ constexpr size_t kMaxSmem = 227 * 1024;
 static cudaError_t launch_zdft(int N, long long nbc, const void* in, int fp64_in, void* out, int fp64_out, int sign,
                                cudaStream_t s) {
   const size_t smem = zdft_smem(N);
-  if (smem > 48 * 1024) cudaFuncSetAttribute(k_zdft, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  {
+    static std::atomic<int> cache[kAttrDevices] = {};
+    const cudaError_t ea = smem_attr(k_zdft, smem, cache);
+    if (ea != cudaSuccess) return ea;
+  }
   const int Nh = (N + 1) / 2;
   const long long blocks = nbc * N * ((Nh + kZB - 1) / kZB);
   if (blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
@@ -1009,7 +1084,11 @@ static cudaError_t launch_zdft(int N, long long nbc, const void* in, int fp64_in
 cudaError_t grid_to_half(int d, int N, int B, int ch, const float* grid, void* half, int fp64, cudaStream_t s) {
   const size_t smem = g2h_smem(N);
   if (smem > kMaxSmem || zdft_smem(N) > kMaxSmem) return cudaErrorInvalidValue;
-  if (smem > 48 * 1024) cudaFuncSetAttribute(k_grid_to_half, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  {
+    static std::atomic<int> cache[kAttrDevices] = {};
+    const cudaError_t ea = smem_attr(k_grid_to_half, smem, cache);
+    if (ea != cudaSuccess) return ea;
+  }
   const int Nz = d == 3 ? N : 1;
   const double scale = 1.0 / ((double)ipow(N, d == 3 ? 3 : 2));
   k_grid_to_half<<<B * Nz * ch, 256, smem, s>>>(N, ch, Nz, grid, half, fp64, scale);
@@ -1024,7 +1103,11 @@ cudaError_t half_to_grid(int d, int N, int B, int ch, const void* half, float* g
                          cudaStream_t s) {
   const size_t smem = h2g_smem(N);
   if (smem > kMaxSmem || zdft_smem(N) > kMaxSmem) return cudaErrorInvalidValue;
-  if (smem > 48 * 1024) cudaFuncSetAttribute(k_half_to_grid, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  {
+    static std::atomic<int> cache[kAttrDevices] = {};
+    const cudaError_t ea = smem_attr(k_half_to_grid, smem, cache);
+    if (ea != cudaSuccess) return ea;
+  }
   if (d == 3) {
     if (!tmp) return cudaErrorInvalidValue;
     NCK(launch_zdft(N, (long long)B * ch, half, fp64, tmp, 0, +1, s));

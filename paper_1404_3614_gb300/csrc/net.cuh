@@ -43,11 +43,20 @@ struct GemmArgs {
   int batch;
   float alpha, beta;
   int vecA, vecC;         // set by gemm_bf16: 16-byte vector loads of A rows / stores of C rows
+  long long spin;         // set by gemm_bf16: polls of the completion barrier before giving up
+  int slot;               // set by gemm_bf16: the calling context's timeout flag
 };
 cudaError_t gemm_bf16(const GemmArgs& g, cudaStream_t s);
-// 1 if a GEMM's bounded wait on its tensor-core completion barrier gave up since the last
-// call (the flag is then cleared), 0 otherwise, -1 if it could not be read. Synchronous.
-int gemm_timeouts();
+// Number of per-context GEMM timeout flags; context k uses flag k mod kGemmFlagSlots.
+constexpr int kGemmFlagSlots = 256;
+// The GEMMs launched by this host thread from now on report a timeout in flag `slot` and
+// poll their completion barrier at most `spin` times (0: the default limit, ~4 M polls;
+// a small value, a test aid, makes the wait give up at once without blocking).
+void gemm_set_context(int slot, long long spin);
+// Clear (async, on `s`) or read into *flag (async copy to pinned host memory) the timeout
+// flag of `slot`: 1 if a GEMM's bounded wait on its tensor-core completion barrier gave up.
+cudaError_t gemm_timeout_clear(int slot, cudaStream_t s);
+cudaError_t gemm_timeout_read(int slot, int* host_flag, cudaStream_t s);
 
 // forward (keeps activations in ws for a backward when train != 0); out [B*N^d, cout]
 cudaError_t net_forward(const NetConfig& c, const float* params, const float* bases, int B, const float* in,
@@ -55,6 +64,9 @@ cudaError_t net_forward(const NetConfig& c, const float* params, const float* ba
 // loss = mean (out - target)^2 ; gradient of the parameters into grad (overwritten)
 cudaError_t net_backward(const NetConfig& c, const float* params, const float* bases, int B, const float* in,
                          const float* target, float* grad, float* loss_dev, float* ws, cudaStream_t s);
+// scale each group of `group` consecutive channels of each of n samples ([n][pts][ch]) to
+// unit RMS over its points and channels
+cudaError_t normalise_groups(float* grid, int n, long long pts, int ch, int group, cudaStream_t s);
 cudaError_t adam_step(float* p, const float* g, float* m, float* v, long long n, float lr, float b1, float b2,
                       float eps, int step, cudaStream_t s);
 // DFT bases for the spectral layers, [bases_floats(c)] floats, computed on the host in FP64
