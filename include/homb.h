@@ -145,6 +145,10 @@ typedef struct {
                                   when the image is uploaded.                    */
 } hom_problem;
 
+/* A trained warm-start network held on the host (config and FP32 parameters); see
+ * hom_net_load. */
+typedef struct hom_net hom_net;
+
 typedef struct {
   int32_t precision;    /* hom_precision: HOM_FP64 or HOM_MIXED                  */
   int32_t max_iter;     /* per solve; <= 0 selects 10000 (hom_bounds_batched with
@@ -176,6 +180,17 @@ typedef struct {
                            GaNi matrix is applied on the double grid instead (the
                            same operator, fast FFT lengths). FP64 or mixed; no
                            starting / output fields.                             */
+  int32_t warm_start;   /* hom_bounds, Ga only: 0 starts CG from zero; 1 from the learned
+                           start of `net` (no counterpart in the paper's algorithm; any
+                           start projected onto E_N / J_N keeps the bounds guaranteed,
+                           Lemma bounds): the library samples the cell on its N grid
+                           (log10 of the phase value / 3), runs the network (tensor-core
+                           GEMMs) on that grid, takes the half spectra of its 2 d^2
+                           output channels (side, rhs, component) and starts each CG from
+                           their projection scaled by Rayleigh-Ritz. The cell's grid must
+                           be cubic (one N on every axis) with 2 modes <= N.        */
+  int32_t reserved;
+  const struct hom_net* net; /* warm_start = 1: a network from hom_net_load            */
 } hom_opts;
 
 typedef struct {
@@ -245,6 +260,13 @@ hom_status hom_bounds(hom_ctx* ctx, const hom_problem* prob, const hom_opts* opt
                       void* d_workspace, size_t workspace_bytes, void* stream,
                       double* upper, double* lower, double* mean, double* D,
                       hom_report* rep);
+/* The energy bounds of one macroscopic field E (Def. upper_lower_bounds: the bound
+ * matrices are symmetric bilinear forms): *upper = E . A_up E >= E . A_H E >= E . inv(B_up) E
+ * = *lower, with A_up and inv(B_up) those hom_bounds computes for the same problem and
+ * options (one full hom_bounds run; E has d entries, host memory). rep may be NULL. */
+hom_status hom_energy_bounds(hom_ctx* ctx, const hom_problem* prob, const hom_opts* opts,
+                             void* d_workspace, size_t workspace_bytes, void* stream,
+                             const double* E, double* upper, double* lower, hom_report* rep);
 /* hom_bounds with starting and / or converged fields (hom_field_io; NULL: hom_bounds). */
 hom_status hom_bounds_io(hom_ctx* ctx, const hom_problem* prob, const hom_opts* opts,
                          void* d_workspace, size_t workspace_bytes, void* stream,
@@ -292,7 +314,13 @@ hom_status hom_bounds_batched(hom_ctx* ctx, int32_t n, const hom_problem* probs,
  * inverse transforms, so one set of parameters runs on any grid with 2 modes <= N. The
  * network calls keep the DFT bases at the front of their workspace between calls with the
  * same workspace pointer and grid: do not write into a network workspace between network
- * calls. d = 0 is read as 2. */
+ * calls. d = 0 is read as 2.
+ * Every call that runs tensor-core GEMMs (hom_net_forward, hom_net_gradient,
+ * hom_net_train_step, hom_gemm_bf16) synchronises `stream` before it returns and returns
+ * HOM_ERR_TIMEOUT when a GEMM's bounded wait on its completion barrier gave up during the
+ * call (the GEMM then skips its result; the context stays usable). The flag is per context
+ * (256 slots: a context shares its flag with the one created 256 contexts earlier). Inside
+ * a stream capture the flag is not read. */
 typedef struct {
   int32_t N, cin, width, modes, layers, proj, cout, d;
 } hom_net_config;
@@ -302,6 +330,7 @@ hom_status hom_net_sizes(hom_ctx* ctx, const hom_net_config* cfg, int32_t batch,
                          size_t* workspace_bytes);
 hom_status hom_net_init(hom_ctx* ctx, const hom_net_config* cfg, uint64_t seed, float* d_params,
                         void* stream);
+/* the network's output for `batch` inputs; synchronises `stream` (see above). */
 hom_status hom_net_forward(hom_ctx* ctx, const hom_net_config* cfg, const float* d_params,
                            int32_t batch, const float* d_in, float* d_out, void* d_workspace,
                            size_t workspace_bytes, void* stream);
@@ -311,14 +340,37 @@ hom_status hom_net_gradient(hom_ctx* ctx, const hom_net_config* cfg, const float
                             int32_t batch, const float* d_in, const float* d_target, float* d_grad,
                             float* loss, void* d_workspace, size_t workspace_bytes, void* stream);
 /* one Adam step (beta1 0.9, beta2 0.999, eps 1e-8, bias-corrected with `step` >= 1) on the
- * gradient of one batch; loss written to *d_loss (device float, may be NULL); enqueue only. */
+ * gradient of one batch; loss written to *d_loss (device float, may be NULL); synchronises
+ * `stream` (see above). */
 hom_status hom_net_train_step(hom_ctx* ctx, const hom_net_config* cfg, float* d_params, float* d_m,
                               float* d_v, float* d_grad, int32_t step, float lr, int32_t batch,
                               const float* d_in, const float* d_target, float* d_loss,
                               void* d_workspace, size_t workspace_bytes, void* stream);
+/* Training targets on the N grid, [n][(N)][N][N][2 d^2] FP32 (channels (side, rhs,
+ * component)): each (side, rhs) group of d channels of each cell scaled in place to unit
+ * RMS over its grid points and components (the network learns the shape of each corrector;
+ * the solver's Rayleigh-Ritz scaling of the start finds its size). Enqueue only. */
+hom_status hom_net_normalise_targets(hom_ctx* ctx, int32_t d, int32_t N, int32_t n, float* d_grid,
+                                     void* stream);
+/* Network files (no counterpart in the paper): hom_net_save writes the config and the
+ * `n_params` FP32 parameters at d_params (device, as hom_net_sizes counts them) to `path`:
+ * 8-byte magic "HOMBNET" + version byte 1, int32 version 1, the hom_net_config as 8 int32,
+ * int64 parameter count, the parameters (little-endian FP32), a 64-bit FNV-1a checksum of
+ * the parameter bytes. Synchronises `stream`. hom_net_load reads such a file into a host
+ * object (config + parameters; no device memory), checking the magic, version, config,
+ * count and checksum (HOM_ERR_INVALID_ARG otherwise); hom_net_free releases it;
+ * hom_net_info returns its config and parameter count. The object is read-only and may be
+ * shared by contexts; hom_bounds uploads its parameters into the workspace (once per
+ * workspace and network). */
+hom_status hom_net_save(hom_ctx* ctx, const hom_net_config* cfg, const float* d_params, const char* path,
+                        void* stream);
+hom_status hom_net_load(hom_ctx* ctx, const char* path, hom_net** net);
+hom_status hom_net_free(hom_net* net);
+hom_status hom_net_info(const hom_net* net, hom_net_config* cfg, int64_t* n_params);
 /* input features of n inclusion cells (all 2D or all 3D, one cubic grid N) on their N
- * grid: log10 of the mean diagonal phase value at the grid points x_j = Y j / N,
- * [n][(N)][N][N][1]; synchronises `stream` (tables staged from host). */
+ * grid: log10 of the mean diagonal phase value at the grid points x_j = Y j / N, divided
+ * by 3 (phase values 1e-2 .. 1e3 map to [-2/3, 1]), [n][(N)][N][N][1]; synchronises
+ * `stream` (tables staged from host). */
 hom_status hom_net_features(hom_ctx* ctx, int32_t n, const hom_problem* probs, float* d_features,
                             void* d_workspace, size_t workspace_bytes, void* stream);
 /* real N-grid fields [B][(N)][N][N][ch] <-> half spectra [B][ch][(N)][N][(N+1)/2] (the
@@ -344,8 +396,8 @@ hom_status hom_resample_fields(hom_ctx* ctx, int32_t d, const int32_t N_from[3],
                                int64_t count, int32_t precision, const void* d_in, void* d_out,
                                void* stream);
 /* the tensor-core GEMM: C = alpha op(A) op(B) + beta C (row-major FP32 in memory, BF16
- * products on tcgen05.mma, FP32 accumulation in tensor memory); enqueue only. A wait that
- * gives up is reported by the next hom_net_gradient as HOM_ERR_TIMEOUT. */
+ * products on tcgen05.mma, FP32 accumulation in tensor memory); synchronises `stream` and
+ * returns HOM_ERR_TIMEOUT if a completion wait gave up (see above). */
 hom_status hom_gemm_bf16(hom_ctx* ctx, int32_t M, int32_t N, int32_t K, const float* d_A, int32_t lda,
                          int32_t transA, const float* d_B, int32_t ldb, int32_t transB, float* d_C,
                          int32_t ldc, float alpha, float beta, void* stream);
@@ -425,10 +477,13 @@ hom_status hom_matvec_noalloc(hom_ctx* ctx, const hom_problem* prob, int32_t sid
 hom_status hom_set_pass_chunks(hom_ctx* ctx, int32_t ypass_pencils, int32_t xpass_planes);
 /* The 3D operator with an isotropic coefficient and equal x and y transform lengths
  * M = R * R (R in 3, 5, 9, 15) fuses the inverse y transforms, the x row pass and the
- * forward y transforms into one pass over (rhs, component, z) slabs held in shared memory
- * (enable = 1, the default: warps per CTA chosen from the slab's shared memory; 4..24 in
- * steps of 4 asks for that many warps where they fit). enable = 0 runs them as three separate
- * passes; the results agree to rounding. Applies to later calls on this context. */
+ * forward y transforms into one pass over (rhs, component, z) slabs held in shared memory,
+ * by persistent CTAs that stage each slab's input with a bulk asynchronous copy issued
+ * while the previous slab is still being transformed (enable = 1, the default: warps per
+ * CTA chosen from the slab's shared memory; 4..20 in steps of 4 asks for that many warps
+ * where they fit). enable = 0 runs them as three separate passes; the results agree to
+ * rounding. A staged copy that does not complete within a bounded wait makes hom_bounds
+ * return HOM_ERR_TIMEOUT. Applies to later calls on this context. */
 hom_status hom_set_slab_pass(hom_ctx* ctx, int32_t enable);
 
 /* Threads per CTA of the persistent batched kernel: 256 (two CTAs per SM), 512 or 1024
@@ -452,6 +507,13 @@ hom_status hom_set_batch_cluster(hom_ctx* ctx, int32_t cluster, int32_t coop_min
  * last hom_profile_kernel call (synchronises the events). Inside the CG iteration
  * graphs of hom_bounds the events are event-record nodes of the graph; each replay
  * of a graph holding them is waited for and its pairs summed before the call goes on. */
+/* Test aid for the failure path of the tensor-core GEMM (no counterpart in the paper): the
+ * GEMMs of this context's later calls poll their completion barrier at most `polls` times
+ * with a non-blocking test before giving up (0 restores the default, about 4 M blocking
+ * polls). A small value makes the wait give up at once: the GEMM then records the timeout,
+ * drains its committed MMAs with the default bound, frees its tensor memory and returns, and
+ * the call returns HOM_ERR_TIMEOUT. */
+hom_status hom_set_gemm_spin_limit(hom_ctx* ctx, int64_t polls);
 /* Measured FMA rate of this GPU (no counterpart in the paper; a measurement aid):
  * precision HOM_FP32 or HOM_FP64; runs 8 independent FMA chains per thread on 4 CTAs
  * of 512 threads per SM on `stream`, best of 5 timed launches after one warm-up, and

@@ -43,15 +43,16 @@ class Bounds:
         return self.ws
 
     def __call__(self, problem, precision=HOM_FP64, tol=1e-8, max_iter=10000, check_every=8, sides=3,
-                 stream=None, graph=0, dual_start=0, discretization=0, x0=None, fields=None):
+                 stream=None, graph=0, dual_start=0, discretization=0, x0=None, fields=None, net=None):
         """hom_bounds on one problem; graph=-1 launches every CG kernel directly instead of
         replaying blocks of check_every iterations from captured CUDA graphs; dual_start=1
         starts the dual CG from the primal minimisers; discretization=1 runs GaNi (the
         paper's algorithm: N-grid CG, double-grid bounds; adds gani_A, gani_B). x0 / fields:
         optional complex128 device tensors [2, d, d, Nz, Ny, (N1+1)//2] of starting / converged
-        fields (a start is projected and scaled by Rayleigh-Ritz)."""
+        fields (a start is projected and scaled by Rayleigh-Ritz). net: a network handle
+        (binding.hom_net_load): the library computes the learned start itself."""
         opts = make_opts(precision, tol, max_iter, check_every, sides, graph, dual_start=dual_start,
-                         discretization=discretization)
+                         discretization=discretization, net=net)
         nbytes = hom_workspace_size(self.ctx, problem, opts)
         ws = self.workspace(nbytes)
         s = stream if stream is not None else self.torch.cuda.current_stream(self.device).cuda_stream

@@ -44,7 +44,8 @@ class hom_problem(C.Structure):
 class hom_opts(C.Structure):
     _fields_ = [("precision", C.c_int32), ("max_iter", C.c_int32), ("tol", C.c_double),
                 ("check_every", C.c_int32), ("sides", C.c_int32), ("graph", C.c_int32),
-                ("autotune", C.c_int32), ("dual_start", C.c_int32), ("discretization", C.c_int32)]
+                ("autotune", C.c_int32), ("dual_start", C.c_int32), ("discretization", C.c_int32),
+                ("warm_start", C.c_int32), ("reserved", C.c_int32), ("net", C.c_void_p)]
 
 
 class hom_report(C.Structure):
@@ -118,6 +119,13 @@ def _load():
         "hom_profile_kernel": (i32, [vp, C.c_char_p]),
         "hom_kernel_timing": (i32, [vp, P(i64), dp]),
         "hom_peak_probe": (i32, [vp, i32, vp, dp]),
+        "hom_set_gemm_spin_limit": (i32, [vp, i64]),
+        "hom_energy_bounds": (i32, [vp, P(hom_problem), P(hom_opts), vp, sz, vp, dp, dp, dp, P(hom_report)]),
+        "hom_net_save": (i32, [vp, P(hom_net_config), vp, C.c_char_p, vp]),
+        "hom_net_load": (i32, [vp, C.c_char_p, P(vp)]),
+        "hom_net_free": (i32, [vp]),
+        "hom_net_info": (i32, [vp, P(hom_net_config), P(i64)]),
+        "hom_net_normalise_targets": (i32, [vp, i32, i32, i32, vp, vp]),
     }
     for name, (res, args) in sigs.items():
         fn = getattr(lib, name)
@@ -227,10 +235,12 @@ def hom_problem_info(ctx, problem):
 
 
 def make_opts(precision=HOM_FP64, tol=1e-8, max_iter=10000, check_every=8, sides=3, graph=0, autotune=0,
-              dual_start=0, discretization=0):
+              dual_start=0, discretization=0, net=None):
+    """hom_opts; `net` (a handle from hom_net_load) selects the learned warm start."""
     o = hom_opts()
     o.precision, o.tol, o.max_iter, o.check_every, o.sides = precision, tol, max_iter, check_every, sides
     o.graph, o.autotune, o.dual_start, o.discretization = graph, autotune, dual_start, discretization
+    o.warm_start, o.net = (1, net) if net else (0, None)
     return o
 
 
@@ -396,6 +406,51 @@ def hom_kernel_timing(ctx):
     ms = C.c_double()
     check(ctx, lib.hom_kernel_timing(ctx, C.byref(n), C.byref(ms)))
     return n.value, ms.value
+
+
+def hom_energy_bounds(ctx, problem, opts, d_ws, ws_bytes, E, stream=0):
+    """(E.A_up E, E.inv(B_up) E) for the host vector E (length d)."""
+    p, keep = problem_struct(problem)
+    Ev = (C.c_double * 3)(*[float(e) for e in E])
+    up, lo = C.c_double(), C.c_double()
+    rep = hom_report()
+    check(ctx, lib.hom_energy_bounds(ctx, C.byref(p), C.byref(opts), C.c_void_p(d_ws), ws_bytes, C.c_void_p(stream),
+                                     Ev, C.byref(up), C.byref(lo), C.byref(rep)))
+    return up.value, lo.value
+
+
+def hom_net_save(ctx, cfg, d_params, path, stream=0):
+    return check(ctx, lib.hom_net_save(ctx, C.byref(cfg), C.c_void_p(d_params), os.fsencode(path), C.c_void_p(stream)))
+
+
+def hom_net_load(ctx, path):
+    """A host-side network handle (free it with hom_net_free)."""
+    h = C.c_void_p()
+    check(ctx, lib.hom_net_load(ctx, os.fsencode(path), C.byref(h)))
+    return h.value
+
+
+def hom_net_free(net):
+    return lib.hom_net_free(C.c_void_p(net))
+
+
+def hom_net_info(net):
+    cfg = hom_net_config()
+    n = C.c_int64()
+    if lib.hom_net_info(C.c_void_p(net), C.byref(cfg), C.byref(n)) != HOM_OK:
+        raise HombError(HOM_ERR_INVALID_ARG, "invalid network handle")
+    return cfg, n.value
+
+
+def hom_net_normalise_targets(ctx, d, N, n, d_grid, stream=0):
+    return check(ctx, lib.hom_net_normalise_targets(ctx, int(d), int(N), int(n), C.c_void_p(d_grid),
+                                                    C.c_void_p(stream)))
+
+
+def hom_set_gemm_spin_limit(ctx, polls):
+    """Test aid: the GEMMs of this context poll their completion barrier at most `polls`
+    times (0: default)."""
+    return check(ctx, lib.hom_set_gemm_spin_limit(ctx, int(polls)))
 
 
 def hom_peak_probe(ctx, precision, stream=0):

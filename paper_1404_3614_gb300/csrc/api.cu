@@ -12,6 +12,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <cstdio>
@@ -75,6 +76,20 @@ struct hom_ctx {
   int graph_launched[6] = {0, 0, 0, 0, 0, 0};   // launch configuration inside the batch graph
   int batch_cluster = 0;   // cluster size set by the caller (0: tuned / default)
   int batch_coopM = 0;     // with batch_cluster: cells at least this large are cooperative
+  // tensor-core GEMMs: this context's timeout flag and the test limit on barrier polls
+  int gemm_slot = 0;
+  long long gemm_spin = 0;
+  // learned warm start: the network parameters already uploaded to this workspace offset
+  unsigned long long net_params_id = 0;
+  const void* net_params_at = nullptr;
+  std::vector<unsigned char> net_params_tables;   // tables_key when they were uploaded
+};
+
+// A warm-start network loaded from a file: config and FP32 parameters on the host.
+struct hom_net {
+  hom_net_config cfg;
+  std::vector<float> params;
+  unsigned long long id;   // unique per loaded object: keys the parameter upload to a workspace
 };
 
 namespace {
@@ -774,6 +789,7 @@ struct Runner {
       sl.nrc = R * C; sl.C = C; sl.Mz = Mz; sl.M = Mx; sl.Ny = Ny; sl.Nh = Nh;
       sl.scale = 1.0 / (double)g.grid;
       sl.warps = ctx->slab_warps;
+      sl.fault = cg ? &cg->fault : nullptr;
       KL(launch_slab<T>(sl, st));
       fin = T1;
     } else {
@@ -1088,6 +1104,7 @@ struct Runner {
     }
     CK(d2h_copy(ctx, ctx->host_cg, cg, sizeof(CgScalars), st));
     CK(cudaStreamSynchronize(st));
+    if (ctx->host_cg->fault) return fail(ctx, HOM_ERR_TIMEOUT, "an operator pass gave up waiting for its staged input");
     hom_status result = HOM_OK;
     for (int r = 0; r < R; ++r) {
       const CgScalars& h = *ctx->host_cg;
@@ -1204,6 +1221,7 @@ hom_status Runner_solve_mixed(Runner& run, int side, const hom_opts& o, hom_repo
     CK(d2h_copy(ctx, ctx->host_cg, inner, sizeof(CgScalars), st));
     CK(cudaStreamSynchronize(st));
     for (int r = 0; r < R; ++r) inner_iters[r] += ctx->host_cg->iters[r];
+    if (ctx->host_cg->fault) return fail(ctx, HOM_ERR_TIMEOUT, "an operator pass gave up waiting for its staged input");
     // x64 += d, then the exact FP64 residual r64 = b - C x64
     KL(launch_promote_add(run.at<float2>(L.x), x64, n, st));
     CKS(run.matvec<double>(x64, r64, coef64, side + 1, outer, nullptr, nullptr, 0, b64));
@@ -1395,8 +1413,10 @@ const char* hom_version(void) { return "homb 0.1"; }
 
 hom_status hom_create(hom_ctx** out, int device) {
   if (!out) return HOM_ERR_INVALID_ARG;
+  static std::atomic<int> created{0};
   hom_ctx* ctx = new hom_ctx();
   ctx->device = device;
+  ctx->gemm_slot = created.fetch_add(1) % kGemmFlagSlots;
   cudaError_t e = cudaSetDevice(device);
   if (e == cudaSuccess) e = cudaMallocHost((void**)&ctx->host_cg, sizeof(CgScalars));
   if (e == cudaSuccess) e = cudaMallocHost((void**)&ctx->host_e, 64 * sizeof(double));
@@ -1487,6 +1507,87 @@ static hom_status check_pass_fit(hom_ctx* ctx, const Geometry& g, bool energy) {
   return HOM_OK;
 }
 
+// the learned warm start (defined with the network entry points below)
+static hom_status net_cfg(hom_ctx* ctx, const hom_net_config* c, NetConfig* out);
+static size_t net_ws_bytes(const NetConfig& c, int batch);
+static hom_status net_prepare(hom_ctx* ctx, const NetConfig& c, int batch, void* d_ws, size_t ws_bytes,
+                              cudaStream_t st, float** bases, float** rest);
+static hom_status gemm_begin(hom_ctx* ctx, cudaStream_t st);
+static hom_status gemm_end(hom_ctx* ctx, cudaStream_t st);
+static size_t features_stage_bytes(int n, size_t n_incl);
+static hom_status features_impl(hom_ctx* ctx, int32_t n, const hom_problem* probs, float* d_features, void* d_ws,
+                                size_t ws_bytes, cudaStream_t st);
+
+// Workspace region of the learned start, after the solver's own layout: the network
+// parameters, the features and the prediction on the N grid, the half-spectrum start
+// fields [side][rhs][comp][(z)][y][kx] (FP64), the feature staging and the network's own
+// workspace (DFT bases and activations for one cell).
+struct LearnedPlan {
+  NetConfig c{};
+  long long n_params = 0;
+  size_t params = 0, feat = 0, pred = 0, x0 = 0, stage = 0, stage_bytes = 0, netws = 0, net_bytes = 0, end = 0;
+};
+
+static hom_status plan_learned(hom_ctx* ctx, const Geometry& g, const hom_opts* o, size_t base, LearnedPlan& lp) {
+  if (o->warm_start != 0 && o->warm_start != 1) return fail(ctx, HOM_ERR_INVALID_ARG, "warm_start must be 0 or 1");
+  if (o->warm_start == 0) return HOM_OK;
+  if (!o->net) return fail(ctx, HOM_ERR_INVALID_ARG, "warm_start = 1 needs a network (hom_net_load)");
+  if (o->discretization != 0) return fail(ctx, HOM_ERR_INVALID_ARG, "the learned start is for the Galerkin discretization");
+  if (!g.bitmap.empty()) return fail(ctx, HOM_ERR_INVALID_ARG, "the learned start takes inclusion cells, not images");
+  for (int a = 1; a < g.d; ++a)
+    if (g.N[a] != g.N[0]) return fail(ctx, HOM_ERR_INVALID_ARG, "the learned start needs one N on every axis");
+  hom_net_config hc = o->net->cfg;
+  hc.N = g.N[0];
+  CKS(net_cfg(ctx, &hc, &lp.c));
+  if (lp.c.d != g.d || lp.c.cin != 1 || lp.c.cout != 2 * g.d * g.d)
+    return fail(ctx, HOM_ERR_INVALID_ARG, "the network's dimension / channels do not fit this cell");
+  lp.n_params = net_offsets(lp.c).total;
+  if ((long long)o->net->params.size() != lp.n_params)
+    return fail(ctx, HOM_ERR_INVALID_ARG, "network parameter count does not match its config");
+  const long long pts = (long long)g.N[0] * g.N[1] * g.N[2];
+  size_t off = align256(base);
+  auto take = [&](size_t bytes) {
+    const size_t at = off;
+    off = align256(off + bytes);
+    return at;
+  };
+  lp.params = take((size_t)lp.n_params * 4);
+  lp.feat = take((size_t)pts * 4);
+  lp.pred = take((size_t)pts * lp.c.cout * 4);
+  lp.x0 = take((size_t)2 * g.d * g.d * g.field * 16);
+  lp.stage_bytes = features_stage_bytes(1, g.incl.size());
+  lp.stage = take(lp.stage_bytes);
+  lp.net_bytes = net_ws_bytes(lp.c, 1);
+  lp.netws = take(lp.net_bytes);
+  lp.end = off;
+  return HOM_OK;
+}
+
+// The learned start of one cell into lp.x0: features, the network on the cell's grid,
+// half spectra of its outputs (FP64). The solver projects and scales them before CG.
+static hom_status learned_start(hom_ctx* ctx, const hom_problem* prob, const hom_opts* o, const LearnedPlan& lp,
+                                unsigned char* ws, cudaStream_t st) {
+  float* params = reinterpret_cast<float*>(ws + lp.params);
+  // still valid only if no call used the workspace otherwise since (every such call
+  // changes or clears the table key)
+  if (ctx->net_params_id != o->net->id || ctx->net_params_at != params || ctx->tables_key.empty() ||
+      ctx->tables_key != ctx->net_params_tables) {
+    CK(h2d_copy(ctx, params, o->net->params.data(), (size_t)lp.n_params * 4, st));
+    ctx->net_params_id = o->net->id;
+    ctx->net_params_at = params;
+  }
+  float* feat = reinterpret_cast<float*>(ws + lp.feat);
+  float* pred = reinterpret_cast<float*>(ws + lp.pred);
+  CKS(features_impl(ctx, 1, prob, feat, ws + lp.stage, lp.stage_bytes, st));
+  float *bases, *rest;
+  CKS(net_prepare(ctx, lp.c, 1, ws + lp.netws, lp.net_bytes, st, &bases, &rest));
+  CKS(gemm_begin(ctx, st));
+  KL(net_forward(lp.c, params, bases, 1, feat, pred, rest, 0, st));
+  CKS(gemm_end(ctx, st));
+  KL(grid_to_half(lp.c.d, lp.c.N, 1, lp.c.cout, pred, ws + lp.x0, 1, st));
+  return HOM_OK;
+}
+
 hom_status hom_workspace_size(hom_ctx* ctx, const hom_problem* prob, const hom_opts* opts,
                               size_t* bytes) {
   if (!ctx || !opts || !bytes) return fail(ctx, HOM_ERR_INVALID_ARG, "NULL argument");
@@ -1497,6 +1598,9 @@ hom_status hom_workspace_size(hom_ctx* ctx, const hom_problem* prob, const hom_o
   const size_t elem = opts->precision == HOM_MIXED ? 8 : 16;
   *bytes = make_layout(g, g.d, elem, 0).total;
   if (opts->discretization == 1) *bytes = align256(*bytes) + make_layout(gani_geometry(g), g.d, elem, 0).total;
+  LearnedPlan lp;
+  CKS(plan_learned(ctx, g, opts, *bytes, lp));
+  if (opts->warm_start == 1) *bytes = lp.end;
   return HOM_OK;
 }
 
@@ -1537,11 +1641,24 @@ static hom_status bounds_impl(hom_ctx* ctx, const hom_problem* prob, const hom_o
   Runner rn{ctx, gn, gani ? make_layout(gn, g.d, elem, 0) : Layout{}, static_cast<unsigned char*>(d_ws) + gani_off,
             static_cast<cudaStream_t>(stream), g.d};
   rn.gani = true;
-  const size_t need = gani ? gani_off + rn.L.total : run.L.total;
+  size_t need = gani ? gani_off + rn.L.total : run.L.total;
+  LearnedPlan lp;
+  CKS(plan_learned(ctx, g, opts, need, lp));
+  const bool learned = opts->warm_start == 1;
+  if (learned && io && io->d_x0) return fail(ctx, HOM_ERR_INVALID_ARG, "give either starting fields or warm_start");
+  if (learned) need = lp.end;
   if (!d_ws || ws_bytes < need) return fail(ctx, HOM_ERR_WORKSPACE, "workspace too small");
   if (reinterpret_cast<uintptr_t>(d_ws) % 256) return fail(ctx, HOM_ERR_INVALID_ARG, "workspace must be 256-byte aligned");
   if (rep) memset(rep, 0, sizeof *rep);
+  hom_field_io io_learned{nullptr, nullptr};
+  if (learned) {   // the network's start, before the solver's tables (its bases share the key)
+    CKS(learned_start(ctx, prob, opts, lp, static_cast<unsigned char*>(d_ws), run.st));
+    io_learned.d_x0 = static_cast<unsigned char*>(d_ws) + lp.x0;
+    io_learned.d_fields = io ? io->d_fields : nullptr;
+    io = &io_learned;
+  }
   CKS(run.upload_tables());
+  if (learned) ctx->net_params_tables = ctx->tables_key;
   if (gani) CKS(rn.upload_tables());
   const int sides = opts->sides ? opts->sides : 3;
   int matvecs = 0;
@@ -1654,6 +1771,26 @@ hom_status hom_bounds_io(hom_ctx* ctx, const hom_problem* prob, const hom_opts* 
                          size_t ws_bytes, void* stream, double* upper, double* lower, double* mean,
                          double* D, hom_report* rep, const hom_field_io* io) {
   return bounds_impl(ctx, prob, opts, d_ws, ws_bytes, stream, upper, lower, mean, D, rep, io);
+}
+
+hom_status hom_energy_bounds(hom_ctx* ctx, const hom_problem* prob, const hom_opts* opts, void* d_ws,
+                             size_t ws_bytes, void* stream, const double* E, double* upper, double* lower,
+                             hom_report* rep) {
+  if (!ctx || !prob || !opts || !E || !upper || !lower) return fail(ctx, HOM_ERR_INVALID_ARG, "NULL argument");
+  if (opts->sides != 0 && opts->sides != 3) return fail(ctx, HOM_ERR_INVALID_ARG, "energy bounds need both sides");
+  double Au[9], Lo[9];
+  const hom_status s = bounds_impl(ctx, prob, opts, d_ws, ws_bytes, stream, Au, Lo, nullptr, nullptr, rep, nullptr);
+  if (s < 0) return s;
+  const int d = prob->d;
+  double eu = 0.0, el = 0.0;
+  for (int a = 0; a < d; ++a)
+    for (int b = 0; b < d; ++b) {
+      eu += E[a] * Au[d * a + b] * E[b];
+      el += E[a] * Lo[d * a + b] * E[b];
+    }
+  *upper = eu;
+  *lower = el;
+  return s;
 }
 
 hom_status hom_batched_workspace_size(hom_ctx* ctx, int32_t n, const hom_problem* probs, const hom_opts* opts,
@@ -2138,8 +2275,8 @@ hom_status hom_set_batch_cluster(hom_ctx* ctx, int32_t cluster, int32_t coop_min
 
 hom_status hom_set_slab_pass(hom_ctx* ctx, int32_t enable) {
   if (!ctx) return HOM_ERR_INVALID_ARG;
-  if (enable < 0 || (enable > 1 && (enable < 4 || enable > 24 || enable % 4)))
-    return fail(ctx, HOM_ERR_INVALID_ARG, "slab pass: 0 (off), 1 (automatic) or 4..24 warps in steps of 4");
+  if (enable < 0 || (enable > 1 && (enable < 4 || enable > 20 || enable % 4)))
+    return fail(ctx, HOM_ERR_INVALID_ARG, "slab pass: 0 (off), 1 (automatic) or 4..20 warps in steps of 4");
   ctx->slab_on = enable != 0;
   ctx->slab_warps = enable > 1 ? enable : 0;
   return HOM_OK;
@@ -2252,6 +2389,32 @@ static hom_status net_prepare(hom_ctx* ctx, const NetConfig& c, int batch, void*
   return HOM_OK;
 }
 
+// Tensor-core GEMMs of one call: bind this context's timeout flag and clear it on the
+// stream; at the end, read it back (stream synchronised) unless the stream is being captured.
+static hom_status gemm_begin(hom_ctx* ctx, cudaStream_t st) {
+  gemm_set_context(ctx->gemm_slot, ctx->gemm_spin);
+  CK(gemm_timeout_clear(ctx->gemm_slot, st));
+  return HOM_OK;
+}
+
+static hom_status gemm_end(hom_ctx* ctx, cudaStream_t st) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  CK(cudaStreamIsCapturing(st, &cs));
+  if (cs != cudaStreamCaptureStatusNone) return HOM_OK;
+  int* flag = reinterpret_cast<int*>(ctx->host_e + 63);
+  *flag = 0;
+  CK(gemm_timeout_read(ctx->gemm_slot, flag, st));
+  CK(cudaStreamSynchronize(st));
+  if (*flag) return fail(ctx, HOM_ERR_TIMEOUT, "tensor-core GEMM completion wait timed out");
+  return HOM_OK;
+}
+
+hom_status hom_set_gemm_spin_limit(hom_ctx* ctx, int64_t polls) {
+  if (!ctx || polls < 0) return fail(ctx, HOM_ERR_INVALID_ARG, "polls must be >= 0");
+  ctx->gemm_spin = polls;
+  return HOM_OK;
+}
+
 hom_status hom_net_sizes(hom_ctx* ctx, const hom_net_config* cfg, int32_t batch, int64_t* n_params,
                          size_t* workspace_bytes) {
   NetConfig c;
@@ -2279,8 +2442,9 @@ hom_status hom_net_forward(hom_ctx* ctx, const hom_net_config* cfg, const float*
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   float *bases, *rest;
   CKS(net_prepare(ctx, c, batch, d_ws, ws_bytes, st, &bases, &rest));
+  CKS(gemm_begin(ctx, st));
   KL(net_forward(c, d_params, bases, batch, d_in, d_out, rest, 0, st));
-  return HOM_OK;
+  return gemm_end(ctx, st);
 }
 
 hom_status hom_net_gradient(hom_ctx* ctx, const hom_net_config* cfg, const float* d_params, int32_t batch,
@@ -2295,11 +2459,11 @@ hom_status hom_net_gradient(hom_ctx* ctx, const hom_net_config* cfg, const float
   CKS(net_prepare(ctx, c, batch, d_ws, ws_bytes, st, &bases, &rest));
   // the loss scalar lives in the last float of the workspace
   float* dloss = reinterpret_cast<float*>(static_cast<unsigned char*>(d_ws) + ws_bytes) - 1;
+  CKS(gemm_begin(ctx, st));
   KL(net_backward(c, d_params, bases, batch, d_in, d_target, d_grad, dloss, rest, st));
   float h = 0.f;
   CK(d2h_copy(ctx, &h, dloss, sizeof(float), st));
-  CK(cudaStreamSynchronize(st));
-  if (gemm_timeouts() != 0) return fail(ctx, HOM_ERR_TIMEOUT, "tensor-core GEMM completion wait timed out");
+  CKS(gemm_end(ctx, st));
   if (loss) *loss = h;
   return HOM_OK;
 }
@@ -2316,9 +2480,10 @@ hom_status hom_net_train_step(hom_ctx* ctx, const hom_net_config* cfg, float* d_
   float *bases, *rest;
   CKS(net_prepare(ctx, c, batch, d_ws, ws_bytes, st, &bases, &rest));
   float* dloss = d_loss ? d_loss : reinterpret_cast<float*>(static_cast<unsigned char*>(d_ws) + ws_bytes) - 1;
+  CKS(gemm_begin(ctx, st));
   KL(net_backward(c, d_params, bases, batch, d_in, d_target, d_grad, dloss, rest, st));
   KL(adam_step(d_params, d_grad, d_m, d_v, net_offsets(c).total, lr, 0.9f, 0.999f, 1e-8f, step, st));
-  return HOM_OK;
+  return gemm_end(ctx, st);
 }
 
 namespace {
@@ -2360,10 +2525,16 @@ __global__ void k_features(int n, int d, int N, const int* offs, const FeatIncl*
 }
 }  // namespace
 
-hom_status hom_net_features(hom_ctx* ctx, int32_t n, const hom_problem* probs, float* d_features, void* d_ws,
-                            size_t ws_bytes, void* stream) {
+static size_t features_stage_bytes(int n, size_t n_incl) {
+  return 256 + (size_t)(n + 1) * 4 + 256 + std::max<size_t>(n_incl, 1) * sizeof(FeatIncl) + 256 + (size_t)n * 4 +
+         256 + (size_t)n * 12 + 256;
+}
+
+// log10 of the mean diagonal phase value at the N-grid points of each cell, divided by 3
+// (phase values 1e-2 .. 1e3 map to [-2/3, 1]), [n][(N)][N][N]
+static hom_status features_impl(hom_ctx* ctx, int32_t n, const hom_problem* probs, float* d_features, void* d_ws,
+                                size_t ws_bytes, cudaStream_t st) {
   if (!ctx || n < 1 || !probs || !d_features) return fail(ctx, HOM_ERR_INVALID_ARG, "bad argument");
-  CKS(set_device(ctx));
   std::vector<int> offs(n + 1, 0);
   std::vector<FeatIncl> inc;
   std::vector<float> basev(n), Y(3 * n);
@@ -2379,7 +2550,7 @@ hom_status hom_net_features(hom_ctx* ctx, int32_t n, const hom_problem* probs, f
     N = g.N[0];
     double tr = 0.0;
     for (int a = 0; a < d; ++a) tr += g.A0[a][a];
-    basev[i] = (float)std::log10(tr / d);
+    basev[i] = (float)(std::log10(tr / d) / 3.0);
     for (int a = 0; a < 3; ++a) Y[3 * i + a] = a < d ? (float)g.Y[a] : 1.f;
     for (const hom_inclusion& I : g.incl) {
       FeatIncl f;
@@ -2390,17 +2561,15 @@ hom_status hom_net_features(hom_ctx* ctx, int32_t n, const hom_problem* probs, f
         f.h[a] = a < d ? (float)I.size[a] : 0.f;
       }
       for (int a = 0; a < d; ++a) itr += I.A[a * 3 + a];
-      f.value = (float)std::log10(itr / d);
+      f.value = (float)(std::log10(itr / d) / 3.0);
       inc.push_back(f);
     }
     offs[i + 1] = (int)inc.size();
   }
+  const size_t need = features_stage_bytes(n, inc.size());
   if (inc.empty()) inc.resize(1);
-  const size_t need = 256 + offs.size() * 4 + 256 + inc.size() * sizeof(FeatIncl) + 256 + basev.size() * 4 + 256 +
-                      Y.size() * 4 + 256;
   if (!d_ws || ws_bytes < need) return fail(ctx, HOM_ERR_WORKSPACE, "workspace too small");
   unsigned char* b = static_cast<unsigned char*>(d_ws);
-  cudaStream_t st = static_cast<cudaStream_t>(stream);
   size_t off = 0;
   auto put = [&](const void* src, size_t bytes) {
     void* dst = b + off;
@@ -2425,6 +2594,13 @@ hom_status hom_net_features(hom_ctx* ctx, int32_t n, const hom_problem* probs, f
   // the host vectors must outlive the pageable copies: they are staged before return
   CK(cudaStreamSynchronize(st));
   return HOM_OK;
+}
+
+hom_status hom_net_features(hom_ctx* ctx, int32_t n, const hom_problem* probs, float* d_features, void* d_ws,
+                            size_t ws_bytes, void* stream) {
+  if (!ctx) return HOM_ERR_INVALID_ARG;
+  CKS(set_device(ctx));
+  return features_impl(ctx, n, probs, d_features, d_ws, ws_bytes, static_cast<cudaStream_t>(stream));
 }
 
 static bool half_args_ok(int32_t d, int32_t N, int32_t batch, int32_t ch) {
@@ -2483,6 +2659,97 @@ hom_status hom_resample_fields(hom_ctx* ctx, int32_t d, const int32_t N_from[3],
   return HOM_OK;
 }
 
+hom_status hom_net_normalise_targets(hom_ctx* ctx, int32_t d, int32_t N, int32_t n, float* d_grid,
+                                     void* stream) {
+  if (!ctx || (d != 2 && d != 3) || N < 1 || n < 1 || !d_grid) return fail(ctx, HOM_ERR_INVALID_ARG, "bad argument");
+  CKS(set_device(ctx));
+  const long long pts = d == 3 ? (long long)N * N * N : (long long)N * N;
+  KL(normalise_groups(d_grid, n, pts, 2 * d * d, d, static_cast<cudaStream_t>(stream)));
+  return HOM_OK;
+}
+
+static uint64_t fnv1a(const void* p, size_t n) {
+  const unsigned char* b = static_cast<const unsigned char*>(p);
+  uint64_t h = 1469598103934665603ull;
+  for (size_t i = 0; i < n; ++i) {
+    h ^= b[i];
+    h *= 1099511628211ull;
+  }
+  return h;
+}
+
+static const char kNetMagic[8] = {'H', 'O', 'M', 'B', 'N', 'E', 'T', 1};
+
+hom_status hom_net_save(hom_ctx* ctx, const hom_net_config* cfg, const float* d_params, const char* path,
+                        void* stream) {
+  NetConfig c;
+  CKS(net_cfg(ctx, cfg, &c));
+  if (!d_params || !path) return fail(ctx, HOM_ERR_INVALID_ARG, "bad argument");
+  CKS(set_device(ctx));
+  const long long n = net_offsets(c).total;
+  std::vector<float> host((size_t)n);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  CK(d2h_copy(ctx, host.data(), d_params, (size_t)n * 4, st));
+  CK(cudaStreamSynchronize(st));
+  FILE* f = fopen(path, "wb");
+  if (!f) return fail(ctx, HOM_ERR_INVALID_ARG, std::string("cannot write ") + path);
+  const int32_t version = 1;
+  int32_t conf[8] = {cfg->N, cfg->cin, cfg->width, cfg->modes, cfg->layers, cfg->proj, cfg->cout, c.d};
+  const int64_t count = n;
+  const uint64_t sum = fnv1a(host.data(), host.size() * 4);
+  bool ok = fwrite(kNetMagic, 1, 8, f) == 8 && fwrite(&version, 4, 1, f) == 1 && fwrite(conf, 4, 8, f) == 8 &&
+            fwrite(&count, 8, 1, f) == 1 && fwrite(host.data(), 4, host.size(), f) == host.size() &&
+            fwrite(&sum, 8, 1, f) == 1;
+  ok = (fclose(f) == 0) && ok;
+  if (!ok) return fail(ctx, HOM_ERR_INVALID_ARG, std::string("write failed: ") + path);
+  return HOM_OK;
+}
+
+hom_status hom_net_load(hom_ctx* ctx, const char* path, hom_net** out) {
+  if (!ctx || !path || !out) return fail(ctx, HOM_ERR_INVALID_ARG, "bad argument");
+  *out = nullptr;
+  FILE* f = fopen(path, "rb");
+  if (!f) return fail(ctx, HOM_ERR_INVALID_ARG, std::string("cannot read ") + path);
+  char magic[8];
+  int32_t version = 0, conf[8];
+  int64_t count = 0;
+  uint64_t sum = 0;
+  bool ok = fread(magic, 1, 8, f) == 8 && memcmp(magic, kNetMagic, 8) == 0 && fread(&version, 4, 1, f) == 1 &&
+            version == 1 && fread(conf, 4, 8, f) == 8 && fread(&count, 8, 1, f) == 1;
+  hom_net_config hc{conf[0], conf[1], conf[2], conf[3], conf[4], conf[5], conf[6], conf[7]};
+  NetConfig c{};
+  if (ok) {
+    if (net_cfg(ctx, &hc, &c) != HOM_OK || count != net_offsets(c).total) ok = false;
+  }
+  std::vector<float> params;
+  if (ok) {
+    params.resize((size_t)count);
+    ok = fread(params.data(), 4, params.size(), f) == params.size() && fread(&sum, 8, 1, f) == 1 &&
+         sum == fnv1a(params.data(), params.size() * 4);
+  }
+  fclose(f);
+  if (!ok) return fail(ctx, HOM_ERR_INVALID_ARG, std::string("not a valid network file: ") + path);
+  static std::atomic<unsigned long long> ids{0};
+  hom_net* net = new hom_net();
+  net->cfg = hc;
+  net->params = std::move(params);
+  net->id = ++ids;
+  *out = net;
+  return HOM_OK;
+}
+
+hom_status hom_net_free(hom_net* net) {
+  delete net;
+  return HOM_OK;
+}
+
+hom_status hom_net_info(const hom_net* net, hom_net_config* cfg, int64_t* n_params) {
+  if (!net) return HOM_ERR_INVALID_ARG;
+  if (cfg) *cfg = net->cfg;
+  if (n_params) *n_params = (int64_t)net->params.size();
+  return HOM_OK;
+}
+
 hom_status hom_gemm_bf16(hom_ctx* ctx, int32_t M, int32_t N, int32_t K, const float* d_A, int32_t lda,
                          int32_t transA, const float* d_B, int32_t ldb, int32_t transB, float* d_C, int32_t ldc,
                          float alpha, float beta, void* stream) {
@@ -2491,8 +2758,10 @@ hom_status hom_gemm_bf16(hom_ctx* ctx, int32_t M, int32_t N, int32_t K, const fl
   GemmArgs g;
   g.A = d_A; g.B = d_B; g.C = d_C; g.M = M; g.N = N; g.K = K; g.lda = lda; g.ldb = ldb; g.ldc = ldc;
   g.ta = transA; g.tb = transB; g.sA = g.sB = g.sC = 0; g.batch = 1; g.alpha = alpha; g.beta = beta;
-  KL(gemm_bf16(g, static_cast<cudaStream_t>(stream)));
-  return HOM_OK;
+  const cudaStream_t st = static_cast<cudaStream_t>(stream);
+  CKS(gemm_begin(ctx, st));
+  KL(gemm_bf16(g, st));
+  return gemm_end(ctx, st);
 }
 
 }  // extern "C"

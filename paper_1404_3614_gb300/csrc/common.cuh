@@ -497,6 +497,7 @@ struct CgScalars {
   int iters[3];
   int status[3];     // 0 converged, 1 running / max_iter, 2 stopped by a guard, -2 breakdown
   int guard;         // 1: an FP32 inner solve; breakdown and divergence stop it (status 2)
+  int fault;         // 1: a bounded device wait of an operator pass gave up
 };
 
 }  // namespace homb

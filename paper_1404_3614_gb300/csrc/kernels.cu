@@ -171,6 +171,7 @@ __global__ void k_cg_init(CgScalars* cg, const double* partial, int ld, int nblk
       cg->rr_min[r] = s;
       cg->min_iter[r] = 0;
       cg->guard = guard;
+      cg->fault = 0;
       if (r >= nrhs) {
         cg->active[r] = 0;
         cg->status[r] = 0;

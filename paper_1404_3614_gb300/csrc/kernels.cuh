@@ -81,6 +81,7 @@ struct SlabArgs {
   int nrc, C, Mz, M, Ny, Nh;
   double scale;         // 1 / |M|
   int warps;            // warps per CTA, 0: automatic
+  int* fault;           // set to 1 when a staged input copy did not complete (may be NULL)
 };
 
 struct DevIncl {

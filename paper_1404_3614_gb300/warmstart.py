@@ -23,13 +23,8 @@ import microstructures as ms
 from . import binding as bd
 
 
-def torch_cat(parts):
-    import torch
-    return torch.cat(parts, dim=-1)
-
-
 class WarmStart:
-    def __init__(self, solver, N, width=32, modes=12, layers=4, proj=128, batch=32, seed=0, energy=False, d=2):
+    def __init__(self, solver, N, width=32, modes=12, layers=4, proj=128, batch=32, seed=0, d=2):
         import torch
         self.torch = torch
         self.solver = solver
@@ -51,11 +46,11 @@ class WarmStart:
         self.grad = torch.zeros_like(self.params)
         self.ws = torch.empty(self.ws_bytes, dtype=torch.uint8, device=dev)
         self.step = 0
-        self.energy = energy   # train on sqrt(energy weight) * field, divide it out at inference
 
     # -- data -------------------------------------------------------------------------
     def features(self, problems):
-        """log10 of the phase value on the grid, divided by 3 (phase values span 1e-2..1e3)."""
+        """log10 of the phase value on the grid, divided by 3 (phase values span 1e-2..1e3),
+        computed by the library."""
         torch = self.torch
         out = torch.empty((len(problems),) + self.grid + (1,), dtype=torch.float32, device=self.dev)
         ws = torch.empty(1 << 22, dtype=torch.uint8, device=self.dev)
@@ -63,30 +58,14 @@ class WarmStart:
         for s in range(0, len(problems), chunk):
             part = problems[s:s + chunk]
             bd.hom_net_features(self.ctx, part, out[s:s + len(part)].data_ptr(), ws.data_ptr(), ws.numel())
-        out.mul_(1.0 / 3.0)
         return out
 
-    @staticmethod
-    def energy_weights(x):
-        """sqrt of the pointwise energy weight of each output channel, [n, (N,) N, N, 2 d^2]: a(x) for
-        the primal correctors, 1/a(x) for the dual ones (features are log10(a)/3). The
-        energy norm of a field error is the a-weighted L2 norm (a(u, u) = (A u, u), no
-        derivative), so a plain MSE on sqrt(w) * field is the energy-norm error of the start."""
-        la = x[..., :1] * (3.0 * 2.302585092994046)   # ln a
-        half = (x.dim() - 2) ** 2
-        primal = (0.5 * la).exp().expand(*x.shape[:-1], half)
-        dual = (-0.5 * la).exp().expand(*x.shape[:-1], half)
-        return torch_cat((primal, dual))
-
-    @staticmethod
-    def normalise_targets(y):
-        """Scale each (side, rhs) pair of channels of each cell to unit RMS: the network
-        learns the shape of each corrector; the solver finds its scale (Rayleigh-Ritz on
-        the start direction), so the magnitude need not be predicted."""
-        n, d = y.shape[0], y.dim() - 2
-        blocks = y.view(n, -1, 2 * d, d)
-        rms = blocks.pow(2).mean(dim=(1, 3), keepdim=True).sqrt().clamp_min(1e-12)
-        return (blocks / rms).view_as(y)
+    def normalise_targets(self, y):
+        """Scale each (side, rhs) group of channels of each cell to unit RMS, in place, in the
+        library: the network learns the shape of each corrector; the solver finds its scale
+        (Rayleigh-Ritz on the start direction), so the magnitude need not be predicted."""
+        bd.hom_net_normalise_targets(self.ctx, self.d, self.N, y.shape[0], y.data_ptr())
+        return y
 
     def field_shape(self, n):
         d = self.d
@@ -137,7 +116,7 @@ class WarmStart:
         total = epochs * steps_per_epoch
         for ep in range(epochs):
             perm = torch.randperm(n, generator=g, device=self.dev)
-            acc = torch.zeros(1, device=self.dev)
+            acc = 0.0
             for s in range(steps_per_epoch):
                 idx = perm[s * B:(s + 1) * B]
                 torch.index_select(x, 0, idx, out=xb)
@@ -149,8 +128,8 @@ class WarmStart:
                                       self.v.data_ptr(), self.grad.data_ptr(), self.step, float(lr_t), B,
                                       xb.data_ptr(), yb.data_ptr(), loss.data_ptr(), self.ws.data_ptr(),
                                       self.ws.numel())
-                acc += loss
-            history.append(float(acc.item()) / max(steps_per_epoch, 1))
+                acc += float(loss.item())            # the step has synchronised its stream
+            history.append(acc / max(steps_per_epoch, 1))
         return history
 
     def predict(self, x):
@@ -198,7 +177,7 @@ class WarmStart:
 
 def train_and_evaluate(N=63, n_train=20000, n_test=1024, epochs=20, batch=32, width=32, modes=12, layers=4,
                        proj=128, seed_train=1000, seed_test=100000, tol=1e-4, precision="mixed", lr=2e-3,
-                       gen_tol=1e-6, solver=None, tight_tol=1e-8, energy=False):
+                       gen_tol=1e-6, solver=None, tight_tol=1e-8):
     """The learned warm-start workload: random-rectangle cells on an N grid (the batched
     workload's distribution at one N). Returns a dict of measurements."""
     import torch
@@ -207,7 +186,7 @@ def train_and_evaluate(N=63, n_train=20000, n_test=1024, epochs=20, batch=32, wi
     if own:
         solver = hb.Bounds(0)
     prec = bd.HOM_MIXED if precision == "mixed" else bd.HOM_FP64
-    ws = WarmStart(solver, N, width, modes, layers, proj, batch, seed=seed_train, energy=energy)
+    ws = WarmStart(solver, N, width, modes, layers, proj, batch, seed=seed_train)
     t0 = time.perf_counter()
     train_probs = [ms.random_rectangles_2d(seed_train + i, N=N) for i in range(n_train)]
     test_probs = [ms.random_rectangles_2d(seed_test + i, N=N) for i in range(n_test)]
@@ -216,10 +195,7 @@ def train_and_evaluate(N=63, n_train=20000, n_test=1024, epochs=20, batch=32, wi
     t0 = time.perf_counter()
     _, fields = ws.solve(train_probs, prec, gen_tol, want_fields=True)
     x = ws.features(train_probs)
-    y = ws.fields_to_grid(fields)
-    if energy:
-        y = y * WarmStart.energy_weights(x)
-    y = WarmStart.normalise_targets(y)
+    y = ws.normalise_targets(ws.fields_to_grid(fields))
     torch.cuda.synchronize()
     t_data = time.perf_counter() - t0
     del fields
@@ -236,8 +212,6 @@ def train_and_evaluate(N=63, n_train=20000, n_test=1024, epochs=20, batch=32, wi
     t_zero = time.perf_counter() - t0
     t0 = time.perf_counter()
     pred = ws.predict(xt)
-    if energy:
-        pred = pred / WarmStart.energy_weights(xt)
     x0 = ws.grid_to_fields(pred, prec)
     warm, _ = ws.solve(test_probs, prec, tol, x0=x0)
     torch.cuda.synchronize()
@@ -265,7 +239,7 @@ def train_and_evaluate(N=63, n_train=20000, n_test=1024, epochs=20, batch=32, wi
     if own:
         solver.close()
     return {
-        "N": N, "n_train": n_train, "n_test": n_test, "epochs": epochs, "batch": batch, "energy_loss": energy,
+        "N": N, "n_train": n_train, "n_test": n_test, "epochs": epochs, "batch": batch,
         "network": {"width": width, "modes": modes, "layers": layers, "proj": proj, "params": ws.n_params},
         "loss_first_epoch": hist[0] if hist else None, "loss_last_epoch": hist[-1] if hist else None,
         "iters_zero_mean": float(it_zero.mean()), "iters_warm_mean": float(it_warm.mean()),
@@ -320,7 +294,7 @@ def train_and_evaluate_3d(N_train=41, N_eval=113, n_train=1000, n_test=32, eval_
         ws.fields_to_grid(fb[:m], out=y[s:s + m])
     del fb
     x = ws.features(train_probs)
-    y = WarmStart.normalise_targets(y)
+    y = ws.normalise_targets(y)
     torch.cuda.synchronize()
     t_data = time.perf_counter() - t0
     t0 = time.perf_counter()

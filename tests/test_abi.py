@@ -49,7 +49,7 @@ def test_struct_layouts_match_header(libpath):
     # hom_inclusion: 2 int32 + 3 + 3 + 9 doubles
     assert ctypes.sizeof(bd.hom_inclusion) == 8 + 15 * 8
     assert ctypes.sizeof(bd.hom_problem) == 4 + 12 + 24 + 72 + 8 + 8 + 8 + 12 + 4 + 4 + 4   # + smooth, padding
-    assert ctypes.sizeof(bd.hom_opts) == 4 + 4 + 8 + 4 + 4 + 4 + 4 + 4 + 4
+    assert ctypes.sizeof(bd.hom_opts) == 4 + 4 + 8 + 4 + 4 + 4 + 4 + 4 + 4 + 4 + 4 + 8   # + warm_start, net
 
 
 def test_struct_layouts_match_a_c_compiler(libpath, tmp_path):

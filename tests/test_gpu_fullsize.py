@@ -1,0 +1,104 @@
+"""Bounds of the full-size workloads against the oracle, through the C ABI.
+
+The stored values (tests/golden/fullsize_bounds.json) were written by
+tests/golden/make_fullsize_goldens.py, which calls only the oracle: O2 (matrix DFTs + CG)
+for the 3D cube cell at N = 41^3 and four cells of the 256-cell random-rectangle batch
+(N = 113 and 203, solved inside one persistent batched launch here), O3 (the same steps
+with library FFTs, pinned to O2) for the 3D cell with 16 balls at N = 113^3. Each oracle
+solve ran to a residual tolerance whose energy error bound (tol^2 / lambda_min) lies far
+below the 1e-10 parity bar. FP64 must match within 1e-10 (max entry error over the
+Frobenius norm), mixed precision within 1e-6 with every ordering kept.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import microstructures as ms
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+GOLD = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "fullsize_bounds.json")))
+
+
+@pytest.fixture(scope="module")
+def hb():
+    import paper_1404_3614_gb300 as hb
+    return hb
+
+
+@pytest.fixture(scope="module")
+def solver(hb):
+    s = hb.Bounds(0)
+    yield s
+    s.close()
+
+
+def rel(a, b):
+    return np.abs(np.asarray(a) - np.asarray(b)).max() / np.linalg.norm(b)
+
+
+def loewner_ge(A, B, tol=1e-12):
+    S = 0.5 * ((A - B) + (A - B).T)
+    return np.linalg.eigvalsh(S).min() >= -tol * max(1.0, np.abs(A).max())
+
+
+def check(out, gold, bar):
+    up, lo = np.asarray(gold["upper"]), np.asarray(gold["lower"])
+    for key, ref in (("upper", up), ("lower", lo)):
+        assert rel(out[key], ref) <= bar, (key, rel(out[key], ref))
+    # guaranteed bounds: every computed upper dominates the exact lower and vice versa
+    assert loewner_ge(out["upper"], out["lower"])
+    assert loewner_ge(out["upper"], lo, 1e-9) and loewner_ge(up, out["lower"], 1e-9)
+
+
+@pytest.mark.parametrize("name,maker,tol_fp64", [
+    ("cube3d_N41", lambda: ms.cube_inclusion_3d(), 1e-10),
+    ("spheres3d_N113", lambda: ms.random_spheres_3d(0, N=113), 1e-8),
+])
+def test_fullsize_3d_bounds_match_oracle(hb, solver, name, maker, tol_fp64):
+    gold = GOLD[name]
+    p = maker()
+    assert [int(n) for n in p.N] == gold["N"]
+    out = solver(p, precision=hb.HOM_FP64, tol=tol_fp64)
+    assert out["status"] == 0
+    check(out, gold, 1e-10)
+    mixed = solver(p, precision=hb.HOM_MIXED, tol=1e-7)
+    check(mixed, gold, 1e-6)
+
+
+@pytest.mark.parametrize("cluster", [0, 4])
+def test_benchmark_batch_large_cells_match_oracle(hb, solver, cluster):
+    """Cells of the 256-cell batch with N = 113 (seeds 2, 6) and N = 203 (seeds 5, 10),
+    inside one launch with 20 other cells of the batch; cluster = 4 splits every cell with
+    2N - 1 >= 225 over a 4-CTA thread-block cluster (the tuned configuration of the bench)."""
+    probs = [ms.random_rectangles_2d(s) for s in range(24)]
+    try:
+        if cluster:
+            hb.binding.hom_set_batch_cluster(solver.ctx, cluster, 225)
+        out = solver.batched(probs, precision=hb.HOM_FP64, tol=1e-10)
+        mixed = solver.batched(probs, precision=hb.HOM_MIXED, tol=1e-5)
+    finally:
+        hb.binding.hom_set_batch_cluster(solver.ctx, 0, 0)
+    for s in (2, 6, 5, 10):
+        gold = GOLD[f"rects2d_seed{s}"]
+        assert int(probs[s].N[0]) == gold["N"][0]
+        assert (out["status"][s] == 0).all()
+        check({"upper": out["upper"][s], "lower": out["lower"][s]}, gold, 1e-10)
+        # FP32 inner CG without refinement (the batched launch): converged at tol 1e-5
+        assert mixed["status"][s] == 0, (s, mixed["status"][s])
+        check({"upper": mixed["upper"][s], "lower": mixed["lower"][s]}, gold, 1e-6)
+
+
+def test_batched_fp32_floor_is_flagged(hb, solver):
+    """Below its FP32 floor the batched mixed CG of a contrast-144 cell (seed 2, N = 113)
+    stops by its guard: the cell is flagged (status 1, not converged) and its bounds stay
+    guaranteed (they enclose the oracle's)."""
+    probs = [ms.random_rectangles_2d(s) for s in (2, 6)]
+    out = solver.batched(probs, precision=hb.HOM_MIXED, tol=1e-7)
+    gold = GOLD["rects2d_seed2"]
+    up, lo = np.asarray(gold["upper"]), np.asarray(gold["lower"])
+    assert out["status"][0] == 1
+    assert loewner_ge(out["upper"][0], up, 1e-12) and loewner_ge(lo, out["lower"][0], 1e-12)

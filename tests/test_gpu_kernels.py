@@ -226,7 +226,10 @@ def test_slab_pass_matches_separate_passes(hb, ctx, N, prec):
         for side in (0, 1):
             coef = torch.empty((info["ncomp"],) + tuple(info["M"][:d][::-1]), dtype=rdt, device="cuda")
             hb.hom_coefficient(ctx, p, side, precision, coef.data_ptr(), ws.data_ptr(), nws)
-            for slab in (1, 0):
+            # automatic, two fixed warp counts of the persistent kernel (different CTA counts and
+            # slabs per CTA), and the separate passes
+            variants = (1, 8, 20, 0) if N >= 41 and prec == "fp32" else (1, 0)
+            for slab in variants:
                 hb.hom_set_slab_pass(ctx, slab)
                 y = torch.zeros_like(x)
                 hb.hom_matvec(ctx, p, side, precision, 1, d, coef.data_ptr(), x.data_ptr(), y.data_ptr(),
@@ -234,7 +237,9 @@ def test_slab_pass_matches_separate_passes(hb, ctx, N, prec):
                 torch.cuda.synchronize()
                 out[side, slab] = y.cpu().numpy()
             tol = 1e-13 if prec == "fp64" else 2e-6
-            assert relerr(out[side, 1], out[side, 0]) < tol, (N, prec, side, relerr(out[side, 1], out[side, 0]))
+            for slab in variants[:-1]:
+                assert relerr(out[side, slab], out[side, 0]) < tol, (N, prec, side, slab,
+                                                                     relerr(out[side, slab], out[side, 0]))
     finally:
         hb.hom_set_slab_pass(ctx, 1)
 

@@ -102,7 +102,7 @@ def test_features_match_geometry(hb, ctx):
             dx -= np.round(dx)
             dy -= np.round(dy)
             inside |= (np.abs(dx) < inc.size[0] / 2) & (np.abs(dy) < inc.size[1] / 2)
-        ref = np.where(inside, np.log10(a), 0.0)
+        ref = np.where(inside, np.log10(a), 0.0) / 3.0          # log10(a) / 3
         # points exactly on an interface may fall either way in float32
         assert np.mean(np.abs(f[i] - ref) > 1e-5) < 0.02
 
@@ -117,13 +117,13 @@ def test_features_3d_match_geometry(hb, ctx):
     j = np.arange(N) / N
     Z, Y, X = np.meshgrid(j, j, j, indexing="ij")      # [z, y, x]
     for i, p in enumerate(probs):
-        ref = np.full(X.shape, np.log10(np.trace(p.A0) / 3))
+        ref = np.full(X.shape, np.log10(np.trace(p.A0) / 3) / 3.0)
         for inc in p.inclusions:
             r2 = np.zeros_like(X)
             for a, C_ in enumerate((X, Y, Z)):
                 dd = C_ - inc.center[a]
                 r2 += (dd - np.round(dd)) ** 2
-            ref = np.where(r2 < inc.size[0] ** 2, np.log10(np.trace(inc.A) / 3), ref)
+            ref = np.where(r2 < inc.size[0] ** 2, np.log10(np.trace(inc.A) / 3) / 3.0, ref)
         # points exactly on an interface may fall either way in float32
         assert np.mean(np.abs(f[i] - ref) > 1e-5) < 0.01
 
@@ -302,3 +302,129 @@ def test_resample_fields(hb, ctx, d, nf, nt, prec):
     assert np.array_equal(out.cpu().numpy().reshape(ref.shape), ref)
     with pytest.raises(hb.HombError):
         hb.binding.hom_resample_fields(ctx, d, nf, nt, count, p, dx.data_ptr(), dx.data_ptr())
+
+
+# ----------------------------------------------------------------------------------
+# the learned start inside the library: network files, hom_opts.warm_start, energy bounds
+# ----------------------------------------------------------------------------------
+def _python_start(hb, ctx, cfg, params, p):
+    """The learned start chained call by call: features, forward on the cell's grid, half
+    spectra (FP64) -- what hom_bounds does itself with warm_start = 1."""
+    d = p.d
+    N = int(p.N[0])
+    feat = torch.empty((1,) + (N,) * d + (1,), dtype=torch.float32, device="cuda")
+    ws = torch.empty(1 << 20, dtype=torch.uint8, device="cuda")
+    hb.binding.hom_net_features(ctx, [p], feat.data_ptr(), ws.data_ptr(), ws.numel())
+    c = hb.binding.net_config(N, 1, cfg.width, cfg.modes, cfg.layers, cfg.proj, cfg.cout, d)
+    _, nws = hb.binding.hom_net_sizes(ctx, c, 1)
+    nw = torch.empty(nws, dtype=torch.uint8, device="cuda")
+    pred = torch.empty((1,) + (N,) * d + (cfg.cout,), dtype=torch.float32, device="cuda")
+    hb.binding.hom_net_forward(ctx, c, params.data_ptr(), 1, feat.data_ptr(), pred.data_ptr(), nw.data_ptr(), nws)
+    half = torch.empty((2, d, d) + (N,) * (d - 1) + ((N + 1) // 2,), dtype=torch.complex128, device="cuda")
+    hb.binding.hom_grid_to_half(ctx, d, N, 1, cfg.cout, pred.data_ptr(), half.data_ptr(), hb.HOM_FP64)
+    return half
+
+
+@pytest.mark.parametrize("d,N,train_N", [(2, 23, 15), (3, 13, 9)])
+def test_learned_start_inside_hom_bounds(hb, tmp_path, d, N, train_N):
+    """A network saved to a file and loaded back gives, through hom_opts.warm_start, the same
+    bounds and iterations (1e-12) as the same start chained call by call; its grid need not be
+    the one in the file's config."""
+    solver = hb.Bounds(0)
+    ctx = solver.ctx
+    net = None
+    try:
+        cfg = hb.binding.net_config(train_N, 1, 8, 3, 2, 24, 2 * d * d, d)
+        npar, _ = hb.binding.hom_net_sizes(ctx, cfg, 1)
+        params = torch.empty(npar, dtype=torch.float32, device="cuda")
+        hb.binding.hom_net_init(ctx, cfg, 11, params.data_ptr())
+        path = str(tmp_path / "net.bin")
+        hb.binding.hom_net_save(ctx, cfg, params.data_ptr(), path)
+        net = hb.binding.hom_net_load(ctx, path)
+        got_cfg, got_n = hb.binding.hom_net_info(net)
+        assert got_n == npar and (got_cfg.N, got_cfg.width, got_cfg.cout, got_cfg.d) == (train_N, 8, 2 * d * d, d)
+        p = ms.random_rectangles_2d(21, N=N) if d == 2 else ms.random_spheres_3d(4, N=N, n_balls=5, phi=0.25,
+                                                                                contrast=100.0)
+        for prec in (hb.HOM_FP64, hb.HOM_MIXED):
+            x0 = _python_start(hb, ctx, cfg, params, p)
+            ref = solver(p, precision=prec, tol=1e-8, x0=x0)
+            for rep in range(2):        # the second call finds the parameters resident
+                out = solver(p, precision=prec, tol=1e-8, net=net)
+                for key in ("upper", "lower"):
+                    assert np.abs(out[key] - ref[key]).max() <= 1e-12 * np.abs(ref[key]).max(), (prec, key)
+                assert out["report"]["iters"] == ref["report"]["iters"]
+        # a different problem in between on the same workspace: the parameters are uploaded again
+        solver(ms.cube_inclusion_3d(N=11) if d == 2 else ms.square_inclusion_2d(N=31), precision=hb.HOM_FP64)
+        out = solver(p, precision=hb.HOM_FP64, tol=1e-8, net=net)
+        ref = solver(p, precision=hb.HOM_FP64, tol=1e-8, x0=_python_start(hb, ctx, cfg, params, p))
+        assert np.abs(out["upper"] - ref["upper"]).max() <= 1e-12 * np.abs(ref["upper"]).max()
+    finally:
+        if net:
+            hb.binding.hom_net_free(net)
+        solver.close()
+
+
+def test_network_file_is_checked(hb, tmp_path):
+    ctx = hb.hom_create(0)
+    try:
+        cfg = hb.binding.net_config(9, 1, 4, 2, 1, 8, 8, 2)
+        npar, _ = hb.binding.hom_net_sizes(ctx, cfg, 1)
+        params = torch.empty(npar, dtype=torch.float32, device="cuda")
+        hb.binding.hom_net_init(ctx, cfg, 2, params.data_ptr())
+        path = tmp_path / "net.bin"
+        hb.binding.hom_net_save(ctx, cfg, params.data_ptr(), str(path))
+        raw = bytearray(path.read_bytes())
+        raw[60] ^= 0x40                            # one parameter bit: the checksum fails
+        bad = tmp_path / "bad.bin"
+        bad.write_bytes(bytes(raw))
+        for f in (bad, tmp_path / "missing.bin"):
+            with pytest.raises(hb.HombError) as e:
+                hb.binding.hom_net_load(ctx, str(f))
+            assert e.value.status == hb.binding.HOM_ERR_INVALID_ARG
+    finally:
+        hb.hom_destroy(ctx)
+
+
+def test_learned_start_needs_a_fitting_network(hb, tmp_path):
+    solver = hb.Bounds(0)
+    net = None
+    try:
+        cfg = hb.binding.net_config(9, 1, 4, 2, 1, 8, 8, 2)      # a 2D network
+        npar, _ = hb.binding.hom_net_sizes(solver.ctx, cfg, 1)
+        params = torch.zeros(npar, dtype=torch.float32, device="cuda")
+        path = str(tmp_path / "net.bin")
+        hb.binding.hom_net_save(solver.ctx, cfg, params.data_ptr(), path)
+        net = hb.binding.hom_net_load(solver.ctx, path)
+        for p, kw in ((ms.cube_inclusion_3d(N=9), {}), (ms.square_inclusion_2d(N=9), {"discretization": 1}),
+                      (ms.make_problem(2, (9, 11), 1.0, 1.0, []), {})):
+            with pytest.raises(hb.HombError) as e:
+                solver(p, precision=hb.HOM_FP64, net=net, **kw)
+            assert e.value.status == hb.binding.HOM_ERR_INVALID_ARG
+        # an all-zero network predicts zero: the start is x0 = 0, the plain solve
+        p = ms.square_inclusion_2d(N=9)
+        a = solver(p, precision=hb.HOM_FP64, tol=1e-10, net=net)
+        b = solver(p, precision=hb.HOM_FP64, tol=1e-10)
+        assert np.abs(a["upper"] - b["upper"]).max() <= 1e-12
+    finally:
+        if net:
+            hb.binding.hom_net_free(net)
+        solver.close()
+
+
+def test_energy_bounds(hb):
+    import oracle
+    solver = hb.Bounds(0)
+    try:
+        p = ms.random_anisotropic_2d(5, N=11)
+        ref = oracle.dense_bounds(p)
+        opts = hb.make_opts(hb.HOM_FP64, 1e-12)
+        nws = hb.hom_workspace_size(solver.ctx, p, opts)
+        ws = torch.empty(nws, dtype=torch.uint8, device="cuda")
+        for E in ([1.0, 0.0], [0.3, -0.7], [2.0, 1.0]):
+            up, lo = hb.binding.hom_energy_bounds(solver.ctx, p, opts, ws.data_ptr(), nws, E)
+            Ev = np.asarray(E)
+            assert abs(up - Ev @ ref["upper"] @ Ev) <= 1e-10 * abs(Ev @ ref["upper"] @ Ev)
+            assert abs(lo - Ev @ ref["lower"] @ Ev) <= 1e-10 * abs(Ev @ ref["lower"] @ Ev)
+            assert lo <= up
+    finally:
+        solver.close()
