@@ -342,8 +342,15 @@ __device__ __noinline__ void col_final(const cpx<T>* T2, cpx<T>* q, const cpx<T>
       q[(r * 2 + 0) * fld_fs + e] = u0;
       q[(r * 2 + 1) * fld_fs + e] = u1;
       const cpx<T> p0 = p[(r * 2 + 0) * fld_fs + e], p1 = p[(r * 2 + 1) * fld_fs + e];
-      const double w = kx == 0 ? 1.0 : 2.0;
-      pq_acc[r] += w * ((double)p0.x * u0.x + (double)p0.y * u0.y + (double)p1.x * u1.x + (double)p1.y * u1.y);
+      if constexpr (sizeof(T) == 4) {
+        // each term in FP32, summed in FP64 (FP64 instructions issue at a small fraction of
+        // the FP32 rate)
+        const float sq = fmaf(p0.x, u0.x, fmaf(p0.y, u0.y, fmaf(p1.x, u1.x, p1.y * u1.y)));
+        pq_acc[r] += (double)(kx == 0 ? sq : 2.f * sq);
+      } else {
+        const double w = kx == 0 ? 1.0 : 2.0;
+        pq_acc[r] += w * ((double)p0.x * u0.x + (double)p0.y * u0.y + (double)p1.x * u1.x + (double)p1.y * u1.y);
+      }
     }
     __syncthreads();
   }
@@ -711,8 +718,13 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 2 : 1) k_batch(BArgs a) {
         rv = mk<T>(fma(-al_, qv.x, rv.x), fma(-al_, qv.y, rv.y));
         vx[i] = xv;
         vr[i] = rv;
-        const double w = (i % Nh) == 0 ? 1.0 : 2.0;
-        rr[r] += w * ((double)rv.x * rv.x + (double)rv.y * rv.y);
+        if constexpr (sizeof(T) == 4) {
+          const float sq = fmaf(rv.x, rv.x, rv.y * rv.y);
+          rr[r] += (double)((i % Nh) == 0 ? sq : 2.f * sq);
+        } else {
+          const double w = (i % Nh) == 0 ? 1.0 : 2.0;
+          rr[r] += w * ((double)rv.x * rv.x + (double)rv.y * rv.y);
+        }
       }
       for (int r = 0; r < 2; ++r) {
         const double s = team_sum(tm, rr[r], s_red, s_xch, parity);

@@ -131,6 +131,11 @@ __global__ void __launch_bounds__(kThreads) k_cg_update(cpx<T>* x, cpx<T>* r, co
   const long long n = (long long)C * field;
   const long long base = (long long)rhs * n;
   double acc = 0.0;
+  // FP32 vectors: each |r|^2 term and runs of up to 8 terms in FP32, the sum of the runs over
+  // the thread and the block in FP64 (on this GPU an FP64 instruction issues at 1/64 of the
+  // FP32 rate: converting and multiplying every term in FP64 made this pass FP64-bound)
+  float run = 0.f;
+  int cnt = 0;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
        e += (long long)gridDim.x * blockDim.x) {
     const cpx<T> pv = p[base + e], qv = q[base + e];
@@ -140,9 +145,19 @@ __global__ void __launch_bounds__(kThreads) k_cg_update(cpx<T>* x, cpx<T>* r, co
     x[base + e] = xv;
     r[base + e] = rv;
     const int ei = (int)e;   // < 2^31 elements per right-hand side (checked by the launcher)
-    const double w = ei - fdNh.div(ei) * (int)fdNh.d == 0 ? 1.0 : 2.0;
-    acc += w * ((double)rv.x * rv.x + (double)rv.y * rv.y);
+    const bool k0 = ei - fdNh.div(ei) * (int)fdNh.d == 0;
+    if constexpr (sizeof(T) == 4) {
+      run = fmaf(k0 ? 1.f : 2.f, fmaf(rv.x, rv.x, rv.y * rv.y), run);
+      if (++cnt == 8) {
+        acc += (double)run;
+        run = 0.f;
+        cnt = 0;
+      }
+    } else {
+      acc += (k0 ? 1.0 : 2.0) * ((double)rv.x * rv.x + (double)rv.y * rv.y);
+    }
   }
+  acc += (double)run;
   const double s = block_sum(acc, red);
   if (threadIdx.x == 0) partial[rhs * ld + blockIdx.x] = s;
 }

@@ -225,6 +225,10 @@ __global__ void __launch_bounds__(kPassThreads) k_final(FinalArgs a) {
                               : nullptr;
   const int half = (a.Nlog - 1) / 2;
   double acc = 0.0;
+  // FP32: the p.Cp terms of up to 8 points in FP32, their sums in FP64 (FP64 instructions
+  // issue at a small fraction of the FP32 rate)
+  float run = 0.f;
+  int cnt = 0;
   for (int t = threadIdx.x; t < a.Nlog * a.XC; t += blockDim.x) {
     const int i = a.fd_XC.div(t);
     const int xx = t - i * a.XC;
@@ -295,16 +299,30 @@ __global__ void __launch_bounds__(kPassThreads) k_final(FinalArgs a) {
     for (int c = 0; c < 3; ++c)
       if (c < C) out[(long long)c * a.out_comp + oi] = u[c];
     if (pdir) {
-      double sq = 0.0;
+      if constexpr (sizeof(T) == 4) {
+        float sq = 0.f;
 #pragma unroll
-      for (int c = 0; c < 3; ++c)
-        if (c < C) {
-          if constexpr (sizeof(T) != 4) pv[c] = pdir[(long long)c * a.out_comp + oi];
-          sq += (double)pv[c].x * (double)u[c].x + (double)pv[c].y * (double)u[c].y;
+        for (int c = 0; c < 3; ++c)
+          if (c < C) sq = fmaf(pv[c].x, u[c].x, fmaf(pv[c].y, u[c].y, sq));
+        run = fmaf(kx == 0 ? 1.f : 2.f, sq, run);
+        if (++cnt == 8) {
+          acc += (double)run;
+          run = 0.f;
+          cnt = 0;
         }
-      acc += (kx == 0 ? 1.0 : 2.0) * sq;
+      } else {
+        double sq = 0.0;
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+          if (c < C) {
+            pv[c] = pdir[(long long)c * a.out_comp + oi];
+            sq += (double)pv[c].x * (double)u[c].x + (double)pv[c].y * (double)u[c].y;
+          }
+        acc += (kx == 0 ? 1.0 : 2.0) * sq;
+      }
     }
   }
+  acc += (double)run;
   if (a.partial) {
     const double sum = block_sum(acc, red);
     if (threadIdx.x == 0) a.partial[rhs * a.partial_ld + blockIdx.x] = sum;
