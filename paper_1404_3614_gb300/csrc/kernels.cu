@@ -136,25 +136,41 @@ __global__ void __launch_bounds__(kThreads) k_cg_update(cpx<T>* x, cpx<T>* r, co
   // FP32 rate: converting and multiplying every term in FP64 made this pass FP64-bound)
   float run = 0.f;
   int cnt = 0;
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
-       e += (long long)gridDim.x * blockDim.x) {
-    const cpx<T> pv = p[base + e], qv = q[base + e];
-    cpx<T> xv = x[base + e], rv = r[base + e];
-    xv = mk<T>(fma(al, pv.x, xv.x), fma(al, pv.y, xv.y));
-    rv = mk<T>(fma(-al, qv.x, rv.x), fma(-al, qv.y, rv.y));
-    x[base + e] = xv;
-    r[base + e] = rv;
-    const int ei = (int)e;   // < 2^31 elements per right-hand side (checked by the launcher)
-    const bool k0 = ei - fdNh.div(ei) * (int)fdNh.d == 0;
-    if constexpr (sizeof(T) == 4) {
-      run = fmaf(k0 ? 1.f : 2.f, fmaf(rv.x, rv.x, rv.y * rv.y), run);
-      if (++cnt == 8) {
-        acc += (double)run;
-        run = 0.f;
-        cnt = 0;
+  // four entries per thread and iteration: their 16 loads are in flight together
+  constexpr int U = 4;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long e0 = blockIdx.x * (long long)blockDim.x + threadIdx.x; e0 < n; e0 += U * stride) {
+    cpx<T> pv[U], qv[U], xv[U], rv[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const long long e = e0 + u * stride;
+      if (e < n) {
+        pv[u] = p[base + e];
+        qv[u] = q[base + e];
+        xv[u] = x[base + e];
+        rv[u] = r[base + e];
       }
-    } else {
-      acc += (k0 ? 1.0 : 2.0) * ((double)rv.x * rv.x + (double)rv.y * rv.y);
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const long long e = e0 + u * stride;
+      if (e >= n) break;
+      xv[u] = mk<T>(fma(al, pv[u].x, xv[u].x), fma(al, pv[u].y, xv[u].y));
+      rv[u] = mk<T>(fma(-al, qv[u].x, rv[u].x), fma(-al, qv[u].y, rv[u].y));
+      x[base + e] = xv[u];
+      r[base + e] = rv[u];
+      const int ei = (int)e;   // < 2^31 elements per right-hand side (checked by the launcher)
+      const bool k0 = ei - fdNh.div(ei) * (int)fdNh.d == 0;
+      if constexpr (sizeof(T) == 4) {
+        run = fmaf(k0 ? 1.f : 2.f, fmaf(rv[u].x, rv[u].x, rv[u].y * rv[u].y), run);
+        if (++cnt == 8) {
+          acc += (double)run;
+          run = 0.f;
+          cnt = 0;
+        }
+      } else {
+        acc += (k0 ? 1.0 : 2.0) * ((double)rv[u].x * rv[u].x + (double)rv[u].y * rv[u].y);
+      }
     }
   }
   acc += (double)run;
@@ -618,6 +634,100 @@ __global__ void k_energy_reduce(const double* partial, int nblk, int nrr, double
   }
 }
 
+// The bound energies from the last FP64 residual of the mixed solve (Def. upper_lower_bounds
+// expanded in Fourier space): for x_b in the range of Gamma with residual r_b = b_b - C x_b
+// and b_a = -Gamma A_hat E_a,
+//   a(E_b + x_b, E_a + x_a) = E_a . <A> E_b - <b_a, x_b> - <x_a, r_b>,
+// <A> = A_hat(0) the cell mean of the coefficient and <u, v> the Parseval inner product of the
+// stored half spectra (weight 1 at kx = 0, else 2). Per block: the R^2 sums <b_a, x_b> and the
+// R^2 sums <x_a, r_b>, over all components and frequencies, [blk][2 R^2].
+__global__ void __launch_bounds__(kThreads) k_energy_identity_part(const double2* b, const double2* x, const double2* r,
+                                                                   int R, int C, long long field, FastDiv fdNh,
+                                                                   double* part) {
+  __shared__ double red[32];
+  double acc[18];
+#pragma unroll
+  for (int i = 0; i < 18; ++i) acc[i] = 0.0;
+  const long long n = (long long)C * field;   // entries of one right-hand side
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int k = (int)(e % field);
+    const double w = k - fdNh.div(k) * (int)fdNh.d == 0 ? 1.0 : 2.0;
+    double2 bv[3], xv[3], rv[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+      if (a < R) {
+        bv[a] = b[(long long)a * n + e];
+        xv[a] = x[(long long)a * n + e];
+        rv[a] = r[(long long)a * n + e];
+      }
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int c = 0; c < 3; ++c)
+        if (a < R && c < R) {
+          acc[a * 3 + c] += w * (bv[a].x * xv[c].x + bv[a].y * xv[c].y);
+          acc[9 + a * 3 + c] += w * (xv[a].x * rv[c].x + xv[a].y * rv[c].y);
+        }
+  }
+  for (int a = 0; a < R; ++a)
+    for (int c = 0; c < R; ++c)
+      for (int h = 0; h < 2; ++h) {
+        const double s = block_sum(acc[h * 9 + a * 3 + c], red);
+        if (threadIdx.x == 0) part[(long long)blockIdx.x * 2 * R * R + h * R * R + a * R + c] = s;
+      }
+}
+
+// per block: the sum of each of the ncomp coefficient components over the double grid
+__global__ void __launch_bounds__(kThreads) k_coef_sum_part(const double* coef, int ncomp, long long grid,
+                                                            double* part) {
+  __shared__ double red[32];
+  for (int q = 0; q < ncomp; ++q) {
+    double acc = 0.0;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < grid;
+         e += (long long)gridDim.x * blockDim.x)
+      acc += coef[(long long)q * grid + e];
+    const double s = block_sum(acc, red);
+    if (threadIdx.x == 0) part[(long long)blockIdx.x * ncomp + q] = s;
+  }
+}
+
+// out[a R + c] = |M| (E_a . <A> E_c - <b_a, x_c> - <x_a, r_c>): the energy-pass convention
+// (grid sums, later scaled by 1/|M|)
+__global__ void k_energy_identity_finish(const double* part, int nblk, const double* cpart, int cblk, int R, int d,
+                                         int ncomp, double gridsize, double* out) {
+  __shared__ double red[32];
+  __shared__ double mean[6];
+  for (int q = 0; q < ncomp; ++q) {
+    double s = 0.0;
+    for (int b = threadIdx.x; b < cblk; b += blockDim.x) s += cpart[(long long)b * ncomp + q];
+    s = block_sum(s, red);
+    if (threadIdx.x == 0) mean[q] = s;   // the grid sum of component q
+    __syncthreads();
+  }
+  for (int i = 0; i < 2 * R * R; ++i) {
+    double s = 0.0;
+    for (int b = threadIdx.x; b < nblk; b += blockDim.x) s += part[(long long)b * 2 * R * R + i];
+    s = block_sum(s, red);
+    if (threadIdx.x == 0) {
+      const int h = i / (R * R), ac = i - h * R * R, a = ac / R, c = ac - a * R;
+      if (h == 0) {
+        int q = 0;
+        if (ncomp > 1) {
+          if (a == c) q = a;
+          else if (d == 2) q = 2;
+          else q = (a + c == 3) ? 3 : ((a + c == 2) ? 4 : 5);
+        }
+        const double A = (ncomp == 1 && a != c) ? 0.0 : mean[q];
+        out[ac] = A - gridsize * s;
+      } else {
+        out[ac] -= gridsize * s;
+      }
+    }
+    __syncthreads();
+  }
+}
+
 __global__ void k_convert_d2f(const double* in, float* out, long long n) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x)
@@ -836,6 +946,17 @@ template cudaError_t launch_negate_norm<float>(void*, int, int, long long, int, 
 cudaError_t launch_energy_reduce(const double* partial, int nblk, int nrr, double* out,
                                  cudaStream_t s) {
   k_energy_reduce<<<1, kThreads, 0, s>>>(partial, nblk, nrr, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_energy_identity(const double2* b, const double2* x, const double2* r, int R, int C,
+                                   long long field, int Nh, const double* coef, int ncomp, long long grid,
+                                   double* part, int nblk, double* cpart, int cblk, double* out, cudaStream_t s) {
+  if (R < 1 || R > 3 || C > 3) return cudaErrorInvalidValue;
+  k_energy_identity_part<<<nblk, kThreads, 0, s>>>(b, x, r, R, C, field, FastDiv((uint32_t)Nh), part);
+  k_coef_sum_part<<<cblk, kThreads, 0, s>>>(coef, ncomp, grid, cpart);
+  const int d = C;
+  k_energy_identity_finish<<<1, kThreads, 0, s>>>(part, nblk, cpart, cblk, R, d, ncomp, (double)grid, out);
   return cudaGetLastError();
 }
 
