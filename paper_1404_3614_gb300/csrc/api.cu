@@ -444,7 +444,9 @@ Layout make_layout(const Geometry& g, int R, size_t elem, int mode) {
   L.partial = L.take((size_t)3 * L.maxblk * sizeof(double));
   L.rrpart = L.take((size_t)6 * kVecBlocks * sizeof(double));
   L.nblk_energy = (int)g.planes;   // upper bound of the energy pass grid
-  L.epart = L.take((size_t)L.nblk_energy * 9 * sizeof(double));
+  // the energy pass's per-block 3x3 sums, or the Fourier-side identity's (kVecBlocks blocks
+  // of 2 x 9 sums and of up to 6 coefficient sums)
+  L.epart = L.take(std::max((size_t)L.nblk_energy * 9, (size_t)kVecBlocks * 24) * sizeof(double));
   L.eout = L.take(2 * 9 * sizeof(double));
   L.total = L.off;
   return L;
@@ -1222,8 +1224,11 @@ hom_status Runner_solve_mixed(Runner& run, int side, const hom_opts& o, hom_repo
     CK(cudaStreamSynchronize(st));
     for (int r = 0; r < R; ++r) inner_iters[r] += ctx->host_cg->iters[r];
     if (ctx->host_cg->fault) return fail(ctx, HOM_ERR_TIMEOUT, "an operator pass gave up waiting for its staged input");
-    // x64 += d, then the exact FP64 residual r64 = b - C x64
+    // x64 += d, re-projected in FP64, then the exact FP64 residual r64 = b - C x64 (so that at
+    // the end x64 lies in the range of Gamma and r64 is its residual: the bound energies follow
+    // from them without another pass over the double grid)
     KL(launch_promote_add(run.at<float2>(L.x), x64, n, st));
+    KL(launch_project_promote<double>(x64, x64, R, g.d, g.N[1], g.N[2], g.Nh, g.invY, side, st));
     CKS(run.matvec<double>(x64, r64, coef64, side + 1, outer, nullptr, nullptr, 0, b64));
     KL(launch_outer_check(outer, partial, L.maxblk, nfin64, R, 0.25, st));
     ++*matvecs;
@@ -1243,8 +1248,20 @@ hom_status Runner_solve_mixed(Runner& run, int side, const hom_opts& o, hom_repo
     else if (stt == 1 && result == HOM_OK) result = HOM_WARN_NOT_CONVERGED;
   }
   if (result == HOM_ERR_BREAKDOWN) return result;
-  KL(launch_project_promote<double>(x64, x64, R, g.d, g.N[1], g.N[2], g.Nh, g.invY, side, st));
-  CKS(run.energy(coef64, x64, 1, side));
+  if (run.gani) {   // the GaNi fields' energies are those of the Galerkin (double-grid) operator
+    KL(launch_project_promote<double>(x64, x64, R, g.d, g.N[1], g.N[2], g.Nh, g.invY, side, st));
+    CKS(run.energy(coef64, x64, 1, side));
+    return result;
+  }
+  // a(E_b + x_b, E_a + x_a) = E_a.<A>E_b - <b_a, x_b> - <x_a, r_b> with the final x64 (in the
+  // range of Gamma) and its FP64 residual r64 = b - C x64 (Def. upper_lower_bounds, Lemma
+  // double-grid: C is the exactly integrated Galerkin operator)
+  {
+    Prof pr(ctx, "energy", st);
+    double* part = run.at<double>(L.epart);
+    KL(launch_energy_identity(b64, x64, r64, R, g.d, g.field, g.Nh, coef64, g.ncomp, g.grid, part, kVecBlocks,
+                              part + (size_t)kVecBlocks * 18, kVecBlocks, run.at<double>(L.eout) + side * 9, st));
+  }
   return result;
 }
 

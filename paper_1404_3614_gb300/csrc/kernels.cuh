@@ -251,6 +251,13 @@ cudaError_t launch_resample(const void* in, void* out, long long count, int d, c
 template <typename T>
 cudaError_t launch_project_promote(const void* x, double2* x64, int nrhs, int d, int Ny, int Nz,
                                    int Nh, const double* invY, int side, cudaStream_t s);
+// The bound energies of a side from x (in the range of Gamma), its residual r = b - C x and b
+// (FP64 half spectra [R][C][field]) and the FP64 double-grid coefficient (its grid sum gives
+// the cell mean): out[a R + c] in the energy pass's convention (grid sums). part needs
+// nblk * 2 R^2 doubles, cpart cblk * ncomp; three launches.
+cudaError_t launch_energy_identity(const double2* b, const double2* x, const double2* r, int R, int C,
+                                   long long field, int Nh, const double* coef, int ncomp, long long grid,
+                                   double* part, int nblk, double* cpart, int cblk, double* out, cudaStream_t s);
 cudaError_t launch_energy_reduce(const double* partial, int nblk, int nrr, double* out,
                                  cudaStream_t s);
 cudaError_t launch_convert_d2f(const double* in, float* out, long long n, cudaStream_t s);
