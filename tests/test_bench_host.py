@@ -30,6 +30,16 @@ def test_traffic_reported_only_for_the_captured_kernel(monkeypatch):
     assert bench.slab_traffic() == 123
 
 
+def test_reference_arm_uses_the_oracles_own_iteration_counts():
+    """The oracle arm extrapolates the 16-ball cell with the oracle CG's own iteration counts to
+    1e-4, read off the residual history of the full-size golden run (equal to the GPU's FP64
+    counts on this cell)."""
+    it = bench.oracle_iters_c5()
+    assert it is not None
+    assert it == {"primal": [176, 176, 176], "dual": [49, 51, 49]}
+    assert bench.reference_iters(bench.workload("spheres3d_N113"), "spheres3d_N113") == it
+
+
 def test_slab_byte_model():
     """Passes 2-4 of the 5-pass model on the 16-ball cell (N = 113, M = 225, Nh = 57), 9 FP32
     field components and 3 coefficient reads."""
