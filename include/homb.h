@@ -187,7 +187,7 @@ typedef struct {
                            (log10 of the phase value / 3), runs the network (tensor-core
                            GEMMs) on that grid, takes the half spectra of its 2 d^2
                            output channels (side, rhs, component) and starts each CG from
-                           their projection scaled by Rayleigh-Ritz. The cell's grid must
+                           their projection (block Rayleigh-Ritz). The cell's grid must
                            be cubic (one N on every axis) with 2 modes <= N.        */
   int32_t reserved;
   const struct hom_net* net; /* warm_start = 1: a network from hom_net_load            */
@@ -239,9 +239,11 @@ hom_status hom_workspace_size(hom_ctx* ctx, const hom_problem* prob, const hom_o
 /* Starting fields in / converged fields out for hom_bounds_io (device memory, complex
  * FP64, layout [side 2][rhs d][comp d][Nz][Ny][(N1+1)/2], the half-spectrum layout of
  * the fields with side 0 primal and 1 dual). A start is projected with Gamma (so any
- * array gives a conforming field, Def. FD_projections) and scaled per right-hand side by
- * the Rayleigh-Ritz factor s = (x.b)/(x.C x), which never gives a larger energy error than
- * x = 0; CG then runs from it and the bounds stay guaranteed (Lemma bounds). The fields
+ * array gives a conforming field, Def. FD_projections); each right-hand side of a side then
+ * starts from its Galerkin solution in the span of the side's d projected starts (block
+ * Rayleigh-Ritz; the per-right-hand-side scaling when they are dependent), which never gives a
+ * larger energy error than x = 0; CG then runs from it and the bounds stay guaranteed (Lemma
+ * bounds). The batched launch scales each start by its own Rayleigh-Ritz factor. The fields
  * out are the FP64 re-projected CG fields the bounds were evaluated with. Either pointer
  * may be NULL; not with GaNi. */
 typedef struct {

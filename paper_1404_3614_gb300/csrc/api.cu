@@ -1069,13 +1069,16 @@ struct Runner {
     const double tol = o.tol > 0 ? o.tol : 1e-8;
     const int nfin = final_blocks(elem);
     if (x0 && sizeof(T) == 8 && user_start) {
-      // a caller's start: x = s Gamma x0 with the Rayleigh-Ritz factor s = (x.b)/(x.C x) per
-      // right-hand side (never a larger energy error than x = 0), r = b - s C x
+      // a caller's start: the Galerkin solution of each right-hand side in the span of the R
+      // projected starts Gamma x0 (block Rayleigh-Ritz: never a larger energy error than the
+      // per-right-hand-side scaling or than x = 0), r = b - C x
       KL(launch_project_promote<double>(x0, at<double2>(L.x), R, g.d, g.N[1], g.N[2], g.Nh, g.invY, side, st));
       CKS(matvec<T>(base + L.x, base + L.q, coefT, side + 1, nullptr, nullptr, nullptr, 0));
       ++*matvecs;
-      KL(launch_rayleigh_ritz<double>(base + L.x, base + L.r, base + L.r, base + L.q, R, g.d, g.field, g.Nh,
-                                      at<double>(L.rrpart), at<double>(L.partial), kVecBlocks, st));
+      double* ep = at<double>(L.epart);
+      KL(launch_block_rayleigh_ritz(at<double2>(L.x), at<double2>(L.r), at<double2>(L.r), at<double2>(L.q), R, g.d,
+                                    g.field, g.Nh, ep, ep + (size_t)kVecBlocks * 18, at<double>(L.partial),
+                                    kVecBlocks, st));
       KL(launch_cg_init(cg, at<double>(L.partial), kVecBlocks, kVecBlocks, R, tol * tol, 0.0, 0, st));
     } else if (x0 && sizeof(T) == 8) {   // x = x0 (after b, which GaNi forms from x = 0); r0 = b - C x0
       CK(cudaMemcpyAsync(base + L.x, x0, fb, cudaMemcpyDeviceToDevice, st));
@@ -1170,13 +1173,14 @@ hom_status Runner_solve_mixed(Runner& run, int side, const hom_opts& o, hom_repo
     }
     return HOM_OK;
   };
-  if (warm && user_start) {   // a caller's start in b64: x64 = s Gamma start, r64 = b - s C x64
+  if (warm && user_start) {   // a caller's start in b64: block Rayleigh-Ritz over its projection, r64 = b - C x64
     KL(launch_project_promote<double>(b64, x64, R, g.d, g.N[1], g.N[2], g.Nh, g.invY, side, st));
     CKS(form_rhs(r64));
     CKS(run.matvec<double>(x64, r64, coef64, side + 1, nullptr, nullptr, nullptr, 0));
     ++*matvecs;
-    KL(launch_rayleigh_ritz<double>(x64, r64, b64, r64, R, g.d, g.field, g.Nh, run.at<double>(L.rrpart), partial,
-                                    kVecBlocks, st));
+    double* ep = run.at<double>(L.epart);
+    KL(launch_block_rayleigh_ritz(x64, r64, b64, r64, R, g.d, g.field, g.Nh, ep, ep + (size_t)kVecBlocks * 18,
+                                  partial, kVecBlocks, st));
     KL(launch_cg_init(outer, partial, kVecBlocks, kVecBlocks, R, tol * tol, 0.0, 0, st));
   } else if (warm) {   // the start is in b64 (Runner::dual_start): x64 = start, r64 = b - C x64
     CK(cudaMemcpyAsync(x64, b64, n * sizeof(double2), cudaMemcpyDeviceToDevice, st));

@@ -943,6 +943,121 @@ template cudaError_t launch_rayleigh_ritz<double>(void*, void*, const void*, con
 template cudaError_t launch_negate_norm<double>(void*, int, int, long long, int, double*, int, cudaStream_t);
 template cudaError_t launch_negate_norm<float>(void*, int, int, long long, int, double*, int, cudaStream_t);
 
+// Block Rayleigh-Ritz start over the R starting fields x_i of one side (their span V):
+// G = V^T C V, H = V^T B with q_i = C x_i; each right-hand side gets the Galerkin solution in V,
+// x_j <- sum_i c_ij x_i with G c_j = H e_j, and r_j = b_j - sum_i c_ij q_i (never a larger
+// energy error than the per-right-hand-side Rayleigh-Ritz scaling or than x = 0). When G is
+// not safely positive definite (dependent starts) the diagonal scaling c_jj = H_jj / G_jj is
+// used instead.
+__global__ void k_brr_solve(const double* part, int nblk, int R, double* coefs) {
+  __shared__ double red[32];
+  __shared__ double GH[18];
+  for (int i = 0; i < 2 * R * R; ++i) {
+    double s = 0.0;
+    for (int b = threadIdx.x; b < nblk; b += blockDim.x) s += part[(long long)b * 2 * R * R + i];
+    s = block_sum(s, red);
+    if (threadIdx.x == 0) GH[i] = s;
+    __syncthreads();
+  }
+  if (threadIdx.x != 0) return;
+  // part holds <b_a, x_c> (H^T) then <x_a, q_c> (G)
+  double G[9], H[9], L[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0}, c[9];
+  for (int a = 0; a < R; ++a)
+    for (int b = 0; b < R; ++b) {
+      H[a * R + b] = GH[b * R + a];                                        // <x_a, b_b>
+      G[a * R + b] = 0.5 * (GH[R * R + a * R + b] + GH[R * R + b * R + a]);   // symmetric part
+    }
+  bool ok = true;
+  double tr = 0.0;
+  for (int a = 0; a < R; ++a) tr += fabs(G[a * R + a]);
+  for (int j = 0; j < R && ok; ++j) {   // Cholesky G = L L^T
+    double dgl = G[j * R + j];
+    for (int k = 0; k < j; ++k) dgl -= L[j * R + k] * L[j * R + k];
+    if (!(dgl > 1e-12 * tr) || !isfinite(dgl)) {
+      ok = false;
+      break;
+    }
+    L[j * R + j] = sqrt(dgl);
+    for (int i = j + 1; i < R; ++i) {
+      double v = G[i * R + j];
+      for (int k = 0; k < j; ++k) v -= L[i * R + k] * L[j * R + k];
+      L[i * R + j] = v / L[j * R + j];
+    }
+  }
+  for (int j = 0; j < R; ++j) {   // column j: G c = H e_j
+    double y[3], cj[3];
+    if (ok) {
+      for (int i = 0; i < R; ++i) {
+        double v = H[i * R + j];
+        for (int k = 0; k < i; ++k) v -= L[i * R + k] * y[k];
+        y[i] = v / L[i * R + i];
+      }
+      for (int i = R - 1; i >= 0; --i) {
+        double v = y[i];
+        for (int k = i + 1; k < R; ++k) v -= L[k * R + i] * cj[k];
+        cj[i] = v / L[i * R + i];
+      }
+    } else {
+      for (int i = 0; i < R; ++i) cj[i] = 0.0;
+      const double gj = G[j * R + j];
+      cj[j] = gj > 0.0 && isfinite(H[j * R + j] / gj) ? H[j * R + j] / gj : 0.0;
+    }
+    for (int i = 0; i < R; ++i) c[i * R + j] = isfinite(cj[i]) ? cj[i] : 0.0;
+  }
+  for (int i = 0; i < R * R; ++i) coefs[i] = c[i];
+}
+
+// x_j <- sum_i c_ij x_i, r_j <- b_j - sum_i c_ij q_i (in place: every right-hand side of one
+// entry is read before any is written; r may alias b or q), |r_j|^2 partials [rhs][blk]
+__global__ void __launch_bounds__(kThreads) k_brr_apply(double2* x, double2* r, const double2* b, const double2* q,
+                                                        int R, long long n, FastDiv fdNh, long long field,
+                                                        const double* coefs, double* partial, int ld) {
+  __shared__ double red[32];
+  double c[9];
+  for (int i = 0; i < R * R; ++i) c[i] = coefs[i];
+  double acc[3] = {0.0, 0.0, 0.0};
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int k = (int)(e % field);
+    const double w = k - fdNh.div(k) * (int)fdNh.d == 0 ? 1.0 : 2.0;
+    double2 xv[3], qv[3], bv[3];
+    for (int i = 0; i < R; ++i) {
+      xv[i] = x[(long long)i * n + e];
+      qv[i] = q[(long long)i * n + e];
+      bv[i] = b[(long long)i * n + e];
+    }
+    for (int j = 0; j < R; ++j) {
+      double2 xn = make_double2(0.0, 0.0), rn = bv[j];
+      for (int i = 0; i < R; ++i) {
+        const double cij = c[i * R + j];
+        xn.x = fma(cij, xv[i].x, xn.x);
+        xn.y = fma(cij, xv[i].y, xn.y);
+        rn.x = fma(-cij, qv[i].x, rn.x);
+        rn.y = fma(-cij, qv[i].y, rn.y);
+      }
+      x[(long long)j * n + e] = xn;
+      r[(long long)j * n + e] = rn;
+      acc[j] += w * (rn.x * rn.x + rn.y * rn.y);
+    }
+  }
+  for (int j = 0; j < R; ++j) {
+    const double s = block_sum(acc[j], red);
+    if (threadIdx.x == 0) partial[(long long)j * ld + blockIdx.x] = s;
+  }
+}
+
+cudaError_t launch_block_rayleigh_ritz(double2* x, double2* r, const double2* b, const double2* q, int R, int C,
+                                       long long field, int Nh, double* part, double* coefs, double* partial,
+                                       int nblk, cudaStream_t s) {
+  if (R < 1 || R > 3 || (long long)C * field >= (1LL << 31)) return cudaErrorInvalidValue;
+  const FastDiv fd((uint32_t)Nh);
+  // <b_a, x_c> and <x_a, q_c> (the energy identity's pair sums with r = q)
+  k_energy_identity_part<<<nblk, kThreads, 0, s>>>(b, x, q, R, C, field, fd, part);
+  k_brr_solve<<<1, kThreads, 0, s>>>(part, nblk, R, coefs);
+  k_brr_apply<<<nblk, kThreads, 0, s>>>(x, r, b, q, R, (long long)C * field, fd, field, coefs, partial, nblk);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_energy_reduce(const double* partial, int nblk, int nrr, double* out,
                                  cudaStream_t s) {
   k_energy_reduce<<<1, kThreads, 0, s>>>(partial, nblk, nrr, out);

@@ -258,6 +258,12 @@ cudaError_t launch_project_promote(const void* x, double2* x64, int nrhs, int d,
 cudaError_t launch_energy_identity(const double2* b, const double2* x, const double2* r, int R, int C,
                                    long long field, int Nh, const double* coef, int ncomp, long long grid,
                                    double* part, int nblk, double* cpart, int cblk, double* out, cudaStream_t s);
+// Block Rayleigh-Ritz start of one side from R FP64 starting fields x (in place), q = C x, the
+// right-hand sides b; writes x, r = b - C x and |r|^2 partials [rhs][nblk]. part: nblk * 18
+// doubles; coefs: 9 doubles. Three launches.
+cudaError_t launch_block_rayleigh_ritz(double2* x, double2* r, const double2* b, const double2* q, int R, int C,
+                                       long long field, int Nh, double* part, double* coefs, double* partial,
+                                       int nblk, cudaStream_t s);
 cudaError_t launch_energy_reduce(const double* partial, int nblk, int nrr, double* out,
                                  cudaStream_t s);
 cudaError_t launch_convert_d2f(const double* in, float* out, long long n, cudaStream_t s);

@@ -48,6 +48,10 @@ template <typename T> inline bool warp_fft_len(int M) { return sizeof(T) == 4 &&
 
 template <typename T, int R>
 __device__ __forceinline__ void pencil_fft_inplace(cpx<T>* p, int l, const cpx<T>* Wt, int dir, bool on);
+template <typename T, int R>
+__device__ __forceinline__ void pencil_fft_pad_inv(cpx<T>* p, int l, const cpx<T>* Wt, bool on);
+template <typename T, int R>
+__device__ __forceinline__ void pencil_fft_fwd_trunc(cpx<T>* p, int l, const cpx<T>* Wt, bool on);
 
 // twiddles w_M^(l k) at [k][l] for the warp FFT of length R * R
 template <typename T, int R>
@@ -59,9 +63,20 @@ __device__ __forceinline__ void stage_twiddles_kl(cpx<T>* Wt, const void* W) {
   }
 }
 
-// G contiguous pencils (stride R*R) in place, R lanes per pencil; ends with __syncthreads
+// G contiguous pencils (stride R*R) in place, R lanes per pencil; ends with __syncthreads.
+// mode 1: zero-padded inverse transforms (at most (M+1)/2 nonzero inputs: the zero band of
+// the lane layout is not read); mode 2: truncating forward transforms (at most (M+1)/2
+// outputs kept: the band's outputs are neither computed nor stored); 0: full transforms.
+// true when Nlog frequencies stored around 0 of a length-M pencil (positions 0..half and the
+// top Nlog - 1 - half) leave the zero band of the warp FFT's lane layout, positions
+// (M+3)/4 .. (3M-3)/4, empty
+__host__ __device__ inline bool zero_band_free(int M, int Nlog) {
+  const int half = (Nlog - 1) / 2, top = Nlog - 1 - half;
+  return half < (M + 3) / 4 && M - top > (3 * M - 3) / 4;
+}
+
 template <typename T, int R>
-__device__ __forceinline__ void fft_warp_all(cpx<T>* A, int G, const cpx<T>* Wt, int dir) {
+__device__ __forceinline__ void fft_warp_all(cpx<T>* A, int G, const cpx<T>* Wt, int dir, int mode = 0) {
   constexpr int PW = 32 / R;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int sub = lane / R, l = lane - sub * R;
@@ -70,7 +85,10 @@ __device__ __forceinline__ void fft_warp_all(cpx<T>* A, int G, const cpx<T>* Wt,
   for (int g0 = 0; g0 < G; g0 += slots) {
     const int g = g0 + warp * PW + sub;
     const bool on = act && g < G;
-    pencil_fft_inplace<T, R>(A + (size_t)(on ? g : 0) * (R * R), l, Wt, dir, on);
+    cpx<T>* p = A + (size_t)(on ? g : 0) * (R * R);
+    if (mode == 1 && dir > 0) pencil_fft_pad_inv<T, R>(p, l, Wt, on);
+    else if (mode == 2 && dir < 0) pencil_fft_fwd_trunc<T, R>(p, l, Wt, on);
+    else pencil_fft_inplace<T, R>(p, l, Wt, dir, on);
   }
   __syncthreads();
 }
@@ -145,7 +163,9 @@ __global__ void __launch_bounds__(kPassThreads) k_pencil(PencilArgs a) {
   __syncthreads();
   cpx<T>* res;
   if constexpr (WR > 0) {
-    fft_warp_all<T, WR>(A, XC, Ws, a.dir);
+    // padded inverse / truncating forward: M >= 2 Nlog - 1, so the zero band holds no data
+    const bool band = zero_band_free(M, a.Nlog);
+    fft_warp_all<T, WR>(A, XC, Ws, a.dir, pad && band ? 1 : (a.dir < 0 && a.Pout != M && band ? 2 : 0));
     res = A;
   } else {
     const bool trunc_ = a.dir < 0 && a.Pout != M;
@@ -213,7 +233,7 @@ __global__ void __launch_bounds__(kPassThreads) k_final(FinalArgs a) {
   __syncthreads();
   cpx<T>* res;
   if constexpr (WR > 0) {
-    fft_warp_all<T, WR>(A, C * XC, Ws, -1);
+    fft_warp_all<T, WR>(A, C * XC, Ws, -1, a.Nlog < M && zero_band_free(M, a.Nlog) ? 2 : 0);
     res = A;
   } else {
     res = fft_any<T, MT>(A, B, C * XC, a.plan, Ws, -1, prune3_ok(M, (a.Nlog - 1) / 2 + 1) ? 2 : 0);

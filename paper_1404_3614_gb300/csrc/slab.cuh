@@ -330,6 +330,34 @@ __device__ __forceinline__ void pencil_fft_fwd_trunc(cpx<T>* p, int l, const cpx
   __syncwarp();
 }
 
+// pencil_fft_inplace for a zero-padded inverse transform (dir = +1): the zero band's inputs
+// are not read
+template <typename T, int R>
+__device__ __forceinline__ void pencil_fft_pad_inv(cpx<T>* p, int l, const cpx<T>* Wt, bool on) {
+  cpx<T> v[R];
+#pragma unroll
+  for (int n = 0; n < R; ++n)
+    if (!ZeroBand<R>::in(n)) v[n] = on ? p[l + R * n] : mk<T>(T(0), T(0));
+  dft_reg_zin<T, R>(v, +1);
+#pragma unroll
+  for (int k = 1; k < R; ++k) v[k] = mulc<T>(v[k], Wt[k * R + l], true);
+  __syncwarp();
+  if (on) {
+#pragma unroll
+    for (int k = 0; k < R; ++k) p[l + R * k] = v[k];
+  }
+  __syncwarp();
+#pragma unroll
+  for (int n = 0; n < R; ++n) v[n] = on ? p[n + R * l] : mk<T>(T(0), T(0));
+  dft_reg<T, R>(v, +1);
+  __syncwarp();
+  if (on) {
+#pragma unroll
+    for (int k = 0; k < R; ++k) p[l + R * k] = v[k];
+  }
+  __syncwarp();
+}
+
 // fft_finish whose outputs of the zero band are not needed (a truncating forward transform)
 template <typename T, int R>
 __device__ __forceinline__ void fft_finish_zout(cpx<T>* v, cpx<T>* S, int l, const cpx<T>* Wt, bool own) {
@@ -346,7 +374,7 @@ __device__ __forceinline__ void fft_finish_zout(cpx<T>* v, cpx<T>* S, int l, con
   dft_reg_zout<T, R>(v, -1);
 }
 
-template <typename T, int R>
+template <typename T, int R, bool ZB>
 __global__ void __launch_bounds__(kSlabMaxThreads) k_slab(SlabArgs a) {
   constexpr int M = R * R;
   constexpr int PW = 32 / R;   // pencils per warp
@@ -445,12 +473,13 @@ __global__ void __launch_bounds__(kSlabMaxThreads) k_slab(SlabArgs a) {
       cpx<T> v[R];
 #pragma unroll
       for (int n = 0; n < R; ++n) {
-        if (ZeroBand<R>::in(n)) continue;   // padding rows only
+        if (ZB && ZeroBand<R>::in(n)) continue;   // padding rows only
         const int pos = l + R * n;
         const int y = pos <= half ? pos : (pos >= M - half ? pos - M + Ny : -1);
         v[n] = (on && y >= 0) ? stage[(size_t)y * Nh + kx] : mk<T>(T(0), T(0));
       }
-      dft_reg_zin<T, R>(v, +1);
+      if constexpr (ZB) dft_reg_zin<T, R>(v, +1);
+      else dft_reg<T, R>(v, +1);
 #pragma unroll
       for (int k = 1; k < R; ++k) v[k] = mulc<T>(v[k], Wt[k * R + l], true);   // inverse: conjugate twiddles
       __syncwarp();
@@ -489,7 +518,7 @@ __global__ void __launch_bounds__(kSlabMaxThreads) k_slab(SlabArgs a) {
       cpx<T> v[R];
 #pragma unroll
       for (int n = 0; n < R; ++n) {
-        if (ZeroBand<R>::in(n)) continue;   // frequencies of the padding only
+        if (ZB && ZeroBand<R>::in(n)) continue;   // frequencies of the padding only
         const int k = l + R * n;
         cpx<T> A = mk<T>(T(0), T(0)), B = mk<T>(T(0), T(0));
         if (on) {
@@ -504,19 +533,21 @@ __global__ void __launch_bounds__(kSlabMaxThreads) k_slab(SlabArgs a) {
         }
         v[n] = mk<T>(A.x - B.y, A.y + B.x);
       }
-      dft_reg_zin<T, R>(v, +1);
+      if constexpr (ZB) dft_reg_zin<T, R>(v, +1);
+      else dft_reg<T, R>(v, +1);
       fft_finish<T, R>(v, Sw, l, Wt, +1, act);
       // v[k1] = z(x = l + R k1): real part row ya, imaginary part row yb
 #pragma unroll
       for (int k = 0; k < R; ++k) v[k] = mk<T>(v[k].x * (ca[k] * scale), v[k].y * (cb[k] * scale));
       // forward transform: lane l holds x[l + R n2] with n2 = k1; the kept frequencies only
       dft_reg<T, R>(v, -1);
-      fft_finish_zout<T, R>(v, Sw, l, Wt, act);
+      if constexpr (ZB) fft_finish_zout<T, R>(v, Sw, l, Wt, act);
+      else fft_finish<T, R>(v, Sw, l, Wt, -1, act);
       __syncwarp();
       if (act) {
 #pragma unroll
         for (int k = 0; k < R; ++k)
-          if (!ZeroBand<R>::in(k)) Sw[l + R * k] = v[k];
+          if (!(ZB && ZeroBand<R>::in(k))) Sw[l + R * k] = v[k];
       }
       __syncwarp();
       if (on) {
@@ -537,11 +568,13 @@ __global__ void __launch_bounds__(kSlabMaxThreads) k_slab(SlabArgs a) {
     const long long sn = next_active(s);
     if (threadIdx.x == 0 && sn < nslabs) issue(sn);
 
-    // ---- forward y transforms (truncated: the zero band's rows are neither computed nor stored)
+    // ---- forward y transforms (truncated; with ZB the zero band's rows are neither computed nor
+    // stored)
     for (int c0 = 0; c0 < Nh; c0 += slots) {
       const int kx = c0 + slot;
       const bool on = act && kx < Nh;
-      pencil_fft_fwd_trunc<T, R>(P + (size_t)(on ? kx : 0) * M, l, Wt, on);
+      if constexpr (ZB) pencil_fft_fwd_trunc<T, R>(P + (size_t)(on ? kx : 0) * M, l, Wt, on);
+      else pencil_fft_inplace<T, R>(P + (size_t)(on ? kx : 0) * M, l, Wt, -1, on);
     }
     __syncthreads();
     cpx<T>* o = out + mem(s) * slab_elems;
@@ -556,22 +589,38 @@ __global__ void __launch_bounds__(kSlabMaxThreads) k_slab(SlabArgs a) {
   }
 }
 
-template <typename T, int R> cudaError_t launch_slab_r(const SlabArgs& a, int warps, cudaStream_t s) {
+template <typename T, int R, bool ZB> cudaError_t launch_slab_rz(const SlabArgs& a, int warps, cudaStream_t s) {
   const size_t smem = slab_smem_bytes(R * R, R, a.Nh, warps, sizeof(cpx<T>));
   static std::atomic<int> cache[kAttrDevices] = {};
-  cudaError_t e = smem_attr(k_slab<T, R>, smem, cache);
+  cudaError_t e = smem_attr(k_slab<T, R, ZB>, smem, cache);
   if (e != cudaSuccess) return e;
   // persistent: as many CTAs as are resident at once, at most one per slab
   int dev = 0, sms = 0, per = 0;
   e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_slab<T, R>, warps * 32, smem);
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_slab<T, R, ZB>, warps * 32, smem);
   if (e != cudaSuccess) return e;
   if (per < 1) return cudaErrorInvalidConfiguration;
   const long long nslabs = (long long)a.nrc * a.Mz;
   const int grid = (int)std::min<long long>(nslabs, (long long)sms * per);
-  k_slab<T, R><<<grid, warps * 32, smem, s>>>(a);
+  k_slab<T, R, ZB><<<grid, warps * 32, smem, s>>>(a);
   return cudaGetLastError();
+}
+
+// The zero band applies when the y rows (Ny stored around 0) and the Hermitian x extension
+// (2 Nh - 1 frequencies around 0) leave it empty: a zero-padded double grid M >= 2N - 1; not
+// when the transforms are as long as the data (GaNi on the N grid, M = N)
+inline bool slab_band_free(int M, int Ny, int Nh) {
+  auto f = [M](int n) {
+    const int half = (n - 1) / 2, top = n - 1 - half;
+    return half < (M + 3) / 4 && M - top > (3 * M - 3) / 4;
+  };
+  return f(Ny) && f(2 * Nh - 1);
+}
+
+template <typename T, int R> cudaError_t launch_slab_r(const SlabArgs& a, int warps, cudaStream_t s) {
+  return slab_band_free(a.M, a.Ny, a.Nh) ? launch_slab_rz<T, R, true>(a, warps, s)
+                                         : launch_slab_rz<T, R, false>(a, warps, s);
 }
 
 // Warps per slab CTA, or 0 when the slab pass does not apply (length not R*R with R in
