@@ -69,6 +69,16 @@ def test_fullsize_3d_bounds_match_oracle(hb, solver, name, maker, tol_fp64):
     check(mixed, gold, 1e-6)
 
 
+def test_mixed_precision_reaches_fp64_accuracy_on_the_cube_cell(hb, solver):
+    """FP32 inner CG with FP64 refinement, run to tol 1e-8, gives the cube cell's bounds within
+    1e-10 of the oracle (the energies come from the final FP64 residual), at a fraction of
+    the cost of plain FP64 CG to the same accuracy."""
+    gold = GOLD["cube3d_N41"]
+    out = solver(ms.cube_inclusion_3d(), precision=hb.HOM_MIXED, tol=1e-8)
+    assert out["status"] == 0
+    check(out, gold, 1e-10)
+
+
 @pytest.mark.parametrize("cluster", [0, 4])
 def test_benchmark_batch_large_cells_match_oracle(hb, solver, cluster):
     """Cells of the 256-cell batch with N = 113 (seeds 2, 6) and N = 203 (seeds 5, 10),
