@@ -180,15 +180,19 @@ typedef struct {
                            GaNi matrix is applied on the double grid instead (the
                            same operator, fast FFT lengths). FP64 or mixed; no
                            starting / output fields.                             */
-  int32_t warm_start;   /* hom_bounds, Ga only: 0 starts CG from zero; 1 from the learned
-                           start of `net` (no counterpart in the paper's algorithm; any
-                           start projected onto E_N / J_N keeps the bounds guaranteed,
-                           Lemma bounds): the library samples the cell on its N grid
-                           (log10 of the phase value / 3), runs the network (tensor-core
-                           GEMMs) on that grid, takes the half spectra of its 2 d^2
-                           output channels (side, rhs, component) and starts each CG from
-                           their projection (block Rayleigh-Ritz). The cell's grid must
-                           be cubic (one N on every axis) with 2 modes <= N.        */
+  int32_t warm_start;   /* hom_bounds and hom_bounds_batched, Ga only: 0 starts CG from
+                           zero; 1 from the learned start of `net` (no counterpart in the
+                           paper's algorithm; any start projected onto E_N / J_N keeps
+                           the bounds guaranteed, Lemma bounds): the library samples the
+                           cell on its N grid (log10 of the phase value / 3), runs the
+                           network (tensor-core GEMMs) on that grid, takes the half
+                           spectra of its 2 d^2 output channels (side, rhs, component)
+                           and starts each CG from their projection (hom_bounds: block
+                           Rayleigh-Ritz; batched: one Rayleigh-Ritz scale per
+                           right-hand side). The grid must be cubic (one N on every
+                           axis) with 2 modes <= N; in a batch every cell has the same
+                           N, and the network runs on chunks of cells (activations of
+                           at most 512 MiB a chunk). Not with starting fields.      */
   int32_t reserved;
   const struct hom_net* net; /* warm_start = 1: a network from hom_net_load            */
 } hom_opts;
@@ -516,6 +520,10 @@ hom_status hom_set_batch_cluster(hom_ctx* ctx, int32_t cluster, int32_t coop_min
  * drains its committed MMAs with the default bound, frees its tensor memory and returns, and
  * the call returns HOM_ERR_TIMEOUT. */
 hom_status hom_set_gemm_spin_limit(hom_ctx* ctx, int64_t polls);
+/* The learned start of hom_bounds_batched runs the network on chunks of at most `cells`
+ * cells (0 restores the default: as many as fit 512 MiB of activations). Changes the
+ * workspace hom_batched_workspace_size reports; results do not depend on it. */
+hom_status hom_set_net_chunk(hom_ctx* ctx, int32_t cells);
 /* Measured FMA rate of this GPU (no counterpart in the paper; a measurement aid):
  * precision HOM_FP32 or HOM_FP64; runs 8 independent FMA chains per thread on 4 CTAs
  * of 512 threads per SM on `stream`, best of 5 timed launches after one warm-up, and

@@ -60,10 +60,11 @@ class Bounds:
                           None if x0 is None else x0.data_ptr(), None if fields is None else fields.data_ptr())
 
     def batched(self, problems, precision=HOM_MIXED, tol=1e-4, max_iter=10000, graph=0, autotune=0,
-                stream=None, x0=None, fields=None):
+                stream=None, x0=None, fields=None, net=None):
         """hom_bounds_batched on a list of 2D problems (one persistent launch). x0 / fields:
-        optional device tensors [n, 2, 2, 2, N, (N+1)//2] complex (starting / final fields)."""
-        opts = make_opts(precision, tol, max_iter, 8, 3, graph, autotune)
+        optional device tensors [n, 2, 2, 2, N, (N+1)//2] complex (starting / final fields);
+        net: a network handle (hom_net_load) for the learned start of every cell."""
+        opts = make_opts(precision, tol, max_iter, 8, 3, graph, autotune, net=net)
         nbytes = hom_batched_workspace_size(self.ctx, problems, opts)
         ws = self.workspace(nbytes)
         s = stream if stream is not None else self.torch.cuda.current_stream(self.device).cuda_stream

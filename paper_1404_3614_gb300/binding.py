@@ -120,6 +120,7 @@ def _load():
         "hom_kernel_timing": (i32, [vp, P(i64), dp]),
         "hom_peak_probe": (i32, [vp, i32, vp, dp]),
         "hom_set_gemm_spin_limit": (i32, [vp, i64]),
+        "hom_set_net_chunk": (i32, [vp, i32]),
         "hom_energy_bounds": (i32, [vp, P(hom_problem), P(hom_opts), vp, sz, vp, dp, dp, dp, P(hom_report)]),
         "hom_net_save": (i32, [vp, P(hom_net_config), vp, C.c_char_p, vp]),
         "hom_net_load": (i32, [vp, C.c_char_p, P(vp)]),
@@ -451,6 +452,11 @@ def hom_set_gemm_spin_limit(ctx, polls):
     """Test aid: the GEMMs of this context poll their completion barrier at most `polls`
     times (0: default)."""
     return check(ctx, lib.hom_set_gemm_spin_limit(ctx, int(polls)))
+
+
+def hom_set_net_chunk(ctx, cells):
+    """Cells per network forward in the learned start of a batch (0: as many as fit 512 MiB)."""
+    return check(ctx, lib.hom_set_net_chunk(ctx, int(cells)))
 
 
 def hom_peak_probe(ctx, precision, stream=0):

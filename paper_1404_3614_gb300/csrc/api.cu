@@ -79,6 +79,7 @@ struct hom_ctx {
   // tensor-core GEMMs: this context's timeout flag and the test limit on barrier polls
   int gemm_slot = 0;
   long long gemm_spin = 0;
+  int net_chunk = 0;        // cells per network forward of a batch's learned start (0: by bytes)
   // learned warm start: the network parameters already uploaded to this workspace offset
   unsigned long long net_params_id = 0;
   const void* net_params_at = nullptr;
@@ -1540,16 +1541,25 @@ static hom_status features_impl(hom_ctx* ctx, int32_t n, const hom_problem* prob
                                 size_t ws_bytes, cudaStream_t st);
 
 // Workspace region of the learned start, after the solver's own layout: the network
-// parameters, the features and the prediction on the N grid, the half-spectrum start
-// fields [side][rhs][comp][(z)][y][kx] (FP64), the feature staging and the network's own
-// workspace (DFT bases and activations for one cell).
+// parameters, the features of every cell and the prediction of one chunk of cells on the N
+// grid, the half-spectrum start fields [cell][side][rhs][comp][(z)][y][kx], the feature
+// staging and the network's own workspace (DFT bases and activations for one chunk).
 struct LearnedPlan {
   NetConfig c{};
   long long n_params = 0;
+  int n = 1, chunk = 1;   // cells, cells per network forward
+  int x0_elem = 16;       // bytes per complex entry of the start fields
   size_t params = 0, feat = 0, pred = 0, x0 = 0, stage = 0, stage_bytes = 0, netws = 0, net_bytes = 0, end = 0;
 };
 
-static hom_status plan_learned(hom_ctx* ctx, const Geometry& g, const hom_opts* o, size_t base, LearnedPlan& lp) {
+// Network activations of one forward call are bounded by this many bytes: a batch of
+// cells is run through the network in chunks of as many cells as fit.
+constexpr size_t kNetChunkBytes = size_t(512) << 20;
+
+// n cells sharing the geometry g's grid (the caller checks that), n_incl inclusions in all,
+// start fields of x0_elem bytes per complex entry.
+static hom_status plan_learned(hom_ctx* ctx, const Geometry& g, const hom_opts* o, size_t base, LearnedPlan& lp,
+                               int n = 1, size_t n_incl = 0, int x0_elem = 16) {
   if (o->warm_start != 0 && o->warm_start != 1) return fail(ctx, HOM_ERR_INVALID_ARG, "warm_start must be 0 or 1");
   if (o->warm_start == 0) return HOM_OK;
   if (!o->net) return fail(ctx, HOM_ERR_INVALID_ARG, "warm_start = 1 needs a network (hom_net_load)");
@@ -1566,6 +1576,14 @@ static hom_status plan_learned(hom_ctx* ctx, const Geometry& g, const hom_opts* 
   if ((long long)o->net->params.size() != lp.n_params)
     return fail(ctx, HOM_ERR_INVALID_ARG, "network parameter count does not match its config");
   const long long pts = (long long)g.N[0] * g.N[1] * g.N[2];
+  lp.n = n;
+  lp.x0_elem = x0_elem;
+  lp.chunk = 1;
+  if (ctx->net_chunk > 0) lp.chunk = std::min(n, ctx->net_chunk);
+  else
+    while (lp.chunk < n &&
+           net_ws_bytes(lp.c, lp.chunk + 1) + (size_t)(lp.chunk + 1) * pts * lp.c.cout * 4 <= kNetChunkBytes)
+      ++lp.chunk;
   size_t off = align256(base);
   auto take = [&](size_t bytes) {
     const size_t at = off;
@@ -1573,19 +1591,20 @@ static hom_status plan_learned(hom_ctx* ctx, const Geometry& g, const hom_opts* 
     return at;
   };
   lp.params = take((size_t)lp.n_params * 4);
-  lp.feat = take((size_t)pts * 4);
-  lp.pred = take((size_t)pts * lp.c.cout * 4);
-  lp.x0 = take((size_t)2 * g.d * g.d * g.field * 16);
-  lp.stage_bytes = features_stage_bytes(1, g.incl.size());
+  lp.feat = take((size_t)n * pts * 4);
+  lp.pred = take((size_t)lp.chunk * pts * lp.c.cout * 4);
+  lp.x0 = take((size_t)n * 2 * g.d * g.d * g.field * x0_elem);
+  lp.stage_bytes = features_stage_bytes(n, n == 1 ? g.incl.size() : n_incl);
   lp.stage = take(lp.stage_bytes);
-  lp.net_bytes = net_ws_bytes(lp.c, 1);
+  lp.net_bytes = net_ws_bytes(lp.c, lp.chunk);
   lp.netws = take(lp.net_bytes);
   lp.end = off;
   return HOM_OK;
 }
 
-// The learned start of one cell into lp.x0: features, the network on the cell's grid,
-// half spectra of its outputs (FP64). The solver projects and scales them before CG.
+// The learned start of lp.n cells into lp.x0 ([cell][side][rhs][comp] half spectra, FP64
+// when lp.x0_elem is 16, else FP32): features, the network on the cells' grid in chunks of
+// lp.chunk cells, half spectra of its outputs. The solver projects and scales them before CG.
 static hom_status learned_start(hom_ctx* ctx, const hom_problem* prob, const hom_opts* o, const LearnedPlan& lp,
                                 unsigned char* ws, cudaStream_t st) {
   float* params = reinterpret_cast<float*>(ws + lp.params);
@@ -1599,13 +1618,19 @@ static hom_status learned_start(hom_ctx* ctx, const hom_problem* prob, const hom
   }
   float* feat = reinterpret_cast<float*>(ws + lp.feat);
   float* pred = reinterpret_cast<float*>(ws + lp.pred);
-  CKS(features_impl(ctx, 1, prob, feat, ws + lp.stage, lp.stage_bytes, st));
+  CKS(features_impl(ctx, lp.n, prob, feat, ws + lp.stage, lp.stage_bytes, st));
   float *bases, *rest;
-  CKS(net_prepare(ctx, lp.c, 1, ws + lp.netws, lp.net_bytes, st, &bases, &rest));
+  CKS(net_prepare(ctx, lp.c, lp.chunk, ws + lp.netws, lp.net_bytes, st, &bases, &rest));
+  const long long pts = (long long)lp.c.N * lp.c.N * (lp.c.d == 3 ? lp.c.N : 1);
+  const long long half = (long long)(lp.c.N + 1) / 2 * lp.c.N * (lp.c.d == 3 ? lp.c.N : 1);
   CKS(gemm_begin(ctx, st));
-  KL(net_forward(lp.c, params, bases, 1, feat, pred, rest, 0, st));
+  for (int c0 = 0; c0 < lp.n; c0 += lp.chunk) {
+    const int nb = std::min(lp.chunk, lp.n - c0);
+    KL(net_forward(lp.c, params, bases, nb, feat + (size_t)c0 * pts, pred, rest, 0, st));
+    KL(grid_to_half(lp.c.d, lp.c.N, nb, lp.c.cout, pred, ws + lp.x0 + (size_t)c0 * lp.c.cout * half * lp.x0_elem,
+                    lp.x0_elem == 16 ? 1 : 0, st));
+  }
   CKS(gemm_end(ctx, st));
-  KL(grid_to_half(lp.c.d, lp.c.N, 1, lp.c.cout, pred, ws + lp.x0, 1, st));
   return HOM_OK;
 }
 
@@ -1814,12 +1839,32 @@ hom_status hom_energy_bounds(hom_ctx* ctx, const hom_problem* prob, const hom_op
   return s;
 }
 
+// The learned start of a batch, after the batch's own layout: every cell on one square grid,
+// start fields in the inner precision (the layout of hom_batch_io.d_x0).
+static hom_status plan_learned_batch(hom_ctx* ctx, int n, const hom_problem* probs, const hom_opts* o,
+                                     const BatchPlan& bp, LearnedPlan& lp) {
+  if (o->warm_start != 1) return plan_learned(ctx, Geometry{}, o, bp.total, lp);
+  Geometry g0;
+  CKS(build_geometry(ctx, &probs[0], g0, true));
+  size_t n_incl = 0;
+  for (int i = 0; i < n; ++i) {
+    Geometry g;
+    CKS(build_geometry(ctx, &probs[i], g, true));
+    if (g.N[0] != g0.N[0] || g.N[1] != g0.N[1])
+      return fail(ctx, HOM_ERR_INVALID_ARG, "the learned start of a batch needs one grid N for every cell");
+    n_incl += g.incl.size();
+  }
+  return plan_learned(ctx, g0, o, bp.total, lp, n, n_incl, o->precision == HOM_MIXED ? 8 : 16);
+}
+
 hom_status hom_batched_workspace_size(hom_ctx* ctx, int32_t n, const hom_problem* probs, const hom_opts* opts,
                                       size_t* bytes) {
   if (!ctx || !opts || !bytes) return fail(ctx, HOM_ERR_INVALID_ARG, "NULL argument");
   BatchPlan bp;
   CKS(build_batch(ctx, n, probs, opts, bp));
-  *bytes = bp.total;
+  LearnedPlan lp;
+  CKS(plan_learned_batch(ctx, n, probs, opts, bp, lp));
+  *bytes = opts->warm_start == 1 ? lp.end : bp.total;
   return HOM_OK;
 }
 
@@ -1835,12 +1880,23 @@ hom_status hom_bounds_batched(hom_ctx* ctx, int32_t n, const hom_problem* probs,
     return fail(ctx, HOM_ERR_INVALID_ARG, "precision must be HOM_FP64 or HOM_MIXED");
   BatchPlan bp;
   CKS(build_batch(ctx, n, probs, opts, bp));
-  if (!d_ws || ws_bytes < bp.total) return fail(ctx, HOM_ERR_WORKSPACE, "workspace too small");
+  LearnedPlan lp;
+  CKS(plan_learned_batch(ctx, n, probs, opts, bp, lp));
+  const bool learned = opts->warm_start == 1;
+  if (learned && io && io->d_x0) return fail(ctx, HOM_ERR_INVALID_ARG, "give either starting fields or warm_start");
+  if (!d_ws || ws_bytes < (learned ? lp.end : bp.total)) return fail(ctx, HOM_ERR_WORKSPACE, "workspace too small");
   ctx->tables_key.clear();
   ctx->net_bases_ws = nullptr;
   if (reinterpret_cast<uintptr_t>(d_ws) % 256) return fail(ctx, HOM_ERR_INVALID_ARG, "workspace must be 256-byte aligned");
   unsigned char* base = static_cast<unsigned char*>(d_ws);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
+  hom_batch_io io_learned{nullptr, nullptr};
+  if (learned) {   // the network's start of every cell, in the layout of hom_batch_io.d_x0
+    CKS(learned_start(ctx, probs, opts, lp, base, st));
+    io_learned.d_x0 = base + lp.x0;
+    io_learned.d_fields = io ? io->d_fields : nullptr;
+    io = &io_learned;
+  }
   const bool f32 = opts->precision == HOM_MIXED;
   const int nt = (int)bp.tasks.size();
   const bool has_io = io && (io->d_x0 || io->d_fields);
@@ -2427,6 +2483,12 @@ static hom_status gemm_end(hom_ctx* ctx, cudaStream_t st) {
   CK(gemm_timeout_read(ctx->gemm_slot, flag, st));
   CK(cudaStreamSynchronize(st));
   if (*flag) return fail(ctx, HOM_ERR_TIMEOUT, "tensor-core GEMM completion wait timed out");
+  return HOM_OK;
+}
+
+hom_status hom_set_net_chunk(hom_ctx* ctx, int32_t cells) {
+  if (!ctx || cells < 0) return fail(ctx, HOM_ERR_INVALID_ARG, "cells must be >= 0");
+  ctx->net_chunk = cells;
   return HOM_OK;
 }
 

@@ -364,6 +364,72 @@ def test_learned_start_inside_hom_bounds(hb, tmp_path, d, N, train_N):
         solver.close()
 
 
+def _python_batch_start(hb, ctx, cfg, params, probs, prec, chunk):
+    """The learned start of a batch chained call by call, the network run on chunks of
+    `chunk` cells: what hom_bounds_batched does itself with warm_start = 1."""
+    n, N = len(probs), int(probs[0].N[0])
+    feat = torch.empty((n, N, N, 1), dtype=torch.float32, device="cuda")
+    ws = torch.empty(1 << 20, dtype=torch.uint8, device="cuda")
+    hb.binding.hom_net_features(ctx, probs, feat.data_ptr(), ws.data_ptr(), ws.numel())
+    c = hb.binding.net_config(N, 1, cfg.width, cfg.modes, cfg.layers, cfg.proj, cfg.cout, 2)
+    _, nws = hb.binding.hom_net_sizes(ctx, c, chunk)
+    nw = torch.empty(nws, dtype=torch.uint8, device="cuda")
+    pred = torch.empty((chunk, N, N, cfg.cout), dtype=torch.float32, device="cuda")
+    f32 = prec == hb.HOM_MIXED
+    half = torch.empty((n, 2, 2, 2, N, (N + 1) // 2), dtype=torch.complex64 if f32 else torch.complex128,
+                       device="cuda")
+    for c0 in range(0, n, chunk):
+        nb = min(chunk, n - c0)
+        fc = feat[c0:c0 + nb].contiguous()
+        hb.binding.hom_net_forward(ctx, c, params.data_ptr(), nb, fc.data_ptr(), pred.data_ptr(), nw.data_ptr(), nws)
+        hb.binding.hom_grid_to_half(ctx, 2, N, nb, cfg.cout, pred.data_ptr(), half[c0:c0 + nb].data_ptr(),
+                                    hb.HOM_FP32 if f32 else hb.HOM_FP64)
+    return half
+
+
+def test_learned_start_inside_hom_bounds_batched(hb, tmp_path):
+    """hom_bounds_batched with warm_start = 1 gives the same bounds (1e-12) and iterations as
+    the same start chained call by call and passed as starting fields, in both precisions,
+    with the network run on the whole batch or on chunks of 3 cells (a ragged last chunk);
+    cells of different N in one batch, or starting fields together with the network, are
+    refused."""
+    solver = hb.Bounds(0)
+    ctx = solver.ctx
+    net = None
+    try:
+        cfg = hb.binding.net_config(15, 1, 8, 3, 2, 24, 8, 2)
+        npar, _ = hb.binding.hom_net_sizes(ctx, cfg, 1)
+        params = torch.empty(npar, dtype=torch.float32, device="cuda")
+        hb.binding.hom_net_init(ctx, cfg, 13, params.data_ptr())
+        path = str(tmp_path / "net.bin")
+        hb.binding.hom_net_save(ctx, cfg, params.data_ptr(), path)
+        net = hb.binding.hom_net_load(ctx, path)
+        probs = [ms.random_rectangles_2d(40 + i, N=23) for i in range(7)]
+        for chunk in (0, 3):
+            hb.binding.hom_set_net_chunk(ctx, chunk)
+            for prec, tol in ((hb.HOM_FP64, 1e-8), (hb.HOM_MIXED, 1e-5)):
+                x0 = _python_batch_start(hb, ctx, cfg, params, probs, prec, chunk or len(probs))
+                ref = solver.batched(probs, precision=prec, tol=tol, x0=x0)
+                out = solver.batched(probs, precision=prec, tol=tol, net=net)
+                for key in ("upper", "lower"):
+                    assert np.abs(out[key] - ref[key]).max() <= 1e-12 * np.abs(ref[key]).max(), (chunk, prec, key)
+                assert np.array_equal(out["iters"], ref["iters"]), (chunk, prec)
+                zero = solver.batched(probs, precision=prec, tol=tol)
+                assert not np.array_equal(out["iters"], zero["iters"])
+        hb.binding.hom_set_net_chunk(ctx, 0)
+        mixed = probs[:2] + [ms.random_rectangles_2d(3, N=25)]
+        with pytest.raises(hb.HombError) as e:
+            solver.batched(mixed, precision=hb.HOM_FP64, net=net)
+        assert e.value.status == hb.binding.HOM_ERR_INVALID_ARG
+        x0 = torch.zeros((7, 2, 2, 2, 23, 12), dtype=torch.complex128, device="cuda")
+        with pytest.raises(hb.HombError):
+            solver.batched(probs, precision=hb.HOM_FP64, x0=x0, net=net)
+    finally:
+        if net:
+            hb.binding.hom_net_free(net)
+        solver.close()
+
+
 def test_network_file_is_checked(hb, tmp_path):
     ctx = hb.hom_create(0)
     try:
