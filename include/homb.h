@@ -491,6 +491,13 @@ hom_status hom_set_pass_chunks(hom_ctx* ctx, int32_t ypass_pencils, int32_t xpas
  * rounding. A staged copy that does not complete within a bounded wait makes hom_bounds
  * return HOM_ERR_TIMEOUT. Applies to later calls on this context. */
 hom_status hom_set_slab_pass(hom_ctx* ctx, int32_t enable);
+/* The first and last passes of the FP32 3D operator at double-grid length 225 along z
+ * (the zero-padded inverse z transform with the CG prologue, and the truncating forward z
+ * transform with Gamma and the CG partial sums) run as persistent CTAs, two per SM, that
+ * stage the input of their next chunk of pencils with asynchronous copies while they
+ * transform the current one (enable = 1, the default). enable = 0 runs the chunked passes
+ * (one CTA per chunk); the results agree to rounding. Applies to later calls. */
+hom_status hom_set_pipe_passes(hom_ctx* ctx, int32_t enable);
 
 /* Threads per CTA of the persistent batched kernel: 256 (two CTAs per SM), 512 or 1024
  * (one CTA per SM: more threads per cell, fewer cells at a time), or 0 (default: the

@@ -121,6 +121,7 @@ def _load():
         "hom_peak_probe": (i32, [vp, i32, vp, dp]),
         "hom_set_gemm_spin_limit": (i32, [vp, i64]),
         "hom_set_net_chunk": (i32, [vp, i32]),
+        "hom_set_pipe_passes": (i32, [vp, i32]),
         "hom_energy_bounds": (i32, [vp, P(hom_problem), P(hom_opts), vp, sz, vp, dp, dp, dp, P(hom_report)]),
         "hom_net_save": (i32, [vp, P(hom_net_config), vp, C.c_char_p, vp]),
         "hom_net_load": (i32, [vp, C.c_char_p, P(vp)]),
@@ -452,6 +453,11 @@ def hom_set_gemm_spin_limit(ctx, polls):
     """Test aid: the GEMMs of this context poll their completion barrier at most `polls`
     times (0: default)."""
     return check(ctx, lib.hom_set_gemm_spin_limit(ctx, int(polls)))
+
+
+def hom_set_pipe_passes(ctx, enable):
+    """Persistent pipelined FP32 z passes at length 225 (1, the default) or the chunked passes (0)."""
+    return check(ctx, lib.hom_set_pipe_passes(ctx, int(enable)))
 
 
 def hom_set_net_chunk(ctx, cells):

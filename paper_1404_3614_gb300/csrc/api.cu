@@ -66,6 +66,8 @@ struct hom_ctx {
   std::vector<CgGraph> cg_graphs;
   bool graphs_off = false;
   bool slab_on = true;   // fused y-x-y slab pass where it applies
+  bool zpipe_on = true;  // persistent pipelined FP32 z passes where they apply
+  int sms = 0;           // SMs of the device (set at creation)
   int slab_warps = 0;     // warps per slab CTA chosen by the caller (0: automatic)
   int ypass_xc = 0;       // pencils per CTA of the operator's y passes (0: automatic)
   int xpass_yb = 0;       // planes per CTA of the operator's row pass (0: automatic)
@@ -779,6 +781,8 @@ struct Runner {
       z.Pin = Nz; z.Pout = Mz; z.Nlog = Nz; z.dir = +1;
       z.slabs_per_rhs = C; z.slabs_per_comp = 1; z.C = C; z.prologue = prologue;
       z.W = W(2); z.plan = g.plan[2]; z.cg = cg;
+      if (sizeof(T) == 4 && ctx->zpipe_on)
+        z.pgrid = zpipe_pad_grid(Mz, z.Pin, z.Pout, z.Nlog, z.dir, z.X, z.nslab, ctx->sms);
       if (z.XC < 1) return fail(ctx, HOM_ERR_INVALID_ARG, "grid too large for the shared-memory FFT");
       KL(launch_pencil<T>(z, st));
       ycur = T1;
@@ -847,13 +851,24 @@ struct Runner {
       f.W = W(g.d == 3 ? 2 : 1); f.plan = g.plan[g.d == 3 ? 2 : 1];
       f.cg = cg; f.partial_ld = L.maxblk; f.bsub = bsub;
       f.partial = ((cg && p_aux) || bsub) ? at<double>(L.partial) : nullptr;
+      if (sizeof(T) == 4 && !bsub) f.pgrid = final_pipe_grid();
       if (f.XC < 1) return fail(ctx, HOM_ERR_INVALID_ARG, "grid too large for the shared-memory FFT");
       KL(launch_final<T>(f, st));
     }
     return HOM_OK;
   }
 
+  // CTAs of the persistent FP32 last pass (0: the chunked pass runs), at most one partial
+  // sum slot per CTA and right-hand side
+  int final_pipe_grid() const {
+    if (!ctx->zpipe_on) return 0;
+    const int pg = zpipe_final_grid(g.d == 3 ? g.M[2] : g.M[1], g.d == 3 ? g.N[2] : g.N[1], g.d, g.d,
+                                    g.d == 3 ? g.N[1] * g.Nh : g.Nh, R, ctx->sms);
+    return std::min(pg, L.maxblk);
+  }
+
   int final_blocks(size_t elem) const {
+    if (elem == 8 && final_pipe_grid() > 0) return final_pipe_grid();
     const int X = g.d == 3 ? g.N[1] * g.Nh : g.Nh;
     const int xc = final_xc_elem(g, elem);
     return (X + xc - 1) / xc;
@@ -925,9 +940,10 @@ struct Runner {
       return HOM_OK;
     }
     std::vector<unsigned char> key = ctx->tables_key;
-    const long long extra[10] = {(long long)side, (long long)sizeof(T), K, (long long)(uintptr_t)coefT,
+    const long long extra[13] = {(long long)side, (long long)sizeof(T), K, (long long)(uintptr_t)coefT,
                                  (long long)(uintptr_t)cg, (long long)L.total, R, nfin, ctx->ypass_xc,
-                                 ctx->xpass_yb};
+                                 ctx->xpass_yb, (long long)ctx->slab_on, ctx->slab_warps,
+                                 (long long)ctx->zpipe_on};
     const unsigned char* eb = reinterpret_cast<const unsigned char*>(extra);
     key.insert(key.end(), eb, eb + sizeof extra);
     key.insert(key.end(), ctx->prof_family.begin(), ctx->prof_family.end());
@@ -1440,6 +1456,7 @@ hom_status hom_create(hom_ctx** out, int device) {
   ctx->device = device;
   ctx->gemm_slot = created.fetch_add(1) % kGemmFlagSlots;
   cudaError_t e = cudaSetDevice(device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->sms, cudaDevAttrMultiProcessorCount, device);
   if (e == cudaSuccess) e = cudaMallocHost((void**)&ctx->host_cg, sizeof(CgScalars));
   if (e == cudaSuccess) e = cudaMallocHost((void**)&ctx->host_e, 64 * sizeof(double));
   if (e != cudaSuccess) {
@@ -2356,6 +2373,13 @@ hom_status hom_set_slab_pass(hom_ctx* ctx, int32_t enable) {
     return fail(ctx, HOM_ERR_INVALID_ARG, "slab pass: 0 (off), 1 (automatic) or 4..20 warps in steps of 4");
   ctx->slab_on = enable != 0;
   ctx->slab_warps = enable > 1 ? enable : 0;
+  return HOM_OK;
+}
+
+hom_status hom_set_pipe_passes(hom_ctx* ctx, int32_t enable) {
+  if (!ctx) return HOM_ERR_INVALID_ARG;
+  if (enable != 0 && enable != 1) return fail(ctx, HOM_ERR_INVALID_ARG, "pipelined passes: 0 (off) or 1 (on)");
+  ctx->zpipe_on = enable != 0;
   return HOM_OK;
 }
 

@@ -25,6 +25,7 @@ struct PencilArgs {
   const void* W;
   FftPlan plan;
   CgScalars* cg;   // may be null: no skipping
+  int pgrid;       // > 0: the persistent pipelined z pass with this many CTAs (zpipe_pad_grid)
   FastDiv fd_XC;   // divides by XC (set by the launcher)
 };
 
@@ -46,6 +47,8 @@ struct FinalArgs {
   double* partial;               // [rhs][gridDim.x]
   int partial_ld;
   const void* bsub;              // residual mode: out = bsub - Gamma(...), partial |out|^2
+  int pgrid;                     // > 0: the persistent pipelined z pass with this many CTAs
+                                 // (zpipe_final_grid; partial sums [rhs][pgrid])
   FastDiv fd_XC, fd_per, fd_Nh;  // set by the launcher
 };
 
@@ -180,6 +183,11 @@ template <typename T> cudaError_t launch_pencil(const PencilArgs& a, cudaStream_
 template <typename T> cudaError_t launch_final(const FinalArgs& a, cudaStream_t s);
 template <typename T> cudaError_t launch_xpass(const XArgs& a, int grid_y, cudaStream_t s);
 template <typename T> int pencil_xc(int M, int X, int C);   // chunk that fits shared memory
+// Persistent pipelined z passes of the FP32 3D operator at M = 225 (zpipe.cuh): their CTA
+// counts on a device with `sms` SMs, 0 where they do not apply (another length, a transform
+// that is not the zero-padded inverse / truncating forward one of the operator)
+int zpipe_pad_grid(int M, int Pin, int Pout, int Nlog, int dir, int X, int nslab, int sms);
+int zpipe_final_grid(int M, int Nlog, int d, int C, int X, int nrhs, int sms);
 template <typename T> int xpass_yb(int M, int rows_per_plane, int planes);
 // fused y-x-y slab pass; cudaErrorNotSupported when the length or size does not apply
 template <typename T> cudaError_t launch_slab(const SlabArgs& a, cudaStream_t s);

@@ -63,6 +63,20 @@ __device__ __forceinline__ void stage_twiddles_kl(cpx<T>* Wt, const void* W) {
   }
 }
 
+// Known zeros of the warp FFTs' transforms of length M = R*R. A zero-padded inverse transform has
+// at most N <= (M+1)/2 nonzero inputs: at positions p <= (M-3)/4 and p >= (3M+3)/4 (the y rows
+// of the padded slab, the Hermitian x extension, Nh <= (M+3)/4); a truncating forward one
+// keeps only the outputs at those positions. In the lane layout p = l + R n of the register
+// FFTs, the rows n in [lo, hi] hold only such positions for every lane l: they are never read
+// as inputs (inverse) and never computed or stored as outputs (forward).
+template <int R> struct ZeroBand {
+  static constexpr int M = R * R;
+  static constexpr int lo = ((M + 3) / 4 + R - 1) / R;
+  static constexpr int hi = ((3 * M - 3) / 4 - (R - 1)) / R;
+  static constexpr bool in(int n) { return n >= lo && n <= hi; }
+};
+static_assert(ZeroBand<15>::lo == 4 && ZeroBand<15>::hi == 10, "zero band of the length-225 transforms");
+
 // G contiguous pencils (stride R*R) in place, R lanes per pencil; ends with __syncthreads.
 // mode 1: zero-padded inverse transforms (at most (M+1)/2 nonzero inputs: the zero band of
 // the lane layout is not read); mode 2: truncating forward transforms (at most (M+1)/2
@@ -348,6 +362,10 @@ __global__ void __launch_bounds__(kPassThreads) k_final(FinalArgs a) {
     if (threadIdx.x == 0) a.partial[rhs * a.partial_ld + blockIdx.x] = sum;
   }
 }
+
+}  // namespace homb
+#include "zpipe.cuh"
+namespace homb {
 
 // ---------------------------------------------------------------------------------
 // row pass along x: Hermitian-half rows, two real rows packed per complex FFT
@@ -651,9 +669,30 @@ cudaError_t launch_fft_batch_m(const void* in, void* out, int M, int howmany, in
 #define HOMB_CASE_XPASS(m) case m: return launch_xpass_m<T, m>(a, grid_y, s);
 #define HOMB_CASE_FFT(m) case m: return launch_fft_batch_m<T, m>(in, out, M, howmany, dir, W, plan, G, s);
 
+template <typename T> cudaError_t launch_zpad_pipe(const PencilArgs& a, cudaStream_t s) {
+  const size_t smem = zp_pad_smem<T, 15>(a.prologue == 1 ? 2 : 1);
+  static std::atomic<int> cache[kAttrDevices] = {};
+  cudaError_t e = smem_attr(k_zpad_pipe<T, 15>, zp_pad_smem<T, 15>(2), cache);
+  if (e != cudaSuccess) return e;
+  k_zpad_pipe<T, 15><<<a.pgrid, kZpThreads, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <typename T> cudaError_t launch_final_pipe(const FinalArgs& a, cudaStream_t s) {
+  constexpr size_t smem = zp_final_smem<T, 15>();
+  static std::atomic<int> cache[kAttrDevices] = {};
+  cudaError_t e = smem_attr(k_final_pipe<T, 15>, smem, cache);
+  if (e != cudaSuccess) return e;
+  k_final_pipe<T, 15><<<a.pgrid, kZpThreads, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
 template <typename T> cudaError_t launch_pencil(const PencilArgs& a0, cudaStream_t s) {
   PencilArgs a = a0;
   a.fd_XC = FastDiv((uint32_t)a.XC);
+  if constexpr (sizeof(T) == 4) {
+    if (a.pgrid > 0) return launch_zpad_pipe<T>(a, s);
+  }
   switch (a.plan.M) {
     HOMB_FOR_EACH_M(HOMB_CASE_PENCIL)
     default: return launch_pencil_m<T, 0>(a, s);
@@ -665,6 +704,9 @@ template <typename T> cudaError_t launch_final(const FinalArgs& a0, cudaStream_t
   a.fd_XC = FastDiv((uint32_t)a.XC);
   a.fd_per = FastDiv((uint32_t)(a.M * a.XC));
   a.fd_Nh = FastDiv((uint32_t)a.Nh);
+  if constexpr (sizeof(T) == 4) {
+    if (a.pgrid > 0) return launch_final_pipe<T>(a, s);
+  }
   switch (a.M) {
     HOMB_FOR_EACH_M(HOMB_CASE_FINAL)
     default: return launch_final_m<T, 0>(a, s);

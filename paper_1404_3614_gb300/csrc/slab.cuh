@@ -37,19 +37,6 @@ inline size_t slab_smem_bytes(int M, int R, int Nh, int warps, size_t elem) {
   return slab_scratch_offset(M, Nh, elem) + elem * scratch;
 }
 
-// Known zeros of the slab's transforms of length M = R*R. A zero-padded inverse transform has
-// at most N <= (M+1)/2 nonzero inputs: at positions p <= (M-3)/4 and p >= (3M+3)/4 (the y rows
-// of the padded slab, the Hermitian x extension, Nh <= (M+3)/4); a truncating forward one
-// keeps only the outputs at those positions. In the lane layout p = l + R n of the register
-// FFTs, the rows n in [lo, hi] hold only such positions for every lane l: they are never read
-// as inputs (inverse) and never computed or stored as outputs (forward).
-template <int R> struct ZeroBand {
-  static constexpr int M = R * R;
-  static constexpr int lo = ((M + 3) / 4 + R - 1) / R;
-  static constexpr int hi = ((3 * M - 3) / 4 - (R - 1)) / R;
-  static constexpr bool in(int n) { return n >= lo && n <= hi; }
-};
-static_assert(ZeroBand<15>::lo == 4 && ZeroBand<15>::hi == 10, "zero band of the length-225 transforms");
 
 // DFT3 of (a0, a1, a2) with compile-time zero inputs (Z0, Z1, Z2), same convention as dft3:
 // y_k = sum_n a_n w^(n k), w = exp(dir 2 pi i / 3). Inputs marked zero are not read.

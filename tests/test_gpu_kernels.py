@@ -60,6 +60,11 @@ PROBLEMS = {
     "spheres3d_N5_M9": lambda: ms.random_spheres_3d(3, N=5, n_balls=3, phi=0.2, contrast=20.0),
     "cube3d_N13_M25": lambda: ms.cube_inclusion_3d(N=13),
     "spheres3d_N41_M81": lambda: ms.random_spheres_3d(4, N=41, n_balls=6, phi=0.25, contrast=100.0),
+    # double-grid length 225 along z only: the persistent pipelined z passes (FP32) with ragged
+    # last chunks (55 positions per z plane), the separate y and x passes
+    "balls3d_N9x11x113_Mz225": lambda: ms.make_problem(3, (9, 11, 113), (1.0, 0.8, 1.2), 1.0,
+                                                       [ms.ball((0.1, 0.0, 0.05), 0.3, 30.0, 3),
+                                                        ms.box((-0.3, 0.25, -0.4), (0.2, 0.2, 0.3), 0.1, 3)]),
 }
 
 
@@ -242,6 +247,51 @@ def test_slab_pass_matches_separate_passes(hb, ctx, N, prec):
                                                                      relerr(out[side, slab], out[side, 0]))
     finally:
         hb.hom_set_slab_pass(ctx, 1)
+
+
+@pytest.mark.parametrize("name", ["balls3d_N9x11x113_Mz225", "spheres3d_N113"])
+def test_pipe_passes_match_chunked_passes(hb, ctx, name):
+    """The persistent pipelined FP32 z passes (length 225) and the chunked passes compute the
+    same operator (2e-6 relative to the largest entry) on both sides, with and without Gamma;
+    through hom_bounds (mixed: the CG prologue p = r + beta p and the partial sums p.Cp) they
+    give the same bounds to the solver's tolerance."""
+    p = PROBLEMS[name]() if name in PROBLEMS else ms.random_spheres_3d(0, N=113)
+    d = 3
+    N = tuple(int(n) for n in p.N)
+    rng = np.random.default_rng([zlib.crc32(name.encode()), 3])
+    info = hb.hom_problem_info(ctx, p)
+    nws = hb.hom_step_workspace_size(ctx, p, d)
+    ws = torch.empty(nws, dtype=torch.uint8, device="cuda")
+    shape = (d, d, N[2], N[1], (N[0] + 1) // 2)
+    x = torch.from_numpy(rng.normal(size=shape) + 1j * rng.normal(size=shape)).to(torch.complex64).cuda()
+    try:
+        for side in (0, 1):
+            coef = torch.empty((info["ncomp"],) + tuple(info["M"][:d][::-1]), dtype=torch.float32, device="cuda")
+            hb.hom_coefficient(ctx, p, side, hb.HOM_FP32, coef.data_ptr(), ws.data_ptr(), nws)
+            for project in (0, 1):
+                out = {}
+                for pipe in (1, 0):
+                    hb.binding.hom_set_pipe_passes(ctx, pipe)
+                    y = torch.full_like(x, float("nan"))
+                    hb.hom_matvec(ctx, p, side, hb.HOM_FP32, project, d, coef.data_ptr(), x.data_ptr(),
+                                  y.data_ptr(), ws.data_ptr(), nws)
+                    torch.cuda.synchronize()
+                    out[pipe] = y.cpu().numpy()
+                assert np.isfinite(out[1]).all()
+                assert relerr(out[1], out[0]) < 2e-6, (name, side, project, relerr(out[1], out[0]))
+        if name in PROBLEMS:
+            solver = hb.Bounds(0)
+            try:
+                res = {}
+                for pipe in (1, 0):
+                    hb.binding.hom_set_pipe_passes(solver.ctx, pipe)
+                    res[pipe] = solver(p, precision=hb.HOM_MIXED, tol=1e-7)
+                for key in ("upper", "lower"):
+                    assert relerr(res[1][key], res[0][key]) < 1e-6, key
+            finally:
+                solver.close()
+    finally:
+        hb.binding.hom_set_pipe_passes(ctx, 1)
 
 
 @pytest.mark.parametrize("N,prec", [(41, "fp64"), (23, "fp64"), (41, "fp32")])
