@@ -498,6 +498,14 @@ hom_status hom_set_slab_pass(hom_ctx* ctx, int32_t enable);
  * transform the current one (enable = 1, the default). enable = 0 runs the chunked passes
  * (one CTA per chunk); the results agree to rounding. Applies to later calls. */
 hom_status hom_set_pipe_passes(hom_ctx* ctx, int32_t enable);
+/* Target of the FP32 inner solves of HOM_MIXED (no counterpart in the paper: a precision
+ * scheme of this library). An inner solve that starts from the FP64 residual r0 stops when its
+ * recursive residual is below max(tol/2, tol - c eps_32 |r0|) (and below 1e-5 |r0|, its FP32
+ * limit), eps_32 = 2^-24: c bounds how far the recursive residual may drift from the true one,
+ * which the FP64 check after the inner solve measures. A larger c costs inner iterations, a
+ * smaller one risks another FP64 refinement step; the bounds stay guaranteed either way.
+ * c >= 0; c = 0 restores the default, 100. Applies to later calls on this context. */
+hom_status hom_set_inner_drift(hom_ctx* ctx, double c);
 
 /* Threads per CTA of the persistent batched kernel: 256 (two CTAs per SM), 512 or 1024
  * (one CTA per SM: more threads per cell, fewer cells at a time), or 0 (default: the

@@ -122,6 +122,7 @@ def _load():
         "hom_set_gemm_spin_limit": (i32, [vp, i64]),
         "hom_set_net_chunk": (i32, [vp, i32]),
         "hom_set_pipe_passes": (i32, [vp, i32]),
+        "hom_set_inner_drift": (i32, [vp, C.c_double]),
         "hom_energy_bounds": (i32, [vp, P(hom_problem), P(hom_opts), vp, sz, vp, dp, dp, dp, P(hom_report)]),
         "hom_net_save": (i32, [vp, P(hom_net_config), vp, C.c_char_p, vp]),
         "hom_net_load": (i32, [vp, C.c_char_p, P(vp)]),
@@ -458,6 +459,11 @@ def hom_set_gemm_spin_limit(ctx, polls):
 def hom_set_pipe_passes(ctx, enable):
     """Persistent pipelined FP32 z passes at length 225 (1, the default) or the chunked passes (0)."""
     return check(ctx, lib.hom_set_pipe_passes(ctx, int(enable)))
+
+
+def hom_set_inner_drift(ctx, c):
+    """Drift coefficient c of the FP32 inner target of HOM_MIXED (0: the default)."""
+    return check(ctx, lib.hom_set_inner_drift(ctx, float(c)))
 
 
 def hom_set_net_chunk(ctx, cells):

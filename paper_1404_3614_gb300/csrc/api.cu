@@ -67,6 +67,7 @@ struct hom_ctx {
   bool graphs_off = false;
   bool slab_on = true;   // fused y-x-y slab pass where it applies
   bool zpipe_on = true;  // persistent pipelined FP32 z passes where they apply
+  double inner_drift = 0.0;   // drift coefficient of the FP32 inner target (0: default)
   int sms = 0;           // SMs of the device (set at creation)
   int slab_warps = 0;     // warps per slab CTA chosen by the caller (0: automatic)
   int ypass_xc = 0;       // pencils per CTA of the operator's y passes (0: automatic)
@@ -97,6 +98,7 @@ struct hom_net {
 
 namespace {
 
+constexpr double kInnerDrift = 100.0;   // default drift coefficient of the FP32 inner target
 constexpr int kVecBlocks = 304;   // 2 x 152 SMs for the elementwise CG kernels
 
 #define CK(expr)                                                                               \
@@ -1214,6 +1216,11 @@ hom_status Runner_solve_mixed(Runner& run, int side, const hom_opts& o, hom_repo
   const int maxit = o.max_iter > 0 ? o.max_iter : ((o.max_iter == 0 && warm && user_start) ? 0 : 10000);
   const int every = o.check_every > 0 ? o.check_every : 8;
   const double eta = 1e-5;
+  // The recursive FP32 residual of an inner solve (restarted from the FP64 residual) stays
+  // within a few eps_32 |r_k| per step of the true one (measured on the 16-ball cell at
+  // contrast 1000: equal to four digits); the inner solve aims at tol less c eps_32 |r0|
+  // (at least tol / 2), so that the FP64 check after it passes without another refinement step.
+  const double drift = (ctx->inner_drift > 0.0 ? ctx->inner_drift : kInnerDrift) * 5.9604644775390625e-8;
   int used = 0;
   int inner_iters[3] = {0, 0, 0};
   for (int outer_it = 0; outer_it < 30; ++outer_it) {
@@ -1222,11 +1229,14 @@ hom_status Runner_solve_mixed(Runner& run, int side, const hom_opts& o, hom_repo
     bool any = false;
     for (int r = 0; r < R; ++r) any = any || ctx->host_cg->active[r];
     if (!any || used >= maxit) break;
-    // inner FP32 CG on the current FP64 residual
+    // inner FP32 CG on the current FP64 residual, from zero (a restart: keeping the last
+    // search direction with the replaced residual made the recursive residual drift from the
+    // true one, and so cost another refinement step)
     KL(launch_demote(r64, run.at<float2>(L.r), R, g.d, g.field, g.Nh, outer, partial, kVecBlocks, st));
     CK(cudaMemsetAsync(base + L.x, 0, n * sizeof(float2), st));
     CK(cudaMemsetAsync(base + L.p, 0, n * sizeof(float2), st));
-    KL(launch_cg_init(inner, partial, kVecBlocks, kVecBlocks, R, 0.25 * tol * tol, eta * eta, 1, st));
+    KL(launch_cg_init(inner, partial, kVecBlocks, kVecBlocks, R, 0.25 * tol * tol, eta * eta, 1, st, tol * tol,
+                      drift));
     CK(d2h_copy(ctx, ctx->host_cg, inner, sizeof(CgScalars), st));
     CK(cudaStreamSynchronize(st));
     bool ia = false;
@@ -2373,6 +2383,13 @@ hom_status hom_set_slab_pass(hom_ctx* ctx, int32_t enable) {
     return fail(ctx, HOM_ERR_INVALID_ARG, "slab pass: 0 (off), 1 (automatic) or 4..20 warps in steps of 4");
   ctx->slab_on = enable != 0;
   ctx->slab_warps = enable > 1 ? enable : 0;
+  return HOM_OK;
+}
+
+hom_status hom_set_inner_drift(hom_ctx* ctx, double c) {
+  if (!ctx) return HOM_ERR_INVALID_ARG;
+  if (!(c >= 0.0) || !std::isfinite(c)) return fail(ctx, HOM_ERR_INVALID_ARG, "drift coefficient must be >= 0");
+  ctx->inner_drift = c;
   return HOM_OK;
 }
 

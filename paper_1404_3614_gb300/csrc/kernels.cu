@@ -185,15 +185,22 @@ __device__ double reduce_row(const double* v, int n, double* red) {
   return s;  // thread 0
 }
 
+// Absolute target of an inner solve that starts from |r0|^2 = s (see launch_cg_init)
+__device__ __forceinline__ double inner_target(double tol2_abs, double tol2_hi, double drift, double s) {
+  if (!(drift > 0.0) || !isfinite(s)) return tol2_abs;
+  const double t = sqrt(tol2_hi) - drift * sqrt(s);
+  return t > 0.0 ? fmax(tol2_abs, t * t) : tol2_abs;
+}
+
 __global__ void k_cg_init(CgScalars* cg, const double* partial, int ld, int nblk, int nrhs,
-                          double tol2_abs, double rel2, int guard) {
+                          double tol2_abs, double rel2, int guard, double tol2_hi, double drift) {
   __shared__ double red[32];
   for (int r = 0; r < 3; ++r) {
     double s = 0.0;
     if (r < nrhs) s = reduce_row(partial + (long long)r * ld, nblk, red);
     __syncthreads();
     if (threadIdx.x == 0) {
-      const double t2 = fmax(tol2_abs, rel2 * s);
+      const double t2 = fmax(inner_target(tol2_abs, tol2_hi, drift, s), rel2 * s);
       cg->tol2[r] = t2;
       cg->beta[r] = 0.0;
       cg->alpha[r] = 0.0;
@@ -777,8 +784,8 @@ cudaError_t launch_cg_update(void* x, void* r, const void* p, const void* q, int
 }
 
 cudaError_t launch_cg_init(CgScalars* cg, const double* partial, int ld, int nblk, int nrhs,
-                           double tol2_abs, double rel2, int guard, cudaStream_t s) {
-  k_cg_init<<<1, kThreads, 0, s>>>(cg, partial, ld, nblk, nrhs, tol2_abs, rel2, guard);
+                           double tol2_abs, double rel2, int guard, cudaStream_t s, double tol2_hi, double drift) {
+  k_cg_init<<<1, kThreads, 0, s>>>(cg, partial, ld, nblk, nrhs, tol2_abs, rel2, guard, tol2_hi, drift);
   return cudaGetLastError();
 }
 cudaError_t launch_outer_check(CgScalars* cg, const double* partial, int ld, int nblk, int nrhs,

@@ -207,8 +207,12 @@ cudaError_t launch_cg_update(void* x, void* r, const void* p, const void* q, int
                              long long field, int Nh, CgScalars* cg, double* partial, int nblk,
                              cudaStream_t s);
 // r.r from the partials; tol2[r] = max(tol2_abs, rel2 * r.r); guard as given.
+// With drift > 0 (an FP32 inner solve), the absolute target is raised from tol2_abs toward
+// tol2_hi: (sqrt(tol2_hi) - drift |r0|)^2 when that is larger, drift |r0| bounding how far the
+// recursive residual may end up from the true one.
 cudaError_t launch_cg_init(CgScalars* cg, const double* partial, int ld, int nblk, int nrhs,
-                           double tol2_abs, double rel2, int guard, cudaStream_t s);
+                           double tol2_abs, double rel2, int guard, cudaStream_t s, double tol2_hi = 0.0,
+                           double drift = 0.0);
 // outer refinement step: r.r_new from the partials; converged when <= tol2[r]; stalled
 // (status 1, stop) when r.r_new > shrink2 * r.r.
 cudaError_t launch_outer_check(CgScalars* cg, const double* partial, int ld, int nblk, int nrhs,

@@ -79,6 +79,28 @@ def test_mixed_precision_reaches_fp64_accuracy_on_the_cube_cell(hb, solver):
     check(out, gold, 1e-10)
 
 
+def test_inner_target_trades_iterations_not_accuracy(hb):
+    """The FP32 inner solves' target (hom_set_inner_drift) changes only how many iterations and
+    FP64 refinement steps a mixed solve takes: with the default and with the most cautious
+    target (tol / 2 always) the cube cell's bounds at tol 1e-8 stay within 1e-10 of the
+    oracle, and the cautious target takes at least as many inner iterations."""
+    gold = GOLD["cube3d_N41"]
+    s = hb.Bounds(0)
+    try:
+        with pytest.raises(hb.HombError):
+            hb.binding.hom_set_inner_drift(s.ctx, -1.0)
+        its = {}
+        for c in (0.0, 1e12):
+            hb.binding.hom_set_inner_drift(s.ctx, c)
+            out = s(ms.cube_inclusion_3d(), precision=hb.HOM_MIXED, tol=1e-8)
+            assert out["status"] == 0
+            check(out, gold, 1e-10)
+            its[c] = int(np.asarray(out["report"]["iters"]).sum())
+        assert its[1e12] >= its[0.0], its
+    finally:
+        s.close()
+
+
 @pytest.mark.parametrize("cluster", [0, 4])
 def test_benchmark_batch_large_cells_match_oracle(hb, solver, cluster):
     """Cells of the 256-cell batch with N = 113 (seeds 2, 6) and N = 203 (seeds 5, 10),
