@@ -521,6 +521,12 @@ hom_status hom_set_batch_threads(hom_ctx* ctx, int32_t threads);
  * Results equal the single-CTA ones to rounding (reduction order). Applies to later
  * hom_bounds_batched calls on this context. */
 hom_status hom_set_batch_cluster(hom_ctx* ctx, int32_t cluster, int32_t coop_min_M);
+/* The CG iterations of HOM_MIXED batches run their transform passes as warp-owned pencils
+ * where every double-grid length of the batch's cells is 45, 125, 225 or 405 (N = 23, 63,
+ * 113, 203): each warp takes whole columns or row pairs from load to store with no CTA
+ * barrier inside a pass (enable = 1, the default); enable = 0 runs the chunked block-level
+ * passes. Results agree to rounding. Applies to later hom_bounds_batched calls. */
+hom_status hom_set_batch_warp_passes(hom_ctx* ctx, int32_t enable);
 
 /* Kernel timing (CUDA events around each launch of one kernel family on the
  * launching stream). name: "zpass", "ypass", "xpass", "slab", "final", "cg", "coef", or ""

@@ -122,6 +122,7 @@ def _load():
         "hom_set_gemm_spin_limit": (i32, [vp, i64]),
         "hom_set_net_chunk": (i32, [vp, i32]),
         "hom_set_pipe_passes": (i32, [vp, i32]),
+        "hom_set_batch_warp_passes": (i32, [vp, i32]),
         "hom_set_inner_drift": (i32, [vp, C.c_double]),
         "hom_energy_bounds": (i32, [vp, P(hom_problem), P(hom_opts), vp, sz, vp, dp, dp, dp, P(hom_report)]),
         "hom_net_save": (i32, [vp, P(hom_net_config), vp, C.c_char_p, vp]),
@@ -385,6 +386,11 @@ def hom_fft(ctx, M, precision, direction, howmany, d_in, d_out, d_ws, ws_bytes, 
 
 def hom_set_batch_threads(ctx, threads):
     return check(ctx, lib.hom_set_batch_threads(ctx, int(threads)))
+
+
+def hom_set_batch_warp_passes(ctx, enable):
+    """Warp-owned pencil passes in the FP32 iterations of batches (1, the default) or not (0)."""
+    return check(ctx, lib.hom_set_batch_warp_passes(ctx, int(enable)))
 
 
 def hom_set_batch_cluster(ctx, cluster, coop_min_M=0):

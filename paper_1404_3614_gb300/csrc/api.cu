@@ -78,6 +78,7 @@ struct hom_ctx {
   int batch_threads = 0;   // threads per batched CTA set by the caller (0: tuned / default)
   int graph_launched[6] = {0, 0, 0, 0, 0, 0};   // launch configuration inside the batch graph
   int batch_cluster = 0;   // cluster size set by the caller (0: tuned / default)
+  int batch_wpass = 1;     // FP32 batched iterations: warp-owned pencil passes where they apply
   int batch_coopM = 0;     // with batch_cluster: cells at least this large are cooperative
   // tensor-core GEMMs: this context's timeout flag and the test limit on barrier polls
   int gemm_slot = 0;
@@ -1973,6 +1974,7 @@ hom_status hom_bounds_batched(hom_ctx* ctx, int32_t n, const hom_problem* probs,
     a.M1max = bp.M1max;
     a.x0 = io ? io->d_x0 : nullptr;
     a.fields = io ? io->d_fields : nullptr;
+    a.wpass = ctx->batch_wpass;
     return a;
   };
   // CTAs of one launch: as many as fit at once (0 when the cluster shape cannot be placed),
@@ -2015,7 +2017,7 @@ hom_status hom_bounds_batched(hom_ctx* ctx, int32_t n, const hom_problem* probs,
     BTask* tk = reinterpret_cast<BTask*>(ctx->pin_in);
     for (long long k = 0; k < nt; ++k) tk[k].plan0.sched = tk[k].plan1.sched = sc;
   };
-  const long long tkey = (long long)bp.Mmax * 4 + (f32 ? 1 : 0);
+  const long long tkey = ((long long)bp.Mmax * 4 + (f32 ? 1 : 0)) * 2 + ctx->batch_wpass;
   bool tuned = false;
   for (auto& kv : ctx->tuned_cap)
     if (kv.key == tkey) {
@@ -2097,7 +2099,8 @@ hom_status hom_bounds_batched(hom_ctx* ctx, int32_t n, const hom_problem* probs,
                                         (long long)(uintptr_t)(io ? io->d_fields : nullptr),
                                         (long long)bp.total, nt, grid, (long long)smem, cap,
                                         (long long)f32, max_iter, (long long)(tol * 1e18), (long long)ctx->pin_in_bytes,
-                                        (long long)ctx->pin_out_bytes, bp.M0max, bp.M1max, bp.slot_bytes};
+                                        (long long)ctx->pin_out_bytes, bp.M0max, bp.M1max, bp.slot_bytes,
+                                        (long long)ctx->batch_wpass};
     if (!ctx->graph_exec || ctx->graph_key != key) {
       if (ctx->graph_exec) cudaGraphExecDestroy(ctx->graph_exec);
       if (ctx->graph) cudaGraphDestroy(ctx->graph);
@@ -2365,6 +2368,13 @@ hom_status hom_set_batch_threads(hom_ctx* ctx, int32_t threads) {
   if (threads != 0 && threads != 256 && threads != 512 && threads != 1024)
     return fail(ctx, HOM_ERR_INVALID_ARG, "batched threads per CTA must be 0, 256, 512 or 1024");
   ctx->batch_threads = threads;
+  return HOM_OK;
+}
+
+hom_status hom_set_batch_warp_passes(hom_ctx* ctx, int32_t enable) {
+  if (!ctx) return HOM_ERR_INVALID_ARG;
+  if (enable != 0 && enable != 1) return fail(ctx, HOM_ERR_INVALID_ARG, "warp passes: 0 (off) or 1 (on)");
+  ctx->batch_wpass = enable;
   return HOM_OK;
 }
 

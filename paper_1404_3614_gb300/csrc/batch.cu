@@ -150,6 +150,10 @@ __device__ __forceinline__ void coef_apply(const U* coef, long long gi, long lon
   }
 }
 
+}  // namespace homb
+#include "wbatch.cuh"
+namespace homb {
+
 // Row pass along x over real rows stored as Hermitian halves of Nin values.
 // mode 0: rows (r, y) pair the two components of one field: c2r, A u * scale, r2c (in place);
 // mode 1: energy, rows (y, r, c) in groups of 4: accumulate u_r . A u_s into acc[4];
@@ -447,6 +451,8 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 2 : 1) k_batch(BArgs a) {
     cpx<T>* T2 = reinterpret_cast<cpx<T>*>(work);
     const long long t2_fs = (long long)M1 * Nh;
     const int capT = f32 ? 2 * a.cap : a.cap;
+    // FP32 iterations: warp-owned pencil passes (wbatch.cuh) where the lengths allow
+    const bool wp = f32 && a.wpass != 0;
     cpx<T>* At = reinterpret_cast<cpx<T>*>(Ad);
     cpx<T>* Bt = reinterpret_cast<cpx<T>*>(Bd);
 
@@ -605,16 +611,21 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 2 : 1) k_batch(BArgs a) {
         s_flist[0] = 0; s_flist[1] = 1; s_flist[2] = 2; s_flist[3] = 3; s_nfl = 4;
       }
       team_sync(tm);
-      col_pass<T>(vp, T2, fld, t2_fs, s_flist, s_nfl, Nh, N1, M1, N1, M1, +1, t.plan1, W1, At, Bt, capT, nullptr,
-                  tm);
+      if (!(wp && wcol_pass_any<T>(M1, vp, T2, fld, t2_fs, s_flist, s_nfl, Nh, N1, W1, At, capT, tm)))
+        col_pass<T>(vp, T2, fld, t2_fs, s_flist, s_nfl, Nh, N1, M1, N1, M1, +1, t.plan1, W1, At, Bt, capT, nullptr,
+                    tm);
       team_sync(tm);
       double dummy0[4];
-      row_pass<T>(0, T2, t2_fs, M1, Nh, Nh, M0, coefT, t.ncomp, T(scale), s_rlist, s_nrl, nullptr, t.plan0, W0,
-                  At, Bt, capT, dummy0, tm);
+      if (!(wp && wrow_pass_any<T>(M0, T2, t2_fs, M1, Nh, coefT, t.ncomp, T(scale), s_rlist, s_nrl, W0, At, capT,
+                                   tm)))
+        row_pass<T>(0, T2, t2_fs, M1, Nh, Nh, M0, coefT, t.ncomp, T(scale), s_rlist, s_nrl, nullptr, t.plan0, W0,
+                    At, Bt, capT, dummy0, tm);
       team_sync(tm);
       double pqd[2] = {0.0, 0.0};
-      col_final<T>(T2, vq, vp, t2_fs, fld, s_rlist, s_nrl, Nh, N1, M1, t.invY[0], t.invY[1], t.side, t.plan1, W1,
-                   At, Bt, capT, pqd, tm);
+      if (!(wp && wcol_final_any<T>(M1, T2, vq, vp, t2_fs, fld, s_rlist, s_nrl, Nh, N1, t.invY[0], t.invY[1], t.side,
+                                    W1, At, capT, pqd, tm)))
+        col_final<T>(T2, vq, vp, t2_fs, fld, s_rlist, s_nrl, Nh, N1, M1, t.invY[0], t.invY[1], t.side, t.plan1, W1,
+                     At, Bt, capT, pqd, tm);
       // Rayleigh-Ritz on span{x0}: x = s x0 with s = (x0.b)/(x0.C x0) minimises the energy
       // functional along the start direction, so a start never does worse than x = 0
       double xb[2] = {0.0, 0.0};
@@ -675,25 +686,35 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 2 : 1) k_batch(BArgs a) {
         s_nfl = m;
       }
       __syncthreads();
-      // p = r + beta p
-      for (long long i = tm.tid(); i < 4 * fld; i += tm.nth()) {
-        const int r = (int)(i / (2 * fld));
+      // p = r + beta p (per right-hand side: 32-bit indices, no division per element)
+      const int n2f = (int)(2 * fld);
+      const int tid0 = (int)tm.tid(), nth = (int)tm.nth();
+      for (int r = 0; r < 2; ++r) {
         if (!s_active[r]) continue;
         const T b = T(s_beta[r]);
-        const cpx<T> pv = vp[i], rv = vr[i];
-        vp[i] = mk<T>(fma(b, pv.x, rv.x), fma(b, pv.y, rv.y));
+        cpx<T>* pr_ = vp + (long long)r * n2f;
+        const cpx<T>* rr_ = vr + (long long)r * n2f;
+        for (int i = tid0; i < n2f; i += nth) {
+          const cpx<T> pv = pr_[i], rv = rr_[i];
+          pr_[i] = mk<T>(fma(b, pv.x, rv.x), fma(b, pv.y, rv.y));
+        }
       }
       team_sync(tm);
-      col_pass<T>(vp, T2, fld, t2_fs, s_flist, s_nfl, Nh, N1, M1, N1, M1, +1, t.plan1, W1, At, Bt, capT,
-                  nullptr, tm);
+      if (!(wp && wcol_pass_any<T>(M1, vp, T2, fld, t2_fs, s_flist, s_nfl, Nh, N1, W1, At, capT, tm)))
+        col_pass<T>(vp, T2, fld, t2_fs, s_flist, s_nfl, Nh, N1, M1, N1, M1, +1, t.plan1, W1, At, Bt, capT,
+                    nullptr, tm);
       team_sync(tm);
       double dummy[4];
-      row_pass<T>(0, T2, t2_fs, M1, Nh, Nh, M0, coefT, t.ncomp, T(scale), s_rlist, s_nrl, nullptr, t.plan0, W0,
-                  At, Bt, capT, dummy, tm);
+      if (!(wp && wrow_pass_any<T>(M0, T2, t2_fs, M1, Nh, coefT, t.ncomp, T(scale), s_rlist, s_nrl, W0, At, capT,
+                                   tm)))
+        row_pass<T>(0, T2, t2_fs, M1, Nh, Nh, M0, coefT, t.ncomp, T(scale), s_rlist, s_nrl, nullptr, t.plan0, W0,
+                    At, Bt, capT, dummy, tm);
       team_sync(tm);
       double pq[2] = {0.0, 0.0};
-      col_final<T>(T2, vq, vp, t2_fs, fld, s_rlist, s_nrl, Nh, N1, M1, t.invY[0], t.invY[1], t.side, t.plan1, W1,
-                   At, Bt, capT, pq, tm);
+      if (!(wp && wcol_final_any<T>(M1, T2, vq, vp, t2_fs, fld, s_rlist, s_nrl, Nh, N1, t.invY[0], t.invY[1], t.side,
+                                    W1, At, capT, pq, tm)))
+        col_final<T>(T2, vq, vp, t2_fs, fld, s_rlist, s_nrl, Nh, N1, M1, t.invY[0], t.invY[1], t.side, t.plan1, W1,
+                     At, Bt, capT, pq, tm);
       for (int r = 0; r < 2; ++r) {
         const double s = team_sum(tm, pq[r], s_red, s_xch, parity);
         if (threadIdx.x == 0 && s_active[r]) {
@@ -708,23 +729,36 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 2 : 1) k_batch(BArgs a) {
       }
       __syncthreads();
       double rr[2] = {0.0, 0.0};
-      for (long long i = tm.tid(); i < 4 * fld; i += tm.nth()) {
-        const int r = (int)(i / (2 * fld));
+      const FastDiv fdNh((uint32_t)Nh);
+#pragma unroll
+      for (int r = 0; r < 2; ++r) {
         if (!s_active[r]) continue;
         const T al_ = T(s_alpha[r]);
-        const cpx<T> pv = vp[i], qv = vq[i];
-        cpx<T> xv = vx[i], rv = vr[i];
-        xv = mk<T>(fma(al_, pv.x, xv.x), fma(al_, pv.y, xv.y));
-        rv = mk<T>(fma(-al_, qv.x, rv.x), fma(-al_, qv.y, rv.y));
-        vx[i] = xv;
-        vr[i] = rv;
-        if constexpr (sizeof(T) == 4) {
-          const float sq = fmaf(rv.x, rv.x, rv.y * rv.y);
-          rr[r] += (double)((i % Nh) == 0 ? sq : 2.f * sq);
-        } else {
-          const double w = (i % Nh) == 0 ? 1.0 : 2.0;
-          rr[r] += w * ((double)rv.x * rv.x + (double)rv.y * rv.y);
+        const long long o = (long long)r * n2f;
+        double acc_r = 0.0;
+        float run = 0.f;   // FP32: runs of up to 8 terms, summed in FP64
+        int cnt = 0;
+        for (int i = tid0; i < n2f; i += nth) {
+          const cpx<T> pv = vp[o + i], qv = vq[o + i];
+          cpx<T> xv = vx[o + i], rv = vr[o + i];
+          xv = mk<T>(fma(al_, pv.x, xv.x), fma(al_, pv.y, xv.y));
+          rv = mk<T>(fma(-al_, qv.x, rv.x), fma(-al_, qv.y, rv.y));
+          vx[o + i] = xv;
+          vr[o + i] = rv;
+          const bool k0 = i - (int)fdNh.div(i) * Nh == 0;
+          if constexpr (sizeof(T) == 4) {
+            const float sq = fmaf(rv.x, rv.x, rv.y * rv.y);
+            run = fmaf(k0 ? 1.f : 2.f, sq, run);
+            if (++cnt == 8) {
+              acc_r += (double)run;
+              run = 0.f;
+              cnt = 0;
+            }
+          } else {
+            acc_r += (k0 ? 1.0 : 2.0) * ((double)rv.x * rv.x + (double)rv.y * rv.y);
+          }
         }
+        rr[r] = acc_r + (double)run;
       }
       for (int r = 0; r < 2; ++r) {
         const double s = team_sum(tm, rr[r], s_red, s_xch, parity);

@@ -146,6 +146,7 @@ struct BArgs {
   int M0max, M1max;
   const void* x0;          // optional starting fields [prob][side][rhs][comp][N1][Nh] (working precision)
   void* fields;            // optional final CG fields, same layout
+  int wpass;               // FP32: warp-owned pencil passes for 2N-1 in {45, 125, 225, 405}
 };
 
 // bytes of one batch scratch slot for a task (same formula on host and device)

@@ -166,3 +166,35 @@ def test_cluster_cooperative_benchmark_cells(hb, solver):
                 assert rel(out[key][i], base[key][i]) <= 1e-9, (i, key)
     finally:
         hb.binding.hom_set_batch_cluster(solver.ctx, 0, 0)
+
+
+@pytest.mark.parametrize("cluster,threads", [(1, 512), (4, 512), (1, 1024)])
+def test_warp_passes_match_block_passes(hb, solver, cluster, threads):
+    """The warp-owned pencil passes of the FP32 iterations (double-grid lengths 45, 125,
+    225, 405) and the chunked block-level passes solve the same problems: cells of the
+    benchmark batch with every N of its mix (23, 63, 113, 203) and a rectangular cell that
+    takes the warp passes along one axis only (N = 23 x 13), single-CTA and cluster-split:
+    at tol 1e-6 both are within 1e-5 of FP64 single solves at tol 1e-10 (the FP32 floor of
+    the batched solve on its high-contrast cells: seed 2 ends near 4e-6 either way), the
+    warp passes no further off than the block passes (up to 1e-6), with lower <= upper."""
+    probs = [ms.random_rectangles_2d(s) for s in (0, 1, 2, 3, 5, 6, 9, 11)]
+    probs.append(ms.make_problem(2, (23, 13), (1.0, 0.6), 1.0, [ms.box((0.1, 0.0), (0.4, 0.3), 50.0, 2)]))
+    assert {int(p.N[0]) for p in probs} >= {23, 63, 113, 203}
+    out = {}
+    try:
+        hb.binding.hom_set_batch_threads(solver.ctx, threads)
+        hb.binding.hom_set_batch_cluster(solver.ctx, cluster, 225)
+        for wp in (1, 0):
+            hb.binding.hom_set_batch_warp_passes(solver.ctx, wp)
+            out[wp] = solver.batched(probs, precision=hb.HOM_MIXED, tol=1e-6)
+            assert (out[wp]["status"] >= 0).all()
+        for i, p in enumerate(probs):
+            assert loewner_ge(out[1]["upper"][i], out[1]["lower"][i])
+            ref = solver(p, precision=hb.HOM_FP64, tol=1e-10)
+            for key in ("upper", "lower"):
+                e1, e0 = rel(out[1][key][i], ref[key]), rel(out[0][key][i], ref[key])
+                assert e1 <= 1e-5 and e0 <= 1e-5 and e1 <= e0 + 1e-6, (i, key, e1, e0)
+    finally:
+        hb.binding.hom_set_batch_warp_passes(solver.ctx, 1)
+        hb.binding.hom_set_batch_threads(solver.ctx, 0)
+        hb.binding.hom_set_batch_cluster(solver.ctx, 0, 0)
