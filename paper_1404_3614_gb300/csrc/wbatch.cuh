@@ -12,8 +12,8 @@
 //
 // Transforms: length M = L * K by a lane group of L lanes: lane l holds x[l + L m] (m < K),
 // does a register DFT of length K, multiplies by w_M^(l k2) and exchanges through the pencil
-// buffer; then lane l (< K) gathers y[j][k2 = l] (j < L), does a register DFT of length L and
-// writes X[l + K k1] in natural order. K <= L, so one round of the second stage suffices.
+// buffer; then lane l gathers y[j][k2] (j < L) for k2 = l, l + L, ... (< K), does register
+// DFTs of length L and writes X[k2 + K k1] in natural order.
 #pragma once
 
 namespace homb {
@@ -32,7 +32,8 @@ __host__ __device__ inline bool wpass_len(int M) { return M == 45 || M == 125 ||
 template <typename T, int L, int K>
 __device__ __forceinline__ void wfft_one(cpx<T>* p, int l, const cpx<T>* W, int dir, bool on) {
   constexpr int M = L * K;
-  static_assert(K <= L && M <= 1024, "one round of the second stage");
+  constexpr int RB = (K + L - 1) / L;   // second-stage rounds per lane
+  static_assert(M <= 1024, "pencil length");
   cpx<T> v[K];
 #pragma unroll
   for (int m = 0; m < K; ++m) v[m] = on ? p[l + L * m] : mk<T>(T(0), T(0));
@@ -45,15 +46,25 @@ __device__ __forceinline__ void wfft_one(cpx<T>* p, int l, const cpx<T>* W, int 
     for (int k2 = 0; k2 < K; ++k2) p[l + L * k2] = v[k2];
   }
   __syncwarp();
-  const bool onb = on && l < K;
-  cpx<T> u[L];
+  // lane l: k2 = l + L rb (rb < RB, k2 < K); all reads before any write
+  cpx<T> u[RB][L];
 #pragma unroll
-  for (int j = 0; j < L; ++j) u[j] = onb ? p[j + L * l] : mk<T>(T(0), T(0));
-  dft_reg<T, L>(u, dir);
+  for (int rb = 0; rb < RB; ++rb) {
+    const int k2 = l + L * rb;
+    const bool onb = on && k2 < K;
+#pragma unroll
+    for (int j = 0; j < L; ++j) u[rb][j] = onb ? p[j + L * k2] : mk<T>(T(0), T(0));
+  }
+#pragma unroll
+  for (int rb = 0; rb < RB; ++rb) dft_reg<T, L>(u[rb], dir);
   __syncwarp();
-  if (onb) {
 #pragma unroll
-    for (int k1 = 0; k1 < L; ++k1) p[l + K * k1] = u[k1];
+  for (int rb = 0; rb < RB; ++rb) {
+    const int k2 = l + L * rb;
+    if (on && k2 < K) {
+#pragma unroll
+      for (int k1 = 0; k1 < L; ++k1) p[k2 + K * k1] = u[rb][k1];
+    }
   }
   __syncwarp();
 }
