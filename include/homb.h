@@ -493,10 +493,11 @@ hom_status hom_set_pass_chunks(hom_ctx* ctx, int32_t ypass_pencils, int32_t xpas
 hom_status hom_set_slab_pass(hom_ctx* ctx, int32_t enable);
 /* The first and last passes of the FP32 3D operator at double-grid length 225 along z
  * (the zero-padded inverse z transform with the CG prologue, and the truncating forward z
- * transform with Gamma and the CG partial sums) run as persistent CTAs, two per SM, that
+ * transform with Gamma and the CG partial sums) can run as persistent CTAs, two per SM, that
  * stage the input of their next chunk of pencils with asynchronous copies while they
- * transform the current one (enable = 1, the default). enable = 0 runs the chunked passes
- * (one CTA per chunk); the results agree to rounding. Applies to later calls. */
+ * transform the current one. enable is a mask: 1 the last pass (the default: measured
+ * faster), 2 the z inverse (measured slower than the chunked pass: its CG prologue goes
+ * through shared memory), 0 neither. The results agree to rounding. Applies to later calls. */
 hom_status hom_set_pipe_passes(hom_ctx* ctx, int32_t enable);
 /* Target of the FP32 inner solves of HOM_MIXED (no counterpart in the paper: a precision
  * scheme of this library). An inner solve that starts from the FP64 residual r0 stops when its

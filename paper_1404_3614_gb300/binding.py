@@ -463,7 +463,7 @@ def hom_set_gemm_spin_limit(ctx, polls):
 
 
 def hom_set_pipe_passes(ctx, enable):
-    """Persistent pipelined FP32 z passes at length 225 (1, the default) or the chunked passes (0)."""
+    """Persistent pipelined FP32 z passes at length 225: mask 1 last pass (default), 2 z inverse."""
     return check(ctx, lib.hom_set_pipe_passes(ctx, int(enable)))
 
 

@@ -66,7 +66,7 @@ struct hom_ctx {
   std::vector<CgGraph> cg_graphs;
   bool graphs_off = false;
   bool slab_on = true;   // fused y-x-y slab pass where it applies
-  bool zpipe_on = true;  // persistent pipelined FP32 z passes where they apply
+  int zpipe_mask = 1;    // persistent pipelined FP32 z passes where they apply: 1 last pass, 2 z inverse
   double inner_drift = 0.0;   // drift coefficient of the FP32 inner target (0: default)
   int sms = 0;           // SMs of the device (set at creation)
   int slab_warps = 0;     // warps per slab CTA chosen by the caller (0: automatic)
@@ -784,7 +784,7 @@ struct Runner {
       z.Pin = Nz; z.Pout = Mz; z.Nlog = Nz; z.dir = +1;
       z.slabs_per_rhs = C; z.slabs_per_comp = 1; z.C = C; z.prologue = prologue;
       z.W = W(2); z.plan = g.plan[2]; z.cg = cg;
-      if (sizeof(T) == 4 && ctx->zpipe_on)
+      if (sizeof(T) == 4 && (ctx->zpipe_mask & 2))
         z.pgrid = zpipe_pad_grid(Mz, z.Pin, z.Pout, z.Nlog, z.dir, z.X, z.nslab, ctx->sms);
       if (z.XC < 1) return fail(ctx, HOM_ERR_INVALID_ARG, "grid too large for the shared-memory FFT");
       KL(launch_pencil<T>(z, st));
@@ -864,7 +864,7 @@ struct Runner {
   // CTAs of the persistent FP32 last pass (0: the chunked pass runs), at most one partial
   // sum slot per CTA and right-hand side
   int final_pipe_grid() const {
-    if (!ctx->zpipe_on) return 0;
+    if (!(ctx->zpipe_mask & 1)) return 0;
     const int pg = zpipe_final_grid(g.d == 3 ? g.M[2] : g.M[1], g.d == 3 ? g.N[2] : g.N[1], g.d, g.d,
                                     g.d == 3 ? g.N[1] * g.Nh : g.Nh, R, ctx->sms);
     return std::min(pg, L.maxblk);
@@ -946,7 +946,7 @@ struct Runner {
     const long long extra[13] = {(long long)side, (long long)sizeof(T), K, (long long)(uintptr_t)coefT,
                                  (long long)(uintptr_t)cg, (long long)L.total, R, nfin, ctx->ypass_xc,
                                  ctx->xpass_yb, (long long)ctx->slab_on, ctx->slab_warps,
-                                 (long long)ctx->zpipe_on};
+                                 (long long)ctx->zpipe_mask};
     const unsigned char* eb = reinterpret_cast<const unsigned char*>(extra);
     key.insert(key.end(), eb, eb + sizeof extra);
     key.insert(key.end(), ctx->prof_family.begin(), ctx->prof_family.end());
@@ -2405,8 +2405,9 @@ hom_status hom_set_inner_drift(hom_ctx* ctx, double c) {
 
 hom_status hom_set_pipe_passes(hom_ctx* ctx, int32_t enable) {
   if (!ctx) return HOM_ERR_INVALID_ARG;
-  if (enable != 0 && enable != 1) return fail(ctx, HOM_ERR_INVALID_ARG, "pipelined passes: 0 (off) or 1 (on)");
-  ctx->zpipe_on = enable != 0;
+  if (enable < 0 || enable > 3)
+    return fail(ctx, HOM_ERR_INVALID_ARG, "pipelined passes: a mask of 1 (last pass) and 2 (z inverse)");
+  ctx->zpipe_mask = enable;
   return HOM_OK;
 }
 

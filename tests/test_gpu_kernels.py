@@ -251,8 +251,9 @@ def test_slab_pass_matches_separate_passes(hb, ctx, N, prec):
 
 @pytest.mark.parametrize("name", ["balls3d_N9x11x113_Mz225", "spheres3d_N113"])
 def test_pipe_passes_match_chunked_passes(hb, ctx, name):
-    """The persistent pipelined FP32 z passes (length 225) and the chunked passes compute the
-    same operator (2e-6 relative to the largest entry) on both sides, with and without Gamma;
+    """The persistent pipelined FP32 z passes (length 225; each of the two, and both) and the
+    chunked passes compute the same operator (2e-6 relative to the largest entry) on both
+    sides, with and without Gamma;
     through hom_bounds (mixed: the CG prologue p = r + beta p and the partial sums p.Cp) they
     give the same bounds to the solver's tolerance."""
     p = PROBLEMS[name]() if name in PROBLEMS else ms.random_spheres_3d(0, N=113)
@@ -270,24 +271,25 @@ def test_pipe_passes_match_chunked_passes(hb, ctx, name):
             hb.hom_coefficient(ctx, p, side, hb.HOM_FP32, coef.data_ptr(), ws.data_ptr(), nws)
             for project in (0, 1):
                 out = {}
-                for pipe in (1, 0):
+                for pipe in (3, 2, 1, 0):
                     hb.binding.hom_set_pipe_passes(ctx, pipe)
                     y = torch.full_like(x, float("nan"))
                     hb.hom_matvec(ctx, p, side, hb.HOM_FP32, project, d, coef.data_ptr(), x.data_ptr(),
                                   y.data_ptr(), ws.data_ptr(), nws)
                     torch.cuda.synchronize()
                     out[pipe] = y.cpu().numpy()
-                assert np.isfinite(out[1]).all()
-                assert relerr(out[1], out[0]) < 2e-6, (name, side, project, relerr(out[1], out[0]))
+                for pipe in (3, 2, 1):
+                    assert np.isfinite(out[pipe]).all()
+                    assert relerr(out[pipe], out[0]) < 2e-6, (name, side, project, pipe, relerr(out[pipe], out[0]))
         if name in PROBLEMS:
             solver = hb.Bounds(0)
             try:
                 res = {}
-                for pipe in (1, 0):
+                for pipe in (3, 0):
                     hb.binding.hom_set_pipe_passes(solver.ctx, pipe)
                     res[pipe] = solver(p, precision=hb.HOM_MIXED, tol=1e-7)
                 for key in ("upper", "lower"):
-                    assert relerr(res[1][key], res[0][key]) < 1e-6, key
+                    assert relerr(res[3][key], res[0][key]) < 1e-6, key
             finally:
                 solver.close()
     finally:
