@@ -69,14 +69,16 @@ __global__ void k_spectrum(SpecArgs a, double2* out) {
   }
 }
 
+// b_r(k) = -Gamma(k) A_hat(k) e_r for every right-hand side r < nrhs from one evaluation of
+// A_hat(k) per frequency (the closed form is the costly part: FP64 transcendental functions and
+// a phase product per inclusion), with the |b_r|^2 partials of each r.
 template <typename T>
-__global__ void __launch_bounds__(kThreads) k_rhs(SpecArgs a, int side, int Nh, int N1, int N2,
+__global__ void __launch_bounds__(kThreads) k_rhs(SpecArgs a, int side, int nrhs, int Nh, int N1, int N2,
                                                    cpx<T>* b, double* partial, int ld) {
   __shared__ double red[32];
-  const int r = blockIdx.y;
   const int C = a.d;
   const long long field = (long long)Nh * N1 * N2;
-  double acc = 0.0;
+  double acc[3] = {0.0, 0.0, 0.0};
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < field;
        e += (long long)gridDim.x * blockDim.x) {
     const int kx = (int)(e % Nh);
@@ -86,34 +88,42 @@ __global__ void __launch_bounds__(kThreads) k_rhs(SpecArgs a, int side, int Nh, 
     const int ni[3] = {kx, ns[1] < 0 ? ns[1] + a.M[1] : ns[1], ns[2] < 0 ? ns[2] + a.M[2] : ns[2]};
     double2 Ah[6];
     ahat_eval(a, ni, ns, Ah);
-    double2 v[3];
-    for (int c = 0; c < C; ++c) {
-      if (a.ncomp == 1) v[c] = c == r ? Ah[0] : make_double2(0.0, 0.0);
-      else v[c] = Ah[sym_index(a.d, c, r)];
-    }
     double xi[3], n2 = 0.0;
-    double2 dot = make_double2(0.0, 0.0);
     for (int c = 0; c < C; ++c) {
       xi[c] = ns[c] * a.invY[c];
       n2 += xi[c] * xi[c];
-      dot.x += xi[c] * v[c].x;
-      dot.y += xi[c] * v[c].y;
     }
     const double w = kx == 0 ? 1.0 : 2.0;
     const bool nyq = nyquist(ns[1], N1) || (a.d == 3 && nyquist(ns[2], N2));
-    for (int c = 0; c < C; ++c) {
-      double2 g = make_double2(0.0, 0.0);
-      if (n2 > 0.0 && !nyq) {
-        const double2 ge = make_double2(xi[c] * dot.x / n2, xi[c] * dot.y / n2);
-        g = side == 0 ? ge : make_double2(v[c].x - ge.x, v[c].y - ge.y);
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+      if (r >= nrhs) break;
+      double2 v[3];
+      double2 dot = make_double2(0.0, 0.0);
+      for (int c = 0; c < C; ++c) {
+        if (a.ncomp == 1) v[c] = c == r ? Ah[0] : make_double2(0.0, 0.0);
+        else v[c] = Ah[sym_index(a.d, c, r)];
+        dot.x += xi[c] * v[c].x;
+        dot.y += xi[c] * v[c].y;
       }
-      const cpx<T> bv = mk<T>(T(-g.x), T(-g.y));
-      b[((long long)r * C + c) * field + e] = bv;
-      acc += w * ((double)bv.x * bv.x + (double)bv.y * bv.y);
+      for (int c = 0; c < C; ++c) {
+        double2 g = make_double2(0.0, 0.0);
+        if (n2 > 0.0 && !nyq) {
+          const double2 ge = make_double2(xi[c] * dot.x / n2, xi[c] * dot.y / n2);
+          g = side == 0 ? ge : make_double2(v[c].x - ge.x, v[c].y - ge.y);
+        }
+        const cpx<T> bv = mk<T>(T(-g.x), T(-g.y));
+        b[((long long)r * C + c) * field + e] = bv;
+        acc[r] += w * ((double)bv.x * bv.x + (double)bv.y * bv.y);
+      }
     }
   }
-  const double s = block_sum(acc, red);
-  if (threadIdx.x == 0) partial[r * ld + blockIdx.x] = s;
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {
+    if (r >= nrhs) break;
+    const double s = block_sum(acc[r], red);
+    if (threadIdx.x == 0) partial[r * ld + blockIdx.x] = s;
+  }
 }
 
 // ---------------------------------------------------------------------------------
@@ -754,7 +764,77 @@ cudaError_t launch_axis_tables(int nincl, int d, const int* M, int Mmax, const d
   return cudaGetLastError();
 }
 
+// A_hat on the half of Z_M, one (y, z) row of x frequencies at a time per CTA: the y and z
+// factors of every inclusion's phase (and of a box's sinc) are formed once per row in shared
+// memory, so that an x frequency needs one complex product per inclusion instead of d - 1.
+// Same terms as ahat_eval, the phase product taken as p_x (p_y p_z).
+constexpr int kSpecRowIncl = 128;
+constexpr int kSpecRowThreads = 128;
+__global__ void __launch_bounds__(kSpecRowThreads) k_spectrum_rows(SpecArgs a, double2* out) {
+  __shared__ double2 qyz[kSpecRowIncl];
+  __shared__ double syz[kSpecRowIncl];
+  const long long total = (long long)a.len[0] * a.len[1] * a.len[2];
+  const int nrows = a.len[1] * a.len[2];
+  for (int row = blockIdx.x; row < nrows; row += gridDim.x) {
+    const int iy = row % a.len[1], iz = row / a.len[1];
+    const int nsy = sfreq(iy, a.Nmod[1]), nsz = a.d == 3 ? sfreq(iz, a.Nmod[2]) : 0;
+    const int niy = nsy < 0 ? nsy + a.M[1] : nsy, niz = nsz < 0 ? nsz + a.M[2] : nsz;
+    __syncthreads();   // the previous row's factors are no longer read
+    for (int j = threadIdx.x; j < a.nincl; j += blockDim.x) {
+      double2 q = a.phase[((long long)j * 3 + 1) * a.Mmax + niy];
+      double sy = a.sinc[((long long)j * 3 + 1) * a.Mmax + niy];
+      if (a.d == 3) {
+        const double2 t = a.phase[((long long)j * 3 + 2) * a.Mmax + niz];
+        q = make_double2(q.x * t.x - q.y * t.y, q.x * t.y + q.y * t.x);
+        sy *= a.sinc[((long long)j * 3 + 2) * a.Mmax + niz];
+      }
+      qyz[j] = q;
+      syz[j] = sy * a.invVol;
+    }
+    __syncthreads();
+    const double yz2 = (nsy * a.invY[1]) * (nsy * a.invY[1]) + (nsz * a.invY[2]) * (nsz * a.invY[2]);
+    for (int ix = threadIdx.x; ix < a.len[0]; ix += blockDim.x) {
+      double2 v[6];
+      for (int q = 0; q < a.ncomp; ++q) v[q] = make_double2(0.0, 0.0);
+      if (ix == 0 && nsy == 0 && nsz == 0)
+        for (int q = 0; q < a.ncomp; ++q) v[q].x = a.A0p[q];
+      double rad = 0.0;
+      for (int j = 0; j < a.nincl; ++j) {
+        const DevIncl& I = a.incl[j];
+        double f;
+        if (I.shape == 0) {
+          f = syz[j] * a.sinc[((long long)j * 3) * a.Mmax + ix];
+        } else {
+          if (!I.same_as_prev) {
+            const double xi = ix * a.invY[0];
+            const double R = I.h[0];
+            const double q = 2.0 * M_PI * R * sqrt(xi * xi + yz2);
+            rad = a.d == 3 ? 4.0 * M_PI * R * R * R * ball_radial(q) : 2.0 * M_PI * R * R * disk_radial(q);
+          }
+          f = rad * a.invVol;
+        }
+        const double2 px = a.phase[((long long)j * 3) * a.Mmax + ix];
+        const double2 q = qyz[j];
+        const double2 ph = make_double2(px.x * q.x - px.y * q.y, px.x * q.y + px.y * q.x);
+        for (int c = 0; c < a.ncomp; ++c) {
+          const double sc = f * I.dA[c];
+          v[c].x = fma(sc, ph.x, v[c].x);
+          v[c].y = fma(sc, ph.y, v[c].y);
+        }
+      }
+      const long long e = (long long)row * a.len[0] + ix;
+      for (int c = 0; c < a.ncomp; ++c) out[c * total + e] = v[c];
+    }
+  }
+}
+
 cudaError_t launch_spectrum(const SpecArgs& a, double2* out, cudaStream_t s) {
+  if (a.nincl <= kSpecRowIncl) {
+    const int nrows = a.len[1] * a.len[2];
+    const int blocks = nrows < 152 * 16 ? nrows : 152 * 16;
+    k_spectrum_rows<<<blocks, kSpecRowThreads, 0, s>>>(a, out);
+    return cudaGetLastError();
+  }
   const long long total = (long long)a.len[0] * a.len[1] * a.len[2];
   long long blocks = (total + kThreads - 1) / kThreads;
   if (blocks > 152 * 64) blocks = 152 * 64;
@@ -765,9 +845,9 @@ cudaError_t launch_spectrum(const SpecArgs& a, double2* out, cudaStream_t s) {
 template <typename T>
 cudaError_t launch_rhs(const SpecArgs& a, int side, int nrhs, int Nh, const int* N, void* b,
                        double* partial, int nblk, cudaStream_t s) {
-  dim3 grid(nblk, nrhs);
-  k_rhs<T><<<grid, kThreads, 0, s>>>(a, side, Nh, N[1], N[2], reinterpret_cast<cpx<T>*>(b),
-                                     partial, nblk);
+  if (nrhs < 1 || nrhs > 3) return cudaErrorInvalidValue;
+  k_rhs<T><<<nblk, kThreads, 0, s>>>(a, side, nrhs, Nh, N[1], N[2], reinterpret_cast<cpx<T>*>(b), partial,
+                                     nblk);
   return cudaGetLastError();
 }
 

@@ -63,19 +63,6 @@ __device__ __forceinline__ void stage_twiddles_kl(cpx<T>* Wt, const void* W) {
   }
 }
 
-// Known zeros of the warp FFTs' transforms of length M = R*R. A zero-padded inverse transform has
-// at most N <= (M+1)/2 nonzero inputs: at positions p <= (M-3)/4 and p >= (3M+3)/4 (the y rows
-// of the padded slab, the Hermitian x extension, Nh <= (M+3)/4); a truncating forward one
-// keeps only the outputs at those positions. In the lane layout p = l + R n of the register
-// FFTs, the rows n in [lo, hi] hold only such positions for every lane l: they are never read
-// as inputs (inverse) and never computed or stored as outputs (forward).
-template <int R> struct ZeroBand {
-  static constexpr int M = R * R;
-  static constexpr int lo = ((M + 3) / 4 + R - 1) / R;
-  static constexpr int hi = ((3 * M - 3) / 4 - (R - 1)) / R;
-  static constexpr bool in(int n) { return n >= lo && n <= hi; }
-};
-static_assert(ZeroBand<15>::lo == 4 && ZeroBand<15>::hi == 10, "zero band of the length-225 transforms");
 
 // G contiguous pencils (stride R*R) in place, R lanes per pencil; ends with __syncthreads.
 // mode 1: zero-padded inverse transforms (at most (M+1)/2 nonzero inputs: the zero band of
@@ -183,7 +170,9 @@ __global__ void __launch_bounds__(kPassThreads) k_pencil(PencilArgs a) {
     res = A;
   } else {
     const bool trunc_ = a.dir < 0 && a.Pout != M;
-    const int prune = (pad && prune3_ok(M, half + 1) ? 1 : 0) | (trunc_ && prune3_ok(M, half + 1) ? 2 : 0);
+    const bool zb = zero_band_free(M, a.Nlog);
+    const int prune = (pad && prune3_ok(M, half + 1) ? 1 : 0) | (trunc_ && prune3_ok(M, half + 1) ? 2 : 0) |
+                      (pad && zb ? 4 : 0) | (trunc_ && zb ? 8 : 0);
     res = fft_any<T, MT>(A, B, XC, a.plan, Ws, a.dir, prune);
   }
   cpx<T>* out = reinterpret_cast<cpx<T>*>(a.out) + (long long)s * a.out_slab;
@@ -250,7 +239,9 @@ __global__ void __launch_bounds__(kPassThreads) k_final(FinalArgs a) {
     fft_warp_all<T, WR>(A, C * XC, Ws, -1, a.Nlog < M && zero_band_free(M, a.Nlog) ? 2 : 0);
     res = A;
   } else {
-    res = fft_any<T, MT>(A, B, C * XC, a.plan, Ws, -1, prune3_ok(M, (a.Nlog - 1) / 2 + 1) ? 2 : 0);
+    res = fft_any<T, MT>(A, B, C * XC, a.plan, Ws, -1,
+                         (prune3_ok(M, (a.Nlog - 1) / 2 + 1) ? 2 : 0) |
+                             (a.Nlog < M && zero_band_free(M, a.Nlog) ? 8 : 0));
   }
   cpx<T>* out = reinterpret_cast<cpx<T>*>(a.out) + (long long)rhs * C * a.out_comp;
   const cpx<T>* pdir = (a.cg && a.aux) ? reinterpret_cast<const cpx<T>*>(a.aux) + (long long)rhs * C * a.out_comp
@@ -449,7 +440,9 @@ __global__ void __launch_bounds__(kPassThreads) k_xpass(XArgs a) {
     A[pp * M + k] = mk<T>(z[0].x - z[1].y, z[0].y + z[1].x);
   }
   __syncthreads();
-  cpx<T>* res = fft_any<T, MT>(A, B, npair, a.plan, Ws, +1, a.mode != 2 && prune3_ok(M, Nin) ? 1 : 0);
+  cpx<T>* res = fft_any<T, MT>(A, B, npair, a.plan, Ws, +1,
+                               a.mode != 2 ? ((prune3_ok(M, Nin) ? 1 : 0) | (zero_band_free(M, 2 * Nin - 1) ? 4 : 0))
+                                           : 0);
   cpx<T>* oth = res == A ? B : A;
   const T* coef = reinterpret_cast<const T*>(a.coef);
   const long long cstride = (long long)a.planes * M;
@@ -476,7 +469,8 @@ __global__ void __launch_bounds__(kPassThreads) k_xpass(XArgs a) {
         }
     }
     __syncthreads();
-    cpx<T>* r2 = fft_any<T, MT>(res, oth, npair, a.plan, Ws, -1, prune3_ok(M, a.Nout) ? 2 : 0);
+    cpx<T>* r2 = fft_any<T, MT>(res, oth, npair, a.plan, Ws, -1,
+                                (prune3_ok(M, a.Nout) ? 2 : 0) | (zero_band_free(M, 2 * a.Nout - 1) ? 8 : 0));
     cpx<T>* out = reinterpret_cast<cpx<T>*>(a.out);
     const int Nout = a.Nout;
     for (int t = threadIdx.x; t < nrow * Nout; t += blockDim.x) {

@@ -38,150 +38,6 @@ inline size_t slab_smem_bytes(int M, int R, int Nh, int warps, size_t elem) {
 }
 
 
-// DFT3 of (a0, a1, a2) with compile-time zero inputs (Z0, Z1, Z2), same convention as dft3:
-// y_k = sum_n a_n w^(n k), w = exp(dir 2 pi i / 3). Inputs marked zero are not read.
-template <typename T, bool Z0, bool Z1, bool Z2>
-__device__ __forceinline__ void dft3_z(const cpx<T>* a, cpx<T>* y, int dir) {
-  const T h = T(0.5);
-  const T s3 = (dir > 0 ? T(1) : T(-1)) * T(0.86602540378443864676372317075294);
-  if constexpr (!Z0 && Z1 && Z2) {
-    y[0] = a[0];
-    y[1] = a[0];
-    y[2] = a[0];
-  } else if constexpr (Z0 && !Z1 && Z2) {   // y1 = w a1, y2 = w^2 a1
-    const cpx<T> b = a[1];
-    const T mx = -h * b.x, my = -h * b.y;
-    y[0] = b;
-    y[1] = mk<T>(fma(-s3, b.y, mx), fma(s3, b.x, my));
-    y[2] = mk<T>(fma(s3, b.y, mx), fma(-s3, b.x, my));
-  } else if constexpr (!Z0 && !Z1 && Z2) {   // y1 = a0 + w a1, y2 = a0 + w^2 a1
-    const cpx<T> m = mk<T>(fma(-h, a[1].x, a[0].x), fma(-h, a[1].y, a[0].y));
-    y[0] = add<T>(a[0], a[1]);
-    y[1] = mk<T>(fma(-s3, a[1].y, m.x), fma(s3, a[1].x, m.y));
-    y[2] = mk<T>(fma(s3, a[1].y, m.x), fma(-s3, a[1].x, m.y));
-  } else if constexpr (!Z0 && Z1 && !Z2) {   // y1 = a0 + w^2 a2, y2 = a0 + w a2
-    const cpx<T> m = mk<T>(fma(-h, a[2].x, a[0].x), fma(-h, a[2].y, a[0].y));
-    y[0] = add<T>(a[0], a[2]);
-    y[1] = mk<T>(fma(s3, a[2].y, m.x), fma(-s3, a[2].x, m.y));
-    y[2] = mk<T>(fma(-s3, a[2].y, m.x), fma(s3, a[2].x, m.y));
-  } else if constexpr (Z0 && !Z1 && !Z2) {   // y1 = w a1 + w^2 a2, y2 = w^2 a1 + w a2
-    const cpx<T> t = add<T>(a[1], a[2]), dd = sub<T>(a[1], a[2]);
-    const T mx = -h * t.x, my = -h * t.y;
-    y[0] = t;
-    y[1] = mk<T>(fma(-s3, dd.y, mx), fma(s3, dd.x, my));
-    y[2] = mk<T>(fma(s3, dd.y, mx), fma(-s3, dd.x, my));
-  } else {
-    y[0] = a[0];
-    y[1] = a[1];
-    y[2] = a[2];
-    dft3<T>(y, dir);
-  }
-}
-
-// DFT5 of b computing only the outputs in the compile-time mask KEEP (bit k: output k); the
-// others are left unchanged. Same convention as dft5.
-template <typename T, int KEEP>
-__device__ __forceinline__ void dft5_keep(cpx<T>* v, int dir) {
-  const T c1 = T(0.30901699437494742410229341718282);    // cos(2 pi/5)
-  const T c2 = T(-0.80901699437494742410229341718282);   // cos(4 pi/5)
-  const T s1 = T(0.95105651629515357211643933337938);    // sin(2 pi/5)
-  const T s2 = T(0.58778525229247312916870595463907);    // sin(4 pi/5)
-  const cpx<T> a1 = add<T>(v[1], v[4]), b1 = sub<T>(v[1], v[4]);
-  const cpx<T> a2 = add<T>(v[2], v[3]), b2 = sub<T>(v[2], v[3]);
-  const int s = dir > 0 ? 1 : -1;
-  cpx<T> o[5];
-  if constexpr ((KEEP & 0x12) != 0) {   // outputs 1, 4
-    const cpx<T> m1 = mk<T>(fma(c1, a1.x, fma(c2, a2.x, v[0].x)), fma(c1, a1.y, fma(c2, a2.y, v[0].y)));
-    const cpx<T> n1 = mk<T>(fma(s1, b1.x, s2 * b2.x), fma(s1, b1.y, s2 * b2.y));
-    const cpx<T> in1 = rot<T>(n1, s);
-    o[1] = add<T>(m1, in1);
-    o[4] = sub<T>(m1, in1);
-  }
-  if constexpr ((KEEP & 0x0c) != 0) {   // outputs 2, 3
-    const cpx<T> m2 = mk<T>(fma(c2, a1.x, fma(c1, a2.x, v[0].x)), fma(c2, a1.y, fma(c1, a2.y, v[0].y)));
-    const cpx<T> n2 = mk<T>(fma(s2, b1.x, -s1 * b2.x), fma(s2, b1.y, -s1 * b2.y));
-    const cpx<T> in2 = rot<T>(n2, s);
-    o[2] = add<T>(m2, in2);
-    o[3] = sub<T>(m2, in2);
-  }
-  if constexpr ((KEEP & 1) != 0) v[0] = add<T>(v[0], add<T>(a1, a2));
-#pragma unroll
-  for (int k = 1; k < 5; ++k)
-    if ((KEEP >> k) & 1) v[k] = o[k];
-}
-
-// Length-15 DFT (prime-factor map as dft15_pfa) with the inputs of the zero band (4..10) known
-// to be zero: they are not read, and the first-layer DFT3s take their reduced forms.
-template <typename T>
-__device__ __forceinline__ void dft15_zin(cpx<T>* v, int dir) {
-  cpx<T> t[15];
-  {
-    const cpx<T> a[3] = {v[0], v[0], v[0]};   // n2 = 0: inputs 0, 5, 10
-    dft3_z<T, false, true, true>(a, t + 0, dir);
-  }
-  {
-    const cpx<T> a[3] = {v[3], v[3], v[13]};   // n2 = 1: inputs 3, 8, 13
-    dft3_z<T, false, true, false>(a, t + 3, dir);
-  }
-  {
-    const cpx<T> a[3] = {v[1], v[11], v[1]};   // n2 = 2: inputs 6, 11, 1
-    dft3_z<T, true, false, false>(a, t + 6, dir);
-  }
-  {
-    const cpx<T> a[3] = {v[14], v[14], v[14]};   // n2 = 3: inputs 9, 14, 4
-    dft3_z<T, true, false, true>(a, t + 9, dir);
-  }
-  {
-    const cpx<T> a[3] = {v[12], v[2], v[2]};   // n2 = 4: inputs 12, 2, 7
-    dft3_z<T, false, false, true>(a, t + 12, dir);
-  }
-#pragma unroll
-  for (int k1 = 0; k1 < 3; ++k1) {
-    cpx<T> b[5];
-#pragma unroll
-    for (int n2 = 0; n2 < 5; ++n2) b[n2] = t[n2 * 3 + k1];
-    dft5<T>(b, dir);
-#pragma unroll
-    for (int k2 = 0; k2 < 5; ++k2) v[(10 * k1 + 6 * k2) % 15] = b[k2];
-  }
-}
-
-// Length-15 DFT (prime-factor map) computing only the outputs outside the zero band (0..3,
-// 11..14); the band's outputs are left undefined.
-template <typename T>
-__device__ __forceinline__ void dft15_zout(cpx<T>* v, int dir) {
-  cpx<T> t[15];
-#pragma unroll
-  for (int n2 = 0; n2 < 5; ++n2) {
-    cpx<T> a[3];
-#pragma unroll
-    for (int n1 = 0; n1 < 3; ++n1) a[n1] = v[(5 * n1 + 3 * n2) % 15];
-    dft3<T>(a, dir);
-#pragma unroll
-    for (int k1 = 0; k1 < 3; ++k1) t[n2 * 3 + k1] = a[k1];
-  }
-  // outputs k = (10 k1 + 6 k2) mod 15 outside 4..10: k1 = 0: k2 in {0, 2, 3} (0, 12, 3);
-  // k1 = 1: k2 in {1, 3} (1, 13); k1 = 2: k2 in {1, 2, 4} (11, 2, 14)
-  cpx<T> b[5];
-#pragma unroll
-  for (int n2 = 0; n2 < 5; ++n2) b[n2] = t[n2 * 3 + 0];
-  dft5_keep<T, 0x0d>(b, dir);
-  v[0] = b[0];
-  v[12] = b[2];
-  v[3] = b[3];
-#pragma unroll
-  for (int n2 = 0; n2 < 5; ++n2) b[n2] = t[n2 * 3 + 1];
-  dft5_keep<T, 0x0a>(b, dir);
-  v[1] = b[1];
-  v[13] = b[3];
-#pragma unroll
-  for (int n2 = 0; n2 < 5; ++n2) b[n2] = t[n2 * 3 + 2];
-  dft5_keep<T, 0x16>(b, dir);
-  v[11] = b[1];
-  v[2] = b[2];
-  v[14] = b[4];
-}
-
 // First-stage DFT of a zero-padded inverse transform (inputs of the zero band not read) and
 // last-stage DFT of a truncating forward one (outputs of the band not computed)
 template <typename T, int R>
