@@ -384,6 +384,8 @@ struct Layout {
   size_t rrpart = 0;                                         // Rayleigh-Ritz partial sums
   size_t gs = 0, gD[2] = {0, 0}, gtw[3] = {0, 0, 0};         // GaNi samples, their DFT, twiddles
   int Mmax, maxblk, nblk_energy;
+  size_t radtab = 0;            // radial factors of the ball groups (0 bytes: evaluated per frequency)
+  int radgroups = 0, radlen = 0;
   size_t off = 0;
   size_t take(size_t bytes) {
     const size_t o = off;
@@ -410,6 +412,25 @@ Layout make_layout(const Geometry& g, int R, size_t elem, int mode) {
   L.incl = L.take(2 * ni * sizeof(DevIncl));
   L.phase = L.take(ni * 3 * L.Mmax * sizeof(double2));
   L.sinc = L.take(ni * 3 * L.Mmax * sizeof(double));
+  {
+    // radial factors of the balls / disks on integer |k|^2 when the cell has one side length
+    // (then |xi|^2 = |k|^2 / Y^2): one table per group of equal consecutive balls
+    bool same_y = true;
+    for (int a = 1; a < g.d; ++a) same_y = same_y && g.Y[a] == g.Y[0];
+    int groups = 0;
+    for (size_t j = 0; j < g.incl.size(); ++j) {
+      const hom_inclusion& I = g.incl[j];
+      if (I.shape == HOM_BALL && !(j > 0 && g.incl[j - 1].shape == HOM_BALL && I.size[0] == g.incl[j - 1].size[0]))
+        ++groups;
+    }
+    long long len = 1;
+    for (int a = 0; a < g.d; ++a) len += (long long)((g.M[a] - 1) / 2) * ((g.M[a] - 1) / 2);
+    if (g.bitmap.empty() && same_y && groups > 0 && (long long)groups * len * 8 <= (32LL << 20)) {
+      L.radgroups = groups;
+      L.radlen = (int)len;
+      L.radtab = L.take((size_t)groups * len * sizeof(double));
+    }
+  }
   if (!g.bitmap.empty()) {
     L.bmp = L.take((size_t)g.npix() * 8);
     L.bmpD[0] = L.take((size_t)g.npix() * 16);
@@ -651,6 +672,8 @@ struct Runner {
     a.phase = at<double2>(L.phase);
     a.sinc = at<double>(L.sinc);
     a.Mmax = L.Mmax;
+    a.radtab = L.radlen > 0 ? at<double>(L.radtab) : nullptr;
+    a.radlen = L.radlen;
     return a;
   }
 
@@ -693,6 +716,7 @@ struct Runner {
     } else {
       KL(launch_axis_tables(sa.nincl, g.d, g.M, L.Mmax, g.invY, sa.incl, at<double2>(L.phase), at<double>(L.sinc),
                             st));
+      if (L.radlen > 0) KL(launch_radial_table(sa, at<double>(L.radtab), L.radgroups, st));
       KL(launch_spectrum(sa, S, st));
     }
     return coefficient_from_spectrum(coef);
@@ -2224,6 +2248,7 @@ hom_status hom_rhs(hom_ctx* ctx, const hom_problem* prob, int32_t side, int32_t 
   SpecArgs sa = run.spec_args(side);
   KL(launch_axis_tables(sa.nincl, g.d, g.M, run.L.Mmax, g.invY, sa.incl, run.at<double2>(run.L.phase),
                         run.at<double>(run.L.sinc), run.st));
+  if (run.L.radlen > 0) KL(launch_radial_table(sa, run.at<double>(run.L.radtab), run.L.radgroups, run.st));
   const int N3[3] = {g.N[0], g.N[1], g.N[2]};
   if (precision == HOM_FP64)
     KL(launch_rhs<double>(sa, side, nrhs, g.Nh, N3, d_b, run.at<double>(run.L.partial), kVecBlocks, run.st));

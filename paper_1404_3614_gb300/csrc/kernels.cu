@@ -9,6 +9,8 @@
 // the epilogue of the last pass together with the CG partial sum p.Cp.
 #include <math.h>
 
+#include <algorithm>
+
 #include "kernels.cuh"
 #include "spectrum.cuh"
 
@@ -799,6 +801,8 @@ __global__ void __launch_bounds__(kSpecRowThreads) k_spectrum_rows(SpecArgs a, d
       if (ix == 0 && nsy == 0 && nsz == 0)
         for (int q = 0; q < a.ncomp; ++q) v[q].x = a.A0p[q];
       double rad = 0.0;
+      int grp = -1;
+      const int n2 = ix * ix + nsy * nsy + nsz * nsz;
       for (int j = 0; j < a.nincl; ++j) {
         const DevIncl& I = a.incl[j];
         double f;
@@ -806,10 +810,13 @@ __global__ void __launch_bounds__(kSpecRowThreads) k_spectrum_rows(SpecArgs a, d
           f = syz[j] * a.sinc[((long long)j * 3) * a.Mmax + ix];
         } else {
           if (!I.same_as_prev) {
-            const double xi = ix * a.invY[0];
-            const double R = I.h[0];
-            const double q = 2.0 * M_PI * R * sqrt(xi * xi + yz2);
-            rad = a.d == 3 ? 4.0 * M_PI * R * R * R * ball_radial(q) : 2.0 * M_PI * R * R * disk_radial(q);
+            ++grp;
+            if (a.radtab) {
+              rad = a.radtab[(long long)grp * a.radlen + n2];
+            } else {
+              const double xi = ix * a.invY[0];
+              rad = radial_factor(a.d, I.h[0], sqrt(xi * xi + yz2));
+            }
           }
           f = rad * a.invVol;
         }
@@ -826,6 +833,28 @@ __global__ void __launch_bounds__(kSpecRowThreads) k_spectrum_rows(SpecArgs a, d
       for (int c = 0; c < a.ncomp; ++c) out[c * total + e] = v[c];
     }
   }
+}
+
+// One entry per (ball group, integer |k|^2): the group's radial factor at |xi| = sqrt(n) / Y
+__global__ void k_radial_table(SpecArgs a, double* tab, int groups) {
+  const long long total = (long long)groups * a.radlen;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int g = (int)(e / a.radlen);
+    const int n = (int)(e - (long long)g * a.radlen);
+    int grp = -1, j = 0;
+    for (; j < a.nincl; ++j)
+      if (a.incl[j].shape != 0 && !a.incl[j].same_as_prev && ++grp == g) break;
+    tab[e] = j < a.nincl ? radial_factor(a.d, a.incl[j].h[0], sqrt((double)n) * a.invY[0]) : 0.0;
+  }
+}
+
+cudaError_t launch_radial_table(const SpecArgs& a, double* radtab, int groups, cudaStream_t s) {
+  if (groups < 1 || a.radlen < 1) return cudaSuccess;
+  const long long total = (long long)groups * a.radlen;
+  const int blocks = (int)std::min<long long>((total + kThreads - 1) / kThreads, 152 * 16);
+  k_radial_table<<<blocks, kThreads, 0, s>>>(a, radtab, groups);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_spectrum(const SpecArgs& a, double2* out, cudaStream_t s) {

@@ -111,6 +111,11 @@ struct SpecArgs {
   int P[3];
   int invert;             // dual side of an image: 1 / a
   int closed;             // GaNi sampling: boundary points belong to the inclusion
+  // Radial factors of the balls / disks, [group][n] for n = |k|^2 = 0 .. radlen - 1 (integer
+  // frequencies, cells with one side length on every axis); a group is a ball and the equal
+  // balls after it (same_as_prev). NULL: evaluated per frequency.
+  const double* radtab = nullptr;
+  int radlen = 0;
 };
 
 // One batched 2D task: a (problem, side) pair solved entirely by one CTA of the
@@ -199,6 +204,8 @@ cudaError_t launch_axis_tables(int nincl, int d, const int* M, int Mmax, const d
 // Fourier coefficients of the side's coefficient on the half index set of Z_M,
 // out [ncomp][Mz][My][(Mx+1)/2] complex FP64.
 cudaError_t launch_spectrum(const SpecArgs& a, double2* out, cudaStream_t s);
+// a.radtab (writable) from the inclusions: entries of each ball group for n = 0 .. radlen - 1
+cudaError_t launch_radial_table(const SpecArgs& a, double* radtab, int groups, cudaStream_t s);
 // b_r(k) = -Gamma(k) A_hat(k) e_r on Z_N (half), FP64 or FP32, plus |b|^2 partials.
 template <typename T>
 cudaError_t launch_rhs(const SpecArgs& a, int side, int nrhs, int Nh, const int* N, void* b,

@@ -25,11 +25,19 @@ __device__ __forceinline__ double disk_radial(double q) {
   return j1(q) / q;
 }
 
+// Radial factor 4 pi R^3 (sin q - q cos q)/q^3 (ball) or 2 pi R^2 J1(q)/q (disk), q = 2 pi R |xi|
+__device__ __forceinline__ double radial_factor(int d, double R, double xi_norm) {
+  const double q = 2.0 * M_PI * R * xi_norm;
+  return d == 3 ? 4.0 * M_PI * R * R * R * ball_radial(q) : 2.0 * M_PI * R * R * disk_radial(q);
+}
+
 __device__ __forceinline__ void ahat_eval(const SpecArgs& a, const int* ni, const int* ns, double2* out) {
   for (int q = 0; q < a.ncomp; ++q) out[q] = make_double2(0.0, 0.0);
   if (ns[0] == 0 && ns[1] == 0 && ns[2] == 0)
     for (int q = 0; q < a.ncomp; ++q) out[q].x = a.A0p[q];
   double rad = 0.0;
+  int grp = -1;
+  const int n2 = ns[0] * ns[0] + ns[1] * ns[1] + ns[2] * ns[2];
   for (int j = 0; j < a.nincl; ++j) {
     const DevIncl& I = a.incl[j];
     double f;
@@ -38,14 +46,17 @@ __device__ __forceinline__ void ahat_eval(const SpecArgs& a, const int* ni, cons
       for (int al = 0; al < a.d; ++al) f *= a.sinc[((long long)j * 3 + al) * a.Mmax + ni[al]];
     } else {
       if (!I.same_as_prev) {
-        double xi2 = 0.0;
-        for (int al = 0; al < a.d; ++al) {
-          const double xi = ns[al] * a.invY[al];
-          xi2 += xi * xi;
+        ++grp;
+        if (a.radtab) {
+          rad = a.radtab[(long long)grp * a.radlen + n2];
+        } else {
+          double xi2 = 0.0;
+          for (int al = 0; al < a.d; ++al) {
+            const double xi = ns[al] * a.invY[al];
+            xi2 += xi * xi;
+          }
+          rad = radial_factor(a.d, I.h[0], sqrt(xi2));
         }
-        const double R = I.h[0];
-        const double q = 2.0 * M_PI * R * sqrt(xi2);
-        rad = a.d == 3 ? 4.0 * M_PI * R * R * R * ball_radial(q) : 2.0 * M_PI * R * R * disk_radial(q);
       }
       f = rad * a.invVol;
     }
