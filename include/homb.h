@@ -497,7 +497,9 @@ hom_status hom_set_slab_pass(hom_ctx* ctx, int32_t enable);
  * stage the input of their next chunk of pencils with asynchronous copies while they
  * transform the current one. enable is a mask: 1 the last pass (the default: measured
  * faster), 2 the z inverse (measured slower than the chunked pass: its CG prologue goes
- * through shared memory), 0 neither. The results agree to rounding. Applies to later calls. */
+ * through shared memory), 4 with 1: the last pass on chunks of 16 positions (one CTA per SM;
+ * measured 5 % slower than 8), 0 neither. The results agree to rounding. Applies to later
+ * calls. */
 hom_status hom_set_pipe_passes(hom_ctx* ctx, int32_t enable);
 /* Target of the FP32 inner solves of HOM_MIXED (no counterpart in the paper: a precision
  * scheme of this library). An inner solve that starts from the FP64 residual r0 stops when its

@@ -463,7 +463,8 @@ def hom_set_gemm_spin_limit(ctx, polls):
 
 
 def hom_set_pipe_passes(ctx, enable):
-    """Persistent pipelined FP32 z passes at length 225: mask 1 last pass (default), 2 z inverse."""
+    """Persistent pipelined FP32 z passes at length 225: mask 1 last pass (default), 2 z inverse,
+    4 wide chunks of the last pass."""
     return check(ctx, lib.hom_set_pipe_passes(ctx, int(enable)))
 
 

@@ -878,7 +878,10 @@ struct Runner {
       f.W = W(g.d == 3 ? 2 : 1); f.plan = g.plan[g.d == 3 ? 2 : 1];
       f.cg = cg; f.partial_ld = L.maxblk; f.bsub = bsub;
       f.partial = ((cg && p_aux) || bsub) ? at<double>(L.partial) : nullptr;
-      if (sizeof(T) == 4 && !bsub) f.pgrid = final_pipe_grid();
+      if (sizeof(T) == 4 && !bsub) {
+        f.pgrid = final_pipe_grid();
+        f.pxc = final_pipe_xc();
+      }
       if (f.XC < 1) return fail(ctx, HOM_ERR_INVALID_ARG, "grid too large for the shared-memory FFT");
       KL(launch_final<T>(f, st));
     }
@@ -890,8 +893,10 @@ struct Runner {
   int final_pipe_grid() const {
     if (!(ctx->zpipe_mask & 1)) return 0;
     const int pg = zpipe_final_grid(g.d == 3 ? g.M[2] : g.M[1], g.d == 3 ? g.N[2] : g.N[1], g.d, g.d,
-                                    g.d == 3 ? g.N[1] * g.Nh : g.Nh, R, ctx->sms);
+                                    g.d == 3 ? g.N[1] * g.Nh : g.Nh, R, ctx->sms, final_pipe_xc());
     return std::min(pg, L.maxblk);
+  }
+  int final_pipe_xc() const { return (ctx->zpipe_mask & 4) ? 16 : 8;
   }
 
   int final_blocks(size_t elem) const {
@@ -2430,8 +2435,8 @@ hom_status hom_set_inner_drift(hom_ctx* ctx, double c) {
 
 hom_status hom_set_pipe_passes(hom_ctx* ctx, int32_t enable) {
   if (!ctx) return HOM_ERR_INVALID_ARG;
-  if (enable < 0 || enable > 3)
-    return fail(ctx, HOM_ERR_INVALID_ARG, "pipelined passes: a mask of 1 (last pass) and 2 (z inverse)");
+  if (enable < 0 || enable > 7)
+    return fail(ctx, HOM_ERR_INVALID_ARG, "pipelined passes: a mask of 1 (last pass), 2 (z inverse), 4 (wide chunks)");
   ctx->zpipe_mask = enable;
   return HOM_OK;
 }

@@ -49,6 +49,7 @@ struct FinalArgs {
   const void* bsub;              // residual mode: out = bsub - Gamma(...), partial |out|^2
   int pgrid;                     // > 0: the persistent pipelined z pass with this many CTAs
                                  // (zpipe_final_grid; partial sums [rhs][pgrid])
+  int pxc;                       // its positions per chunk: 8 or 16
   FastDiv fd_XC, fd_per, fd_Nh;  // set by the launcher
 };
 
@@ -193,7 +194,7 @@ template <typename T> int pencil_xc(int M, int X, int C);   // chunk that fits s
 // counts on a device with `sms` SMs, 0 where they do not apply (another length, a transform
 // that is not the zero-padded inverse / truncating forward one of the operator)
 int zpipe_pad_grid(int M, int Pin, int Pout, int Nlog, int dir, int X, int nslab, int sms);
-int zpipe_final_grid(int M, int Nlog, int d, int C, int X, int nrhs, int sms);
+int zpipe_final_grid(int M, int Nlog, int d, int C, int X, int nrhs, int sms, int xc = 8);
 template <typename T> int xpass_yb(int M, int rows_per_plane, int planes);
 // fused y-x-y slab pass; cudaErrorNotSupported when the length or size does not apply
 template <typename T> cudaError_t launch_slab(const SlabArgs& a, cudaStream_t s);

@@ -672,13 +672,16 @@ template <typename T> cudaError_t launch_zpad_pipe(const PencilArgs& a, cudaStre
   return cudaGetLastError();
 }
 
-template <typename T> cudaError_t launch_final_pipe(const FinalArgs& a, cudaStream_t s) {
-  constexpr size_t smem = zp_final_smem<T, 15>();
+template <typename T, int XC> cudaError_t launch_final_pipe_xc(const FinalArgs& a, cudaStream_t s) {
+  constexpr size_t smem = zp_final_smem<T, 15, XC>();
   static std::atomic<int> cache[kAttrDevices] = {};
-  cudaError_t e = smem_attr(k_final_pipe<T, 15>, smem, cache);
+  cudaError_t e = smem_attr(k_final_pipe<T, 15, XC>, smem, cache);
   if (e != cudaSuccess) return e;
-  k_final_pipe<T, 15><<<a.pgrid, kZpThreads, smem, s>>>(a);
+  k_final_pipe<T, 15, XC><<<a.pgrid, zp_final_threads(XC), smem, s>>>(a);
   return cudaGetLastError();
+}
+template <typename T> cudaError_t launch_final_pipe(const FinalArgs& a, cudaStream_t s) {
+  return a.pxc == 16 ? launch_final_pipe_xc<T, 16>(a, s) : launch_final_pipe_xc<T, 8>(a, s);
 }
 
 template <typename T> cudaError_t launch_pencil(const PencilArgs& a0, cudaStream_t s) {

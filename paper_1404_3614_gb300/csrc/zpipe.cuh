@@ -31,9 +31,11 @@ __device__ __forceinline__ void zp_wait() {
   asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 
+// Threads of the last pass with XC positions per chunk (3 XC pencils, two per warp)
+constexpr int zp_final_threads(int XC) { return 48 * XC; }
 // Shared memory of the two kernels (bytes)
-template <typename T, int R> constexpr size_t zp_final_smem() {
-  return sizeof(cpx<T>) * (size_t)(R * R) * (1 + 2 * kZpPencils) + 32 * sizeof(double);
+template <typename T, int R, int XC = kZpFinalXC> constexpr size_t zp_final_smem() {
+  return sizeof(cpx<T>) * (size_t)(R * R) * (1 + 2 * 3 * XC) + 32 * sizeof(double);
 }
 template <typename T, int R> constexpr size_t zp_pad_smem(int staged_fields) {
   return sizeof(cpx<T>) * ((size_t)(R * R) * (1 + kZpPencils) + (size_t)staged_fields * ((R * R + 1) / 2) * kZpPadXC);
@@ -45,15 +47,15 @@ template <typename T, int R> constexpr size_t zp_pad_smem(int staged_fields) {
 // position (xx = tid % 8) and the rows tid / 8 + 48 k of the output, so its frequency
 // decoding is done once per chunk and its loads of the CG direction are issued before the
 // transforms. Partial sums: partial[rhs * partial_ld + blockIdx.x] for every rhs < nrhs.
-template <typename T, int R>
-__global__ void __launch_bounds__(kZpThreads, 2) k_final_pipe(FinalArgs a) {
+template <typename T, int R, int XC>
+__global__ void __launch_bounds__(zp_final_threads(XC), XC <= 8 ? 2 : 1) k_final_pipe(FinalArgs a) {
   constexpr int M = R * R;
-  constexpr int XC = kZpFinalXC;
   constexpr int C = 3;
   constexpr int G = C * XC;
-  constexpr int RS = kZpThreads / XC;   // rows per sweep (48)
-  constexpr int IT = 3;                 // output rows per thread: Nlog <= 3 * 48
-  static_assert(G == kZpPencils, "one pencil per lane group");
+  constexpr int NT = zp_final_threads(XC);
+  constexpr int RS = NT / XC;   // rows per sweep (48)
+  constexpr int IT = 3;         // output rows per thread: Nlog <= 3 * 48
+  static_assert(G == 2 * (NT / 32), "one pencil per lane group");
   extern __shared__ __align__(16) unsigned char smem[];
   cpx<T>* Wt = reinterpret_cast<cpx<T>*>(smem);
   cpx<T>* buf0 = Wt + M;
@@ -260,10 +262,10 @@ __global__ void __launch_bounds__(kZpThreads, 2) k_zpad_pipe(PencilArgs a) {
   }
 }
 
-// Persistent grids: two CTAs per SM, at most one per chunk
-inline int zp_final_grid(int X, int nrhs, int sms) {
-  const int nq = nrhs * ((X + kZpFinalXC - 1) / kZpFinalXC);
-  return std::max(1, std::min(nq, 2 * sms));
+// Persistent grids: two CTAs per SM (one with 16 positions per chunk), at most one per chunk
+inline int zp_final_grid(int X, int nrhs, int sms, int XC = kZpFinalXC) {
+  const int nq = nrhs * ((X + XC - 1) / XC);
+  return std::max(1, std::min(nq, (XC <= 8 ? 2 : 1) * sms));
 }
 inline int zp_pad_grid(int X, int nslab, int sms) {
   const int nq = nslab * ((X + kZpPadXC - 1) / kZpPadXC);

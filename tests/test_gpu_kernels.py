@@ -251,7 +251,8 @@ def test_slab_pass_matches_separate_passes(hb, ctx, N, prec):
 
 @pytest.mark.parametrize("name", ["balls3d_N9x11x113_Mz225", "spheres3d_N113"])
 def test_pipe_passes_match_chunked_passes(hb, ctx, name):
-    """The persistent pipelined FP32 z passes (length 225; each of the two, and both) and the
+    """The persistent pipelined FP32 z passes (length 225; each of the two, both, and the last
+    pass with 16 positions per chunk) and the
     chunked passes compute the same operator (2e-6 relative to the largest entry) on both
     sides, with and without Gamma;
     through hom_bounds (mixed: the CG prologue p = r + beta p and the partial sums p.Cp) they
@@ -271,14 +272,14 @@ def test_pipe_passes_match_chunked_passes(hb, ctx, name):
             hb.hom_coefficient(ctx, p, side, hb.HOM_FP32, coef.data_ptr(), ws.data_ptr(), nws)
             for project in (0, 1):
                 out = {}
-                for pipe in (3, 2, 1, 0):
+                for pipe in (3, 2, 1, 5, 0):
                     hb.binding.hom_set_pipe_passes(ctx, pipe)
                     y = torch.full_like(x, float("nan"))
                     hb.hom_matvec(ctx, p, side, hb.HOM_FP32, project, d, coef.data_ptr(), x.data_ptr(),
                                   y.data_ptr(), ws.data_ptr(), nws)
                     torch.cuda.synchronize()
                     out[pipe] = y.cpu().numpy()
-                for pipe in (3, 2, 1):
+                for pipe in (3, 2, 1, 5):
                     assert np.isfinite(out[pipe]).all()
                     assert relerr(out[pipe], out[0]) < 2e-6, (name, side, project, pipe, relerr(out[pipe], out[0]))
         if name in PROBLEMS:
