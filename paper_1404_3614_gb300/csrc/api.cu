@@ -546,6 +546,7 @@ struct Runner {
   cudaStream_t st;
   int R;
   bool gani = false;   // GaNi: g is the N grid (M = N), coefficient sampled at the grid points
+  int coef_side = -1;  // side whose double-grid coefficient build_coefficient left in L.coef64
 
   template <typename X> X* at(size_t off) const { return reinterpret_cast<X*>(base + off); }
 
@@ -706,8 +707,30 @@ struct Runner {
     return dft3(at<double2>(L.bmpD[0]), at<double2>(L.bmpD[1]), g.P, g.pplan, L.bmptw);
   }
 
+  // One material in the inclusions of an isotropic cell (scalar phases a0, a1): the double-grid
+  // coefficient is A_M = a0 + (a1 - a0) F_M with F_M the double-grid interpolant of the
+  // inclusions' indicator sum, the same F_M on both sides (the dual side's pointwise inverse is
+  // 1/a0 + (1/a1 - 1/a0) sum f_j), so the dual coefficient is an affine map of the primal one.
+  bool one_material(double* a0, double* a1) const {
+    if (g.ncomp != 1 || !g.bitmap.empty() || g.incl.empty()) return false;
+    for (const hom_inclusion& I : g.incl)
+      for (int k = 0; k < 9; ++k)
+        if (I.A[k] != g.incl[0].A[k]) return false;
+    *a0 = g.A0[0][0];
+    *a1 = g.incl[0].A[0];
+    return *a1 != *a0;
+  }
+
   hom_status build_coefficient(int side, double* coef) {
     Prof pr(ctx, "coef", st);
+    double a0 = 0.0, a1 = 0.0;
+    if (side == 1 && coef_side == 0 && coef == at<double>(L.coef64) && one_material(&a0, &a1)) {
+      // A^-1_M = 1/a0 + (1/a1 - 1/a0) F_M = 1/a0 + b (A_M - a0), b = (1/a1 - 1/a0) / (a1 - a0)
+      KL(launch_affine(coef, (long long)g.grid, a0, (1.0 / a1 - 1.0 / a0) / (a1 - a0), 1.0 / a0, st));
+      coef_side = 1;
+      return HOM_OK;
+    }
+    coef_side = coef == at<double>(L.coef64) ? side : -1;
     SpecArgs sa = spec_args(side);
     double2* S = at<double2>(L.t1);
     if (!g.bitmap.empty()) {

@@ -747,6 +747,13 @@ __global__ void k_energy_identity_finish(const double* part, int nblk, const dou
   }
 }
 
+// x = c + b (x - a) elementwise (the dual coefficient of a one-material cell from the primal one)
+__global__ void k_affine(double* x, long long n, double a, double b, double c) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    x[i] = fma(b, x[i] - a, c);
+}
+
 __global__ void k_convert_d2f(const double* in, float* out, long long n) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x)
@@ -1188,6 +1195,13 @@ cudaError_t launch_energy_identity(const double2* b, const double2* x, const dou
   k_coef_sum_part<<<cblk, kThreads, 0, s>>>(coef, ncomp, grid, cpart);
   const int d = C;
   k_energy_identity_finish<<<1, kThreads, 0, s>>>(part, nblk, cpart, cblk, R, d, ncomp, (double)grid, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_affine(double* x, long long n, double a, double b, double c, cudaStream_t s) {
+  long long blocks = (n + kThreads - 1) / kThreads;
+  if (blocks > 152 * 32) blocks = 152 * 32;
+  k_affine<<<(int)blocks, kThreads, 0, s>>>(x, n, a, b, c);
   return cudaGetLastError();
 }
 

@@ -288,6 +288,8 @@ cudaError_t launch_block_rayleigh_ritz(double2* x, double2* r, const double2* b,
 cudaError_t launch_energy_reduce(const double* partial, int nblk, int nrr, double* out,
                                  cudaStream_t s);
 cudaError_t launch_convert_d2f(const double* in, float* out, long long n, cudaStream_t s);
+// x = c + b (x - a) for n doubles
+cudaError_t launch_affine(double* x, long long n, double a, double b, double c, cudaStream_t s);
 template <typename T>
 cudaError_t launch_fft_batch(const void* in, void* out, int M, int howmany, int dir, const void* W,
                              const FftPlan& plan, cudaStream_t s);
