@@ -84,6 +84,7 @@ __device__ __forceinline__ void fft_warp_all(cpx<T>* A, int G, const cpx<T>* Wt,
   const bool act = sub < PW;
   const int slots = (blockDim.x >> 5) * PW;
   for (int g0 = 0; g0 < G; g0 += slots) {
+    if (g0 + warp * PW >= G) break;   // warps with no pencil left skip the arithmetic on zeros
     const int g = g0 + warp * PW + sub;
     const bool on = act && g < G;
     cpx<T>* p = A + (size_t)(on ? g : 0) * (R * R);

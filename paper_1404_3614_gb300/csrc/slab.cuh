@@ -310,6 +310,7 @@ __global__ void __launch_bounds__(kSlabMaxThreads) k_slab(SlabArgs a) {
     // ---- inverse y transforms of the Nh columns: input rows from the staged slab
     // (row-major [Ny][Nh]), zero padded to M, results into column kx of P
     for (int c0 = 0; c0 < Nh; c0 += slots) {
+      if (c0 + warp * PW >= Nh) break;   // no column for this warp in this or a later round
       const int kx = c0 + slot;
       const bool on = act && kx < Nh;
       cpx<T>* p = P + (size_t)(on ? kx : 0) * M;
@@ -347,6 +348,7 @@ __global__ void __launch_bounds__(kSlabMaxThreads) k_slab(SlabArgs a) {
     cpx<T>* Sw = S + (size_t)(act ? slot : 0) * M;
     const T* coefz = reinterpret_cast<const T*>(a.coef) + (size_t)z * M * M;
     for (int p0 = 0; p0 < npairs; p0 += slots) {
+      if (p0 + warp * PW >= npairs) break;   // no row pair for this warp
       const int pr = p0 + slot;
       const bool on = act && pr < npairs;
       const int ya = 2 * pr, yb = 2 * pr + 1;
@@ -414,6 +416,7 @@ __global__ void __launch_bounds__(kSlabMaxThreads) k_slab(SlabArgs a) {
     // ---- forward y transforms (truncated; with ZB the zero band's rows are neither computed nor
     // stored)
     for (int c0 = 0; c0 < Nh; c0 += slots) {
+      if (c0 + warp * PW >= Nh) break;
       const int kx = c0 + slot;
       const bool on = act && kx < Nh;
       if constexpr (ZB) pencil_fft_fwd_trunc<T, R>(P + (size_t)(on ? kx : 0) * M, l, Wt, on);
