@@ -977,10 +977,11 @@ struct Runner {
   hom_status cg_iteration(CgScalars* cg, const void* coefT, int side, int nfin) {
     CKS(matvec<T>(base + L.p, base + L.q, coefT, side + 1, cg, base + L.r, base + L.p, 1));
     Prof pr(ctx, "cg", st);
-    KL(launch_cg_alpha(cg, at<double>(L.partial), L.maxblk, nfin, R, st));
+    // alpha inside the update (from the last pass's p.Cp partials in L.partial), the |r|^2
+    // partials into L.rrpart (the update's CTAs still read L.partial while others write)
     KL(launch_cg_update<T>(base + L.x, base + L.r, base + L.p, base + L.q, R, g.d, g.field, g.Nh, cg,
-                           at<double>(L.partial), kVecBlocks, st));
-    KL(launch_cg_beta(cg, at<double>(L.partial), kVecBlocks, kVecBlocks, R, st));
+                           at<double>(L.rrpart), kVecBlocks, at<double>(L.partial), L.maxblk, nfin, st));
+    KL(launch_cg_beta(cg, at<double>(L.rrpart), kVecBlocks, kVecBlocks, R, st));
     return HOM_OK;
   }
 

@@ -131,15 +131,41 @@ __global__ void __launch_bounds__(kThreads) k_rhs(SpecArgs a, int side, int nrhs
 // ---------------------------------------------------------------------------------
 // CG vector update and scalar kernels (one CTA), deterministic reductions
 // ---------------------------------------------------------------------------------
+__device__ double reduce_row(const double* v, int n, double* red);
+
+// CG step of one right-hand side: alpha = r.r / p.Cp from the last operator pass's partial
+// sums pq_part[rhs][pq_nblk] (every CTA forms the same sum in the same order, so all agree;
+// CTA 0 records alpha and p.Cp, or the breakdown p.Cp <= 0 / non-finite, which stops the
+// right-hand side in every CTA), then x += alpha p, r -= alpha Cp and the |r|^2 partials.
 template <typename T>
 __global__ void __launch_bounds__(kThreads) k_cg_update(cpx<T>* x, cpx<T>* r, const cpx<T>* p,
                                                          const cpx<T>* q, int C, long long field,
                                                          FastDiv fdNh, CgScalars* cg, double* partial,
-                                                         int ld) {
+                                                         int ld, const double* pq_part, int pq_ld,
+                                                         int pq_nblk) {
   __shared__ double red[32];
+  __shared__ double s_alpha;
+  __shared__ int s_on;
   const int rhs = blockIdx.y;
   if (!cg->active[rhs]) return;
-  const T al = T(cg->alpha[rhs]);
+  const double pq = reduce_row(pq_part + (long long)rhs * pq_ld, pq_nblk, red);
+  if (threadIdx.x == 0) {
+    const bool ok = pq > 0.0 && isfinite(pq);
+    s_on = ok ? 1 : 0;
+    s_alpha = ok ? cg->rr[rhs] / pq : 0.0;
+    if (blockIdx.x == 0) {
+      cg->pq[rhs] = pq;
+      if (ok) {
+        cg->alpha[rhs] = s_alpha;
+      } else {
+        cg->active[rhs] = 0;
+        cg->status[rhs] = cg->guard ? 2 : -2;
+      }
+    }
+  }
+  __syncthreads();
+  if (!s_on) return;
+  const T al = T(s_alpha);
   const long long n = (long long)C * field;
   const long long base = (long long)rhs * n;
   double acc = 0.0;
@@ -233,25 +259,6 @@ __global__ void k_cg_init(CgScalars* cg, const double* partial, int ld, int nblk
         cg->status[r] = s > t2 ? 1 : 0;
       }
     }
-  }
-}
-
-__global__ void k_cg_alpha(CgScalars* cg, const double* partial, int ld, int nblk, int nrhs) {
-  __shared__ double red[32];
-  for (int r = 0; r < nrhs; ++r) {
-    if (!cg->active[r]) continue;
-    const double pq = reduce_row(partial + (long long)r * ld, nblk, red);
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      cg->pq[r] = pq;
-      if (!(pq > 0.0) || !isfinite(pq)) {
-        cg->active[r] = 0;
-        cg->status[r] = cg->guard ? 2 : -2;
-      } else {
-        cg->alpha[r] = cg->rr[r] / pq;
-      }
-    }
-    __syncthreads();
   }
 }
 
@@ -890,12 +897,13 @@ cudaError_t launch_rhs(const SpecArgs& a, int side, int nrhs, int Nh, const int*
 template <typename T>
 cudaError_t launch_cg_update(void* x, void* r, const void* p, const void* q, int nrhs, int C,
                              long long field, int Nh, CgScalars* cg, double* partial, int nblk,
-                             cudaStream_t s) {
+                             const double* pq_part, int pq_ld, int pq_nblk, cudaStream_t s) {
   if ((long long)C * field >= (1LL << 31)) return cudaErrorInvalidValue;
   dim3 grid(nblk, nrhs);
   k_cg_update<T><<<grid, kThreads, 0, s>>>(
       reinterpret_cast<cpx<T>*>(x), reinterpret_cast<cpx<T>*>(r), reinterpret_cast<const cpx<T>*>(p),
-      reinterpret_cast<const cpx<T>*>(q), C, field, FastDiv((uint32_t)Nh), cg, partial, nblk);
+      reinterpret_cast<const cpx<T>*>(q), C, field, FastDiv((uint32_t)Nh), cg, partial, nblk, pq_part, pq_ld,
+      pq_nblk);
   return cudaGetLastError();
 }
 
@@ -920,11 +928,6 @@ cudaError_t launch_promote_add(const float2* x32, double2* x64, long long n, cud
   long long blocks = (n + kThreads - 1) / kThreads;
   if (blocks > 152 * 32) blocks = 152 * 32;
   k_promote_add<<<(int)blocks, kThreads, 0, s>>>(x32, x64, n);
-  return cudaGetLastError();
-}
-cudaError_t launch_cg_alpha(CgScalars* cg, const double* partial, int ld, int nblk, int nrhs,
-                            cudaStream_t s) {
-  k_cg_alpha<<<1, kThreads, 0, s>>>(cg, partial, ld, nblk, nrhs);
   return cudaGetLastError();
 }
 cudaError_t launch_cg_beta(CgScalars* cg, const double* partial, int ld, int nblk, int nrhs,
@@ -1218,7 +1221,7 @@ cudaError_t launch_convert_d2f(const double* in, float* out, long long n, cudaSt
                                      int, cudaStream_t);                                         \
   template cudaError_t launch_cg_update<T>(void*, void*, const void*, const void*, int, int,     \
                                            long long, int, CgScalars*, double*, int,             \
-                                           cudaStream_t);                                        \
+                                           const double*, int, int, cudaStream_t);               \
   template cudaError_t launch_project_promote<T>(const void*, double2*, int, int, int, int, int, \
                                                  const double*, int, cudaStream_t);
 HOMB_INST(double)

@@ -211,10 +211,12 @@ cudaError_t launch_radial_table(const SpecArgs& a, double* radtab, int groups, c
 template <typename T>
 cudaError_t launch_rhs(const SpecArgs& a, int side, int nrhs, int Nh, const int* N, void* b,
                        double* partial, int nblk, cudaStream_t s);
+// alpha from the operator pass's p.Cp partials pq_part[rhs][pq_nblk] (row stride pq_ld), then
+// x += alpha p, r -= alpha Cp and the |r|^2 partials into `partial` (a different buffer)
 template <typename T>
 cudaError_t launch_cg_update(void* x, void* r, const void* p, const void* q, int nrhs, int C,
                              long long field, int Nh, CgScalars* cg, double* partial, int nblk,
-                             cudaStream_t s);
+                             const double* pq_part, int pq_ld, int pq_nblk, cudaStream_t s);
 // r.r from the partials; tol2[r] = max(tol2_abs, rel2 * r.r); guard as given.
 // With drift > 0 (an FP32 inner solve), the absolute target is raised from tol2_abs toward
 // tol2_hi: (sqrt(tol2_hi) - drift |r0|)^2 when that is larger, drift |r0| bounding how far the
@@ -231,8 +233,6 @@ cudaError_t launch_demote(const double2* r64, float2* r32, int nrhs, int C, long
                           const CgScalars* outer, double* partial, int nblk, cudaStream_t s);
 // x64 += (double) x32
 cudaError_t launch_promote_add(const float2* x32, double2* x64, long long n, cudaStream_t s);
-cudaError_t launch_cg_alpha(CgScalars* cg, const double* partial, int ld, int nblk, int nrhs,
-                            cudaStream_t s);
 cudaError_t launch_cg_beta(CgScalars* cg, const double* partial, int ld, int nblk, int nrhs,
                            cudaStream_t s);
 // GaNi coefficient sampled at the grid points of the M = N grid (a.M = N), packed symmetric
