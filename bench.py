@@ -34,8 +34,9 @@ sys.path.insert(0, ROOT)
 
 METRIC = "time to bounds at 1e-4 rel. residual; matvec HBM GB/s; vs plain FP64 CG"
 WORKLOAD = ("3D d=3, N=113^3 (double grid 225^3), 16 random non-overlapping balls (seed 0), volume "
-            "fraction 0.3, contrast 1000 (a=1 matrix, a=1000 balls), FP32 inner CG with FP64 refinement, "
-            "re-projection and bounds, primal and dual bounds for E=e1,e2,e3, stop at ||r|| <= 1e-4 ||E||")
+            "fraction 0.3, contrast 1000 (a=1 matrix, a=1000 balls), FP32 inner CG with FP64 refinement "
+            "(residuals in float-float arithmetic on FP64 data), FP64 re-projection and bounds, primal and dual "
+            "bounds for E=e1,e2,e3, stop at ||r|| <= 1e-4 ||E||")
 CUBE_WORKLOAD = ("3D d=3, N=41^3 (double grid 81^3), centred cube inclusion side 0.5, contrast 100 "
                  "(a=1 matrix, a=100 inclusion), plain FP64 CG")
 TOL = 1e-4
@@ -190,8 +191,8 @@ def run_matvec_only(args):
     problem = workload(args.workload)
     solver = hb.Bounds(0)
     stream = torch.cuda.current_stream()
-    mv = matvec_timings(hb, solver, problem, torch.device("cuda", 0), stream, reps=args.reps,
-                        precisions=(args.precision,) if args.precision != "mixed" else ("fp32",))
+    prec = args.matvec_precision or ("fp32" if args.precision == "mixed" else args.precision)
+    mv = matvec_timings(hb, solver, problem, torch.device("cuda", 0), stream, reps=args.reps, precisions=(prec,))
     print(json.dumps({"workload": WORKLOADS[args.workload], "matvec": mv}), flush=True)
     solver.close()
     return 0
@@ -587,7 +588,7 @@ def run_gpu(args):
     line = {
         "metric": METRIC, "value": ms_step, "unit": "ms", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": False, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64" if prec == hb.HOM_FP64 else "f32+f64", "data": "synthetic",
+        "vs_baseline": None, "dtype": "f64" if prec == hb.HOM_FP64 else "f32+f32x2+f64", "data": "synthetic",
         "config": {"workload": WORKLOAD if args.workload == "spheres3d_N113" else WORKLOADS[args.workload],
                    "precision": args.precision, "tol": TOL,
                    "l2": "flushed between steps (256 MiB write, outside the timed region)",
@@ -792,9 +793,10 @@ def slab_flops(problem, nrhs: int) -> float:
     return family_flops_per_launch(problem, "slab", nrhs)
 
 
-def matvec_timings(hb, solver, problem, dev, stream, reps=20, precisions=("fp64", "fp32"), profile=None):
-    """Device time of one operator application on d fields, FP64 and FP32; with `profile`
-    a kernel family, its launches are timed too (in separate, instrumented applications)."""
+def matvec_timings(hb, solver, problem, dev, stream, reps=20, precisions=("fp64", "ff", "fp32"), profile=None):
+    """Device time of one operator application on d fields, FP64, float-float (FP64 fields,
+    the residual arithmetic of the mixed refinement) and FP32; with `profile` a kernel
+    family, its FP32 launches are timed too (in separate, instrumented applications)."""
     import torch
     ctx = solver.ctx
     info = hb.hom_problem_info(ctx, problem)
@@ -804,10 +806,12 @@ def matvec_timings(hb, solver, problem, dev, stream, reps=20, precisions=("fp64"
     shape = (d, d, int(problem.N[2]), int(problem.N[1]), (int(problem.N[0]) + 1) // 2)
     out = {}
     for name, prec, cdt, rdt in (("fp64", hb.HOM_FP64, torch.complex128, torch.float64),
+                                 ("ff", hb.HOM_FF, torch.complex128, torch.float32),
                                  ("fp32", hb.HOM_FP32, torch.complex64, torch.float32)):
         if name not in precisions:
             continue
-        coef = torch.empty((info["ncomp"],) + tuple(info["M"][::-1]), dtype=rdt, device=dev)
+        coef = torch.empty((info["ncomp"],) + tuple(info["M"][::-1]) + ((2,) if name == "ff" else ()), dtype=rdt,
+                           device=dev)
         hb.hom_coefficient(ctx, problem, 0, prec, coef.data_ptr(), ws.data_ptr(), nws, stream.cuda_stream)
         x = torch.randn(shape, dtype=cdt, device=dev)
         y = torch.empty_like(x)
@@ -828,12 +832,12 @@ def matvec_timings(hb, solver, problem, dev, stream, reps=20, precisions=("fp64"
         ms = e0.elapsed_time(e1) / n_rep
         flops = sum(family_flops_per_launch(problem, f, d) * (2 if f == "ypass" else 1)
                     for f in ("zpass", "ypass", "xpass", "final"))
-        nbytes = matvec_bytes(problem, 8 if name == "fp64" else 4)
+        nbytes = matvec_bytes(problem, 4 if name == "fp32" else 8)
         gbs = nbytes / (ms * 1e-3) / 1e9
         hbm = measured_peaks()["hbm_gbs"]
         out[name] = {"ms": ms, "matvecs_per_s": 1e3 / ms, "fft_tflops": flops / (ms * 1e-3) / 1e12, "fields": d,
                      "model_bytes": nbytes, "model_gbs": gbs, "model_hbm_frac": gbs / hbm}
-        if profile:
+        if profile and name == "fp32":
             hb.hom_profile_kernel(ctx, profile)
             for _ in range(n_rep):
                 apply()
@@ -880,6 +884,8 @@ def main():
     ap.add_argument("--workload", default="spheres3d_N113", choices=sorted(WORKLOADS))
     ap.add_argument("--matvec-only", action="store_true", help="operator applications only")
     ap.add_argument("--reps", type=int, default=20)
+    ap.add_argument("--matvec-precision", default="", choices=["", "fp64", "ff", "fp32"],
+                    help="with --matvec-only: that arithmetic alone (default: the inner solves' FP32, or FP64)")
     ap.add_argument("--batched-only", action="store_true", help="the batched workload only")
     ap.add_argument("--batch-n", type=int, default=256, help="cells in the batched workload")
     ap.add_argument("--batch-threads", type=int, default=0, help="fix the threads per CTA (no autotune)")

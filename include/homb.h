@@ -78,7 +78,10 @@ typedef enum {
 
 typedef enum { HOM_BOX = 0, HOM_BALL = 1 /* disk when d == 2 */ } hom_shape;
 typedef enum { HOM_FP64 = 0, HOM_MIXED = 1 /* FP32 inner CG, FP64 scalars/bounds */,
-               HOM_FP32 = 2 /* step-level calls only */ } hom_precision;
+               HOM_FP32 = 2 /* step-level calls only */,
+               HOM_FF = 3   /* hom_coefficient and hom_matvec only: float-float arithmetic
+                               (pairs of FP32, about 48 significant bits) on FP64 fields */
+} hom_precision;
 typedef enum { HOM_PRIMAL = 0 /* A, Gamma^E: upper bound */,
                HOM_DUAL = 1   /* A^{-1}, Gamma^J: lower bound */ } hom_side;
 
@@ -416,8 +419,9 @@ hom_status hom_step_workspace_size(hom_ctx* ctx, const hom_problem* prob, int32_
 /* Double-grid coefficient A_{2N-1}(x_j) = sum_{n in Z_{2N-1}} w^{jn} A_hat(n) (Eq. MBA_GA)
  * of the primal (A) or dual (A^{-1}) side from the closed-form inclusion
  * coefficients (Lemma bounds_for_matrix-inclusion). d_coef: real, coefficient
- * layout above, FP64 (precision HOM_FP64) or FP32 (HOM_FP32: computed in FP64,
- * rounded). */
+ * layout above, FP64 (precision HOM_FP64), FP32 (HOM_FP32: computed in FP64,
+ * rounded) or float-float (HOM_FF: computed in FP64, each value as two floats hi, lo
+ * with hi = fl32(a), lo = fl32(a - hi); 8 bytes a value). */
 hom_status hom_coefficient(hom_ctx* ctx, const hom_problem* prob, int32_t side,
                            int32_t precision, void* d_coef, void* d_workspace,
                            size_t workspace_bytes, void* stream);
@@ -430,7 +434,11 @@ hom_status hom_rhs(hom_ctx* ctx, const hom_problem* prob, int32_t side, int32_t 
 
 /* Galerkin operator on nrhs fields: d_out = Gamma P_N F_M (A_M/|M|) F_M^{-1} Pad(d_in)
  * (project = 1) or without Gamma (project = 0). d_coef from hom_coefficient in the
- * same precision; d_in / d_out half-spectrum fields [nrhs][d]... (must not alias). */
+ * same precision; d_in / d_out half-spectrum fields [nrhs][d]... (must not alias), double2
+ * for HOM_FP64 and HOM_FF, float2 for HOM_FP32. HOM_FF (odd grids, not the even-grid
+ * path) computes every transform, the coefficient product and Gamma in float-float
+ * arithmetic between FP64 input and output: the residual arithmetic of HOM_MIXED's
+ * refinement steps (hom_set_refine_arith). */
 hom_status hom_matvec(hom_ctx* ctx, const hom_problem* prob, int32_t side, int32_t precision,
                       int32_t project, int32_t nrhs, const void* d_coef, const void* d_in,
                       void* d_out, void* d_workspace, size_t workspace_bytes, void* stream);
@@ -509,6 +517,25 @@ hom_status hom_set_pipe_passes(hom_ctx* ctx, int32_t enable);
  * smaller one risks another FP64 refinement step; the bounds stay guaranteed either way.
  * c >= 0; c = 0 restores the default, 100. Applies to later calls on this context. */
 hom_status hom_set_inner_drift(hom_ctx* ctx, double c);
+/* Relative floor eta of the FP32 inner target of HOM_MIXED (a precision scheme of this
+ * library): an inner solve that starts from the FP64 residual r0 stops no lower than
+ * eta |r0|, the depth to which its FP32 recursive residual is trusted to follow the true
+ * one; below that a restart from a fresh FP64 residual takes over. 0 <= eta < 1; 0 restores
+ * the default, 1e-5. The bounds stay guaranteed for any eta; it only moves work between inner
+ * iterations and FP64 refinement steps. Applies to later calls on this context. */
+hom_status hom_set_inner_floor(hom_ctx* ctx, double eta);
+/* Arithmetic of the residual b - C x64 that every refinement step of HOM_MIXED evaluates
+ * (a precision scheme of this library): mode 1 FP64; mode 2 float-float, i.e. every
+ * transform pass in pairs of FP32 numbers (about 48 significant bits, error-free
+ * TwoSum / FMA product steps) between the FP64 iterate and the FP64 residual, on the FP32
+ * pipes (this GPU issues FP64 at under a sixtieth of the FP32 rate); mode 0, the default:
+ * float-float when the solve starts cold (x = 0) and its tolerance is at least 1e-12 |b|
+ * (then float-float rounding, about 1e-14 of |C x| ~ |b|, stays below a hundredth of the
+ * tolerance), FP64 otherwise. The iterate, the residual, the re-projection and the bound
+ * energies stay FP64 in memory either way, so the bounds stay guaranteed; mode 2 at a
+ * tolerance near 1e-14 |b| may stop on a stalled refinement (status 1). Applies to later
+ * calls on this context. */
+hom_status hom_set_refine_arith(hom_ctx* ctx, int32_t mode);
 
 /* Threads per CTA of the persistent batched kernel: 256 (two CTAs per SM), 512 or 1024
  * (one CTA per SM: more threads per cell, fewer cells at a time), or 0 (default: the

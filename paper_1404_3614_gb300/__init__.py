@@ -8,7 +8,7 @@ built library raises ImportError: there is no CPU fallback.
 from __future__ import annotations
 
 from . import binding
-from .binding import (HOM_BALL, HOM_BOX, HOM_DUAL, HOM_FP32, HOM_FP64, HOM_MIXED, HOM_PRIMAL,
+from .binding import (HOM_BALL, HOM_BOX, HOM_DUAL, HOM_FF, HOM_FP32, HOM_FP64, HOM_MIXED, HOM_PRIMAL,
                       HombError, hom_batched_workspace_size, hom_bounds, hom_bounds_batched, hom_coefficient, hom_create, hom_destroy, hom_energy,
                       hom_fft, hom_kernel_timing, hom_last_error, hom_matvec, hom_problem_info,
                       hom_profile_kernel, hom_rhs, hom_set_slab_pass, hom_step_workspace_size, hom_version,
@@ -19,7 +19,7 @@ __all__ = ["binding", "Bounds", "HombError", "hom_bounds", "hom_bounds_batched",
            "hom_destroy", "hom_energy", "hom_fft", "hom_kernel_timing", "hom_last_error",
            "hom_matvec", "hom_problem_info", "hom_profile_kernel", "hom_rhs", "hom_set_slab_pass",
            "hom_step_workspace_size", "hom_version", "hom_workspace_size", "make_opts",
-           "HOM_FP64", "HOM_MIXED", "HOM_FP32", "HOM_PRIMAL", "HOM_DUAL", "HOM_BOX", "HOM_BALL"]
+           "HOM_FP64", "HOM_MIXED", "HOM_FP32", "HOM_FF", "HOM_PRIMAL", "HOM_DUAL", "HOM_BOX", "HOM_BALL"]
 
 
 class Bounds:

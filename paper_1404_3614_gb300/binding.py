@@ -25,7 +25,7 @@ HOM_ERR_TIMEOUT = -5
 HOM_ERR_NOT_SPD_RESULT = -6
 
 HOM_BOX, HOM_BALL = 0, 1
-HOM_FP64, HOM_MIXED, HOM_FP32 = 0, 1, 2
+HOM_FP64, HOM_MIXED, HOM_FP32, HOM_FF = 0, 1, 2, 3
 HOM_PRIMAL, HOM_DUAL = 0, 1
 
 
@@ -124,6 +124,8 @@ def _load():
         "hom_set_pipe_passes": (i32, [vp, i32]),
         "hom_set_batch_warp_passes": (i32, [vp, i32]),
         "hom_set_inner_drift": (i32, [vp, C.c_double]),
+        "hom_set_inner_floor": (i32, [vp, C.c_double]),
+        "hom_set_refine_arith": (i32, [vp, i32]),
         "hom_energy_bounds": (i32, [vp, P(hom_problem), P(hom_opts), vp, sz, vp, dp, dp, dp, P(hom_report)]),
         "hom_net_save": (i32, [vp, P(hom_net_config), vp, C.c_char_p, vp]),
         "hom_net_load": (i32, [vp, C.c_char_p, P(vp)]),
@@ -471,6 +473,16 @@ def hom_set_pipe_passes(ctx, enable):
 def hom_set_inner_drift(ctx, c):
     """Drift coefficient c of the FP32 inner target of HOM_MIXED (0: the default)."""
     return check(ctx, lib.hom_set_inner_drift(ctx, float(c)))
+
+
+def hom_set_inner_floor(ctx, eta):
+    """Relative floor eta of the FP32 inner target of HOM_MIXED (0: the default, 1e-5)."""
+    return check(ctx, lib.hom_set_inner_floor(ctx, float(eta)))
+
+
+def hom_set_refine_arith(ctx, mode):
+    """Residual arithmetic of HOM_MIXED's refinement steps: 1 FP64, 2 float-float, 0 the default."""
+    return check(ctx, lib.hom_set_refine_arith(ctx, int(mode)))
 
 
 def hom_set_net_chunk(ctx, cells):

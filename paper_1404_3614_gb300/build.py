@@ -20,7 +20,7 @@ ROOT = os.path.dirname(HERE)
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-I", os.path.join(ROOT, "include")]
-SOURCES = ["kernels.cu", "passes_f64.cu", "passes_f32.cu", "batch.cu", "net.cu", "api.cu", "probe.cu"]
+SOURCES = ["kernels.cu", "passes_f64.cu", "passes_f32.cu", "passes_ff_pencil.cu", "passes_ff_final.cu", "passes_ff_xpass.cu", "batch.cu", "net.cu", "api.cu", "probe.cu"]
 
 
 def nvcc() -> str:

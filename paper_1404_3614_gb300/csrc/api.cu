@@ -68,6 +68,8 @@ struct hom_ctx {
   bool slab_on = true;   // fused y-x-y slab pass where it applies
   int zpipe_mask = 1;    // persistent pipelined FP32 z passes where they apply: 1 last pass, 2 z inverse
   double inner_drift = 0.0;   // drift coefficient of the FP32 inner target (0: default)
+  double inner_floor = 0.0;   // relative floor of the FP32 inner target (0: default)
+  int refine_arith = 0;       // arithmetic of the mixed residual: 0 default, 1 FP64, 2 float-float
   int sms = 0;           // SMs of the device (set at creation)
   int slab_warps = 0;     // warps per slab CTA chosen by the caller (0: automatic)
   int ypass_xc = 0;       // pencils per CTA of the operator's y passes (0: automatic)
@@ -100,6 +102,10 @@ struct hom_net {
 namespace {
 
 constexpr double kInnerDrift = 100.0;   // default drift coefficient of the FP32 inner target
+constexpr double kInnerFloor = 1e-5;    // default relative floor of the FP32 inner target
+constexpr bool kRefineFF = true;         // default arithmetic of the mixed residual: float-float (measured faster)
+constexpr double kFFResidRel = 1e-14;    // rounding of a float-float operator application relative
+                                         // to its output (measured 7.4e-15 on the 16-ball cell)
 constexpr int kVecBlocks = 304;   // 2 x 152 SMs for the elementwise CG kernels
 
 #define CK(expr)                                                                               \
@@ -378,13 +384,14 @@ void pack_sym(const double* A, int d, int ncomp, double* out) {  // A leading di
 // workspace layout
 // ---------------------------------------------------------------------------------
 struct Layout {
-  size_t tw64[3], tw32[3], incl, phase, sinc, coef64, coef32, x, r, p, q, x64, b64, r64, t1, t2,
+  size_t tw64[3], tw32[3], twff[3], incl, phase, sinc, coef64, coef32, x, r, p, q, x64, b64, r64, t1, t2,
       cg[2], cgo[2], partial, epart, eout, total;
   size_t bmp = 0, bmpD[2] = {0, 0}, bmptw[3] = {0, 0, 0};   // pixel image, its DFT buffers, twiddles
   size_t rrpart = 0;                                         // Rayleigh-Ritz partial sums
   size_t gs = 0, gD[2] = {0, 0}, gtw[3] = {0, 0, 0};         // GaNi samples, their DFT, twiddles
   int Mmax, maxblk, nblk_energy;
   size_t radtab = 0;            // radial factors of the ball groups (0 bytes: evaluated per frequency)
+  size_t coefff = 0;            // float-float coefficient of the mixed residual (0: none)
   int radgroups = 0, radlen = 0;
   size_t off = 0;
   size_t take(size_t bytes) {
@@ -407,6 +414,7 @@ Layout make_layout(const Geometry& g, int R, size_t elem, int mode) {
   for (int a = 0; a < 3; ++a) {
     L.tw64[a] = L.take((size_t)g.M[a] * 16);
     L.tw32[a] = L.take((size_t)g.M[a] * 8);
+    L.twff[a] = L.take((size_t)g.M[a] * 16);
   }
   const size_t ni = std::max<size_t>(g.incl.size(), 1);
   L.incl = L.take(2 * ni * sizeof(DevIncl));
@@ -452,6 +460,7 @@ Layout make_layout(const Geometry& g, int R, size_t elem, int mode) {
   if (mode == 0) {
     L.coef64 = L.take((size_t)g.ncomp * g.grid * 8);
     L.coef32 = elem == 8 ? L.take((size_t)g.ncomp * g.grid * 4) : 0;
+    L.coefff = elem == 8 ? L.take((size_t)g.ncomp * g.grid * 8) : 0;
     const size_t fb = (size_t)RC * g.field * elem;
     L.x = L.take(fb);
     L.r = L.take(fb);
@@ -466,7 +475,8 @@ Layout make_layout(const Geometry& g, int R, size_t elem, int mode) {
   L.cgo[0] = L.take(sizeof(CgScalars));
   L.cgo[1] = L.take(sizeof(CgScalars));
   const int X = g.d == 3 ? g.N[1] * g.Nh : g.Nh;
-  const int xc = std::max(1, std::min(final_xc_elem(g, 16), final_xc_elem(g, 8)));
+  const int xcff = pencil_xc<ffloat>(g.d == 3 ? g.M[2] : g.M[1], X, g.d);
+  const int xc = std::max(1, std::min(std::min(final_xc_elem(g, 16), final_xc_elem(g, 8)), xcff > 0 ? xcff : 1 << 30));
   L.maxblk = std::max(kVecBlocks, (X + xc - 1) / xc);
   L.partial = L.take((size_t)3 * L.maxblk * sizeof(double));
   L.rrpart = L.take((size_t)6 * kVecBlocks * sizeof(double));
@@ -479,14 +489,20 @@ Layout make_layout(const Geometry& g, int R, size_t elem, int mode) {
   return L;
 }
 
-void twiddles(int M, std::vector<double2>& w64, std::vector<float2>& w32) {
+void twiddles(int M, std::vector<double2>& w64, std::vector<float2>& w32, std::vector<ffloat2>* wff = nullptr) {
   w64.resize(M);
   w32.resize(M);
+  if (wff) wff->resize(M);
+  auto split = [](long double v) {   // nearest float-float: hi = fl32(v), lo = fl32(v - hi)
+    const float h = (float)v;
+    return ffloat(h, (float)(v - (long double)h));
+  };
   for (int j = 0; j < M; ++j) {
     const long double ang = -2.0L * 3.14159265358979323846264338327950288L * (long double)j / (long double)M;
     const long double c = std::cos(ang), s = std::sin(ang);
     w64[j] = make_double2((double)c, (double)s);
     w32[j] = make_float2((float)c, (float)s);
+    if (wff) (*wff)[j] = ffloat2{split(c), split(s)};
   }
 }
 
@@ -600,10 +616,12 @@ struct Runner {
       }
     std::vector<double2> w64;
     std::vector<float2> w32;
+    std::vector<ffloat2> wff;
     for (int a = 0; a < 3; ++a) {
-      twiddles(g.M[a], w64, w32);
+      twiddles(g.M[a], w64, w32, &wff);
       CK(h2d_copy(ctx, base + L.tw64[a], w64.data(), w64.size() * sizeof(double2), st));
       CK(h2d_copy(ctx, base + L.tw32[a], w32.data(), w32.size() * sizeof(float2), st));
+      CK(h2d_copy(ctx, base + L.twff[a], wff.data(), wff.size() * sizeof(ffloat2), st));
     }
     // inclusion tables for both sides: [side][j]
     const size_t n = g.incl.size();
@@ -814,8 +832,8 @@ struct Runner {
   template <typename T>
   hom_status matvec(const void* in, void* out, const void* coef, int project, CgScalars* cg,
                     const void* r_aux, const void* p_aux, int prologue, const void* bsub = nullptr) {
-    const size_t tw = sizeof(T) == 8 ? 0 : 1;
-    auto W = [&](int a) -> const void* { return base + (tw == 0 ? L.tw64[a] : L.tw32[a]); };
+    constexpr bool ff = is_ff<T>::value;   // float-float: in and out FP64, passes in FP32 pairs
+    auto W = [&](int a) -> const void* { return base + (ff ? L.twff[a] : sizeof(T) == 8 ? L.tw64[a] : L.tw32[a]); };
     const int C = g.d;
     const int Mx = g.M[0], My = g.M[1], Mz = g.M[2];
     const int Ny = g.N[1], Nz = g.N[2], Nh = g.Nh;
@@ -830,7 +848,7 @@ struct Runner {
       z.nslab = R * C; z.X = Ny * Nh; z.XC = pencil_xc<T>(Mz, z.X, 1);
       z.Pin = Nz; z.Pout = Mz; z.Nlog = Nz; z.dir = +1;
       z.slabs_per_rhs = C; z.slabs_per_comp = 1; z.C = C; z.prologue = prologue;
-      z.W = W(2); z.plan = g.plan[2]; z.cg = cg;
+      z.W = W(2); z.plan = g.plan[2]; z.cg = cg; z.in64 = ff;
       if (sizeof(T) == 4 && (ctx->zpipe_mask & 2))
         z.pgrid = zpipe_pad_grid(Mz, z.Pin, z.Pout, z.Nlog, z.dir, z.X, z.nslab, ctx->sms);
       if (z.XC < 1) return fail(ctx, HOM_ERR_INVALID_ARG, "grid too large for the shared-memory FFT");
@@ -838,17 +856,22 @@ struct Runner {
       ycur = T1;
     }
     const void* fin = T2;
-    if (g.d == 3 && g.ncomp == 1 && g.M[0] == g.M[1] && ctx->slab_on && slab_warps<T>(g.M[0], Nh) > 0) {
+    bool use_slab = false;
+    if constexpr (!ff)
+      use_slab = g.d == 3 && g.ncomp == 1 && g.M[0] == g.M[1] && ctx->slab_on && slab_warps<T>(g.M[0], Nh) > 0;
+    if (use_slab) {
       // fused inverse y, x row pass and forward y on each (rhs, comp, z) slab of T1
-      Prof pr(ctx, "slab", st);
-      SlabArgs sl{};
-      sl.in = T1; sl.out = T1; sl.coef = coef; sl.W = W(0); sl.cg = cg;
-      sl.nrc = R * C; sl.C = C; sl.Mz = Mz; sl.M = Mx; sl.Ny = Ny; sl.Nh = Nh;
-      sl.scale = 1.0 / (double)g.grid;
-      sl.warps = ctx->slab_warps;
-      sl.fault = cg ? &cg->fault : nullptr;
-      KL(launch_slab<T>(sl, st));
-      fin = T1;
+      if constexpr (!ff) {
+        Prof pr(ctx, "slab", st);
+        SlabArgs sl{};
+        sl.in = T1; sl.out = T1; sl.coef = coef; sl.W = W(0); sl.cg = cg;
+        sl.nrc = R * C; sl.C = C; sl.Mz = Mz; sl.M = Mx; sl.Ny = Ny; sl.Nh = Nh;
+        sl.scale = 1.0 / (double)g.grid;
+        sl.warps = ctx->slab_warps;
+        sl.fault = cg ? &cg->fault : nullptr;
+        KL(launch_slab<T>(sl, st));
+        fin = T1;
+      }
     } else {
     {
       Prof pr(ctx, "ypass", st);
@@ -859,7 +882,7 @@ struct Runner {
       y.Pin = Ny; y.Pout = My; y.Nlog = Ny; y.dir = +1;
       y.slabs_per_rhs = C * Mz; y.slabs_per_comp = Mz; y.C = C;
       y.prologue = g.d == 3 ? 0 : prologue;
-      y.W = W(1); y.plan = g.plan[1]; y.cg = cg;
+      y.W = W(1); y.plan = g.plan[1]; y.cg = cg; y.in64 = ff && g.d == 2;
       if (y.XC < 1) return fail(ctx, HOM_ERR_INVALID_ARG, "grid too large for the shared-memory FFT");
       KL(launch_pencil<T>(y, st));
     }
@@ -920,6 +943,14 @@ struct Runner {
     return std::min(pg, L.maxblk);
   }
   int final_pipe_xc() const { return (ctx->zpipe_mask & 4) ? 16 : 8;
+  }
+
+  // CTAs (partial sums per right-hand side) of the float-float last pass
+  int final_blocks_ff() const {
+    const int M = g.d == 3 ? g.M[2] : g.M[1];
+    const int X = g.d == 3 ? g.N[1] * g.Nh : g.Nh;
+    const int xc = pencil_xc<ffloat>(M, X, g.d);
+    return xc > 0 ? (X + xc - 1) / xc : 0;
   }
 
   int final_blocks(size_t elem) const {
@@ -1220,7 +1251,14 @@ hom_status Runner_solve_mixed(Runner& run, int side, const hom_opts& o, hom_repo
   double* coef64 = run.at<double>(L.coef64);
   if (run.gani) CKS(run.sample_coefficient(side, coef64));
   else CKS(run.build_coefficient(side, coef64));
-  KL(launch_convert_d2f(coef64, run.at<float>(L.coef32), (long long)g.ncomp * g.grid, st));
+  // the residual b - C x64 of every refinement step in float-float (FP64 data, FP32-pair
+  // arithmetic) or in FP64
+  bool ffres = (ctx->refine_arith == 0 ? kRefineFF : ctx->refine_arith == 2) && L.coefff != 0;
+  if (ffres)
+    KL(launch_convert_d2f_ff(coef64, run.at<float>(L.coef32), run.at<ffloat>(L.coefff), (long long)g.ncomp * g.grid,
+                             st));
+  else
+    KL(launch_convert_d2f(coef64, run.at<float>(L.coef32), (long long)g.ncomp * g.grid, st));
   const float* coef32 = run.at<float>(L.coef32);
   const long long n = (long long)R * g.d * g.field;
   double2* b64 = run.at<double2>(L.b64);
@@ -1232,7 +1270,7 @@ hom_status Runner_solve_mixed(Runner& run, int side, const hom_opts& o, hom_repo
   const int N3[3] = {g.N[0], g.N[1], g.N[2]};
   double* partial = run.at<double>(L.partial);
   const double tol = o.tol > 0 ? o.tol : 1e-8;
-  const int nfin32 = run.final_blocks(8), nfin64 = run.final_blocks(16);
+  const int nfin32 = run.final_blocks(8), nfin64 = run.final_blocks(16), nfinff = run.final_blocks_ff();
   // b in FP64: closed form, or for a pixel image and for GaNi the operator applied to the
   // constant field (x = 0 taken from `zero`), negated
   auto form_rhs = [&](double2* zero) -> hom_status {
@@ -1269,7 +1307,7 @@ hom_status Runner_solve_mixed(Runner& run, int side, const hom_opts& o, hom_repo
   }
   const int maxit = o.max_iter > 0 ? o.max_iter : ((o.max_iter == 0 && warm && user_start) ? 0 : 10000);
   const int every = o.check_every > 0 ? o.check_every : 8;
-  const double eta = 1e-5;
+  const double eta = ctx->inner_floor > 0.0 ? ctx->inner_floor : kInnerFloor;
   // The recursive FP32 residual of an inner solve (restarted from the FP64 residual) stays
   // within a few eps_32 |r_k| per step of the true one (measured on the 16-ball cell at
   // contrast 1000: equal to four digits); the inner solve aims at tol less c eps_32 |r0|
@@ -1280,6 +1318,15 @@ hom_status Runner_solve_mixed(Runner& run, int side, const hom_opts& o, hom_repo
   for (int outer_it = 0; outer_it < 30; ++outer_it) {
     CK(d2h_copy(ctx, ctx->host_cg, outer, sizeof(CgScalars), st));
     CK(cudaStreamSynchronize(st));
+    if (outer_it == 0 && ffres && ctx->refine_arith == 0) {
+      // the default keeps float-float residuals only while their rounding, about
+      // kFFResidRel |C x64| ~ kFFResidRel |b|, stays a hundredth of the tolerance: the first
+      // residual of a cold start is b itself; a warm start does not know |b| and keeps FP64
+      double b2 = 0.0;
+      for (int r = 0; r < R; ++r) b2 = std::max(b2, ctx->host_cg->rr[r]);
+      const double lim = 100.0 * kFFResidRel;
+      ffres = !warm && tol * tol >= lim * lim * b2;
+    }
     bool any = false;
     for (int r = 0; r < R; ++r) any = any || ctx->host_cg->active[r];
     if (!any || used >= maxit) break;
@@ -1314,8 +1361,10 @@ hom_status Runner_solve_mixed(Runner& run, int side, const hom_opts& o, hom_repo
     // from them without another pass over the double grid)
     KL(launch_promote_add(run.at<float2>(L.x), x64, n, st));
     KL(launch_project_promote<double>(x64, x64, R, g.d, g.N[1], g.N[2], g.Nh, g.invY, side, st));
-    CKS(run.matvec<double>(x64, r64, coef64, side + 1, outer, nullptr, nullptr, 0, b64));
-    KL(launch_outer_check(outer, partial, L.maxblk, nfin64, R, 0.25, st));
+    if (ffres) CKS(run.matvec<ffloat>(x64, r64, run.at<ffloat>(L.coefff), side + 1, outer, nullptr, nullptr, 0, b64));
+    else CKS(run.matvec<double>(x64, r64, coef64, side + 1, outer, nullptr, nullptr, 0, b64));
+    // (the float-float last pass runs the warp FFTs on larger chunks: fewer partial sums)
+    KL(launch_outer_check(outer, partial, L.maxblk, ffres ? nfinff : nfin64, R, 0.25, st));
     ++*matvecs;
   }
   CK(d2h_copy(ctx, ctx->host_cg, outer, sizeof(CgScalars), st));
@@ -2240,7 +2289,8 @@ hom_status hom_coefficient(hom_ctx* ctx, const hom_problem* prob, int32_t side, 
                            void* d_coef, void* d_ws, size_t ws_bytes, void* stream) {
   if (!ctx || !d_coef) return fail(ctx, HOM_ERR_INVALID_ARG, "NULL argument");
   if (side != 0 && side != 1) return fail(ctx, HOM_ERR_INVALID_ARG, "side must be 0 or 1");
-  if (precision != HOM_FP64 && precision != HOM_FP32) return fail(ctx, HOM_ERR_INVALID_ARG, "precision");
+  if (precision != HOM_FP64 && precision != HOM_FP32 && precision != HOM_FF)
+    return fail(ctx, HOM_ERR_INVALID_ARG, "precision");
   CKS(set_device(ctx));
   Geometry g;
   CKS(build_geometry(ctx, prob, g));
@@ -2250,10 +2300,13 @@ hom_status hom_coefficient(hom_ctx* ctx, const hom_problem* prob, int32_t side, 
   if (!d_ws || ws_bytes < run.L.total) return fail(ctx, HOM_ERR_WORKSPACE, "workspace too small");
   CKS(run.upload_tables());
   if (precision == HOM_FP64) return run.build_coefficient(side, static_cast<double*>(d_coef));
-  // FP32: build in FP64 into the buffer the last pass does not read, then round
+  // FP32 / float-float: build in FP64 into the buffer the last pass does not read, then round
   double* tmp = run.at<double>(g.d == 3 ? run.L.t2 : run.L.t1);
   CKS(run.build_coefficient(side, tmp));
-  KL(launch_convert_d2f(tmp, static_cast<float*>(d_coef), (long long)g.ncomp * g.grid, run.st));
+  if (precision == HOM_FF)
+    KL(launch_convert_d2f_ff(tmp, nullptr, static_cast<ffloat*>(d_coef), (long long)g.ncomp * g.grid, run.st));
+  else
+    KL(launch_convert_d2f(tmp, static_cast<float*>(d_coef), (long long)g.ncomp * g.grid, run.st));
   return HOM_OK;
 }
 
@@ -2292,7 +2345,8 @@ hom_status hom_matvec(hom_ctx* ctx, const hom_problem* prob, int32_t side, int32
   if (!ctx || !d_coef || !d_in || !d_out) return fail(ctx, HOM_ERR_INVALID_ARG, "NULL argument");
   if (d_in == d_out) return fail(ctx, HOM_ERR_INVALID_ARG, "d_in and d_out must not alias");
   if (side != 0 && side != 1) return fail(ctx, HOM_ERR_INVALID_ARG, "side must be 0 or 1");
-  if (precision != HOM_FP64 && precision != HOM_FP32) return fail(ctx, HOM_ERR_INVALID_ARG, "precision");
+  if (precision != HOM_FP64 && precision != HOM_FP32 && precision != HOM_FF)
+    return fail(ctx, HOM_ERR_INVALID_ARG, "precision");
   CKS(set_device(ctx));
   Geometry g;
   CKS(build_geometry(ctx, prob, g));
@@ -2305,6 +2359,8 @@ hom_status hom_matvec(hom_ctx* ctx, const hom_problem* prob, int32_t side, int32
   const int proj = project ? side + 1 : 0;
   if (precision == HOM_FP64)
     return run.matvec<double>(d_in, d_out, d_coef, proj, nullptr, nullptr, nullptr, 0);
+  if (precision == HOM_FF)
+    return run.matvec<ffloat>(d_in, d_out, d_coef, proj, nullptr, nullptr, nullptr, 0);
   return run.matvec<float>(d_in, d_out, d_coef, proj, nullptr, nullptr, nullptr, 0);
 }
 
@@ -2454,6 +2510,20 @@ hom_status hom_set_inner_drift(hom_ctx* ctx, double c) {
   if (!ctx) return HOM_ERR_INVALID_ARG;
   if (!(c >= 0.0) || !std::isfinite(c)) return fail(ctx, HOM_ERR_INVALID_ARG, "drift coefficient must be >= 0");
   ctx->inner_drift = c;
+  return HOM_OK;
+}
+
+hom_status hom_set_refine_arith(hom_ctx* ctx, int32_t mode) {
+  if (!ctx) return HOM_ERR_INVALID_ARG;
+  if (mode < 0 || mode > 2) return fail(ctx, HOM_ERR_INVALID_ARG, "refinement arithmetic: 0 default, 1 FP64, 2 float-float");
+  ctx->refine_arith = mode;
+  return HOM_OK;
+}
+
+hom_status hom_set_inner_floor(hom_ctx* ctx, double eta) {
+  if (!ctx) return HOM_ERR_INVALID_ARG;
+  if (!(eta >= 0.0 && eta < 1.0)) return fail(ctx, HOM_ERR_INVALID_ARG, "inner floor must be in [0, 1)");
+  ctx->inner_floor = eta;
   return HOM_OK;
 }
 

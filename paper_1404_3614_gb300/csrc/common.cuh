@@ -9,6 +9,10 @@ namespace homb {
 template <typename T> struct cplx_t;
 template <> struct cplx_t<double> { using type = double2; };
 template <> struct cplx_t<float> { using type = float2; };
+}  // namespace homb
+#include "ffloat.cuh"
+namespace homb {
+template <> struct cplx_t<ffloat> { using type = ffloat2; };
 template <typename T> using cpx = typename cplx_t<T>::type;
 
 template <typename T> __device__ __forceinline__ cpx<T> mk(T x, T y) { cpx<T> r; r.x = x; r.y = y; return r; }
@@ -653,13 +657,14 @@ __device__ __forceinline__ cpx<T>* cfft_from(cpx<T>* a, cpx<T>* b, int G, const 
 }
 
 // G contiguous pencils of compile-time length M (stride M), ping-pong between a and b.
-// FP32 uses the composite register radices (fewer shared-memory passes); FP64 keeps
+// FP32 and float-float use the composite register radices (fewer shared-memory passes, and
+// no twiddle products inside a prime-factor radix 15); FP64 keeps
 // radices 3 and 5, which need the fewest FP64 operations, except at M = 225 = 15 * 15, where
 // the radix-15 stages with the zero band pruned (bits 4 and 8) need fewer.
 constexpr int kBandM64 = 225;
 template <typename T, int M>
 __device__ __forceinline__ cpx<T>* cfft(cpx<T>* a, cpx<T>* b, int G, const cpx<T>* W, int dir, int prune = 0) {
-  return cfft_from<T, M, 0, (sizeof(T) == 4 || M == kBandM64)>(a, b, G, W, dir, prune);
+  return cfft_from<T, M, 0, (sizeof(T) == 4 || is_ff<T>::value || M == kBandM64)>(a, b, G, W, dir, prune);
 }
 
 // Prune bits valid for a length-M transform whose spectrum is nonzero (inverse) or needed

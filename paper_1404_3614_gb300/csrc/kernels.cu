@@ -767,6 +767,17 @@ __global__ void k_convert_d2f(const double* in, float* out, long long n) {
     out[i] = (float)in[i];
 }
 
+// FP64 -> FP32 (out, may be null) and the nearest float-float (hi = the FP32 value,
+// lo = fl32(x - hi)) in one pass
+__global__ void k_convert_d2f_ff(const double* in, float* out, ffloat* off, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const ffloat v = ff_from(in[i]);
+    if (out) out[i] = v.hi;
+    off[i] = v;
+  }
+}
+
 // ---------------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------------
@@ -1212,6 +1223,13 @@ cudaError_t launch_convert_d2f(const double* in, float* out, long long n, cudaSt
   long long blocks = (n + kThreads - 1) / kThreads;
   if (blocks > 152 * 32) blocks = 152 * 32;
   k_convert_d2f<<<(int)blocks, kThreads, 0, s>>>(in, out, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_convert_d2f_ff(const double* in, float* out, ffloat* off, long long n, cudaStream_t s) {
+  long long blocks = (n + kThreads - 1) / kThreads;
+  if (blocks > 152 * 32) blocks = 152 * 32;
+  k_convert_d2f_ff<<<(int)blocks, kThreads, 0, s>>>(in, out, off, n);
   return cudaGetLastError();
 }
 

@@ -26,6 +26,7 @@ struct PencilArgs {
   FftPlan plan;
   CgScalars* cg;   // may be null: no skipping
   int pgrid;       // > 0: the persistent pipelined z pass with this many CTAs (zpipe_pad_grid)
+  int in64;        // float-float passes: `in` holds FP64 (double2) data, converted on load
   FastDiv fd_XC;   // divides by XC (set by the launcher)
 };
 
@@ -288,6 +289,8 @@ cudaError_t launch_block_rayleigh_ritz(double2* x, double2* r, const double2* b,
 cudaError_t launch_energy_reduce(const double* partial, int nblk, int nrr, double* out,
                                  cudaStream_t s);
 cudaError_t launch_convert_d2f(const double* in, float* out, long long n, cudaStream_t s);
+// FP64 -> FP32 (out) and float-float (off) in one pass
+cudaError_t launch_convert_d2f_ff(const double* in, float* out, ffloat* off, long long n, cudaStream_t s);
 // x = c + b (x - a) for n doubles
 cudaError_t launch_affine(double* x, long long n, double a, double b, double c, cudaStream_t s);
 template <typename T>

@@ -40,11 +40,19 @@ __device__ __forceinline__ cpx<T>* fft_any(cpx<T>* a, cpx<T>* b, int G, const Ff
   else return fft_pencils<T>(a, b, G, plan.M, plan, W, dir);
 }
 
-// FP32 pencils of length 225 = 15 * 15 are transformed by warp-level in-register FFTs in
-// place (slab.cuh), with no ping-pong buffer (measured faster there; at 81 the shared-memory
-// Stockham passes stay ahead).
-template <typename T, int MT> constexpr int warp_fft_r() { return sizeof(T) == 4 && MT == 225 ? 15 : 0; }
-template <typename T> inline bool warp_fft_len(int M) { return sizeof(T) == 4 && M == 225; }
+// FP32 and float-float pencils of length 225 = 15 * 15 are transformed by warp-level
+// in-register FFTs in place (slab.cuh), with no ping-pong buffer (measured faster there; at 81
+// the shared-memory Stockham passes stay ahead). Float-float's long dependent chains of FP32
+// operations need the warp FFT's 30 busy lanes of 32: a block-level radix-15 stage keeps
+// only M / 15 threads a pencil busy.
+template <typename T, int MT> constexpr int warp_fft_r() {
+  return (sizeof(T) == 4 || is_ff<T>::value) && MT == 225 ? 15 : 0;
+}
+template <typename T> inline bool warp_fft_len(int M) { return (sizeof(T) == 4 || is_ff<T>::value) && M == 225; }
+// the float-float row pass at 225 runs the warp FFTs too (the FP32 row pass keeps its
+// shared-memory stages: the fused slab pass replaces it in 3D)
+template <typename T, int MT> constexpr int xpass_warp_r() { return is_ff<T>::value ? warp_fft_r<T, MT>() : 0; }
+template <typename T> inline bool xpass_warp_len(int M) { return is_ff<T>::value && M == 225; }
 
 template <typename T, int R>
 __device__ __forceinline__ void pencil_fft_inplace(cpx<T>* p, int l, const cpx<T>* Wt, int dir, bool on);
@@ -142,7 +150,11 @@ __global__ void __launch_bounds__(kPassThreads) k_pencil(PencilArgs a) {
         if (xx < XC) {
           p[u] = pp;
           gi[u] = (long long)pp * a.X + x0 + xx;
-          v[u] = pin[gi[u]];
+          if constexpr (is_ff<T>::value) {
+            v[u] = a.in64 ? ff2_from(reinterpret_cast<const double2*>(pin)[gi[u]]) : pin[gi[u]];
+          } else {
+            v[u] = pin[gi[u]];
+          }
           if (a.prologue == 1) r[u] = reinterpret_cast<const cpx<T>*>(a.aux)[(long long)s * a.in_slab + gi[u]];
         }
       }
@@ -226,7 +238,9 @@ __global__ void __launch_bounds__(kPassThreads) k_final(FinalArgs a) {
         const int xx = rem - p * a.XC;
         if (xx < XC) {
           dst[u] = (g * XC + xx) * M + p;
-          v[u] = __ldg(in + (long long)g * a.in_comp + (long long)p * a.X + x0 + xx);
+          const cpx<T>* src = in + (long long)g * a.in_comp + (long long)p * a.X + x0 + xx;
+          if constexpr (is_ff<T>::value) v[u] = *src;
+          else v[u] = __ldg(src);
         }
       }
     }
@@ -250,6 +264,13 @@ __global__ void __launch_bounds__(kPassThreads) k_final(FinalArgs a) {
   const cpx<T>* bsub = a.bsub ? reinterpret_cast<const cpx<T>*>(a.bsub) + (long long)rhs * C * a.out_comp
                               : nullptr;
   const int half = (a.Nlog - 1) / 2;
+  // float-float: the reciprocal cell lengths once per thread, so that xi = k / Y is one
+  // float-float product per component (k is exact in FP32)
+  T invYf[3];
+  if constexpr (is_ff<T>::value) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) invYf[c] = T(a.invY[c]);
+  }
   double acc = 0.0;
   // FP32: the p.Cp terms of up to 8 points in FP32, their sums in FP64 (FP64 instructions
   // issue at a small fraction of the FP32 rate)
@@ -289,7 +310,16 @@ __global__ void __launch_bounds__(kPassThreads) k_final(FinalArgs a) {
 #pragma unroll
     for (int c = 0; c < 3; ++c) u[c] = c < C && !nyq ? res[(c * XC + xx) * M + pos] : mk<T>(T(0), T(0));
     if (a.project) {
-      const T xi[3] = {T(kx * a.invY[0]), T(ky * a.invY[1]), T(kz * a.invY[2])};
+      T xi[3];
+      if constexpr (is_ff<T>::value) {
+        xi[0] = T((float)kx, 0.f) * invYf[0];
+        xi[1] = T((float)ky, 0.f) * invYf[1];
+        xi[2] = T((float)kz, 0.f) * invYf[2];
+      } else {
+        xi[0] = T(kx * a.invY[0]);
+        xi[1] = T(ky * a.invY[1]);
+        xi[2] = T(kz * a.invY[2]);
+      }
       T n2 = T(0);
       cpx<T> dot = mk<T>(T(0), T(0));
 #pragma unroll
@@ -310,6 +340,26 @@ __global__ void __launch_bounds__(kPassThreads) k_final(FinalArgs a) {
             u[c] = a.project == 1 ? ge : sub<T>(u[c], ge);
           }
       }
+    }
+    if constexpr (is_ff<T>::value) {
+      // float-float passes write FP64: C u, or the residual b - C u with b in FP64 (no CG
+      // direction: the launcher rejects aux)
+      const double2* b64 = reinterpret_cast<const double2*>(bsub);
+      double2* o64 = reinterpret_cast<double2*>(out);
+      double sq = 0.0;
+#pragma unroll
+      for (int c = 0; c < 3; ++c)
+        if (c < C) {
+          double2 w = ff2_to(u[c]);
+          if (b64) {
+            const double2 bb = b64[(long long)c * a.out_comp + oi];
+            w = make_double2(bb.x - w.x, bb.y - w.y);
+            sq += w.x * w.x + w.y * w.y;
+          }
+          o64[(long long)c * a.out_comp + oi] = w;
+        }
+      if (b64) acc += (kx == 0 ? 1.0 : 2.0) * sq;
+      continue;
     }
     if (bsub) {
       double sq = 0.0;
@@ -382,6 +432,89 @@ __device__ __forceinline__ void apply_coef(const T* coef, long long gi, long lon
   }
 }
 
+// mode-0 row pass with warp-owned register FFTs (float-float at M = R * R): the pair
+// pencils Z = X_a + i X_b are formed straight from the global rows (Z(k) and Z(M - k) from
+// X_a(k), X_b(k): no staging copy), transformed in place, multiplied by the coefficient,
+// transformed back and split. A: [npair][M] after the twiddles Ws [R][R].
+template <typename T, int R>
+__device__ __forceinline__ void xpass_warp(const XArgs& a, cpx<T>* Ws, cpx<T>* A, int p0, int YB, int rhs) {
+  constexpr int M = R * R;
+  const int rpp = a.fd_rpp.d;
+  const int nrow = YB * rpp;
+  const int npair = (nrow + 1) / 2;
+  const int Nin = a.Nin;
+  const cpx<T>* in = reinterpret_cast<const cpx<T>*>(a.in);
+  auto row_off = [&](int row) -> long long {
+    const int yy = a.fd_rpp.div(row);
+    return (long long)(rhs * a.C + row - yy * rpp) * a.comp_stride + (long long)(p0 + yy) * Nin;
+  };
+  stage_twiddles_kl<T, R>(Ws, a.W);
+  const bool bin = zero_band_free(M, 2 * Nin - 1);
+  for (int t = threadIdx.x; t < npair * Nin; t += blockDim.x) {
+    const int pp = a.fd_Nin.div(t);
+    const int k = t - pp * Nin;
+    const int r0 = 2 * pp;
+    cpx<T> xa = in[row_off(r0) + k];
+    cpx<T> xb = r0 + 1 < nrow ? in[row_off(r0 + 1) + k] : mk<T>(T(0), T(0));
+    if (k == 0) {
+      xa.y = T(0);
+      xb.y = T(0);
+    }
+    cpx<T>* z = A + (size_t)pp * M;
+    z[k] = mk<T>(xa.x - xb.y, xa.y + xb.x);                    // X_a(k) + i X_b(k)
+    if (k > 0) z[M - k] = mk<T>(xa.x + xb.y, xb.x - xa.y);     // conj(X_a(k)) + i conj(X_b(k))
+  }
+  // the positions between the two ends that the inverse reads: zero (with the zero band,
+  // the lane rows ZeroBand<R>::lo..hi, positions R lo .. R hi + R - 1, are not read)
+  const int gap = M - 2 * Nin + 1;
+  for (int t = threadIdx.x; t < npair * gap; t += blockDim.x) {
+    const int pp = t / gap;
+    const int k = Nin + (t - pp * gap);
+    if (!(bin && k >= R * ZeroBand<R>::lo && k < R * (ZeroBand<R>::hi + 1))) A[(size_t)pp * M + k] = mk<T>(T(0), T(0));
+  }
+  __syncthreads();
+  fft_warp_all<T, R>(A, npair, Ws, +1, bin ? 1 : 0);
+  const T* coef = reinterpret_cast<const T*>(a.coef);
+  const long long cstride = (long long)a.planes * M;
+  const int C = a.C;
+  const T scale = T(a.scale);
+  for (int t = threadIdx.x; t < YB * M; t += blockDim.x) {
+    const int yy = t / M;
+    const int x = t - yy * M;
+    T u[3], v[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+      if (c < C) {
+        const int row = yy * C + c;
+        const cpx<T> z = A[(row >> 1) * M + x];
+        u[c] = (row & 1) ? z.y : z.x;
+      }
+    apply_coef<T>(coef, (long long)(p0 + yy) * M + x, cstride, a.ncomp, C, u, v, scale);
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+      if (c < C) {
+        const int row = yy * C + c;
+        if (row & 1) A[(row >> 1) * M + x].y = v[c];
+        else A[(row >> 1) * M + x].x = v[c];
+      }
+  }
+  __syncthreads();
+  fft_warp_all<T, R>(A, npair, Ws, -1, zero_band_free(M, 2 * a.Nout - 1) ? 2 : 0);
+  cpx<T>* out = reinterpret_cast<cpx<T>*>(a.out);
+  const int Nout = a.Nout;
+  for (int t = threadIdx.x; t < nrow * Nout; t += blockDim.x) {
+    const int row = a.fd_Nout.div(t);
+    const int k = t - row * Nout;
+    const int pp = row >> 1;
+    const cpx<T> zk = A[pp * M + k];
+    const cpx<T> zm = A[pp * M + (k == 0 ? 0 : M - k)];
+    cpx<T> X;
+    if ((row & 1) == 0) X = mk<T>(T(0.5) * (zk.x + zm.x), T(0.5) * (zk.y - zm.y));
+    else X = mk<T>(T(0.5) * (zk.y + zm.y), T(-0.5) * (zk.x - zm.x));
+    out[row_off(row) + k] = X;
+  }
+}
+
 template <typename T, int MT>
 __global__ void __launch_bounds__(kPassThreads) k_xpass(XArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -395,6 +528,12 @@ __global__ void __launch_bounds__(kPassThreads) k_xpass(XArgs a) {
     if (a.cg != nullptr && !a.cg->active[rhs]) return;
   } else if (a.mode == 2) {
     comp0 = blockIdx.y;
+  }
+  constexpr int WX = xpass_warp_r<T, MT>();
+  if constexpr (WX > 0) {   // mode 0 only (the launcher rejects the others)
+    cpx<T>* Ws = reinterpret_cast<cpx<T>*>(smem);
+    xpass_warp<T, WX>(a, Ws, Ws + M, p0, YB, rhs);
+    return;
   }
   const int nrow = YB * rpp;
   const int npair = (nrow + 1) / 2;
@@ -449,6 +588,7 @@ __global__ void __launch_bounds__(kPassThreads) k_xpass(XArgs a) {
   const long long cstride = (long long)a.planes * M;
   if (a.mode == 0) {
     const int C = a.C;
+    const T scale = T(a.scale);
     for (int t = threadIdx.x; t < YB * M; t += blockDim.x) {
       const int yy = t / M;
       const int x = t - yy * M;
@@ -460,7 +600,7 @@ __global__ void __launch_bounds__(kPassThreads) k_xpass(XArgs a) {
           const cpx<T> z = res[(row >> 1) * M + x];
           u[c] = (row & 1) ? z.y : z.x;
         }
-      apply_coef<T>(coef, (long long)(p0 + yy) * M + x, cstride, a.ncomp, C, u, v, T(a.scale));
+      apply_coef<T>(coef, (long long)(p0 + yy) * M + x, cstride, a.ncomp, C, u, v, scale);
 #pragma unroll
       for (int c = 0; c < 3; ++c)
         if (c < C) {
@@ -593,6 +733,17 @@ template <typename T> int pencil_xc(int M, int X, int C) {
 template <typename T> int xpass_yb(int M, int rpp, int planes) {
   const size_t sz = sizeof(cpx<T>);
   const size_t fixed = M * sz + 512;
+  if (xpass_warp_len<T>(M)) {
+    // warp FFTs: at most one round of pair pencils, 2 per warp (30 of 32 lanes), and one
+    // buffer of pairs (no staging copy, no ping-pong)
+    long long yb = (2LL * (kPassThreads / 32) * (32 / 15)) / rpp;
+    if (yb < 1) yb = 1;
+    while (yb > 1 && fixed + (size_t)((yb * rpp + 1) / 2) * M * sz > kPassSmemMax) --yb;
+    if (fixed + (size_t)((yb * rpp + 1) / 2) * M * sz > kPassSmemMax) return 0;
+    if (yb > planes) yb = planes;
+    const long long nch = (planes + yb - 1) / yb;
+    return (int)((planes + nch - 1) / nch);
+  }
   const long long npmax =
       kPassSmemBudget > fixed ? (long long)((kPassSmemBudget - fixed) / (2 * (size_t)(M + 1) * sz)) : 0;
   long long yb = (2 * npmax) / rpp;
@@ -634,8 +785,11 @@ template <typename T, int MT> cudaError_t launch_final_m(FinalArgs a, cudaStream
 template <typename T, int MT> cudaError_t launch_xpass_m(XArgs a, int grid_y, cudaStream_t s) {
   const int rpp = a.mode == 0 ? a.C : (a.mode == 1 ? a.R * a.C : 1);
   const int npair = (a.YB * rpp + 1) / 2;
-  const size_t smem = (size_t)a.M * sizeof(cpx<T>) + 2 * (size_t)npair * (a.M + 1) * sizeof(cpx<T>) +
-                      32 * sizeof(double);
+  constexpr bool warp = xpass_warp_r<T, MT>() > 0;
+  if (warp && a.mode != 0) return cudaErrorInvalidValue;
+  const size_t smem = warp ? (size_t)a.M * sizeof(cpx<T>) * (1 + (size_t)npair)
+                           : (size_t)a.M * sizeof(cpx<T>) + 2 * (size_t)npair * (a.M + 1) * sizeof(cpx<T>) +
+                                 32 * sizeof(double);
   static std::atomic<int> cache[kAttrDevices] = {};
   cudaError_t e = smem_attr(k_xpass<T, MT>, smem, cache);
   if (e != cudaSuccess) return e;
@@ -698,6 +852,7 @@ template <typename T> cudaError_t launch_pencil(const PencilArgs& a0, cudaStream
 }
 
 template <typename T> cudaError_t launch_final(const FinalArgs& a0, cudaStream_t s) {
+  if (is_ff<T>::value && a0.aux != nullptr) return cudaErrorInvalidValue;   // FP64 output only
   FinalArgs a = a0;
   a.fd_XC = FastDiv((uint32_t)a.XC);
   a.fd_per = FastDiv((uint32_t)(a.M * a.XC));

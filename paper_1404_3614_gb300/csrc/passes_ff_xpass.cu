@@ -1,0 +1,8 @@
+// Operator pass kernels, float-float instantiations of the xpass pass (the FP64-accurate
+// residual of the mixed-precision refinement on the FP32 pipes; one pass per translation
+// unit, so that the three compile in parallel).
+#include "passes.cuh"
+namespace homb {
+template cudaError_t launch_xpass<ffloat>(const XArgs&, int, cudaStream_t);
+template int xpass_yb<ffloat>(int, int, int);
+}  // namespace homb

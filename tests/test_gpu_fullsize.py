@@ -101,6 +101,39 @@ def test_inner_target_trades_iterations_not_accuracy(hb):
         s.close()
 
 
+@pytest.mark.parametrize("name,maker,tol", [
+    ("cube3d_N41", lambda: ms.cube_inclusion_3d(), 1e-8),
+    ("spheres3d_N113", lambda: ms.random_spheres_3d(0, N=113), 1e-5),
+])
+def test_refinement_residual_float_float_matches_fp64(hb, name, maker, tol):
+    """The residual b - C x64 of every refinement step of a mixed solve, evaluated in
+    float-float (hom_set_refine_arith 2) and in FP64 (1): both meet the oracle's bounds (1e-10
+    on the cube cell at tol 1e-8, 1e-6 on the 16-ball cell at tol 1e-5), take the same inner
+    iterations (within one: the demoted FP32 residuals may differ in a last bit), and their
+    bounds agree to 1e-11 (float-float rounding, about 1e-14 of |b| a residual, lies far below
+    these tolerances; at 1e-7 on the 16-ball cell it does not, and the default takes FP64
+    there)."""
+    gold = GOLD[name]
+    p = maker()
+    s = hb.Bounds(0)
+    try:
+        with pytest.raises(hb.HombError):
+            hb.binding.hom_set_refine_arith(s.ctx, 3)
+        outs = {}
+        for mode in (1, 2):
+            hb.binding.hom_set_refine_arith(s.ctx, mode)
+            out = s(p, precision=hb.HOM_MIXED, tol=tol)
+            assert out["status"] == 0
+            check(out, gold, 1e-10 if name == "cube3d_N41" else 1e-6)
+            outs[mode] = out
+    finally:
+        s.close()
+    it1, it2 = np.asarray(outs[1]["report"]["iters"]), np.asarray(outs[2]["report"]["iters"])
+    assert np.abs(it1 - it2).max() <= 1, (it1, it2)
+    for key in ("upper", "lower"):
+        assert rel(outs[2][key], outs[1][key]) <= 1e-11, (key, rel(outs[2][key], outs[1][key]))
+
+
 @pytest.mark.parametrize("cluster", [0, 4])
 def test_benchmark_batch_large_cells_match_oracle(hb, solver, cluster):
     """Cells of the 256-cell batch with N = 113 (seeds 2, 6) and N = 203 (seeds 5, 10),

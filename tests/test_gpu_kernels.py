@@ -135,9 +135,13 @@ def test_matvec_matches_oracle(hb, ctx, name, side, project):
     fields = [random_real_field(rng, d, N) for _ in range(d)]
     ref = np.stack([full_to_half(op.apply(u, project=bool(project)), d) for u in fields])
     uin = np.stack([full_to_half(u, d) for u in fields])
+    # HOM_FF: float-float arithmetic (about 48 bits) between FP64 input and output, the
+    # coefficient as (hi, lo) float pairs; its bar is FP64's
     for prec, cdt, rdt, tol in ((hb.HOM_FP64, torch.complex128, torch.float64, 1e-12),
+                                (hb.HOM_FF, torch.complex128, torch.float32, 1e-12),
                                 (hb.HOM_FP32, torch.complex64, torch.float32, 5e-6)):
-        coef = torch.empty((info["ncomp"],) + tuple(info["M"][:d][::-1]), dtype=rdt, device="cuda")
+        cshape = (info["ncomp"],) + tuple(info["M"][:d][::-1]) + ((2,) if prec == hb.HOM_FF else ())
+        coef = torch.empty(cshape, dtype=rdt, device="cuda")
         hb.hom_coefficient(ctx, p, side, prec, coef.data_ptr(), ws.data_ptr(), nws)
         x = dev(uin.astype(np.complex128)).to(cdt)
         y = torch.zeros_like(x)
