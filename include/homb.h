@@ -529,7 +529,7 @@ hom_status hom_set_inner_floor(hom_ctx* ctx, double eta);
  * transform pass in pairs of FP32 numbers (about 48 significant bits, error-free
  * TwoSum / FMA product steps) between the FP64 iterate and the FP64 residual, on the FP32
  * pipes (this GPU issues FP64 at under a sixtieth of the FP32 rate); mode 0, the default:
- * float-float when the solve starts cold (x = 0) and its tolerance is at least 1e-12 |b|
+ * float-float when the solve starts cold (x = 0) and its tolerance is at least 2e-12 |b|
  * (then float-float rounding, about 1e-14 of |C x| ~ |b|, stays below a hundredth of the
  * tolerance), FP64 otherwise. The iterate, the residual, the re-projection and the bound
  * energies stay FP64 in memory either way, so the bounds stay guaranteed; mode 2 at a

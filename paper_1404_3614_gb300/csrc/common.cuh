@@ -29,6 +29,20 @@ template <typename T> __device__ __forceinline__ cpx<T> mulc(cpx<T> a, cpx<T> b,
   T by = conjb ? -b.y : b.y;
   return mk<T>(fma(a.x, b.x, -a.y * by), fma(a.x, by, a.y * b.x));
 }
+// A value as stored between transform stages: float-float pairs renormalised there (their
+// sums and products do not renormalise, and a low part left to grow through a whole chain
+// of stages would make the rounding error grow with the square of its depth); FP32 and FP64
+// values pass unchanged.
+template <typename T> __device__ __forceinline__ cpx<T> st_norm(cpx<T> v) {
+  if constexpr (is_ff<T>::value) {
+    cpx<T> r;
+    r.x = ff_norm(v.x);
+    r.y = ff_norm(v.y);
+    return r;
+  } else {
+    return v;
+  }
+}
 // i * a  (s = +1) or -i * a (s = -1)
 template <typename T> __device__ __forceinline__ cpx<T> rot(cpx<T> a, int s) {
   return s > 0 ? mk<T>(-a.y, a.x) : mk<T>(a.y, -a.x);
@@ -431,7 +445,7 @@ __device__ __forceinline__ void stage_bfly(const cpx<T>* __restrict__ src, cpx<T
   else dftR<T, R>(v, W, M, dir);
   const int base = (j / Ns) * Ns * R + k;
 #pragma unroll
-  for (int q = 0; q < R; ++q) dst[base + q * Ns] = v[q];
+  for (int q = 0; q < R; ++q) dst[base + q * Ns] = st_norm<T>(v[q]);
 }
 
 // Runtime radix (2 or a prime above 13) straight from shared memory: output s of butterfly j,
@@ -452,7 +466,7 @@ __device__ void stage_out_generic(const cpx<T>* __restrict__ src, cpx<T>* __rest
     const cpx<T> vq = mulc<T>(src[j + q * nb], W[q * tstep], dir > 0);
     acc = add<T>(acc, mulc<T>(vq, W[ws * step], dir > 0));
   }
-  dst[base + s * Ns] = acc;
+  dst[base + s * Ns] = st_norm<T>(acc);
 }
 
 // G pencils of length M at a + g*ld (ping-pong with b, same strides). The CTA runs
@@ -519,7 +533,7 @@ __device__ __forceinline__ void cbfly(const cpx<T>* __restrict__ src, cpx<T>* __
   dft_reg<T, R>(v, dir);
   const int base = (j / Ns) * Ns * R + k;
 #pragma unroll
-  for (int q = 0; q < R; ++q) dst[base + q * Ns] = v[q];
+  for (int q = 0; q < R; ++q) dst[base + q * Ns] = st_norm<T>(v[q]);
 }
 
 // Radix-3 butterflies of a first stage whose middle inputs are all zero (a zero-padded
@@ -572,7 +586,7 @@ __device__ __forceinline__ cpx<T>* cfft_from(cpx<T>* a, cpx<T>* b, int G, const 
           dft3_mid_in0<T>(v, dir);
           cpx<T>* dst = b + g * M;
 #pragma unroll
-          for (int q = 0; q < 3; ++q) dst[3 * j + q] = v[q];   // Ns = 1: base = 3 j
+          for (int q = 0; q < 3; ++q) dst[3 * j + q] = st_norm<T>(v[q]);   // Ns = 1: base = 3 j
         }
         __syncthreads();
         return cfft_from<T, M, S + 1, BIG>(b, a, G, W, dir, prune);
@@ -591,7 +605,7 @@ __device__ __forceinline__ cpx<T>* cfft_from(cpx<T>* a, cpx<T>* b, int G, const 
           dft15_zin<T>(v, dir);
           cpx<T>* dst = b + g * M;
 #pragma unroll
-          for (int q = 0; q < 15; ++q) dst[15 * j + q] = v[q];   // Ns = 1: base = 15 j
+          for (int q = 0; q < 15; ++q) dst[15 * j + q] = st_norm<T>(v[q]);   // Ns = 1: base = 15 j
         }
         __syncthreads();
         return cfft_from<T, M, S + 1, BIG>(b, a, G, W, dir, prune);
@@ -617,7 +631,7 @@ __device__ __forceinline__ cpx<T>* cfft_from(cpx<T>* a, cpx<T>* b, int G, const 
           const int base = (j / Ns) * Ns * R + k;
 #pragma unroll
           for (int q = 0; q < 15; ++q)
-            if (!ZeroBand<15>::in(q)) dst[base + q * Ns] = v[q];
+            if (!ZeroBand<15>::in(q)) dst[base + q * Ns] = st_norm<T>(v[q]);
         }
         __syncthreads();
         return b;
@@ -639,8 +653,8 @@ __device__ __forceinline__ cpx<T>* cfft_from(cpx<T>* a, cpx<T>* b, int G, const 
           dft3_skip_out1<T>(v, dir);
           cpx<T>* dst = b + g * M;
           const int base = (j / Ns) * Ns * R + k;
-          dst[base] = v[0];
-          dst[base + 2 * Ns] = v[2];
+          dst[base] = st_norm<T>(v[0]);
+          dst[base + 2 * Ns] = st_norm<T>(v[2]);
         }
         __syncthreads();
         return b;

@@ -70,7 +70,7 @@ __device__ __forceinline__ void pencil_fft_inplace(cpx<T>* p, int l, const cpx<T
   __syncwarp();
   if (on) {
 #pragma unroll
-    for (int k = 0; k < R; ++k) p[l + R * k] = v[k];
+    for (int k = 0; k < R; ++k) p[l + R * k] = st_norm<T>(v[k]);
   }
   __syncwarp();
 #pragma unroll
@@ -79,7 +79,7 @@ __device__ __forceinline__ void pencil_fft_inplace(cpx<T>* p, int l, const cpx<T
   __syncwarp();
   if (on) {
 #pragma unroll
-    for (int k = 0; k < R; ++k) p[l + R * k] = v[k];
+    for (int k = 0; k < R; ++k) p[l + R * k] = st_norm<T>(v[k]);
   }
   __syncwarp();
 }
@@ -94,7 +94,7 @@ __device__ __forceinline__ void fft_finish(cpx<T>* v, cpx<T>* S, int l, const cp
   __syncwarp();
   if (own) {
 #pragma unroll
-    for (int k = 0; k < R; ++k) S[l + R * k] = v[k];
+    for (int k = 0; k < R; ++k) S[l + R * k] = st_norm<T>(v[k]);
   }
   __syncwarp();
 #pragma unroll
@@ -158,7 +158,7 @@ __device__ __forceinline__ void pencil_fft_fwd_trunc(cpx<T>* p, int l, const cpx
   __syncwarp();
   if (on) {
 #pragma unroll
-    for (int k = 0; k < R; ++k) p[l + R * k] = v[k];
+    for (int k = 0; k < R; ++k) p[l + R * k] = st_norm<T>(v[k]);
   }
   __syncwarp();
 #pragma unroll
@@ -168,7 +168,7 @@ __device__ __forceinline__ void pencil_fft_fwd_trunc(cpx<T>* p, int l, const cpx
   if (on) {
 #pragma unroll
     for (int k = 0; k < R; ++k)
-      if (!ZeroBand<R>::in(k)) p[l + R * k] = v[k];
+      if (!ZeroBand<R>::in(k)) p[l + R * k] = st_norm<T>(v[k]);
   }
   __syncwarp();
 }
@@ -187,7 +187,7 @@ __device__ __forceinline__ void pencil_fft_pad_inv(cpx<T>* p, int l, const cpx<T
   __syncwarp();
   if (on) {
 #pragma unroll
-    for (int k = 0; k < R; ++k) p[l + R * k] = v[k];
+    for (int k = 0; k < R; ++k) p[l + R * k] = st_norm<T>(v[k]);
   }
   __syncwarp();
 #pragma unroll
@@ -196,7 +196,7 @@ __device__ __forceinline__ void pencil_fft_pad_inv(cpx<T>* p, int l, const cpx<T
   __syncwarp();
   if (on) {
 #pragma unroll
-    for (int k = 0; k < R; ++k) p[l + R * k] = v[k];
+    for (int k = 0; k < R; ++k) p[l + R * k] = st_norm<T>(v[k]);
   }
   __syncwarp();
 }
@@ -209,7 +209,7 @@ __device__ __forceinline__ void fft_finish_zout(cpx<T>* v, cpx<T>* S, int l, con
   __syncwarp();
   if (own) {
 #pragma unroll
-    for (int k = 0; k < R; ++k) S[l + R * k] = v[k];
+    for (int k = 0; k < R; ++k) S[l + R * k] = st_norm<T>(v[k]);
   }
   __syncwarp();
 #pragma unroll
