@@ -10,6 +10,7 @@
 // task is independent. Data live in a per-CTA global scratch slot (L2-resident for the
 // small grids) and pass through shared memory in chunks of FFT pencils.
 #include <atomic>
+#include <type_traits>
 #include <cooperative_groups.h>
 #include <math.h>
 
@@ -81,8 +82,12 @@ __device__ __noinline__ cpx<T>* fft_sched(cpx<T>* a, cpx<T>* b, int G, int M, co
 template <typename T>
 __device__ __forceinline__ cpx<T>* fft_dyn(cpx<T>* a, cpx<T>* b, int G, int M, const FftPlan& plan,
                                            const cpx<T>* W, int dir) {
-  const bool big = plan.sched == 0 ? sizeof(T) == 4 : plan.sched == 2;
-  return big ? fft_sched<T, true>(a, b, G, M, plan, W, dir) : fft_sched<T, false>(a, b, G, M, plan, W, dir);
+  if constexpr (is_ff<T>::value) {   // float-float: the register radices only
+    return fft_sched<T, true>(a, b, G, M, plan, W, dir);
+  } else {
+    const bool big = plan.sched == 0 ? sizeof(T) == 4 : plan.sched == 2;
+    return big ? fft_sched<T, true>(a, b, G, M, plan, W, dir) : fft_sched<T, false>(a, b, G, M, plan, W, dir);
+  }
 }
 
 // Column pass over a list of fields: in field f (base in + f*in_fs) a column x holds Pin
@@ -267,10 +272,10 @@ __device__ __noinline__ void row_pass(int mode, cpx<U>* rows, long long field_st
         U a0, a1, b0, b1;
         coef_apply<U>(coef, (long long)y * M + x, cs, ncomp, z0.x, z0.y, &a0, &a1, U(1));
         coef_apply<U>(coef, (long long)y * M + x, cs, ncomp, z1.x, z1.y, &b0, &b1, U(1));
-        acc[0] += (double)z0.x * a0 + (double)z0.y * a1;   // W[0][0]
-        acc[1] += (double)z0.x * b0 + (double)z0.y * b1;   // W[0][1]
-        acc[2] += (double)z1.x * a0 + (double)z1.y * a1;   // W[1][0]
-        acc[3] += (double)z1.x * b0 + (double)z1.y * b1;   // W[1][1]
+        acc[0] += (double)z0.x * (double)a0 + (double)z0.y * (double)a1;   // W[0][0]
+        acc[1] += (double)z0.x * (double)b0 + (double)z0.y * (double)b1;   // W[0][1]
+        acc[2] += (double)z1.x * (double)a0 + (double)z1.y * (double)a1;   // W[1][0]
+        acc[3] += (double)z1.x * (double)b0 + (double)z1.y * (double)b1;   // W[1][1]
       }
     } else {
       for (int t = threadIdx.x; t < P * M; t += blockDim.x) {
@@ -381,6 +386,15 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 2 : 1) k_batch(BArgs a) {
   double2* Ad = reinterpret_cast<double2*>(smem + tw_bytes);
   double2* Bd = Ad + a.cap;
   const bool f32 = sizeof(T) == 4;
+  // Arithmetic of the coefficient's inverse transform and of the energies' transforms: FP64,
+  // or for FP32 iterations float-float (pairs of FP32 on the FP32 pipes, about 48 bits, in
+  // the same 16-byte complex slots: the FP64 tables, scratch and chunk buffers are reused)
+  using E = typename std::conditional<sizeof(T) == 4, ffloat, double>::type;
+  constexpr bool eff = is_ff<E>::value;
+  cpx<E>* W0e = reinterpret_cast<cpx<E>*>(W0d);
+  cpx<E>* W1e = reinterpret_cast<cpx<E>*>(W1d);
+  cpx<E>* Ae = reinterpret_cast<cpx<E>*>(Ad);
+  cpx<E>* Be = reinterpret_cast<cpx<E>*>(Bd);
   // Tasks [0, ncoop) are taken by whole clusters (the CTAs of a cluster work on one task
   // together, in the scratch slot of its rank-0 CTA); then every CTA takes tasks
   // [ncoop, ntasks) on its own. The switch happens at the same pop in every CTA of a
@@ -458,11 +472,13 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 2 : 1) k_batch(BArgs a) {
 
     // ---- twiddles
     for (int i = threadIdx.x; i < M0; i += blockDim.x) {
-      W0d[i] = a.tw64[t.tw0 + i];
+      if constexpr (eff) W0e[i] = ff2_from(a.tw64[t.tw0 + i]);
+      else W0d[i] = a.tw64[t.tw0 + i];
       if (f32) reinterpret_cast<float2*>(W0t)[i] = a.tw32[t.tw0 + i];
     }
     for (int i = threadIdx.x; i < M1; i += blockDim.x) {
-      W1d[i] = a.tw64[t.tw1 + i];
+      if constexpr (eff) W1e[i] = ff2_from(a.tw64[t.tw1 + i]);
+      else W1d[i] = a.tw64[t.tw1 + i];
       if (f32) reinterpret_cast<float2*>(W1t)[i] = a.tw32[t.tw1 + i];
     }
     const cpx<T>* W0 = f32 ? W0t : reinterpret_cast<const cpx<T>*>(W0d);
@@ -515,23 +531,29 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 2 : 1) k_batch(BArgs a) {
         const int ni[3] = {ix, iy, 0};
         double2 v[6];
         ahat_eval(sa, ni, ns, v);
-        for (int q = 0; q < t.ncomp; ++q) work[q * plane + e] = v[q];
+        for (int q = 0; q < t.ncomp; ++q) {
+          if constexpr (eff) reinterpret_cast<cpx<E>*>(work)[q * plane + e] = ff2_from(v[q]);
+          else work[q * plane + e] = v[q];
+        }
       }
     }
     team_sync(tm);
     {
       int flist[3] = {0, 1, 2};
-      col_pass<double>(work, work, (long long)M1 * Nxs, (long long)M1 * Nxs, flist, t.ncomp, Nxs, M1, M1, M1,
-                       M1, +1, t.plan1, W1d, Ad, Bd, a.cap, nullptr, tm);
+      cpx<E>* workE = reinterpret_cast<cpx<E>*>(work);
+      col_pass<E>(workE, workE, (long long)M1 * Nxs, (long long)M1 * Nxs, flist, t.ncomp, Nxs, M1, M1, M1, M1, +1,
+                  t.plan1, W1e, Ae, Be, a.cap, nullptr, tm);
       team_sync(tm);
       double dummy[4];
-      row_pass<double>(2, work, (long long)M1 * Nxs, M1, Nxs, 0, M0, nullptr, t.ncomp, 1.0, nullptr, 0,
-                       coef64, t.plan0, W0d, Ad, Bd, a.cap, dummy, tm);
+      row_pass<E>(2, workE, (long long)M1 * Nxs, M1, Nxs, 0, M0, nullptr, t.ncomp, E(1.0), nullptr, 0,
+                  reinterpret_cast<E*>(coef64), t.plan0, W0e, Ae, Be, a.cap, dummy, tm);
       team_sync(tm);
     }
     if (f32) {
-      for (long long i = tm.tid(); i < (long long)t.ncomp * M1 * M0; i += tm.nth())
-        coefT[i] = T(coef64[i]);
+      for (long long i = tm.tid(); i < (long long)t.ncomp * M1 * M0; i += tm.nth()) {
+        if constexpr (eff) coefT[i] = T(ff_norm(reinterpret_cast<const E*>(coef64)[i]).hi);
+        else coefT[i] = T(coef64[i]);
+      }
       team_sync(tm);
     }
 
@@ -816,20 +838,25 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 2 : 1) k_batch(BArgs a) {
           g1 = make_double2(u1.x - g1.x, u1.y - g1.y);
         }
       }
-      x64[(r * 2 + 0) * fld + k] = g0;
-      x64[(r * 2 + 1) * fld + k] = g1;
+      if constexpr (eff) {
+        reinterpret_cast<cpx<E>*>(x64)[(r * 2 + 0) * fld + k] = ff2_from(g0);
+        reinterpret_cast<cpx<E>*>(x64)[(r * 2 + 1) * fld + k] = ff2_from(g1);
+      } else {
+        x64[(r * 2 + 0) * fld + k] = g0;
+        x64[(r * 2 + 1) * fld + k] = g1;
+      }
     }
     if (threadIdx.x == 0) {
       s_flist[0] = 0; s_flist[1] = 1; s_flist[2] = 2; s_flist[3] = 3;
       s_adde[0] = 1; s_adde[1] = 0; s_adde[2] = 0; s_adde[3] = 1;   // e_r in component r of field r
     }
     team_sync(tm);
-    col_pass<double>(x64, work, fld, t2_fs, s_flist, 4, Nh, N1, M1, N1, M1, +1, t.plan1, W1d, Ad, Bd, a.cap,
-                     s_adde, tm);
+    col_pass<E>(reinterpret_cast<cpx<E>*>(x64), reinterpret_cast<cpx<E>*>(work), fld, t2_fs, s_flist, 4, Nh, N1, M1,
+                N1, M1, +1, t.plan1, W1e, Ae, Be, a.cap, s_adde, tm);
     team_sync(tm);
     double eacc[4] = {0.0, 0.0, 0.0, 0.0};
-    row_pass<double>(1, work, t2_fs, M1, Nh, 0, M0, coef64, t.ncomp, 1.0, nullptr, 0, nullptr, t.plan0, W0d, Ad,
-                     Bd, a.cap, eacc, tm);
+    row_pass<E>(1, reinterpret_cast<cpx<E>*>(work), t2_fs, M1, Nh, 0, M0, reinterpret_cast<const E*>(coef64), t.ncomp,
+                E(1.0), nullptr, 0, nullptr, t.plan0, W0e, Ae, Be, a.cap, eacc, tm);
     for (int i = 0; i < 4; ++i) {
       const double s = team_sum(tm, eacc[i], s_red, s_xch, parity);
       if (threadIdx.x == 0 && tm.rank == 0) a.energy[(long long)task * 4 + i] = s * scale;

@@ -262,36 +262,63 @@ __global__ void k_cg_init(CgScalars* cg, const double* partial, int ld, int nblk
   }
 }
 
+// Three block sums at once, each in block_sum's order (thread strides, then the warp
+// shuffle tree, then the warps in order by thread 0): the loads and the shuffles of the
+// right-hand sides overlap instead of running one reduction after another.
+__device__ __forceinline__ void block_sum3(double (&v)[3], double (*red)[32]) {
+  for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) v[c] += __shfl_down_sync(0xffffffffu, v[c], o);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) red[c][wid] = v[c];
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const int nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      double t = 0.0;
+      for (int w = 0; w < nw; ++w) t += red[c][w];
+      v[c] = t;
+    }
+  }
+}
+
 __global__ void k_cg_beta(CgScalars* cg, const double* partial, int ld, int nblk, int nrhs) {
-  __shared__ double red[32];
+  __shared__ double red[3][32];
+  double v[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+  for (int r = 0; r < 3; ++r)
+    if (r < nrhs)
+      for (int i = threadIdx.x; i < nblk; i += blockDim.x) v[r] += partial[(long long)r * ld + i];
+  block_sum3(v, red);
+  if (threadIdx.x != 0) return;
   for (int r = 0; r < nrhs; ++r) {
     if (!cg->active[r]) continue;
-    const double rr = reduce_row(partial + (long long)r * ld, nblk, red);
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      cg->iters[r] += 1;
-      if (!isfinite(rr)) {
-        cg->active[r] = 0;
-        cg->status[r] = cg->guard ? 2 : -2;
-      } else if (rr <= cg->tol2[r]) {
-        cg->active[r] = 0;
-        cg->status[r] = 0;
-        cg->rr[r] = rr;
-      } else if (cg->guard && (rr > 1e4 * cg->rr_min[r] || cg->iters[r] - cg->min_iter[r] > 40)) {
-        // FP32 inner solve diverging or stagnating at its accuracy floor: stop, keep x
-        cg->active[r] = 0;
-        cg->status[r] = 2;
-        cg->rr[r] = rr;
-      } else {
-        cg->beta[r] = rr / cg->rr[r];
-        cg->rr[r] = rr;
-        if (rr < cg->rr_min[r]) {
-          cg->rr_min[r] = rr;
-          cg->min_iter[r] = cg->iters[r];
-        }
+    const double rr = v[r];
+    cg->iters[r] += 1;
+    if (!isfinite(rr)) {
+      cg->active[r] = 0;
+      cg->status[r] = cg->guard ? 2 : -2;
+    } else if (rr <= cg->tol2[r]) {
+      cg->active[r] = 0;
+      cg->status[r] = 0;
+      cg->rr[r] = rr;
+    } else if (cg->guard && (rr > 1e4 * cg->rr_min[r] || cg->iters[r] - cg->min_iter[r] > 40)) {
+      // FP32 inner solve diverging or stagnating at its accuracy floor: stop, keep x
+      cg->active[r] = 0;
+      cg->status[r] = 2;
+      cg->rr[r] = rr;
+    } else {
+      cg->beta[r] = rr / cg->rr[r];
+      cg->rr[r] = rr;
+      if (rr < cg->rr_min[r]) {
+        cg->rr_min[r] = rr;
+        cg->min_iter[r] = cg->iters[r];
       }
     }
-    __syncthreads();
   }
 }
 
