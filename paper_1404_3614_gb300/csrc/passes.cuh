@@ -698,7 +698,20 @@ __global__ void __launch_bounds__(kPassThreads) k_fft_batch(const cpx<T>* in, cp
 template <typename T> int pencil_xc(int M, int X, int C) {
   const size_t sz = sizeof(cpx<T>);
   const size_t fixed = M * sz + 512;
-  const size_t per = (warp_fft_len<T>(M) ? 1 : 2) * (size_t)C * M * sz;
+  if (warp_fft_len<T>(M)) {
+    // warp FFTs: one round of the CTA's lane groups (2 pencils a warp), as many positions as
+    // fill it (a second, partial round left most warps idle: measured 1.4 ms slower a step
+    // on the 16-ball cell's z inverse, and also with two full rounds)
+    const long long slots = (kPassThreads / 32) * (32 / 15);
+    const size_t per1 = (size_t)C * M * sz;
+    long long xc = slots / C > 1 ? slots / C : 1;
+    while (xc > 1 && fixed + (size_t)xc * per1 > kPassSmemMax) --xc;
+    if (fixed + (size_t)xc * per1 > kPassSmemMax) return 0;
+    if (xc > X) xc = X;
+    const long long nch = (X + xc - 1) / xc;
+    return (int)((X + nch - 1) / nch);
+  }
+  const size_t per = 2 * (size_t)C * M * sz;
   long long xc = (long long)((kPassSmemBudget > fixed ? kPassSmemBudget - fixed : 0) / per);
   if (xc < 1) xc = (fixed + per <= kPassSmemMax) ? 1 : 0;
   if (xc > 32) xc = 32;
