@@ -392,6 +392,7 @@ struct Layout {
   int Mmax, maxblk, nblk_energy;
   size_t radtab = 0;            // radial factors of the ball groups (0 bytes: evaluated per frequency)
   size_t coefff = 0;            // float-float coefficient of the mixed residual (0: none)
+  size_t phaseff = 0, sincff = 0, radff = 0;   // float-float spectrum tables (mixed path; 0: none)
   int radgroups = 0, radlen = 0;
   size_t off = 0;
   size_t take(size_t bytes) {
@@ -461,6 +462,11 @@ Layout make_layout(const Geometry& g, int R, size_t elem, int mode) {
     L.coef64 = L.take((size_t)g.ncomp * g.grid * 8);
     L.coef32 = elem == 8 ? L.take((size_t)g.ncomp * g.grid * 4) : 0;
     L.coefff = elem == 8 ? L.take((size_t)g.ncomp * g.grid * 8) : 0;
+    if (elem == 8 && g.bitmap.empty() && !g.incl.empty() && g.incl.size() <= 128) {
+      L.phaseff = L.take(g.incl.size() * 3 * L.Mmax * sizeof(ffloat2));
+      L.sincff = L.take(g.incl.size() * 3 * L.Mmax * sizeof(ffloat));
+      L.radff = L.take(std::max<size_t>((size_t)L.radgroups * L.radlen, 1) * sizeof(ffloat));
+    }
     const size_t fb = (size_t)RC * g.field * elem;
     L.x = L.take(fb);
     L.r = L.take(fb);
@@ -563,6 +569,7 @@ struct Runner {
   int R;
   bool gani = false;   // GaNi: g is the N grid (M = N), coefficient sampled at the grid points
   int coef_side = -1;  // side whose double-grid coefficient build_coefficient left in L.coef64
+  bool spec_ff = false;  // closed-form spectrum in float-float (the mixed path)
 
   template <typename X> X* at(size_t off) const { return reinterpret_cast<X*>(base + off); }
 
@@ -758,7 +765,13 @@ struct Runner {
       KL(launch_axis_tables(sa.nincl, g.d, g.M, L.Mmax, g.invY, sa.incl, at<double2>(L.phase), at<double>(L.sinc),
                             st));
       if (L.radlen > 0) KL(launch_radial_table(sa, at<double>(L.radtab), L.radgroups, st));
-      KL(launch_spectrum(sa, S, st));
+      bool balls = false;
+      for (const hom_inclusion& I : g.incl) balls = balls || I.shape == HOM_BALL;
+      if (spec_ff && L.phaseff != 0 && (!balls || L.radlen > 0))
+        KL(launch_spectrum_ff(sa, (long long)L.radgroups * L.radlen, at<ffloat2>(L.phaseff), at<ffloat>(L.sincff),
+                              at<ffloat>(L.radff), S, st));
+      else
+        KL(launch_spectrum(sa, S, st));
     }
     return coefficient_from_spectrum(coef);
   }
@@ -1249,6 +1262,8 @@ hom_status Runner_solve_mixed(Runner& run, int side, const hom_opts& o, hom_repo
   cudaStream_t st = run.st;
   unsigned char* base = run.base;
   double* coef64 = run.at<double>(L.coef64);
+  // the closed-form spectrum in float-float unless the caller asked for FP64 residuals
+  run.spec_ff = ctx->refine_arith != 1;
   if (run.gani) CKS(run.sample_coefficient(side, coef64));
   else CKS(run.build_coefficient(side, coef64));
   // the residual b - C x64 of every refinement step in float-float (FP64 data, FP32-pair

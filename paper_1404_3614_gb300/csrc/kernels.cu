@@ -887,6 +887,90 @@ __global__ void __launch_bounds__(kSpecRowThreads) k_spectrum_rows(SpecArgs a, d
   }
 }
 
+// The closed-form coefficient spectrum of k_spectrum_rows in float-float arithmetic (pairs of
+// FP32 on the FP32 pipes, about 48 bits; the mixed-precision path, whose operator and
+// residuals run in FP32 and float-float): the same terms in the same order, from float-float
+// copies of the phase, sinc and radial tables (k_tables_ff); the spectrum is written in FP64.
+__global__ void k_tables_ff(const double2* phase, const double* sinc, long long nps, const double* radtab,
+                            long long nrad, ffloat2* phase_ff, ffloat* sinc_ff, ffloat* rad_ff) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nps + nrad;
+       i += (long long)gridDim.x * blockDim.x) {
+    if (i < nps) {
+      phase_ff[i] = ff2_from(phase[i]);
+      sinc_ff[i] = ff_from(sinc[i]);
+    } else {
+      rad_ff[i - nps] = ff_from(radtab[i - nps]);
+    }
+  }
+}
+
+__device__ __forceinline__ ffloat2 ff_cmul(ffloat2 a, ffloat2 b) {
+  ffloat2 r;
+  r.x = fma(a.x, b.x, -(a.y * b.y));
+  r.y = fma(a.x, b.y, a.y * b.x);
+  return r;
+}
+
+__global__ void __launch_bounds__(kSpecRowThreads) k_spectrum_rows_ff(SpecArgs a, const ffloat2* phase,
+                                                                     const ffloat* sinc, const ffloat* radtab,
+                                                                     double2* out) {
+  __shared__ ffloat2 qyz[kSpecRowIncl];
+  __shared__ ffloat syz[kSpecRowIncl];
+  __shared__ ffloat sdA[kSpecRowIncl][6];
+  const long long total = (long long)a.len[0] * a.len[1] * a.len[2];
+  const int nrows = a.len[1] * a.len[2];
+  const ffloat invVol(a.invVol);
+  for (int j = threadIdx.x; j < a.nincl; j += blockDim.x)
+    for (int c = 0; c < a.ncomp; ++c) sdA[j][c] = ffloat(a.incl[j].dA[c]);
+  for (int row = blockIdx.x; row < nrows; row += gridDim.x) {
+    const int iy = row % a.len[1], iz = row / a.len[1];
+    const int nsy = sfreq(iy, a.Nmod[1]), nsz = a.d == 3 ? sfreq(iz, a.Nmod[2]) : 0;
+    const int niy = nsy < 0 ? nsy + a.M[1] : nsy, niz = nsz < 0 ? nsz + a.M[2] : nsz;
+    __syncthreads();   // the previous row's factors are no longer read (and sdA is written)
+    for (int j = threadIdx.x; j < a.nincl; j += blockDim.x) {
+      ffloat2 q = phase[((long long)j * 3 + 1) * a.Mmax + niy];
+      ffloat sy = sinc[((long long)j * 3 + 1) * a.Mmax + niy];
+      if (a.d == 3) {
+        q = ff_cmul(q, phase[((long long)j * 3 + 2) * a.Mmax + niz]);
+        sy = sy * sinc[((long long)j * 3 + 2) * a.Mmax + niz];
+      }
+      qyz[j] = q;
+      syz[j] = sy * invVol;
+    }
+    __syncthreads();
+    for (int ix = threadIdx.x; ix < a.len[0]; ix += blockDim.x) {
+      ffloat2 v[6];
+      for (int q = 0; q < a.ncomp; ++q) v[q] = ffloat2{ffloat(0.f, 0.f), ffloat(0.f, 0.f)};
+      if (ix == 0 && nsy == 0 && nsz == 0)
+        for (int q = 0; q < a.ncomp; ++q) v[q].x = ffloat(a.A0p[q]);
+      ffloat rad(0.f, 0.f);
+      int grp = -1;
+      const int n2 = ix * ix + nsy * nsy + nsz * nsz;
+      for (int j = 0; j < a.nincl; ++j) {
+        const DevIncl& I = a.incl[j];
+        ffloat f;
+        if (I.shape == 0) {
+          f = syz[j] * sinc[((long long)j * 3) * a.Mmax + ix];
+        } else {
+          if (!I.same_as_prev) {
+            ++grp;
+            rad = radtab[(long long)grp * a.radlen + n2];
+          }
+          f = rad * invVol;
+        }
+        const ffloat2 ph = ff_cmul(phase[((long long)j * 3) * a.Mmax + ix], qyz[j]);
+        for (int c = 0; c < a.ncomp; ++c) {
+          const ffloat sc = f * sdA[j][c];
+          v[c].x = fma(sc, ph.x, v[c].x);
+          v[c].y = fma(sc, ph.y, v[c].y);
+        }
+      }
+      const long long e = (long long)row * a.len[0] + ix;
+      for (int c = 0; c < a.ncomp; ++c) out[c * total + e] = ff2_to(v[c]);
+    }
+  }
+}
+
 // One entry per (ball group, integer |k|^2): the group's radial factor at |xi| = sqrt(n) / Y
 __global__ void k_radial_table(SpecArgs a, double* tab, int groups) {
   const long long total = (long long)groups * a.radlen;
@@ -906,6 +990,21 @@ cudaError_t launch_radial_table(const SpecArgs& a, double* radtab, int groups, c
   const long long total = (long long)groups * a.radlen;
   const int blocks = (int)std::min<long long>((total + kThreads - 1) / kThreads, 152 * 16);
   k_radial_table<<<blocks, kThreads, 0, s>>>(a, radtab, groups);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_spectrum_ff(const SpecArgs& a, long long nrad, ffloat2* phase_ff, ffloat* sinc_ff, ffloat* rad_ff,
+                              double2* out, cudaStream_t s) {
+  if (a.nincl > kSpecRowIncl || a.ncomp > 6) return cudaErrorInvalidValue;
+  const long long nps = (long long)a.nincl * 3 * a.Mmax;
+  if (nps + nrad > 0) {
+    long long blocks = (nps + nrad + kThreads - 1) / kThreads;
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    k_tables_ff<<<(int)blocks, kThreads, 0, s>>>(a.phase, a.sinc, nps, a.radtab, nrad, phase_ff, sinc_ff, rad_ff);
+  }
+  const int nrows = a.len[1] * a.len[2];
+  const int blocks = nrows < 152 * 16 ? nrows : 152 * 16;
+  k_spectrum_rows_ff<<<blocks, kSpecRowThreads, 0, s>>>(a, phase_ff, sinc_ff, rad_ff, out);
   return cudaGetLastError();
 }
 

@@ -208,6 +208,11 @@ cudaError_t launch_axis_tables(int nincl, int d, const int* M, int Mmax, const d
 cudaError_t launch_spectrum(const SpecArgs& a, double2* out, cudaStream_t s);
 // a.radtab (writable) from the inclusions: entries of each ball group for n = 0 .. radlen - 1
 cudaError_t launch_radial_table(const SpecArgs& a, double* radtab, int groups, cudaStream_t s);
+// The closed-form spectrum in float-float arithmetic from float-float copies of a's tables
+// (phase_ff, sinc_ff: nincl x 3 x Mmax entries; rad_ff: the nrad entries of a.radtab, which
+// every ball needs); at most 128 inclusions. Written in FP64 like launch_spectrum.
+cudaError_t launch_spectrum_ff(const SpecArgs& a, long long nrad, ffloat2* phase_ff, ffloat* sinc_ff, ffloat* rad_ff,
+                               double2* out, cudaStream_t s);
 // b_r(k) = -Gamma(k) A_hat(k) e_r on Z_N (half), FP64 or FP32, plus |b|^2 partials.
 template <typename T>
 cudaError_t launch_rhs(const SpecArgs& a, int side, int nrhs, int Nh, const int* N, void* b,
