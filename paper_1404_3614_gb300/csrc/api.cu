@@ -666,6 +666,12 @@ struct Runner {
     return HOM_OK;
   }
 
+  bool has_balls() const {
+    for (const hom_inclusion& I : g.incl)
+      if (I.shape == HOM_BALL) return true;
+    return false;
+  }
+
   SpecArgs spec_args(int side) const {
     SpecArgs a{};
     a.d = g.d;
@@ -765,9 +771,7 @@ struct Runner {
       KL(launch_axis_tables(sa.nincl, g.d, g.M, L.Mmax, g.invY, sa.incl, at<double2>(L.phase), at<double>(L.sinc),
                             st));
       if (L.radlen > 0) KL(launch_radial_table(sa, at<double>(L.radtab), L.radgroups, st));
-      bool balls = false;
-      for (const hom_inclusion& I : g.incl) balls = balls || I.shape == HOM_BALL;
-      if (spec_ff && L.phaseff != 0 && (!balls || L.radlen > 0))
+      if (spec_ff && L.phaseff != 0 && (!has_balls() || L.radlen > 0))
         KL(launch_spectrum_ff(sa, (long long)L.radgroups * L.radlen, at<ffloat2>(L.phaseff), at<ffloat>(L.sincff),
                               at<ffloat>(L.radff), S, st));
       else
@@ -1290,7 +1294,19 @@ hom_status Runner_solve_mixed(Runner& run, int side, const hom_opts& o, hom_repo
   // constant field (x = 0 taken from `zero`), negated
   auto form_rhs = [&](double2* zero) -> hom_status {
     if (g.bitmap.empty() && !run.gani) {
-      KL(launch_rhs<double>(sa, side, R, g.Nh, N3, b64, partial, kVecBlocks, st));
+      const double2* hat = nullptr;
+      if (run.spec_ff && L.phaseff != 0 && (L.radlen > 0 || !run.has_balls())) {
+        // A_hat at the N-grid frequencies in float-float (the coefficient's tables), into the
+        // second pass buffer, which nothing holds before the solve
+        SpecArgs sn = sa;
+        sn.len[0] = g.Nh; sn.len[1] = g.N[1]; sn.len[2] = g.d == 3 ? g.N[2] : 1;
+        sn.Nmod[1] = g.N[1]; sn.Nmod[2] = g.d == 3 ? g.N[2] : 1;
+        double2* h = run.at<double2>(L.t2);
+        KL(launch_spectrum_ff(sn, (long long)L.radgroups * L.radlen, run.at<ffloat2>(L.phaseff),
+                              run.at<ffloat>(L.sincff), run.at<ffloat>(L.radff), h, st));
+        hat = h;
+      }
+      KL(launch_rhs<double>(sa, side, R, g.Nh, N3, b64, partial, kVecBlocks, st, hat));
     } else {
       CK(cudaMemsetAsync(zero, 0, n * sizeof(double2), st));
       CKS(run.matvec<double>(zero, b64, coef64, side + 1, nullptr, nullptr, nullptr, 2));

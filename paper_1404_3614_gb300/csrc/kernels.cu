@@ -73,10 +73,11 @@ __global__ void k_spectrum(SpecArgs a, double2* out) {
 
 // b_r(k) = -Gamma(k) A_hat(k) e_r for every right-hand side r < nrhs from one evaluation of
 // A_hat(k) per frequency (the closed form is the costly part: FP64 transcendental functions and
-// a phase product per inclusion), with the |b_r|^2 partials of each r.
+// a phase product per inclusion), with the |b_r|^2 partials of each r. With `hat` the values
+// A_hat(k) are read instead ([ncomp][N2][N1][Nh], e.g. from launch_spectrum_ff on the N grid).
 template <typename T>
 __global__ void __launch_bounds__(kThreads) k_rhs(SpecArgs a, int side, int nrhs, int Nh, int N1, int N2,
-                                                   cpx<T>* b, double* partial, int ld) {
+                                                   cpx<T>* b, double* partial, int ld, const double2* hat) {
   __shared__ double red[32];
   const int C = a.d;
   const long long field = (long long)Nh * N1 * N2;
@@ -89,7 +90,11 @@ __global__ void __launch_bounds__(kThreads) k_rhs(SpecArgs a, int side, int nrhs
     const int ns[3] = {kx, sfreq(iy, N1), a.d == 3 ? sfreq(iz, N2) : 0};
     const int ni[3] = {kx, ns[1] < 0 ? ns[1] + a.M[1] : ns[1], ns[2] < 0 ? ns[2] + a.M[2] : ns[2]};
     double2 Ah[6];
-    ahat_eval(a, ni, ns, Ah);
+    if (hat) {
+      for (int q = 0; q < a.ncomp; ++q) Ah[q] = hat[q * field + e];
+    } else {
+      ahat_eval(a, ni, ns, Ah);
+    }
     double xi[3], n2 = 0.0;
     for (int c = 0; c < C; ++c) {
       xi[c] = ns[c] * a.invY[c];
@@ -1024,10 +1029,10 @@ cudaError_t launch_spectrum(const SpecArgs& a, double2* out, cudaStream_t s) {
 
 template <typename T>
 cudaError_t launch_rhs(const SpecArgs& a, int side, int nrhs, int Nh, const int* N, void* b,
-                       double* partial, int nblk, cudaStream_t s) {
+                       double* partial, int nblk, cudaStream_t s, const double2* hat) {
   if (nrhs < 1 || nrhs > 3) return cudaErrorInvalidValue;
   k_rhs<T><<<nblk, kThreads, 0, s>>>(a, side, nrhs, Nh, N[1], N[2], reinterpret_cast<cpx<T>*>(b), partial,
-                                     nblk);
+                                     nblk, hat);
   return cudaGetLastError();
 }
 
@@ -1361,8 +1366,8 @@ cudaError_t launch_convert_d2f_ff(const double* in, float* out, ffloat* off, lon
 
 // explicit instantiations
 #define HOMB_INST(T)                                                                             \
-  template cudaError_t launch_rhs<T>(const SpecArgs&, int, int, int, const int*, void*, double*, \
-                                     int, cudaStream_t);                                         \
+  template cudaError_t launch_rhs<T>(const SpecArgs&, int, int, int, const int*, void*, double*,  \
+                                     int, cudaStream_t, const double2*);                         \
   template cudaError_t launch_cg_update<T>(void*, void*, const void*, const void*, int, int,     \
                                            long long, int, CgScalars*, double*, int,             \
                                            const double*, int, int, cudaStream_t);               \

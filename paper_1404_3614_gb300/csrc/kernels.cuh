@@ -213,10 +213,11 @@ cudaError_t launch_radial_table(const SpecArgs& a, double* radtab, int groups, c
 // every ball needs); at most 128 inclusions. Written in FP64 like launch_spectrum.
 cudaError_t launch_spectrum_ff(const SpecArgs& a, long long nrad, ffloat2* phase_ff, ffloat* sinc_ff, ffloat* rad_ff,
                                double2* out, cudaStream_t s);
-// b_r(k) = -Gamma(k) A_hat(k) e_r on Z_N (half), FP64 or FP32, plus |b|^2 partials.
+// b_r(k) = -Gamma(k) A_hat(k) e_r on Z_N (half), FP64 or FP32, plus |b|^2 partials; A_hat(k)
+// from the closed form, or read from `hat` ([ncomp][N2][N1][Nh]) when it is given.
 template <typename T>
 cudaError_t launch_rhs(const SpecArgs& a, int side, int nrhs, int Nh, const int* N, void* b,
-                       double* partial, int nblk, cudaStream_t s);
+                       double* partial, int nblk, cudaStream_t s, const double2* hat = nullptr);
 // alpha from the operator pass's p.Cp partials pq_part[rhs][pq_nblk] (row stride pq_ld), then
 // x += alpha p, r -= alpha Cp and the |r|^2 partials into `partial` (a different buffer)
 template <typename T>
