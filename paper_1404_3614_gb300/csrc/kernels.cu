@@ -80,18 +80,21 @@ __global__ void __launch_bounds__(kThreads) k_rhs(SpecArgs a, int side, int nrhs
                                                    cpx<T>* b, double* partial, int ld, const double2* hat) {
   __shared__ double red[32];
   const int C = a.d;
-  const long long field = (long long)Nh * N1 * N2;
+  const int field = Nh * N1 * N2;   // < 2^31 (checked by the launcher)
+  const FastDiv fdNh((uint32_t)Nh), fdN1((uint32_t)N1);
   double acc[3] = {0.0, 0.0, 0.0};
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < field;
-       e += (long long)gridDim.x * blockDim.x) {
-    const int kx = (int)(e % Nh);
-    const int iy = (int)((e / Nh) % N1);
-    const int iz = (int)(e / ((long long)Nh * N1));
+  for (long long el = blockIdx.x * (long long)blockDim.x + threadIdx.x; el < field;
+       el += (long long)gridDim.x * blockDim.x) {
+    const int e = (int)el;
+    const int q1 = fdNh.div(e);
+    const int kx = e - q1 * Nh;
+    const int iz = fdN1.div(q1);
+    const int iy = q1 - iz * N1;
     const int ns[3] = {kx, sfreq(iy, N1), a.d == 3 ? sfreq(iz, N2) : 0};
     const int ni[3] = {kx, ns[1] < 0 ? ns[1] + a.M[1] : ns[1], ns[2] < 0 ? ns[2] + a.M[2] : ns[2]};
     double2 Ah[6];
     if (hat) {
-      for (int q = 0; q < a.ncomp; ++q) Ah[q] = hat[q * field + e];
+      for (int q = 0; q < a.ncomp; ++q) Ah[q] = hat[(long long)q * field + e];
     } else {
       ahat_eval(a, ni, ns, Ah);
     }
@@ -102,6 +105,7 @@ __global__ void __launch_bounds__(kThreads) k_rhs(SpecArgs a, int side, int nrhs
     }
     const double w = kx == 0 ? 1.0 : 2.0;
     const bool nyq = nyquist(ns[1], N1) || (a.d == 3 && nyquist(ns[2], N2));
+    const double inv = n2 > 0.0 ? 1.0 / n2 : 0.0;
 #pragma unroll
     for (int r = 0; r < 3; ++r) {
       if (r >= nrhs) break;
@@ -113,10 +117,11 @@ __global__ void __launch_bounds__(kThreads) k_rhs(SpecArgs a, int side, int nrhs
         dot.x += xi[c] * v[c].x;
         dot.y += xi[c] * v[c].y;
       }
+      dot = make_double2(dot.x * inv, dot.y * inv);
       for (int c = 0; c < C; ++c) {
         double2 g = make_double2(0.0, 0.0);
         if (n2 > 0.0 && !nyq) {
-          const double2 ge = make_double2(xi[c] * dot.x / n2, xi[c] * dot.y / n2);
+          const double2 ge = make_double2(xi[c] * dot.x, xi[c] * dot.y);
           g = side == 0 ? ge : make_double2(v[c].x - ge.x, v[c].y - ge.y);
         }
         const cpx<T> bv = mk<T>(T(-g.x), T(-g.y));
@@ -647,16 +652,20 @@ __global__ void k_combine_fields(double2* x, int nrhs, int d, long long field, C
 
 template <typename T>
 __global__ void k_project_promote(const cpx<T>* x, double2* x64, int nrhs, int d, int Ny, int Nz,
-                                  int Nh, double iy0, double iy1, double iy2, int side) {
-  const long long field = (long long)Nh * Ny * Nz;
+                                  int Nh, double iy0, double iy1, double iy2, int side, FastDiv fdNh, FastDiv fdNy) {
+  // one right-hand side per grid row (blockIdx.y); 32-bit index decoding (field < 2^31, checked
+  // by the launcher) and one FP64 reciprocal a frequency: FP64 division and 64-bit integer
+  // division are many instructions on this GPU
+  const int field = Nh * Ny * Nz;
   const double invY[3] = {iy0, iy1, iy2};
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nrhs * field;
-       t += (long long)gridDim.x * blockDim.x) {
-    const int r = (int)(t / field);
-    const long long e = t - r * field;
-    const int kx = (int)(e % Nh);
-    const int iy = (int)((e / Nh) % Ny);
-    const int iz = (int)(e / ((long long)Nh * Ny));
+  const int r = blockIdx.y;
+  for (long long el = blockIdx.x * (long long)blockDim.x + threadIdx.x; el < field;
+       el += (long long)gridDim.x * blockDim.x) {
+    const int e = (int)el;
+    const int q1 = fdNh.div(e);
+    const int kx = e - q1 * Nh;
+    const int iz = fdNy.div(q1);
+    const int iy = q1 - iz * Ny;
     const int ks[3] = {kx, sfreq(iy, Ny), d == 3 ? sfreq(iz, Nz) : 0};
     double2 u[3];
     double xi[3], n2 = 0.0;
@@ -670,10 +679,12 @@ __global__ void k_project_promote(const cpx<T>* x, double2* x64, int nrhs, int d
       dot.y += xi[c] * u[c].y;
     }
     const bool nyq = nyquist(ks[1], Ny) || (d == 3 && nyquist(ks[2], Nz));
+    const double inv = n2 > 0.0 ? 1.0 / n2 : 0.0;
+    const double2 dn = make_double2(dot.x * inv, dot.y * inv);
     for (int c = 0; c < d; ++c) {
       double2 g = make_double2(0.0, 0.0);
       if (n2 > 0.0 && !nyq) {
-        const double2 ge = make_double2(xi[c] * dot.x / n2, xi[c] * dot.y / n2);
+        const double2 ge = make_double2(xi[c] * dn.x, xi[c] * dn.y);
         g = side == 0 ? ge : make_double2(u[c].x - ge.x, u[c].y - ge.y);
       }
       x64[((long long)r * d + c) * field + e] = g;
@@ -1031,6 +1042,7 @@ template <typename T>
 cudaError_t launch_rhs(const SpecArgs& a, int side, int nrhs, int Nh, const int* N, void* b,
                        double* partial, int nblk, cudaStream_t s, const double2* hat) {
   if (nrhs < 1 || nrhs > 3) return cudaErrorInvalidValue;
+  if ((long long)Nh * N[1] * N[2] >= (1LL << 31)) return cudaErrorInvalidValue;
   k_rhs<T><<<nblk, kThreads, 0, s>>>(a, side, nrhs, Nh, N[1], N[2], reinterpret_cast<cpx<T>*>(b), partial,
                                      nblk, hat);
   return cudaGetLastError();
@@ -1081,11 +1093,13 @@ cudaError_t launch_cg_beta(CgScalars* cg, const double* partial, int ld, int nbl
 template <typename T>
 cudaError_t launch_project_promote(const void* x, double2* x64, int nrhs, int d, int Ny, int Nz,
                                    int Nh, const double* invY, int side, cudaStream_t s) {
-  const long long total = (long long)nrhs * Nh * Ny * Nz;
-  long long blocks = (total + kThreads - 1) / kThreads;
-  if (blocks > 152 * 32) blocks = 152 * 32;
-  k_project_promote<T><<<(int)blocks, kThreads, 0, s>>>(reinterpret_cast<const cpx<T>*>(x), x64, nrhs,
-                                                        d, Ny, Nz, Nh, invY[0], invY[1], invY[2], side);
+  const long long field = (long long)Nh * Ny * Nz;
+  if (field >= (1LL << 31) || nrhs < 1) return cudaErrorInvalidValue;
+  long long blocks = (field + kThreads - 1) / kThreads;
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  k_project_promote<T><<<dim3((unsigned)blocks, (unsigned)nrhs), kThreads, 0, s>>>(
+      reinterpret_cast<const cpx<T>*>(x), x64, nrhs, d, Ny, Nz, Nh, invY[0], invY[1], invY[2], side,
+      FastDiv((uint32_t)Nh), FastDiv((uint32_t)Ny));
   return cudaGetLastError();
 }
 
