@@ -125,6 +125,12 @@ constexpr int kVecBlocks = 304;   // 2 x 152 SMs for the elementwise CG kernels
     CK(expr);             \
     ++ctx->launches;      \
   } while (0)
+// a launcher that starts n kernels
+#define KLN(expr, n)          \
+  do {                        \
+    CK(expr);                 \
+    ctx->launches += (n);     \
+  } while (0)
 
 #define CKS(expr)                                                                              \
   do {                                                                                         \
@@ -772,8 +778,8 @@ struct Runner {
                             st));
       if (L.radlen > 0) KL(launch_radial_table(sa, at<double>(L.radtab), L.radgroups, st));
       if (spec_ff && L.phaseff != 0 && (!has_balls() || L.radlen > 0))
-        KL(launch_spectrum_ff(sa, (long long)L.radgroups * L.radlen, at<ffloat2>(L.phaseff), at<ffloat>(L.sincff),
-                              at<ffloat>(L.radff), S, st));
+        KLN(launch_spectrum_ff(sa, (long long)L.radgroups * L.radlen, at<ffloat2>(L.phaseff), at<ffloat>(L.sincff),
+                              at<ffloat>(L.radff), S, st), 2);
       else
         KL(launch_spectrum(sa, S, st));
     }
@@ -1197,9 +1203,9 @@ struct Runner {
       CKS(matvec<T>(base + L.x, base + L.q, coefT, side + 1, nullptr, nullptr, nullptr, 0));
       ++*matvecs;
       double* ep = at<double>(L.epart);
-      KL(launch_block_rayleigh_ritz(at<double2>(L.x), at<double2>(L.r), at<double2>(L.r), at<double2>(L.q), R, g.d,
+      KLN(launch_block_rayleigh_ritz(at<double2>(L.x), at<double2>(L.r), at<double2>(L.r), at<double2>(L.q), R, g.d,
                                     g.field, g.Nh, ep, ep + (size_t)kVecBlocks * 18, at<double>(L.partial),
-                                    kVecBlocks, st));
+                                    kVecBlocks, st), 3);
       KL(launch_cg_init(cg, at<double>(L.partial), kVecBlocks, kVecBlocks, R, tol * tol, 0.0, 0, st));
     } else if (x0 && sizeof(T) == 8) {   // x = x0 (after b, which GaNi forms from x = 0); r0 = b - C x0
       CK(cudaMemcpyAsync(base + L.x, x0, fb, cudaMemcpyDeviceToDevice, st));
@@ -1302,8 +1308,8 @@ hom_status Runner_solve_mixed(Runner& run, int side, const hom_opts& o, hom_repo
         sn.len[0] = g.Nh; sn.len[1] = g.N[1]; sn.len[2] = g.d == 3 ? g.N[2] : 1;
         sn.Nmod[1] = g.N[1]; sn.Nmod[2] = g.d == 3 ? g.N[2] : 1;
         double2* h = run.at<double2>(L.t2);
-        KL(launch_spectrum_ff(sn, (long long)L.radgroups * L.radlen, run.at<ffloat2>(L.phaseff),
-                              run.at<ffloat>(L.sincff), run.at<ffloat>(L.radff), h, st));
+        KLN(launch_spectrum_ff(sn, (long long)L.radgroups * L.radlen, run.at<ffloat2>(L.phaseff),
+                              run.at<ffloat>(L.sincff), run.at<ffloat>(L.radff), h, st), 2);
         hat = h;
       }
       KL(launch_rhs<double>(sa, side, R, g.Nh, N3, b64, partial, kVecBlocks, st, hat));
@@ -1321,8 +1327,8 @@ hom_status Runner_solve_mixed(Runner& run, int side, const hom_opts& o, hom_repo
     CKS(run.matvec<double>(x64, r64, coef64, side + 1, nullptr, nullptr, nullptr, 0));
     ++*matvecs;
     double* ep = run.at<double>(L.epart);
-    KL(launch_block_rayleigh_ritz(x64, r64, b64, r64, R, g.d, g.field, g.Nh, ep, ep + (size_t)kVecBlocks * 18,
-                                  partial, kVecBlocks, st));
+    KLN(launch_block_rayleigh_ritz(x64, r64, b64, r64, R, g.d, g.field, g.Nh, ep, ep + (size_t)kVecBlocks * 18,
+                                  partial, kVecBlocks, st), 3);
     KL(launch_cg_init(outer, partial, kVecBlocks, kVecBlocks, R, tol * tol, 0.0, 0, st));
   } else if (warm) {   // the start is in b64 (Runner::dual_start): x64 = start, r64 = b - C x64
     CK(cudaMemcpyAsync(x64, b64, n * sizeof(double2), cudaMemcpyDeviceToDevice, st));
@@ -1424,8 +1430,8 @@ hom_status Runner_solve_mixed(Runner& run, int side, const hom_opts& o, hom_repo
   {
     Prof pr(ctx, "energy", st);
     double* part = run.at<double>(L.epart);
-    KL(launch_energy_identity(b64, x64, r64, R, g.d, g.field, g.Nh, coef64, g.ncomp, g.grid, part, kVecBlocks,
-                              part + (size_t)kVecBlocks * 18, kVecBlocks, run.at<double>(L.eout) + side * 9, st));
+    KLN(launch_energy_identity(b64, x64, r64, R, g.d, g.field, g.Nh, coef64, g.ncomp, g.grid, part, kVecBlocks,
+                              part + (size_t)kVecBlocks * 18, kVecBlocks, run.at<double>(L.eout) + side * 9, st), 3);
   }
   return result;
 }
