@@ -296,38 +296,47 @@ __device__ __forceinline__ void block_sum3(double (&v)[3], double (*red)[32]) {
   }
 }
 
+// The beta step: r.r of every right-hand side from the partials, then per right-hand side
+// (one thread each) the stopping tests and beta = r.r / r.r_old. Each thread loads its
+// side's scalars together before it stores any of them, so that the small kernel waits for
+// one round of memory latency instead of a chain of dependent loads.
 __global__ void k_cg_beta(CgScalars* cg, const double* partial, int ld, int nblk, int nrhs) {
   __shared__ double red[3][32];
+  __shared__ double s_rr[3];
   double v[3] = {0.0, 0.0, 0.0};
 #pragma unroll
   for (int r = 0; r < 3; ++r)
     if (r < nrhs)
       for (int i = threadIdx.x; i < nblk; i += blockDim.x) v[r] += partial[(long long)r * ld + i];
   block_sum3(v, red);
-  if (threadIdx.x != 0) return;
-  for (int r = 0; r < nrhs; ++r) {
-    if (!cg->active[r]) continue;
-    const double rr = v[r];
-    cg->iters[r] += 1;
-    if (!isfinite(rr)) {
-      cg->active[r] = 0;
-      cg->status[r] = cg->guard ? 2 : -2;
-    } else if (rr <= cg->tol2[r]) {
-      cg->active[r] = 0;
-      cg->status[r] = 0;
-      cg->rr[r] = rr;
-    } else if (cg->guard && (rr > 1e4 * cg->rr_min[r] || cg->iters[r] - cg->min_iter[r] > 40)) {
-      // FP32 inner solve diverging or stagnating at its accuracy floor: stop, keep x
-      cg->active[r] = 0;
-      cg->status[r] = 2;
-      cg->rr[r] = rr;
-    } else {
-      cg->beta[r] = rr / cg->rr[r];
-      cg->rr[r] = rr;
-      if (rr < cg->rr_min[r]) {
-        cg->rr_min[r] = rr;
-        cg->min_iter[r] = cg->iters[r];
-      }
+  if (threadIdx.x == 0)
+    for (int r = 0; r < 3; ++r) s_rr[r] = v[r];
+  __syncthreads();
+  const int r = threadIdx.x;
+  if (r >= nrhs) return;
+  const int active = cg->active[r], guard = cg->guard, it = cg->iters[r] + 1, min_iter = cg->min_iter[r];
+  const double tol2 = cg->tol2[r], rr_min = cg->rr_min[r], rr_old = cg->rr[r];
+  if (!active) return;
+  const double rr = s_rr[r];
+  cg->iters[r] = it;
+  if (!isfinite(rr)) {
+    cg->active[r] = 0;
+    cg->status[r] = guard ? 2 : -2;
+  } else if (rr <= tol2) {
+    cg->active[r] = 0;
+    cg->status[r] = 0;
+    cg->rr[r] = rr;
+  } else if (guard && (rr > 1e4 * rr_min || it - min_iter > 40)) {
+    // FP32 inner solve diverging or stagnating at its accuracy floor: stop, keep x
+    cg->active[r] = 0;
+    cg->status[r] = 2;
+    cg->rr[r] = rr;
+  } else {
+    cg->beta[r] = rr / rr_old;
+    cg->rr[r] = rr;
+    if (rr < rr_min) {
+      cg->rr_min[r] = rr;
+      cg->min_iter[r] = it;
     }
   }
 }
