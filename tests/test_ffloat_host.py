@@ -7,6 +7,9 @@ checked against exact or long-double references: TwoSum and FastTwoSum are error
 few 2^-48 of the operands' magnitudes, a stage of operations followed by the stores'
 renormalisation keeps that bound, and the division is accurate to about 2^-46.
 
+The warp-level register FFTs of csrc/slab.cuh (the float-float passes at length 225) run as
+15 host threads, one per lane of a lane group, with the warp barrier as a thread barrier.
+
 The block-level FFT engine of csrc/common.cuh is compiled the same way, as one thread that
 runs every butterfly of a stage in turn (its loops stride by the block size, and the barriers
 become no-ops), and its float-float transforms are checked against the DFT's definition
@@ -339,3 +342,127 @@ def test_operator_like_chain_keeps_the_error_at_one_transforms(fft_errors):
     the renormalisation at the stage stores the same chain reaches 4.8e-14 and 6.3e-14: the
     unnormalised low parts grow along the chain."""
     assert max(fft_errors[10:12]) < 4e-14, fft_errors
+
+
+WARP_NAMES = ("dft_reg_zin", "dft_reg_zout", "pencil_fft_inplace", "pencil_fft_fwd_trunc", "pencil_fft_pad_inv")
+
+
+def extract_warp_functions():
+    """The register-FFT device functions of slab.cuh, cut out by name (template line to the
+    matching closing brace): the rest of that header is the GPU-only slab kernel."""
+    src = open(os.path.join(CSRC, "slab.cuh")).read()
+    out = []
+    for name in WARP_NAMES:
+        head = "template <typename T, int R>\n__device__ __forceinline__ void " + name + "("
+        i = src.index(head)
+        j = src.index("{", i)
+        depth = 0
+        for k in range(j, len(src)):
+            if src[k] == "{":
+                depth += 1
+            elif src[k] == "}":
+                depth -= 1
+                if depth == 0:
+                    break
+        out.append(src[i:k + 1])
+    return "\n\n".join(out)
+
+
+WARP_DRIVER = r"""
+#include <barrier>
+#include <cstdio>
+#include <cmath>
+#include <thread>
+#include <vector>
+#include "common.cuh"
+namespace homb {
+#include "warpfft.inc"
+}
+using namespace homb;
+typedef long double LD;
+static const LD PI = 3.141592653589793238462643383279502884L;
+static uint64_t st = 0xD1B54A32D192ED03ull;
+static double urand() { st ^= st << 13; st ^= st >> 7; st ^= st << 17; return (double)(st >> 11) / 4503599627370496.0 - 1.0; }
+static ffloat split(LD v) { const float h = (float)v; return ffloat(h, (float)(v - (LD)h)); }
+static LD val(ffloat a) { return (LD)a.hi + (LD)a.lo; }
+constexpr int R = 15, M = R * R;
+
+// mode 0: full transform; 1: padded inverse (zero band inputs zero, not read); 2: truncating
+// forward (the band's outputs not compared)
+static double run(int dir, int mode) {
+  std::vector<ffloat2> p(M), Wt(M);
+  for (int t = 0; t < M; ++t) {
+    const int k = t / R, l = t - k * R;
+    const LD ang = -2 * PI * (LD)(l * k) / M;
+    Wt[t] = ffloat2{split(std::cos(ang)), split(std::sin(ang))};
+  }
+  std::vector<LD> xr(M), xi(M);
+  for (int n = 0; n < M; ++n) {
+    const bool zero = mode == 1 && ZeroBand<R>::in(n / R);
+    p[n] = zero ? ffloat2{ffloat(0.f, 0.f), ffloat(0.f, 0.f)} : ffloat2{ffloat(urand()), ffloat(urand())};
+    xr[n] = val(p[n].x); xi[n] = val(p[n].y);
+  }
+  std::barrier<> bar(R);
+  g_bar = &bar;
+  std::vector<std::thread> lanes;
+  for (int l = 0; l < R; ++l)
+    lanes.emplace_back([&, l] {
+      if (mode == 1) pencil_fft_pad_inv<ffloat, R>(p.data(), l, Wt.data(), true);
+      else if (mode == 2) pencil_fft_fwd_trunc<ffloat, R>(p.data(), l, Wt.data(), true);
+      else pencil_fft_inplace<ffloat, R>(p.data(), l, Wt.data(), dir, true);
+    });
+  for (auto& t : lanes) t.join();
+  double worst = 0, scale = 0;
+  for (int k = 0; k < M; ++k) {
+    LD sr = 0, si = 0;
+    for (int n = 0; n < M; ++n) {
+      const LD ang = dir * 2 * PI * (LD)((long long)n * k % M) / M;
+      sr += xr[n] * std::cos(ang) - xi[n] * std::sin(ang);
+      si += xr[n] * std::sin(ang) + xi[n] * std::cos(ang);
+    }
+    scale = std::fmax(scale, (double)std::sqrt(sr * sr + si * si));
+    if (mode == 2 && ZeroBand<R>::in(k / R)) continue;
+    const LD er = val(p[k].x) - sr, ei = val(p[k].y) - si;
+    worst = std::fmax(worst, (double)std::sqrt(er * er + ei * ei));
+  }
+  return worst / scale;
+}
+
+int main() {
+  std::printf("%.3e %.3e %.3e %.3e\n", run(-1, 0), run(+1, 0), run(+1, 1), run(-1, 2));
+  return 0;
+}
+"""
+
+WARP_SHIM_EXTRA = r"""
+#include <barrier>
+inline std::barrier<>* g_bar = nullptr;
+inline void __syncwarp() { g_bar->arrive_and_wait(); }
+"""
+
+
+@pytest.fixture(scope="module")
+def warp_errors(tmp_path_factory):
+    cxx = shutil.which("g++") or shutil.which("c++")
+    if cxx is None:
+        pytest.skip("no C++ compiler")
+    d = tmp_path_factory.mktemp("ffloat_warp")
+    (d / "cuda_runtime.h").write_text(SHIM + FFT_SHIM_EXTRA + WARP_SHIM_EXTRA)
+    (d / "warpfft.inc").write_text(extract_warp_functions())
+    (d / "main.cpp").write_text(WARP_DRIVER)
+    exe = d / "warpcheck"
+    r = subprocess.run([cxx, "-std=c++20", "-O1", "-ffp-contract=off", "-fno-fast-math", "-pthread", "-I", str(d),
+                        "-I", CSRC, str(d / "main.cpp"), "-o", str(exe)], capture_output=True, text=True)
+    if r.returncode != 0 and "barrier" in r.stderr:
+        pytest.skip("no C++20 std::barrier")
+    assert r.returncode == 0, r.stderr
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split()
+    return [float(v) for v in out]
+
+
+def test_warp_register_ffts_at_225(warp_errors):
+    """The lane-group FFT of length 225 = 15 x 15 (two register radix-15 stages, twiddles, the
+    exchange through the pencil), forward and inverse, its padded inverse (the zero band's input
+    rows not read) and its truncating forward (the band's output rows not computed): within
+    5e-14 of the DFT's scale, as the block-level engine."""
+    assert max(warp_errors) < 5e-14, warp_errors
