@@ -470,7 +470,8 @@ hom_status hom_fft(hom_ctx* ctx, int32_t M, int32_t precision, int32_t dir, int3
  * an unpredictable moment. Instead of a workspace it uses one scratch array that lives
  * in the library itself (HOM_NOALLOC_SCRATCH_BYTES = 32 MiB of device memory, held on
  * every GPU that loads the library until the process exits).
- * Arguments and results are those of hom_matvec without d_workspace/workspace_bytes.
+ * Arguments and results are those of hom_matvec without d_workspace/workspace_bytes, for
+ * precision HOM_FP64 or HOM_FP32 (HOM_FF is refused with HOM_ERR_INVALID_ARG).
  * - Problems whose scratch (twiddle and inclusion tables plus the two intermediate
  *   double-grid buffers) exceeds the array are rejected with HOM_ERR_WORKSPACE and a
  *   message giving the bytes needed; e.g. the 3D N = 41 cube with 3 fields in FP64 fits.
